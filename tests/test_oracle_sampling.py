@@ -1,0 +1,112 @@
+"""Pins of the oracle's AMM sampler (RANDSAMPLE / BasicMatrixMultiplication, Section 3.2)."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import synth
+from oracle import philox
+from oracle import tucker as ot
+
+
+def test_quantize_weights_hand_values():
+    w = np.array([0.0, 1.0, 0.5, 1e-9, 0.25 + 2.0 ** -30])
+    W = ot.quantize_weights(w)
+    assert W.tolist() == [0, 1 << 24, 1 << 23, 1, (1 << 22) + 1]
+    assert ot.quantize_weights(np.zeros(5)).tolist() == [1] * 5
+
+
+def _bucket_table(W):
+    """Brute force: the index owning each integer v in [0, S)."""
+    table = []
+    for j, wj in enumerate(W.tolist()):
+        table += [j] * int(wj)
+    return table
+
+
+@pytest.mark.parametrize("kind", ["mixed", "spiky", "ones"])
+def test_inverse_cdf_against_expanded_table(kind):
+    W = synth.sample_weights(40, seed=3, kind=kind) % np.uint64(50)   # keep S small
+    if int(W.sum()) == 0:
+        W[0] = 1
+    table = _bucket_table(W)
+    S = len(table)
+    T = 300
+    idx, scale = ot.randsample(W, T, seed=5, mode=1)
+    words = philox.sampling_words(5, 1, T)
+    for t in range(T):
+        v = (words[t] * S) >> 64
+        assert idx[t] == table[v]
+        p = int(W[idx[t]]) / S
+        assert scale[t] == 1.0 / math.sqrt(T * p)
+        assert W[idx[t]] > 0       # zero-weight fibers are never drawn
+
+
+def test_sampled_frequencies_follow_p():
+    W = np.array([1, 2, 3, 4, 0, 10], dtype=np.uint64)
+    T = 20000
+    idx, _ = ot.randsample(W, T, seed=11, mode=0)
+    counts = np.bincount(idx, minlength=len(W))
+    p = W.astype(float) / W.sum()
+    mask = p > 0
+    chi = stats.chisquare(counts[mask], T * p[mask])
+    assert chi.pvalue > 1e-4
+    assert counts[4] == 0
+
+
+@pytest.mark.parametrize("prob", [ot.PROB_NEARLY_OPTIMAL, ot.PROB_UNIFORM])
+@pytest.mark.parametrize("T", [2, 3])
+def test_amm_unbiased_by_enumeration(prob, T):
+    """E[C' C'^T] = M M^T exactly: enumerate every index tuple with its probability."""
+    M = np.random.default_rng(2).standard_normal((3, 4))
+    M[:, 2] *= 0.01                          # uneven fiber norms
+    W = ot.quantize_weights(ot.fiber_weights(M, prob))
+    S = int(W.sum())
+    p = W.astype(np.float64) / S
+    acc = np.zeros((3, 3))
+    for tup in itertools.product(range(4), repeat=T):
+        pr = np.prod([p[j] for j in tup])
+        if pr == 0:
+            continue
+        scale = np.array([1.0 / math.sqrt(T * p[j]) for j in tup])
+        C = ot.amm_matrix(M, np.array(tup), scale)
+        acc += pr * (C @ C.T)
+    assert np.allclose(acc, M @ M.T, rtol=1e-13, atol=1e-13)
+
+
+def test_amm_error_shrinks_like_inverse_sqrt_T():
+    """Corollary 1 / Lemmas 5-6: E||M M^T - C'C'^T||_F decays like 1/sqrt(T)."""
+    rng = np.random.default_rng(0)
+    M = rng.standard_normal((20, 400)) * (1 + 5 * rng.random(400))
+    ref = M @ M.T
+    Ts = [25, 100, 400]
+    errs = []
+    for T in Ts:
+        W = ot.quantize_weights(ot.fiber_weights(M, ot.PROB_NEARLY_OPTIMAL))
+        e = []
+        for seed in range(120):
+            idx, scale = ot.randsample(W, T, seed=seed, mode=0)
+            C = ot.amm_matrix(M, idx, scale)
+            e.append(np.linalg.norm(ref - C @ C.T))
+        errs.append(np.mean(e))
+    slope = np.polyfit(np.log(Ts), np.log(errs), 1)[0]
+    assert -0.6 < slope < -0.4
+
+
+def test_nearly_optimal_beats_uniform_on_skewed_fibers():
+    rng = np.random.default_rng(1)
+    M = rng.standard_normal((10, 500))
+    M[:, :10] *= 50.0                        # a few heavy fibers
+    ref = M @ M.T
+    out = {}
+    for prob in (ot.PROB_NEARLY_OPTIMAL, ot.PROB_UNIFORM):
+        W = ot.quantize_weights(ot.fiber_weights(M, prob))
+        e = []
+        for seed in range(40):
+            idx, scale = ot.randsample(W, 100, seed=seed, mode=0)
+            C = ot.amm_matrix(M, idx, scale)
+            e.append(np.linalg.norm(ref - C @ C.T))
+        out[prob] = np.mean(e)
+    assert out[ot.PROB_NEARLY_OPTIMAL] < out[ot.PROB_UNIFORM]
