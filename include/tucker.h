@@ -1,0 +1,211 @@
+/*
+ * tucker.h - C ABI of the GB300 (sm_103a) randomized Tucker library.
+ *
+ * Che, Wei, Yan, "Efficient algorithms for Tucker decomposition via
+ * approximate matrix multiplication" (arXiv 2303.11612).
+ *
+ * Problem 1 (Section 1): given a tensor A of size I_1 x ... x I_N and target
+ * multilinear ranks R_n (the paper's mu_n), find orthonormal U_n (I_n x R_n)
+ * and the core G = A x_1 U_1^T ... x_N U_N^T (R_1 x ... x R_N).
+ *
+ * Conventions shared by every entry point
+ *  - Tensors are dense, element (i_1, ..., i_N) at offset
+ *    i_1 + I_1 (i_2 + I_2 (i_3 + ...)) (i_1 fastest), the order implied by the
+ *    mode-n unfolding of Section 2. Mode indices are 0-based (mode 0 = the
+ *    paper's mode 1). Matrices are column-major with leading dimension = rows.
+ *  - The mode-n unfolding A_(n) is I_n x J_n with J_n = prod_{m != n} I_m; its
+ *    column j = i_1 + I_1 (i_2 + ...) over the modes m != n in increasing order
+ *    (Section 2). It is never materialised.
+ *  - Pointers may be device or host memory (the library asks the CUDA driver):
+ *    host buffers are staged through device copies inside the call. All
+ *    buffers are owned by the caller; the library keeps no pointer after the
+ *    call returns. A is never written.
+ *  - Work is issued on opts->stream (NULL = the legacy default stream). Unless
+ *    TUCKER_FLAG_ASYNC is set the call synchronises that stream before it
+ *    returns and reports device-side failures (Cholesky breakdown that could not
+ *    be repaired, non-finite values) in its status. With TUCKER_FLAG_ASYNC the
+ *    call returns after enqueueing; the device status is then read by
+ *    tucker_last_device_status().
+ *  - Scratch memory: opts->workspace / workspace_bytes (device memory of at
+ *    least tucker_workspace_size() bytes, 256-byte aligned) when given;
+ *    otherwise the library allocates it from the stream-ordered pool and frees
+ *    it before returning.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit
+ *    seed, counter (block_lo, block_hi, stream, 0) with stream = purpose << 8 |
+ *    mode; purpose 0 = Gaussian test matrix, 1 = fiber-sampling uniforms. A
+ *    word x maps to u = ((x >> 9) + 0.5) 2^-23 in (0, 1); Gaussian element e
+ *    uses block e / 4, lane e % 4 and Box-Muller on the lane pairs (0,1), (2,3).
+ *  - Errors: argument errors are detected before any launch and return
+ *    TUCKER_ERR_INVALID_ARG without side effects.
+ */
+#ifndef TUCKER_H
+#define TUCKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TUCKER_OK = 0,
+    TUCKER_ERR_INVALID_ARG = 1,
+    TUCKER_ERR_OOM = 2,
+    TUCKER_ERR_CUDA = 3,
+    TUCKER_ERR_NUMERICAL = 4,   /* non-finite values, or a breakdown not repaired */
+    TUCKER_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    TUCKER_ERR_UNSUPPORTED = 6, /* valid request outside what is built (e.g. a size limit) */
+    TUCKER_ERR_BUDGET = 7       /* serving: request larger than the memory budget */
+} tucker_status;
+
+/* Sampling probabilities for approximate matrix multiplication (remark after
+ * Algorithm 3): nearly-optimal p_j proportional to ||fiber_j||^2 (the optimal
+ * probabilities for A_(n) A_(n)^T), or uniform p_j = 1 / J_n. */
+typedef enum { TUCKER_PROB_NEARLY_OPTIMAL = 0, TUCKER_PROB_UNIFORM = 1 } tucker_prob;
+
+/* Element type of tensors, factors and the core. The sketch and the mode-n
+ * products compute in this type; Gram matrices and Cholesky factors in FP64. */
+typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
+
+/* Which sketch is taken.
+ *  PAPER (default): C_n = (A_(n) A_(n)^T)^q Omega_n, Omega_n I_n x L_n Gaussian
+ *    (Algorithms 1, 2, 4, 5; Strategy A of the remark after Algorithm 1).
+ *  RANGE: Y = A_(n) Omega with Omega J_n x L_n, then q times
+ *    Y = A_(n) (A_(n)^T orth(Y)) (the form the introduction contrasts, item (c)).
+ * Either way U_n = the R_n leading left singular vectors of the sketch (remark
+ * after Algorithm 5), each column's largest-magnitude entry made positive. */
+typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1 } tucker_form;
+
+/* Arithmetic of the sketch / power products. FP32 = exact FP32 FMA. */
+typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2 } tucker_sketch_prec;
+
+#define TUCKER_FLAG_ASYNC 0x1u
+
+typedef struct {
+    uint32_t struct_size;   /* sizeof(tucker_opts) */
+    int32_t form;           /* tucker_form */
+    int32_t prec;           /* tucker_sketch_prec (TUCKER_SK_FP32 when not built) */
+    uint32_t flags;         /* TUCKER_FLAG_* */
+    double alpha;           /* T_n = ceil(alpha J_n) when c == 0 and alpha > 0 (Section 3.3) */
+    void* stream;           /* cudaStream_t; NULL = legacy default stream */
+    void* workspace;        /* device scratch, may be NULL */
+    size_t workspace_bytes;
+    double* rel_error;      /* host out, may be NULL: RE = sqrt(1 - ||G||^2/||A||^2) (Eq. 8) */
+    int64_t* const* sample_idx; /* may be NULL: N device/host arrays receiving the T_n
+                                   sampled fiber indices of each mode (AMM only) */
+} tucker_opts;
+
+/* ---------------------------------------------------------------- drivers */
+
+/* Randomized T-HOSVD with the power scheme: Algorithm 1 (c == 0 and alpha == 0)
+ * or Algorithm 4 (c > 0: T_n = min(c, J_n) fibers of A_(n) sampled, Section 3.2).
+ *   A      : tensor, dims[0] x ... x dims[N-1], element type dt (read only)
+ *   dims   : host array of N extents, 1 <= N <= 8
+ *   ranks  : host array of N target ranks, 1 <= R_n <= I_n
+ *   P      : oversampling (the paper's K), >= 0; L_n = min(R_n + P, I_n)
+ *   q      : power steps, >= 1
+ *   c      : AMM sample count (0 = no sampling)
+ *   prob   : sampling probabilities (ignored when no sampling)
+ *   seed   : Philox key
+ *   U      : host array of N pointers, U[n] receives I_n x R_n (column-major)
+ *   G      : receives the R_1 x ... x R_N core (r_1 fastest)
+ *   opts   : may be NULL (defaults: paper form, FP32 sketch, synchronous) */
+tucker_status tucker_rthosvd(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                             const int32_t* ranks, int32_t P, int32_t q, int64_t c,
+                             tucker_prob prob, uint64_t seed, void* const* U, void* G,
+                             const tucker_opts* opts);
+
+/* Randomized ST-HOSVD with the power scheme: Algorithm 2 (no sampling) or
+ * Algorithm 5 (sampling), processing order 1..N (Section 4). After U_n the
+ * working tensor becomes B x_n U_n^T; the last one is the core. Arguments as
+ * for tucker_rthosvd; for mode n, J_n = R_1 ... R_{n-1} I_{n+1} ... I_N. */
+tucker_status tucker_rsthosvd(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                              const int32_t* ranks, int32_t P, int32_t q, int64_t c,
+                              tucker_prob prob, uint64_t seed, void* const* U, void* G,
+                              const tucker_opts* opts);
+
+/* Scratch bytes a driver call needs. which = 0 (T-HOSVD) or 1 (ST-HOSVD). */
+tucker_status tucker_workspace_size(int which, tucker_dtype dt, const int64_t* dims, int N,
+                                    const int32_t* ranks, int32_t P, int32_t q, int64_t c,
+                                    const tucker_opts* opts, size_t* bytes);
+
+const char* tucker_status_string(tucker_status s);
+
+/* Device status word of the last TUCKER_FLAG_ASYNC call on this host thread
+ * (synchronises its stream first). */
+tucker_status tucker_last_device_status(void);
+
+/* ---------------------------------------------------------------- steps
+ * One entry point per step of the path, for tests and for callers that build
+ * their own pipelines. "mode view" arguments (A, dt, dims, N, mode) describe
+ * the mode-n unfolding of a tensor as above. */
+
+/* Gaussian test matrix (Algorithm 1, "generate a standard Gaussian matrix"):
+ * out (rows x cols, column-major, dt) gets element (i, l) = Gaussian element
+ * e = i * cols + l of Philox stream `stream_id` under `seed`. */
+tucker_status tucker_gaussian(void* out, tucker_dtype dt, int64_t rows, int64_t cols,
+                              uint64_t seed, uint32_t stream_id, const tucker_opts* opts);
+
+/* One power step of Strategy A fused into a single pass over the tensor:
+ * X_out = A_(n) (A_(n)^T X_in), X_in and X_out I_n x L column-major. */
+tucker_status tucker_power_step(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                                int mode, const void* X_in, int64_t L, void* X_out,
+                                const tucker_opts* opts);
+
+/* Range-form sketch Y = A_(n) Omega (Omega J_n x L Gaussian, element (j, l) =
+ * e = j * L + l of stream (0 << 8 | mode)), Omega generated inside the kernel. */
+tucker_status tucker_range_sketch(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                                  int mode, int64_t L, uint64_t seed, void* Y,
+                                  const tucker_opts* opts);
+
+/* Squared fiber norms w_j = ||A_(n)(:, j)||^2, j < J_n (FP64 out; the sum is
+ * carried in paired FP32 words or FP64, about 2^-44 relative). */
+tucker_status tucker_fiber_norms(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                                 int mode, double* w, const tucker_opts* opts);
+
+/* Integer sampling weights W_j = ceil(w_j / max(w) * 2^24) (0 where w_j == 0;
+ * all ones if every w_j is 0), or all ones for uniform probabilities. */
+tucker_status tucker_quantize_weights(const double* w, int64_t J, tucker_prob prob,
+                                      uint64_t* W, const tucker_opts* opts);
+
+/* RANDSAMPLE(T, p) with p_j = W_j / S, S = sum W (Section 3.2): draw t uses the
+ * 64-bit Philox word r_t of stream (1 << 8 | mode) (block t / 2; words (x0,x1)
+ * for even t, (x2,x3) for odd t), v = floor(r_t S / 2^64), idx[t] = the least j
+ * with W_0 + ... + W_j > v, scale[t] = 1 / sqrt(T W_idx / S). Bit-exact. */
+tucker_status tucker_sample_fibers(const uint64_t* W, int64_t J, int64_t T, uint64_t seed,
+                                   int mode, int64_t* idx, double* scale,
+                                   const tucker_opts* opts);
+
+/* C' = A_(n) S (Algorithms 4/5): column t of C' (I_n x T, column-major, dt) is
+ * scale[t] times fiber idx[t]. */
+tucker_status tucker_gather_fibers(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                                   int mode, const int64_t* idx, const double* scale, int64_t T,
+                                   void* Cp, const tucker_opts* opts);
+
+/* U (I x R, column-major, dt) = the R leading left singular vectors of the
+ * sketch C (I x L, column-major, dt), largest-magnitude entry of each column
+ * positive (remark after Algorithm 5). FP64 CholeskyQR2 (shifted CholeskyQR3
+ * when the Gram matrix is numerically singular) then a one-sided Jacobi SVD of
+ * the triangular factor. */
+tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, int64_t L,
+                                    int64_t R, void* U, const tucker_opts* opts);
+
+/* Mode-n product out = A x_n M (Section 2) with M given by M_ptr, a column-major
+ * matrix: transpose == 0: M is K x I_n (out has K in mode n);
+ *         transpose == 1: M_ptr holds I_n x K and M is its transpose
+ *         (out = A x_n M_ptr^T, the truncation B x_n U^T of Algorithm 2). */
+tucker_status tucker_ttm(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode,
+                         const void* M_ptr, int64_t K, int transpose, void* out,
+                         const tucker_opts* opts);
+
+/* RE = ||A - G x_1 U_1 ... x_N U_N||_F / ||A||_F (Eq. 8) by explicit
+ * reconstruction on the device; *re receives it (host pointer). */
+tucker_status tucker_relative_error(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                                    const int32_t* ranks, void* const* U, const void* G,
+                                    double* re, const tucker_opts* opts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUCKER_H */

@@ -22,8 +22,9 @@ the oracle consume the same random numbers:
   * Gaussian element e uses block e // 4 and lane e % 4: the words
     (x0, x1) give z0 = r cos(2 pi u1), z1 = r sin(2 pi u1) with
     r = sqrt(-2 ln u0), and (x2, x3) give z2, z3 the same way;
-  * a word x maps to the uniform u = ((x >> 8) + 0.5) * 2^-24, which lies
-    strictly inside (0, 1) and is exact in FP32 and FP64;
+  * a word x maps to the uniform u = ((x >> 9) + 0.5) * 2^-23, which lies
+    strictly inside (0, 1) and is exact in FP32 and FP64 (24 significant
+    bits; a 24-bit integer plus one half would need 25);
   * sampling draw t uses block t // 2 and the 64-bit word
     r = x_lo | x_hi << 32 from (x0, x1) for even t and (x2, x3) for odd t.
 """
@@ -80,8 +81,8 @@ def blocks(seed: int, stream: int, block_idx):
 
 
 def word_to_uniform(x):
-    """u = ((x >> 8) + 0.5) * 2^-24 in FP64."""
-    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(8)).astype(np.float64) + 0.5) * 2.0 ** -24
+    """u = ((x >> 9) + 0.5) * 2^-23 in FP64."""
+    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(9)).astype(np.float64) + 0.5) * 2.0 ** -23
 
 
 def gaussian_elements(seed: int, stream: int, count: int) -> np.ndarray:

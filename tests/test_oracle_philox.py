@@ -31,10 +31,14 @@ def test_philox_known_answers(row):
 
 
 def test_uniform_map_endpoints():
-    # u = ((x >> 8) + 0.5) 2^-24: strictly inside (0, 1), symmetric about 1/2
-    assert philox.word_to_uniform(0) == 2.0 ** -25
-    assert philox.word_to_uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -25
-    assert philox.word_to_uniform(0x80000000) == 0.5 + 2.0 ** -25
+    # u = ((x >> 9) + 0.5) 2^-23: strictly inside (0, 1), symmetric about 1/2,
+    # and every value is an FP32 number (24 significant bits)
+    assert philox.word_to_uniform(0) == 2.0 ** -24
+    assert philox.word_to_uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    assert philox.word_to_uniform(0x80000000) == 0.5 + 2.0 ** -24
+    x = np.array([0, 1 << 9, 0x7FFFFFFF, 0xFFFFFE00, 0xFFFFFFFF], dtype=np.uint64)
+    u = philox.word_to_uniform(x)
+    assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
 
 
 def test_gaussian_moments_and_ks():
