@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the randomized ST-HOSVD path on GB300.
+
+Workload (one "step" = one batch covering every step of the path): randomized
+ST-HOSVD (Algorithms 2 and 5) with R_n = 20, P = 10 on two synthetic
+400 x 400 x 400 FP32 tensors, a Tucker tensor with a 20^3 N(0,1) core plus
+noise at 1e-2 relative Frobenius norm and the Hilbert tensor
+1 / (i + j + k - 2):
+  1. low-rank, q = 1, no sampling               (Algorithm 2)
+  2. low-rank, q = 1, c = 4000, nearly-optimal  (Algorithm 5)
+  3. Hilbert,  q = 2, no sampling               (Algorithm 2)
+  4. Hilbert,  q = 1, c = 4000, uniform         (Algorithm 5)
+value = decompositions per second with the tensors resident in HBM;
+e2e = the same through the C ABI with pinned host buffers (host->device copy of
+each input and device->host copy of the factors and core inside the timed
+region). Each tensor is 256 MB, larger than the 129 MB L2, so no flush is
+needed between steps.
+
+--impl reference times the FP64 CPU oracle on the same workload (one
+decomposition per step, cycling through the four variants).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (400, 400, 400)
+RANKS = (20, 20, 20)
+P = 10
+SEED = 0
+VARIANTS = [
+    dict(name="lowrank_q1", tensor="lowrank", q=1, c=0, prob="uniform"),
+    dict(name="lowrank_q1_amm4000_nearly_optimal", tensor="lowrank", q=1, c=4000, prob="nearly_optimal"),
+    dict(name="hilbert_q2", tensor="hilbert", q=2, c=0, prob="uniform"),
+    dict(name="hilbert_q1_amm4000_uniform", tensor="hilbert", q=1, c=4000, prob="uniform"),
+]
+BASELINE_METRIC = "decomps/s & sketch HBM GB/s, BF16 vs FP32 at equal rel err; serving p50/p99 ms"
+WORKLOAD = ("randomized ST-HOSVD, 400x400x400 FP32 (Tucker core 20^3 + 1e-2 noise, and Hilbert), "
+            "R=20 P=10, batch of 4: q=1; q=1 AMM c=4000 nearly-optimal; Hilbert q=2; Hilbert q=1 AMM c=4000 uniform")
+
+
+def tensors():
+    import numpy as np
+    import synth
+    lowrank = synth.lowrank_noise(DIMS, RANKS, rel_noise=1e-2, seed=SEED, dtype=np.float32)
+    hilbert = synth.hilbert(DIMS, dtype=np.float32)
+    return {"lowrank": synth.flat(lowrank), "hilbert": synth.flat(hilbert)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def oracle_decomposition(host, v):
+    import numpy as np
+    import synth
+    from oracle import tucker as ot
+    A = synth.from_flat(host[v["tensor"]], DIMS).astype(np.float64)
+    return ot.rsthosvd(A, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(host, budget_s=20.0):
+    """The oracle as it stands, on this host's cores, over whole decompositions of
+    the batch (in order) until the time budget is used (at least one)."""
+    done, t0 = 0, time.perf_counter()
+    names = []
+    while True:
+        v = VARIANTS[done % len(VARIANTS)]
+        oracle_decomposition(host, v)
+        names.append(v["name"])
+        done += 1
+        if time.perf_counter() - t0 > budget_s or done >= 2 * len(VARIANTS):
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "decomps/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{done} whole 400^3 decompositions of the batch ({', '.join(names)}) in {dt:.1f} s, "
+                      f"numpy FP64 with its BLAS on all host cores"}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    host = tensors()
+    for k in range(args.warmup):
+        oracle_decomposition(host, VARIANTS[k % len(VARIANTS)])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle_decomposition(host, VARIANTS[k % len(VARIANTS)])
+    dt = time.perf_counter() - t0
+    val = args.steps / dt
+    line = {"impl": "reference", "metric": "decomps/s", "value": val, "unit": "decomps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "baseline_metric": BASELINE_METRIC,
+            "config": {"workload": WORKLOAD + " (reference: FP64 CPU oracle, one decomposition per step)"},
+            "cpu_baseline": {"value": val, "unit": "decomps/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"{args.steps} decompositions cycling through the 4 variants"},
+            "e2e": {"value": val, "unit": "decomps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+    import paper_2303_11612_gb300 as tk
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    host = tensors()
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+    ws_bytes = max(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"]) for v in VARIANTS)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    outs = [([tk.factor_tensor(I, R, torch.float32, "cuda") for I, R in zip(DIMS, RANKS)],
+             torch.empty(int(np.prod(RANKS)), dtype=torch.float32, device="cuda")) for _ in VARIANTS]
+    houts = [([torch.empty((R, I), dtype=torch.float32).pin_memory().t() for I, R in zip(DIMS, RANKS)],
+              torch.empty(int(np.prod(RANKS)), dtype=torch.float32).pin_memory()) for _ in VARIANTS]
+
+    def step():
+        for v, out in zip(VARIANTS, outs):
+            tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
+                        workspace=ws, stream=stream, out=out, flags=tk.FLAG_ASYNC)
+
+    def step_e2e():
+        for v, out in zip(VARIANTS, houts):
+            tk.rsthosvd(pinned[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
+                        stream=stream, out=out)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # correctness of what is timed: every variant succeeds and reports its RE
+    res = {}
+    for v in VARIANTS:
+        _, _, re = tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
+                               want_rel_error=True)
+        res[v["name"]] = re
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    if tk.last_device_status() != 0:
+        raise RuntimeError("device status not OK after warm-up")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    tk.profile_enable(True)
+    n0 = tk.launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    stream.synchronize()
+    n1 = tk.launch_count()
+    barrier()
+    clk = clocks.stop()
+    st = tk.last_device_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} in the timed region")
+    ms = ev0.elapsed_time(ev1)
+    prof = {k: tk.profile_read(k) for k in ("power", "ttm", "gather", "norms")}
+    tk.profile_enable(False)
+    ms = max_over_ranks(ms)
+    decomps = len(VARIANTS) * args.steps * world
+    value = decomps / (ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    for _ in range(1):
+        step_e2e()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, args.steps // 4)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        step_e2e()
+    e1.record(stream)
+    stream.synchronize()
+    wall = time.perf_counter() - t0
+    e2e_s = max_over_ranks(max(wall, e0.elapsed_time(e1) / 1e3))
+    h2d = sum(host[v["tensor"]].nbytes for v in VARIANTS)
+    d2h = sum((sum(I * R for I, R in zip(DIMS, RANKS)) + int(np.prod(RANKS))) * 4 for _ in VARIANTS)
+
+    peaks, peak_kind = load_peaks()
+    pw_n, pw_ms, pw_bytes, pw_flops = prof["power"]
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12    # FFMA lanes x 2 flops x max SM clock
+    achieved_tflops = pw_flops / (pw_ms / 1e3) / 1e12 if pw_ms > 0 else 0.0
+    achieved_gbs = pw_bytes / (pw_ms / 1e3) / 1e9 if pw_ms > 0 else 0.0
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f).get("power_kernel_400cubed")
+        src = open(os.path.join(ROOT, "paper_2303_11612_gb300", "csrc", "kernels_sketch.cu"), "rb").read()
+        import hashlib
+        if tr and tr.get("source_sha256") == hashlib.sha256(src).hexdigest():
+            traffic = tr["dram_bytes_per_launch"]
+    except Exception:
+        traffic = None
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tflops / fp32_peak_tflops, "traffic": traffic,
+                "kernel": "power_kernel (fused A(A^T X) pass, FP32 FFMA)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "launches": pw_n, "ms_per_launch": pw_ms / max(pw_n, 1),
+                "algorithmic_bytes_per_launch": pw_bytes / max(pw_n, 1),
+                "hbm_gbs": achieved_gbs, "hbm_frac": achieved_gbs / peaks["hbm_gbs"],
+                "hbm_peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind}
+    others = {}
+    for k in ("ttm", "gather", "norms"):
+        n, kms, b, f = prof[k]
+        if n:
+            others[k] = {"launches": n, "ms_per_launch": kms / n, "gbs": b / (kms / 1e3) / 1e9,
+                         "hbm_frac": b / (kms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                         "tflops": f / (kms / 1e3) / 1e12}
+    line = {"metric": "decomps/s", "value": value, "unit": "decomps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "baseline_metric": BASELINE_METRIC,
+            "config": {"workload": WORKLOAD, "tensor_bytes": 256_000_000,
+                       "l2": "inputs larger than L2 (256 MB per tensor), no flush",
+                       "parallelism": "replicas (each rank decomposes its own batch)" if world > 1 else "single GPU",
+                       "sketch": "paper form, FP32 SIMT"},
+            "e2e": {"value": len(VARIANTS) * e2e_steps * world / e2e_s, "unit": "decomps/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": n1 - n0,
+            "roofline": roofline, "kernels": others,
+            "sketch_hbm_gbs": achieved_gbs,
+            "rel_error": res, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(host)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

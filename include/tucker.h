@@ -205,6 +205,31 @@ tucker_status tucker_relative_error(const void* A, tucker_dtype dt, const int64_
                                     const int32_t* ranks, void* const* U, const void* G,
                                     double* re, const tucker_opts* opts);
 
+/* ---------------------------------------------------------------- measurement
+ * Not part of the paper's method: counters for benchmarking the path. */
+
+/* Cumulative number of kernel launches this library has made in the process. */
+int64_t tucker_launch_count(void);
+
+/* Kernel classes timed by the profiler. */
+typedef enum {
+    TUCKER_KERNEL_POWER = 0,   /* fused power step / range sketch (one pass over the unfolding) */
+    TUCKER_KERNEL_TTM = 1,     /* mode-n product */
+    TUCKER_KERNEL_GATHER = 2,  /* AMM rescaled gather */
+    TUCKER_KERNEL_NORMS = 3    /* squared fiber norms */
+} tucker_kernel_class;
+
+/* on != 0: clear the accumulators and bracket every launch of the classes
+ * above with CUDA events on its stream; on == 0: stop. */
+tucker_status tucker_profile_enable(int on);
+
+/* Totals since the last enable for one class: launches, summed event time
+ * (ms), algorithmic bytes (the operands' size: each tensor element read once,
+ * each output written once) and flops (2 per multiply-add). Synchronises on
+ * the recorded events. Any output pointer may be NULL. */
+tucker_status tucker_profile_read(int kernel_class, int64_t* launches, double* total_ms, double* bytes,
+                                  double* flops);
+
 #ifdef __cplusplus
 }
 #endif

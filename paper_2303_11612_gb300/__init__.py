@@ -1,0 +1,17 @@
+"""GB300 (sm_103a) randomized Tucker decompositions: randomized T-HOSVD and
+ST-HOSVD with the power scheme and approximate matrix multiplication
+(Che, Wei, Yan, arXiv 2303.11612).
+
+The compute path is the CUDA library libtucker.so (C ABI in include/tucker.h);
+this package only marshals torch tensors into it. There is no CPU fallback:
+importing the binding builds the library if needed and raises if it cannot be
+loaded.
+"""
+from ._binding import (  # noqa: F401
+    TuckerError, decompose, rthosvd, rsthosvd, workspace_size, factor_tensor, gaussian, power_step,
+    range_sketch, fiber_norms, quantize_weights, sample_fibers, gather_fibers, leading_factor, ttm,
+    relative_error, last_device_status, lib, exported_symbols, FLAG_ASYNC, launch_count, profile_enable,
+    profile_read,
+)
+
+__all__ = ["rthosvd", "rsthosvd", "decompose", "workspace_size", "TuckerError"]

@@ -1,0 +1,346 @@
+"""ctypes binding of libtucker.so: argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts torch
+tensors (device or pinned/host memory) into the plain pointers and sizes of
+the C ABI declared in include/tucker.h, and raises on a non-OK status.
+
+Tensor convention: a tensor of size I_1 x ... x I_N is passed as any
+contiguous torch tensor whose memory holds it with i_1 fastest (e.g. a torch
+tensor of shape (I_N, ..., I_1)); ``dims`` gives (I_1, ..., I_N). Factor
+matrices are returned as (I_n, R_n) tensors with column-major strides; the
+core as a flat tensor in r_1-fastest order (``core.view(R_N, ..., R_1)``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import torch
+
+from . import build as _build
+
+_LIB = None
+
+TUCKER_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+                4: "numerical failure", 5: "timeout", 6: "unsupported", 7: "over budget"}
+PROB = {"nearly_optimal": 0, "uniform": 1}
+FORM = {"paper": 0, "range": 1}
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2}
+FLAG_ASYNC = 1
+
+
+class TuckerError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn} failed: {STATUS_NAMES.get(status, status)} (status {status})")
+
+
+class Opts(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("form", C.c_int32), ("prec", C.c_int32), ("flags", C.c_uint32),
+                ("alpha", C.c_double), ("stream", C.c_void_p), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t), ("rel_error", C.POINTER(C.c_double)),
+                ("sample_idx", C.POINTER(C.c_void_p))]
+
+
+_VP, _I64, _I32, _U64, _U32, _INT, _DBL = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64, C.c_uint32, C.c_int, C.c_double
+_P = C.POINTER
+_SIGS = {
+    "tucker_rthosvd": [_VP, _INT, _P(_I64), _INT, _P(_I32), _I32, _I32, _I64, _INT, _U64, _P(_VP), _VP, _P(Opts)],
+    "tucker_rsthosvd": [_VP, _INT, _P(_I64), _INT, _P(_I32), _I32, _I32, _I64, _INT, _U64, _P(_VP), _VP, _P(Opts)],
+    "tucker_workspace_size": [_INT, _INT, _P(_I64), _INT, _P(_I32), _I32, _I32, _I64, _P(Opts), _P(C.c_size_t)],
+    "tucker_status_string": [_INT],
+    "tucker_last_device_status": [],
+    "tucker_gaussian": [_VP, _INT, _I64, _I64, _U64, _U32, _P(Opts)],
+    "tucker_power_step": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _VP, _P(Opts)],
+    "tucker_range_sketch": [_VP, _INT, _P(_I64), _INT, _INT, _I64, _U64, _VP, _P(Opts)],
+    "tucker_fiber_norms": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _P(Opts)],
+    "tucker_quantize_weights": [_VP, _I64, _INT, _VP, _P(Opts)],
+    "tucker_sample_fibers": [_VP, _I64, _I64, _U64, _INT, _VP, _VP, _P(Opts)],
+    "tucker_gather_fibers": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _VP, _I64, _VP, _P(Opts)],
+    "tucker_leading_factor": [_VP, _INT, _I64, _I64, _I64, _VP, _P(Opts)],
+    "tucker_ttm": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _INT, _VP, _P(Opts)],
+    "tucker_relative_error": [_VP, _INT, _P(_I64), _INT, _P(_I32), _P(_VP), _VP, _P(_DBL), _P(Opts)],
+    "tucker_launch_count": [],
+    "tucker_profile_enable": [_INT],
+    "tucker_profile_read": [_INT, _P(_I64), _P(_DBL), _P(_DBL), _P(_DBL)],
+}
+_RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int64}
+KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3}
+
+
+def lib():
+    """The loaded library; builds it first if it is missing. Raises if it cannot."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not found at {path}")
+        L = C.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _RESTYPES.get(name, C.c_int)
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(fn: str, status: int):
+    if status != TUCKER_OK:
+        raise TuckerError(fn, status)
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return 0
+    if t.dtype == torch.float64:
+        return 1
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _i64(xs) -> C.Array:
+    return (C.c_int64 * len(xs))(*[int(x) for x in xs])
+
+
+def _i32(xs) -> C.Array:
+    return (C.c_int32 * len(xs))(*[int(x) for x in xs])
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream or None
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def make_opts(form="paper", prec="fp32", alpha=0.0, stream=None, workspace: Optional[torch.Tensor] = None,
+              rel_error: Optional[C.c_double] = None, sample_idx=None, flags=0) -> Opts:
+    o = Opts()
+    o.struct_size = C.sizeof(Opts)
+    o.form = FORM[form]
+    o.prec = PREC[prec]
+    o.flags = flags
+    o.alpha = float(alpha)
+    o.stream = _stream_handle(stream)
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    if rel_error is not None:
+        o.rel_error = C.pointer(rel_error)
+    if sample_idx is not None:
+        arr = (C.c_void_p * len(sample_idx))(*[t.data_ptr() for t in sample_idx])
+        o._keep = arr
+        o.sample_idx = C.cast(arr, C.POINTER(C.c_void_p))
+    return o
+
+
+def _ptr(t: torch.Tensor) -> int:
+    if not t.is_contiguous() and not (t.dim() == 2 and t.stride(0) == 1):
+        raise ValueError("tensor memory must be contiguous")
+    return t.data_ptr()
+
+
+def factor_tensor(I: int, R: int, dtype, device) -> torch.Tensor:
+    """An (I, R) tensor with column-major strides (the ABI's matrix layout)."""
+    return torch.empty((R, I), dtype=dtype, device=device).t()
+
+
+def workspace_size(which: str, dims, ranks, P=10, q=1, c=0, dtype=torch.float32, **kw) -> int:
+    n = C.c_size_t(0)
+    o = make_opts(**kw)
+    st = lib().tucker_workspace_size(0 if which == "T" else 1, 0 if dtype == torch.float32 else 1,
+                                     _i64(dims), len(dims), _i32(ranks), int(P), int(q), int(c), C.byref(o),
+                                     C.byref(n))
+    _check("tucker_workspace_size", st)
+    return int(n.value)
+
+
+def decompose(which: str, A: torch.Tensor, dims: Sequence[int], ranks: Sequence[int], P=10, q=1, c=0,
+              prob="uniform", seed=0, form="paper", prec="fp32", alpha=0.0, stream=None, workspace=None,
+              want_rel_error=False, want_samples=False, out=None, flags=0):
+    """Randomized T-HOSVD (which='T', Algorithms 1/4) or ST-HOSVD (which='ST',
+    Algorithms 2/5). Returns (U list, G flat[, rel_error][, sample indices])."""
+    dims = [int(d) for d in dims]
+    ranks = [int(r) for r in ranks]
+    N = len(dims)
+    if A.numel() != int(torch.tensor(dims).prod()):
+        raise ValueError("A.numel() must equal prod(dims)")
+    dev = A.device
+    if out is None:
+        U = [factor_tensor(I, R, A.dtype, dev) for I, R in zip(dims, ranks)]
+        G = torch.empty(int(torch.tensor(ranks).prod()), dtype=A.dtype, device=dev)
+    else:
+        U, G = out
+    re = C.c_double(float("nan")) if want_rel_error else None
+    samples = None
+    if want_samples:
+        samples = []
+        # sizes follow T_n = min(c, J_n) with J_n of the tensor each mode works on
+        cur = list(dims)
+        for n in range(N):
+            J = 1
+            for m in range(N):
+                if m != n:
+                    J *= cur[m]
+            T = min(c, J) if c > 0 else (int(-(-alpha * J // 1)) if alpha > 0 else 0)
+            samples.append(torch.full((max(T, 1),), -1, dtype=torch.int64, device=dev))
+            if which == "ST":
+                cur[n] = ranks[n]
+    o = make_opts(form, prec, alpha, stream, workspace, re, samples, flags)
+    Uptrs = (C.c_void_p * N)(*[u.data_ptr() for u in U])
+    fn = lib().tucker_rthosvd if which == "T" else lib().tucker_rsthosvd
+    st = fn(A.data_ptr(), _dt(A), _i64(dims), N, _i32(ranks), int(P), int(q), int(c), PROB[prob],
+            C.c_uint64(int(seed) & (2**64 - 1)), Uptrs, G.data_ptr(), C.byref(o))
+    _check("tucker_rthosvd" if which == "T" else "tucker_rsthosvd", st)
+    res = [U, G]
+    if want_rel_error:
+        res.append(re.value)
+    if want_samples:
+        res.append(samples)
+    return tuple(res)
+
+
+def rthosvd(A, dims, ranks, **kw):
+    return decompose("T", A, dims, ranks, **kw)
+
+
+def rsthosvd(A, dims, ranks, **kw):
+    return decompose("ST", A, dims, ranks, **kw)
+
+
+def last_device_status() -> int:
+    return int(lib().tucker_last_device_status())
+
+
+# ---------------------------------------------------------------- step entry points
+def gaussian(rows, cols, seed, stream_id, dtype=torch.float32, device="cuda", stream=None):
+    out = factor_tensor(rows, cols, dtype, device)
+    o = make_opts(stream=stream)
+    _check("tucker_gaussian", lib().tucker_gaussian(out.data_ptr(), _dt(out), rows, cols,
+                                                    C.c_uint64(seed), C.c_uint32(stream_id), C.byref(o)))
+    return out
+
+
+def power_step(A, dims, mode, X, stream=None):
+    I = dims[mode]
+    L = X.shape[1]
+    out = factor_tensor(I, L, A.dtype, A.device)
+    o = make_opts(stream=stream)
+    _check("tucker_power_step", lib().tucker_power_step(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode,
+                                                        X.data_ptr(), L, out.data_ptr(), C.byref(o)))
+    return out
+
+
+def range_sketch(A, dims, mode, L, seed, stream=None):
+    out = factor_tensor(dims[mode], L, A.dtype, A.device)
+    o = make_opts(stream=stream)
+    _check("tucker_range_sketch", lib().tucker_range_sketch(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode, L,
+                                                            C.c_uint64(seed), out.data_ptr(), C.byref(o)))
+    return out
+
+
+def fiber_norms(A, dims, mode, stream=None):
+    J = 1
+    for m, d in enumerate(dims):
+        if m != mode:
+            J *= d
+    w = torch.empty(J, dtype=torch.float64, device=A.device)
+    o = make_opts(stream=stream)
+    _check("tucker_fiber_norms", lib().tucker_fiber_norms(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode,
+                                                          w.data_ptr(), C.byref(o)))
+    return w
+
+
+def quantize_weights(w, prob="nearly_optimal", stream=None):
+    W = torch.empty(w.numel(), dtype=torch.int64, device=w.device)   # uint64 bits
+    o = make_opts(stream=stream)
+    _check("tucker_quantize_weights", lib().tucker_quantize_weights(w.data_ptr(), w.numel(), PROB[prob],
+                                                                    W.data_ptr(), C.byref(o)))
+    return W
+
+
+def sample_fibers(W, T, seed, mode, stream=None):
+    idx = torch.empty(max(T, 1), dtype=torch.int64, device=W.device)
+    scale = torch.empty(max(T, 1), dtype=torch.float64, device=W.device)
+    o = make_opts(stream=stream)
+    _check("tucker_sample_fibers", lib().tucker_sample_fibers(W.data_ptr(), W.numel(), T, C.c_uint64(seed), mode,
+                                                              idx.data_ptr(), scale.data_ptr(), C.byref(o)))
+    return idx[:T], scale[:T]
+
+
+def gather_fibers(A, dims, mode, idx, scale, stream=None):
+    T = idx.numel()
+    out = factor_tensor(dims[mode], max(T, 1), A.dtype, A.device)
+    o = make_opts(stream=stream)
+    _check("tucker_gather_fibers", lib().tucker_gather_fibers(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode,
+                                                              idx.data_ptr(), scale.data_ptr(), T, out.data_ptr(),
+                                                              C.byref(o)))
+    return out[:, :T]
+
+
+def leading_factor(Cm, R, stream=None):
+    I, L = Cm.shape
+    if Cm.stride(0) != 1:
+        Cm = Cm.t().contiguous().t()
+    U = factor_tensor(I, R, Cm.dtype, Cm.device)
+    o = make_opts(stream=stream)
+    _check("tucker_leading_factor", lib().tucker_leading_factor(Cm.data_ptr(), _dt(Cm), I, L, R, U.data_ptr(),
+                                                                C.byref(o)))
+    return U
+
+
+def ttm(A, dims, mode, M, transpose=False, stream=None):
+    """A x_n M (transpose=False, M is K x I_n) or A x_n M^T (transpose=True, M is I_n x K);
+    M must have column-major strides."""
+    K = M.shape[1] if transpose else M.shape[0]
+    if M.stride(0) != 1:
+        M = M.t().contiguous().t()
+    out_dims = list(dims)
+    out_dims[mode] = K
+    n = 1
+    for d in out_dims:
+        n *= d
+    out = torch.empty(n, dtype=A.dtype, device=A.device)
+    o = make_opts(stream=stream)
+    _check("tucker_ttm", lib().tucker_ttm(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode, M.data_ptr(), K,
+                                          int(transpose), out.data_ptr(), C.byref(o)))
+    return out
+
+
+def relative_error(A, dims, ranks, U, G, stream=None):
+    re = C.c_double(0.0)
+    o = make_opts(stream=stream)
+    Up = (C.c_void_p * len(U))(*[u.data_ptr() for u in U])
+    _check("tucker_relative_error", lib().tucker_relative_error(A.data_ptr(), _dt(A), _i64(dims), len(dims),
+                                                                _i32(ranks), Up, G.data_ptr(), C.byref(re),
+                                                                C.byref(o)))
+    return re.value
+
+
+# ---------------------------------------------------------------- measurement
+def launch_count() -> int:
+    """Kernel launches the library has made so far in this process."""
+    return int(lib().tucker_launch_count())
+
+
+def profile_enable(on: bool = True):
+    _check("tucker_profile_enable", lib().tucker_profile_enable(int(bool(on))))
+
+
+def profile_read(kernel: str):
+    """(launches, total_ms, algorithmic bytes, flops) since profile_enable(True)."""
+    n = C.c_int64(0)
+    ms, b, f = C.c_double(0), C.c_double(0), C.c_double(0)
+    _check("tucker_profile_read", lib().tucker_profile_read(KERNEL_CLASSES[kernel], C.byref(n), C.byref(ms),
+                                                            C.byref(b), C.byref(f)))
+    return int(n.value), ms.value, b.value, f.value

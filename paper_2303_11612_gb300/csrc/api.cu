@@ -1,0 +1,735 @@
+// C ABI of the library: argument checks, workspace planning, host/device
+// staging and the per-mode orchestration of Algorithms 1, 2, 4 and 5.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace tk {
+
+int num_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    return n;
+}
+
+namespace {
+
+constexpr int kMaxOrder = 8;
+constexpr int64_t kMaxI = 1024;      // power-step register tiling (4 rows per thread)
+constexpr int kMaxL = 110;           // FP64 Cholesky of an L x L Gram in shared memory
+
+thread_local cudaStream_t g_async_stream = nullptr;
+thread_local int* g_async_status = nullptr;
+
+tucker_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return TUCKER_OK;
+    if (e == cudaErrorMemoryAllocation) return TUCKER_ERR_OOM;
+    return TUCKER_ERR_CUDA;
+}
+
+bool on_device(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+ModeView view_of(const int64_t* dims, int N, int n) {
+    ModeView v{1, dims[n], 1};
+    for (int m = 0; m < n; ++m) v.lf *= dims[m];
+    for (int m = n + 1; m < N; ++m) v.rt *= dims[m];
+    return v;
+}
+
+int64_t prod(const int64_t* d, int N) {
+    int64_t p = 1;
+    for (int k = 0; k < N; ++k) p *= d[k];
+    return p;
+}
+
+uint32_t stream_id(int purpose, int mode) { return ((uint32_t)purpose << 8) | (uint32_t)(mode & 0xFF); }
+
+struct Opts {
+    int form = TUCKER_FORM_PAPER;
+    int prec = TUCKER_SK_FP32;
+    uint32_t flags = 0;
+    double alpha = 0.0;
+    cudaStream_t stream = nullptr;
+    void* workspace = nullptr;
+    size_t workspace_bytes = 0;
+    double* rel_error = nullptr;
+    int64_t* const* sample_idx = nullptr;
+};
+
+tucker_status read_opts(const tucker_opts* o, Opts& out) {
+    if (!o) return TUCKER_OK;
+    if (o->struct_size < sizeof(tucker_opts)) return TUCKER_ERR_INVALID_ARG;
+    out.form = o->form;
+    out.prec = o->prec;
+    out.flags = o->flags;
+    out.alpha = o->alpha;
+    out.stream = reinterpret_cast<cudaStream_t>(o->stream);
+    out.workspace = o->workspace;
+    out.workspace_bytes = o->workspace_bytes;
+    out.rel_error = o->rel_error;
+    out.sample_idx = o->sample_idx;
+    if (out.form != TUCKER_FORM_PAPER && out.form != TUCKER_FORM_RANGE) return TUCKER_ERR_INVALID_ARG;
+    if (out.prec < TUCKER_SK_FP32 || out.prec > TUCKER_SK_BF16) return TUCKER_ERR_INVALID_ARG;
+    if (!(out.alpha >= 0.0) || out.alpha > 1.0) return TUCKER_ERR_INVALID_ARG;
+    if (out.prec != TUCKER_SK_FP32) return TUCKER_ERR_UNSUPPORTED;
+    return TUCKER_OK;
+}
+
+int64_t sample_count(int64_t c, double alpha, int64_t J) {
+    if (c > 0) return std::min(c, J);
+    if (alpha > 0.0) {
+        double t = alpha * (double)J;
+        int64_t T = (int64_t)t;
+        if ((double)T < t) ++T;
+        return std::min(T, J);
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------ plan
+struct ModePlan {
+    ModeView v;        // view of the tensor the mode works on
+    ModeView mv;       // view of the matrix that is sketched (v, or the I x T gather)
+    int L;
+    int R;
+    int64_t T;         // AMM samples (0 = none)
+    PowerPlan pp;
+    OrthPlan op;
+};
+
+struct Plan {
+    int N = 0;
+    bool st = false;
+    int elem = 4;
+    int form = 0;
+    int q = 1;
+    int64_t dims[kMaxOrder];
+    int64_t cur[kMaxOrder][kMaxOrder];   // dims of the tensor each mode works on (ST shrinks)
+    ModePlan m[kMaxOrder];
+    int64_t maxI = 0, maxL = 0, maxJ = 0, maxT = 0, maxIT = 0;
+    size_t max_partials = 0, max_orth = 0;
+    int64_t inter_elems = 0;             // largest intermediate tensor of the TTM chain
+};
+
+tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int32_t* ranks, int32_t P, int32_t q,
+                        int64_t c, const Opts& o, Plan& p) {
+    if (N < 1 || N > kMaxOrder || !dims || !ranks) return TUCKER_ERR_INVALID_ARG;
+    if (q < 1 || P < 0 || c < 0) return TUCKER_ERR_INVALID_ARG;
+    for (int n = 0; n < N; ++n) {
+        if (dims[n] < 1 || ranks[n] < 1 || ranks[n] > dims[n]) return TUCKER_ERR_INVALID_ARG;
+    }
+    p.N = N;
+    p.st = st;
+    p.elem = elem;
+    p.form = o.form;
+    p.q = q;
+    const int sms = num_sms();
+    int64_t d[kMaxOrder];
+    for (int n = 0; n < N; ++n) d[n] = p.dims[n] = dims[n];
+    for (int n = 0; n < N; ++n) {
+        for (int k = 0; k < N; ++k) p.cur[n][k] = d[k];
+        ModePlan& mp = p.m[n];
+        mp.v = view_of(d, N, n);
+        mp.R = ranks[n];
+        mp.L = (int)std::min<int64_t>((int64_t)ranks[n] + P, d[n]);
+        const int64_t J = mp.v.fibers();
+        mp.T = sample_count(c, o.alpha, J);
+        mp.mv = mp.T > 0 ? ModeView{1, d[n], mp.T} : mp.v;
+        if (d[n] > kMaxI || mp.L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
+        if (elem == 8 && d[n] > 512) return TUCKER_ERR_UNSUPPORTED;
+        mp.pp = power_plan(mp.mv, mp.L, elem, sms);
+        mp.op = orth_plan(d[n], mp.L, sms);
+        p.maxI = std::max(p.maxI, d[n]);
+        p.maxL = std::max<int64_t>(p.maxL, mp.L);
+        p.maxJ = std::max(p.maxJ, J);
+        p.maxT = std::max(p.maxT, mp.T);
+        p.maxIT = std::max(p.maxIT, d[n] * mp.T);
+        p.max_partials = std::max(p.max_partials, power_partials_bytes(mp.pp, mp.mv, mp.L, elem));
+        p.max_orth = std::max(p.max_orth, orth_scratch_bytes(mp.op, elem));
+        if (st) d[n] = ranks[n];
+        if (st && n < N - 1) p.inter_elems = std::max(p.inter_elems, prod(d, N));
+    }
+    if (!st) {
+        int64_t e[kMaxOrder];
+        for (int n = 0; n < N; ++n) e[n] = dims[n];
+        for (int n = 0; n < N - 1; ++n) {
+            e[n] = ranks[n];
+            p.inter_elems = std::max(p.inter_elems, prod(e, N));
+        }
+    }
+    return TUCKER_OK;
+}
+
+struct Work {
+    int* status;
+    void* X0; void* X1; void* Q; void* Qt;
+    double* factors;
+    void* partials;
+    void* orth;
+    double* w; uint64_t* W; void* samp; int64_t* idx; double* scale; void* Cp;
+    void* inter[2];
+    void* sumsq;
+    double* norms;     // [2]: ||A||^2, ||G||^2
+};
+
+void carve(const Plan& p, Arena& a, Work& w) {
+    const size_t IL = (size_t)p.maxI * p.maxL * p.elem;
+    const int slots = p.form == TUCKER_FORM_PAPER ? p.q : 1;
+    w.status = (int*)a.take(sizeof(int) * 64);
+    w.X0 = a.take(IL);
+    w.X1 = a.take(IL);
+    w.Q = a.take(IL);
+    w.Qt = a.take(IL);
+    w.factors = (double*)a.take(sizeof(double) * 3 * slots * (size_t)p.maxL * p.maxL);
+    w.partials = a.take(p.max_partials);
+    w.orth = a.take(p.max_orth);
+    if (p.maxT > 0) {
+        w.w = (double*)a.take(sizeof(double) * (size_t)p.maxJ);
+        w.W = (uint64_t*)a.take(sizeof(uint64_t) * (size_t)p.maxJ);
+        w.samp = a.take(std::max(sample_scratch_bytes(p.maxJ), quantize_scratch_bytes(p.maxJ)));
+        w.idx = (int64_t*)a.take(sizeof(int64_t) * (size_t)p.maxT);
+        w.scale = (double*)a.take(sizeof(double) * (size_t)p.maxT);
+        w.Cp = a.take((size_t)p.maxIT * p.elem);
+    } else {
+        w.w = nullptr; w.W = nullptr; w.samp = nullptr; w.idx = nullptr; w.scale = nullptr; w.Cp = nullptr;
+    }
+    w.inter[0] = a.take((size_t)p.inter_elems * p.elem);
+    w.inter[1] = a.take((size_t)p.inter_elems * p.elem);
+    w.sumsq = a.take(sumsq_scratch_bytes());
+    w.norms = (double*)a.take(sizeof(double) * 2);
+}
+
+#define TK_TRY(x)                                   \
+    do {                                            \
+        cudaError_t _e = (x);                       \
+        if (_e != cudaSuccess) return _e;           \
+    } while (0)
+
+// One mode's factor U (I_n x R_n) from the tensor B (view mp.v).
+template <typename T>
+cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, uint64_t seed, int form, T* U,
+                        const Work& w, int64_t* sample_out, cudaStream_t s) {
+    const T* M = B;
+    if (mp.T > 0) {
+        const int64_t J = mp.v.fibers();
+        if (prob == TUCKER_PROB_NEARLY_OPTIMAL) TK_TRY(launch_fiber_norms<T>(B, mp.v, w.w, s));
+        TK_TRY(launch_quantize(w.w, J, prob, w.W, w.samp, s));
+        TK_TRY(launch_sample(w.W, J, mp.T, seed, stream_id(1, n), w.idx, w.scale, w.samp, s));
+        TK_TRY(launch_gather<T>(B, mp.v, w.idx, w.scale, mp.T, (T*)w.Cp, s));
+        if (sample_out) TK_TRY(cudaMemcpyAsync(sample_out, w.idx, sizeof(int64_t) * mp.T, cudaMemcpyDefault, s));
+        M = (const T*)w.Cp;
+    }
+    const int L = mp.L;
+    T* X0 = (T*)w.X0; T* X1 = (T*)w.X1; T* Q = (T*)w.Q; T* Qt = (T*)w.Qt;
+    int nf;
+    if (form == TUCKER_FORM_PAPER) {
+        // C = (M M^T)^q Omega in factored form: after each step X = Q_k R_k and the
+        // next step multiplies Q_k, so C = Q_q (R_q ... R_1) without overflow or
+        // loss of the weaker directions to rounding.
+        TK_TRY(launch_gaussian<T>(X0, mp.v.i, L, seed, stream_id(0, n), s));
+        for (int k = 0; k < q; ++k) {
+            const T* xin = X0;
+            if (k > 0) {
+                TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, k - 1, w.orth, w.status, s));
+                xin = Q;
+            }
+            TK_TRY(launch_power<T>(M, mp.mv, xin, L, X1, w.partials, mp.pp, false, 0, 0, s));
+        }
+        TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, q - 1, w.orth, w.status, s));
+        nf = 3 * q;
+    } else {
+        TK_TRY(launch_power<T>(M, mp.mv, nullptr, L, X1, w.partials, mp.pp, true, seed, stream_id(0, n), s));
+        for (int k = 0; k < q; ++k) {
+            TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, 0, w.orth, w.status, s));
+            TK_TRY(launch_power<T>(M, mp.mv, Q, L, X1, w.partials, mp.pp, false, 0, 0, s));
+        }
+        TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, 0, w.orth, w.status, s));
+        nf = 3;
+    }
+    return launch_extract<T>(Q, mp.op, w.factors, nf, mp.R, U, w.orth, w.status, s);
+}
+
+template <typename T>
+cudaError_t run_driver(const Plan& p, const T* A, const int32_t* ranks, int q, int prob, uint64_t seed, T* const* U,
+                       T* G, const Work& w, int64_t* const* sample_out, bool want_re, cudaStream_t s) {
+    const int N = p.N;
+    if (want_re) TK_TRY(launch_sumsq<T>(A, nullptr, prod(p.dims, N), &w.norms[0], w.sumsq, s));
+    if (p.st) {
+        const T* cur = A;
+        for (int n = 0; n < N; ++n) {
+            const ModePlan& mp = p.m[n];
+            TK_TRY(factor_mode<T>(cur, mp, n, q, prob, seed, p.form, U[n], w,
+                                  sample_out ? sample_out[n] : nullptr, s));
+            T* out = n == N - 1 ? G : (T*)w.inter[n & 1];
+            TK_TRY(launch_ttm<T>(cur, mp.v, U[n], ranks[n], 1, mp.v.i, out, s));
+            cur = out;
+        }
+    } else {
+        for (int n = 0; n < N; ++n)
+            TK_TRY(factor_mode<T>(A, p.m[n], n, q, prob, seed, p.form, U[n], w,
+                                  sample_out ? sample_out[n] : nullptr, s));
+        int64_t e[kMaxOrder];
+        for (int n = 0; n < N; ++n) e[n] = p.dims[n];
+        const T* cur = A;
+        for (int n = 0; n < N; ++n) {
+            const ModeView v = view_of(e, N, n);
+            T* out = n == N - 1 ? G : (T*)w.inter[n & 1];
+            TK_TRY(launch_ttm<T>(cur, v, U[n], ranks[n], 1, v.i, out, s));
+            e[n] = ranks[n];
+            cur = out;
+        }
+    }
+    if (want_re) {
+        int64_t r = 1;
+        for (int n = 0; n < N; ++n) r *= ranks[n];
+        TK_TRY(launch_sumsq<T>(G, nullptr, r, &w.norms[1], w.sumsq, s));
+    }
+    return cudaSuccess;
+}
+
+tucker_status finish(cudaStream_t s, int* dev_status, const Opts& o, double* dev_norms) {
+    if (o.flags & TUCKER_FLAG_ASYNC) {
+        g_async_stream = s;
+        g_async_status = dev_status;
+        return TUCKER_OK;
+    }
+    int st = 0;
+    double nrm[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(&st, dev_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && o.rel_error && dev_norms)
+        e = cudaMemcpyAsync(nrm, dev_norms, sizeof(nrm), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (o.rel_error && dev_norms) {
+        const double r = nrm[0] > 0 ? 1.0 - nrm[1] / nrm[0] : 0.0;
+        *o.rel_error = r > 0 ? sqrt(r) : 0.0;
+    }
+    if (st & kStatTimeout) return TUCKER_ERR_TIMEOUT;
+    if (st & kStatNumerical) return TUCKER_ERR_NUMERICAL;
+    return TUCKER_OK;
+}
+
+tucker_status driver(bool st, const void* A, tucker_dtype dt, const int64_t* dims, int N, const int32_t* ranks,
+                     int32_t P, int32_t q, int64_t c, tucker_prob prob, uint64_t seed, void* const* U, void* G,
+                     const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    if (prob != TUCKER_PROB_NEARLY_OPTIMAL && prob != TUCKER_PROB_UNIFORM) return TUCKER_ERR_INVALID_ARG;
+    if (!A || !U || !G) return TUCKER_ERR_INVALID_ARG;
+    for (int n = 0; n < N && n < kMaxOrder; ++n)
+        if (!U[n]) return TUCKER_ERR_INVALID_ARG;
+    const int elem = dt == TUCKER_F64 ? 8 : 4;
+    Plan p;
+    rs = make_plan(st, elem, dims, N, ranks, P, q, c, o, p);
+    if (rs != TUCKER_OK) return rs;
+    if ((o.flags & TUCKER_FLAG_ASYNC) && !o.workspace) return TUCKER_ERR_INVALID_ARG;
+
+    cudaStream_t s = o.stream;
+    // stage host buffers
+    const int64_t E = prod(dims, N);
+    int64_t Gn = 1, Un = 0;
+    for (int n = 0; n < N; ++n) { Gn *= ranks[n]; Un += dims[n] * ranks[n]; }
+    const bool hA = !on_device(A), hG = !on_device(G);
+    bool hU = false;
+    for (int n = 0; n < N; ++n) hU = hU || !on_device(U[n]);
+    if ((o.flags & TUCKER_FLAG_ASYNC) && (hA || hG || hU)) return TUCKER_ERR_INVALID_ARG;
+
+    Arena a;
+    Work w;
+    carve(p, a, w);      // measure
+    size_t need = a.used;
+    size_t stage = 0;
+    if (hA) stage += ((size_t)E * elem + 255) & ~size_t(255);
+    if (hU) stage += ((size_t)Un * elem + 255) & ~size_t(255);
+    if (hG) stage += ((size_t)Gn * elem + 255) & ~size_t(255);
+
+    void* owned = nullptr;
+    char* base;
+    if (o.workspace) {
+        if (o.workspace_bytes < need) return TUCKER_ERR_INVALID_ARG;
+        base = (char*)o.workspace;
+    } else {
+        cudaError_t e = cudaMallocAsync(&owned, need, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        base = (char*)owned;
+    }
+    void* stage_buf = nullptr;
+    if (stage) {
+        cudaError_t e = cudaMallocAsync(&stage_buf, stage, s);
+        if (e != cudaSuccess) {
+            if (owned) cudaFreeAsync(owned, s);
+            return from_cuda(e);
+        }
+    }
+    Arena b;
+    b.base = base;
+    b.cap = need;
+    carve(p, b, w);
+
+    char* sp = (char*)stage_buf;
+    const void* dA = A;
+    void* dU[kMaxOrder];
+    void* dG = G;
+    cudaError_t e = cudaSuccess;
+    if (hA) {
+        dA = sp;
+        e = cudaMemcpyAsync(sp, A, (size_t)E * elem, cudaMemcpyHostToDevice, s);
+        sp += ((size_t)E * elem + 255) & ~size_t(255);
+    }
+    for (int n = 0; n < N; ++n) dU[n] = U[n];
+    if (hU) {
+        for (int n = 0; n < N; ++n) {
+            dU[n] = sp;
+            sp += (size_t)dims[n] * ranks[n] * elem;
+        }
+        sp = (char*)(((uintptr_t)sp + 255) & ~uintptr_t(255));
+    }
+    if (hG) dG = sp;
+
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        if (elem == 4)
+            e = run_driver<float>(p, (const float*)dA, ranks, q, prob, seed, (float* const*)dU, (float*)dG, w,
+                                  o.sample_idx, o.rel_error != nullptr, s);
+        else
+            e = run_driver<double>(p, (const double*)dA, ranks, q, prob, seed, (double* const*)dU, (double*)dG, w,
+                                   o.sample_idx, o.rel_error != nullptr, s);
+    }
+    if (e == cudaSuccess && hU)
+        for (int n = 0; n < N && e == cudaSuccess; ++n)
+            e = cudaMemcpyAsync(U[n], dU[n], (size_t)dims[n] * ranks[n] * elem, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && hG) e = cudaMemcpyAsync(G, dG, (size_t)Gn * elem, cudaMemcpyDeviceToHost, s);
+    tucker_status out = e == cudaSuccess ? finish(s, w.status, o, w.norms) : from_cuda(e);
+    if (owned) cudaFreeAsync(owned, s);
+    if (stage_buf) cudaFreeAsync(stage_buf, s);
+    if (owned || stage_buf) cudaStreamSynchronize(s);
+    return out;
+}
+
+// Scratch for a single step entry point.
+struct Scratch {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    tucker_status get(size_t n, cudaStream_t st) {
+        s = st;
+        return from_cuda(cudaMallocAsync(&p, n ? n : 256, st));
+    }
+    ~Scratch() {
+        if (p) {
+            cudaFreeAsync(p, s);
+            cudaStreamSynchronize(s);
+        }
+    }
+};
+
+tucker_status sync_status(cudaStream_t s, const int* dev_status) {
+    int st = 0;
+    cudaError_t e = cudaSuccess;
+    if (dev_status) e = cudaMemcpyAsync(&st, dev_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (st & kStatNumerical) return TUCKER_ERR_NUMERICAL;
+    return TUCKER_OK;
+}
+
+bool mode_args_ok(const void* A, const int64_t* dims, int N, int mode) {
+    if (!A || !dims || N < 1 || N > kMaxOrder || mode < 0 || mode >= N) return false;
+    for (int n = 0; n < N; ++n)
+        if (dims[n] < 1) return false;
+    return true;
+}
+
+}  // namespace
+}  // namespace tk
+
+using namespace tk;
+
+extern "C" {
+
+tucker_status tucker_rthosvd(const void* A, tucker_dtype dt, const int64_t* dims, int N, const int32_t* ranks,
+                             int32_t P, int32_t q, int64_t c, tucker_prob prob, uint64_t seed, void* const* U, void* G,
+                             const tucker_opts* opts) {
+    return driver(false, A, dt, dims, N, ranks, P, q, c, prob, seed, U, G, opts);
+}
+
+tucker_status tucker_rsthosvd(const void* A, tucker_dtype dt, const int64_t* dims, int N, const int32_t* ranks,
+                              int32_t P, int32_t q, int64_t c, tucker_prob prob, uint64_t seed, void* const* U,
+                              void* G, const tucker_opts* opts) {
+    return driver(true, A, dt, dims, N, ranks, P, q, c, prob, seed, U, G, opts);
+}
+
+tucker_status tucker_workspace_size(int which, tucker_dtype dt, const int64_t* dims, int N, const int32_t* ranks,
+                                    int32_t P, int32_t q, int64_t c, const tucker_opts* opts, size_t* bytes) {
+    if (!bytes || (which != 0 && which != 1)) return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    Plan p;
+    rs = make_plan(which == 1, dt == TUCKER_F64 ? 8 : 4, dims, N, ranks, P, q, c, o, p);
+    if (rs != TUCKER_OK) return rs;
+    Arena a;
+    Work w;
+    carve(p, a, w);
+    *bytes = a.used;
+    return TUCKER_OK;
+}
+
+const char* tucker_status_string(tucker_status s) {
+    switch (s) {
+        case TUCKER_OK: return "ok";
+        case TUCKER_ERR_INVALID_ARG: return "invalid argument";
+        case TUCKER_ERR_OOM: return "out of device memory";
+        case TUCKER_ERR_CUDA: return "CUDA error";
+        case TUCKER_ERR_NUMERICAL: return "numerical failure (non-finite values or unrepaired breakdown)";
+        case TUCKER_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case TUCKER_ERR_UNSUPPORTED: return "request outside the supported sizes or options";
+        case TUCKER_ERR_BUDGET: return "request larger than the memory budget";
+    }
+    return "unknown status";
+}
+
+tucker_status tucker_last_device_status(void) {
+    if (!g_async_status) return TUCKER_OK;
+    return sync_status(g_async_stream, g_async_status);
+}
+
+tucker_status tucker_gaussian(void* out, tucker_dtype dt, int64_t rows, int64_t cols, uint64_t seed,
+                              uint32_t stream_id, const tucker_opts* opts) {
+    Opts o;
+    if (read_opts(opts, o) != TUCKER_OK) return TUCKER_ERR_INVALID_ARG;
+    if (!out || rows < 0 || cols < 0 || (dt != TUCKER_F32 && dt != TUCKER_F64)) return TUCKER_ERR_INVALID_ARG;
+    if (!on_device(out)) return TUCKER_ERR_INVALID_ARG;
+    cudaError_t e = dt == TUCKER_F32 ? launch_gaussian<float>((float*)out, rows, cols, seed, stream_id, o.stream)
+                                     : launch_gaussian<double>((double*)out, rows, cols, seed, stream_id, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_power_step(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode,
+                                const void* X_in, int64_t L, void* X_out, const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!mode_args_ok(A, dims, N, mode) || !X_in || !X_out || L < 1) return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    const ModeView v = view_of(dims, N, mode);
+    const int elem = dt == TUCKER_F64 ? 8 : 4;
+    if (v.i > kMaxI || L > 4096 || (elem == 8 && v.i > 512)) return TUCKER_ERR_UNSUPPORTED;
+    const PowerPlan pp = power_plan(v, (int)L, elem, num_sms());
+    Scratch sc;
+    if ((rs = sc.get(power_partials_bytes(pp, v, (int)L, elem), o.stream)) != TUCKER_OK) return rs;
+    cudaError_t e = elem == 4 ? launch_power<float>((const float*)A, v, (const float*)X_in, (int)L, (float*)X_out,
+                                                    sc.p, pp, false, 0, 0, o.stream)
+                              : launch_power<double>((const double*)A, v, (const double*)X_in, (int)L,
+                                                     (double*)X_out, sc.p, pp, false, 0, 0, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_range_sketch(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode, int64_t L,
+                                  uint64_t seed, void* Y, const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!mode_args_ok(A, dims, N, mode) || !Y || L < 1) return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    const ModeView v = view_of(dims, N, mode);
+    const int elem = dt == TUCKER_F64 ? 8 : 4;
+    if (v.i > kMaxI || L > 4096 || (elem == 8 && v.i > 512)) return TUCKER_ERR_UNSUPPORTED;
+    const PowerPlan pp = power_plan(v, (int)L, elem, num_sms());
+    Scratch sc;
+    if ((rs = sc.get(power_partials_bytes(pp, v, (int)L, elem), o.stream)) != TUCKER_OK) return rs;
+    const uint32_t sid = stream_id(0, mode);
+    cudaError_t e = elem == 4 ? launch_power<float>((const float*)A, v, nullptr, (int)L, (float*)Y, sc.p, pp, true,
+                                                    seed, sid, o.stream)
+                              : launch_power<double>((const double*)A, v, nullptr, (int)L, (double*)Y, sc.p, pp,
+                                                     true, seed, sid, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_fiber_norms(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode, double* w,
+                                 const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!mode_args_ok(A, dims, N, mode) || !w) return TUCKER_ERR_INVALID_ARG;
+    const ModeView v = view_of(dims, N, mode);
+    cudaError_t e = dt == TUCKER_F32 ? launch_fiber_norms<float>((const float*)A, v, w, o.stream)
+                  : dt == TUCKER_F64 ? launch_fiber_norms<double>((const double*)A, v, w, o.stream)
+                                     : cudaErrorInvalidValue;
+    if (e == cudaErrorInvalidValue) return TUCKER_ERR_INVALID_ARG;
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_quantize_weights(const double* w, int64_t J, tucker_prob prob, uint64_t* W,
+                                      const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!w || !W || J < 1) return TUCKER_ERR_INVALID_ARG;
+    if (prob != TUCKER_PROB_NEARLY_OPTIMAL && prob != TUCKER_PROB_UNIFORM) return TUCKER_ERR_INVALID_ARG;
+    Scratch sc;
+    if ((rs = sc.get(quantize_scratch_bytes(J), o.stream)) != TUCKER_OK) return rs;
+    cudaError_t e = launch_quantize(w, J, prob, W, sc.p, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_sample_fibers(const uint64_t* W, int64_t J, int64_t T, uint64_t seed, int mode, int64_t* idx,
+                                   double* scale, const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!W || J < 1 || T < 0 || (T > 0 && (!idx || !scale)) || mode < 0 || mode > 255) return TUCKER_ERR_INVALID_ARG;
+    Scratch sc;
+    if ((rs = sc.get(sample_scratch_bytes(J), o.stream)) != TUCKER_OK) return rs;
+    cudaError_t e = launch_sample(W, J, T, seed, stream_id(1, mode), idx, scale, sc.p, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_gather_fibers(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode,
+                                   const int64_t* idx, const double* scale, int64_t T, void* Cp,
+                                   const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!mode_args_ok(A, dims, N, mode) || T < 0 || (T > 0 && (!idx || !scale || !Cp))) return TUCKER_ERR_INVALID_ARG;
+    const ModeView v = view_of(dims, N, mode);
+    cudaError_t e = dt == TUCKER_F32 ? launch_gather<float>((const float*)A, v, idx, scale, T, (float*)Cp, o.stream)
+                  : dt == TUCKER_F64 ? launch_gather<double>((const double*)A, v, idx, scale, T, (double*)Cp, o.stream)
+                                     : cudaErrorInvalidValue;
+    if (e == cudaErrorInvalidValue) return TUCKER_ERR_INVALID_ARG;
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, int64_t L, int64_t R, void* U,
+                                    const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!C || !U || I < 1 || L < 1 || R < 1 || R > L || L > I) return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    if (L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
+    const int elem = dt == TUCKER_F64 ? 8 : 4;
+    const OrthPlan op = orth_plan(I, (int)L, num_sms());
+    Arena a;
+    const size_t IL = (size_t)I * L * elem;
+    a.take(sizeof(int) * 64); a.take(IL); a.take(IL); a.take(sizeof(double) * 3 * L * L);
+    a.take(orth_scratch_bytes(op, elem));
+    Scratch sc;
+    if ((rs = sc.get(a.used, o.stream)) != TUCKER_OK) return rs;
+    Arena b;
+    b.base = (char*)sc.p;
+    b.cap = a.used;
+    int* status = (int*)b.take(sizeof(int) * 64);
+    void* Q = b.take(IL);
+    void* Qt = b.take(IL);
+    double* F = (double*)b.take(sizeof(double) * 3 * L * L);
+    void* orth = b.take(orth_scratch_bytes(op, elem));
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
+    if (e == cudaSuccess) {
+        if (elem == 4) {
+            e = launch_cholqr<float>((const float*)C, (float*)Q, (float*)Qt, op, F, 0, orth, status, o.stream);
+            if (e == cudaSuccess)
+                e = launch_extract<float>((const float*)Q, op, F, 3, (int)R, (float*)U, orth, status, o.stream);
+        } else {
+            e = launch_cholqr<double>((const double*)C, (double*)Q, (double*)Qt, op, F, 0, orth, status, o.stream);
+            if (e == cudaSuccess)
+                e = launch_extract<double>((const double*)Q, op, F, 3, (int)R, (double*)U, orth, status, o.stream);
+        }
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, status);
+}
+
+tucker_status tucker_ttm(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode, const void* M_ptr,
+                         int64_t K, int transpose, void* out, const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!mode_args_ok(A, dims, N, mode) || !M_ptr || !out || K < 1) return TUCKER_ERR_INVALID_ARG;
+    const ModeView v = view_of(dims, N, mode);
+    // M(k, i): transpose == 0: M_ptr is K x I_n (col-major) -> M_ptr[k + i K]
+    //          transpose == 1: M_ptr is I_n x K               -> M_ptr[i + k I_n]
+    const int64_t ld_i = transpose ? 1 : K, ld_k = transpose ? v.i : 1;
+    cudaError_t e = dt == TUCKER_F32 ? launch_ttm<float>((const float*)A, v, (const float*)M_ptr, K, ld_i, ld_k,
+                                                         (float*)out, o.stream)
+                  : dt == TUCKER_F64 ? launch_ttm<double>((const double*)A, v, (const double*)M_ptr, K, ld_i, ld_k,
+                                                          (double*)out, o.stream)
+                                     : cudaErrorInvalidValue;
+    if (e == cudaErrorInvalidValue) return TUCKER_ERR_INVALID_ARG;
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_relative_error(const void* A, tucker_dtype dt, const int64_t* dims, int N, const int32_t* ranks,
+                                    void* const* U, const void* G, double* re, const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!A || !dims || !ranks || !U || !G || !re || N < 1 || N > kMaxOrder) return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    for (int n = 0; n < N; ++n)
+        if (dims[n] < 1 || ranks[n] < 1 || ranks[n] > dims[n] || !U[n]) return TUCKER_ERR_INVALID_ARG;
+    const int elem = dt == TUCKER_F64 ? 8 : 4;
+    const int64_t E = prod(dims, N);
+    // expand G x_1 U_1 ... x_N U_N through two buffers of at most E elements
+    Arena a;
+    a.take((size_t)E * elem); a.take((size_t)E * elem); a.take(sumsq_scratch_bytes()); a.take(sizeof(double) * 2);
+    Scratch sc;
+    if ((rs = sc.get(a.used, o.stream)) != TUCKER_OK) return rs;
+    Arena b;
+    b.base = (char*)sc.p;
+    b.cap = a.used;
+    void* buf[2] = {b.take((size_t)E * elem), b.take((size_t)E * elem)};
+    void* ss = b.take(sumsq_scratch_bytes());
+    double* nrm = (double*)b.take(sizeof(double) * 2);
+    int64_t e_[kMaxOrder];
+    for (int n = 0; n < N; ++n) e_[n] = ranks[n];
+    const void* cur = G;
+    cudaError_t e = cudaSuccess;
+    for (int n = 0; n < N && e == cudaSuccess; ++n) {
+        const ModeView v = view_of(e_, N, n);
+        // out = cur x_n U_n, M(k = i_out, i = r) = U[i_out + r I_n]
+        void* dst = buf[n & 1];
+        e = elem == 4 ? launch_ttm<float>((const float*)cur, v, (const float*)U[n], dims[n], dims[n], 1, (float*)dst,
+                                          o.stream)
+                      : launch_ttm<double>((const double*)cur, v, (const double*)U[n], dims[n], dims[n], 1,
+                                           (double*)dst, o.stream);
+        e_[n] = dims[n];
+        cur = dst;
+    }
+    if (e == cudaSuccess)
+        e = elem == 4 ? launch_sumsq<float>((const float*)A, (const float*)cur, E, &nrm[0], ss, o.stream)
+                      : launch_sumsq<double>((const double*)A, (const double*)cur, E, &nrm[0], ss, o.stream);
+    if (e == cudaSuccess)
+        e = elem == 4 ? launch_sumsq<float>((const float*)A, nullptr, E, &nrm[1], ss, o.stream)
+                      : launch_sumsq<double>((const double*)A, nullptr, E, &nrm[1], ss, o.stream);
+    double h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, o.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    *re = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+    return TUCKER_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Host-side launchers shared between the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tk {
+
+// Bump allocator over a caller- or library-provided device block. With a null
+// base it only measures, which is how the workspace size is computed.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t used = 0;
+    bool ok = true;
+    void* take(size_t bytes) {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + ((bytes + 255) & ~size_t(255));
+        if (!base) return nullptr;
+        if (used > cap) { ok = false; return nullptr; }
+        return base + off;
+    }
+};
+
+// ---- sketch (kernels_sketch.cu)
+struct PowerPlan {
+    int groups, parts, jb, lg;
+    size_t smem;
+    int64_t tiles;
+};
+PowerPlan power_plan(const ModeView& v, int L, int elem_size, int num_sms);
+size_t power_partials_bytes(const PowerPlan& p, const ModeView& v, int L, int elem_size);
+
+template <typename T>
+cudaError_t launch_gaussian(T* out, int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
+                            cudaStream_t s);
+// X_out = A_(n) (A_(n)^T X_in) (range == false) or Y = A_(n) Omega (range == true).
+template <typename T>
+cudaError_t launch_power(const T* A, const ModeView& v, const T* X_in, int L, T* X_out,
+                         void* partials, const PowerPlan& plan, bool range, uint64_t seed,
+                         uint32_t stream_id, cudaStream_t s);
+
+// ---- sampling (kernels_amm.cu)
+template <typename T>
+cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStream_t s);
+size_t quantize_scratch_bytes(int64_t J);
+cudaError_t launch_quantize(const double* w, int64_t J, int prob, uint64_t* W, void* scratch,
+                            cudaStream_t s);
+size_t sample_scratch_bytes(int64_t J);
+cudaError_t launch_sample(const uint64_t* W, int64_t J, int64_t T, uint64_t seed, uint32_t stream_id,
+                          int64_t* idx, double* scale, void* scratch, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather(const T* A, const ModeView& v, const int64_t* idx, const double* scale,
+                          int64_t T_, T* Cp, cudaStream_t s);
+
+// ---- orthonormalisation and extraction (kernels_orth.cu)
+struct OrthPlan {
+    int64_t I;
+    int L;
+    int gram_blocks;
+};
+OrthPlan orth_plan(int64_t I, int L, int num_sms);
+size_t orth_scratch_bytes(const OrthPlan& p, int elem_size);
+// One CholeskyQR pass group (2 passes + a 3rd when pass 1 needed a shift):
+// X (I x L) -> Q, appending three L x L upper-triangular FP64 factors at
+// factors + 3 * slot * L * L. X and Q may not alias.
+template <typename T>
+cudaError_t launch_cholqr(const T* X, T* Q, T* Qtmp, const OrthPlan& p, double* factors, int slot,
+                          void* scratch, int* status, cudaStream_t s);
+// U = Q * (R leading left singular vectors of M), M = product of the first
+// nfactors factors (last applied first), sign-fixed.
+template <typename T>
+cudaError_t launch_extract(const T* Q, const OrthPlan& p, const double* factors, int nfactors,
+                           int R, T* U, void* scratch, int* status, cudaStream_t s);
+
+// ---- mode products and norms (kernels_ttm.cu)
+// out = A x_n M: M(k_out, i) read as Mp[i * ld_i + k_out * ld_k].
+template <typename T>
+cudaError_t launch_ttm(const T* A, const ModeView& v, const T* Mp, int64_t K_out, int64_t ld_i,
+                       int64_t ld_k, T* out, cudaStream_t s);
+size_t sumsq_scratch_bytes();
+// *out (device double) = sum (a - b)^2 (b may be null).
+template <typename T>
+cudaError_t launch_sumsq(const T* a, const T* b, int64_t n, double* out, void* scratch,
+                         cudaStream_t s);
+
+int num_sms();
+
+// ---- launch counting and profiling (profile.cu)
+enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKernelClasses = 4 };
+void note_launch();
+void profile_drain();
+// Brackets one launch with CUDA events when profiling is on.
+class ProfScope {
+  public:
+    ProfScope(int cls, double bytes, double flops, cudaStream_t s);
+    ~ProfScope();
+  private:
+    int cls_;
+    double bytes_, flops_;
+    cudaStream_t s_;
+    void* a_ = nullptr;
+    void* b_ = nullptr;
+};
+
+}  // namespace tk

@@ -1,0 +1,275 @@
+// Approximate matrix multiplication by fiber sampling (Section 3.2,
+// Algorithms 3-5): squared fiber norms, integer sampling weights, their
+// inclusive prefix sum, the multinomial draws (inverse CDF, exact integer
+// arithmetic) and the rescaled gather C' = A_(n) S.
+#include "internal.h"
+
+namespace tk {
+namespace {
+
+constexpr int kT = kThreads;
+constexpr int kScanItems = 4;                 // elements per thread in the scan
+constexpr int kScanBlock = kT * kScanItems;   // elements per scan block
+
+// ---------------------------------------------------------------- fiber norms
+template <typename T> struct NormAcc;
+template <> struct NormAcc<float> {
+    Pair s{0.f, 0.f};
+    __device__ void add(float x) { pair_add_prod(s, x, x); }
+    __device__ void warp_reduce() { s = warp_sum_pair(s); }
+    __device__ double value() const { return pair_value(s); }
+};
+template <> struct NormAcc<double> {
+    double s = 0.0;
+    __device__ void add(double x) { s = fma(x, x, s); }
+    __device__ void warp_reduce() { s = warp_sum(s); }
+    __device__ double value() const { return s; }
+};
+
+// Contiguous fibers (mode 1): one warp per fiber.
+template <typename T>
+__global__ void __launch_bounds__(kT) norms_contig_kernel(const T* __restrict__ A, int64_t I, int64_t J,
+                                                          double* __restrict__ w) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)kT + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kT) >> 5;
+    for (int64_t j = warp; j < J; j += nwarps) {
+        NormAcc<T> acc;
+        const T* f = A + j * I;
+        for (int64_t i = lane; i < I; i += 32) acc.add(__ldg(f + i));
+        acc.warp_reduce();
+        if (lane == 0) w[j] = acc.value();
+    }
+}
+
+// Strided fibers: one thread per fiber; consecutive threads read consecutive
+// addresses because neighbouring fibers differ in the fastest index.
+template <typename T>
+__global__ void __launch_bounds__(kT) norms_strided_kernel(const T* __restrict__ A, ModeView v,
+                                                           double* __restrict__ w) {
+    const int64_t J = v.fibers();
+    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < J; j += (int64_t)gridDim.x * kT) {
+        NormAcc<T> acc;
+        const T* f = A + v.base(j);
+        for (int64_t i = 0; i < v.i; ++i) acc.add(__ldg(f + i * v.lf));
+        w[j] = acc.value();
+    }
+}
+
+// ---------------------------------------------------------------- integer weights
+__global__ void __launch_bounds__(kT) max_kernel(const double* __restrict__ w, int64_t J,
+                                                 unsigned long long* __restrict__ out) {
+    double m = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < J; j += (int64_t)gridDim.x * kT)
+        m = fmax(m, w[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void __launch_bounds__(kT) quantize_kernel(const double* __restrict__ w, int64_t J, int uniform,
+                                                      const unsigned long long* __restrict__ maxbits,
+                                                      uint64_t* __restrict__ W) {
+    const double wmax = uniform ? 0.0 : __longlong_as_double((long long)*maxbits);
+    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < J; j += (int64_t)gridDim.x * kT) {
+        uint64_t q = 1;
+        if (!uniform && wmax > 0.0) {
+            const double x = w[j];
+            q = x > 0.0 ? (uint64_t)ceil((x / wmax) * 16777216.0) : 0;
+        }
+        W[j] = q;
+    }
+}
+
+// ---------------------------------------------------------------- inclusive scan
+__device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t x, uint64_t* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t s = lane < kT / 32 ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kT / 32) sh[lane] = s;
+    }
+    __syncthreads();
+    const uint64_t off = warp ? sh[warp - 1] : 0;
+    __syncthreads();
+    return x + off;
+}
+
+__global__ void __launch_bounds__(kT) scan_block_sums(const uint64_t* __restrict__ W, int64_t J,
+                                                      uint64_t* __restrict__ bsum) {
+    __shared__ uint64_t sh[kT / 32];
+    const int64_t base = blockIdx.x * (int64_t)kScanBlock + threadIdx.x * kScanItems;
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < J) s += W[base + k];
+    s = block_inclusive_scan(s, sh);
+    if (threadIdx.x == kT - 1) bsum[blockIdx.x] = s;
+}
+
+// Exclusive scan of the block sums in one block, in chunks of kT.
+__global__ void __launch_bounds__(kT) scan_offsets(uint64_t* __restrict__ bsum, int64_t nb) {
+    __shared__ uint64_t sh[kT / 32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t c = 0; c < nb; c += kT) {
+        const int64_t k = c + threadIdx.x;
+        const uint64_t x = k < nb ? bsum[k] : 0;
+        const uint64_t inc = block_inclusive_scan(x, sh);
+        const uint64_t base = carry;
+        if (k < nb) bsum[k] = base + inc - x;
+        __syncthreads();
+        if (threadIdx.x == kT - 1) carry = base + inc;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kT) scan_final(const uint64_t* __restrict__ W, int64_t J,
+                                                 const uint64_t* __restrict__ boff, uint64_t* __restrict__ cdf) {
+    __shared__ uint64_t sh[kT / 32];
+    const int64_t base = blockIdx.x * (int64_t)kScanBlock + threadIdx.x * kScanItems;
+    uint64_t v[kScanItems];
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < J ? W[base + k] : 0;
+        s += v[k];
+    }
+    const uint64_t inc = block_inclusive_scan(s, sh);
+    uint64_t run = boff[blockIdx.x] + inc - s;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        run += v[k];
+        if (base + k < J) cdf[base + k] = run;
+    }
+}
+
+// ---------------------------------------------------------------- multinomial draws
+__global__ void __launch_bounds__(kT) sample_kernel(const uint64_t* __restrict__ cdf, const uint64_t* __restrict__ W,
+                                                    int64_t J, int64_t T_, uint64_t seed, uint32_t stream_id,
+                                                    int64_t* __restrict__ idx, double* __restrict__ scale) {
+    const uint64_t S = cdf[J - 1];
+    for (int64_t t = blockIdx.x * (int64_t)kT + threadIdx.x; t < T_; t += (int64_t)gridDim.x * kT) {
+        const uint4 x = philox_block(seed, stream_id, (uint64_t)(t >> 1));
+        const uint64_t r = (t & 1) ? ((uint64_t)x.w << 32 | x.z) : ((uint64_t)x.y << 32 | x.x);
+        const uint64_t v = __umul64hi(r, S);          // floor(r * S / 2^64)
+        int64_t lo = 0, hi = J - 1;                   // least j with cdf[j] > v
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cdf[mid] > v) hi = mid; else lo = mid + 1;
+        }
+        idx[t] = lo;
+        const double p = (double)W[lo] / (double)S;
+        scale[t] = 1.0 / sqrt((double)T_ * p);
+    }
+}
+
+// ---------------------------------------------------------------- rescaled gather
+template <typename T>
+__global__ void __launch_bounds__(kT) gather_kernel(const T* __restrict__ A, ModeView v,
+                                                    const int64_t* __restrict__ idx,
+                                                    const double* __restrict__ scale, int64_t T_,
+                                                    T* __restrict__ Cp) {
+    // one warp per sampled fiber; lanes walk the fiber
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)kT + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kT) >> 5;
+    for (int64_t t = warp; t < T_; t += nwarps) {
+        const T* f = A + v.base(idx[t]);
+        const T s = (T)scale[t];
+        T* out = Cp + t * v.i;
+        for (int64_t i = lane; i < v.i; i += 32) out[i] = s * __ldg(f + i * v.lf);
+    }
+}
+
+unsigned grid_for(int64_t n, int per_block, int cap) {
+    int64_t b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStream_t s) {
+    const int64_t J = v.fibers();
+    if (J == 0) return cudaSuccess;
+    ProfScope prof(kKNorms, (double)v.i * (double)J * sizeof(T), 2.0 * (double)v.i * (double)J, s);
+    if (v.lf == 1)
+        norms_contig_kernel<T><<<grid_for(J, kT / 32, 8192), kT, 0, s>>>(A, v.i, J, w);
+    else
+        norms_strided_kernel<T><<<grid_for(J, kT, 8192), kT, 0, s>>>(A, v, w);
+    note_launch();
+    return cudaGetLastError();
+}
+
+size_t quantize_scratch_bytes(int64_t) { return 256; }
+
+cudaError_t launch_quantize(const double* w, int64_t J, int prob, uint64_t* W, void* scratch, cudaStream_t s) {
+    auto* mx = reinterpret_cast<unsigned long long*>(scratch);
+    const int uniform = prob == TUCKER_PROB_UNIFORM;
+    if (!uniform) {
+        cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
+        max_kernel<<<grid_for(J, kT, 1024), kT, 0, s>>>(w, J, mx);
+        note_launch();
+    }
+    quantize_kernel<<<grid_for(J, kT, 8192), kT, 0, s>>>(w, J, uniform, mx, W);
+    note_launch();
+    return cudaGetLastError();
+}
+
+size_t sample_scratch_bytes(int64_t J) {
+    const int64_t nb = (J + kScanBlock - 1) / kScanBlock;
+    return sizeof(uint64_t) * (size_t)J + sizeof(uint64_t) * (size_t)(nb + 1) + 512;
+}
+
+cudaError_t launch_sample(const uint64_t* W, int64_t J, int64_t T_, uint64_t seed, uint32_t stream_id,
+                          int64_t* idx, double* scale, void* scratch, cudaStream_t s) {
+    if (T_ == 0) return cudaSuccess;
+    auto* cdf = reinterpret_cast<uint64_t*>(scratch);
+    auto* bsum = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(scratch) +
+                                             (((sizeof(uint64_t) * (size_t)J) + 255) & ~size_t(255)));
+    const int64_t nb = (J + kScanBlock - 1) / kScanBlock;
+    scan_block_sums<<<(unsigned)nb, kT, 0, s>>>(W, J, bsum);
+    note_launch();
+    scan_offsets<<<1, kT, 0, s>>>(bsum, nb);
+    note_launch();
+    scan_final<<<(unsigned)nb, kT, 0, s>>>(W, J, bsum, cdf);
+    note_launch();
+    sample_kernel<<<grid_for(T_, kT, 4096), kT, 0, s>>>(cdf, W, J, T_, seed, stream_id, idx, scale);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather(const T* A, const ModeView& v, const int64_t* idx, const double* scale, int64_t T_,
+                          T* Cp, cudaStream_t s) {
+    if (T_ == 0) return cudaSuccess;
+    ProfScope prof(kKGather, 2.0 * (double)v.i * (double)T_ * sizeof(T), (double)v.i * (double)T_, s);
+    gather_kernel<T><<<grid_for(T_, kT / 32, 8192), kT, 0, s>>>(A, v, idx, scale, T_, Cp);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fiber_norms<float>(const float*, const ModeView&, double*, cudaStream_t);
+template cudaError_t launch_fiber_norms<double>(const double*, const ModeView&, double*, cudaStream_t);
+template cudaError_t launch_gather<float>(const float*, const ModeView&, const int64_t*, const double*, int64_t,
+                                          float*, cudaStream_t);
+template cudaError_t launch_gather<double>(const double*, const ModeView&, const int64_t*, const double*, int64_t,
+                                           double*, cudaStream_t);
+
+}  // namespace tk

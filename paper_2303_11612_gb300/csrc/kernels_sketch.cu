@@ -1,0 +1,293 @@
+// Sketch kernels: Gaussian test matrices, the fused power step of Strategy A
+// (remark after Algorithm 1) and the range-form sketch with the Gaussian
+// generated inside the kernel.
+//
+// Power step X_out = A_(n) (A_(n)^T X_in). The unfolding's columns (mode-n
+// fibers) are streamed in tiles of JB fibers; for each tile T (JB x I_n):
+//   W = T X_in           (JB x L)   phase 1, split over I_n and reduced in smem
+//   X_acc += T^T W       (I_n x L)  phase 2, accumulated in registers
+// so every element of A is read once per power step. Each CTA accumulates the
+// tiles it owns and writes one partial; a second kernel sums the partials in a
+// fixed order, which makes the result independent of scheduling.
+#include "internal.h"
+
+namespace tk {
+
+namespace {
+
+constexpr int kT = kThreads;
+
+template <typename T>
+__global__ void __launch_bounds__(kT) gaussian_kernel(T* __restrict__ out, int64_t rows, int64_t cols,
+                                                      uint64_t seed, uint32_t stream_id) {
+    const int64_t n = rows * cols;
+    for (int64_t k = blockIdx.x * (int64_t)kT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kT) {
+        const int64_t l = k / rows, i = k - l * rows;      // column-major position
+        out[k] = gaussian_at<T>(seed, stream_id, (uint64_t)(i * cols + l));
+    }
+}
+
+// Loads the JB x I tile of fibers j0 .. j0+JB-1 into Ts (row stride ldt).
+template <typename T, int JB>
+__device__ __forceinline__ void load_tile(const T* __restrict__ A, const ModeView& v, int64_t j0,
+                                          int64_t J, T* Ts, int ldt, int64_t* bases) {
+    const int I = (int)v.i;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (v.lf == 1) {
+        // fibers are contiguous runs of I elements
+        for (int jj = warp; jj < JB; jj += kT / 32) {
+            const int64_t j = j0 + jj;
+            T* dst = Ts + jj * ldt;
+            if (j < J) {
+                const T* src = A + j * (int64_t)I;
+                for (int i = lane; i < I; i += 32) dst[i] = __ldg(src + i);
+            } else {
+                for (int i = lane; i < I; i += 32) dst[i] = T(0);
+            }
+        }
+    } else {
+        if (tid < JB) {
+            const int64_t j = j0 + tid;
+            bases[tid] = j < J ? v.base(j) : -1;
+        }
+        __syncthreads();
+        const int64_t lf = v.lf;
+        for (int e = tid; e < JB * I; e += kT) {
+            const int jj = e % JB, i = e / JB;
+            const int64_t b = bases[jj];
+            Ts[jj * ldt + i] = b >= 0 ? __ldg(A + b + (int64_t)i * lf) : T(0);
+        }
+    }
+}
+
+// RANGE == false: W = T X (phase 1). RANGE == true: W = Omega rows (Philox).
+template <typename T, int JB, int LG, int KR, bool RANGE>
+__global__ void __launch_bounds__(kT) power_kernel(const T* __restrict__ A, ModeView v,
+                                                   const T* __restrict__ X, int L,
+                                                   T* __restrict__ partial, int64_t tiles,
+                                                   uint64_t seed, uint32_t stream_id) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int KS = kT / JB;            // phase-1 split of the I dimension
+    const int I = (int)v.i;
+    const int64_t J = v.fibers();
+    const int l0 = blockIdx.x * LG;
+    const int lg = min(LG, L - l0);
+    const int ldt = I | 1;                 // odd row stride: conflict-free column reads
+    T* Xs = reinterpret_cast<T*>(smem_raw);               // [I][LG]
+    T* Ts = Xs + (RANGE ? 0 : I * LG);                     // [JB][ldt]
+    T* Wp = Ts + JB * ldt;                                 // [KS][JB][LG]
+    T* Ws = Wp + KS * JB * LG;                             // [JB][LG]
+    int64_t* bases = reinterpret_cast<int64_t*>(Ws + JB * LG);
+    const int tid = threadIdx.x;
+
+    if (!RANGE) {
+        for (int e = tid; e < I * LG; e += kT) {
+            const int i = e / LG, l = e % LG;
+            Xs[e] = l < lg ? X[(int64_t)(l0 + l) * I + i] : T(0);
+        }
+    }
+    T acc2[KR][LG];
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+#pragma unroll
+        for (int l = 0; l < LG; ++l) acc2[k][l] = T(0);
+
+    for (int64_t tile = blockIdx.y; tile < tiles; tile += gridDim.y) {
+        const int64_t j0 = tile * JB;
+        __syncthreads();                    // previous tile fully consumed
+        load_tile<T, JB>(A, v, j0, J, Ts, ldt, bases);
+        if (RANGE) {
+            for (int e = tid; e < JB * LG; e += kT) {
+                const int jj = e / LG, l = e % LG;
+                const int64_t j = j0 + jj;
+                Ws[e] = (j < J && l < lg)
+                            ? gaussian_at<T>(seed, stream_id, (uint64_t)(j * L + l0 + l))
+                            : T(0);
+            }
+            __syncthreads();
+        } else {
+            __syncthreads();
+            // phase 1: W(jj, :) partial over this thread's slice of I
+            const int jj = tid % JB, ks = tid / JB;
+            const int ib = (int)((int64_t)I * ks / KS), ie = (int)((int64_t)I * (ks + 1) / KS);
+            T acc[LG];
+#pragma unroll
+            for (int l = 0; l < LG; ++l) acc[l] = T(0);
+            const T* trow = Ts + jj * ldt;
+            for (int i = ib; i < ie; ++i) {
+                const T t = trow[i];
+                const T* xr = Xs + i * LG;
+#pragma unroll
+                for (int l = 0; l < LG; ++l) acc[l] = fma(t, xr[l], acc[l]);
+            }
+            T* wp = Wp + (ks * JB + jj) * LG;
+#pragma unroll
+            for (int l = 0; l < LG; ++l) wp[l] = acc[l];
+            __syncthreads();
+            for (int e = tid; e < JB * LG; e += kT) {
+                T s = T(0);
+#pragma unroll 4
+                for (int k = 0; k < KS; ++k) s += Wp[k * JB * LG + e];
+                Ws[e] = s;
+            }
+            __syncthreads();
+        }
+        // phase 2: X_acc(i, :) += sum_jj T(jj, i) W(jj, :)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const int i = tid + k * kT;
+            if (i < I) {
+                for (int jj = 0; jj < JB; ++jj) {
+                    const T t = Ts[jj * ldt + i];
+                    const T* w = Ws + jj * LG;
+#pragma unroll
+                    for (int l = 0; l < LG; ++l) acc2[k][l] = fma(t, w[l], acc2[k][l]);
+                }
+            }
+        }
+    }
+    T* out = partial + (int64_t)blockIdx.y * ((int64_t)I * L);
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+        const int i = tid + k * kT;
+        if (i < I) {
+#pragma unroll
+            for (int l = 0; l < LG; ++l)
+                if (l < lg) out[(int64_t)(l0 + l) * I + i] = acc2[k][l];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT) reduce_partials_kernel(const T* __restrict__ partial, int parts,
+                                                             int64_t count, T* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)kT + threadIdx.x; e < count; e += (int64_t)gridDim.x * kT) {
+        T s = T(0);
+        for (int p = 0; p < parts; ++p) s += partial[(int64_t)p * count + e];
+        out[e] = s;
+    }
+}
+
+template <typename T, int JB, int LG, int KR, bool RANGE>
+size_t power_smem(int I) {
+    const int ldt = I | 1;
+    return sizeof(T) * ((RANGE ? 0 : (size_t)I * LG) + (size_t)JB * ldt + (size_t)(kT / JB) * JB * LG +
+                        (size_t)JB * LG) + sizeof(int64_t) * JB + 16;
+}
+
+}  // namespace
+
+PowerPlan power_plan(const ModeView& v, int L, int elem_size, int num_sms) {
+    PowerPlan p{};
+    const int I = (int)v.i;
+    const bool dbl = elem_size == 8;
+    p.jb = (dbl || I > 512) ? 16 : 32;
+    p.lg = (dbl || I > 512) ? 16 : 32;
+    if (L < p.lg) p.lg = L <= 8 ? 8 : (L <= 16 ? 16 : p.lg);
+    p.groups = (L + p.lg - 1) / p.lg;
+    p.tiles = (v.fibers() + p.jb - 1) / p.jb;
+    int64_t want = (int64_t)num_sms / p.groups;
+    if (want < 1) want = 1;
+    p.parts = (int)(want < p.tiles ? want : p.tiles);
+    const int ldt = I | 1;
+    p.smem = (size_t)elem_size * ((size_t)I * p.lg + (size_t)p.jb * ldt + (size_t)(kThreads / p.jb) * p.jb * p.lg +
+                                  (size_t)p.jb * p.lg) + sizeof(int64_t) * p.jb + 16;
+    return p;
+}
+
+size_t power_partials_bytes(const PowerPlan& p, const ModeView& v, int L, int elem_size) {
+    return (size_t)p.parts * (size_t)v.i * (size_t)L * elem_size;
+}
+
+template <typename T>
+cudaError_t launch_gaussian(T* out, int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
+                            cudaStream_t s) {
+    const int64_t n = rows * cols;
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + kT - 1) / kT;
+    if (blocks > 4096) blocks = 4096;
+    gaussian_kernel<T><<<(unsigned)blocks, kT, 0, s>>>(out, rows, cols, seed, stream_id);
+    note_launch();
+    return cudaGetLastError();
+}
+
+namespace {
+template <typename T, int JB, int LG, int KR>
+cudaError_t launch_power_t(const T* A, const ModeView& v, const T* X_in, int L, T* partials,
+                           const PowerPlan& plan, bool range, uint64_t seed, uint32_t sid, cudaStream_t s) {
+    dim3 grid(plan.groups, plan.parts);
+    const int I = (int)v.i;
+    const double elems = (double)v.i * (double)v.fibers();
+    ProfScope prof(kKPower, elems * sizeof(T), (range ? 2.0 : 4.0) * elems * L, s);
+    if (range) {
+        auto k = power_kernel<T, JB, LG, KR, true>;
+        const size_t smem = power_smem<T, JB, LG, KR, true>(I);
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kT, smem, s>>>(A, v, X_in, L, partials, plan.tiles, seed, sid);
+        note_launch();
+    } else {
+        auto k = power_kernel<T, JB, LG, KR, false>;
+        const size_t smem = power_smem<T, JB, LG, KR, false>(I);
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kT, smem, s>>>(A, v, X_in, L, partials, plan.tiles, seed, sid);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int JB, int LG>
+cudaError_t dispatch_kr(const T* A, const ModeView& v, const T* X_in, int L, T* partials,
+                        const PowerPlan& plan, bool range, uint64_t seed, uint32_t sid, cudaStream_t s) {
+    const int kr = (int)((v.i + kT - 1) / kT);
+    switch (kr) {
+        case 1: return launch_power_t<T, JB, LG, 1>(A, v, X_in, L, partials, plan, range, seed, sid, s);
+        case 2: return launch_power_t<T, JB, LG, 2>(A, v, X_in, L, partials, plan, range, seed, sid, s);
+        case 3: return launch_power_t<T, JB, LG, 3>(A, v, X_in, L, partials, plan, range, seed, sid, s);
+        case 4: return launch_power_t<T, JB, LG, 4>(A, v, X_in, L, partials, plan, range, seed, sid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+template <typename T>
+cudaError_t launch_power(const T* A, const ModeView& v, const T* X_in, int L, T* X_out, void* partials,
+                         const PowerPlan& plan, bool range, uint64_t seed, uint32_t stream_id,
+                         cudaStream_t s) {
+    T* part = reinterpret_cast<T*>(partials);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 8) {
+        if (plan.jb == 16 && plan.lg == 16)
+            e = dispatch_kr<T, 16, 16>(A, v, X_in, L, part, plan, range, seed, stream_id, s);
+        else if (plan.jb == 16 && plan.lg == 8)
+            e = dispatch_kr<T, 16, 8>(A, v, X_in, L, part, plan, range, seed, stream_id, s);
+        else
+            return cudaErrorInvalidValue;
+    } else if (plan.jb == 32 && plan.lg == 32)
+        e = dispatch_kr<T, 32, 32>(A, v, X_in, L, part, plan, range, seed, stream_id, s);
+    else if (plan.jb == 32 && plan.lg == 16)
+        e = dispatch_kr<T, 32, 16>(A, v, X_in, L, part, plan, range, seed, stream_id, s);
+    else if (plan.jb == 32 && plan.lg == 8)
+        e = dispatch_kr<T, 32, 8>(A, v, X_in, L, part, plan, range, seed, stream_id, s);
+    else if (plan.jb == 16 && plan.lg == 16)
+        e = dispatch_kr<T, 16, 16>(A, v, X_in, L, part, plan, range, seed, stream_id, s);
+    else if (plan.jb == 16 && plan.lg == 8)
+        e = dispatch_kr<T, 16, 8>(A, v, X_in, L, part, plan, range, seed, stream_id, s);
+    else
+        return cudaErrorInvalidValue;
+    if (e != cudaSuccess) return e;
+    const int64_t count = v.i * (int64_t)L;
+    int64_t blocks = (count + kT - 1) / kT;
+    if (blocks > 2048) blocks = 2048;
+    reduce_partials_kernel<T><<<(unsigned)blocks, kT, 0, s>>>(part, plan.parts, count, X_out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gaussian<float>(float*, int64_t, int64_t, uint64_t, uint32_t, cudaStream_t);
+template cudaError_t launch_gaussian<double>(double*, int64_t, int64_t, uint64_t, uint32_t, cudaStream_t);
+template cudaError_t launch_power<float>(const float*, const ModeView&, const float*, int, float*, void*,
+                                         const PowerPlan&, bool, uint64_t, uint32_t, cudaStream_t);
+template cudaError_t launch_power<double>(const double*, const ModeView&, const double*, int, double*, void*,
+                                          const PowerPlan&, bool, uint64_t, uint32_t, cudaStream_t);
+
+}  // namespace tk

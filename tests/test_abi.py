@@ -1,0 +1,84 @@
+"""The C-ABI library loads and exports every entry point include/tucker.h
+declares; host-side argument checks reject bad input before any launch.
+Runs without a GPU (no compute calls)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:tucker_status|const char\*|int64_t)\s+(tucker_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2303_11612_gb300 import _binding
+    return _binding.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for must in ("tucker_rthosvd", "tucker_rsthosvd", "tucker_workspace_size", "tucker_status_string"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2303_11612_gb300 import _binding
+    assert set(declared()) <= set(_binding.exported_symbols())
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.tucker_status_string(s)
+
+
+def _ws(lib, dims, ranks, P=10, q=1, c=0, which=1):
+    from paper_2303_11612_gb300 import _binding as B
+    n = C.c_size_t(0)
+    st = lib.tucker_workspace_size(which, 0, B._i64(dims), len(dims), B._i32(ranks), P, q, c, None, C.byref(n))
+    return st, n.value
+
+
+def test_workspace_size_and_argument_checks(lib):
+    st, n = _ws(lib, (400, 400, 400), (20, 20, 20))
+    assert st == 0 and n > 0
+    st2, n2 = _ws(lib, (400, 400, 400), (20, 20, 20), c=4000)
+    assert st2 == 0 and n2 > n                   # AMM buffers
+    assert _ws(lib, (400, 400, 400), (401, 20, 20))[0] == 1       # R > I
+    assert _ws(lib, (400, 400, 400), (0, 20, 20))[0] == 1         # R < 1
+    assert _ws(lib, (400, 400, 400), (20, 20, 20), q=0)[0] == 1   # q < 1
+    assert _ws(lib, (400, 400, 400), (20, 20, 20), P=-1)[0] == 1  # P < 0
+    assert _ws(lib, (4096, 8, 8), (4, 4, 4))[0] == 6             # I_n beyond the built limit
+    assert _ws(lib, (), ())[0] == 1
+
+
+def test_drivers_reject_bad_arguments_without_touching_memory(lib):
+    from paper_2303_11612_gb300 import _binding as B
+    U = (C.c_void_p * 3)(1, 1, 1)
+    # rank larger than the dimension: rejected before any CUDA call
+    st = lib.tucker_rsthosvd(C.c_void_p(1), 0, B._i64((10, 10, 10)), 3, B._i32((11, 2, 2)), 5, 1, 0, 1,
+                             C.c_uint64(0), U, C.c_void_p(1), None)
+    assert st == 1
+    st = lib.tucker_rthosvd(None, 0, B._i64((10, 10, 10)), 3, B._i32((2, 2, 2)), 5, 1, 0, 1,
+                            C.c_uint64(0), U, C.c_void_p(1), None)
+    assert st == 1
+    o = B.make_opts()
+    o.struct_size = 4                                  # too small
+    st = lib.tucker_rsthosvd(C.c_void_p(1), 0, B._i64((10, 10, 10)), 3, B._i32((2, 2, 2)), 5, 1, 0, 1,
+                             C.c_uint64(0), U, C.c_void_p(1), C.byref(o))
+    assert st == 1
