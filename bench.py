@@ -181,6 +181,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single", default=None, choices=[v["name"] for v in VARIANTS],
+                    help="run one decomposition of one variant after one warm-up and exit (profiling case)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -199,6 +201,14 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     host = tensors()
+    if args.single:
+        v = next(x for x in VARIANTS if x["name"] == args.single)
+        A = torch.from_numpy(host[v["tensor"]]).cuda()
+        for _ in range(2):
+            tk.rsthosvd(A, DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED)
+        torch.cuda.synchronize()
+        print(json.dumps({"single": v["name"], "ok": True}))
+        return 0
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
     ws_bytes = max(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"]) for v in VARIANTS)
@@ -298,7 +308,8 @@ def main():
         src = open(os.path.join(ROOT, "paper_2303_11612_gb300", "csrc", "kernels_sketch.cu"), "rb").read()
         import hashlib
         if tr and tr.get("source_sha256") == hashlib.sha256(src).hexdigest():
-            traffic = tr["dram_bytes_per_launch"]
+            # DRAM bytes per algorithmic byte from one ncu capture, times this run's bytes per launch
+            traffic = tr["dram_bytes_per_algorithmic_byte"] * pw_bytes / max(pw_n, 1)
     except Exception:
         traffic = None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
