@@ -205,6 +205,26 @@ tucker_status tucker_relative_error(const void* A, tucker_dtype dt, const int64_
                                     const int32_t* ranks, void* const* U, const void* G,
                                     double* re, const tucker_opts* opts);
 
+/* ---------------------------------------------------------------- allocation-free variant
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory while they run (memory reserved once at start,
+ * or hosts where cudaMalloc/cudaFree would stall other work).
+ *
+ * tucker_power_step_noalloc computes exactly what tucker_power_step computes
+ * (X_out = A_(n) (A_(n)^T X_in), same arguments and layouts) but takes its
+ * partial sums from a fixed block of TUCKER_NOALLOC_SCRATCH_BYTES of device
+ * memory that belongs to the library (held on every GPU that loads it until
+ * the process exits) and calls no allocator. The first call on a device looks
+ * up that block's address and should come before any stream capture. Calls
+ * share the block, so calls whose GPU work overlaps race; order them. Returns
+ * TUCKER_ERR_UNSUPPORTED when one I_n x L partial (I_n * L * element size
+ * bytes) exceeds the block, and otherwise the statuses of tucker_power_step;
+ * it synchronises opts->stream before returning. */
+#define TUCKER_NOALLOC_SCRATCH_BYTES (8u << 20)
+tucker_status tucker_power_step_noalloc(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                                        int mode, const void* X_in, int64_t L, void* X_out,
+                                        const tucker_opts* opts);
+
 /* ---------------------------------------------------------------- measurement
  * Not part of the paper's method: counters for benchmarking the path. */
 

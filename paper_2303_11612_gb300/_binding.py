@@ -62,6 +62,7 @@ _SIGS = {
     "tucker_leading_factor": [_VP, _INT, _I64, _I64, _I64, _VP, _P(Opts)],
     "tucker_ttm": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _INT, _VP, _P(Opts)],
     "tucker_relative_error": [_VP, _INT, _P(_I64), _INT, _P(_I32), _P(_VP), _VP, _P(_DBL), _P(Opts)],
+    "tucker_power_step_noalloc": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _VP, _P(Opts)],
     "tucker_launch_count": [],
     "tucker_profile_enable": [_INT],
     "tucker_profile_read": [_INT, _P(_I64), _P(_DBL), _P(_DBL), _P(_DBL)],
@@ -344,3 +345,16 @@ def profile_read(kernel: str):
     _check("tucker_profile_read", lib().tucker_profile_read(KERNEL_CLASSES[kernel], C.byref(n), C.byref(ms),
                                                             C.byref(b), C.byref(f)))
     return int(n.value), ms.value, b.value, f.value
+
+
+def power_step_noalloc(A, dims, mode, X, stream=None):
+    """tucker_power_step_noalloc: the power step with the library's fixed scratch
+    block instead of an allocation (see include/tucker.h)."""
+    I = dims[mode]
+    L = X.shape[1]
+    out = factor_tensor(I, L, A.dtype, A.device)
+    o = make_opts(stream=stream)
+    _check("tucker_power_step_noalloc", lib().tucker_power_step_noalloc(A.data_ptr(), _dt(A), _i64(dims), len(dims),
+                                                                        mode, X.data_ptr(), L, out.data_ptr(),
+                                                                        C.byref(o)))
+    return out
