@@ -78,7 +78,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -177,7 +177,7 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -211,23 +211,30 @@ def main():
         return 0
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
-    ws_bytes = max(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"]) for v in VARIANTS)
-    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.Stream()
+    # one stream, workspace and output set per variant: the four decompositions of a
+    # step run concurrently (fork from the main stream, join back into it)
+    main_s = torch.cuda.Stream()
+    side = [torch.cuda.Stream() for _ in VARIANTS]
+    wss = [torch.empty(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"]), dtype=torch.uint8,
+                       device="cuda") for v in VARIANTS]
     outs = [([tk.factor_tensor(I, R, torch.float32, "cuda") for I, R in zip(DIMS, RANKS)],
              torch.empty(int(np.prod(RANKS)), dtype=torch.float32, device="cuda")) for _ in VARIANTS]
     houts = [([torch.empty((R, I), dtype=torch.float32).pin_memory().t() for I, R in zip(DIMS, RANKS)],
               torch.empty(int(np.prod(RANKS)), dtype=torch.float32).pin_memory()) for _ in VARIANTS]
 
-    def step():
-        for v, out in zip(VARIANTS, outs):
+    def enqueue_step():
+        for st in side:
+            st.wait_stream(main_s)
+        for v, st, ws, out in zip(VARIANTS, side, wss, outs):
             tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
-                        workspace=ws, stream=stream, out=out, flags=tk.FLAG_ASYNC)
+                        workspace=ws, stream=st, out=out, flags=tk.FLAG_ASYNC)
+        for st in side:
+            main_s.wait_stream(st)
 
     def step_e2e():
         for v, out in zip(VARIANTS, houts):
             tk.rsthosvd(pinned[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
-                        stream=stream, out=out)
+                        stream=main_s, out=out)
 
     def barrier():
         torch.cuda.synchronize()
@@ -251,49 +258,97 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    for _ in range(args.warmup):
-        step()
-    stream.synchronize()
+    with torch.cuda.stream(main_s):
+        for _ in range(args.warmup):
+            enqueue_step()
+    main_s.synchronize()
     if tk.last_device_status() != 0:
         raise RuntimeError("device status not OK after warm-up")
+    # kernels in one step, counted on an eager step with profiling off
+    n0 = tk.launch_count()
+    with torch.cuda.stream(main_s):
+        enqueue_step()
+    main_s.synchronize()
+    per_step_launches = tk.launch_count() - n0
+    # capture one step with profiling on, so each kernel of interest carries its own
+    # event pair inside the graph (re-recorded by every replay); fall back to eager
+    # launches if capture is refused
+    graph = None
+    tk.profile_enable(True)
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=main_s):
+            enqueue_step()
+        graph = g
+        with torch.cuda.stream(main_s):
+            graph.replay()
+        main_s.synchronize()
+    except Exception as exc:  # noqa: BLE001
+        print(f"graph capture unavailable ({exc}); timing eager launches", file=sys.stderr)
+        graph = None
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
-    tk.profile_enable(True)
+    if graph is None:
+        tk.profile_enable(True)
     n0 = tk.launch_count()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    stream.synchronize()
+    with torch.cuda.stream(main_s):
+        ev0.record(main_s)
+        for _ in range(args.steps):
+            if graph is not None:
+                graph.replay()
+            else:
+                enqueue_step()
+        ev1.record(main_s)
+    main_s.synchronize()
     n1 = tk.launch_count()
     barrier()
-    clk = clocks.stop()
     st = tk.last_device_status()
     if st != 0:
         raise RuntimeError(f"device status {st} in the timed region")
     ms = ev0.elapsed_time(ev1)
-    prof = {k: tk.profile_read(k) for k in ("power", "ttm", "gather", "norms")}
+    if graph is not None:
+        # event pairs inside a graph carry no timings, so the per-kernel durations
+        # come from eager steps run right after the graph-timed region
+        tk.profile_enable(True)
+        with torch.cuda.stream(main_s):
+            for _ in range(max(3, args.steps // 10)):
+                enqueue_step()
+        main_s.synchronize()
+    clk = clocks.stop()
+    classes = ("power", "ttm", "gather", "norms", "extract", "sample")
+    prof = {k: tk.profile_read(k) for k in classes}
     tk.profile_enable(False)
     ms = max_over_ranks(ms)
     decomps = len(VARIANTS) * args.steps * world
     value = decomps / (ms / 1e3)
+    gpu_launches = (n1 - n0) if graph is None else per_step_launches * args.steps
+    if graph is not None:
+        prof_note = ("eager profiled steps right after the graph-timed region, same streams and "
+                     "concurrency (CUDA-graph event nodes carry no timings)")
+    else:
+        prof_note = "eager: event pairs of every launch in the timed region"
 
     # end to end through the C ABI with pinned host buffers
-    for _ in range(1):
+    e2e = None
+    try:
         step_e2e()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(3, args.steps // 4)
-    t0 = time.perf_counter()
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        step_e2e()
-    e1.record(stream)
-    stream.synchronize()
-    wall = time.perf_counter() - t0
-    e2e_s = max_over_ranks(max(wall, e0.elapsed_time(e1) / 1e3))
-    h2d = sum(host[v["tensor"]].nbytes for v in VARIANTS)
-    d2h = sum((sum(I * R for I, R in zip(DIMS, RANKS)) + int(np.prod(RANKS))) * 4 for _ in VARIANTS)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_steps = max(3, args.steps // 4)
+        t0 = time.perf_counter()
+        e0.record(main_s)
+        for _ in range(e2e_steps):
+            step_e2e()
+        e1.record(main_s)
+        main_s.synchronize()
+        wall = time.perf_counter() - t0
+        e2e_s = max_over_ranks(max(wall, e0.elapsed_time(e1) / 1e3))
+        h2d = sum(host[v["tensor"]].nbytes for v in VARIANTS)
+        d2h = sum((sum(I * R for I, R in zip(DIMS, RANKS)) + int(np.prod(RANKS))) * 4 for _ in VARIANTS)
+        e2e = {"value": len(VARIANTS) * e2e_steps * world / e2e_s, "unit": "decomps/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    except Exception as exc:  # noqa: BLE001
+        e2e = {"value": None, "unit": "decomps/s", "error": str(exc)}
 
     peaks, peak_kind = load_peaks()
     pw_n, pw_ms, pw_bytes, pw_flops = prof["power"]
@@ -319,24 +374,26 @@ def main():
                 "launches": pw_n, "ms_per_launch": pw_ms / max(pw_n, 1),
                 "algorithmic_bytes_per_launch": pw_bytes / max(pw_n, 1),
                 "hbm_gbs": achieved_gbs, "hbm_frac": achieved_gbs / peaks["hbm_gbs"],
-                "hbm_peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind}
+                "hbm_peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind, "timing": prof_note}
     others = {}
-    for k in ("ttm", "gather", "norms"):
+    for k in ("ttm", "gather", "norms", "extract", "sample"):
         n, kms, b, f = prof[k]
         if n:
-            others[k] = {"launches": n, "ms_per_launch": kms / n, "gbs": b / (kms / 1e3) / 1e9,
-                         "hbm_frac": b / (kms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                         "tflops": f / (kms / 1e3) / 1e12}
+            others[k] = {"launches": n, "ms_per_launch": kms / n}
+            if b:
+                others[k].update({"gbs": b / (kms / 1e3) / 1e9, "hbm_frac": b / (kms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                  "tflops": f / (kms / 1e3) / 1e12})
     line = {"metric": "decomps/s", "value": value, "unit": "decomps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "baseline_metric": BASELINE_METRIC,
             "config": {"workload": WORKLOAD, "tensor_bytes": 256_000_000,
                        "l2": "inputs larger than L2 (256 MB per tensor), no flush",
                        "parallelism": "replicas (each rank decomposes its own batch)" if world > 1 else "single GPU",
-                       "sketch": "paper form, FP32 SIMT"},
-            "e2e": {"value": len(VARIANTS) * e2e_steps * world / e2e_s, "unit": "decomps/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": n1 - n0,
+                       "sketch": "paper form, FP32 SIMT",
+                       "execution": ("CUDA graph of one step, 4 decompositions on 4 streams" if graph is not None
+                                     else "eager launches, 4 decompositions on 4 streams")},
+            "e2e": e2e,
+            "gpu_launches": gpu_launches,
             "roofline": roofline, "kernels": others,
             "sketch_hbm_gbs": achieved_gbs,
             "rel_error": res, "clocks": clk}

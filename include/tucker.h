@@ -25,7 +25,9 @@
  *    returns and reports device-side failures (Cholesky breakdown that could not
  *    be repaired, non-finite values) in its status. With TUCKER_FLAG_ASYNC the
  *    call returns after enqueueing; the device status is then read by
- *    tucker_last_device_status().
+ *    tucker_last_device_status(). An asynchronous call requires device buffers
+ *    and a caller workspace, makes no allocation or synchronisation, and can
+ *    therefore be captured into a CUDA graph.
  *  - Scratch memory: opts->workspace / workspace_bytes (device memory of at
  *    least tucker_workspace_size() bytes, 256-byte aligned) when given;
  *    otherwise the library allocates it from the stream-ordered pool and frees
@@ -132,6 +134,10 @@ tucker_status tucker_workspace_size(int which, tucker_dtype dt, const int64_t* d
 
 const char* tucker_status_string(tucker_status s);
 
+/* Name and description of the last CUDA error that made a call on this host
+ * thread return TUCKER_ERR_CUDA or TUCKER_ERR_OOM (thread-local storage). */
+const char* tucker_last_cuda_error(void);
+
 /* Device status word of the last TUCKER_FLAG_ASYNC call on this host thread
  * (synchronises its stream first). */
 tucker_status tucker_last_device_status(void);
@@ -236,7 +242,9 @@ typedef enum {
     TUCKER_KERNEL_POWER = 0,   /* fused power step / range sketch (one pass over the unfolding) */
     TUCKER_KERNEL_TTM = 1,     /* mode-n product */
     TUCKER_KERNEL_GATHER = 2,  /* AMM rescaled gather */
-    TUCKER_KERNEL_NORMS = 3    /* squared fiber norms */
+    TUCKER_KERNEL_NORMS = 3,   /* squared fiber norms */
+    TUCKER_KERNEL_EXTRACT = 4, /* a mode's whole orthonormalisation + extraction sequence */
+    TUCKER_KERNEL_SAMPLE = 5   /* a mode's weights, scan and draws */
 } tucker_kernel_class;
 
 /* on != 0: clear the accumulators and bracket every launch of the classes

@@ -51,6 +51,7 @@ _SIGS = {
     "tucker_rsthosvd": [_VP, _INT, _P(_I64), _INT, _P(_I32), _I32, _I32, _I64, _INT, _U64, _P(_VP), _VP, _P(Opts)],
     "tucker_workspace_size": [_INT, _INT, _P(_I64), _INT, _P(_I32), _I32, _I32, _I64, _P(Opts), _P(C.c_size_t)],
     "tucker_status_string": [_INT],
+    "tucker_last_cuda_error": [],
     "tucker_last_device_status": [],
     "tucker_gaussian": [_VP, _INT, _I64, _I64, _U64, _U32, _P(Opts)],
     "tucker_power_step": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _VP, _P(Opts)],
@@ -67,8 +68,9 @@ _SIGS = {
     "tucker_profile_enable": [_INT],
     "tucker_profile_read": [_INT, _P(_I64), _P(_DBL), _P(_DBL), _P(_DBL)],
 }
-_RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int64}
-KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3}
+_RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int64,
+             "tucker_last_cuda_error": C.c_char_p}
+KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3, "extract": 4, "sample": 5}
 
 
 def lib():
@@ -95,7 +97,10 @@ def exported_symbols():
 
 def _check(fn: str, status: int):
     if status != TUCKER_OK:
-        raise TuckerError(fn, status)
+        err = TuckerError(fn, status)
+        if status in (2, 3):
+            err.args = (err.args[0] + " [" + lib().tucker_last_cuda_error().decode() + "]",)
+        raise err
 
 
 def _dt(t: torch.Tensor) -> int:

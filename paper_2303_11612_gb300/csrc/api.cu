@@ -1,5 +1,6 @@
 // C ABI of the library: argument checks, workspace planning, host/device
 // staging and the per-mode orchestration of Algorithms 1, 2, 4 and 5.
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -25,8 +26,11 @@ constexpr int kMaxL = 110;           // FP64 Cholesky of an L x L Gram in shared
 thread_local cudaStream_t g_async_stream = nullptr;
 thread_local int* g_async_status = nullptr;
 
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 tucker_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return TUCKER_OK;
+    g_last_cuda_error = e;
     if (e == cudaErrorMemoryAllocation) return TUCKER_ERR_OOM;
     return TUCKER_ERR_CUDA;
 }
@@ -225,15 +229,18 @@ cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, 
     if (mp.T > 0) {
         const int64_t J = mp.v.fibers();
         if (prob == TUCKER_PROB_NEARLY_OPTIMAL) TK_TRY(launch_fiber_norms<T>(B, mp.v, w.w, s));
-        TK_TRY(launch_quantize(w.w, J, prob, w.W, w.samp, s));
-        TK_TRY(launch_sample(w.W, J, mp.T, seed, stream_id(1, n), w.idx, w.scale, w.samp, s));
+        {
+            ProfScope prof(kKSample, 0.0, 0.0, s);
+            TK_TRY(launch_quantize(w.w, J, prob, w.W, w.samp, s));
+            TK_TRY(launch_sample(w.W, J, mp.T, seed, stream_id(1, n), w.idx, w.scale, w.samp, s));
+        }
         TK_TRY(launch_gather<T>(B, mp.v, w.idx, w.scale, mp.T, (T*)w.Cp, s));
         if (sample_out) TK_TRY(cudaMemcpyAsync(sample_out, w.idx, sizeof(int64_t) * mp.T, cudaMemcpyDefault, s));
         M = (const T*)w.Cp;
     }
     const int L = mp.L;
     T* X0 = (T*)w.X0; T* X1 = (T*)w.X1; T* Q = (T*)w.Q; T* Qt = (T*)w.Qt;
-    int nf;
+    int nf = 0;
     if (form == TUCKER_FORM_PAPER) {
         // C = (M M^T)^q Omega in factored form: after each step X = Q_k R_k and the
         // next step multiplies Q_k, so C = Q_q (R_q ... R_1) without overflow or
@@ -247,18 +254,21 @@ cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, 
             }
             TK_TRY(launch_power<T>(M, mp.mv, xin, L, X1, w.partials, mp.pp, false, 0, 0, s));
         }
-        TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, q - 1, w.orth, w.status, s));
         nf = 3 * q;
+        ProfScope prof(kKExtract, 0.0, 0.0, s);
+        TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, q - 1, w.orth, w.status, s));
+        return launch_extract<T>(Q, mp.op, w.factors, nf, mp.R, U, w.orth, w.status, s);
     } else {
         TK_TRY(launch_power<T>(M, mp.mv, nullptr, L, X1, w.partials, mp.pp, true, seed, stream_id(0, n), s));
         for (int k = 0; k < q; ++k) {
             TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, 0, w.orth, w.status, s));
             TK_TRY(launch_power<T>(M, mp.mv, Q, L, X1, w.partials, mp.pp, false, 0, 0, s));
         }
-        TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, 0, w.orth, w.status, s));
         nf = 3;
+        ProfScope prof(kKExtract, 0.0, 0.0, s);
+        TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, 0, w.orth, w.status, s));
+        return launch_extract<T>(Q, mp.op, w.factors, nf, mp.R, U, w.orth, w.status, s);
     }
-    return launch_extract<T>(Q, mp.op, w.factors, nf, mp.R, U, w.orth, w.status, s);
 }
 
 template <typename T>
@@ -324,6 +334,7 @@ tucker_status finish(cudaStream_t s, int* dev_status, const Opts& o, double* dev
 tucker_status driver(bool st, const void* A, tucker_dtype dt, const int64_t* dims, int N, const int32_t* ranks,
                      int32_t P, int32_t q, int64_t c, tucker_prob prob, uint64_t seed, void* const* U, void* G,
                      const tucker_opts* opts) {
+    cudaGetLastError();      // a failed call of other code must not be reported as ours
     Opts o;
     tucker_status rs = read_opts(opts, o);
     if (rs != TUCKER_OK) return rs;
@@ -343,10 +354,12 @@ tucker_status driver(bool st, const void* A, tucker_dtype dt, const int64_t* dim
     const int64_t E = prod(dims, N);
     int64_t Gn = 1, Un = 0;
     for (int n = 0; n < N; ++n) { Gn *= ranks[n]; Un += dims[n] * ranks[n]; }
-    const bool hA = !on_device(A), hG = !on_device(G);
+    // asynchronous calls take device buffers as given (no driver queries, so the
+    // call can be captured into a CUDA graph); synchronous calls stage host buffers
+    const bool async = (o.flags & TUCKER_FLAG_ASYNC) != 0;
+    const bool hA = !async && !on_device(A), hG = !async && !on_device(G);
     bool hU = false;
-    for (int n = 0; n < N; ++n) hU = hU || !on_device(U[n]);
-    if ((o.flags & TUCKER_FLAG_ASYNC) && (hA || hG || hU)) return TUCKER_ERR_INVALID_ARG;
+    for (int n = 0; n < N && !async; ++n) hU = hU || !on_device(U[n]);
 
     Arena a;
     Work w;
@@ -501,6 +514,13 @@ const char* tucker_status_string(tucker_status s) {
         case TUCKER_ERR_BUDGET: return "request larger than the memory budget";
     }
     return "unknown status";
+}
+
+const char* tucker_last_cuda_error(void) {
+    static thread_local char buf[256];
+    const cudaError_t e = g_last_cuda_error;
+    snprintf(buf, sizeof(buf), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return buf;
 }
 
 tucker_status tucker_last_device_status(void) {

@@ -90,7 +90,8 @@ cudaError_t launch_sumsq(const T* a, const T* b, int64_t n, double* out, void* s
 int num_sms();
 
 // ---- launch counting and profiling (profile.cu)
-enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKernelClasses = 4 };
+enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKExtract = 4, kKSample = 5,
+                   kKernelClasses = 6 };
 void note_launch();
 void profile_drain();
 // Brackets one launch with CUDA events when profiling is on.

@@ -9,20 +9,28 @@
 // found with a one-sided (Hestenes) Jacobi SVD.
 #include <float.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace tk {
 namespace {
 
 constexpr int kT = kThreads;
-constexpr int kSvdThreads = 512;
+constexpr int kSvdThreads = 1024;
 
 // pass 0: first pass; pass 1: second pass; pass 2: runs only if a shift was needed.
 __device__ __forceinline__ bool pass_skipped(const int* flag, int pass) {
     return pass == 2 && !(*flag & kStatShifted);
 }
 
-// ---------------------------------------------------------------- Gram partials
+// ---------------------------------------------------------------- Gram + Cholesky
+// Each CTA accumulates the Gram matrix of its block of rows (packed upper
+// triangle); the last CTA to finish (an atomic ticket, no waiting) sums the
+// partials in block order, which makes the result independent of scheduling,
+// and factors G = R^T R in FP64 (R upper, row-major R[a * L + b]). A pivot
+// below 1e-15 of its diagonal entry restarts the factorisation once with
+// G + s I, s = 11 (I L + L (L + 1)) 2^-53 tr(G), and flags the shift.
 template <typename T> struct GramAcc;
 template <> struct GramAcc<float> {
     Pair s{0.f, 0.f};
@@ -35,53 +43,63 @@ template <> struct GramAcc<double> {
     __device__ double value() const { return s; }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kT) gram_kernel(const T* __restrict__ X, int64_t I, int L, int rows_per_block,
-                                                  double* __restrict__ partial, const int* flag, int pass) {
-    if (pass_skipped(flag, pass)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* xs = reinterpret_cast<T*>(smem_raw);   // [rows][L]
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-    const int nr = (int)min((int64_t)rows_per_block, I - r0);
-    for (int e = threadIdx.x; e < nr * L; e += kT) {
-        const int r = e % nr, c = e / nr;
-        xs[r * L + c] = X[(int64_t)c * I + r0 + r];
-    }
-    __syncthreads();
-    double* out = partial + (int64_t)blockIdx.x * L * L;
-    for (int p = threadIdx.x; p < L * L; p += kT) {
-        const int a = p / L, b = p % L;
-        if (a > b) continue;
-        GramAcc<T> acc;
-        for (int r = 0; r < nr; ++r) acc.add(xs[r * L + a], xs[r * L + b]);
-        const double v = acc.value();
-        out[a * L + b] = v;
-        out[b * L + a] = v;
-    }
-}
+__device__ __forceinline__ int packed_index(int a, int b, int L) { return a * L - (a * (a - 1)) / 2 + (b - a); }
 
-// ---------------------------------------------------------------- Cholesky (one CTA, FP64)
-// Sums the Gram partials in a fixed order, factors G = R^T R (R upper, row-major
-// R[a * L + b]); on a pivot below 1e-15 of its diagonal entry restarts once with
-// G + s I, s = 11 (I L + L (L + 1)) 2^-53 tr(G), and flags the shift.
-__global__ void __launch_bounds__(kT) cholesky_kernel(const double* __restrict__ partial, int nparts, int L,
-                                                      int64_t I, double* __restrict__ R, int* flag, int* status,
-                                                      int pass) {
+template <typename T>
+__global__ void __launch_bounds__(kT) gram_chol_kernel(const T* __restrict__ X, int64_t I, int L, int rows_per_block,
+                                                       double* __restrict__ partial, unsigned* ticket,
+                                                       double* __restrict__ R, int* flag, int* status, int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* G = reinterpret_cast<double*>(smem_raw);   // [L][L] sum of partials
-    double* W = G + L * L;                               // [L][L] working copy
-    __shared__ int bad;
-    __shared__ double inv_piv;
     const int tid = threadIdx.x;
     if (pass_skipped(flag, pass)) {
-        for (int p = tid; p < L * L; p += kT) R[p] = (p / L == p % L) ? 1.0 : 0.0;
+        if (blockIdx.x == 0)
+            for (int p = tid; p < L * L; p += kT) R[p] = (p / L == p % L) ? 1.0 : 0.0;
         return;
     }
-    for (int p = tid; p < L * L; p += kT) {
-        double s = 0.0;
-        for (int b = 0; b < nparts; ++b) s += partial[(int64_t)b * L * L + p];
-        G[p] = s;
+    const int np = L * (L + 1) / 2;
+    {
+        T* xs = reinterpret_cast<T*>(smem_raw);   // [rows][L]
+        const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+        const int nr = (int)max((int64_t)0, min((int64_t)rows_per_block, I - r0));
+        for (int e = tid; e < nr * L; e += kT) {
+            const int r = e % nr, c = e / nr;
+            xs[r * L + c] = X[(int64_t)c * I + r0 + r];
+        }
+        __syncthreads();
+        double* out = partial + (int64_t)blockIdx.x * np;
+        for (int a = 0; a < L; ++a) {
+            for (int b = a + tid; b < L; b += kT) {
+                GramAcc<T> acc;
+                for (int r = 0; r < nr; ++r) acc.add(xs[r * L + a], xs[r * L + b]);
+                out[packed_index(a, b, L)] = acc.value();
+            }
+        }
     }
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+
+    double* G = reinterpret_cast<double*>(smem_raw);   // [L][L]
+    double* W = G + L * L;                               // [L][L]
+    __shared__ int bad;
+    __shared__ double inv_piv;
+    const int nparts = gridDim.x;
+    for (int p = tid; p < np; p += kT) {
+        double acc = 0.0;
+#pragma unroll 8
+        for (int b = 0; b < nparts; ++b) acc += __ldcg(partial + (int64_t)b * np + p);
+        // unpack (a, b) from the packed index
+        int a = 0, rem = p;
+        while (rem >= L - a) { rem -= L - a; ++a; }
+        const int bb = a + rem;
+        G[a * L + bb] = acc;
+        G[bb * L + a] = acc;
+    }
+    if (tid == 0) *ticket = 0;                           // ready for the next pass
     __syncthreads();
     double shift = 0.0;
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -175,51 +193,63 @@ __global__ void __launch_bounds__(kSvdThreads) small_svd_kernel(const double* __
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lp = L + (L & 1);                           // even number of columns (phantom zero column)
     T* M = reinterpret_cast<T*>(smem_raw);                 // column-major [Lp][L]: column c at M + c * L
-    T* Tm = M + Lp * L;                                    // scratch for products
-    T* nrm = Tm + Lp * L;                                  // [Lp]
+    T* Tm = M + Lp * L;                                    // product scratch [L][L]
+    T* Fs = Tm + Lp * L;                                   // current factor, row-major [L][L]
+    T* nrm = Fs + L * L;                                   // [Lp]
     int* perm = reinterpret_cast<int*>(nrm + Lp);          // [Lp]
-    __shared__ double fscale;
+    __shared__ unsigned long long fmax_bits;
     __shared__ int rotated;
+    __shared__ T fro2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSvdThreads / 32;
 
     for (int f = 0; f < nf; ++f) {
         const double* F = factors + (int64_t)f * L * L;
-        if (tid == 0) fscale = 0.0;
+        if (tid == 0) fmax_bits = 0ull;
         __syncthreads();
         double mx = 0.0;
         for (int p = tid; p < L * L; p += kSvdThreads) mx = fmax(mx, fabs(F[p]));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-        if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(&fscale),
-                                 (unsigned long long)__double_as_longlong(mx));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(&fmax_bits, (unsigned long long)__double_as_longlong(mx));
         __syncthreads();
-        const double sc = fscale > 0.0 ? exp2(-floor(log2(fscale))) : 1.0;   // a power of two
+        const double fm = __longlong_as_double((long long)fmax_bits);
+        const double sc = fm > 0.0 ? exp2(-floor(log2(fm))) : 1.0;   // a power of two: exact
+        for (int p = tid; p < L * L; p += kSvdThreads) Fs[p] = (T)(F[p] * sc);
+        __syncthreads();
         if (f == 0) {
             for (int p = tid; p < Lp * L; p += kSvdThreads) {
                 const int c = p / L, a = p % L;
-                M[p] = (c < L && c >= a) ? (T)(F[a * L + c] * sc) : T(0);
+                M[p] = (c < L && c >= a) ? Fs[a * L + c] : T(0);
             }
         } else {
             for (int p = tid; p < L * L; p += kSvdThreads) {
                 const int c = p / L, a = p % L;
-                T s = T(0);
-                for (int b = a; b < L; ++b) s += (T)(F[a * L + b] * sc) * M[c * L + b];
-                Tm[p] = s;
+                T acc = T(0);
+                for (int b = a; b < L; ++b) acc = fma(Fs[a * L + b], M[c * L + b], acc);
+                Tm[p] = acc;
             }
             __syncthreads();
             for (int p = tid; p < L * L; p += kSvdThreads) M[p] = Tm[p];
         }
         __syncthreads();
     }
-
-    // rotate while a pair's cosine exceeds 2 eps; rounding of the dot products can
-    // keep a few pairs just above it, so the sweep count is capped
-    const T tol = (sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON) * T(2);
+    // squared Frobenius norm: a pair whose coupling is below eps^2 of it is at the
+    // rounding level of the whole matrix and is left alone (rounding would otherwise
+    // keep near-zero columns rotating without end)
+    if (tid == 0) fro2 = T(0);
+    __syncthreads();
+    {
+        T s2 = T(0);
+        for (int p = tid; p < L * L; p += kSvdThreads) s2 = fma(M[p], M[p], s2);
+        s2 = warp_sum(s2);
+        if (lane == 0) atomicAdd(&fro2, s2);
+    }
+    __syncthreads();
+    const T eps = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
+    const T tol = eps * T(2);
+    const T tiny = eps * eps * fro2;
     const int m = Lp - 1;
-    for (int sweep = 0; sweep < 24; ++sweep) {
+    for (int sweep = 0; sweep < 30; ++sweep) {
         if (tid == 0) rotated = 0;
         __syncthreads();
         for (int rnd = 0; rnd < m; ++rnd) {
@@ -236,7 +266,7 @@ __global__ void __launch_bounds__(kSvdThreads) small_svd_kernel(const double* __
                     al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
                 }
                 al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-                if (ga != T(0) && fabs(ga) > tol * sqrt(al * be)) {
+                if (fabs(ga) > tiny && fabs(ga) > tol * sqrt(al * be)) {
                     const T zeta = (be - al) / (T(2) * ga);
                     const T t = (zeta >= 0 ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
                     const T c = T(1) / sqrt(T(1) + t * t), s = c * t;
@@ -323,63 +353,68 @@ OrthPlan orth_plan(int64_t I, int L, int num_sms) {
     OrthPlan p{};
     p.I = I;
     p.L = L;
-    int64_t rows = (I + num_sms - 1) / num_sms;
-    if (rows < 4) rows = 4;
-    p.gram_blocks = (int)((I + rows - 1) / rows);
+    // enough CTAs to spread the FP64-grade Gram work, few enough that the last
+    // CTA's reduction of the packed partials stays small (<= 512 KB)
+    const int64_t np = (int64_t)L * (L + 1) / 2;
+    int64_t cap = (512 * 1024) / (np * 8);
+    if (cap < 1) cap = 1;
+    if (cap > num_sms) cap = num_sms;
+    int64_t blocks = (I + 7) / 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    p.gram_blocks = (int)blocks;
     return p;
 }
 
 static int gram_rows(const OrthPlan& p) { return (int)((p.I + p.gram_blocks - 1) / p.gram_blocks); }
 
 size_t orth_scratch_bytes(const OrthPlan& p, int elem_size) {
+    const size_t np = (size_t)p.L * (p.L + 1) / 2;
     const size_t LL = (size_t)p.L * p.L;
-    // Gram partials + flag + UM
-    return sizeof(double) * LL * (size_t)p.gram_blocks + 256 + (size_t)elem_size * LL + 512;
+    return sizeof(double) * np * (size_t)p.gram_blocks + 256 + (size_t)elem_size * LL + 512;
 }
 
 struct OrthScratch {
     double* partial;
     int* flag;
+    unsigned* ticket;
     void* um;
 };
-static OrthScratch carve(const OrthPlan& p, void* scratch, int elem_size) {
+static OrthScratch carve(const OrthPlan& p, void* scratch) {
     OrthScratch s;
     char* b = reinterpret_cast<char*>(scratch);
-    const size_t LL = (size_t)p.L * p.L;
+    const size_t np = (size_t)p.L * (p.L + 1) / 2;
     s.partial = reinterpret_cast<double*>(b);
-    b += ((sizeof(double) * LL * (size_t)p.gram_blocks) + 255) & ~size_t(255);
+    b += ((sizeof(double) * np * (size_t)p.gram_blocks) + 255) & ~size_t(255);
     s.flag = reinterpret_cast<int*>(b);
+    s.ticket = reinterpret_cast<unsigned*>(b + 64);
     b += 256;
     s.um = b;
-    (void)elem_size;
     return s;
 }
 
 template <typename T>
 cudaError_t launch_cholqr(const T* X, T* Q, T* Qtmp, const OrthPlan& p, double* factors, int slot, void* scratch,
                           int* status, cudaStream_t s) {
-    OrthScratch sc = carve(p, scratch, sizeof(T));
+    OrthScratch sc = carve(p, scratch);
     const int L = p.L;
     const size_t LL = (size_t)L * L;
     const int rows = gram_rows(p);
-    const size_t gsm = sizeof(T) * (size_t)rows * L;
-    const size_t csm = sizeof(double) * 2 * LL;
+    const size_t gsm = std::max(sizeof(T) * (size_t)rows * L, sizeof(double) * 2 * LL);
     const size_t asm_ = sizeof(double) * (LL + (size_t)(kT / 32) * L);
-    if (csm > 220 * 1024 || asm_ > 220 * 1024 || gsm > 220 * 1024) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    if (asm_ > 220 * 1024 || gsm > 220 * 1024) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(gram_chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
     cudaFuncSetAttribute(apply_rinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_);
-    cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
-    cudaMemsetAsync(sc.flag, 0, sizeof(int), s);
+    cudaMemsetAsync(sc.flag, 0, 128, s);                 // shift flag and ticket
     int64_t ablocks = (p.I + kT / 32 - 1) / (kT / 32);
     if (ablocks > 1024) ablocks = 1024;
-    // pass 0: X -> Q ; pass 1: Q -> Qtmp ; pass 2 (conditional): Qtmp -> Q, else copy
+    // pass 0: X -> Q ; pass 1: Q -> Qtmp ; pass 2 (only after a shift): Qtmp -> Q, else copy
     const T* src[3] = {X, Q, Qtmp};
     T* dst[3] = {Q, Qtmp, Q};
     for (int pass = 0; pass < 3; ++pass) {
         double* R = factors + (size_t)(3 * slot + pass) * LL;
-        gram_kernel<T><<<p.gram_blocks, kT, gsm, s>>>(src[pass], p.I, L, rows, sc.partial, sc.flag, pass);
-        note_launch();
-        cholesky_kernel<<<1, kT, csm, s>>>(sc.partial, p.gram_blocks, L, p.I, R, sc.flag, status, pass);
+        gram_chol_kernel<T><<<p.gram_blocks, kT, gsm, s>>>(src[pass], p.I, L, rows, sc.partial, sc.ticket, R,
+                                                           sc.flag, status, pass);
         note_launch();
         apply_rinv_kernel<T><<<(unsigned)ablocks, kT, asm_, s>>>(src[pass], p.I, L, R, dst[pass], sc.flag, pass);
         note_launch();
@@ -390,10 +425,10 @@ cudaError_t launch_cholqr(const T* X, T* Q, T* Qtmp, const OrthPlan& p, double* 
 template <typename T>
 cudaError_t launch_extract(const T* Q, const OrthPlan& p, const double* factors, int nfactors, int R, T* U,
                            void* scratch, int* status, cudaStream_t s) {
-    OrthScratch sc = carve(p, scratch, sizeof(T));
+    OrthScratch sc = carve(p, scratch);
     const int L = p.L;
     const int Lp = L + (L & 1);
-    const size_t ssm = sizeof(T) * (2 * (size_t)Lp * L + Lp) + sizeof(int) * Lp + 64;
+    const size_t ssm = sizeof(T) * (2 * (size_t)Lp * L + (size_t)L * L + Lp) + sizeof(int) * Lp + 64;
     if (ssm > 220 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(small_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
     T* um = reinterpret_cast<T*>(sc.um);

@@ -13,13 +13,22 @@ namespace tk {
 namespace {
 
 constexpr int kT = kThreads;
-constexpr int JB = 32, OB = 64, KC = 32;
+constexpr int JB = 64, KC = 32;
 
-template <typename T>
+// OB = output block (a multiple of 8 covering K_out, or 64 with several blocks);
+// thread (jj = tid % JB, og = tid / JB) owns fiber jj and outputs og*OPT .. +OPT.
+template <typename T, int OB>
 __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeView v, const T* __restrict__ Mp,
                                                  int64_t K_out, int64_t ld_i, int64_t ld_k, T* __restrict__ out) {
-    __shared__ __align__(16) T Ts[JB][KC + 1];
-    __shared__ __align__(16) T Ms[KC][OB];
+    constexpr int OPT = OB / (kT / JB);
+    // the tile buffers (Ts, Ms) are dead once the products are done, so the output
+    // staging block Os reuses their storage
+    constexpr size_t kTileBytes = sizeof(T) * (JB * (KC + 1) + KC * OB);
+    constexpr size_t kOutBytes = sizeof(T) * JB * (OB + 1);
+    __shared__ __align__(16) unsigned char smem[kTileBytes > kOutBytes ? kTileBytes : kOutBytes];
+    auto Ts = reinterpret_cast<T(*)[KC + 1]>(smem);
+    auto Ms = reinterpret_cast<T(*)[OB]>(smem + sizeof(T) * JB * (KC + 1));
+    auto Os = reinterpret_cast<T(*)[OB + 1]>(smem);
     __shared__ int64_t bases[JB];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t J = v.fibers();
@@ -31,44 +40,56 @@ __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeVi
         bases[tid] = j < J ? v.base(j) : -1;
     }
     __syncthreads();
-    const int jj = lane, og = warp;           // this thread: fiber jj, outputs og*8 .. og*8+7
-    T acc[OB / 8];
+    const int jj = tid % JB, og = tid / JB;
+    T acc[OPT];
 #pragma unroll
-    for (int u = 0; u < OB / 8; ++u) acc[u] = T(0);
+    for (int u = 0; u < OPT; ++u) acc[u] = T(0);
     for (int i0 = 0; i0 < I; i0 += KC) {
-        // fiber tile chunk
         if (v.lf == 1) {
+            // contiguous fibers: a warp reads KC consecutive elements of one fiber
             for (int r = warp; r < JB; r += kT / 32) {
                 const int64_t b = bases[r];
                 const int i = i0 + lane;
                 Ts[r][lane] = (b >= 0 && i < I) ? __ldg(A + b + i) : T(0);
             }
         } else {
-            for (int c = warp; c < KC; c += kT / 32) {
-                const int64_t b = bases[lane];
+            // strided fibers: a warp reads one element of 32 neighbouring fibers
+            for (int e = tid; e < JB * KC; e += kT) {
+                const int r = e % JB, c = e / JB;
+                const int64_t b = bases[r];
                 const int i = i0 + c;
-                Ts[lane][c] = (b >= 0 && i < I) ? __ldg(A + b + (int64_t)i * v.lf) : T(0);
+                Ts[r][c] = (b >= 0 && i < I) ? __ldg(A + b + (int64_t)i * v.lf) : T(0);
             }
         }
-        for (int e = tid; e < KC * OB; e += kT) {
-            const int kk = e / OB, oo = e % OB;
-            const int i = i0 + kk;
-            const int64_t o = o0 + oo;
-            Ms[kk][oo] = (i < I && o < K_out) ? Mp[(int64_t)i * ld_i + o * ld_k] : T(0);
+        // M chunk: walk the unit-stride index across threads
+        if (ld_i == 1) {
+            for (int e = tid; e < KC * OB; e += kT) {
+                const int kk = e % KC, oo = e / KC;
+                const int i = i0 + kk;
+                const int64_t o = o0 + oo;
+                Ms[kk][oo] = (i < I && o < K_out) ? __ldg(Mp + i + o * ld_k) : T(0);
+            }
+        } else {
+            for (int e = tid; e < KC * OB; e += kT) {
+                const int kk = e / OB, oo = e % OB;
+                const int i = i0 + kk;
+                const int64_t o = o0 + oo;
+                Ms[kk][oo] = (i < I && o < K_out) ? __ldg(Mp + (int64_t)i * ld_i + o * ld_k) : T(0);
+            }
         }
         __syncthreads();
         const int kc = min(KC, I - i0);
         for (int kk = 0; kk < kc; ++kk) {
             const T t = Ts[jj][kk];
+            const T* mr = &Ms[kk][og * OPT];
 #pragma unroll
-            for (int u = 0; u < OB / 8; ++u) acc[u] = fma(t, Ms[kk][og * (OB / 8) + u], acc[u]);
+            for (int u = 0; u < OPT; ++u) acc[u] = fma(t, mr[u], acc[u]);
         }
         __syncthreads();
     }
-    // stage the JB x OB block through shared memory for coalesced stores
-    __shared__ T Os[JB][OB + 1];
+    // (the loop ends with a barrier, so every thread is done reading Ts and Ms)
 #pragma unroll
-    for (int u = 0; u < OB / 8; ++u) Os[jj][og * (OB / 8) + u] = acc[u];
+    for (int u = 0; u < OPT; ++u) Os[jj][og * OPT + u] = acc[u];
     __syncthreads();
     if (v.lf == 1) {
         // out[o + j K_out]: consecutive threads -> consecutive o
@@ -142,10 +163,16 @@ cudaError_t launch_ttm(const T* A, const ModeView& v, const T* Mp, int64_t K_out
                        cudaStream_t s) {
     const int64_t J = v.fibers();
     if (J == 0 || K_out == 0) return cudaSuccess;
+    const int OB = K_out <= 8 ? 8 : K_out <= 16 ? 16 : K_out <= 32 ? 32 : 64;
     dim3 grid((unsigned)((J + JB - 1) / JB), (unsigned)((K_out + OB - 1) / OB));
     const double ein = (double)v.i * (double)J, eout = (double)K_out * (double)J;
     ProfScope prof(kKTtm, (ein + eout) * sizeof(T), 2.0 * ein * (double)K_out, s);
-    ttm_kernel<T><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out);
+    switch (OB) {
+        case 8: ttm_kernel<T, 8><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        case 16: ttm_kernel<T, 16><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        case 32: ttm_kernel<T, 32><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        default: ttm_kernel<T, 64><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+    }
     note_launch();
     return cudaGetLastError();
 }

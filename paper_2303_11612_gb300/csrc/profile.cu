@@ -65,7 +65,9 @@ void profile_drain() {
     std::lock_guard<std::mutex> g(g_mu);
     for (const Rec& r : g_pending) {
         float ms = 0.f;
-        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        const bool ok = cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess;
+        if (!ok) cudaGetLastError();     // leave no stale error for the next launch check
+        if (ok) {
             Accum& a = g_acc[r.cls];
             a.launches += 1;
             a.ms += ms;
