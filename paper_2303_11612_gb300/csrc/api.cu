@@ -87,7 +87,7 @@ tucker_status read_opts(const tucker_opts* o, Opts& out) {
     if (out.form != TUCKER_FORM_PAPER && out.form != TUCKER_FORM_RANGE) return TUCKER_ERR_INVALID_ARG;
     if (out.prec < TUCKER_SK_FP32 || out.prec > TUCKER_SK_BF16) return TUCKER_ERR_INVALID_ARG;
     if (!(out.alpha >= 0.0) || out.alpha > 1.0) return TUCKER_ERR_INVALID_ARG;
-    if (out.prec != TUCKER_SK_FP32) return TUCKER_ERR_UNSUPPORTED;
+    if (out.prec == TUCKER_SK_TF32) return TUCKER_ERR_UNSUPPORTED;
     return TUCKER_OK;
 }
 
@@ -109,6 +109,7 @@ struct ModePlan {
     int L;
     int R;
     int64_t T;         // AMM samples (0 = none)
+    bool tc;           // power steps on the tensor cores (bf16 operands)
     PowerPlan pp;
     OrthPlan op;
 };
@@ -154,6 +155,10 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         if (d[n] > kMaxI || mp.L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
         if (elem == 8 && d[n] > 512) return TUCKER_ERR_UNSUPPORTED;
         mp.pp = power_plan(mp.mv, mp.L, elem, sms);
+        // bf16 tensor-core power steps where the tile fits; the FP32 kernel elsewhere
+        mp.tc = o.prec == TUCKER_SK_BF16 && elem == 4 && power_tc_supported(mp.mv, mp.L);
+        if (mp.tc)
+            p.max_partials = std::max(p.max_partials, power_tc_partials_bytes(mp.mv, mp.L, sms));
         mp.op = orth_plan(d[n], mp.L, sms);
         p.maxI = std::max(p.maxI, d[n]);
         p.maxL = std::max<int64_t>(p.maxL, mp.L);
@@ -196,7 +201,7 @@ void carve(const Plan& p, Arena& a, Work& w) {
     w.X1 = a.take(IL);
     w.Q = a.take(IL);
     w.Qt = a.take(IL);
-    w.factors = (double*)a.take(sizeof(double) * 3 * slots * (size_t)p.maxL * p.maxL);
+    w.factors = (double*)a.take(sizeof(double) * slots * (size_t)p.maxL * p.maxL);
     w.partials = a.take(p.max_partials);
     w.orth = a.take(p.max_orth);
     if (p.maxT > 0) {
@@ -221,6 +226,16 @@ void carve(const Plan& p, Arena& a, Work& w) {
         if (_e != cudaSuccess) return _e;           \
     } while (0)
 
+// X_out = M M^T X_in on the tensor cores (bf16) or with FP32/FP64 FMA.
+template <typename T>
+cudaError_t power_step(const T* M, const ModePlan& mp, const T* X_in, T* X_out, const Work& w, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (mp.tc)
+            return launch_power_tc(M, mp.mv, X_in, mp.L, X_out, w.partials, w.status, num_sms(), s);
+    }
+    return launch_power<T>(M, mp.mv, X_in, mp.L, X_out, w.partials, mp.pp, false, 0, 0, s);
+}
+
 // One mode's factor U (I_n x R_n) from the tensor B (view mp.v).
 template <typename T>
 cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, uint64_t seed, int form, T* U,
@@ -239,36 +254,31 @@ cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, 
         M = (const T*)w.Cp;
     }
     const int L = mp.L;
-    T* X0 = (T*)w.X0; T* X1 = (T*)w.X1; T* Q = (T*)w.Q; T* Qt = (T*)w.Qt;
-    int nf = 0;
+    T* X0 = (T*)w.X0; T* X1 = (T*)w.X1; T* Q = (T*)w.Q;
+    const size_t LL = (size_t)L * L;
     if (form == TUCKER_FORM_PAPER) {
-        // C = (M M^T)^q Omega in factored form: after each step X = Q_k R_k and the
-        // next step multiplies Q_k, so C = Q_q (R_q ... R_1) without overflow or
-        // loss of the weaker directions to rounding.
+        // C = (M M^T)^q Omega in factored form: after each step X_k = Q_k F_k and
+        // the next step multiplies Q_k, so C = X_q F_{q-1} ... F_1 with no overflow
+        // and no loss of the weaker directions to FP32 rounding.
         TK_TRY(launch_gaussian<T>(X0, mp.v.i, L, seed, stream_id(0, n), s));
         for (int k = 0; k < q; ++k) {
             const T* xin = X0;
             if (k > 0) {
-                TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, k - 1, w.orth, w.status, s));
+                TK_TRY(launch_cholqr<T>(X1, Q, mp.op, w.factors + (size_t)(k - 1) * LL, w.orth, w.status, s));
                 xin = Q;
             }
-            TK_TRY(launch_power<T>(M, mp.mv, xin, L, X1, w.partials, mp.pp, false, 0, 0, s));
+            TK_TRY(power_step<T>(M, mp, xin, X1, w, s));
         }
-        nf = 3 * q;
         ProfScope prof(kKExtract, 0.0, 0.0, s);
-        TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, q - 1, w.orth, w.status, s));
-        return launch_extract<T>(Q, mp.op, w.factors, nf, mp.R, U, w.orth, w.status, s);
-    } else {
-        TK_TRY(launch_power<T>(M, mp.mv, nullptr, L, X1, w.partials, mp.pp, true, seed, stream_id(0, n), s));
-        for (int k = 0; k < q; ++k) {
-            TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, 0, w.orth, w.status, s));
-            TK_TRY(launch_power<T>(M, mp.mv, Q, L, X1, w.partials, mp.pp, false, 0, 0, s));
-        }
-        nf = 3;
-        ProfScope prof(kKExtract, 0.0, 0.0, s);
-        TK_TRY(launch_cholqr<T>(X1, Q, Qt, mp.op, w.factors, 0, w.orth, w.status, s));
-        return launch_extract<T>(Q, mp.op, w.factors, nf, mp.R, U, w.orth, w.status, s);
+        return launch_extract<T>(X1, mp.op, w.factors, q - 1, mp.R, U, w.orth, w.status, s);
     }
+    TK_TRY(launch_power<T>(M, mp.mv, nullptr, L, X1, w.partials, mp.pp, true, seed, stream_id(0, n), s));
+    for (int k = 0; k < q; ++k) {
+        TK_TRY(launch_cholqr<T>(X1, Q, mp.op, w.factors, w.orth, w.status, s));
+        TK_TRY(power_step<T>(M, mp, Q, X1, w, s));
+    }
+    ProfScope prof(kKExtract, 0.0, 0.0, s);
+    return launch_extract<T>(X1, mp.op, nullptr, 0, mp.R, U, w.orth, w.status, s);
 }
 
 template <typename T>
@@ -341,6 +351,7 @@ tucker_status driver(bool st, const void* A, tucker_dtype dt, const int64_t* dim
     if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
     if (prob != TUCKER_PROB_NEARLY_OPTIMAL && prob != TUCKER_PROB_UNIFORM) return TUCKER_ERR_INVALID_ARG;
     if (!A || !U || !G) return TUCKER_ERR_INVALID_ARG;
+    if (o.prec == TUCKER_SK_BF16 && dt != TUCKER_F32) return TUCKER_ERR_UNSUPPORTED;
     for (int n = 0; n < N && n < kMaxOrder; ++n)
         if (!U[n]) return TUCKER_ERR_INVALID_ARG;
     const int elem = dt == TUCKER_F64 ? 8 : 4;
@@ -455,6 +466,7 @@ tucker_status sync_status(cudaStream_t s, const int* dev_status) {
     if (dev_status) e = cudaMemcpyAsync(&st, dev_status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return from_cuda(e);
+    if (st & kStatTimeout) return TUCKER_ERR_TIMEOUT;
     if (st & kStatNumerical) return TUCKER_ERR_NUMERICAL;
     return TUCKER_OK;
 }
@@ -551,6 +563,18 @@ tucker_status tucker_power_step(const void* A, tucker_dtype dt, const int64_t* d
     const int elem = dt == TUCKER_F64 ? 8 : 4;
     if (v.i > kMaxI || L > 4096 || (elem == 8 && v.i > 512)) return TUCKER_ERR_UNSUPPORTED;
     const PowerPlan pp = power_plan(v, (int)L, elem, num_sms());
+    if (o.prec == TUCKER_SK_BF16) {
+        if (elem != 4 || !power_tc_supported(v, (int)L)) return TUCKER_ERR_UNSUPPORTED;
+        Scratch sc;
+        if ((rs = sc.get(power_tc_partials_bytes(v, (int)L, num_sms()) + 256, o.stream)) != TUCKER_OK) return rs;
+        int* status = reinterpret_cast<int*>(sc.p);
+        cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
+        if (e == cudaSuccess)
+            e = launch_power_tc((const float*)A, v, (const float*)X_in, (int)L, (float*)X_out,
+                                reinterpret_cast<char*>(sc.p) + 256, status, num_sms(), o.stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        return sync_status(o.stream, status);
+    }
     Scratch sc;
     if ((rs = sc.get(power_partials_bytes(pp, v, (int)L, elem), o.stream)) != TUCKER_OK) return rs;
     cudaError_t e = elem == 4 ? launch_power<float>((const float*)A, v, (const float*)X_in, (int)L, (float*)X_out,
@@ -652,8 +676,7 @@ tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, i
     const int elem = dt == TUCKER_F64 ? 8 : 4;
     const OrthPlan op = orth_plan(I, (int)L, num_sms());
     Arena a;
-    const size_t IL = (size_t)I * L * elem;
-    a.take(sizeof(int) * 64); a.take(IL); a.take(IL); a.take(sizeof(double) * 3 * L * L);
+    a.take(sizeof(int) * 64);
     a.take(orth_scratch_bytes(op, elem));
     Scratch sc;
     if ((rs = sc.get(a.used, o.stream)) != TUCKER_OK) return rs;
@@ -661,22 +684,13 @@ tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, i
     b.base = (char*)sc.p;
     b.cap = a.used;
     int* status = (int*)b.take(sizeof(int) * 64);
-    void* Q = b.take(IL);
-    void* Qt = b.take(IL);
-    double* F = (double*)b.take(sizeof(double) * 3 * L * L);
     void* orth = b.take(orth_scratch_bytes(op, elem));
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
-    if (e == cudaSuccess) {
-        if (elem == 4) {
-            e = launch_cholqr<float>((const float*)C, (float*)Q, (float*)Qt, op, F, 0, orth, status, o.stream);
-            if (e == cudaSuccess)
-                e = launch_extract<float>((const float*)Q, op, F, 3, (int)R, (float*)U, orth, status, o.stream);
-        } else {
-            e = launch_cholqr<double>((const double*)C, (double*)Q, (double*)Qt, op, F, 0, orth, status, o.stream);
-            if (e == cudaSuccess)
-                e = launch_extract<double>((const double*)Q, op, F, 3, (int)R, (double*)U, orth, status, o.stream);
-        }
-    }
+    if (e == cudaSuccess)
+        e = elem == 4 ? launch_extract<float>((const float*)C, op, nullptr, 0, (int)R, (float*)U, orth, status,
+                                              o.stream)
+                      : launch_extract<double>((const double*)C, op, nullptr, 0, (int)R, (double*)U, orth, status,
+                                               o.stream);
     if (e != cudaSuccess) return from_cuda(e);
     return sync_status(o.stream, status);
 }

@@ -43,6 +43,16 @@ cudaError_t launch_power(const T* A, const ModeView& v, const T* X_in, int L, T*
                          void* partials, const PowerPlan& plan, bool range, uint64_t seed,
                          uint32_t stream_id, cudaStream_t s);
 
+// out[e] = sum_{p < parts} partial[p * count + e], summed in part order.
+template <typename T>
+cudaError_t launch_reduce_partials(const T* partial, int parts, int64_t count, T* out, cudaStream_t s);
+
+// ---- tensor-core power step, bf16 operands / fp32 accumulation (kernels_tc.cu)
+bool power_tc_supported(const ModeView& v, int L);
+size_t power_tc_partials_bytes(const ModeView& v, int L, int num_sms);
+cudaError_t launch_power_tc(const float* A, const ModeView& v, const float* X_in, int L, float* X_out, void* partials,
+                            int* status, int num_sms, cudaStream_t s);
+
 // ---- sampling (kernels_amm.cu)
 template <typename T>
 cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStream_t s);
@@ -64,17 +74,17 @@ struct OrthPlan {
 };
 OrthPlan orth_plan(int64_t I, int L, int num_sms);
 size_t orth_scratch_bytes(const OrthPlan& p, int elem_size);
-// One CholeskyQR pass group (2 passes + a 3rd when pass 1 needed a shift):
-// X (I x L) -> Q, appending three L x L upper-triangular FP64 factors at
-// factors + 3 * slot * L * L. X and Q may not alias.
+// One CholeskyQR pass: X (I x L) = Q F, F upper triangular (FP64, row-major,
+// written to `factor`), Q = X F^-1. X and Q may not alias.
 template <typename T>
-cudaError_t launch_cholqr(const T* X, T* Q, T* Qtmp, const OrthPlan& p, double* factors, int slot,
-                          void* scratch, int* status, cudaStream_t s);
-// U = Q * (R leading left singular vectors of M), M = product of the first
-// nfactors factors (last applied first), sign-fixed.
+cudaError_t launch_cholqr(const T* X, T* Q, const OrthPlan& p, double* factor, void* scratch, int* status,
+                          cudaStream_t s);
+// U (I x R) = the R leading left singular vectors of C = X P, P = prev[nprev-1]
+// ... prev[0] (upper triangular FP64 factors of earlier steps; nprev may be 0),
+// sign-fixed.
 template <typename T>
-cudaError_t launch_extract(const T* Q, const OrthPlan& p, const double* factors, int nfactors,
-                           int R, T* U, void* scratch, int* status, cudaStream_t s);
+cudaError_t launch_extract(const T* X, const OrthPlan& p, const double* prev, int nprev, int R, T* U, void* scratch,
+                           int* status, cudaStream_t s);
 
 // ---- mode products and norms (kernels_ttm.cu)
 // out = A x_n M: M(k_out, i) read as Mp[i * ld_i + k_out * ld_k].

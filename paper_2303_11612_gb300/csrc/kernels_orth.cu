@@ -1,12 +1,22 @@
 // Orthonormalisation of the sketch and extraction of the leading left singular
 // vectors (remark after Algorithm 5: Q_n = U(:, 1:mu_n) from the SVD of C_n).
 //
-// C (I x L) = Q M with Q orthonormal and M = R_k ... R_1 upper triangular is
-// formed by CholeskyQR2 (Gram in FP64 from exact FP32 products, Cholesky in
-// FP64); when the first Gram matrix is numerically singular its Cholesky is
-// shifted (shifted CholeskyQR, Fukaya et al. 2020) and a third pass runs. The
-// leading left singular vectors of C are then Q times those of the small M,
-// found with a one-sided (Hestenes) Jacobi SVD.
+// The sketch is held as C = X F, where X (I x L) is the last power-step output
+// and F = F_k ... F_1 collects the triangular factors of the earlier steps
+// (each earlier step orthonormalised its output X_j = Q_j F_j and multiplied Q_j,
+// which leaves C unchanged). Extraction:
+//   1. G = X^T X from exact FP32 products summed in paired FP32 (about 2^-44),
+//      reduced across CTAs in a fixed order; FP64 Cholesky G = R^T R (shifted
+//      once on a numerically singular pivot, Fukaya et al. 2020). Then
+//      C = Q M with Q = X R^-1 orthonormal and M = R F (L x L).
+//   2. One-sided (Hestenes) Jacobi on the columns of M with paired-precision
+//      dot products: M V = U_M S. The leading left singular vectors of C are
+//      Q U_M = C V S^-1, so U = X W with W = F V S^-1 (L x R) -- no triangular
+//      solve and no explicit Q.
+//   3. U = X W in paired precision; each column's largest-magnitude entry made
+//      positive. Columns whose singular value is at rounding level are
+//      completed by Gram-Schmidt against the others.
+// Intermediate power steps need only Q_j and F_j: one CholeskyQR pass.
 #include <float.h>
 
 #include <algorithm>
@@ -17,20 +27,9 @@ namespace tk {
 namespace {
 
 constexpr int kT = kThreads;
-constexpr int kSvdThreads = 1024;
+constexpr int kXT = 1024;                // threads of the extraction kernel
+constexpr int kDegenerate = 8;           // flag bit: some factor column needs completion
 
-// pass 0: first pass; pass 1: second pass; pass 2: runs only if a shift was needed.
-__device__ __forceinline__ bool pass_skipped(const int* flag, int pass) {
-    return pass == 2 && !(*flag & kStatShifted);
-}
-
-// ---------------------------------------------------------------- Gram + Cholesky
-// Each CTA accumulates the Gram matrix of its block of rows (packed upper
-// triangle); the last CTA to finish (an atomic ticket, no waiting) sums the
-// partials in block order, which makes the result independent of scheduling,
-// and factors G = R^T R in FP64 (R upper, row-major R[a * L + b]). A pivot
-// below 1e-15 of its diagonal entry restarts the factorisation once with
-// G + s I, s = 11 (I L + L (L + 1)) 2^-53 tr(G), and flags the shift.
 template <typename T> struct GramAcc;
 template <> struct GramAcc<float> {
     Pair s{0.f, 0.f};
@@ -45,65 +44,65 @@ template <> struct GramAcc<double> {
 
 __device__ __forceinline__ int packed_index(int a, int b, int L) { return a * L - (a * (a - 1)) / 2 + (b - a); }
 
+// Gram partial of this CTA's rows (packed upper triangle) -> partial[blockIdx.x].
 template <typename T>
-__global__ void __launch_bounds__(kT) gram_chol_kernel(const T* __restrict__ X, int64_t I, int L, int rows_per_block,
-                                                       double* __restrict__ partial, unsigned* ticket,
-                                                       double* __restrict__ R, int* flag, int* status, int pass) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int tid = threadIdx.x;
-    if (pass_skipped(flag, pass)) {
-        if (blockIdx.x == 0)
-            for (int p = tid; p < L * L; p += kT) R[p] = (p / L == p % L) ? 1.0 : 0.0;
-        return;
+__device__ void gram_partial(const T* __restrict__ X, int64_t I, int L, int rows, double* __restrict__ partial,
+                             unsigned char* smem) {
+    T* xs = reinterpret_cast<T*>(smem);   // [rows][L]
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int nr = (int)max((int64_t)0, min((int64_t)rows, I - r0));
+    for (int e = threadIdx.x; e < nr * L; e += blockDim.x) {
+        const int r = e % nr, c = e / nr;
+        xs[r * L + c] = X[(int64_t)c * I + r0 + r];
     }
-    const int np = L * (L + 1) / 2;
-    {
-        T* xs = reinterpret_cast<T*>(smem_raw);   // [rows][L]
-        const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-        const int nr = (int)max((int64_t)0, min((int64_t)rows_per_block, I - r0));
-        for (int e = tid; e < nr * L; e += kT) {
-            const int r = e % nr, c = e / nr;
-            xs[r * L + c] = X[(int64_t)c * I + r0 + r];
-        }
-        __syncthreads();
-        double* out = partial + (int64_t)blockIdx.x * np;
-        for (int a = 0; a < L; ++a) {
-            for (int b = a + tid; b < L; b += kT) {
-                GramAcc<T> acc;
-                for (int r = 0; r < nr; ++r) acc.add(xs[r * L + a], xs[r * L + b]);
-                out[packed_index(a, b, L)] = acc.value();
-            }
+    __syncthreads();
+    double* out = partial + (int64_t)blockIdx.x * (L * (L + 1) / 2);
+    for (int a = 0; a < L; ++a) {
+        for (int b = a + threadIdx.x; b < L; b += blockDim.x) {
+            GramAcc<T> acc;
+            for (int r = 0; r < nr; ++r) acc.add(xs[r * L + a], xs[r * L + b]);
+            out[packed_index(a, b, L)] = acc.value();
         }
     }
+}
+
+// True in exactly one CTA: the last to finish its partial (an atomic ticket, no waiting).
+__device__ bool last_cta(unsigned* ticket) {
     __shared__ int last;
     __threadfence();
     __syncthreads();
-    if (tid == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (!last) return;
-    __threadfence();
+    if (last) __threadfence();
+    return last;
+}
 
-    double* G = reinterpret_cast<double*>(smem_raw);   // [L][L]
-    double* W = G + L * L;                               // [L][L]
+// Sum the partials in block order into G (L x L, shared) and factor G = R^T R
+// (R upper, row-major, left in W with zeros below the diagonal). A pivot below
+// 1e-15 of its diagonal entry restarts once with G + s I,
+// s = 11 (I L + L (L + 1)) 2^-53 tr(G). Returns false if that also fails.
+__device__ bool reduce_cholesky(const double* __restrict__ partial, int nparts, int L, int64_t I, double* G,
+                                double* W, unsigned* ticket, int* status) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int np = L * (L + 1) / 2;
     __shared__ int bad;
     __shared__ double inv_piv;
-    const int nparts = gridDim.x;
-    for (int p = tid; p < np; p += kT) {
+    __shared__ double tr;
+    for (int p = tid; p < np; p += nt) {
         double acc = 0.0;
 #pragma unroll 8
         for (int b = 0; b < nparts; ++b) acc += __ldcg(partial + (int64_t)b * np + p);
-        // unpack (a, b) from the packed index
         int a = 0, rem = p;
         while (rem >= L - a) { rem -= L - a; ++a; }
         const int bb = a + rem;
         G[a * L + bb] = acc;
         G[bb * L + a] = acc;
     }
-    if (tid == 0) *ticket = 0;                           // ready for the next pass
+    if (tid == 0) *ticket = 0;                           // ready for the next use
     __syncthreads();
     double shift = 0.0;
     for (int attempt = 0; attempt < 2; ++attempt) {
-        for (int p = tid; p < L * L; p += kT) W[p] = G[p] + ((p / L == p % L) ? shift : 0.0);
+        for (int p = tid; p < L * L; p += nt) W[p] = G[p] + ((p / L == p % L) ? shift : 0.0);
         if (tid == 0) bad = 0;
         __syncthreads();
         for (int k = 0; k < L; ++k) {
@@ -120,10 +119,10 @@ __global__ void __launch_bounds__(kT) gram_chol_kernel(const T* __restrict__ X, 
             }
             __syncthreads();
             if (bad) break;
-            for (int j = k + 1 + tid; j < L; j += kT) W[k * L + j] *= inv_piv;
+            for (int j = k + 1 + tid; j < L; j += nt) W[k * L + j] *= inv_piv;
             __syncthreads();
             const int m = L - k - 1;
-            for (int p = tid; p < m * m; p += kT) {
+            for (int p = tid; p < m * m; p += nt) {
                 const int i = k + 1 + p / m, j = k + 1 + p % m;
                 if (j >= i) W[i * L + j] -= W[k * L + i] * W[k * L + j];
             }
@@ -131,45 +130,54 @@ __global__ void __launch_bounds__(kT) gram_chol_kernel(const T* __restrict__ X, 
         }
         if (!bad) break;
         if (attempt == 0) {
-            __shared__ double tr;
             if (tid == 0) {
                 double t = 0.0;
                 for (int k = 0; k < L; ++k) t += G[k * L + k];
                 tr = t > 0.0 ? t : 1.0;
-                *flag |= kStatShifted;
             }
             __syncthreads();
             shift = 11.0 * ((double)I * L + (double)L * (L + 1)) * 1.1102230246251565e-16 * tr;
             __syncthreads();
         }
     }
-    if (bad && tid == 0) set_status(status, kStatNumerical);
-    for (int p = tid; p < L * L; p += kT) {
+    const int failed = bad;
+    __syncthreads();
+    for (int p = tid; p < L * L; p += nt) {
         const int a = p / L, b = p % L;
-        R[p] = (b >= a && !bad) ? W[p] : (a == b ? 1.0 : 0.0);
+        if (failed) W[p] = (a == b) ? 1.0 : 0.0;
+        else if (b < a) W[p] = 0.0;
     }
+    if (failed && tid == 0) set_status(status, kStatNumerical);
+    __syncthreads();
+    return !failed;
 }
 
-// ---------------------------------------------------------------- Q = X R^{-1}
-// One warp per row: forward substitution q_l = (x_l - sum_{m<l} q_m R[m][l]) / R[l][l] in FP64.
+// ---------------------------------------------------------------- one CholeskyQR pass
+template <typename T>
+__global__ void __launch_bounds__(kT) gram_chol_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
+                                                       double* __restrict__ partial, unsigned* ticket,
+                                                       double* __restrict__ R, int* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    gram_partial<T>(X, I, L, rows, partial, smem_raw);
+    if (!last_cta(ticket)) return;
+    double* G = reinterpret_cast<double*>(smem_raw);
+    double* W = G + L * L;
+    reduce_cholesky(partial, gridDim.x, L, I, G, W, ticket, status);
+    for (int p = threadIdx.x; p < L * L; p += blockDim.x) R[p] = W[p];
+}
+
+// Q = X R^-1, one warp per row: forward substitution in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kT) apply_rinv_kernel(const T* __restrict__ X, int64_t I, int L,
-                                                        const double* __restrict__ R, T* __restrict__ Q,
-                                                        const int* flag, int pass) {
+                                                        const double* __restrict__ R, T* __restrict__ Q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const bool copy = pass_skipped(flag, pass);
     double* Rs = reinterpret_cast<double*>(smem_raw);    // [L][L]
     double* qs = Rs + L * L;                               // [warps][L]
-    if (!copy)
-        for (int p = threadIdx.x; p < L * L; p += kT) Rs[p] = R[p];
+    for (int p = threadIdx.x; p < L * L; p += kT) Rs[p] = R[p];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* q = qs + warp * L;
     for (int64_t i = (int64_t)blockIdx.x * (kT / 32) + warp; i < I; i += (int64_t)gridDim.x * (kT / 32)) {
-        if (copy) {
-            for (int l = lane; l < L; l += 32) Q[(int64_t)l * I + i] = X[(int64_t)l * I + i];
-            continue;
-        }
         for (int l = 0; l < L; ++l) {
             double s = 0.0;
             for (int m = lane; m < l; m += 32) s = fma(q[m], Rs[m * L + l], s);
@@ -182,75 +190,120 @@ __global__ void __launch_bounds__(kT) apply_rinv_kernel(const T* __restrict__ X,
     }
 }
 
-// ---------------------------------------------------------------- small SVD
-// M = F_{n-1} ... F_0 (each F upper triangular FP64, row-major), formed in T
-// after scaling every factor by a power of two; then one-sided Jacobi on the
-// columns of M (M V = U S); the R columns of largest norm, normalised, are the
-// leading left singular vectors. Output UM (L x R, column-major).
-template <typename T>
-__global__ void __launch_bounds__(kSvdThreads) small_svd_kernel(const double* __restrict__ factors, int nf, int L,
-                                                                int R, T* __restrict__ UM, int* status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Lp = L + (L & 1);                           // even number of columns (phantom zero column)
-    T* M = reinterpret_cast<T*>(smem_raw);                 // column-major [Lp][L]: column c at M + c * L
-    T* Tm = M + Lp * L;                                    // product scratch [L][L]
-    T* Fs = Tm + Lp * L;                                   // current factor, row-major [L][L]
-    T* nrm = Fs + L * L;                                   // [Lp]
-    int* perm = reinterpret_cast<int*>(nrm + Lp);          // [Lp]
-    __shared__ unsigned long long fmax_bits;
-    __shared__ int rotated;
-    __shared__ T fro2;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSvdThreads / 32;
+// ---------------------------------------------------------------- fused extraction
+template <typename T> struct DotAcc;
+template <> struct DotAcc<float> {
+    Pair s{0.f, 0.f};
+    __device__ void add(float a, float b) { pair_add_prod(s, a, b); }
+    __device__ void reduce() { s = warp_sum_pair(s); }
+    __device__ double value() const { return pair_value(s); }
+};
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ void reduce() { s = warp_sum(s); }
+    __device__ double value() const { return s; }
+};
 
-    for (int f = 0; f < nf; ++f) {
-        const double* F = factors + (int64_t)f * L * L;
-        if (tid == 0) fmax_bits = 0ull;
+constexpr int kMaxPerThread = 12;        // L * L / kXT for L <= 110
+
+// Grid of Gram CTAs (kXT threads each). The last CTA: Cholesky of X^T X,
+// M = R P with P = prev[nprev-1] ... prev[0], Jacobi on M, and
+// W = P V S^-1 for the R leading columns (FP64, L x R, column-major).
+// Columns with a singular value at rounding level get W = 0 and raise the
+// kDegenerate flag.
+template <typename T>
+__global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
+                                                      double* __restrict__ partial, unsigned* ticket,
+                                                      const double* __restrict__ prev, int nprev, int R,
+                                                      double* __restrict__ Wout, int* flag, int* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    gram_partial<T>(X, I, L, rows, partial, smem_raw);
+    if (!last_cta(ticket)) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kXT / 32;
+    const int Lp = L + (L & 1);
+    double* G = reinterpret_cast<double*>(smem_raw);     // [L][L]; after the Cholesky: P
+    double* Rf = G + L * L;                                // [L][L] Cholesky factor (upper, row-major)
+    T* Mc = reinterpret_cast<T*>(Rf + L * L);              // column-major [Lp][L]
+    T* V = Mc + Lp * L;                                    // column-major [Lp][L]
+    T* sig = V + Lp * L;                                   // [Lp]
+    int* perm = reinterpret_cast<int*>(sig + Lp);          // [Lp]
+    __shared__ unsigned long long mx_bits;
+    __shared__ int nrot;
+    __shared__ double fro2;
+
+    reduce_cholesky(partial, gridDim.x, L, I, G, Rf, ticket, status);
+
+    // P = prev[nprev-1] ... prev[0] (upper triangular, FP64) into G
+    if (nprev > 0) {
+        for (int p = tid; p < L * L; p += kXT) G[p] = prev[p];
         __syncthreads();
-        double mx = 0.0;
-        for (int p = tid; p < L * L; p += kSvdThreads) mx = fmax(mx, fabs(F[p]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) atomicMax(&fmax_bits, (unsigned long long)__double_as_longlong(mx));
-        __syncthreads();
-        const double fm = __longlong_as_double((long long)fmax_bits);
-        const double sc = fm > 0.0 ? exp2(-floor(log2(fm))) : 1.0;   // a power of two: exact
-        for (int p = tid; p < L * L; p += kSvdThreads) Fs[p] = (T)(F[p] * sc);
-        __syncthreads();
-        if (f == 0) {
-            for (int p = tid; p < Lp * L; p += kSvdThreads) {
-                const int c = p / L, a = p % L;
-                M[p] = (c < L && c >= a) ? Fs[a * L + c] : T(0);
-            }
-        } else {
-            for (int p = tid; p < L * L; p += kSvdThreads) {
-                const int c = p / L, a = p % L;
-                T acc = T(0);
-                for (int b = a; b < L; ++b) acc = fma(Fs[a * L + b], M[c * L + b], acc);
-                Tm[p] = acc;
+        for (int f = 1; f < nprev; ++f) {
+            const double* F = prev + (int64_t)f * L * L;
+            double acc[kMaxPerThread];
+            int cnt = 0;
+            for (int p = tid; p < L * L; p += kXT, ++cnt) {
+                const int a = p / L, c = p % L;
+                double s = 0.0;
+                for (int b = a; b <= c; ++b) s = fma(F[a * L + b], G[b * L + c], s);
+                acc[cnt] = s;
             }
             __syncthreads();
-            for (int p = tid; p < L * L; p += kSvdThreads) M[p] = Tm[p];
+            cnt = 0;
+            for (int p = tid; p < L * L; p += kXT, ++cnt) G[p] = acc[cnt];
+            __syncthreads();
         }
-        __syncthreads();
     }
-    // squared Frobenius norm: a pair whose coupling is below eps^2 of it is at the
-    // rounding level of the whole matrix and is left alone (rounding would otherwise
-    // keep near-zero columns rotating without end)
-    if (tid == 0) fro2 = T(0);
+    // M = R P (or R), stored in T after scaling by a power of two
+    if (tid == 0) mx_bits = 0ull;
     __syncthreads();
     {
-        T s2 = T(0);
-        for (int p = tid; p < L * L; p += kSvdThreads) s2 = fma(M[p], M[p], s2);
+        double mxl = 0.0;
+        for (int p = tid; p < L * L; p += kXT) {
+            const int a = p % L, c = p / L;               // row a, column c
+            double s = 0.0;
+            if (nprev > 0) {
+                for (int b = a; b <= c; ++b) s = fma(Rf[a * L + b], G[b * L + c], s);
+            } else if (c >= a) {
+                s = Rf[a * L + c];
+            }
+            mxl = fmax(mxl, fabs(s));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mxl = fmax(mxl, __shfl_xor_sync(0xffffffffu, mxl, o));
+        if (lane == 0) atomicMax(&mx_bits, (unsigned long long)__double_as_longlong(mxl));
+    }
+    __syncthreads();
+    const double mxv = __longlong_as_double((long long)mx_bits);
+    const double sc = mxv > 0.0 ? exp2(-floor(log2(mxv))) : 1.0;      // exact power of two
+    for (int p = tid; p < Lp * L; p += kXT) {
+        const int c = p / L, a = p % L;
+        double s = 0.0;
+        if (c < L) {
+            if (nprev > 0) {
+                for (int b = a; b <= c; ++b) s = fma(Rf[a * L + b], G[b * L + c], s);
+            } else if (c >= a) {
+                s = Rf[a * L + c];
+            }
+        }
+        Mc[p] = (T)(s * sc);
+        V[p] = (T)((c == a) ? 1.0 : 0.0);
+    }
+    if (tid == 0) fro2 = 0.0;
+    __syncthreads();
+    {
+        double s2 = 0.0;
+        for (int p = tid; p < L * L; p += kXT) s2 = fma((double)Mc[p], (double)Mc[p], s2);
         s2 = warp_sum(s2);
         if (lane == 0) atomicAdd(&fro2, s2);
     }
     __syncthreads();
-    const T eps = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
-    const T tol = eps * T(2);
-    const T tiny = eps * eps * fro2;
+    const double eps = sizeof(T) == 4 ? (double)FLT_EPSILON : DBL_EPSILON;
+    const double tol = 2.0 * eps;
+    const double tiny = eps * eps * fro2;
     const int m = Lp - 1;
     for (int sweep = 0; sweep < 30; ++sweep) {
-        if (tid == 0) rotated = 0;
+        if (tid == 0) nrot = 0;
         __syncthreads();
         for (int rnd = 0; rnd < m; ++rnd) {
             for (int pi = warp; pi < Lp / 2; pi += nwarps) {
@@ -258,75 +311,116 @@ __global__ void __launch_bounds__(kSvdThreads) small_svd_kernel(const double* __
                 if (pi == 0) { p = rnd; q = m; }
                 else { p = (rnd + pi) % m; q = (rnd - pi + m) % m; }
                 if (p >= L || q >= L) continue;
-                T* cp = M + p * L;
-                T* cq = M + q * L;
-                T al = 0, be = 0, ga = 0;
+                T* cp = Mc + p * L;
+                T* cq = Mc + q * L;
+                DotAcc<T> al, be, ga;
                 for (int r = lane; r < L; r += 32) {
                     const T x = cp[r], y = cq[r];
-                    al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+                    al.add(x, x);
+                    be.add(y, y);
+                    ga.add(x, y);
                 }
-                al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-                if (fabs(ga) > tiny && fabs(ga) > tol * sqrt(al * be)) {
-                    const T zeta = (be - al) / (T(2) * ga);
-                    const T t = (zeta >= 0 ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-                    const T c = T(1) / sqrt(T(1) + t * t), s = c * t;
+                al.reduce();
+                be.reduce();
+                ga.reduce();
+                const double a = al.value(), b = be.value(), g = ga.value();
+                if (fabs(g) > tiny && fabs(g) > tol * sqrt(a * b)) {
+                    const double zeta = (b - a) / (2.0 * g);
+                    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cs = 1.0 / sqrt(1.0 + t * t);
+                    const T c = (T)cs, s = (T)(cs * t);
+                    T* vp = V + p * L;
+                    T* vq = V + q * L;
                     for (int r = lane; r < L; r += 32) {
                         const T x = cp[r], y = cq[r];
                         cp[r] = c * x - s * y;
                         cq[r] = s * x + c * y;
+                        const T u = vp[r], w = vq[r];
+                        vp[r] = c * u - s * w;
+                        vq[r] = s * u + c * w;
                     }
-                    if (lane == 0) rotated = 1;
+                    if (lane == 0) atomicAdd(&nrot, 1);
                 }
             }
             __syncthreads();
         }
-        if (!rotated) break;
+        if (nrot == 0) break;
         __syncthreads();
     }
-    // column norms, order by decreasing norm (ties: lower index first)
+    // singular values (column norms), decreasing order, lower index first on ties
     for (int c = warp; c < L; c += nwarps) {
-        T s = 0;
-        for (int r = lane; r < L; r += 32) s = fma(M[c * L + r], M[c * L + r], s);
-        s = warp_sum(s);
-        if (lane == 0) nrm[c] = sqrt(s);
+        DotAcc<T> s;
+        for (int r = lane; r < L; r += 32) s.add(Mc[c * L + r], Mc[c * L + r]);
+        s.reduce();
+        if (lane == 0) sig[c] = (T)sqrt(s.value());
     }
     __syncthreads();
-    for (int c = tid; c < L; c += kSvdThreads) {
+    for (int c = tid; c < L; c += kXT) {
         int rank = 0;
-        for (int d = 0; d < L; ++d) rank += (nrm[d] > nrm[c]) || (nrm[d] == nrm[c] && d < c);
+        for (int d = 0; d < L; ++d) rank += (sig[d] > sig[c]) || (sig[d] == sig[c] && d < c);
         perm[rank] = c;
     }
     __syncthreads();
-    for (int p = tid; p < L * R; p += kSvdThreads) {
+    const double smax = (double)sig[perm[0]];
+    const double floor_rel = 64.0 * eps;
+    // W(:, r) = P V(:, c) / (sigma_c / sc), c = perm[r]
+    for (int p = tid; p < L * R; p += kXT) {
         const int r = p / L, a = p % L;
         const int c = perm[r];
-        const T n = nrm[c];
-        UM[p] = n > T(0) ? M[c * L + a] / n : T(0);
+        const double sg = (double)sig[c];
+        double w = 0.0;
+        if (sg > floor_rel * smax && sg > 0.0) {
+            double s = 0.0;
+            if (nprev > 0) {
+                for (int b = a; b < L; ++b) s = fma(G[a * L + b], (double)V[c * L + b], s);
+            } else {
+                s = (double)V[c * L + a];
+            }
+            w = s * sc / sg;
+        }
+        Wout[(int64_t)r * L + a] = w;
     }
-    if (tid == 0 && R > 0 && !(nrm[perm[R - 1]] > T(0))) set_status(status, kStatNumerical);
+    if (tid == 0) {
+        int deg = 0;
+        for (int r = 0; r < R; ++r) {
+            const double sg = (double)sig[perm[r]];
+            deg |= !(sg > floor_rel * smax && sg > 0.0);
+        }
+        *flag = deg ? kDegenerate : 0;
+    }
 }
 
-// ---------------------------------------------------------------- U = Q UM, sign rule
+// U(:, r) = X W(:, r) in paired precision, then the sign rule. One CTA per column.
 template <typename T>
-__global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ Q, int64_t I, int L,
-                                                    const T* __restrict__ UM, T* __restrict__ U) {
+__global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ X, int64_t I, int L,
+                                                    const double* __restrict__ W, T* __restrict__ U) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* um = reinterpret_cast<T*>(smem_raw);   // [L]
-    T* col = um + L;                          // [I]
+    T* whi = reinterpret_cast<T*>(smem_raw);  // [L]
+    T* wlo = whi + L;                         // [L]
+    T* col = wlo + L;                         // [I]
     __shared__ T best_v[kT / 32];
     __shared__ int64_t best_i[kT / 32];
     __shared__ T sgn;
     const int r = blockIdx.x;
-    for (int c = threadIdx.x; c < L; c += kT) um[c] = UM[(int64_t)r * L + c];
+    for (int c = threadIdx.x; c < L; c += kT) {
+        const double w = W[(int64_t)r * L + c];
+        whi[c] = (T)w;
+        wlo[c] = (T)(w - (double)whi[c]);
+    }
     __syncthreads();
     T bv = T(-1);
     int64_t bi = 0;
     for (int64_t i = threadIdx.x; i < I; i += kT) {
-        T s = 0;
-        for (int c = 0; c < L; ++c) s = fma(Q[(int64_t)c * I + i], um[c], s);
-        col[i] = s;
-        const T a = fabs(s);
-        if (a > bv) { bv = a; bi = i; }     // first (lowest) index wins ties within a thread
+        DotAcc<T> s;
+        for (int c = 0; c < L; ++c) {
+            const T x = X[(int64_t)c * I + i];
+            s.add(x, whi[c]);
+            s.add(x, wlo[c]);
+        }
+        const T v = (T)s.value();
+        col[i] = v;
+        const T a = fabs(v);
+        if (a > bv) { bv = a; bi = i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -347,14 +441,96 @@ __global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ Q, int
     for (int64_t i = threadIdx.x; i < I; i += kT) U[(int64_t)r * I + i] = sgn * col[i];
 }
 
+// Columns whose singular value is at rounding level: the first unit vector e_k
+// (k increasing) that keeps a long residual after two Gram-Schmidt passes
+// against every valid column, normalised and sign-fixed. The squared residuals
+// of e_0 .. e_{I-1} average (I - d) / I for d valid columns, so accepting one
+// above half that average always succeeds. Runs only when flagged.
+template <typename T>
+__global__ void __launch_bounds__(kT) complete_kernel(int64_t I, int L, int R, const double* __restrict__ W,
+                                                      T* __restrict__ U, const int* flag) {
+    if (!(*flag & kDegenerate)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* v = reinterpret_cast<double*>(smem_raw);   // [I]
+    int* valid = reinterpret_cast<int*>(v + I);        // [R]
+    __shared__ double red[kT / 32];
+    __shared__ double bcast;
+    __shared__ double bv;
+    __shared__ int64_t bi;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int r = tid; r < R; r += kT) {
+        int nz = 0;
+        for (int c = 0; c < L; ++c) nz |= W[(int64_t)r * L + c] != 0.0;
+        valid[r] = nz;
+    }
+    __syncthreads();
+    int nvalid = 0;
+    for (int r = 0; r < R; ++r) nvalid += valid[r];
+    int64_t k = 0;
+    for (int r = 0; r < R; ++r) {
+        if (valid[r]) continue;
+        const double accept = 0.5 * (double)(I - nvalid) / (double)I;
+        for (; k < I; ++k) {
+            for (int64_t i = tid; i < I; i += kT) v[i] = (i == k) ? 1.0 : 0.0;
+            __syncthreads();
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int j = 0; j < R; ++j) {
+                    if (!valid[j]) continue;
+                    double s = 0.0;
+                    for (int64_t i = tid; i < I; i += kT) s = fma((double)U[(int64_t)j * I + i], v[i], s);
+                    s = warp_sum(s);
+                    if (lane == 0) red[warp] = s;
+                    __syncthreads();
+                    if (tid == 0) {
+                        double t = 0.0;
+                        for (int w = 0; w < kT / 32; ++w) t += red[w];
+                        bcast = t;
+                    }
+                    __syncthreads();
+                    const double d = bcast;
+                    for (int64_t i = tid; i < I; i += kT) v[i] -= d * (double)U[(int64_t)j * I + i];
+                    __syncthreads();
+                }
+            }
+            double s = 0.0;
+            for (int64_t i = tid; i < I; i += kT) s = fma(v[i], v[i], s);
+            s = warp_sum(s);
+            if (lane == 0) red[warp] = s;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < kT / 32; ++w) t += red[w];
+                bcast = sqrt(t);
+                bv = -1.0;
+                bi = 0;
+                for (int64_t i = 0; i < I; ++i)
+                    if (fabs(v[i]) > bv) { bv = fabs(v[i]); bi = i; }
+            }
+            __syncthreads();
+            const double nrm = bcast;
+            if (nrm * nrm > accept) {
+                const double f = (v[bi] < 0 ? -1.0 : 1.0) / nrm;
+                for (int64_t i = tid; i < I; i += kT) U[(int64_t)r * I + i] = (T)(v[i] * f);
+                __syncthreads();
+                if (tid == 0) valid[r] = 1;
+                __syncthreads();
+                ++nvalid;
+                ++k;
+                break;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 }  // namespace
 
 OrthPlan orth_plan(int64_t I, int L, int num_sms) {
     OrthPlan p{};
     p.I = I;
     p.L = L;
-    // enough CTAs to spread the FP64-grade Gram work, few enough that the last
-    // CTA's reduction of the packed partials stays small (<= 512 KB)
+    // enough CTAs to spread the paired-precision Gram work, few enough that the
+    // last CTA's reduction of the packed partials stays small (<= 512 KB)
     const int64_t np = (int64_t)L * (L + 1) / 2;
     int64_t cap = (512 * 1024) / (np * 8);
     if (cap < 1) cap = 1;
@@ -369,16 +545,17 @@ OrthPlan orth_plan(int64_t I, int L, int num_sms) {
 static int gram_rows(const OrthPlan& p) { return (int)((p.I + p.gram_blocks - 1) / p.gram_blocks); }
 
 size_t orth_scratch_bytes(const OrthPlan& p, int elem_size) {
+    (void)elem_size;
     const size_t np = (size_t)p.L * (p.L + 1) / 2;
     const size_t LL = (size_t)p.L * p.L;
-    return sizeof(double) * np * (size_t)p.gram_blocks + 256 + (size_t)elem_size * LL + 512;
+    return ((sizeof(double) * np * (size_t)p.gram_blocks + 255) & ~size_t(255)) + 256 + sizeof(double) * LL + 512;
 }
 
 struct OrthScratch {
     double* partial;
     int* flag;
     unsigned* ticket;
-    void* um;
+    double* W;
 };
 static OrthScratch carve(const OrthPlan& p, void* scratch) {
     OrthScratch s;
@@ -389,13 +566,13 @@ static OrthScratch carve(const OrthPlan& p, void* scratch) {
     s.flag = reinterpret_cast<int*>(b);
     s.ticket = reinterpret_cast<unsigned*>(b + 64);
     b += 256;
-    s.um = b;
+    s.W = reinterpret_cast<double*>(b);
     return s;
 }
 
 template <typename T>
-cudaError_t launch_cholqr(const T* X, T* Q, T* Qtmp, const OrthPlan& p, double* factors, int slot, void* scratch,
-                          int* status, cudaStream_t s) {
+cudaError_t launch_cholqr(const T* X, T* Q, const OrthPlan& p, double* factor, void* scratch, int* status,
+                          cudaStream_t s) {
     OrthScratch sc = carve(p, scratch);
     const int L = p.L;
     const size_t LL = (size_t)L * L;
@@ -405,50 +582,56 @@ cudaError_t launch_cholqr(const T* X, T* Q, T* Qtmp, const OrthPlan& p, double* 
     if (asm_ > 220 * 1024 || gsm > 220 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(gram_chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
     cudaFuncSetAttribute(apply_rinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_);
-    cudaMemsetAsync(sc.flag, 0, 128, s);                 // shift flag and ticket
+    cudaMemsetAsync(sc.flag, 0, 128, s);                 // flag and ticket
     int64_t ablocks = (p.I + kT / 32 - 1) / (kT / 32);
     if (ablocks > 1024) ablocks = 1024;
-    // pass 0: X -> Q ; pass 1: Q -> Qtmp ; pass 2 (only after a shift): Qtmp -> Q, else copy
-    const T* src[3] = {X, Q, Qtmp};
-    T* dst[3] = {Q, Qtmp, Q};
-    for (int pass = 0; pass < 3; ++pass) {
-        double* R = factors + (size_t)(3 * slot + pass) * LL;
-        gram_chol_kernel<T><<<p.gram_blocks, kT, gsm, s>>>(src[pass], p.I, L, rows, sc.partial, sc.ticket, R,
-                                                           sc.flag, status, pass);
-        note_launch();
-        apply_rinv_kernel<T><<<(unsigned)ablocks, kT, asm_, s>>>(src[pass], p.I, L, R, dst[pass], sc.flag, pass);
-        note_launch();
-    }
+    gram_chol_kernel<T><<<p.gram_blocks, kT, gsm, s>>>(X, p.I, L, rows, sc.partial, sc.ticket, factor, status);
+    note_launch();
+    apply_rinv_kernel<T><<<(unsigned)ablocks, kT, asm_, s>>>(X, p.I, L, factor, Q);
+    note_launch();
     return cudaGetLastError();
+}
+
+static size_t extract_smem_bytes(int L, int elem, int rows) {
+    const int Lp = L + (L & 1);
+    const size_t last = sizeof(double) * 2 * (size_t)L * L + (size_t)elem * (2 * (size_t)Lp * L + Lp) +
+                        sizeof(int) * Lp + 64;
+    return std::max(last, (size_t)elem * (size_t)rows * L);
 }
 
 template <typename T>
-cudaError_t launch_extract(const T* Q, const OrthPlan& p, const double* factors, int nfactors, int R, T* U,
-                           void* scratch, int* status, cudaStream_t s) {
+cudaError_t launch_extract(const T* X, const OrthPlan& p, const double* prev, int nprev, int R, T* U, void* scratch,
+                           int* status, cudaStream_t s) {
     OrthScratch sc = carve(p, scratch);
     const int L = p.L;
-    const int Lp = L + (L & 1);
-    const size_t ssm = sizeof(T) * (2 * (size_t)Lp * L + (size_t)L * L + Lp) + sizeof(int) * Lp + 64;
-    if (ssm > 220 * 1024) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(small_svd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
-    T* um = reinterpret_cast<T*>(sc.um);
-    small_svd_kernel<T><<<1, kSvdThreads, ssm, s>>>(factors, nfactors, L, R, um, status);
+    const int rows = gram_rows(p);
+    if ((int64_t)L * L > (int64_t)kXT * kMaxPerThread) return cudaErrorInvalidValue;
+    const size_t xsm = extract_smem_bytes(L, sizeof(T), rows);
+    if (xsm > 220 * 1024) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(extract_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
+    cudaMemsetAsync(sc.flag, 0, 128, s);
+    extract_kernel<T><<<p.gram_blocks, kXT, xsm, s>>>(X, p.I, L, rows, sc.partial, sc.ticket, prev, nprev, R, sc.W,
+                                                      sc.flag, status);
     note_launch();
-    const size_t fsm = sizeof(T) * ((size_t)L + (size_t)p.I) + 64;
+    const size_t fsm = sizeof(T) * (2 * (size_t)L + (size_t)p.I) + 64;
     if (fsm > 220 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(form_u_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-    form_u_kernel<T><<<R, kT, fsm, s>>>(Q, p.I, L, um, U);
+    form_u_kernel<T><<<R, kT, fsm, s>>>(X, p.I, L, sc.W, U);
+    note_launch();
+    const size_t csm = sizeof(double) * (size_t)p.I + sizeof(int) * (size_t)R + 64;
+    if (csm > 220 * 1024) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(complete_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    complete_kernel<T><<<1, kT, csm, s>>>(p.I, L, R, sc.W, U, sc.flag);
     note_launch();
     return cudaGetLastError();
 }
 
-template cudaError_t launch_cholqr<float>(const float*, float*, float*, const OrthPlan&, double*, int, void*, int*,
-                                          cudaStream_t);
-template cudaError_t launch_cholqr<double>(const double*, double*, double*, const OrthPlan&, double*, int, void*,
-                                           int*, cudaStream_t);
+template cudaError_t launch_cholqr<float>(const float*, float*, const OrthPlan&, double*, void*, int*, cudaStream_t);
+template cudaError_t launch_cholqr<double>(const double*, double*, const OrthPlan&, double*, void*, int*,
+                                           cudaStream_t);
 template cudaError_t launch_extract<float>(const float*, const OrthPlan&, const double*, int, int, float*, void*,
                                            int*, cudaStream_t);
-template cudaError_t launch_extract<double>(const double*, const OrthPlan&, const double*, int, int, double*,
-                                            void*, int*, cudaStream_t);
+template cudaError_t launch_extract<double>(const double*, const OrthPlan&, const double*, int, int, double*, void*,
+                                            int*, cudaStream_t);
 
 }  // namespace tk

@@ -275,13 +275,20 @@ cudaError_t launch_power(const T* A, const ModeView& v, const T* X_in, int L, T*
     else
         return cudaErrorInvalidValue;
     if (e != cudaSuccess) return e;
-    const int64_t count = v.i * (int64_t)L;
+    return launch_reduce_partials<T>(part, plan.parts, v.i * (int64_t)L, X_out, s);
+}
+
+template <typename T>
+cudaError_t launch_reduce_partials(const T* partial, int parts, int64_t count, T* out, cudaStream_t s) {
     int64_t blocks = (count + kT - 1) / kT;
     if (blocks > 2048) blocks = 2048;
-    reduce_partials_kernel<T><<<(unsigned)blocks, kT, 0, s>>>(part, plan.parts, count, X_out);
+    if (blocks < 1) blocks = 1;
+    reduce_partials_kernel<T><<<(unsigned)blocks, kT, 0, s>>>(partial, parts, count, out);
     note_launch();
     return cudaGetLastError();
 }
+template cudaError_t launch_reduce_partials<float>(const float*, int, int64_t, float*, cudaStream_t);
+template cudaError_t launch_reduce_partials<double>(const double*, int, int64_t, double*, cudaStream_t);
 
 template cudaError_t launch_gaussian<float>(float*, int64_t, int64_t, uint64_t, uint32_t, cudaStream_t);
 template cudaError_t launch_gaussian<double>(double*, int64_t, int64_t, uint64_t, uint32_t, cudaStream_t);
