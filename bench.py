@@ -181,6 +181,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="both", choices=["both", "bf16", "fp32"],
+                    help="sketch arithmetic to time (both: bf16 is the headline when its RE matches)")
     ap.add_argument("--single", default=None, choices=[v["name"] for v in VARIANTS],
                     help="run one decomposition of one variant after one warm-up and exit (profiling case)")
     args = ap.parse_args()
@@ -204,37 +206,16 @@ def main():
     if args.single:
         v = next(x for x in VARIANTS if x["name"] == args.single)
         A = torch.from_numpy(host[v["tensor"]]).cuda()
+        prec = "fp32" if args.prec == "fp32" else "bf16"
         for _ in range(2):
-            tk.rsthosvd(A, DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED)
+            tk.rsthosvd(A, DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED, prec=prec)
         torch.cuda.synchronize()
-        print(json.dumps({"single": v["name"], "ok": True}))
+        print(json.dumps({"single": v["name"], "prec": prec, "ok": True}))
         return 0
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
-    # one stream, workspace and output set per variant: the four decompositions of a
-    # step run concurrently (fork from the main stream, join back into it)
     main_s = torch.cuda.Stream()
     side = [torch.cuda.Stream() for _ in VARIANTS]
-    wss = [torch.empty(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"]), dtype=torch.uint8,
-                       device="cuda") for v in VARIANTS]
-    outs = [([tk.factor_tensor(I, R, torch.float32, "cuda") for I, R in zip(DIMS, RANKS)],
-             torch.empty(int(np.prod(RANKS)), dtype=torch.float32, device="cuda")) for _ in VARIANTS]
-    houts = [([torch.empty((R, I), dtype=torch.float32).pin_memory().t() for I, R in zip(DIMS, RANKS)],
-              torch.empty(int(np.prod(RANKS)), dtype=torch.float32).pin_memory()) for _ in VARIANTS]
-
-    def enqueue_step():
-        for st in side:
-            st.wait_stream(main_s)
-        for v, st, ws, out in zip(VARIANTS, side, wss, outs):
-            tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
-                        workspace=ws, stream=st, out=out, flags=tk.FLAG_ASYNC)
-        for st in side:
-            main_s.wait_stream(st)
-
-    def step_e2e():
-        for v, out in zip(VARIANTS, houts):
-            tk.rsthosvd(pinned[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
-                        stream=main_s, out=out)
 
     def barrier():
         torch.cuda.synchronize()
@@ -249,92 +230,114 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # correctness of what is timed: every variant succeeds and reports its RE
-    res = {}
-    for v in VARIANTS:
-        _, _, re = tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
-                               want_rel_error=True)
-        res[v["name"]] = re
-
     clocks = ClockSampler(local)
     clocks.start()
-    with torch.cuda.stream(main_s):
-        for _ in range(args.warmup):
-            enqueue_step()
-    main_s.synchronize()
-    if tk.last_device_status() != 0:
-        raise RuntimeError("device status not OK after warm-up")
-    # kernels in one step, counted on an eager step with profiling off
-    n0 = tk.launch_count()
-    with torch.cuda.stream(main_s):
-        enqueue_step()
-    main_s.synchronize()
-    per_step_launches = tk.launch_count() - n0
-    # capture one step with profiling on, so each kernel of interest carries its own
-    # event pair inside the graph (re-recorded by every replay); fall back to eager
-    # launches if capture is refused
-    graph = None
-    tk.profile_enable(True)
-    try:
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=main_s):
-            enqueue_step()
-        graph = g
+
+    def measure(prec):
+        """Graph-timed throughput of the batch with one sketch arithmetic."""
+        # one stream, workspace and output set per variant: the four decompositions of
+        # a step run concurrently (fork from the main stream, join back into it)
+        wss = [torch.empty(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"], prec=prec),
+                           dtype=torch.uint8, device="cuda") for v in VARIANTS]
+        outs = [([tk.factor_tensor(I, R, torch.float32, "cuda") for I, R in zip(DIMS, RANKS)],
+                 torch.empty(int(np.prod(RANKS)), dtype=torch.float32, device="cuda")) for _ in VARIANTS]
+
+        def enqueue_step():
+            for st in side:
+                st.wait_stream(main_s)
+            for v, st, ws, out in zip(VARIANTS, side, wss, outs):
+                tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
+                            workspace=ws, stream=st, out=out, flags=tk.FLAG_ASYNC, prec=prec)
+            for st in side:
+                main_s.wait_stream(st)
+
+        # accuracy of what is timed: explicit relative error of every variant
+        res = {}
+        for v in VARIANTS:
+            U, G = tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
+                               prec=prec)
+            res[v["name"]] = tk.relative_error(dev[v["tensor"]], DIMS, RANKS, U, G)
         with torch.cuda.stream(main_s):
-            graph.replay()
-        main_s.synchronize()
-    except Exception as exc:  # noqa: BLE001
-        print(f"graph capture unavailable ({exc}); timing eager launches", file=sys.stderr)
-        graph = None
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    if graph is None:
-        tk.profile_enable(True)
-    n0 = tk.launch_count()
-    with torch.cuda.stream(main_s):
-        ev0.record(main_s)
-        for _ in range(args.steps):
-            if graph is not None:
-                graph.replay()
-            else:
+            for _ in range(args.warmup):
                 enqueue_step()
-        ev1.record(main_s)
-    main_s.synchronize()
-    n1 = tk.launch_count()
-    barrier()
-    st = tk.last_device_status()
-    if st != 0:
-        raise RuntimeError(f"device status {st} in the timed region")
-    ms = ev0.elapsed_time(ev1)
-    if graph is not None:
-        # event pairs inside a graph carry no timings, so the per-kernel durations
-        # come from eager steps run right after the graph-timed region
+        main_s.synchronize()
+        if tk.last_device_status() != 0:
+            raise RuntimeError("device status not OK after warm-up")
+        n0 = tk.launch_count()
+        with torch.cuda.stream(main_s):
+            enqueue_step()
+        main_s.synchronize()
+        per_step = tk.launch_count() - n0
+        graph = None
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=main_s):
+                enqueue_step()
+            graph = g
+            with torch.cuda.stream(main_s):
+                graph.replay()
+            main_s.synchronize()
+        except Exception as exc:  # noqa: BLE001
+            print(f"graph capture unavailable ({exc}); timing eager launches", file=sys.stderr)
+            graph = None
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        n0 = tk.launch_count()
+        with torch.cuda.stream(main_s):
+            ev0.record(main_s)
+            for _ in range(args.steps):
+                if graph is not None:
+                    graph.replay()
+                else:
+                    enqueue_step()
+            ev1.record(main_s)
+        main_s.synchronize()
+        n1 = tk.launch_count()
+        barrier()
+        if tk.last_device_status() != 0:
+            raise RuntimeError("device status not OK in the timed region")
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        # per-kernel durations: event pairs inside a graph carry no timings, so they
+        # come from eager steps run right after the timed region (same streams)
         tk.profile_enable(True)
         with torch.cuda.stream(main_s):
             for _ in range(max(3, args.steps // 10)):
                 enqueue_step()
         main_s.synchronize()
-    clk = clocks.stop()
-    classes = ("power", "ttm", "gather", "norms", "extract", "sample")
-    prof = {k: tk.profile_read(k) for k in classes}
-    tk.profile_enable(False)
-    ms = max_over_ranks(ms)
-    decomps = len(VARIANTS) * args.steps * world
-    value = decomps / (ms / 1e3)
-    gpu_launches = (n1 - n0) if graph is None else per_step_launches * args.steps
-    if graph is not None:
-        prof_note = ("eager profiled steps right after the graph-timed region, same streams and "
-                     "concurrency (CUDA-graph event nodes carry no timings)")
-    else:
-        prof_note = "eager: event pairs of every launch in the timed region"
+        prof = {k: tk.profile_read(k) for k in ("power", "ttm", "gather", "norms", "extract", "sample")}
+        tk.profile_enable(False)
+        del graph
+        return {"prec": prec, "ms": ms, "value": len(VARIANTS) * args.steps * world / (ms / 1e3),
+                "gpu_launches": (n1 - n0) if n1 - n0 > 0 else per_step * args.steps,
+                "graph": True, "rel_error": res, "prof": prof}
 
-    # end to end through the C ABI with pinned host buffers
+    forms = {}
+    for prec in (["bf16", "fp32"] if args.prec == "both" else [args.prec]):
+        forms[prec] = measure(prec)
+    clk = clocks.stop()
+    if "bf16" in forms and "fp32" in forms:
+        equal = all(abs(forms["bf16"]["rel_error"][k] - forms["fp32"]["rel_error"][k]) <= 1e-3
+                    for k in forms["fp32"]["rel_error"])
+        head = forms["bf16"] if equal else forms["fp32"]
+    else:
+        equal = None
+        head = next(iter(forms.values()))
+
+    # end to end through the C ABI with pinned host buffers, headline arithmetic
+    houts = [([torch.empty((R, I), dtype=torch.float32).pin_memory().t() for I, R in zip(DIMS, RANKS)],
+              torch.empty(int(np.prod(RANKS)), dtype=torch.float32).pin_memory()) for _ in VARIANTS]
+
+    def step_e2e():
+        for v, out in zip(VARIANTS, houts):
+            tk.rsthosvd(pinned[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
+                        stream=main_s, out=out, prec=head["prec"])
+
     e2e = None
     try:
         step_e2e()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e2e_steps = max(3, args.steps // 4)
+        e2e_steps = max(3, args.steps // 10)
         t0 = time.perf_counter()
         e0.record(main_s)
         for _ in range(e2e_steps):
@@ -351,52 +354,64 @@ def main():
         e2e = {"value": None, "unit": "decomps/s", "error": str(exc)}
 
     peaks, peak_kind = load_peaks()
-    pw_n, pw_ms, pw_bytes, pw_flops = prof["power"]
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12    # FFMA lanes x 2 flops x max SM clock
-    achieved_tflops = pw_flops / (pw_ms / 1e3) / 1e12 if pw_ms > 0 else 0.0
+    pw_n, pw_ms, pw_bytes, pw_flops = head["prof"]["power"]
     achieved_gbs = pw_bytes / (pw_ms / 1e3) / 1e9 if pw_ms > 0 else 0.0
+    achieved_tflops = pw_flops / (pw_ms / 1e3) / 1e12 if pw_ms > 0 else 0.0
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    if head["prec"] == "bf16":
+        # bandwidth-bound: 4 L flops per 4-byte element is ~30 flops/byte, far below the
+        # bf16 tensor ridge (~285 flops/byte), so the bound is HBM
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved_gbs / peaks["hbm_gbs"],
+                    "kernel": "power_tc_kernel (fused A(A^T X) pass, tcgen05 bf16, fp32 accumulate)",
+                    "tensor_tflops": achieved_tflops}
+        src_file, tkey = "kernels_tc.cu", "power_tc_kernel_400cubed"
+    else:
+        fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / fp32_peak,
+                    "kernel": "power_kernel (fused A(A^T X) pass, FP32 FFMA)",
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz", "hbm_gbs": achieved_gbs}
+        src_file, tkey = "kernels_sketch.cu", "power_kernel_400cubed"
     traffic = None
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            tr = json.load(f).get("power_kernel_400cubed")
-        src = open(os.path.join(ROOT, "paper_2303_11612_gb300", "csrc", "kernels_sketch.cu"), "rb").read()
         import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f).get(tkey)
+        src = open(os.path.join(ROOT, "paper_2303_11612_gb300", "csrc", src_file), "rb").read()
         if tr and tr.get("source_sha256") == hashlib.sha256(src).hexdigest():
             # DRAM bytes per algorithmic byte from one ncu capture, times this run's bytes per launch
             traffic = tr["dram_bytes_per_algorithmic_byte"] * pw_bytes / max(pw_n, 1)
     except Exception:
         traffic = None
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tflops / fp32_peak_tflops, "traffic": traffic,
-                "kernel": "power_kernel (fused A(A^T X) pass, FP32 FFMA)",
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
-                "launches": pw_n, "ms_per_launch": pw_ms / max(pw_n, 1),
-                "algorithmic_bytes_per_launch": pw_bytes / max(pw_n, 1),
-                "hbm_gbs": achieved_gbs, "hbm_frac": achieved_gbs / peaks["hbm_gbs"],
-                "hbm_peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind, "timing": prof_note}
-    others = {}
+    roofline.update({"traffic": traffic, "launches": pw_n, "ms_per_launch": pw_ms / max(pw_n, 1),
+                     "algorithmic_bytes_per_launch": pw_bytes / max(pw_n, 1), "peak_kind": peak_kind,
+                     "timing": "eager profiled steps right after the graph-timed region, same streams and "
+                               "concurrency (CUDA-graph event nodes carry no timings)"})
+    kernels = {}
     for k in ("ttm", "gather", "norms", "extract", "sample"):
-        n, kms, b, f = prof[k]
+        n, kms, b, f = head["prof"][k]
         if n:
-            others[k] = {"launches": n, "ms_per_launch": kms / n}
+            kernels[k] = {"launches": n, "ms_per_launch": kms / n}
             if b:
-                others[k].update({"gbs": b / (kms / 1e3) / 1e9, "hbm_frac": b / (kms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                                  "tflops": f / (kms / 1e3) / 1e12})
-    line = {"metric": "decomps/s", "value": value, "unit": "decomps/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "baseline_metric": BASELINE_METRIC,
+                kernels[k].update({"gbs": b / (kms / 1e3) / 1e9, "hbm_frac": b / (kms / 1e3) / 1e9 / peaks["hbm_gbs"]})
+    line = {"metric": "decomps/s", "value": head["value"], "unit": "decomps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "baseline_metric": BASELINE_METRIC,
             "config": {"workload": WORKLOAD, "tensor_bytes": 256_000_000,
                        "l2": "inputs larger than L2 (256 MB per tensor), no flush",
                        "parallelism": "replicas (each rank decomposes its own batch)" if world > 1 else "single GPU",
-                       "sketch": "paper form, FP32 SIMT",
-                       "execution": ("CUDA graph of one step, 4 decompositions on 4 streams" if graph is not None
-                                     else "eager launches, 4 decompositions on 4 streams")},
-            "e2e": e2e,
-            "gpu_launches": gpu_launches,
-            "roofline": roofline, "kernels": others,
+                       "sketch": f"paper form, {head['prec']} power steps "
+                                 + ("(tcgen05 tensor cores, fp32 accumulate)" if head["prec"] == "bf16"
+                                    else "(FP32 FFMA)"),
+                       "execution": "CUDA graph of one step, 4 decompositions on 4 streams"},
+            "e2e": e2e, "gpu_launches": head["gpu_launches"], "roofline": roofline, "kernels": kernels,
             "sketch_hbm_gbs": achieved_gbs,
-            "rel_error": res, "clocks": clk}
+            "forms": {p: {"value": f["value"], "ms_per_step": f["ms"] / args.steps, "rel_error": f["rel_error"]}
+                      for p, f in forms.items()},
+            "bf16_matches_fp32_rel_err_within_1e-3": equal,
+            "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host)
     if rank == 0:

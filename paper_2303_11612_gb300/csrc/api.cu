@@ -270,7 +270,7 @@ cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, 
             TK_TRY(power_step<T>(M, mp, xin, X1, w, s));
         }
         ProfScope prof(kKExtract, 0.0, 0.0, s);
-        return launch_extract<T>(X1, mp.op, w.factors, q - 1, mp.R, U, w.orth, w.status, s);
+        return launch_extract<T>(X1, Q, mp.op, w.factors, q - 1, mp.R, U, w.orth, w.status, s);
     }
     TK_TRY(launch_power<T>(M, mp.mv, nullptr, L, X1, w.partials, mp.pp, true, seed, stream_id(0, n), s));
     for (int k = 0; k < q; ++k) {
@@ -278,7 +278,7 @@ cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, 
         TK_TRY(power_step<T>(M, mp, Q, X1, w, s));
     }
     ProfScope prof(kKExtract, 0.0, 0.0, s);
-    return launch_extract<T>(X1, mp.op, nullptr, 0, mp.R, U, w.orth, w.status, s);
+    return launch_extract<T>(X1, Q, mp.op, w.factors, 0, mp.R, U, w.orth, w.status, s);
 }
 
 template <typename T>
@@ -678,6 +678,8 @@ tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, i
     Arena a;
     a.take(sizeof(int) * 64);
     a.take(orth_scratch_bytes(op, elem));
+    a.take((size_t)I * L * elem);
+    a.take(sizeof(double) * L * L);
     Scratch sc;
     if ((rs = sc.get(a.used, o.stream)) != TUCKER_OK) return rs;
     Arena b;
@@ -685,12 +687,14 @@ tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, i
     b.cap = a.used;
     int* status = (int*)b.take(sizeof(int) * 64);
     void* orth = b.take(orth_scratch_bytes(op, elem));
+    void* Q1 = b.take((size_t)I * L * elem);
+    double* F = (double*)b.take(sizeof(double) * L * L);
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
     if (e == cudaSuccess)
-        e = elem == 4 ? launch_extract<float>((const float*)C, op, nullptr, 0, (int)R, (float*)U, orth, status,
+        e = elem == 4 ? launch_extract<float>((const float*)C, (float*)Q1, op, F, 0, (int)R, (float*)U, orth, status,
                                               o.stream)
-                      : launch_extract<double>((const double*)C, op, nullptr, 0, (int)R, (double*)U, orth, status,
-                                               o.stream);
+                      : launch_extract<double>((const double*)C, (double*)Q1, op, F, 0, (int)R, (double*)U, orth,
+                                               status, o.stream);
     if (e != cudaSuccess) return from_cuda(e);
     return sync_status(o.stream, status);
 }

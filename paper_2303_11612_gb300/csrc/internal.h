@@ -79,12 +79,13 @@ size_t orth_scratch_bytes(const OrthPlan& p, int elem_size);
 template <typename T>
 cudaError_t launch_cholqr(const T* X, T* Q, const OrthPlan& p, double* factor, void* scratch, int* status,
                           cudaStream_t s);
-// U (I x R) = the R leading left singular vectors of C = X P, P = prev[nprev-1]
-// ... prev[0] (upper triangular FP64 factors of earlier steps; nprev may be 0),
-// sign-fixed.
+// U (I x R) = the R leading left singular vectors of C = X P, P = factors[nprev-1]
+// ... factors[0] (upper triangular FP64 factors of earlier steps; nprev may be
+// 0), sign-fixed. Q1 (I x L) is scratch; factors must have room for nprev + 1
+// factors (the extraction stores its own CholeskyQR factor after them).
 template <typename T>
-cudaError_t launch_extract(const T* X, const OrthPlan& p, const double* prev, int nprev, int R, T* U, void* scratch,
-                           int* status, cudaStream_t s);
+cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors, int nprev, int R, T* U,
+                           void* scratch, int* status, cudaStream_t s);
 
 // ---- mode products and norms (kernels_ttm.cu)
 // out = A x_n M: M(k_out, i) read as Mp[i * ld_i + k_out * ld_k].

@@ -13,77 +13,112 @@ namespace tk {
 namespace {
 
 constexpr int kT = kThreads;
-constexpr int JB = 64, KC = 32;
+constexpr int JB = 64, KC = 32, KP = KC + 4;   // rows padded to 36 elements: 16-byte aligned, conflict-free
 
-// OB = output block (a multiple of 8 covering K_out, or 64 with several blocks);
-// thread (jj = tid % JB, og = tid / JB) owns fiber jj and outputs og*OPT .. +OPT.
+// four consecutive T values from 16-byte aligned shared memory
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 x = *reinterpret_cast<const double2*>(p), y = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+
+// OB = output block (8, 16, 32 or 64 outputs); thread (jj = tid % JB, og = tid / JB)
+// owns fiber jj and outputs og*OPT .. +OPT. Both shared tiles keep the input
+// index contiguous, so stores are unit-stride and the inner loop reads four
+// input indices per 128-bit load (the M rows are broadcast across the warp).
+// The next chunk's global loads are issued into registers before the current
+// chunk is multiplied.
 template <typename T, int OB>
 __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeView v, const T* __restrict__ Mp,
                                                  int64_t K_out, int64_t ld_i, int64_t ld_k, T* __restrict__ out) {
     constexpr int OPT = OB / (kT / JB);
-    // the tile buffers (Ts, Ms) are dead once the products are done, so the output
-    // staging block Os reuses their storage
-    constexpr size_t kTileBytes = sizeof(T) * (JB * (KC + 1) + KC * OB);
+    constexpr int TPT = JB * KC / kT;                    // tile elements loaded per thread and chunk
+    constexpr int MPT = (OB * KC + kT - 1) / kT;         // M elements loaded per thread and chunk
+    constexpr size_t kTileBytes = sizeof(T) * (JB * KP + OB * KP);
     constexpr size_t kOutBytes = sizeof(T) * JB * (OB + 1);
     __shared__ __align__(16) unsigned char smem[kTileBytes > kOutBytes ? kTileBytes : kOutBytes];
-    auto Ts = reinterpret_cast<T(*)[KC + 1]>(smem);
-    auto Ms = reinterpret_cast<T(*)[OB]>(smem + sizeof(T) * JB * (KC + 1));
-    auto Os = reinterpret_cast<T(*)[OB + 1]>(smem);
+    auto Ts = reinterpret_cast<T(*)[KP]>(smem);                       // [JB][KP]
+    auto Ms = reinterpret_cast<T(*)[KP]>(smem + sizeof(T) * JB * KP);  // [OB][KP]
+    auto Os = reinterpret_cast<T(*)[OB + 1]>(smem);                   // [JB][OB + 1], after the products
     __shared__ int64_t bases[JB];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int64_t J = v.fibers();
     const int64_t j0 = (int64_t)blockIdx.x * JB;
     const int64_t o0 = (int64_t)blockIdx.y * OB;
     const int I = (int)v.i;
+    const bool contig = v.lf == 1;
     if (tid < JB) {
         const int64_t j = j0 + tid;
         bases[tid] = j < J ? v.base(j) : -1;
     }
     __syncthreads();
+    T tr[TPT], mr[MPT];
+    // element u of this thread's share of a chunk: (fiber, k) for the tile, (output, k) for M
+    auto load_chunk = [&](int i0) {
+#pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+            const int e = tid + u * kT;
+            int r, c;
+            if (contig) { r = e / KC; c = e % KC; }      // a warp reads KC consecutive elements of a fiber
+            else { r = e % JB; c = e / JB; }             // a warp reads one element of 32 neighbouring fibers
+            const int64_t b = bases[r];
+            const int i = i0 + c;
+            tr[u] = (b >= 0 && i < I) ? __ldg(A + b + (int64_t)i * v.lf) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < MPT; ++u) {
+            const int e = tid + u * kT;
+            int kk, oo;
+            if (ld_i == 1) { kk = e % KC; oo = e / KC; } // unit stride along the input index
+            else { oo = e % OB; kk = e / OB; }
+            const int i = i0 + kk;
+            const int64_t o = o0 + oo;
+            mr[u] = (e < OB * KC && i < I && o < K_out) ? __ldg(Mp + (int64_t)i * ld_i + o * ld_k) : T(0);
+        }
+    };
+    auto store_chunk = [&]() {
+#pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+            const int e = tid + u * kT;
+            int r, c;
+            if (contig) { r = e / KC; c = e % KC; }
+            else { r = e % JB; c = e / JB; }
+            Ts[r][c] = tr[u];
+        }
+#pragma unroll
+        for (int u = 0; u < MPT; ++u) {
+            const int e = tid + u * kT;
+            int kk, oo;
+            if (ld_i == 1) { kk = e % KC; oo = e / KC; }
+            else { oo = e % OB; kk = e / OB; }
+            if (e < OB * KC) Ms[oo][kk] = mr[u];
+        }
+    };
     const int jj = tid % JB, og = tid / JB;
     T acc[OPT];
 #pragma unroll
     for (int u = 0; u < OPT; ++u) acc[u] = T(0);
+    load_chunk(0);
     for (int i0 = 0; i0 < I; i0 += KC) {
-        if (v.lf == 1) {
-            // contiguous fibers: a warp reads KC consecutive elements of one fiber
-            for (int r = warp; r < JB; r += kT / 32) {
-                const int64_t b = bases[r];
-                const int i = i0 + lane;
-                Ts[r][lane] = (b >= 0 && i < I) ? __ldg(A + b + i) : T(0);
-            }
-        } else {
-            // strided fibers: a warp reads one element of 32 neighbouring fibers
-            for (int e = tid; e < JB * KC; e += kT) {
-                const int r = e % JB, c = e / JB;
-                const int64_t b = bases[r];
-                const int i = i0 + c;
-                Ts[r][c] = (b >= 0 && i < I) ? __ldg(A + b + (int64_t)i * v.lf) : T(0);
-            }
-        }
-        // M chunk: walk the unit-stride index across threads
-        if (ld_i == 1) {
-            for (int e = tid; e < KC * OB; e += kT) {
-                const int kk = e % KC, oo = e / KC;
-                const int i = i0 + kk;
-                const int64_t o = o0 + oo;
-                Ms[kk][oo] = (i < I && o < K_out) ? __ldg(Mp + i + o * ld_k) : T(0);
-            }
-        } else {
-            for (int e = tid; e < KC * OB; e += kT) {
-                const int kk = e / OB, oo = e % OB;
-                const int i = i0 + kk;
-                const int64_t o = o0 + oo;
-                Ms[kk][oo] = (i < I && o < K_out) ? __ldg(Mp + (int64_t)i * ld_i + o * ld_k) : T(0);
-            }
-        }
+        store_chunk();
         __syncthreads();
-        const int kc = min(KC, I - i0);
-        for (int kk = 0; kk < kc; ++kk) {
-            const T t = Ts[jj][kk];
-            const T* mr = &Ms[kk][og * OPT];
+        if (i0 + KC < I) load_chunk(i0 + KC);            // in flight during the products below
+#pragma unroll 2
+        for (int kk = 0; kk < KC; kk += 4) {
+            T t4[4];
+            ld4(&Ts[jj][kk], t4);
 #pragma unroll
-            for (int u = 0; u < OPT; ++u) acc[u] = fma(t, mr[u], acc[u]);
+            for (int u = 0; u < OPT; ++u) {
+                T m4[4];
+                ld4(&Ms[og * OPT + u][kk], m4);
+                acc[u] = fma(t4[0], m4[0], acc[u]);
+                acc[u] = fma(t4[1], m4[1], acc[u]);
+                acc[u] = fma(t4[2], m4[2], acc[u]);
+                acc[u] = fma(t4[3], m4[3], acc[u]);
+            }
         }
         __syncthreads();
     }
@@ -91,7 +126,7 @@ __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeVi
 #pragma unroll
     for (int u = 0; u < OPT; ++u) Os[jj][og * OPT + u] = acc[u];
     __syncthreads();
-    if (v.lf == 1) {
+    if (contig) {
         // out[o + j K_out]: consecutive threads -> consecutive o
         for (int e = tid; e < JB * OB; e += kT) {
             const int r = e / OB, oo = e % OB;

@@ -73,7 +73,7 @@ def test_driver_matches_oracle(tk, case, dims, ranks):
     assert abs(re_gpu - re_o) < 1e-5
     assert abs(re - re_o) < 1e-4                    # the identity-based RE reported by the call
     for n, (u, uo) in enumerate(zip(U, Uo)):
-        assert np.linalg.norm(u.T @ u - np.eye(u.shape[1])) < 1e-5
+        assert np.linalg.norm(u.T @ u - np.eye(u.shape[1])) < 10 * u.shape[1] * 1.19e-7
         assert np.linalg.norm(proj(u) - proj(uo), 2) < 1e-4, n
     rec = ot.reconstruct(G, U)
     rec_o = ot.reconstruct(Go, Uo)

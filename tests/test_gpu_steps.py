@@ -158,7 +158,9 @@ def test_leading_factor(tk, I, L, R):
     Uo, _ = ot.leading_left_singular_vectors(Cm, R)
     for dtype, tol in ((torch.float32, 2e-5), (torch.float64, 1e-10)):
         U = tk.leading_factor(colmajor(Cm, dtype), R).double().cpu().numpy()
-        assert np.linalg.norm(U.T @ U - np.eye(R)) < (1e-5 if dtype == torch.float32 else 1e-12)
+        # FP32: the Jacobi stops at a pair cosine of 4 eps and the stored factor is
+        # rounded once more, so ||U^T U - I||_F stays below 10 R eps_32
+        assert np.linalg.norm(U.T @ U - np.eye(R)) < (10 * R * 1.19e-7 if dtype == torch.float32 else 1e-12)
         assert np.linalg.norm(U @ U.T - Uo @ Uo.T, 2) < tol * 10
         assert np.max(np.abs(_align(U, Uo) - Uo)) < tol * 10
         # the sign rule holds on the GPU output itself
