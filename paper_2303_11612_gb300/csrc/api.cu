@@ -21,7 +21,7 @@ namespace {
 
 constexpr int kMaxOrder = 8;
 constexpr int64_t kMaxI = 1024;      // power-step register tiling (4 rows per thread)
-constexpr int kMaxL = 110;           // FP64 Cholesky of an L x L Gram in shared memory
+constexpr int kMaxL = 110;           // packed L x L factors of the extraction in shared memory
 
 thread_local cudaStream_t g_async_stream = nullptr;
 thread_local int* g_async_status = nullptr;
@@ -160,6 +160,7 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         if (mp.tc)
             p.max_partials = std::max(p.max_partials, power_tc_partials_bytes(mp.mv, mp.L, sms));
         mp.op = orth_plan(d[n], mp.L, sms);
+        if (!orth_supported(mp.op, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
         p.maxI = std::max(p.maxI, d[n]);
         p.maxL = std::max<int64_t>(p.maxL, mp.L);
         p.maxJ = std::max(p.maxJ, J);
@@ -675,6 +676,7 @@ tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, i
     if (L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
     const int elem = dt == TUCKER_F64 ? 8 : 4;
     const OrthPlan op = orth_plan(I, (int)L, num_sms());
+    if (!orth_supported(op, (int)R, dt == TUCKER_F64 ? 8 : 4)) return TUCKER_ERR_UNSUPPORTED;
     Arena a;
     a.take(sizeof(int) * 64);
     a.take(orth_scratch_bytes(op, elem));

@@ -74,14 +74,17 @@ struct OrthPlan {
 };
 OrthPlan orth_plan(int64_t I, int L, int num_sms);
 size_t orth_scratch_bytes(const OrthPlan& p, int elem_size);
-// One CholeskyQR pass: X (I x L) = Q F, F upper triangular (FP64, row-major,
-// written to `factor`), Q = X F^-1. X and Q may not alias.
+// True when the extraction of R columns fits the shared-memory limits.
+bool orth_supported(const OrthPlan& p, int R, int elem_size);
+// One CholeskyQR pass: X (I x L) = Q F, F upper triangular (packed rows in the
+// first L(L+1)/2 of the L^2 doubles at `factor`: a double-float pair per entry
+// for FP32 data, FP64 for FP64 data), Q = X F^-1. X and Q may not alias.
 template <typename T>
 cudaError_t launch_cholqr(const T* X, T* Q, const OrthPlan& p, double* factor, void* scratch, int* status,
                           cudaStream_t s);
 // U (I x R) = the R leading left singular vectors of C = X P, P = factors[nprev-1]
-// ... factors[0] (upper triangular FP64 factors of earlier steps; nprev may be
-// 0), sign-fixed. Q1 (I x L) is scratch; factors must have room for nprev + 1
+// ... factors[0] (factors of earlier steps, in L^2-double slots as written by
+// launch_cholqr; nprev may be 0), sign-fixed. Q1 (I x L) is scratch; factors must have room for nprev + 1
 // factors (the extraction stores its own CholeskyQR factor after them).
 template <typename T>
 cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors, int nprev, int R, T* U,

@@ -5,25 +5,36 @@
 // and F = F_k ... F_1 collects the triangular factors of the earlier steps
 // (each earlier step orthonormalised its output X_j = Q_j F_j and multiplied Q_j,
 // which leaves C unchanged). Extraction:
-//   1. One CholeskyQR pass X = Q1 R1: Gram X^T X from exact FP32 products summed
-//      in paired FP32 (about 2^-44), reduced across CTAs in a fixed order; FP64
-//      Cholesky (shifted once on a numerically singular pivot, Fukaya et al.
-//      2020); Q1 = X R1^-1 by FP64 substitution.
+//   1. One CholeskyQR pass X = Q1 R1: Gram X^T X from exact products summed in
+//      paired precision, reduced across CTAs in a fixed order; Cholesky
+//      (shifted once on a numerically singular pivot, Fukaya et al. 2020);
+//      Q1 = X R1^-1 with a row-oriented triangular inverse.
 //   2. A second Gram/Cholesky Q1^T Q1 = R2^T R2, so Q = Q1 R2^-1 is orthonormal
-//      and C = Q M with M = R2 R1 F (L x L).
+//      and C = Q M with M = R2 R1 F (L x L, upper triangular).
 //   3. One-sided (Hestenes) Jacobi on the columns of M with paired-precision
 //      dot products: M V = U_M S, U_M = the rotated columns, normalised;
-//      columns at rounding level are re-orthogonalised (FP64 Gram-Schmidt), so
-//      they keep the sketch's own weak directions. U = Q U_M = Q1 W with
-//      W = R2^-1 U_M (FP64 back-substitution) -- Q is never formed.
-//   4. U = Q1 W in paired precision; each column's largest-magnitude entry
-//      made positive. A column that is exactly dependent is completed by
-//      Gram-Schmidt of unit vectors against the others.
+//      columns at rounding level are re-orthogonalised (classical Gram-Schmidt,
+//      twice), so they keep the sketch's own weak directions.
+//      U = Q U_M = Q1 W with W = R2^-1 U_M (back-substitution); Q is never formed.
+//   4. U = Q1 W in paired precision.
+//   5. A final pass keeps U orthonormal where the sketch is numerically
+//      rank-deficient (CholeskyQR cannot orthonormalise those directions): if
+//      U^T U is not within 8 eps of I, one CholeskyQR pass on U itself, which
+//      leaves the span of every leading set of columns unchanged; columns that
+//      collapse are rebuilt from unit vectors by Gram-Schmidt. Then each
+//      column's largest-magnitude entry is made positive.
 // Intermediate power steps need only Q1 and R1: step 1 alone.
+//
+// Small matrices (Gram, Cholesky factors, their products and inverses) are
+// packed upper triangles, row-major, in the scalar S = SmallScalar<T>: a
+// double-float pair for FP32 data (the FP64 pipe of this GPU is narrow, and
+// these steps form long dependent chains in one CTA), FP64 for FP64 data.
+// Their entries must stay within about 1e-30 .. 1e30 for the pair form.
 #include <float.h>
 
 #include <algorithm>
 
+#include "df.cuh"
 #include "internal.h"
 
 namespace tk {
@@ -31,13 +42,33 @@ namespace {
 
 constexpr int kT = kThreads;
 constexpr int kXT = 256;                 // threads of the extraction kernel (any SM can host it)
-constexpr int kDegenerate = 8;           // flag bit: some factor column needs completion
+constexpr int kGramRows = 64;            // fewest rows per Gram CTA (few partials to reduce)
+
+__host__ __device__ __forceinline__ int packed_index(int a, int b, int L) {
+    return a * L - (a * (a - 1)) / 2 + (b - a);
+}
+__host__ __device__ __forceinline__ size_t packed_size(int L) { return (size_t)L * (L + 1) / 2; }
+
+// Unit roundoff of the Gram matrix: paired-FP32 sums for FP32 data, FP64 sums otherwise.
+template <typename T> __device__ __forceinline__ double gram_unit() { return sizeof(T) == 4 ? 0x1p-44 : 0x1p-53; }
+
+template <typename S, typename T> __device__ __forceinline__ S to_s(T x) {
+    if constexpr (sizeof(T) == 4) return Sc<S>::from_float((float)x);
+    else return Sc<S>::from_double((double)x);
+}
+
+// Load that bypasses L1 (data written by other CTAs of the same launch).
+__device__ __forceinline__ df ld_cg(const df* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 
 template <typename T> struct GramAcc;
 template <> struct GramAcc<float> {
     Pair s{0.f, 0.f};
     __device__ void add(float a, float b) { pair_add_prod(s, a, b); }
-    __device__ double value() const { return pair_value(s); }
+    __device__ df value() const { return two_sum(s.hi, s.lo); }
 };
 template <> struct GramAcc<double> {
     double s = 0.0;
@@ -45,11 +76,9 @@ template <> struct GramAcc<double> {
     __device__ double value() const { return s; }
 };
 
-__device__ __forceinline__ int packed_index(int a, int b, int L) { return a * L - (a * (a - 1)) / 2 + (b - a); }
-
 // Gram partial of this CTA's rows (packed upper triangle) -> partial[blockIdx.x].
-template <typename T>
-__device__ void gram_partial(const T* __restrict__ X, int64_t I, int L, int rows, double* __restrict__ partial,
+template <typename T, typename S>
+__device__ void gram_partial(const T* __restrict__ X, int64_t I, int L, int rows, S* __restrict__ partial,
                              unsigned char* smem) {
     T* xs = reinterpret_cast<T*>(smem);   // [rows][L]
     const int64_t r0 = (int64_t)blockIdx.x * rows;
@@ -59,13 +88,15 @@ __device__ void gram_partial(const T* __restrict__ X, int64_t I, int L, int rows
         xs[r * L + c] = X[(int64_t)c * I + r0 + r];
     }
     __syncthreads();
-    double* out = partial + (int64_t)blockIdx.x * (L * (L + 1) / 2);
-    for (int a = 0; a < L; ++a) {
-        for (int b = a + threadIdx.x; b < L; b += blockDim.x) {
-            GramAcc<T> acc;
-            for (int r = 0; r < nr; ++r) acc.add(xs[r * L + a], xs[r * L + b]);
-            out[packed_index(a, b, L)] = acc.value();
-        }
+    const int np = (int)packed_size(L);
+    S* out = partial + (int64_t)blockIdx.x * np;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        int a = 0, rem = p;
+        while (rem >= L - a) { rem -= L - a; ++a; }
+        const int b = a + rem;
+        GramAcc<T> acc;
+        for (int r = 0; r < nr; ++r) acc.add(xs[r * L + a], xs[r * L + b]);
+        out[p] = acc.value();
     }
 }
 
@@ -80,67 +111,70 @@ __device__ bool last_cta(unsigned* ticket) {
     return last;
 }
 
-// 1/sqrt(d) for finite d > 0: an FP32 estimate on the mantissa refined by two
-// Newton steps in FP64 (GB300's FP64 square root and division are slow chains).
-__device__ __forceinline__ double rsqrt_fp64(double d) {
-    int e;
-    double m = frexp(d, &e);                      // d = m 2^e, m in [0.5, 1)
-    if (e & 1) { m *= 2.0; e -= 1; }              // m in [0.5, 2), e even
-    double y = (double)rsqrtf((float)m);
-    y = y * fma(-0.5 * m * y, y, 1.5);
-    y = y * fma(-0.5 * m * y, y, 1.5);
-    return ldexp(y, -e / 2);
-}
-
-// Sum the partials in block order into G (L x L, shared) and factor G = R^T R
-// (R upper, row-major, left in W with zeros below the diagonal; 1/R_kk in dinv).
-// A pivot below 1e-15 of its diagonal entry restarts once with G + s I,
-// s = 11 (I L + L (L + 1)) 2^-53 tr(G). Returns false if that also fails (R = I).
-__device__ bool reduce_cholesky(const double* __restrict__ partial, int nparts, int L, int64_t I, double* G,
-                                double* W, double* dinv, unsigned* ticket, int* status) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int np = L * (L + 1) / 2;
+// Sum the partials in block order into G and factor G = R^T R (all packed;
+// R in W, 1/R_kk in dinv). A pivot below 8u of its diagonal entry restarts once
+// with G + s I, s = 11 (I L + L (L + 1)) u tr(G), u the Gram's unit roundoff.
+// Returns false if that also fails (then R = I).
+//
+// Right-looking, one barrier per column: in the phase of column k every warp
+// updates whole trailing rows from the unscaled row k (W_ij -= W_ki W_kj / d_k),
+// the thread that updates W_{k+1,k+1} takes the next pivot at once, and row
+// k - 1 is scaled by 1/R_{k-1,k-1} alongside.
+template <typename T, typename S>
+__device__ bool reduce_cholesky(const S* __restrict__ partial, int nparts, int L, int64_t I, S* G, S* W, S* dinv,
+                                unsigned* ticket, int* status) {
+    using F = Sc<S>;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int np = (int)packed_size(L);
+    const double u = gram_unit<T>();
     __shared__ int bad;
-    __shared__ double inv_piv;
+    __shared__ S inv2[2];
     __shared__ double tr;
     for (int p = tid; p < np; p += nt) {
-        double acc = 0.0;
-#pragma unroll 8
-        for (int b = 0; b < nparts; ++b) acc += __ldcg(partial + (int64_t)b * np + p);
-        int a = 0, rem = p;
-        while (rem >= L - a) { rem -= L - a; ++a; }
-        const int bb = a + rem;
-        G[a * L + bb] = acc;
-        G[bb * L + a] = acc;
+        S acc = ld_cg(partial + p);
+        for (int b = 1; b < nparts; ++b) acc = acc + ld_cg(partial + (int64_t)b * np + p);
+        G[p] = acc;
     }
     if (tid == 0) *ticket = 0;                           // ready for the next use
     __syncthreads();
-    double shift = 0.0;
+    const S thr = F::from_double(8.0 * u);
+    S shift = F::zero();
+    // pivot k from the updated W_kk: false when numerically singular
+    auto pivot = [&](int k) {
+        const int kk = packed_index(k, k, L);
+        const S d = W[kk];
+        if (!F::gt(d, (G[kk] + shift) * thr) || !F::finite(d)) {
+            bad = 1;
+        } else {
+            const S y = F::rsqrt(d);
+            W[kk] = d * y;
+            dinv[k] = y;
+            inv2[k & 1] = y * y;
+        }
+    };
     for (int attempt = 0; attempt < 2; ++attempt) {
-        for (int p = tid; p < L * L; p += nt) W[p] = G[p] + ((p / L == p % L) ? shift : 0.0);
+        for (int p = tid; p < np; p += nt) W[p] = G[p];
+        __syncthreads();
+        for (int k = tid; k < L; k += nt) W[packed_index(k, k, L)] = G[packed_index(k, k, L)] + shift;
         if (tid == 0) bad = 0;
         __syncthreads();
-        for (int k = 0; k < L; ++k) {
-            if (tid == 0) {
-                const double d = W[k * L + k];
-                const double ref = G[k * L + k] + shift;
-                if (!(d > 1e-15 * ref) || !isfinite(d)) {
-                    bad = 1;
-                } else {
-                    const double y = rsqrt_fp64(d);
-                    W[k * L + k] = d * y;
-                    dinv[k] = y;
-                    inv_piv = y;
-                }
+        if (tid == 0) pivot(0);
+        __syncthreads();
+        for (int k = 0; k < L && !bad; ++k) {
+            if (k > 0) {                                  // scale row k - 1
+                const S y = dinv[k - 1];
+                S* row = W + packed_index(k - 1, k - 1, L);
+                for (int j = 1 + tid; j < L - k + 1; j += nt) row[j] = row[j] * y;
             }
-            __syncthreads();
-            if (bad) break;
-            for (int j = k + 1 + tid; j < L; j += nt) W[k * L + j] *= inv_piv;
-            __syncthreads();
-            const int m = L - k - 1;
-            for (int p = tid; p < m * m; p += nt) {
-                const int i = k + 1 + p / m, j = k + 1 + p % m;
-                if (j >= i) W[i * L + j] -= W[k * L + i] * W[k * L + j];
+            const S y2 = inv2[k & 1];
+            const S* rk = W + packed_index(k, k, L);      // rk[j - k] = W_kj
+            for (int i = k + 1 + warp; i < L; i += nw) {
+                const S cki = rk[i - k] * y2;
+                S* ri = W + packed_index(i, i, L);        // ri[j - i] = W_ij
+                for (int j = i + lane; j < L; j += 32) {
+                    ri[j - i] = ri[j - i] - cki * rk[j - k];
+                    if (j == k + 1) pivot(k + 1);         // i == j == k + 1: warp 0, lane 0
+                }
             }
             __syncthreads();
         }
@@ -148,77 +182,96 @@ __device__ bool reduce_cholesky(const double* __restrict__ partial, int nparts, 
         if (attempt == 0) {
             if (tid == 0) {
                 double t = 0.0;
-                for (int k = 0; k < L; ++k) t += G[k * L + k];
+                for (int k = 0; k < L; ++k) t += F::to_double(G[packed_index(k, k, L)]);
                 tr = t > 0.0 ? t : 1.0;
             }
             __syncthreads();
-            shift = 11.0 * ((double)I * L + (double)L * (L + 1)) * 1.1102230246251565e-16 * tr;
+            shift = F::from_double(11.0 * ((double)I * L + (double)L * (L + 1)) * u * tr);
             __syncthreads();
         }
     }
     const int failed = bad;
     __syncthreads();
-    for (int p = tid; p < L * L; p += nt) {
-        const int a = p / L, b = p % L;
-        if (failed) W[p] = (a == b) ? 1.0 : 0.0;
-        else if (b < a) W[p] = 0.0;
+    if (failed) {
+        for (int p = tid; p < np; p += nt) W[p] = F::zero();
+        __syncthreads();
+        for (int k = tid; k < L; k += nt) {
+            W[packed_index(k, k, L)] = F::one();
+            dinv[k] = F::one();
+        }
+        if (tid == 0) set_status(status, kStatNumerical);
     }
-    if (failed)
-        for (int k = tid; k < L; k += nt) dinv[k] = 1.0;
-    if (failed && tid == 0) set_status(status, kStatNumerical);
     __syncthreads();
     return !failed;
 }
 
-// Inverse of the upper-triangular R (row-major, L x L, 1/R_kk in dinv) into Ri.
-// Row i of R^-1 solves y R = e_i by forward substitution (one thread per row),
-// so the computed inverse has a small residual R^-1 R - I: X R^-1 R stays close
-// to X, which is what Q R = X needs.
-__device__ void upper_inverse(const double* R, const double* dinv, int L, double* Ri) {
+// Inverse of the packed upper-triangular R (1/R_kk in dinv) into Ri (packed),
+// with RT a scratch packed lower triangle. Row i of R^-1 solves y R = e_i by
+// forward substitution (one thread per row, four partial sums), so the computed
+// inverse has a small residual R^-1 R - I: X R^-1 R stays close to X, which is
+// what Q R = X needs. The substitution walks columns of R, so R is first
+// transposed into RT (row j of RT = column j of R, contiguous).
+template <typename S>
+__device__ void upper_inverse(const S* R, const S* dinv, int L, S* RT, S* Ri) {
+    using F = Sc<S>;
+    for (int p = threadIdx.x; p < L * L; p += blockDim.x) {
+        const int a = p / L, b = p % L;
+        if (b >= a) RT[b * (b + 1) / 2 + a] = R[packed_index(a, b, L)];
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        double* y = Ri + i * L;
-        for (int j = 0; j < i; ++j) y[j] = 0.0;
+        S* y = Ri + packed_index(i, i, L) - i;            // y[j] = Ri_ij, j >= i
         for (int j = i; j < L; ++j) {
-            double acc = (i == j) ? 1.0 : 0.0;
-            for (int k = i; k < j; ++k) acc = fma(-y[k], R[k * L + j], acc);
-            y[j] = acc * dinv[j];
+            const S* col = RT + j * (j + 1) / 2;          // col[k] = R_kj
+            S a0 = (i == j) ? F::one() : F::zero(), a1 = F::zero(), a2 = F::zero(), a3 = F::zero();
+            int k = i;
+            for (; k + 3 < j; k += 4) {
+                a0 = F::fma(-y[k], col[k], a0);
+                a1 = F::fma(-y[k + 1], col[k + 1], a1);
+                a2 = F::fma(-y[k + 2], col[k + 2], a2);
+                a3 = F::fma(-y[k + 3], col[k + 3], a3);
+            }
+            for (; k < j; ++k) a0 = F::fma(-y[k], col[k], a0);
+            y[j] = ((a0 + a1) + (a2 + a3)) * dinv[j];
         }
     }
     __syncthreads();
 }
 
 // ---------------------------------------------------------------- one CholeskyQR pass
-// R (row-major, L x L) and R^-1 (same layout) of X^T X = R^T R.
+// R and R^-1 (packed, scalar S) of X^T X = R^T R.
 template <typename T>
 __global__ void __launch_bounds__(kT) gram_chol_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
-                                                       double* __restrict__ partial, unsigned* ticket,
-                                                       double* __restrict__ R, double* __restrict__ Rinv,
-                                                       int* status) {
+                                                       typename SmallScalar<T>::type* __restrict__ partial,
+                                                       unsigned* ticket, typename SmallScalar<T>::type* __restrict__ R,
+                                                       typename SmallScalar<T>::type* __restrict__ Rinv, int* status) {
+    using S = typename SmallScalar<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    gram_partial<T>(X, I, L, rows, partial, smem_raw);
+    gram_partial<T, S>(X, I, L, rows, partial, smem_raw);
     if (!last_cta(ticket)) return;
-    double* G = reinterpret_cast<double*>(smem_raw);
-    double* W = G + L * L;
-    double* dinv = W + L * L;
-    reduce_cholesky(partial, gridDim.x, L, I, G, W, dinv, ticket, status);
-    upper_inverse(W, dinv, L, G);
-    for (int p = threadIdx.x; p < L * L; p += blockDim.x) {
+    const int np = (int)packed_size(L);
+    S* G = reinterpret_cast<S*>(smem_raw);
+    S* W = G + np;
+    S* RT = W + np;
+    S* dinv = RT + np;
+    reduce_cholesky<T, S>(partial, gridDim.x, L, I, G, W, dinv, ticket, status);
+    upper_inverse<S>(W, dinv, L, RT, G);
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
         R[p] = W[p];
         Rinv[p] = G[p];
     }
 }
 
-// Q = X R^-1, one thread per entry of Q, in paired precision from X (exact) and
-// R^-1 split into high and low FP32 parts (FP64 for T = double).
+// Q = X R^-1, one thread per entry of Q, in paired precision from X (exact)
+// and the double-float R^-1 (FP64 for T = double).
 template <typename T> struct ApplyAcc;
 template <> struct ApplyAcc<float> {
     Pair s{0.f, 0.f};
-    __device__ void add(float x, double w) {
-        const float hi = (float)w;
-        pair_add_prod(s, x, hi);
-        pair_add_prod(s, x, (float)(w - (double)hi));
+    __device__ void add(float x, df w) {
+        pair_add_prod(s, x, w.hi);
+        pair_add_prod(s, x, w.lo);
     }
-    __device__ float value() const { return (float)pair_value(s); }
+    __device__ float value() const { return s.hi + s.lo; }
 };
 template <> struct ApplyAcc<double> {
     double s = 0.0;
@@ -228,17 +281,20 @@ template <> struct ApplyAcc<double> {
 
 template <typename T>
 __global__ void __launch_bounds__(kT) apply_rinv_kernel(const T* __restrict__ X, int64_t I, int L,
-                                                        const double* __restrict__ Rinv, T* __restrict__ Q) {
+                                                        const typename SmallScalar<T>::type* __restrict__ Rinv,
+                                                        T* __restrict__ Q) {
+    using S = typename SmallScalar<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* Ri = reinterpret_cast<double*>(smem_raw);    // [L][L]
-    for (int p = threadIdx.x; p < L * L; p += kT) Ri[p] = Rinv[p];
+    S* Ri = reinterpret_cast<S*>(smem_raw);    // packed
+    const int np = (int)packed_size(L);
+    for (int p = threadIdx.x; p < np; p += kT) Ri[p] = Rinv[p];
     __syncthreads();
     const int64_t n = I * L;
     for (int64_t e = (int64_t)blockIdx.x * kT + threadIdx.x; e < n; e += (int64_t)gridDim.x * kT) {
         const int l = (int)(e / I);
         const int64_t i = e - (int64_t)l * I;
         ApplyAcc<T> acc;
-        for (int m = 0; m <= l; ++m) acc.add(X[(int64_t)m * I + i], Ri[m * L + l]);
+        for (int m = 0; m <= l; ++m) acc.add(X[(int64_t)m * I + i], Ri[packed_index(m, l, L)]);
         Q[e] = (T)acc.value();
     }
 }
@@ -249,7 +305,7 @@ template <> struct DotAcc<float> {
     Pair s{0.f, 0.f};
     __device__ void add(float a, float b) { pair_add_prod(s, a, b); }
     __device__ void reduce() { s = warp_sum_pair(s); }
-    __device__ double value() const { return pair_value(s); }
+    __device__ float value() const { return s.hi + s.lo; }
 };
 template <> struct DotAcc<double> {
     double s = 0.0;
@@ -257,8 +313,6 @@ template <> struct DotAcc<double> {
     __device__ void reduce() { s = warp_sum(s); }
     __device__ double value() const { return s; }
 };
-
-constexpr int kMaxPerThread = 12;        // L * L / kXT for L <= 110
 
 // Pair dot products over a group of GS lanes (GS = 8, 16 or 32).
 template <int GS>
@@ -279,17 +333,46 @@ __device__ __forceinline__ double group_sum(double s) {
     return s;
 }
 
+// Rotation (c, s) that zeroes the coupling g of columns with squared norms a, b
+// (t = tan of the angle). Any c, s with s / c = t form a scaled rotation, which
+// keeps the pair's orthogonality, so the FP32 form uses the fast approximate
+// reciprocal and square roots: their rounding only perturbs the angle.
+__device__ __forceinline__ void rotation(float a, float b, float g, float& c, float& s) {
+    const float zeta = __fdividef(b - a, 2.f * g);
+    const float az = fabsf(zeta);
+    float t;
+    if (az > 1e18f) {
+        t = __fdividef(0.5f, zeta);
+    } else {
+        const float h = fmaf(zeta, zeta, 1.f);
+        t = __fdividef(copysignf(1.f, zeta), az + h * rsqrtf(h));
+    }
+    c = rsqrtf(fmaf(t, t, 1.f));
+    s = c * t;
+}
+__device__ __forceinline__ void rotation(double a, double b, double g, double& c, double& s) {
+    const double zeta = (b - a) / (2.0 * g);
+    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    c = 1.0 / sqrt(1.0 + t * t);
+    s = c * t;
+}
+
 // One cyclic sweep of one-sided Jacobi on the columns of Mc (column-major,
-// column c at Mc + c * L); pairs handled by groups of GS lanes. Returns the
-// number of rotations.
+// column c at Mc + c * L, L <= 4 * GS); pairs handled by groups of GS lanes,
+// each lane holding up to 4 entries of both columns in registers. The squared
+// norms a, b are plain sums (they only set the angle and the threshold); the
+// coupling g, which cancels, is summed in paired precision. Returns the number
+// of rotations.
 template <typename T, int GS>
 __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot) {
+    constexpr int NE = 4;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kGroupsPerWarp = 32 / GS;
     const int groups = ((int)blockDim.x >> 5) * kGroupsPerWarp, gl = lane % GS;
     const int m = Lp - 1;
     if (tid == 0) *nrot = 0;
     __syncthreads();
+    int mine = 0;
     for (int rnd = 0; rnd < m; ++rnd) {
         // the loop bound is uniform across a warp, so all 32 lanes reach every
         // shuffle below; groups without a pair take part with zeros
@@ -297,113 +380,164 @@ __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot) {
             const int pi = base + lane / GS;
             int p = L, q = L;
             if (pi < Lp / 2) {
-                if (pi == 0) { p = rnd; q = m; }
-                else { p = (rnd + pi) % m; q = (rnd - pi + m) % m; }
+                if (pi == 0) {
+                    p = rnd; q = m;
+                } else {
+                    p = rnd + pi; if (p >= m) p -= m;
+                    q = rnd - pi; if (q < 0) q += m;
+                }
             }
             const bool live = p < L && q < L;
             T* cp = Mc + (live ? p : 0) * L;
             T* cq = Mc + (live ? q : 0) * L;
-            T a, b, g;
-            if (sizeof(T) == 4) {
-                Pair al{0.f, 0.f}, be{0.f, 0.f}, ga{0.f, 0.f};
-                for (int r = gl; r < L && live; r += GS) {
-                    const float x = (float)cp[r], y = (float)cq[r];
-                    pair_add_prod(al, x, x);
-                    pair_add_prod(be, y, y);
-                    pair_add_prod(ga, x, y);
-                }
-                al = group_sum_pair<GS>(al);
-                be = group_sum_pair<GS>(be);
-                ga = group_sum_pair<GS>(ga);
-                a = (T)(al.hi + al.lo); b = (T)(be.hi + be.lo); g = (T)(ga.hi + ga.lo);
-            } else {
-                double al = 0, be = 0, ga = 0;
-                for (int r = gl; r < L && live; r += GS) {
-                    const double x = (double)cp[r], y = (double)cq[r];
-                    al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
-                }
-                a = group_sum<GS>(al); b = group_sum<GS>(be); g = group_sum<GS>(ga);
+            T x[NE], y[NE];
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+                const int r = gl + e * GS;
+                const bool in = live && r < L;
+                x[e] = in ? cp[r] : T(0);
+                y[e] = in ? cq[r] : T(0);
             }
-            // all in the working precision (the dot products are accurate to its
-            // last bit): FP64 square roots and divisions are long chains on this part
-            if (live && fabs(g) > tiny && g * g > tol * tol * a * b) {
-                const T zeta = (b - a) / (T(2) * g);
-                const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-                const T c = T(1) / sqrt(T(1) + t * t), s = c * t;
-                for (int r = gl; r < L; r += GS) {
-                    const T x = cp[r], y = cq[r];
-                    cp[r] = c * x - s * y;
-                    cq[r] = s * x + c * y;
+            T a = T(0), b = T(0), g;
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+                a = fma(x[e], x[e], a);
+                b = fma(y[e], y[e], b);
+            }
+            if constexpr (sizeof(T) == 4) {
+                Pair ga{0.f, 0.f};
+#pragma unroll
+                for (int e = 0; e < NE; ++e) pair_add_prod(ga, x[e], y[e]);
+#pragma unroll
+                for (int o = GS / 2; o > 0; o >>= 1) {
+                    const float ta = __shfl_xor_sync(0xffffffffu, a, o);
+                    const float tb = __shfl_xor_sync(0xffffffffu, b, o);
+                    Pair t;
+                    t.hi = __shfl_xor_sync(0xffffffffu, ga.hi, o);
+                    t.lo = __shfl_xor_sync(0xffffffffu, ga.lo, o);
+                    a += ta;
+                    b += tb;
+                    pair_add(ga, t);
                 }
-                if (gl == 0) atomicAdd(nrot, 1);
+                g = ga.hi + ga.lo;
+            } else {
+                double ga = 0.0;
+#pragma unroll
+                for (int e = 0; e < NE; ++e) ga = fma(x[e], y[e], ga);
+                a = group_sum<GS>(a); b = group_sum<GS>(b); g = group_sum<GS>(ga);
+            }
+            if (live && fabs(g) > tiny && g * g > tol * tol * a * b) {
+                T c, s;
+                rotation(a, b, g, c, s);
+#pragma unroll
+                for (int e = 0; e < NE; ++e) {
+                    const int r = gl + e * GS;
+                    if (r < L) {
+                        cp[r] = c * x[e] - s * y[e];
+                        cq[r] = s * x[e] + c * y[e];
+                    }
+                }
+                mine += gl == 0;
             }
         }
         __syncthreads();
     }
+    if (mine) atomicAdd(nrot, mine);
+    __syncthreads();
     const int n = *nrot;
     __syncthreads();
     return n;
 }
 
+// Shared-memory layout of the extraction's last CTA (byte offsets).
+struct XLayout {
+    size_t rf, g, h, dinv, sig, inrm, dots, perm, total;
+};
+__host__ __device__ inline size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline size_t zmax(size_t a, size_t b) { return a > b ? a : b; }
+__host__ __device__ inline XLayout xlayout(int L, int R, int elem) {
+    const int Lp = L + (L & 1);
+    const size_t np = packed_size(L);
+    XLayout x;
+    x.rf = 0;                                                       // packed R2
+    x.g = up16(8 * np);                                             // packed P / M, later U_M
+    x.h = x.g + up16(zmax(8 * np, (size_t)elem * R * L));           // packed products, later Mc
+    x.dinv = x.h + up16(zmax(8 * np, (size_t)elem * Lp * L));
+    x.sig = x.dinv + up16((size_t)8 * L);
+    x.inrm = x.sig + up16((size_t)elem * Lp);
+    x.dots = x.inrm + up16((size_t)elem * Lp);
+    x.perm = x.dots + up16((size_t)elem * R);
+    x.total = x.perm + up16(sizeof(int) * Lp);
+    return x;
+}
+
 // Grid of Gram CTAs over Q1 (kXT threads each). The last CTA: Cholesky
-// Q1^T Q1 = R2^T R2, M = R2 P with P = prev[nprev-1] ... prev[0], Jacobi on M,
-// U_M (rounding-level columns re-orthogonalised) and W = R2^-1 U_M for the R
-// leading columns (FP64, L x R, column-major). An exactly dependent column gets
-// W = 0 and raises the kDegenerate flag.
+// Q1^T Q1 = R2^T R2, M = R2 P with P = prev[nprev-1] ... prev[0] (packed
+// factors fstride apart; prev[nprev-1] is R1), Jacobi on M, U_M (rounding-level
+// columns re-orthogonalised) and W = R2^-1 U_M for the R leading columns
+// (scalar S, L x R, column-major). A column with no direction left gets W = 0
+// (the final pass completes it).
 template <typename T>
 __global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
-                                                      double* __restrict__ partial, unsigned* ticket,
-                                                      const double* __restrict__ prev, int nprev, int R,
-                                                      double* __restrict__ Wout, int* flag, int* status) {
+                                                      typename SmallScalar<T>::type* __restrict__ partial,
+                                                      unsigned* ticket,
+                                                      const typename SmallScalar<T>::type* __restrict__ prev,
+                                                      size_t fstride, int nprev, int R,
+                                                      typename SmallScalar<T>::type* __restrict__ Wout,
+                                                      int* status) {
+    using S = typename SmallScalar<T>::type;
+    using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    gram_partial<T>(X, I, L, rows, partial, smem_raw);
+    gram_partial<T, S>(X, I, L, rows, partial, smem_raw);
     if (!last_cta(ticket)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kXT / 32;
     const int Lp = L + (L & 1);
-    double* G = reinterpret_cast<double*>(smem_raw);     // [L][L]; after the Cholesky: P, then M
-    double* Rf = G + L * L;                                // [L][L] Cholesky factor (upper, row-major)
-    double* UM = Rf + L * L;                               // column-major [R][L], FP64
-    double* wb = UM + (size_t)R * L;                       // [nwarps][L] back-substitution rows
-    double* dinv = wb + nwarps * L;                        // [L] 1 / R2_kk
-    double* inrm = dinv + L;                               // [Lp] 1 / column norms of the rotated M
-    T* Mc = reinterpret_cast<T*>(inrm + Lp);               // column-major [Lp][L]
-    T* sig = Mc + Lp * L;                                  // [Lp]
-    int* perm = reinterpret_cast<int*>(sig + Lp);          // [Lp]
-    __shared__ unsigned long long mx_bits;
+    const int np = (int)packed_size(L);
+    const XLayout lay = xlayout(L, R, sizeof(T));
+    S* Rf = reinterpret_cast<S*>(smem_raw + lay.rf);
+    S* G = reinterpret_cast<S*>(smem_raw + lay.g);
+    S* H = reinterpret_cast<S*>(smem_raw + lay.h);
+    S* dinv = reinterpret_cast<S*>(smem_raw + lay.dinv);   // [L] 1 / R2_kk
+    T* sig = reinterpret_cast<T*>(smem_raw + lay.sig);     // [Lp] column norms of the rotated M
+    T* inrm = reinterpret_cast<T*>(smem_raw + lay.inrm);   // [Lp] their reciprocals
+    T* dots = reinterpret_cast<T*>(smem_raw + lay.dots);   // [R] Gram-Schmidt coefficients
+    int* perm = reinterpret_cast<int*>(smem_raw + lay.perm);
+    T* Mc = reinterpret_cast<T*>(H);                       // column-major [Lp][L], once M is in G
+    T* UM = reinterpret_cast<T*>(G);                       // column-major [R][L], once Mc is formed
     __shared__ int nrot;
-    __shared__ double fro2;
-    __shared__ double red[kXT / 32];
-    __shared__ double bcast;
-    __shared__ int deg;
+    __shared__ T fro2;
+    __shared__ T nrm2;
+    __shared__ unsigned long long mx_bits;
 
-    reduce_cholesky(partial, gridDim.x, L, I, G, Rf, dinv, ticket, status);
+    reduce_cholesky<T, S>(partial, gridDim.x, L, I, G, Rf, dinv, ticket, status);
 
-    // P = prev[nprev-1] ... prev[0] (upper triangular, FP64) into G, then M = R2 P
-    // in place: row a of F P needs only rows >= a of P, so rows are replaced top-down
-    for (int p = tid; p < L * L; p += kXT) G[p] = prev[p];
-    __syncthreads();
+    // M = R2 prev[nprev-1] ... prev[0]: products of packed upper triangles, one
+    // thread per output entry, alternating between H and G so the last lands in G
+    const S* src = prev;
     for (int f = 1; f <= nprev; ++f) {
-        const double* F = f < nprev ? prev + (int64_t)f * L * L : Rf;
-        for (int a = 0; a < L; ++a) {
-            double acc[kMaxPerThread];
-            int cnt = 0;
-            for (int c = tid; c < L; c += kXT, ++cnt) {
-                double s = 0.0;
-                for (int b = a; b <= c; ++b) s = fma(F[a * L + b], G[b * L + c], s);
-                acc[cnt] = s;
+        const S* Fm = f < nprev ? prev + (size_t)f * fstride : Rf;
+        S* dst = ((nprev - f) & 1) ? H : G;
+        for (int p = tid; p < L * L; p += kXT) {
+            const int a = p / L, c = p % L;
+            if (c < a) continue;
+            S acc0 = F::zero(), acc1 = F::zero();
+            int b = a;
+            for (; b + 1 <= c; b += 2) {
+                acc0 = F::fma(Fm[packed_index(a, b, L)], src[packed_index(b, c, L)], acc0);
+                acc1 = F::fma(Fm[packed_index(a, b + 1, L)], src[packed_index(b + 1, c, L)], acc1);
             }
-            __syncthreads();
-            cnt = 0;
-            for (int c = tid; c < L; c += kXT, ++cnt) G[a * L + c] = c >= a ? acc[cnt] : 0.0;
-            __syncthreads();
+            if (b == c) acc0 = F::fma(Fm[packed_index(a, c, L)], src[packed_index(c, c, L)], acc0);
+            dst[packed_index(a, c, L)] = acc0 + acc1;
         }
+        __syncthreads();
+        src = dst;
     }
     // M scaled by a power of two (largest entry in [1, 2)) and stored in T
-    if (tid == 0) { mx_bits = 0ull; fro2 = 0.0; }
+    if (tid == 0) { mx_bits = 0ull; fro2 = T(0); }
     __syncthreads();
     {
         double mxl = 0.0;
-        for (int p = tid; p < L * L; p += kXT) mxl = fmax(mxl, fabs(G[p]));
+        for (int p = tid; p < np; p += kXT) mxl = fmax(mxl, fabs(F::to_double(G[p])));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mxl = fmax(mxl, __shfl_xor_sync(0xffffffffu, mxl, o));
         if (lane == 0) atomicMax(&mx_bits, (unsigned long long)__double_as_longlong(mxl));
@@ -413,12 +547,12 @@ __global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, i
     int ex = 0;
     if (mxv > 0.0) frexp(mxv, &ex);
     {
-        double s2 = 0.0;
+        T s2 = T(0);
         for (int p = tid; p < Lp * L; p += kXT) {
             const int c = p / L, a = p % L;
-            const T v = c < L ? (T)ldexp(G[a * L + c], 1 - ex) : T(0);
+            const T v = (c < L && a <= c) ? (T)ldexp(F::to_double(G[packed_index(a, c, L)]), 1 - ex) : T(0);
             Mc[p] = v;
-            s2 = fma((double)v, (double)v, s2);
+            s2 += v * v;
         }
         s2 = warp_sum(s2);
         if (lane == 0) atomicAdd(&fro2, s2);
@@ -429,12 +563,12 @@ __global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, i
     // their own, so the sweep count is capped
     const T eps = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
     const T tol = T(4) * eps;
-    const T tiny = eps * eps * (T)fro2;
+    const T tiny = eps * eps * fro2;
     for (int sweep = 0; sweep < 20; ++sweep) {
         int n;
         if (L <= 32) n = jacobi_sweep<T, 8>(Mc, L, Lp, tol, tiny, &nrot);
         else if (L <= 64) n = jacobi_sweep<T, 16>(Mc, L, Lp, tol, tiny, &nrot);
-        else n = jacobi_sweep<T, 32>(Mc, L, Lp, tol, tiny, &nrot);
+        else n = jacobi_sweep<T, 32>(Mc, L, Lp, tol, tiny, &nrot);     // L <= 128
         if (n == 0) break;
     }
     // singular values (column norms), decreasing order, lower index first on ties
@@ -443,10 +577,9 @@ __global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, i
         for (int r = lane; r < L; r += 32) s.add(Mc[c * L + r], Mc[c * L + r]);
         s.reduce();
         if (lane == 0) {
-            const double ss = s.value();
-            const double y = ss > 0.0 ? rsqrt_fp64(ss) : 0.0;
-            inrm[c] = y;
-            sig[c] = (T)(ss * y);
+            const T sg = sqrt((T)s.value());
+            sig[c] = sg;
+            inrm[c] = sg > T(0) ? T(1) / sg : T(0);
         }
     }
     __syncthreads();
@@ -456,195 +589,330 @@ __global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, i
         perm[rank] = c;
     }
     __syncthreads();
-    const double smax = (double)sig[perm[0]];
-    const double weak = 64.0 * (double)eps * smax;
-    // U_M: rotated columns in decreasing order, normalised (FP64)
+    const T weak = T(64) * eps * sig[perm[0]];
+    // U_M: rotated columns in decreasing order, normalised
     for (int p = tid; p < L * R; p += kXT) {
         const int r = p / L, a = p % L;
         const int c = perm[r];
-        UM[p] = (double)Mc[c * L + a] * inrm[c];
+        UM[p] = Mc[c * L + a] * inrm[c];
     }
-    if (tid == 0) deg = 0;
     __syncthreads();
-    // rounding-level columns: two Gram-Schmidt passes against every earlier column
+    // rounding-level columns: classical Gram-Schmidt against every earlier
+    // column, twice (coefficients one warp each, then one update per entry)
     for (int r = 0; r < R; ++r) {
-        if (!((double)sig[perm[r]] <= weak)) continue;
-        double* u = UM + (size_t)r * L;
+        if (!(sig[perm[r]] <= weak)) continue;
+        T* u = UM + (size_t)r * L;
         for (int pass = 0; pass < 2; ++pass) {
-            for (int j = 0; j < r; ++j) {
-                const double* v = UM + (size_t)j * L;
-                double s = 0.0;
-                for (int a = tid; a < L; a += kXT) s = fma(v[a], u[a], s);
-                s = warp_sum(s);
-                if (lane == 0) red[warp] = s;
-                __syncthreads();
-                if (tid == 0) {
-                    double t = 0.0;
-                    for (int w = 0; w < nwarps; ++w) t += red[w];
-                    bcast = t;
-                }
-                __syncthreads();
-                const double d = bcast;
-                for (int a = tid; a < L; a += kXT) u[a] -= d * v[a];
-                __syncthreads();
+            for (int j = warp; j < r; j += nwarps) {
+                const T* v = UM + (size_t)j * L;
+                DotAcc<T> s;
+                for (int a = lane; a < L; a += 32) s.add(v[a], u[a]);
+                s.reduce();
+                if (lane == 0) dots[j] = (T)s.value();
             }
+            __syncthreads();
+            for (int a = tid; a < L; a += kXT) {
+                T acc = u[a];
+                for (int j = 0; j < r; ++j) acc -= dots[j] * UM[(size_t)j * L + a];
+                u[a] = acc;
+            }
+            __syncthreads();
         }
-        double s = 0.0;
-        for (int a = tid; a < L; a += kXT) s = fma(u[a], u[a], s);
-        s = warp_sum(s);
-        if (lane == 0) red[warp] = s;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < nwarps; ++w) t += red[w];
-            bcast = t;
+        if (warp == 0) {
+            DotAcc<T> s;
+            for (int a = lane; a < L; a += 32) s.add(u[a], u[a]);
+            s.reduce();
+            if (lane == 0) nrm2 = (T)s.value();
         }
         __syncthreads();
-        const double n2 = bcast;
-        const bool ok = n2 > 1e-6;                     // else the sketch has no direction left here
-        const double f = ok ? rsqrt_fp64(n2) : 0.0;
+        const T n2 = nrm2;
+        const bool ok = n2 > T(1e-6);                  // else the sketch has no direction left here
+        const T f = ok ? T(1) / sqrt(n2) : T(0);
         for (int a = tid; a < L; a += kXT) u[a] *= f;
-        if (tid == 0 && !ok) deg = 1;
         __syncthreads();
     }
-    // W(:, r) = R2^-1 U_M(:, r): back-substitution in FP64, one warp per column
-    double* w = wb + warp * L;
-    for (int r = warp; r < R; r += nwarps) {
-        const double* u = UM + (size_t)r * L;
+    // W(:, r) = R2^-1 U_M(:, r): back-substitution, one thread per column (row l
+    // of R2 is contiguous in the packed layout)
+    for (int r = tid; r < R; r += kXT) {
+        const T* u = UM + (size_t)r * L;
+        S* w = Wout + (size_t)r * L;
         for (int l = L - 1; l >= 0; --l) {
-            double s = 0.0;
-            for (int k = l + 1 + lane; k < L; k += 32) s = fma(Rf[l * L + k], w[k], s);
-            s = warp_sum(s);
-            if (lane == 0) w[l] = (u[l] - s) * dinv[l];
-            __syncwarp();
+            const S* row = Rf + packed_index(l, l, L) - l;      // row[k] = R2_lk
+            S a0 = F::zero(), a1 = F::zero(), a2 = F::zero(), a3 = F::zero();
+            int k = l + 1;
+            for (; k + 3 < L; k += 4) {
+                a0 = F::fma(row[k], w[k], a0);
+                a1 = F::fma(row[k + 1], w[k + 1], a1);
+                a2 = F::fma(row[k + 2], w[k + 2], a2);
+                a3 = F::fma(row[k + 3], w[k + 3], a3);
+            }
+            for (; k < L; ++k) a0 = F::fma(row[k], w[k], a0);
+            w[l] = (to_s<S>(u[l]) - ((a0 + a1) + (a2 + a3))) * dinv[l];
         }
-        for (int l = lane; l < L; l += 32) Wout[(int64_t)r * L + l] = w[l];
-        __syncwarp();
     }
-    if (tid == 0) *flag = deg ? kDegenerate : 0;
 }
 
-// U(:, r) = X W(:, r) in paired precision, then the sign rule. One CTA per column.
+// U(:, r) = X W(:, r) in paired precision, one thread per entry of U.
 template <typename T>
-__global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ X, int64_t I, int L,
-                                                    const double* __restrict__ W, T* __restrict__ U) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* whi = reinterpret_cast<T*>(smem_raw);  // [L]
-    T* wlo = whi + L;                         // [L]
-    T* col = wlo + L;                         // [I]
-    __shared__ T best_v[kT / 32];
-    __shared__ int64_t best_i[kT / 32];
-    __shared__ T sgn;
-    const int r = blockIdx.x;
-    for (int c = threadIdx.x; c < L; c += kT) {
-        const double w = W[(int64_t)r * L + c];
-        whi[c] = (T)w;
-        wlo[c] = (T)(w - (double)whi[c]);
-    }
-    __syncthreads();
-    T bv = T(-1);
-    int64_t bi = 0;
-    for (int64_t i = threadIdx.x; i < I; i += kT) {
+__global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ X, int64_t I, int L, int R,
+                                                    const typename SmallScalar<T>::type* __restrict__ W,
+                                                    T* __restrict__ U) {
+    const int64_t n = I * R;
+    for (int64_t e = (int64_t)blockIdx.x * kT + threadIdx.x; e < n; e += (int64_t)gridDim.x * kT) {
+        const int r = (int)(e / I);
+        const int64_t i = e - (int64_t)r * I;
+        const auto* w = W + (int64_t)r * L;
         DotAcc<T> s;
         for (int c = 0; c < L; ++c) {
             const T x = X[(int64_t)c * I + i];
-            s.add(x, whi[c]);
-            s.add(x, wlo[c]);
+            if constexpr (sizeof(T) == 4) {
+                s.add(x, w[c].hi);
+                s.add(x, w[c].lo);
+            } else {
+                s.add(x, w[c]);
+            }
         }
-        const T v = (T)s.value();
-        col[i] = v;
-        const T a = fabs(v);
-        if (a > bv) { bv = a; bi = i; }
+        U[e] = (T)s.value();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    if ((threadIdx.x & 31) == 0) { best_v[threadIdx.x >> 5] = bv; best_i[threadIdx.x >> 5] = bi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        T v = best_v[0];
-        int64_t k = best_i[0];
-        for (int w = 1; w < kT / 32; ++w)
-            if (best_v[w] > v || (best_v[w] == v && best_i[w] < k)) { v = best_v[w]; k = best_i[w]; }
-        sgn = col[k] < T(0) ? T(-1) : T(1);
-    }
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < I; i += kT) U[(int64_t)r * I + i] = sgn * col[i];
 }
 
-// Columns whose singular value is at rounding level: the first unit vector e_k
-// (k increasing) that keeps a long residual after two Gram-Schmidt passes
-// against every valid column, normalised and sign-fixed. The squared residuals
-// of e_0 .. e_{I-1} average (I - d) / I for d valid columns, so accepting one
-// above half that average always succeeds. Runs only when flagged.
+constexpr int kFRows = 64;               // rows of U staged per step of the final Gram
+
+struct FLayout {
+    size_t g, w, rt, dinv, valid, xs, total;
+};
+__host__ __device__ inline FLayout flayout(int R, int elem) {
+    const size_t np = packed_size(R);
+    FLayout f;
+    f.g = 0;                                              // packed Gram (as Pair sums), then R^-1
+    f.w = up16(8 * np);                                   // packed Cholesky factor
+    f.rt = f.w + up16(8 * np);                            // transposed factor
+    f.dinv = f.rt + up16(8 * np);
+    f.valid = f.dinv + up16((size_t)8 * R);
+    f.xs = f.valid + up16(sizeof(int) * (size_t)R);
+    f.total = f.xs + up16((size_t)elem * kFRows * R);
+    return f;
+}
+
+// Final pass over U (I x R, column-major), one CTA:
+//   1. Gram U^T U in paired precision. If it is within 8 eps of I, U is kept.
+//   2. Otherwise Cholesky U^T U = R_U^T R_U, dropping every column whose
+//      remaining squared norm is below 1/4 of its own (it lies mostly in the
+//      span of the earlier columns, or is zero), and U <- U R_U^-1 in place:
+//      column r mixes with earlier columns only, so the span of the first k
+//      columns is unchanged for every k. This restores orthonormality where
+//      the sketch was numerically rank-deficient and CholeskyQR could not.
+//   3. Sign rule: each column's largest-magnitude entry positive (lowest row on ties).
+//   4. Dropped columns: the first unit vector e_k (k increasing) that keeps a long
+//      residual after two Gram-Schmidt passes against every valid column. The
+//      squared residuals of e_0 .. e_{I-1} average (I - d) / I for d valid
+//      columns, so accepting one above half that average always succeeds.
 template <typename T>
-__global__ void __launch_bounds__(kT) complete_kernel(int64_t I, int L, int R, const double* __restrict__ W,
-                                                      T* __restrict__ U, const int* flag) {
-    if (!(*flag & kDegenerate)) return;
+__global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I, int R) {
+    using S = typename SmallScalar<T>::type;
+    using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* v = reinterpret_cast<double*>(smem_raw);   // [I]
-    int* valid = reinterpret_cast<int*>(v + I);        // [R]
+    const FLayout lay = flayout(R, sizeof(T));
+    Pair* GP = reinterpret_cast<Pair*>(smem_raw + lay.g);
+    S* Ri = reinterpret_cast<S*>(smem_raw + lay.g);
+    S* W = reinterpret_cast<S*>(smem_raw + lay.w);
+    S* RT = reinterpret_cast<S*>(smem_raw + lay.rt);
+    S* dinv = reinterpret_cast<S*>(smem_raw + lay.dinv);
+    int* valid = reinterpret_cast<int*>(smem_raw + lay.valid);
+    T* xs = reinterpret_cast<T*>(smem_raw + lay.xs);     // [kFRows][R]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kT / 32;
+    const int np = (int)packed_size(R);
+    __shared__ int offdiag;
     __shared__ double red[kT / 32];
     __shared__ double bcast;
-    __shared__ double bv;
-    __shared__ int64_t bi;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int r = tid; r < R; r += kT) {
-        int nz = 0;
-        for (int c = 0; c < L; ++c) nz |= W[(int64_t)r * L + c] != 0.0;
-        valid[r] = nz;
+    __shared__ T bvs[kT / 32];
+    __shared__ int64_t bis[kT / 32];
+
+    // 1. Gram (FP32 data: Pair sums; FP64 data: the Pair slots hold one double)
+    double* GD = reinterpret_cast<double*>(smem_raw + lay.g);
+    for (int p = tid; p < np; p += kT) {
+        if constexpr (sizeof(T) == 4) GP[p] = Pair{0.f, 0.f};
+        else GD[p] = 0.0;
+    }
+    if (tid == 0) offdiag = 0;
+    for (int64_t r0 = 0; r0 < I; r0 += kFRows) {
+        const int nr = (int)min((int64_t)kFRows, I - r0);
+        __syncthreads();
+        for (int e = tid; e < nr * R; e += kT) {
+            const int r = e % nr, c = e / nr;
+            xs[r * R + c] = U[(int64_t)c * I + r0 + r];
+        }
+        __syncthreads();
+        for (int p = tid; p < np; p += kT) {
+            int a = 0, rem = p;
+            while (rem >= R - a) { rem -= R - a; ++a; }
+            const int b = a + rem;
+            if constexpr (sizeof(T) == 4) {
+                Pair acc = GP[p];
+                for (int r = 0; r < nr; ++r) pair_add_prod(acc, xs[r * R + a], xs[r * R + b]);
+                GP[p] = acc;
+            } else {
+                double acc = GD[p];
+                for (int r = 0; r < nr; ++r) acc = fma(xs[r * R + a], xs[r * R + b], acc);
+                GD[p] = acc;
+            }
+        }
     }
     __syncthreads();
+    const double eps = sizeof(T) == 4 ? (double)FLT_EPSILON : DBL_EPSILON;
+    for (int p = tid; p < np; p += kT) {
+        int a = 0, rem = p;
+        while (rem >= R - a) { rem -= R - a; ++a; }
+        S g;
+        if constexpr (sizeof(T) == 4) g = two_sum(GP[p].hi, GP[p].lo);
+        else g = GD[p];
+        W[p] = g;
+        const double dev = fabs(F::to_double(g) - (rem == 0 ? 1.0 : 0.0));
+        if (!(dev <= 8.0 * eps)) offdiag = 1;
+    }
+    for (int k = tid; k < R; k += kT) valid[k] = 1;
+    __syncthreads();
+
+    if (offdiag) {
+        // 2. Cholesky with column dropping (G kept in RT for the reference norms)
+        for (int p = tid; p < np; p += kT) RT[p] = W[p];
+        __syncthreads();
+        for (int k = 0; k < R; ++k) {
+            if (tid == 0) {
+                const int kk = packed_index(k, k, R);
+                const S d = W[kk];
+                const bool keep = F::gt(d, RT[kk] * F::from_double(0.25)) && F::finite(d);
+                valid[k] = keep;
+                if (keep) {
+                    const S y = F::rsqrt(d);
+                    W[kk] = d * y;
+                    dinv[k] = y;
+                } else {
+                    W[kk] = F::one();
+                    dinv[k] = F::one();
+                }
+            }
+            __syncthreads();
+            const int kk = packed_index(k, k, R);
+            if (!valid[k]) {
+                for (int j = k + 1 + tid; j < R; j += kT) W[kk + (j - k)] = F::zero();
+                __syncthreads();
+                continue;
+            }
+            const S y = dinv[k];
+            for (int j = k + 1 + tid; j < R; j += kT) W[kk + (j - k)] = W[kk + (j - k)] * y;
+            __syncthreads();
+            for (int i = k + 1 + warp; i < R; i += nw) {
+                const S cki = W[kk + (i - k)];
+                S* ri = W + packed_index(i, i, R);
+                for (int j = i + lane; j < R; j += 32) ri[j - i] = ri[j - i] - cki * W[kk + (j - k)];
+            }
+            __syncthreads();
+        }
+        upper_inverse<S>(W, dinv, R, RT, Ri);
+        // U <- U R_U^-1, one thread per row, columns from the last (in place)
+        for (int64_t i = tid; i < I; i += kT) {
+            for (int l = R - 1; l >= 0; --l) {
+                T v = T(0);
+                if (valid[l]) {
+                    DotAcc<T> acc;
+                    for (int m = 0; m <= l; ++m) {
+                        const S w = Ri[packed_index(m, l, R)];
+                        const T x = U[(int64_t)m * I + i];
+                        if constexpr (sizeof(T) == 4) {
+                            acc.add(x, w.hi);
+                            acc.add(x, w.lo);
+                        } else {
+                            acc.add(x, w);
+                        }
+                    }
+                    v = (T)acc.value();
+                }
+                U[(int64_t)l * I + i] = v;
+            }
+        }
+        __syncthreads();
+    }
+
+    // 3. sign rule, one warp per column
+    for (int r = warp; r < R; r += nw) {
+        if (!valid[r]) continue;
+        T bv = T(-1);
+        int64_t bi = 0;
+        for (int64_t i = lane; i < I; i += 32) {
+            const T a = fabs(U[(int64_t)r * I + i]);
+            if (a > bv) { bv = a; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (U[(int64_t)r * I + bi] < T(0))
+            for (int64_t i = lane; i < I; i += 32) U[(int64_t)r * I + i] = -U[(int64_t)r * I + i];
+    }
+    __syncthreads();
+
+    // 4. completion of dropped columns (the residual is formed in U's own column)
     int nvalid = 0;
     for (int r = 0; r < R; ++r) nvalid += valid[r];
     int64_t k = 0;
     for (int r = 0; r < R; ++r) {
         if (valid[r]) continue;
-        const double accept = 0.5 * (double)(I - nvalid) / (double)I;
+        T* v = U + (int64_t)r * I;
         for (; k < I; ++k) {
-            for (int64_t i = tid; i < I; i += kT) v[i] = (i == k) ? 1.0 : 0.0;
+            for (int64_t i = tid; i < I; i += kT) v[i] = (i == k) ? T(1) : T(0);
             __syncthreads();
             for (int pass = 0; pass < 2; ++pass) {
                 for (int j = 0; j < R; ++j) {
                     if (!valid[j]) continue;
                     double s = 0.0;
-                    for (int64_t i = tid; i < I; i += kT) s = fma((double)U[(int64_t)j * I + i], v[i], s);
+                    for (int64_t i = tid; i < I; i += kT) s = fma((double)U[(int64_t)j * I + i], (double)v[i], s);
                     s = warp_sum(s);
                     if (lane == 0) red[warp] = s;
                     __syncthreads();
                     if (tid == 0) {
                         double t = 0.0;
-                        for (int w = 0; w < kT / 32; ++w) t += red[w];
+                        for (int w = 0; w < nw; ++w) t += red[w];
                         bcast = t;
                     }
                     __syncthreads();
                     const double d = bcast;
-                    for (int64_t i = tid; i < I; i += kT) v[i] -= d * (double)U[(int64_t)j * I + i];
+                    for (int64_t i = tid; i < I; i += kT) v[i] = (T)((double)v[i] - d * (double)U[(int64_t)j * I + i]);
                     __syncthreads();
                 }
             }
             double s = 0.0;
-            for (int64_t i = tid; i < I; i += kT) s = fma(v[i], v[i], s);
+            T bv = T(-1);
+            int64_t bi = 0;
+            for (int64_t i = tid; i < I; i += kT) {
+                s = fma((double)v[i], (double)v[i], s);
+                if (fabs(v[i]) > bv) { bv = fabs(v[i]); bi = i; }
+            }
             s = warp_sum(s);
-            if (lane == 0) red[warp] = s;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if (lane == 0) { red[warp] = s; bvs[warp] = bv; bis[warp] = bi; }
             __syncthreads();
             if (tid == 0) {
                 double t = 0.0;
-                for (int w = 0; w < kT / 32; ++w) t += red[w];
-                bcast = sqrt(t);
-                bv = -1.0;
-                bi = 0;
-                for (int64_t i = 0; i < I; ++i)
-                    if (fabs(v[i]) > bv) { bv = fabs(v[i]); bi = i; }
+                T b = bvs[0];
+                int64_t ii = bis[0];
+                for (int w = 0; w < nw; ++w) {
+                    t += red[w];
+                    if (bvs[w] > b || (bvs[w] == b && bis[w] < ii)) { b = bvs[w]; ii = bis[w]; }
+                }
+                bcast = t > 0.5 * (double)(I - nvalid) / (double)I ? (v[ii] < T(0) ? -1.0 : 1.0) / sqrt(t) : 0.0;
             }
             __syncthreads();
-            const double nrm = bcast;
-            if (nrm * nrm > accept) {
-                const double f = (v[bi] < 0 ? -1.0 : 1.0) / nrm;
-                for (int64_t i = tid; i < I; i += kT) U[(int64_t)r * I + i] = (T)(v[i] * f);
+            const double f = bcast;
+            if (f != 0.0) {
+                for (int64_t i = tid; i < I; i += kT) v[i] = (T)((double)v[i] * f);
                 __syncthreads();
                 if (tid == 0) valid[r] = 1;
                 __syncthreads();
@@ -663,13 +931,13 @@ OrthPlan orth_plan(int64_t I, int L, int num_sms) {
     OrthPlan p{};
     p.I = I;
     p.L = L;
-    // enough CTAs to spread the paired-precision Gram work, few enough that the
-    // last CTA's reduction of the packed partials stays small (<= 512 KB)
-    const int64_t np = (int64_t)L * (L + 1) / 2;
+    // at least kGramRows rows per CTA (few partials for the serial reduction),
+    // and the packed partials within 512 KB
+    const int64_t np = (int64_t)packed_size(L);
     int64_t cap = (512 * 1024) / (np * 8);
     if (cap < 1) cap = 1;
     if (cap > num_sms) cap = num_sms;
-    int64_t blocks = (I + 7) / 8;
+    int64_t blocks = (I + kGramRows - 1) / kGramRows;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     p.gram_blocks = (int)blocks;
@@ -678,87 +946,99 @@ OrthPlan orth_plan(int64_t I, int L, int num_sms) {
 
 static int gram_rows(const OrthPlan& p) { return (int)((p.I + p.gram_blocks - 1) / p.gram_blocks); }
 
+// Largest dynamic shared memory any orthonormalisation kernel may take.
+static constexpr size_t kSmemCap = 220 * 1024;
+
+static size_t gram_chol_smem(const OrthPlan& p, int elem) {
+    const size_t np = packed_size(p.L);
+    return std::max((size_t)elem * (size_t)gram_rows(p) * p.L, 8 * (3 * np + (size_t)p.L));
+}
+static size_t extract_smem(const OrthPlan& p, int R, int elem) {
+    return std::max(xlayout(p.L, R, elem).total, (size_t)elem * (size_t)gram_rows(p) * p.L);
+}
+static size_t finish_smem(int R, int elem) { return flayout(R, elem).total; }
+
+bool orth_supported(const OrthPlan& p, int R, int elem) {
+    return gram_chol_smem(p, elem) <= kSmemCap && extract_smem(p, R, elem) <= kSmemCap &&
+           8 * packed_size(p.L) <= kSmemCap && finish_smem(R, elem) <= kSmemCap;
+}
+
 size_t orth_scratch_bytes(const OrthPlan& p, int elem_size) {
     (void)elem_size;
-    const size_t np = (size_t)p.L * (p.L + 1) / 2;
+    const size_t np = packed_size(p.L);
     const size_t LL = (size_t)p.L * p.L;
-    return ((sizeof(double) * np * (size_t)p.gram_blocks + 255) & ~size_t(255)) + 256 + sizeof(double) * LL + 512;
+    return ((8 * np * (size_t)p.gram_blocks + 255) & ~size_t(255)) + 256 + 8 * LL + 512;
 }
 
 struct OrthScratch {
-    double* partial;
+    void* partial;
     int* flag;
     unsigned* ticket;
-    double* W;
+    void* W;       // R^-1 of a CholeskyQR pass (packed), then the extraction's W (L x R)
 };
 static OrthScratch carve(const OrthPlan& p, void* scratch) {
     OrthScratch s;
     char* b = reinterpret_cast<char*>(scratch);
-    const size_t np = (size_t)p.L * (p.L + 1) / 2;
-    s.partial = reinterpret_cast<double*>(b);
-    b += ((sizeof(double) * np * (size_t)p.gram_blocks) + 255) & ~size_t(255);
+    const size_t np = packed_size(p.L);
+    s.partial = b;
+    b += (8 * np * (size_t)p.gram_blocks + 255) & ~size_t(255);
     s.flag = reinterpret_cast<int*>(b);
     s.ticket = reinterpret_cast<unsigned*>(b + 64);
     b += 256;
-    s.W = reinterpret_cast<double*>(b);
+    s.W = b;
     return s;
 }
 
 template <typename T>
 cudaError_t launch_cholqr(const T* X, T* Q, const OrthPlan& p, double* factor, void* scratch, int* status,
                           cudaStream_t s) {
+    using S = typename SmallScalar<T>::type;
+    static_assert(sizeof(S) == sizeof(double), "factor slots hold one double per entry");
     OrthScratch sc = carve(p, scratch);
     const int L = p.L;
-    const size_t LL = (size_t)L * L;
     const int rows = gram_rows(p);
-    const size_t gsm = std::max(sizeof(T) * (size_t)rows * L, sizeof(double) * (2 * LL + L));
-    const size_t asm_ = sizeof(double) * LL;
-    if (asm_ > 220 * 1024 || gsm > 220 * 1024) return cudaErrorInvalidValue;
+    const size_t gsm = gram_chol_smem(p, sizeof(T));
+    const size_t asm_ = 8 * packed_size(L);
+    if (asm_ > kSmemCap || gsm > kSmemCap) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(gram_chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
     cudaFuncSetAttribute(apply_rinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_);
     cudaMemsetAsync(sc.flag, 0, 128, s);                 // flag and ticket
     int64_t ablocks = (p.I * L + kT - 1) / kT;
     if (ablocks > 4 * 1024) ablocks = 4 * 1024;
     // R^-1 goes to the W block, which the extraction writes only after this pass
-    gram_chol_kernel<T><<<p.gram_blocks, kT, gsm, s>>>(X, p.I, L, rows, sc.partial, sc.ticket, factor, sc.W, status);
+    gram_chol_kernel<T><<<p.gram_blocks, kT, gsm, s>>>(X, p.I, L, rows, (S*)sc.partial, sc.ticket, (S*)factor,
+                                                        (S*)sc.W, status);
     note_launch();
-    apply_rinv_kernel<T><<<(unsigned)ablocks, kT, asm_, s>>>(X, p.I, L, sc.W, Q);
+    apply_rinv_kernel<T><<<(unsigned)ablocks, kT, asm_, s>>>(X, p.I, L, (const S*)sc.W, Q);
     note_launch();
     return cudaGetLastError();
-}
-
-static size_t extract_smem_bytes(int L, int R, int elem, int rows) {
-    const int Lp = L + (L & 1);
-    const size_t last = sizeof(double) * (2 * (size_t)L * L + (size_t)R * L + (size_t)(kXT / 32) * L + L + Lp) +
-                        (size_t)elem * ((size_t)Lp * L + Lp) + sizeof(int) * Lp + 64;
-    return std::max(last, (size_t)elem * (size_t)rows * L);
 }
 
 template <typename T>
 cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors, int nprev, int R, T* U,
                            void* scratch, int* status, cudaStream_t s) {
+    using S = typename SmallScalar<T>::type;
     // X = Q1 R1 (R1 stored after the earlier factors), then C = Q1 (R1 F)
-    cudaError_t e = launch_cholqr<T>(X, Q1, p, factors + (size_t)nprev * p.L * p.L, scratch, status, s);
+    const size_t slot = (size_t)p.L * p.L;                 // factor slots hold L^2 doubles
+    cudaError_t e = launch_cholqr<T>(X, Q1, p, factors + (size_t)nprev * slot, scratch, status, s);
     if (e != cudaSuccess) return e;
+    if (!orth_supported(p, R, sizeof(T))) return cudaErrorInvalidValue;
     OrthScratch sc = carve(p, scratch);
     const int L = p.L;
     const int rows = gram_rows(p);
-    const size_t xsm = extract_smem_bytes(L, R, sizeof(T), rows);
-    if (xsm > 220 * 1024 || L > kXT * kMaxPerThread) return cudaErrorInvalidValue;
+    const size_t xsm = extract_smem(p, R, sizeof(T));
     cudaFuncSetAttribute(extract_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
     cudaMemsetAsync(sc.flag, 0, 128, s);
-    extract_kernel<T><<<p.gram_blocks, kXT, xsm, s>>>(Q1, p.I, L, rows, sc.partial, sc.ticket, factors, nprev + 1, R,
-                                                      sc.W, sc.flag, status);
+    extract_kernel<T><<<p.gram_blocks, kXT, xsm, s>>>(Q1, p.I, L, rows, (S*)sc.partial, sc.ticket,
+                                                      (const S*)factors, slot, nprev + 1, R, (S*)sc.W, status);
     note_launch();
-    const size_t fsm = sizeof(T) * (2 * (size_t)L + (size_t)p.I) + 64;
-    if (fsm > 220 * 1024) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(form_u_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-    form_u_kernel<T><<<R, kT, fsm, s>>>(Q1, p.I, L, sc.W, U);
+    int64_t ublocks = (p.I * R + kT - 1) / kT;
+    if (ublocks > 4 * 1024) ublocks = 4 * 1024;
+    form_u_kernel<T><<<(unsigned)ublocks, kT, 0, s>>>(Q1, p.I, L, R, (const S*)sc.W, U);
     note_launch();
-    const size_t csm = sizeof(double) * (size_t)p.I + sizeof(int) * (size_t)R + 64;
-    if (csm > 220 * 1024) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(complete_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
-    complete_kernel<T><<<1, kT, csm, s>>>(p.I, L, R, sc.W, U, sc.flag);
+    const size_t fsm = finish_smem(R, sizeof(T));
+    cudaFuncSetAttribute(finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    finish_kernel<T><<<1, kT, fsm, s>>>(U, p.I, R);
     note_launch();
     return cudaGetLastError();
 }

@@ -141,3 +141,22 @@ def test_caller_workspace_and_stream(tk):
     for a, b in zip(U1, U2):
         assert torch.equal(a, b)                       # deterministic: fixed-order reductions
     assert torch.equal(G1, G2)
+
+
+@pytest.mark.parametrize("which", ["ST", "T"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_rank_deficient_sketch_stays_orthonormal(tk, which, prec):
+    # The 400^3 Hilbert tensor's mode-n singular values fall by orders of
+    # magnitude per index, so with q = 2 the sketch (A A^T)^2 Omega of L = 30
+    # columns is numerically rank-deficient in FP32: CholeskyQR alone cannot
+    # orthonormalise its weak directions. Every factor must still have
+    # orthonormal columns (bar: 10 R eps_32 in Frobenius norm), and the error
+    # stays at the level the oracle reaches (its FP64 RE is 9.2e-5).
+    dims, ranks = (400, 400, 400), (20, 20, 20)
+    A = flat_dev(synth.hilbert(dims))
+    U, G = tk.decompose(which, A, dims, ranks, P=10, q=2, seed=0, prec=prec)
+    for u in U:
+        ud = u.double()
+        dev = torch.linalg.norm(ud.t() @ ud - torch.eye(u.shape[1], dtype=torch.float64, device="cuda"))
+        assert float(dev) < 10 * u.shape[1] * 1.19e-7
+    assert tk.relative_error(A, dims, ranks, U, G) < 2e-3
