@@ -45,7 +45,7 @@ VARIANTS = [
 ]
 BASELINE_METRIC = "decomps/s & sketch HBM GB/s, BF16 vs FP32 at equal rel err; serving p50/p99 ms"
 WORKLOAD = ("randomized ST-HOSVD, 400x400x400 FP32 (Tucker core 20^3 + 1e-2 noise, and Hilbert), "
-            "R=20 P=10, batch of 4: q=1; q=1 AMM c=4000 nearly-optimal; Hilbert q=2; Hilbert q=1 AMM c=4000 uniform")
+            "R=20 P=10, variants: q=1; q=1 AMM c=4000 nearly-optimal; Hilbert q=2; Hilbert q=1 AMM c=4000 uniform")
 
 
 def tensors():
@@ -183,6 +183,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="both", choices=["both", "bf16", "fp32"],
                     help="sketch arithmetic to time (both: bf16 is the headline when its RE matches)")
+    ap.add_argument("--copies", type=int, default=8,
+                    help="decompositions of each variant in flight per step (each on its own stream)")
     ap.add_argument("--single", default=None, choices=[v["name"] for v in VARIANTS],
                     help="run one decomposition of one variant after one warm-up and exit (profiling case)")
     args = ap.parse_args()
@@ -215,7 +217,8 @@ def main():
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
     main_s = torch.cuda.Stream()
-    side = [torch.cuda.Stream() for _ in VARIANTS]
+    batch = [v for v in VARIANTS for _ in range(args.copies)]
+    side = [torch.cuda.Stream() for _ in batch]
 
     def barrier():
         torch.cuda.synchronize()
@@ -238,14 +241,14 @@ def main():
         # one stream, workspace and output set per variant: the four decompositions of
         # a step run concurrently (fork from the main stream, join back into it)
         wss = [torch.empty(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"], prec=prec),
-                           dtype=torch.uint8, device="cuda") for v in VARIANTS]
+                           dtype=torch.uint8, device="cuda") for v in batch]
         outs = [([tk.factor_tensor(I, R, torch.float32, "cuda") for I, R in zip(DIMS, RANKS)],
-                 torch.empty(int(np.prod(RANKS)), dtype=torch.float32, device="cuda")) for _ in VARIANTS]
+                 torch.empty(int(np.prod(RANKS)), dtype=torch.float32, device="cuda")) for _ in batch]
 
         def enqueue_step():
             for st in side:
                 st.wait_stream(main_s)
-            for v, st, ws, out in zip(VARIANTS, side, wss, outs):
+            for v, st, ws, out in zip(batch, side, wss, outs):
                 tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
                             workspace=ws, stream=st, out=out, flags=tk.FLAG_ASYNC, prec=prec)
             for st in side:
@@ -307,7 +310,7 @@ def main():
         prof = {k: tk.profile_read(k) for k in ("power", "ttm", "gather", "norms", "extract", "sample")}
         tk.profile_enable(False)
         del graph
-        return {"prec": prec, "ms": ms, "value": len(VARIANTS) * args.steps * world / (ms / 1e3),
+        return {"prec": prec, "ms": ms, "value": len(batch) * args.steps * world / (ms / 1e3),
                 "gpu_launches": (n1 - n0) if n1 - n0 > 0 else per_step * args.steps,
                 "graph": True, "rel_error": res, "prof": prof}
 
@@ -405,7 +408,8 @@ def main():
                        "sketch": f"paper form, {head['prec']} power steps "
                                  + ("(tcgen05 tensor cores, fp32 accumulate)" if head["prec"] == "bf16"
                                     else "(FP32 FFMA)"),
-                       "execution": "CUDA graph of one step, 4 decompositions on 4 streams"},
+                       "execution": f"CUDA graph of one step: {len(batch)} decompositions ({args.copies} of each "
+                                    f"variant, inputs shared read-only) on {len(batch)} streams"},
             "e2e": e2e, "gpu_launches": head["gpu_launches"], "roofline": roofline, "kernels": kernels,
             "sketch_hbm_gbs": achieved_gbs,
             "forms": {p: {"value": f["value"], "ms_per_step": f["ms"] / args.steps, "rel_error": f["rel_error"]}

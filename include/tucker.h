@@ -79,7 +79,13 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  * after Algorithm 5), each column's largest-magnitude entry made positive. */
 typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1 } tucker_form;
 
-/* Arithmetic of the sketch / power products. FP32 = exact FP32 FMA. */
+/* Arithmetic of the sketch / power products.
+ *  FP32: exact FP32 FMA on the CUDA cores.
+ *  TF32: not built (TUCKER_ERR_UNSUPPORTED).
+ *  BF16: tcgen05 tensor cores with FP32 accumulation, split form: A and the
+ *    intermediate A^T X are each held as a bf16 high part plus a bf16 low part
+ *    (about 16 significant bits), so the sketch is of A itself; A is still read
+ *    once, in FP32. Used where I_n <= 512 and L_n <= 64; other modes run FP32. */
 typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2 } tucker_sketch_prec;
 
 #define TUCKER_FLAG_ASYNC 0x1u

@@ -1,13 +1,25 @@
 // Power step of Strategy A on the 5th-generation tensor cores (tcgen05, BF16
 // operands, FP32 accumulation in tensor memory): X_out = A_(n) (A_(n)^T X_in).
 //
-// Each CTA streams tiles of 128 mode-n fibers. A tile T (128 fibers x I_n) is
-// converted to bf16 into ONE shared-memory buffer in the no-swizzle
-// core-matrix layout, which serves both products:
-//   W    = T X     (M = 128 fibers, N = L, K = I_n)      accumulator in TMEM
-//   Xacc += T^T W  (M = 128 rows of I_n per block, K = 128 fibers)
-// For contiguous fibers (mode 1) the buffer is K-major for the first product
+// Split-BF16 arithmetic: each FP32 entry a of A is held as a_hi + a_lo with
+// a_hi = bf16(a) and a_lo = bf16(a - a_hi), which represents a to about 2^-17
+// relative, and the FP32 product W = T^T X is split the same way. The products
+//   W    = T_hi X + T_lo X
+//   Xacc += T_hi W_hi + T_lo W_hi + T_hi W_lo          (T_lo W_lo, ~2^-18, dropped)
+// therefore sketch A itself rather than its BF16 rounding (which alone would
+// set a relative-error floor near 1e-3), at the same HBM traffic: A is read
+// once, in FP32, and the extra tensor-core work stays far below the ridge.
+// X_in is rounded to bf16 once: that only replaces the starting block by a
+// nearby full-rank one, and the range of A A^T X is still a sketch of A.
+//
+// Each CTA streams tiles of 64 mode-n fibers. A tile T (64 fibers x I_n) is
+// converted into two shared-memory buffers (hi, lo) in the no-swizzle
+// core-matrix layout, which serve both products:
+//   W    = T X     (M = 64 fibers, N = L, K = I_n)       accumulator in TMEM
+//   Xacc += T^T W  (M = 128 rows of I_n per block, K = 64 fibers)
+// For contiguous fibers (mode 1) the buffers are K-major for the first product
 // and MN-major for the second; for strided fibers it is the other way round.
+// With M = 64, accumulator row m sits in TMEM lane (m % 16) + 32 (m / 16).
 // W travels TMEM -> registers -> bf16 shared memory to become the second
 // product's B operand. X_acc stays in TMEM across all tiles of the CTA and is
 // written once as the CTA's partial; partials are summed in a fixed order.
@@ -20,7 +32,7 @@ namespace tk {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr int kJB = 128;                 // fibers per tile
+constexpr int kJB = 64;                  // fibers per tile (M of the first product)
 // Descriptor convention for MN-major operands: LBO is the stride between core
 // matrices along K, SBO the stride along M/N (checked on the device).
 constexpr bool kMnLboIsK = true;
@@ -33,15 +45,17 @@ __device__ __forceinline__ uint32_t t_off(bool contig, int jj, int i, int ipt) {
                   : (uint32_t)((i >> 3) * (kJB >> 3) * 128 + (jj >> 3) * 128 + (i & 7) * 16 + (jj & 7) * 2);
 }
 
-__device__ __forceinline__ uint4 pack8(const float* x) {
-    uint4 u;
-    __nv_bfloat162 p0 = __floats2bfloat162_rn(x[0], x[1]), p1 = __floats2bfloat162_rn(x[2], x[3]);
-    __nv_bfloat162 p2 = __floats2bfloat162_rn(x[4], x[5]), p3 = __floats2bfloat162_rn(x[6], x[7]);
-    u.x = *reinterpret_cast<uint32_t*>(&p0);
-    u.y = *reinterpret_cast<uint32_t*>(&p1);
-    u.z = *reinterpret_cast<uint32_t*>(&p2);
-    u.w = *reinterpret_cast<uint32_t*>(&p3);
-    return u;
+__device__ __forceinline__ uint32_t bf2(float a, float b) {
+    __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&p);
+}
+// Eight FP32 values -> their bf16 high parts and bf16 low parts (x - hi).
+__device__ __forceinline__ void pack8_split(const float* x, uint4& hi, uint4& lo) {
+    float r[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] = x[k] - __bfloat162float(__float2bfloat16_rn(x[k]));
+    hi = make_uint4(bf2(x[0], x[1]), bf2(x[2], x[3]), bf2(x[4], x[5]), bf2(x[6], x[7]));
+    lo = make_uint4(bf2(r[0], r[1]), bf2(r[2], r[3]), bf2(r[4], r[5]), bf2(r[6], r[7]));
 }
 
 // Loads are issued in batches of kBatch chunks per thread before any of them is
@@ -51,7 +65,8 @@ constexpr int kBatch = 8;
 
 template <bool CONTIG>
 __device__ __forceinline__ void load_tile_bf16(const float* __restrict__ A, const ModeView& v, int64_t j0, int64_t J,
-                                               unsigned char* T, int ipt, const int64_t* bases, bool vec4) {
+                                               unsigned char* T, unsigned char* Tlo, int ipt, const int64_t* bases,
+                                               bool vec4) {
     const int I = (int)v.i;
     const int tid = threadIdx.x;
     if (CONTIG) {
@@ -85,7 +100,11 @@ __device__ __forceinline__ void load_tile_bf16(const float* __restrict__ A, cons
                 if (e < nchunks) {
                     const int jlo = e & 7, rest = e >> 3;
                     const int i8 = rest % n8, jj = (rest / n8) * 8 + jlo;
-                    *reinterpret_cast<uint4*>(T + t_off(true, jj, i8 * 8, ipt)) = pack8(x[u]);
+                    const uint32_t o = t_off(true, jj, i8 * 8, ipt);
+                    uint4 h, l;
+                    pack8_split(x[u], h, l);
+                    *reinterpret_cast<uint4*>(T + o) = h;
+                    *reinterpret_cast<uint4*>(Tlo + o) = l;
                 }
             }
         }
@@ -114,7 +133,11 @@ __device__ __forceinline__ void load_tile_bf16(const float* __restrict__ A, cons
                 if (e < nchunks) {
                     const int ilo = e & 7, rest = e >> 3;
                     const int j8 = rest % (kJB >> 3), i = (rest / (kJB >> 3)) * 8 + ilo;
-                    *reinterpret_cast<uint4*>(T + t_off(false, j8 * 8, i, ipt)) = pack8(x[u]);
+                    const uint32_t o = t_off(false, j8 * 8, i, ipt);
+                    uint4 h, l;
+                    pack8_split(x[u], h, l);
+                    *reinterpret_cast<uint4*>(T + o) = h;
+                    *reinterpret_cast<uint4*>(Tlo + o) = l;
                 }
             }
         }
@@ -131,13 +154,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) power_tc_kernel(const float* __
     const int nb = (I + 127) / 128;                 // 128-row blocks of I_n
     const int ipt = nb * 128;                       // padded I_n of the tile and X buffers
     const int64_t J = v.fibers();
-    unsigned char* T = smem;                                        // kJB x ipt bf16
-    unsigned char* Xs = T + (size_t)kJB * ipt * 2;                  // LP x ipt bf16
-    unsigned char* Ws = Xs + (size_t)LP * ipt * 2;                  // LP x kJB bf16
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(Ws + (size_t)LP * kJB * 2);   // [2]
+    unsigned char* T = smem;                                        // kJB x ipt bf16, high parts
+    unsigned char* Tlo = T + (size_t)kJB * ipt * 2;                 // kJB x ipt bf16, low parts
+    unsigned char* Xs = Tlo + (size_t)kJB * ipt * 2;                // LP x ipt bf16
+    unsigned char* Ws = Xs + (size_t)LP * ipt * 2;                  // LP x kJB bf16, high parts
+    unsigned char* Wlo = Ws + (size_t)LP * kJB * 2;                 // LP x kJB bf16, low parts
+    const size_t used = ((size_t)2 * kJB * ipt + (size_t)LP * ipt + (size_t)2 * LP * kJB) * 2;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + used);      // [2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
     int* flag = reinterpret_cast<int*>(tmem_slot + 1);
-    int64_t* bases = reinterpret_cast<int64_t*>(smem + (((size_t)kJB * ipt + (size_t)LP * ipt + (size_t)LP * kJB) * 2 + 64));
+    int64_t* bases = reinterpret_cast<int64_t*>(smem + used + 64);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, half = warp >> 2;
 
@@ -163,7 +189,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) power_tc_kernel(const float* __
     const uint32_t tmem = *tmem_slot;
 
     const uint32_t t_base = tc::smem_u32(T), x_base = tc::smem_u32(Xs), w_base = tc::smem_u32(Ws);
-    const uint32_t id1 = tc::idesc_bf16(128, LP, !CONTIG, false);
+    const uint32_t tlo_off = (uint32_t)(Tlo - T), wlo_off = (uint32_t)(Wlo - Ws);
+    const uint32_t id1 = tc::idesc_bf16(kJB, LP, !CONTIG, false);
     const uint32_t id2 = tc::idesc_bf16(128, LP, CONTIG, false);
     const uint32_t kdir_t = CONTIG ? 128u : (uint32_t)(kJB / 8) * 128u;        // i-group stride in T
     const uint32_t jdir_t = CONTIG ? (uint32_t)(ipt / 8) * 128u : 128u;        // fiber-group stride in T
@@ -178,20 +205,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) power_tc_kernel(const float* __
             bases[tid] = j < J ? v.base(j) : -1;
         }
         __syncthreads();
-        load_tile_bf16<CONTIG>(A, v, j0, J, T, ipt, bases, vec4 != 0);
+        load_tile_bf16<CONTIG>(A, v, j0, J, T, Tlo, ipt, bases, vec4 != 0);
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
         if (tid == 0) {
-            // W = T X: K runs over I_n in steps of 16 (two core matrices)
-            for (int s = 0; s < ipt / 16; ++s) {
-                uint64_t a;
-                if (CONTIG) a = tc::desc(t_base + s * 2 * kdir_t, kdir_t, jdir_t);      // K-major
-                else a = kMnLboIsK ? tc::desc(t_base + s * 2 * kdir_t, kdir_t, jdir_t)  // MN-major
-                                   : tc::desc(t_base + s * 2 * kdir_t, jdir_t, kdir_t);
-                const uint64_t b = tc::desc(x_base + s * 256, 128, xsbo);
-                tc::mma_bf16(tmem, a, b, id1, s > 0);
+            // W = T_hi X + T_lo X: K runs over I_n in steps of 16 (two core matrices)
+            for (int part = 0; part < 2; ++part) {
+                const uint32_t tb = t_base + (part ? tlo_off : 0u);
+                for (int s = 0; s < ipt / 16; ++s) {
+                    uint64_t a;
+                    if (CONTIG) a = tc::desc(tb + s * 2 * kdir_t, kdir_t, jdir_t);      // K-major
+                    else a = kMnLboIsK ? tc::desc(tb + s * 2 * kdir_t, kdir_t, jdir_t)  // MN-major
+                                       : tc::desc(tb + s * 2 * kdir_t, jdir_t, kdir_t);
+                    const uint64_t b = tc::desc(x_base + s * 256, 128, xsbo);
+                    tc::mma_bf16(tmem, a, b, id1, part > 0 || s > 0);
+                }
             }
             tc::commit(&mbar[0]);
             if (!tc::mbar_wait(&mbar[0], it & 1, kWaitIters)) { *flag = 1; set_status(status, kStatTimeout); }
@@ -199,16 +229,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) power_tc_kernel(const float* __
         __syncthreads();
         if (*flag) { ok = false; break; }
         tc::fence_after_sync();
-        // W (TMEM lanes = fibers, columns = l) -> bf16 B operand (N = l, K = fiber), K-major
+        // W (TMEM: fiber m in lane (m % 16) + 32 (m / 16), columns = l) -> bf16 high
+        // and low B operands (N = l, K = fiber), K-major. Warp q reads lanes
+        // 32 q .. 32 q + 31, of which the first 16 hold fibers 16 q .. 16 q + 15.
         for (int c = half; c < LP / 16; c += 2) {
             uint32_t r[16];
             tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 16), r);
-            const int jj = q * 32 + lane;
+            const int jj = q * 16 + lane;
+            if (lane < 16) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int l = c * 16 + u;
-                *reinterpret_cast<__nv_bfloat16*>(Ws + (l >> 3) * (kJB >> 3) * 128 + (jj >> 3) * 128 + (l & 7) * 16 +
-                                                  (jj & 7) * 2) = __float2bfloat16_rn(__uint_as_float(r[u]));
+                for (int u = 0; u < 16; ++u) {
+                    const int l = c * 16 + u;
+                    const uint32_t o = (l >> 3) * (kJB >> 3) * 128 + (jj >> 3) * 128 + (l & 7) * 16 + (jj & 7) * 2;
+                    const float w = __uint_as_float(r[u]);
+                    const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                    *reinterpret_cast<__nv_bfloat16*>(Ws + o) = h;
+                    *reinterpret_cast<__nv_bfloat16*>(Wlo + o) = __float2bfloat16_rn(w - __bfloat162float(h));
+                }
             }
         }
         tc::fence_async_smem();
@@ -216,15 +253,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) power_tc_kernel(const float* __
         __syncthreads();
         tc::fence_after_sync();
         if (tid == 0) {
-            // X_acc[b] += T^T W: K runs over the 128 fibers in steps of 16
+            // X_acc[b] += T_hi W_hi + T_lo W_hi + T_hi W_lo: K runs over the fibers in steps of 16
             for (int b = 0; b < nb; ++b) {
-                for (int s = 0; s < kJB / 16; ++s) {
-                    const uint32_t start = t_base + b * 16 * kdir_t + s * 2 * jdir_t;
-                    uint64_t a;
-                    if (CONTIG) a = kMnLboIsK ? tc::desc(start, jdir_t, kdir_t) : tc::desc(start, kdir_t, jdir_t);
-                    else a = tc::desc(start, jdir_t, kdir_t);                            // K-major
-                    const uint64_t bd = tc::desc(w_base + s * 256, 128, (uint32_t)(kJB / 8) * 128u);
-                    tc::mma_bf16(tmem + (uint32_t)(LP * (1 + b)), a, bd, id2, it > 0 || s > 0);
+                for (int part = 0; part < 3; ++part) {
+                    const uint32_t ta = t_base + (part == 1 ? tlo_off : 0u);
+                    const uint32_t wb = w_base + (part == 2 ? wlo_off : 0u);
+                    for (int s = 0; s < kJB / 16; ++s) {
+                        const uint32_t start = ta + b * 16 * kdir_t + s * 2 * jdir_t;
+                        uint64_t a;
+                        if (CONTIG) a = kMnLboIsK ? tc::desc(start, jdir_t, kdir_t) : tc::desc(start, kdir_t, jdir_t);
+                        else a = tc::desc(start, jdir_t, kdir_t);                        // K-major
+                        const uint64_t bd = tc::desc(wb + s * 256, 128, (uint32_t)(kJB / 8) * 128u);
+                        tc::mma_bf16(tmem + (uint32_t)(LP * (1 + b)), a, bd, id2, it > 0 || part > 0 || s > 0);
+                    }
                 }
             }
             tc::commit(&mbar[1]);
@@ -257,7 +298,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) power_tc_kernel(const float* __
 
 size_t tc_smem_bytes(int I, int LP) {
     const int ipt = round_up(I, 128);
-    return ((size_t)kJB * ipt + (size_t)LP * ipt + (size_t)LP * kJB) * 2 + 64 + sizeof(int64_t) * kJB + 64;
+    return ((size_t)2 * kJB * ipt + (size_t)LP * ipt + (size_t)2 * LP * kJB) * 2 + 64 + sizeof(int64_t) * kJB + 64;
 }
 
 template <bool CONTIG, int LP>
