@@ -25,9 +25,12 @@
  *    returns and reports device-side failures (Cholesky breakdown that could not
  *    be repaired, non-finite values) in its status. With TUCKER_FLAG_ASYNC the
  *    call returns after enqueueing; the device status is then read by
- *    tucker_last_device_status(). An asynchronous call requires device buffers
- *    and a caller workspace, makes no allocation or synchronisation, and can
- *    therefore be captured into a CUDA graph.
+ *    tucker_last_device_status(), or directly: the first 4 bytes of the
+ *    caller's workspace hold it (0 = success; bit 0 numerical failure, bit 1 a
+ *    bounded wait timed out) once the stream reaches the end of the call's
+ *    work. An asynchronous call requires device buffers and a caller
+ *    workspace, makes no allocation or synchronisation, and can therefore be
+ *    captured into a CUDA graph.
  *  - Scratch memory: opts->workspace / workspace_bytes (device memory of at
  *    least tucker_workspace_size() bytes, 256-byte aligned) when given;
  *    otherwise the library allocates it from the stream-ordered pool and frees
@@ -236,6 +239,70 @@ tucker_status tucker_relative_error(const void* A, tucker_dtype dt, const int64_
 tucker_status tucker_power_step_noalloc(const void* A, tucker_dtype dt, const int64_t* dims, int N,
                                         int mode, const void* X_in, int64_t L, void* X_out,
                                         const tucker_opts* opts);
+
+/* ---------------------------------------------------------------- serving
+ * Not part of the paper's method: a request loop for many decompositions of
+ * different orders, sizes and ranks arriving over time. A server owns one
+ * worker thread and max_inflight CUDA streams on the current device. Submitted
+ * requests wait in FIFO order and are admitted when a stream is free and their
+ * device memory (workspace, plus staging for host inputs and outputs) fits in
+ * what the budget has left; each admitted request runs as a TUCKER_FLAG_ASYNC
+ * decomposition on its own stream, so the work of admitted requests overlaps
+ * on the device, and a request that arrives while others run is admitted as
+ * soon as a stream and memory free up. Results do not depend on what else runs:
+ * every kernel reduces in a fixed order. */
+typedef struct tucker_server tucker_server;
+
+typedef struct {
+    uint32_t struct_size;   /* sizeof(tucker_server_opts) */
+    int32_t max_inflight;   /* requests on the device at once (streams), 1 .. 256 */
+    size_t budget_bytes;    /* device memory admitted requests may hold together */
+    int32_t form;           /* tucker_form of every request */
+    int32_t prec;           /* tucker_sketch_prec of every request */
+} tucker_server_opts;
+
+typedef struct {
+    uint32_t struct_size;   /* sizeof(tucker_request) */
+    int32_t which;          /* 0 = randomized T-HOSVD (Alg. 1/4), 1 = ST-HOSVD (Alg. 2/5) */
+    tucker_dtype dt;
+    const void* A;          /* host or device; must stay valid and unchanged until completion */
+    const int64_t* dims;    /* N extents (copied at submission) */
+    int32_t N;
+    const int32_t* ranks;   /* N ranks (copied) */
+    int32_t P, q;
+    int64_t c;
+    tucker_prob prob;
+    uint64_t seed;
+    void* const* U;         /* N host or device outputs (pointers copied), written by completion */
+    void* G;                /* host or device core output */
+} tucker_request;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* submission -> completion latency of completed requests */
+    double throughput;      /* completed / (last completion - first submission), per second */
+    size_t peak_bytes;      /* largest device memory held by admitted requests together */
+    int32_t peak_inflight;  /* largest number of requests on the device together */
+} tucker_server_stats;
+
+/* Creates a server on the calling thread's current device. */
+tucker_status tucker_server_create(const tucker_server_opts* opts, tucker_server** out);
+
+/* Queues a request and returns at once with its ticket (1, 2, ...). Argument
+ * errors are reported here; TUCKER_ERR_BUDGET when the request alone needs more
+ * device memory than the budget. Any host thread may submit. */
+tucker_status tucker_server_submit(tucker_server* srv, const tucker_request* req, uint64_t* ticket);
+
+/* Waits up to timeout_ms (< 0: without limit, 0: poll) for a request. Returns
+ * TUCKER_OK with the request's own status in *result once it has completed
+ * (outputs written), TUCKER_ERR_TIMEOUT while it has not. */
+tucker_status tucker_server_wait(tucker_server* srv, uint64_t ticket, int64_t timeout_ms,
+                                 tucker_status* result);
+
+tucker_status tucker_server_stats_get(tucker_server* srv, tucker_server_stats* out);
+
+/* Waits for every submitted request, then releases the server. */
+tucker_status tucker_server_destroy(tucker_server* srv);
 
 /* ---------------------------------------------------------------- measurement
  * Not part of the paper's method: counters for benchmarking the path. */

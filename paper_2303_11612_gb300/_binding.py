@@ -44,6 +44,24 @@ class Opts(C.Structure):
                 ("sample_idx", C.POINTER(C.c_void_p))]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("max_inflight", C.c_int32), ("budget_bytes", C.c_size_t),
+                ("form", C.c_int32), ("prec", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("which", C.c_int32), ("dt", C.c_int), ("A", C.c_void_p),
+                ("dims", C.POINTER(C.c_int64)), ("N", C.c_int32), ("ranks", C.POINTER(C.c_int32)),
+                ("P", C.c_int32), ("q", C.c_int32), ("c", C.c_int64), ("prob", C.c_int), ("seed", C.c_uint64),
+                ("U", C.POINTER(C.c_void_p)), ("G", C.c_void_p)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+                ("throughput", C.c_double), ("peak_bytes", C.c_size_t), ("peak_inflight", C.c_int32)]
+
+
 _VP, _I64, _I32, _U64, _U32, _INT, _DBL = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64, C.c_uint32, C.c_int, C.c_double
 _P = C.POINTER
 _SIGS = {
@@ -64,6 +82,11 @@ _SIGS = {
     "tucker_ttm": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _INT, _VP, _P(Opts)],
     "tucker_relative_error": [_VP, _INT, _P(_I64), _INT, _P(_I32), _P(_VP), _VP, _P(_DBL), _P(Opts)],
     "tucker_power_step_noalloc": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _VP, _P(Opts)],
+    "tucker_server_create": [_P(ServerOpts), _P(_VP)],
+    "tucker_server_submit": [_VP, _P(Request), _P(_U64)],
+    "tucker_server_wait": [_VP, _U64, _I64, _P(_INT)],
+    "tucker_server_stats_get": [_VP, _P(ServerStats)],
+    "tucker_server_destroy": [_VP],
     "tucker_launch_count": [],
     "tucker_profile_enable": [_INT],
     "tucker_profile_read": [_INT, _P(_I64), _P(_DBL), _P(_DBL), _P(_DBL)],
@@ -363,3 +386,69 @@ def power_step_noalloc(A, dims, mode, X, stream=None):
                                                                         mode, X.data_ptr(), L, out.data_ptr(),
                                                                         C.byref(o)))
     return out
+
+
+class Server:
+    """Request loop of the C library (tucker_server_*): submit decompositions of
+    any order, size and rank; they are admitted against ``budget_bytes`` of
+    device memory and run concurrently on up to ``max_inflight`` streams.
+
+    ``submit`` takes the tensor (device or host, pinned for overlap) and returns
+    a ticket; the output tensors are created here on ``out_device`` unless given.
+    The binding keeps every tensor of a request alive until ``wait`` has seen it
+    complete."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 8, form="paper", prec="fp32"):
+        o = ServerOpts(C.sizeof(ServerOpts), int(max_inflight), int(budget_bytes), FORM[form], PREC[prec])
+        h = C.c_void_p()
+        _check("tucker_server_create", lib().tucker_server_create(C.byref(o), C.byref(h)))
+        self._h = h
+        self._live = {}
+
+    def submit(self, which: str, A: torch.Tensor, dims, ranks, P=5, q=1, c=0, prob="uniform", seed=0,
+               out=None, out_device=None):
+        dims = [int(d) for d in dims]
+        ranks = [int(r) for r in ranks]
+        N = len(dims)
+        if A.numel() != int(torch.tensor(dims).prod()):
+            raise ValueError("A.numel() must equal prod(dims)")
+        dev = A.device if out_device is None else torch.device(out_device)
+        if out is None:
+            U = [factor_tensor(I, R, A.dtype, dev) for I, R in zip(dims, ranks)]
+            G = torch.empty(int(torch.tensor(ranks).prod()), dtype=A.dtype, device=dev)
+        else:
+            U, G = out
+        d64, r32 = _i64(dims), _i32(ranks)
+        Up = (C.c_void_p * N)(*[u.data_ptr() for u in U])
+        req = Request(C.sizeof(Request), 0 if which == "T" else 1, _dt(A), A.data_ptr(), d64, N, r32, int(P), int(q),
+                      int(c), PROB[prob], int(seed) & (2**64 - 1), Up, G.data_ptr())
+        t = C.c_uint64(0)
+        _check("tucker_server_submit", lib().tucker_server_submit(self._h, C.byref(req), C.byref(t)))
+        self._live[t.value] = (A, U, G)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(U, G) once the request has completed; raises on its failure, or
+        TuckerError(status 5) if it has not completed within timeout_ms."""
+        res = C.c_int(0)
+        _check("tucker_server_wait", lib().tucker_server_wait(self._h, int(ticket), int(timeout_ms), C.byref(res)))
+        A, U, G = self._live.pop(ticket)
+        _check(f"request {ticket}", res.value)
+        return U, G
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check("tucker_server_stats_get", lib().tucker_server_stats_get(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _check("tucker_server_destroy", lib().tucker_server_destroy(self._h))
+            self._h = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
