@@ -173,6 +173,67 @@ def run_reference(args, rank):
     return 0
 
 
+# ---------------------------------------------------------------- serving
+SERVE_N = 300
+SERVE_BUDGET = 40 << 30
+
+
+def serving_requests(torch, n=SERVE_N, seed=0):
+    """A bounded sample of the serving stream: orders 3 and 4 (50/50), ranks
+    U{4..32} (at most the extent), P = 5, q = 1, low-rank + 1e-2 noise built on
+    the device. Extents U{32..256} for order 3 and U{32..96} for order 4 (the
+    full stream's order-4 requests reach 256^4 = 17 GB each; the sample keeps
+    the whole set resident)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    out = []
+    for k in range(n):
+        N = 3 if rng.random() < 0.5 else 4
+        dims = [int(x) for x in rng.integers(32, (256 if N == 3 else 96) + 1, size=N)]
+        ranks = [int(min(d, r)) for d, r in zip(dims, rng.integers(4, 33, size=N))]
+        X = torch.randn(*reversed(ranks), device="cuda", generator=g)
+        for m in range(N):                 # X x_m U_m, i_1 fastest: torch axis N-1-m
+            Um = torch.linalg.qr(torch.randn(dims[m], ranks[m], device="cuda", generator=g))[0]
+            X = torch.movedim(torch.tensordot(X, Um, dims=([N - 1 - m], [1])), -1, N - 1 - m)
+        X = X / X.norm()
+        E = torch.randn(X.shape, device="cuda", generator=g)
+        X = (X + 1e-2 * E / E.norm()).contiguous().view(-1)
+        out.append(dict(A=X, dims=dims, ranks=ranks, seed=k))
+    torch.cuda.synchronize()
+    return out
+
+
+def serving_bench(tk, torch, reqs, prec, load=0.7):
+    """Saturation throughput (every request submitted at once), then p50/p99
+    latency under Poisson arrivals at `load` times that throughput."""
+    import numpy as np
+    with tk.Server(budget_bytes=SERVE_BUDGET, max_inflight=16, prec=prec) as srv:
+        t0 = time.perf_counter()
+        ts = [srv.submit("ST", r["A"], r["dims"], r["ranks"], P=5, q=1, seed=r["seed"]) for r in reqs]
+        for t in ts:
+            srv.wait(t)
+        sat = len(reqs) / (time.perf_counter() - t0)
+    rate = load * sat
+    gaps = np.random.default_rng(1).exponential(1.0 / rate, size=len(reqs))
+    with tk.Server(budget_bytes=SERVE_BUDGET, max_inflight=16, prec=prec) as srv:
+        t0 = time.perf_counter()
+        due = t0
+        ts = []
+        for r, gap in zip(reqs, gaps):
+            due += gap
+            while time.perf_counter() < due:
+                pass
+            ts.append(srv.submit("ST", r["A"], r["dims"], r["ranks"], P=5, q=1, seed=r["seed"]))
+        for t in ts:
+            srv.wait(t)
+        st = srv.stats()
+    return {"saturation_decomps_per_s": sat, "offered_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "mean_ms": st["mean_ms"], "max_ms": st["max_ms"], "decomps_per_s": st["throughput"],
+            "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"], "failed": st["failed"]}
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -183,6 +244,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="both", choices=["both", "bf16", "fp32"],
                     help="sketch arithmetic to time (both: bf16 is the headline when its RE matches)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--copies", type=int, default=8,
                     help="decompositions of each variant in flight per step (each on its own stream)")
     ap.add_argument("--single", default=None, choices=[v["name"] for v in VARIANTS],
@@ -318,6 +380,16 @@ def main():
     for prec in (["bf16", "fp32"] if args.prec == "both" else [args.prec]):
         forms[prec] = measure(prec)
     clk = clocks.stop()
+    serving = None
+    if not args.no_serving:
+        reqs = serving_requests(torch)
+        serving = {p: serving_bench(tk, torch, reqs, p) for p in (["bf16", "fp32"] if args.prec == "both"
+                                                                  else [args.prec])}
+        serving["sample"] = (f"{len(reqs)} randomized ST-HOSVD requests (P=5, q=1), orders 3/4, extents U{{32..256}} "
+                             f"(order 3) / U{{32..96}} (order 4), ranks U{{4..32}}, low-rank + 1e-2 noise, device-"
+                             f"resident; budget {SERVE_BUDGET >> 30} GB, 16 streams; latencies at 0.7x the "
+                             f"saturation throughput, Poisson arrivals")
+        del reqs
     if "bf16" in forms and "fp32" in forms:
         equal = all(abs(forms["bf16"]["rel_error"][k] - forms["fp32"]["rel_error"][k]) <= 1e-3
                     for k in forms["fp32"]["rel_error"])
@@ -326,33 +398,35 @@ def main():
         equal = None
         head = next(iter(forms.values()))
 
-    # end to end through the C ABI with pinned host buffers, headline arithmetic
+    # end to end through the public API with pinned host buffers, headline arithmetic:
+    # every step submits the whole batch to the library's request loop, which
+    # stages each input host->device and each result device->host on the
+    # request's own stream, so copies of one request overlap work of others
     houts = [([torch.empty((R, I), dtype=torch.float32).pin_memory().t() for I, R in zip(DIMS, RANKS)],
-              torch.empty(int(np.prod(RANKS)), dtype=torch.float32).pin_memory()) for _ in VARIANTS]
-
-    def step_e2e():
-        for v, out in zip(VARIANTS, houts):
-            tk.rsthosvd(pinned[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
-                        stream=main_s, out=out, prec=head["prec"])
+              torch.empty(int(np.prod(RANKS)), dtype=torch.float32).pin_memory()) for _ in batch]
 
     e2e = None
     try:
-        step_e2e()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e2e_steps = max(3, args.steps // 10)
-        t0 = time.perf_counter()
-        e0.record(main_s)
-        for _ in range(e2e_steps):
+        with tk.Server(budget_bytes=64 << 30, max_inflight=len(batch), prec=head["prec"]) as srv:
+            def step_e2e():
+                ts = [srv.submit("ST", pinned[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"],
+                                 seed=SEED, out=out) for v, out in zip(batch, houts)]
+                for t in ts:
+                    srv.wait(t)
+
             step_e2e()
-        e1.record(main_s)
-        main_s.synchronize()
-        wall = time.perf_counter() - t0
-        e2e_s = max_over_ranks(max(wall, e0.elapsed_time(e1) / 1e3))
-        h2d = sum(host[v["tensor"]].nbytes for v in VARIANTS)
-        d2h = sum((sum(I * R for I, R in zip(DIMS, RANKS)) + int(np.prod(RANKS))) * 4 for _ in VARIANTS)
-        e2e = {"value": len(VARIANTS) * e2e_steps * world / e2e_s, "unit": "decomps/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            barrier()
+            e2e_steps = max(3, args.steps // 10)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                step_e2e()
+            e2e_s = max_over_ranks(time.perf_counter() - t0)
+        h2d = sum(host[v["tensor"]].nbytes for v in batch)
+        d2h = sum((sum(I * R for I, R in zip(DIMS, RANKS)) + int(np.prod(RANKS))) * 4 for _ in batch)
+        e2e = {"value": len(batch) * e2e_steps * world / e2e_s, "unit": "decomps/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "path": f"tucker_server_* request loop, {len(batch)} requests per step, pinned host input and "
+                       f"output buffers, host clock around the steps"}
     except Exception as exc:  # noqa: BLE001
         e2e = {"value": None, "unit": "decomps/s", "error": str(exc)}
 
@@ -415,6 +489,7 @@ def main():
             "forms": {p: {"value": f["value"], "ms_per_step": f["ms"] / args.steps, "rel_error": f["rel_error"]}
                       for p, f in forms.items()},
             "bf16_matches_fp32_rel_err_within_1e-3": equal,
+            "serving": serving,
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host)

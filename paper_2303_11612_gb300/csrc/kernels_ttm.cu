@@ -3,17 +3,17 @@
 // 1/4, and the reconstruction used by the relative error (Eq. 8); plus
 // deterministic sums of squares.
 //
-// Each CTA takes JB consecutive mode-n fibers and OB output indices; the fiber
-// tile streams through shared memory in chunks of KC input indices while the
-// JB x OB block of results stays in registers, so the input is read once per
-// output block (one block whenever K_out <= OB).
+// Each CTA takes JB = 64 NF consecutive mode-n fibers and OB = 4 OPT output
+// indices; the fiber tile streams through shared memory in chunks of KC input
+// indices while the JB x OB block of results stays in registers, so the input
+// is read once per output block (one block whenever K_out <= 64).
 #include "internal.h"
 
 namespace tk {
 namespace {
 
 constexpr int kT = kThreads;
-constexpr int JB = 64, KC = 32, KP = KC + 4;   // rows padded to 36 elements: 16-byte aligned, conflict-free
+constexpr int KC = 32, KP = KC + 4;   // rows padded to 36 elements: 16-byte aligned, conflict-free
 
 // four consecutive T values from 16-byte aligned shared memory
 __device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
@@ -25,16 +25,16 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
     v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
 }
 
-// OB = output block (8, 16, 32 or 64 outputs); thread (jj = tid % JB, og = tid / JB)
-// owns fiber jj and outputs og*OPT .. +OPT. Both shared tiles keep the input
+// Thread (lane64 = tid % 64, og = tid / 64) owns fibers lane64 + 64 f (f < NF)
+// and outputs og * OPT .. og * OPT + OPT - 1. Both shared tiles keep the input
 // index contiguous, so stores are unit-stride and the inner loop reads four
-// input indices per 128-bit load (the M rows are broadcast across the warp).
-// The next chunk's global loads are issued into registers before the current
-// chunk is multiplied.
-template <typename T, int OB>
+// input indices per 128-bit load; the M rows are the same across a warp
+// (broadcast) and each serves 4 NF multiply-adds. The next chunk's global
+// loads are issued into registers before the current chunk is multiplied.
+template <typename T, int OPT, int NF>
 __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeView v, const T* __restrict__ Mp,
                                                  int64_t K_out, int64_t ld_i, int64_t ld_k, T* __restrict__ out) {
-    constexpr int OPT = OB / (kT / JB);
+    constexpr int JB = 64 * NF, OB = 4 * OPT;
     constexpr int TPT = JB * KC / kT;                    // tile elements loaded per thread and chunk
     constexpr int MPT = (OB * KC + kT - 1) / kT;         // M elements loaded per thread and chunk
     constexpr size_t kTileBytes = sizeof(T) * (JB * KP + OB * KP);
@@ -50,9 +50,9 @@ __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeVi
     const int64_t o0 = (int64_t)blockIdx.y * OB;
     const int I = (int)v.i;
     const bool contig = v.lf == 1;
-    if (tid < JB) {
-        const int64_t j = j0 + tid;
-        bases[tid] = j < J ? v.base(j) : -1;
+    for (int r = tid; r < JB; r += kT) {
+        const int64_t j = j0 + r;
+        bases[r] = j < J ? v.base(j) : -1;
     }
     __syncthreads();
     T tr[TPT], mr[MPT];
@@ -97,10 +97,12 @@ __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeVi
             if (e < OB * KC) Ms[oo][kk] = mr[u];
         }
     };
-    const int jj = tid % JB, og = tid / JB;
-    T acc[OPT];
+    const int jl = tid % 64, og = tid / 64;
+    T acc[NF][OPT];
 #pragma unroll
-    for (int u = 0; u < OPT; ++u) acc[u] = T(0);
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int u = 0; u < OPT; ++u) acc[f][u] = T(0);
     load_chunk(0);
     for (int i0 = 0; i0 < I; i0 += KC) {
         store_chunk();
@@ -108,23 +110,29 @@ __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeVi
         if (i0 + KC < I) load_chunk(i0 + KC);            // in flight during the products below
 #pragma unroll 2
         for (int kk = 0; kk < KC; kk += 4) {
-            T t4[4];
-            ld4(&Ts[jj][kk], t4);
+            T t4[NF][4];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) ld4(&Ts[jl + 64 * f][kk], t4[f]);
 #pragma unroll
             for (int u = 0; u < OPT; ++u) {
                 T m4[4];
                 ld4(&Ms[og * OPT + u][kk], m4);
-                acc[u] = fma(t4[0], m4[0], acc[u]);
-                acc[u] = fma(t4[1], m4[1], acc[u]);
-                acc[u] = fma(t4[2], m4[2], acc[u]);
-                acc[u] = fma(t4[3], m4[3], acc[u]);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    acc[f][u] = fma(t4[f][0], m4[0], acc[f][u]);
+                    acc[f][u] = fma(t4[f][1], m4[1], acc[f][u]);
+                    acc[f][u] = fma(t4[f][2], m4[2], acc[f][u]);
+                    acc[f][u] = fma(t4[f][3], m4[3], acc[f][u]);
+                }
             }
         }
         __syncthreads();
     }
     // (the loop ends with a barrier, so every thread is done reading Ts and Ms)
 #pragma unroll
-    for (int u = 0; u < OPT; ++u) Os[jj][og * OPT + u] = acc[u];
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int u = 0; u < OPT; ++u) Os[jl + 64 * f][og * OPT + u] = acc[f][u];
     __syncthreads();
     if (contig) {
         // out[o + j K_out]: consecutive threads -> consecutive o
@@ -198,15 +206,26 @@ cudaError_t launch_ttm(const T* A, const ModeView& v, const T* Mp, int64_t K_out
                        cudaStream_t s) {
     const int64_t J = v.fibers();
     if (J == 0 || K_out == 0) return cudaSuccess;
-    const int OB = K_out <= 8 ? 8 : K_out <= 16 ? 16 : K_out <= 32 ? 32 : 64;
-    dim3 grid((unsigned)((J + JB - 1) / JB), (unsigned)((K_out + OB - 1) / OB));
+    // outputs per thread: the smallest instantiated OPT with 4 OPT >= K_out (at most 16)
+    static const int kOpts[] = {1, 2, 3, 4, 5, 6, 8, 12, 16};
+    int OPT = 16;
+    for (int o : kOpts)
+        if (4 * o >= K_out) { OPT = o; break; }
+    constexpr int NF = sizeof(T) == 4 ? 2 : 1;
+    const int OB = 4 * OPT, JBl = 64 * NF;
+    dim3 grid((unsigned)((J + JBl - 1) / JBl), (unsigned)((K_out + OB - 1) / OB));
     const double ein = (double)v.i * (double)J, eout = (double)K_out * (double)J;
     ProfScope prof(kKTtm, (ein + eout) * sizeof(T), 2.0 * ein * (double)K_out, s);
-    switch (OB) {
-        case 8: ttm_kernel<T, 8><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        case 16: ttm_kernel<T, 16><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        case 32: ttm_kernel<T, 32><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        default: ttm_kernel<T, 64><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+    switch (OPT) {
+        case 1: ttm_kernel<T, 1, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        case 2: ttm_kernel<T, 2, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        case 3: ttm_kernel<T, 3, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        case 4: ttm_kernel<T, 4, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        case 5: ttm_kernel<T, 5, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        case 6: ttm_kernel<T, 6, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        case 8: ttm_kernel<T, 8, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        case 12: ttm_kernel<T, 12, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        default: ttm_kernel<T, 16, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
     }
     note_launch();
     return cudaGetLastError();
