@@ -679,17 +679,19 @@ __global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ X, int
 constexpr int kFRows = 64;               // rows of U staged per step of the final Gram
 
 struct FLayout {
-    size_t g, w, rt, dinv, valid, xs, total;
+    size_t g, w, rt, dinv, valid, idx, lev, xs, total;
 };
-__host__ __device__ inline FLayout flayout(int R, int elem) {
+__host__ __device__ inline FLayout flayout(int R, int elem, int64_t I) {
     const size_t np = packed_size(R);
     FLayout f;
     f.g = 0;                                              // packed Gram (as Pair sums), then R^-1
-    f.w = up16(8 * np);                                   // packed Cholesky factor
+    f.w = up16(8 * np);                                   // packed Cholesky factor; with rt: coefficients
     f.rt = f.w + up16(8 * np);                            // transposed factor
     f.dinv = f.rt + up16(8 * np);
     f.valid = f.dinv + up16((size_t)8 * R);
-    f.xs = f.valid + up16(sizeof(int) * (size_t)R);
+    f.idx = f.valid + up16(sizeof(int) * (size_t)R);      // [2][R]: dropped columns, candidate rows
+    f.lev = f.idx + up16(sizeof(int) * 2 * (size_t)R);    // [I] row leverages
+    f.xs = f.lev + up16((size_t)elem * (size_t)I);
     f.total = f.xs + up16((size_t)elem * kFRows * R);
     return f;
 }
@@ -702,17 +704,25 @@ __host__ __device__ inline FLayout flayout(int R, int elem) {
 //      column r mixes with earlier columns only, so the span of the first k
 //      columns is unchanged for every k. This restores orthonormality where
 //      the sketch was numerically rank-deficient and CholeskyQR could not.
-//   3. Sign rule: each column's largest-magnitude entry positive (lowest row on ties).
-//   4. Dropped columns: the first unit vector e_k (k increasing) that keeps a long
-//      residual after two Gram-Schmidt passes against every valid column. The
-//      squared residuals of e_0 .. e_{I-1} average (I - d) / I for d valid
-//      columns, so accepting one above half that average always succeeds.
+//   3. Dropped columns, all at once: the m dropped columns (in order) take the
+//      unit vectors e_k of the first m rows k whose leverage
+//      ||U_valid(k, :)||^2 leaves a long residual, 1 - leverage_k >
+//      (I - d) / (2 I) for d valid columns (the leverages average d / I, so
+//      enough rows qualify), projected out of the valid columns twice
+//      (e_k - U_v U_v(k, :)^T, then once more by inner products); steps 1-2
+//      then run once more over all R columns to orthonormalise them.
+//   4. Sign rule: each column's largest-magnitude entry positive (lowest row on ties).
+//   5. Any column still dropped (not expected): the first unit vector e_k (k
+//      increasing) that keeps a long residual after two Gram-Schmidt passes
+//      against every valid column. The squared residuals of e_0 .. e_{I-1}
+//      average (I - d) / I for d valid columns, so accepting one above half
+//      that average always succeeds.
 template <typename T>
 __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I, int R) {
     using S = typename SmallScalar<T>::type;
     using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const FLayout lay = flayout(R, sizeof(T));
+    const FLayout lay = flayout(R, sizeof(T), I);
     Pair* GP = reinterpret_cast<Pair*>(smem_raw + lay.g);
     S* Ri = reinterpret_cast<S*>(smem_raw + lay.g);
     S* W = reinterpret_cast<S*>(smem_raw + lay.w);
@@ -720,16 +730,23 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I
     S* dinv = reinterpret_cast<S*>(smem_raw + lay.dinv);
     int* valid = reinterpret_cast<int*>(smem_raw + lay.valid);
     T* xs = reinterpret_cast<T*>(smem_raw + lay.xs);     // [kFRows][R]
+    int* drop = reinterpret_cast<int*>(smem_raw + lay.idx);   // [R] dropped columns, in order
+    int* cand = drop + R;                                      // [R] their candidate rows
+    T* lev = reinterpret_cast<T*>(smem_raw + lay.lev);    // [I]
+    T* coef = reinterpret_cast<T*>(smem_raw + lay.w);     // [R][R] projection coefficients (W and RT)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kT / 32;
     const int np = (int)packed_size(R);
-    __shared__ int offdiag;
+    __shared__ int offdiag, ndrop;
     __shared__ double red[kT / 32];
     __shared__ double bcast;
     __shared__ T bvs[kT / 32];
     __shared__ int64_t bis[kT / 32];
 
+    const double eps = sizeof(T) == 4 ? (double)FLT_EPSILON : DBL_EPSILON;
+    for (int pass = 0; pass < 2; ++pass) {
     // 1. Gram (FP32 data: Pair sums; FP64 data: the Pair slots hold one double)
     double* GD = reinterpret_cast<double*>(smem_raw + lay.g);
+    __syncthreads();
     for (int p = tid; p < np; p += kT) {
         if constexpr (sizeof(T) == 4) GP[p] = Pair{0.f, 0.f};
         else GD[p] = 0.0;
@@ -759,7 +776,6 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I
         }
     }
     __syncthreads();
-    const double eps = sizeof(T) == 4 ? (double)FLT_EPSILON : DBL_EPSILON;
     for (int p = tid; p < np; p += kT) {
         int a = 0, rem = p;
         while (rem >= R - a) { rem -= R - a; ++a; }
@@ -772,8 +788,8 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I
     }
     for (int k = tid; k < R; k += kT) valid[k] = 1;
     __syncthreads();
-
-    if (offdiag) {
+    if (!offdiag) break;
+    {
         // 2. Cholesky with column dropping (G kept in RT for the reference norms)
         for (int p = tid; p < np; p += kT) RT[p] = W[p];
         __syncthreads();
@@ -833,8 +849,72 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I
         }
         __syncthreads();
     }
+    if (tid == 0) {
+        int m = 0;
+        for (int r = 0; r < R; ++r)
+            if (!valid[r]) drop[m++] = r;
+        ndrop = m;
+    }
+    __syncthreads();
+    const int m = ndrop;
+    if (m == 0 || pass == 1) break;
+    // 3. candidates: the first m rows k (increasing) whose unit vector keeps a
+    //    long residual, 1 - leverage_k > (I - valid columns) / (2 I)
+    for (int64_t i = tid; i < I; i += kT) {
+        T a = T(0);
+        for (int r = 0; r < R; ++r)
+            if (valid[r]) a = fma(U[(int64_t)r * I + i], U[(int64_t)r * I + i], a);
+        lev[i] = a;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const T keep = T(0.5) * (T)(I - (R - m)) / (T)I;
+        int t = 0;
+        for (int64_t k = 0; k < I && t < m; ++k)
+            if (T(1) - lev[k] > keep) cand[t++] = (int)k;
+        for (int64_t k = 0; k < I && t < m; ++k) {         // any shortfall: the next rows in order
+            bool used = false;
+            for (int u = 0; u < t; ++u) used |= cand[u] == (int)k;
+            if (!used) cand[t++] = (int)k;
+        }
+    }
+    __syncthreads();
+    // first projection, from the candidate rows of the valid columns
+    for (int64_t e = tid; e < I * m; e += kT) {
+        const int t = (int)(e / I);
+        const int64_t i = e - (int64_t)t * I;
+        const int k = cand[t];
+        T v = i == k ? T(1) : T(0);
+        for (int r = 0; r < R; ++r)
+            if (valid[r]) v -= U[(int64_t)r * I + i] * U[(int64_t)r * I + k];
+        U[(int64_t)drop[t] * I + i] = v;
+    }
+    __syncthreads();
+    // second projection by inner products (one warp per pair)
+    for (int pr = warp; pr < R * m; pr += nw) {
+        const int r = pr / m, t = pr % m;
+        T c = T(0);
+        if (valid[r]) {
+            DotAcc<T> acc;
+            for (int64_t i = lane; i < I; i += 32) acc.add(U[(int64_t)r * I + i], U[(int64_t)drop[t] * I + i]);
+            acc.reduce();
+            c = (T)acc.value();
+        }
+        if (lane == 0) coef[r * m + t] = c;
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < I * m; e += kT) {
+        const int t = (int)(e / I);
+        const int64_t i = e - (int64_t)t * I;
+        T v = U[(int64_t)drop[t] * I + i];
+        for (int r = 0; r < R; ++r)
+            if (valid[r]) v -= coef[r * m + t] * U[(int64_t)r * I + i];
+        U[(int64_t)drop[t] * I + i] = v;
+    }
+    __syncthreads();
+    }
 
-    // 3. sign rule, one warp per column
+    // 4. sign rule, one warp per column
     for (int r = warp; r < R; r += nw) {
         if (!valid[r]) continue;
         T bv = T(-1);
@@ -854,7 +934,7 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I
     }
     __syncthreads();
 
-    // 4. completion of dropped columns (the residual is formed in U's own column)
+    // 5. completion of columns still dropped (the residual is formed in U's own column)
     int nvalid = 0;
     for (int r = 0; r < R; ++r) nvalid += valid[r];
     int64_t k = 0;
@@ -956,11 +1036,11 @@ static size_t gram_chol_smem(const OrthPlan& p, int elem) {
 static size_t extract_smem(const OrthPlan& p, int R, int elem) {
     return std::max(xlayout(p.L, R, elem).total, (size_t)elem * (size_t)gram_rows(p) * p.L);
 }
-static size_t finish_smem(int R, int elem) { return flayout(R, elem).total; }
+static size_t finish_smem(int R, int elem, int64_t I) { return flayout(R, elem, I).total; }
 
 bool orth_supported(const OrthPlan& p, int R, int elem) {
     return gram_chol_smem(p, elem) <= kSmemCap && extract_smem(p, R, elem) <= kSmemCap &&
-           8 * packed_size(p.L) <= kSmemCap && finish_smem(R, elem) <= kSmemCap;
+           8 * packed_size(p.L) <= kSmemCap && finish_smem(R, elem, p.I) <= kSmemCap;
 }
 
 size_t orth_scratch_bytes(const OrthPlan& p, int elem_size) {
@@ -1036,7 +1116,7 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
     if (ublocks > 4 * 1024) ublocks = 4 * 1024;
     form_u_kernel<T><<<(unsigned)ublocks, kT, 0, s>>>(Q1, p.I, L, R, (const S*)sc.W, U);
     note_launch();
-    const size_t fsm = finish_smem(R, sizeof(T));
+    const size_t fsm = finish_smem(R, sizeof(T), p.I);
     cudaFuncSetAttribute(finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
     finish_kernel<T><<<1, kT, fsm, s>>>(U, p.I, R);
     note_launch();
