@@ -200,16 +200,19 @@ tucker_status tucker_gather_fibers(const void* A, tucker_dtype dt, const int64_t
 
 /* U (I x R, column-major, dt) = the R leading left singular vectors of the
  * sketch C (I x L, column-major, dt), largest-magnitude entry of each column
- * positive (remark after Algorithm 5). FP64 CholeskyQR2 (shifted CholeskyQR3
- * when the Gram matrix is numerically singular) then a one-sided Jacobi SVD of
- * the triangular factor. */
+ * positive (remark after Algorithm 5). CholeskyQR2 (shifted once when the Gram
+ * matrix is numerically singular) with the small triangular algebra in
+ * double-float (FP32 data) or FP64 (FP64 data), then a one-sided Jacobi SVD of
+ * the triangular factor; a final CholeskyQR pass on U keeps it orthonormal
+ * where the sketch is numerically rank-deficient. */
 tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, int64_t L,
                                     int64_t R, void* U, const tucker_opts* opts);
 
 /* Mode-n product out = A x_n M (Section 2) with M given by M_ptr, a column-major
  * matrix: transpose == 0: M is K x I_n (out has K in mode n);
  *         transpose == 1: M_ptr holds I_n x K and M is its transpose
- *         (out = A x_n M_ptr^T, the truncation B x_n U^T of Algorithm 2). */
+ *         (out = A x_n M_ptr^T, the truncation B x_n U^T of Algorithm 2).
+ * Exact FP32 / FP64 FMA. */
 tucker_status tucker_ttm(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode,
                          const void* M_ptr, int64_t K, int transpose, void* out,
                          const tucker_opts* opts);
