@@ -234,6 +234,33 @@ def serving_bench(tk, torch, reqs, prec, load=0.7):
             "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"], "failed": st["failed"]}
 
 
+# ---------------------------------------------------------------- ranks
+def rank_barrier(dist, torch, cuda=True):
+    """Every rank's queued GPU work done, then all ranks meet (timed regions
+    start and end here)."""
+    if cuda:
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    if cuda:
+        torch.cuda.synchronize()
+
+
+def rank_max(dist, torch, x, device):
+    """Largest value over the ranks (the slowest rank's time)."""
+    if not dist:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Weak scaling: every rank processes units_per_rank; the job takes the
+    slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -283,17 +310,10 @@ def main():
     side = [torch.cuda.Stream() for _ in batch]
 
     def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
+        rank_barrier(dist, torch, cuda=True)
 
     def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(dist, torch, x, "cuda")
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -372,7 +392,7 @@ def main():
         prof = {k: tk.profile_read(k) for k in ("power", "ttm", "gather", "norms", "extract", "sample")}
         tk.profile_enable(False)
         del graph
-        return {"prec": prec, "ms": ms, "value": len(batch) * args.steps * world / (ms / 1e3),
+        return {"prec": prec, "ms": ms, "value": whole_job_rate(len(batch) * args.steps, world, ms / 1e3),
                 "gpu_launches": (n1 - n0) if n1 - n0 > 0 else per_step * args.steps,
                 "graph": True, "rel_error": res, "prof": prof}
 
@@ -423,7 +443,7 @@ def main():
             e2e_s = max_over_ranks(time.perf_counter() - t0)
         h2d = sum(host[v["tensor"]].nbytes for v in batch)
         d2h = sum((sum(I * R for I, R in zip(DIMS, RANKS)) + int(np.prod(RANKS))) * 4 for _ in batch)
-        e2e = {"value": len(batch) * e2e_steps * world / e2e_s, "unit": "decomps/s",
+        e2e = {"value": whole_job_rate(len(batch) * e2e_steps, world, e2e_s), "unit": "decomps/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "path": f"tucker_server_* request loop, {len(batch)} requests per step, pinned host input and "
                        f"output buffers, host clock around the steps"}
