@@ -294,7 +294,7 @@ cudaError_t run_driver(const Plan& p, const T* A, const int32_t* ranks, int q, i
             TK_TRY(factor_mode<T>(cur, mp, n, q, prob, seed, p.form, U[n], w,
                                   sample_out ? sample_out[n] : nullptr, s));
             T* out = n == N - 1 ? G : (T*)w.inter[n & 1];
-            TK_TRY(launch_ttm<T>(cur, mp.v, U[n], ranks[n], 1, mp.v.i, out, s));
+            TK_TRY(launch_ttm<T>(cur, mp.v, U[n], ranks[n], 1, mp.v.i, out, s, w.status));
             cur = out;
         }
     } else {
@@ -307,7 +307,7 @@ cudaError_t run_driver(const Plan& p, const T* A, const int32_t* ranks, int q, i
         for (int n = 0; n < N; ++n) {
             const ModeView v = view_of(e, N, n);
             T* out = n == N - 1 ? G : (T*)w.inter[n & 1];
-            TK_TRY(launch_ttm<T>(cur, v, U[n], ranks[n], 1, v.i, out, s));
+            TK_TRY(launch_ttm<T>(cur, v, U[n], ranks[n], 1, v.i, out, s, w.status));
             e[n] = ranks[n];
             cur = out;
         }
@@ -711,14 +711,17 @@ tucker_status tucker_ttm(const void* A, tucker_dtype dt, const int64_t* dims, in
     // M(k, i): transpose == 0: M_ptr is K x I_n (col-major) -> M_ptr[k + i K]
     //          transpose == 1: M_ptr is I_n x K               -> M_ptr[i + k I_n]
     const int64_t ld_i = transpose ? 1 : K, ld_k = transpose ? v.i : 1;
+    Scratch sc;
+    if ((rs = sc.get(256, o.stream)) != TUCKER_OK) return rs;
+    if (cudaMemsetAsync(sc.p, 0, sizeof(int), o.stream) != cudaSuccess) return from_cuda(cudaGetLastError());
     cudaError_t e = dt == TUCKER_F32 ? launch_ttm<float>((const float*)A, v, (const float*)M_ptr, K, ld_i, ld_k,
-                                                         (float*)out, o.stream)
+                                                         (float*)out, o.stream, (int*)sc.p)
                   : dt == TUCKER_F64 ? launch_ttm<double>((const double*)A, v, (const double*)M_ptr, K, ld_i, ld_k,
                                                           (double*)out, o.stream)
                                      : cudaErrorInvalidValue;
     if (e == cudaErrorInvalidValue) return TUCKER_ERR_INVALID_ARG;
     if (e != cudaSuccess) return from_cuda(e);
-    return sync_status(o.stream, nullptr);
+    return sync_status(o.stream, (const int*)sc.p);
 }
 
 tucker_status tucker_relative_error(const void* A, tucker_dtype dt, const int64_t* dims, int N, const int32_t* ranks,

@@ -91,10 +91,12 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
                            void* scratch, int* status, cudaStream_t s);
 
 // ---- mode products and norms (kernels_ttm.cu)
-// out = A x_n M: M(k_out, i) read as Mp[i * ld_i + k_out * ld_k].
+// out = A x_n M: M(k_out, i) read as Mp[i * ld_i + k_out * ld_k]. With a
+// device status word (FP32) the TMA-fed kernel is used where the shape allows;
+// a bounded wait that times out sets kStatTimeout there.
 template <typename T>
 cudaError_t launch_ttm(const T* A, const ModeView& v, const T* Mp, int64_t K_out, int64_t ld_i,
-                       int64_t ld_k, T* out, cudaStream_t s);
+                       int64_t ld_k, T* out, cudaStream_t s, int* status = nullptr);
 size_t sumsq_scratch_bytes();
 // *out (device double) = sum (a - b)^2 (b may be null).
 template <typename T>

@@ -182,7 +182,11 @@ def test_leading_factor_rank_deficient_sketch(tk):
     assert np.linalg.norm(U @ U.T - Uo @ Uo.T, 2) < 1e-3
 
 
-@pytest.mark.parametrize("dims", [(30, 20, 17), (7, 6, 5, 4), (100, 3, 2)])
+# (64, 48, 40) and (400, 40, 36) take the TMA-fed kernel in every mode (extents
+# and slab strides multiples of 4): ragged last index chunks (I = 40, 400),
+# slabs narrower than a 128-fiber tile (L_f = 64) and partial tiles (L_f = 400);
+# the odd shapes take the register-staged kernel.
+@pytest.mark.parametrize("dims", [(30, 20, 17), (7, 6, 5, 4), (100, 3, 2), (64, 48, 40), (400, 40, 36)])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_ttm(tk, dims, transpose):
     A = synth.lowrank_noise(dims, [2] * len(dims), rel_noise=0.5, seed=10)
