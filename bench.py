@@ -272,6 +272,8 @@ def main():
     ap.add_argument("--prec", default="both", choices=["both", "bf16", "fp32"],
                     help="sketch arithmetic to time (both: bf16 is the headline when its RE matches)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default kernel configurations (no tuning in the synchronous warm-up calls)")
     ap.add_argument("--copies", type=int, default=8,
                     help="decompositions of each variant in flight per step (each on its own stream)")
     ap.add_argument("--single", default=None, choices=[v["name"] for v in VARIANTS],
@@ -303,6 +305,10 @@ def main():
         torch.cuda.synchronize()
         print(json.dumps({"single": v["name"], "prec": prec, "ok": True}))
         return 0
+    if not args.no_autotune:
+        # the synchronous accuracy checks below meet every shape class first and
+        # tune it; the graph-captured steps then reuse the kept choices
+        tk.autotune_enable(True)
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
     main_s = torch.cuda.Stream()
@@ -510,6 +516,7 @@ def main():
                       for p, f in forms.items()},
             "bf16_matches_fp32_rel_err_within_1e-3": equal,
             "serving": serving,
+            "autotune": tk.autotune_entries(),
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host)

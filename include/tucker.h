@@ -307,6 +307,26 @@ tucker_status tucker_server_stats_get(tucker_server* srv, tucker_server_stats* o
 /* Waits for every submitted request, then releases the server. */
 tucker_status tucker_server_destroy(tucker_server* srv);
 
+/* ---------------------------------------------------------------- autotuning
+ * Not part of the paper's method. When enabled, the first synchronous call
+ * (never an asynchronous one, never under stream capture) that meets a new
+ * shape class of a tunable kernel times each candidate configuration on that
+ * call's own data and stream (one warm-up and one timed launch each) and keeps
+ * the fastest; every later call of the class, synchronous or not, uses it.
+ * Classes and candidates:
+ *   mode-n product (I_n, K_out, L_f, J_n): register-staged tiles, TMA-fed tiles
+ *     with 2 or 3 stages - all three give bitwise the same result;
+ *   FP32 power step (I_n, L_n, +-L_f, J_n): fiber-tile x column-group shapes
+ *     32x32, 32x16, 16x16, 32x8, 16x8 within the planned partial storage -
+ *     these differ in summation order, so results can change in the last bits.
+ * Choices are kept for the process. */
+tucker_status tucker_autotune_enable(int on);
+/* Number of shape classes tuned so far. */
+int64_t tucker_autotune_count(void);
+/* Class k (0 <= k < count): one line naming the class, its choice and the
+ * candidates' times; valid until the next call on this thread. */
+const char* tucker_autotune_entry(int64_t k);
+
 /* ---------------------------------------------------------------- measurement
  * Not part of the paper's method: counters for benchmarking the path. */
 

@@ -87,12 +87,16 @@ _SIGS = {
     "tucker_server_wait": [_VP, _U64, _I64, _P(_INT)],
     "tucker_server_stats_get": [_VP, _P(ServerStats)],
     "tucker_server_destroy": [_VP],
+    "tucker_autotune_enable": [_INT],
+    "tucker_autotune_count": [],
+    "tucker_autotune_entry": [_I64],
     "tucker_launch_count": [],
     "tucker_profile_enable": [_INT],
     "tucker_profile_read": [_INT, _P(_I64), _P(_DBL), _P(_DBL), _P(_DBL)],
 }
 _RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int64,
-             "tucker_last_cuda_error": C.c_char_p}
+             "tucker_last_cuda_error": C.c_char_p, "tucker_autotune_count": C.c_int64,
+             "tucker_autotune_entry": C.c_char_p}
 KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3, "extract": 4, "sample": 5}
 
 
@@ -357,6 +361,17 @@ def relative_error(A, dims, ranks, U, G, stream=None):
 
 
 # ---------------------------------------------------------------- measurement
+def autotune_enable(on: bool = True):
+    """Turn the library's autotuner on or off (tucker_autotune_enable)."""
+    _check("tucker_autotune_enable", lib().tucker_autotune_enable(1 if on else 0))
+
+
+def autotune_entries():
+    """One line per tuned shape class: the class, its choice, the candidates' times."""
+    L = lib()
+    return [L.tucker_autotune_entry(k).decode() for k in range(L.tucker_autotune_count())]
+
+
 def launch_count() -> int:
     """Kernel launches the library has made so far in this process."""
     return int(lib().tucker_launch_count())

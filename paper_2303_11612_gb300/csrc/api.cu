@@ -369,6 +369,7 @@ tucker_status driver(bool st, const void* A, tucker_dtype dt, const int64_t* dim
     // asynchronous calls take device buffers as given (no driver queries, so the
     // call can be captured into a CUDA graph); synchronous calls stage host buffers
     const bool async = (o.flags & TUCKER_FLAG_ASYNC) != 0;
+    TuneAllow tune(!async);                // a synchronous call may time kernel candidates
     const bool hA = !async && !on_device(A), hG = !async && !on_device(G);
     bool hU = false;
     for (int n = 0; n < N && !async; ++n) hU = hU || !on_device(U[n]);
@@ -560,6 +561,7 @@ tucker_status tucker_power_step(const void* A, tucker_dtype dt, const int64_t* d
     if (rs != TUCKER_OK) return rs;
     if (!mode_args_ok(A, dims, N, mode) || !X_in || !X_out || L < 1) return TUCKER_ERR_INVALID_ARG;
     if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    TuneAllow tune((o.flags & TUCKER_FLAG_ASYNC) == 0);
     const ModeView v = view_of(dims, N, mode);
     const int elem = dt == TUCKER_F64 ? 8 : 4;
     if (v.i > kMaxI || L > 4096 || (elem == 8 && v.i > 512)) return TUCKER_ERR_UNSUPPORTED;
@@ -711,6 +713,7 @@ tucker_status tucker_ttm(const void* A, tucker_dtype dt, const int64_t* dims, in
     // M(k, i): transpose == 0: M_ptr is K x I_n (col-major) -> M_ptr[k + i K]
     //          transpose == 1: M_ptr is I_n x K               -> M_ptr[i + k I_n]
     const int64_t ld_i = transpose ? 1 : K, ld_k = transpose ? v.i : 1;
+    TuneAllow tune(true);
     Scratch sc;
     if ((rs = sc.get(256, o.stream)) != TUCKER_OK) return rs;
     if (cudaMemsetAsync(sc.p, 0, sizeof(int), o.stream) != cudaSuccess) return from_cuda(cudaGetLastError());

@@ -1,6 +1,10 @@
 // Host-side launchers shared between the translation units of the library.
 #pragma once
 
+#include <functional>
+#include <string>
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -123,4 +127,29 @@ class ProfScope {
     void* b_ = nullptr;
 };
 
+// ---- autotuner (autotune.cu)
+enum TuneSite : int { kTuneTtm = 0, kTunePower = 1 };
+struct TuneKey {
+    int site;
+    int64_t k[4];
+};
+bool operator<(const TuneKey& a, const TuneKey& b);
+// Marks the calling thread as inside a synchronous library call (tuning may
+// synchronise its stream) for the object's lifetime.
+class TuneAllow {
+public:
+    explicit TuneAllow(bool allow);
+    ~TuneAllow();
+    TuneAllow(const TuneAllow&) = delete;
+    TuneAllow& operator=(const TuneAllow&) = delete;
+private:
+    bool on_;
+};
+bool tune_active(cudaStream_t s);
+int tune_get(const TuneKey& k);            // the kept choice, or -1
+// Times every candidate (warm-up + one timed launch), keeps and returns the fastest.
+int tune_pick(cudaStream_t s, const TuneKey& key, const char* what, const std::vector<std::string>& names,
+              const std::function<cudaError_t(int)>& launch_candidate, int fallback);
+
 }  // namespace tk
+

@@ -9,6 +9,10 @@
 // so every element of A is read once per power step. Each CTA accumulates the
 // tiles it owns and writes one partial; a second kernel sums the partials in a
 // fixed order, which makes the result independent of scheduling.
+#include <string>
+#include <utility>
+#include <vector>
+
 #include "internal.h"
 
 namespace tk {
@@ -249,10 +253,70 @@ cudaError_t dispatch_kr(const T* A, const ModeView& v, const T* X_in, int L, T* 
 }
 }  // namespace
 
+namespace {
+// The plan with tile shape (jb, lg): more fiber groups share the SMs, so the
+// number of partials (and their memory) never exceeds the base plan's.
+PowerPlan plan_with(const PowerPlan& base, const ModeView& v, int L, int jb, int lg) {
+    PowerPlan p = base;
+    p.jb = jb;
+    p.lg = lg;
+    p.groups = (L + lg - 1) / lg;
+    p.tiles = (v.fibers() + jb - 1) / jb;
+    int64_t parts = (int64_t)base.parts * base.groups / p.groups;
+    if (parts < 1) parts = 1;
+    if (parts > p.tiles) parts = p.tiles;
+    if (parts > base.parts) parts = base.parts;
+    p.parts = (int)parts;
+    return p;
+}
+}  // namespace
+
+template <typename T>
+cudaError_t launch_power_plan(const T* A, const ModeView& v, const T* X_in, int L, T* X_out, void* partials,
+                              const PowerPlan& plan, bool range, uint64_t seed, uint32_t stream_id, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_power(const T* A, const ModeView& v, const T* X_in, int L, T* X_out, void* partials,
                          const PowerPlan& plan, bool range, uint64_t seed, uint32_t stream_id,
                          cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the autotuner may pick another tile shape (jb fibers x lg columns)
+        // for this shape class; shapes differ in summation order, so a tuned run
+        // can differ from an untuned one in the last bits
+        std::vector<std::pair<int, int>> shapes;
+        std::vector<std::string> names;
+        for (auto jl : {std::pair<int, int>{32, 32}, {32, 16}, {16, 16}, {32, 8}, {16, 8}}) {
+            if (jl.second > plan.lg || (jl.first == 32 && v.i > 512)) continue;
+            shapes.push_back(jl);
+            names.push_back("jb" + std::to_string(jl.first) + "/lg" + std::to_string(jl.second));
+        }
+        const TuneKey key{kTunePower, {v.i, L, v.lf * (range ? -1 : 1), v.fibers()}};
+        int choice = tune_get(key);
+        if (choice < 0 && shapes.size() > 1 && tune_active(s)) {
+            int base = 0;
+            for (size_t c = 0; c < shapes.size(); ++c)
+                if (shapes[c].first == plan.jb && shapes[c].second == plan.lg) base = (int)c;
+            choice = tune_pick(
+                s, key, "FP32 power step (I, L, +-L_f, J)", names,
+                [&](int c) {
+                    return launch_power_plan<T>(A, v, X_in, L, X_out, partials,
+                                                plan_with(plan, v, L, shapes[c].first, shapes[c].second), range,
+                                                seed, stream_id, s);
+                },
+                base);
+        }
+        if (choice >= 0 && choice < (int)shapes.size())
+            return launch_power_plan<T>(A, v, X_in, L, X_out, partials,
+                                        plan_with(plan, v, L, shapes[choice].first, shapes[choice].second), range,
+                                        seed, stream_id, s);
+    }
+    return launch_power_plan<T>(A, v, X_in, L, X_out, partials, plan, range, seed, stream_id, s);
+}
+
+template <typename T>
+cudaError_t launch_power_plan(const T* A, const ModeView& v, const T* X_in, int L, T* X_out, void* partials,
+                              const PowerPlan& plan, bool range, uint64_t seed, uint32_t stream_id,
+                              cudaStream_t s) {
     T* part = reinterpret_cast<T*>(partials);
     cudaError_t e;
     if constexpr (sizeof(T) == 8) {

@@ -160,22 +160,23 @@ __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeVi
 // (contiguous fibers: 128 fibers of the mode-1 view; strided fibers: 128
 // consecutive l of one slab t, the last tile of a slab partly beyond L_f) and
 // OB = 4 OPT outputs. The fiber tile arrives in chunks of 32 input indices
-// (16 KB) by cp.async.bulk.tensor into a ring of 2 shared-memory stages; the
-// CTA's block of M stays in shared memory. Two stages keep a CTA near 66 KB so
-// three fit on an SM: the kernel is bound by issue (20 multiply-adds per
-// element at K_out = 20), and occupancy beat deeper staging when measured
-// (4 stages: 0.151 ms, 2 stages: 0.137 ms on a 400^3 mode-2 product). Contiguous fibers land 128B-swizzled (16-byte chunk
+// (16 KB) by cp.async.bulk.tensor into a ring of 2 or 3 shared-memory stages
+// (the autotuner picks; 2 by default); the CTA's block of M stays in shared
+// memory. Two stages keep a CTA near 66 KB so three fit on an SM: the kernel is
+// bound by issue (20 multiply-adds per element at K_out = 20), and occupancy
+// beat deeper staging when measured (4 stages: 0.151 ms, 2 stages: 0.137 ms on
+// a 400^3 mode-2 product). Contiguous fibers land 128B-swizzled (16-byte chunk
 // c of fiber row r at chunk c ^ (r % 8)), so the four-index reads of eight
 // neighbouring fibers hit distinct banks; strided fibers land index-major.
 // One thread waits (bounded) on each stage's mbarrier and refills the stage
 // once every thread has read it; out-of-range indices and fibers load as 0.
-constexpr int kTJB = 128, kTKC = 32, kTStages = 2;
+constexpr int kTJB = 128, kTKC = 32;
 constexpr uint32_t kTStageBytes = kTJB * kTKC * 4;
 constexpr int kTWaitIters = 1 << 24;
 
 __host__ __device__ inline int tma_ipad(int I) { return (I + kTKC - 1) / kTKC * kTKC; }
 
-template <int OPT, bool CONTIG>
+template <int OPT, bool CONTIG, int kTStages>
 __global__ void __launch_bounds__(kT, 3) ttm_tma_kernel(const __grid_constant__ CUtensorMap map, ModeView v,
                                                         const float* __restrict__ Mp, int64_t K_out, int64_t ld_i,
                                                         int64_t ld_k, float* __restrict__ out, int64_t tiles_per_t,
@@ -300,13 +301,13 @@ __global__ void __launch_bounds__(kT, 3) ttm_tma_kernel(const __grid_constant__ 
     }
 }
 
-size_t ttm_tma_smem(int I, int OPT) {
-    return 1024 + (size_t)kTStages * kTStageBytes + (size_t)4 * OPT * tma_ipad(I) * sizeof(float) + 8 * kTStages;
+size_t ttm_tma_smem(int I, int OPT, int stages) {
+    return 1024 + (size_t)stages * kTStageBytes + (size_t)4 * OPT * tma_ipad(I) * sizeof(float) + 8 * stages;
 }
 
 // Encodes the tile map and launches; false when the shape or alignment does not
 // suit the TMA path (the caller then runs ttm_kernel).
-template <int OPT>
+template <int OPT, int STAGES>
 bool launch_ttm_tma_t(const float* A, const ModeView& v, const float* Mp, int64_t K_out, int64_t ld_i, int64_t ld_k,
                       float* out, int* status, cudaStream_t s, cudaError_t* err) {
     const bool contig = v.lf == 1;
@@ -328,15 +329,17 @@ bool launch_ttm_tma_t(const float* A, const ModeView& v, const float* Mp, int64_
         tiles_per_t = (v.lf + kTJB - 1) / kTJB;
         tiles = tiles_per_t * v.rt;
     }
-    const size_t smem = ttm_tma_smem((int)v.i, OPT);
+    const size_t smem = ttm_tma_smem((int)v.i, OPT, STAGES);
     if (!ok || smem > 200 * 1024 || tiles > 0x7fffffff) return false;
     dim3 grid((unsigned)tiles, (unsigned)((K_out + 4 * OPT - 1) / (4 * OPT)));
     if (contig) {
-        cudaFuncSetAttribute(ttm_tma_kernel<OPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        ttm_tma_kernel<OPT, true><<<grid, kT, smem, s>>>(map, v, Mp, K_out, ld_i, ld_k, out, tiles_per_t, status);
+        auto k = ttm_tma_kernel<OPT, true, STAGES>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kT, smem, s>>>(map, v, Mp, K_out, ld_i, ld_k, out, tiles_per_t, status);
     } else {
-        cudaFuncSetAttribute(ttm_tma_kernel<OPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        ttm_tma_kernel<OPT, false><<<grid, kT, smem, s>>>(map, v, Mp, K_out, ld_i, ld_k, out, tiles_per_t, status);
+        auto k = ttm_tma_kernel<OPT, false, STAGES>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kT, smem, s>>>(map, v, Mp, K_out, ld_i, ld_k, out, tiles_per_t, status);
     }
     note_launch();
     *err = cudaGetLastError();
@@ -405,40 +408,56 @@ cudaError_t launch_ttm(const T* A, const ModeView& v, const T* Mp, int64_t K_out
     dim3 grid((unsigned)((J + JBl - 1) / JBl), (unsigned)((K_out + OB - 1) / OB));
     const double ein = (double)v.i * (double)J, eout = (double)K_out * (double)J;
     ProfScope prof(kKTtm, (ein + eout) * sizeof(T), 2.0 * ein * (double)K_out, s);
+    auto run_register = [&]() -> cudaError_t {
+        switch (OPT) {
+            case 1: ttm_kernel<T, 1, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+            case 2: ttm_kernel<T, 2, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+            case 3: ttm_kernel<T, 3, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+            case 4: ttm_kernel<T, 4, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+            case 5: ttm_kernel<T, 5, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+            case 6: ttm_kernel<T, 6, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+            case 8: ttm_kernel<T, 8, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+            case 12: ttm_kernel<T, 12, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+            default: ttm_kernel<T, 16, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
+        }
+        note_launch();
+        return cudaGetLastError();
+    };
     if constexpr (sizeof(T) == 4) {
         // FP32 with a status word for the bounded waits: the TMA-fed kernel where
-        // the shape and alignment allow it
+        // the shape and alignment allow it (2 stages unless the tuner chose else)
         if (status && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
-            cudaError_t e = cudaSuccess;
-            bool used = false;
-            switch (OPT) {
-                case 1: used = launch_ttm_tma_t<1>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, &e); break;
-                case 2: used = launch_ttm_tma_t<2>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, &e); break;
-                case 3: used = launch_ttm_tma_t<3>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, &e); break;
-                case 4: used = launch_ttm_tma_t<4>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, &e); break;
-                case 5: used = launch_ttm_tma_t<5>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, &e); break;
-                case 6: used = launch_ttm_tma_t<6>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, &e); break;
-                case 8: used = launch_ttm_tma_t<8>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, &e); break;
-                case 12: used = launch_ttm_tma_t<12>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, &e); break;
-                default: used = launch_ttm_tma_t<16>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, &e); break;
-            }
-            if (used) return e;
+            auto run_tma = [&](int stages, cudaError_t* e) -> bool {
+#define TK_TMA_CASE(O)                                                                                        \
+    case O:                                                                                                   \
+        return stages == 3 ? launch_ttm_tma_t<O, 3>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, e)          \
+                           : launch_ttm_tma_t<O, 2>(A, v, Mp, K_out, ld_i, ld_k, out, status, s, e);
+                switch (OPT) {
+                    TK_TMA_CASE(1) TK_TMA_CASE(2) TK_TMA_CASE(3) TK_TMA_CASE(4) TK_TMA_CASE(5)
+                    TK_TMA_CASE(6) TK_TMA_CASE(8) TK_TMA_CASE(12)
+                    default: TK_TMA_CASE(16)
+                }
+#undef TK_TMA_CASE
+            };
+            // candidates: 0 register-staged, 1 TMA 2 stages, 2 TMA 3 stages (same results)
+            auto run = [&](int c) -> cudaError_t {
+                if (c == 0) return run_register();
+                cudaError_t e = cudaSuccess;
+                return run_tma(c == 1 ? 2 : 3, &e) ? e : cudaErrorNotSupported;
+            };
+            const TuneKey key{kTuneTtm, {v.i, K_out, v.lf, J}};
+            int choice = tune_get(key);
+            if (choice < 0 && tune_active(s))
+                choice = tune_pick(s, key, "mode-n product (I, K_out, L_f, J)", {"register", "tma2", "tma3"}, run, 1);
+            if (choice < 0) choice = 1;
+            const cudaError_t e = run(choice);
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();
         }
     }
-    switch (OPT) {
-        case 1: ttm_kernel<T, 1, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        case 2: ttm_kernel<T, 2, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        case 3: ttm_kernel<T, 3, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        case 4: ttm_kernel<T, 4, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        case 5: ttm_kernel<T, 5, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        case 6: ttm_kernel<T, 6, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        case 8: ttm_kernel<T, 8, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        case 12: ttm_kernel<T, 12, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-        default: ttm_kernel<T, 16, NF><<<grid, kT, 0, s>>>(A, v, Mp, K_out, ld_i, ld_k, out); break;
-    }
-    note_launch();
-    return cudaGetLastError();
+    return run_register();
 }
+
 
 size_t sumsq_scratch_bytes() { return sizeof(double) * kSumBlocks + 256; }
 
