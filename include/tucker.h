@@ -307,6 +307,32 @@ tucker_status tucker_server_stats_get(tucker_server* srv, tucker_server_stats* o
 /* Waits for every submitted request, then releases the server. */
 tucker_status tucker_server_destroy(tucker_server* srv);
 
+/* ---------------------------------------------------------------- batches
+ * Not part of the paper's method: many independent decompositions (Algorithms
+ * 1, 2, 4, 5 with any shapes and parameters each) launched together as one CUDA
+ * graph. The requests use the tucker_request layout with DEVICE buffers only.
+ * The first call with a given signature - n, every request's fields and buffer
+ * addresses, opts->form, opts->prec, the workspace pointer and size - captures
+ * the requests' asynchronous launch sequences, each on its own stream, into one
+ * graph; a later call with the same signature replays that graph with one
+ * launch (the 16 most recently used graphs are kept). The graph runs after the
+ * work already on opts->stream and before what is enqueued there next. Each
+ * request's results are bitwise those of the same request run alone. */
+
+/* Device workspace bytes (256-byte aligned per request) a batch needs; opts
+ * may be NULL (paper form, FP32). */
+tucker_status tucker_batch_workspace_size(int n, const tucker_request* reqs, const tucker_opts* opts,
+                                          size_t* bytes);
+
+/* Runs n >= 1 requests. opts is required: opts->workspace must be device
+ * memory of tucker_batch_workspace_size() bytes; opts->stream orders the batch;
+ * rel_error and sample_idx are ignored. Without TUCKER_FLAG_ASYNC the call
+ * synchronises opts->stream and returns the first failing request's device
+ * status (TUCKER_ERR_TIMEOUT before TUCKER_ERR_NUMERICAL); with it, it returns
+ * after enqueueing, and request k's status word is the first 4 bytes of its
+ * workspace slice. Argument errors of any request return before any launch. */
+tucker_status tucker_batch_run(int n, const tucker_request* reqs, const tucker_opts* opts);
+
 /* ---------------------------------------------------------------- autotuning
  * Not part of the paper's method. When enabled, the first synchronous call
  * (never an asynchronous one, never under stream capture) that meets a new

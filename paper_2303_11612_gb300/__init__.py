@@ -11,7 +11,7 @@ from ._binding import (  # noqa: F401
     TuckerError, decompose, rthosvd, rsthosvd, workspace_size, factor_tensor, gaussian, power_step,
     range_sketch, fiber_norms, quantize_weights, sample_fibers, gather_fibers, leading_factor, ttm,
     relative_error, last_device_status, lib, exported_symbols, FLAG_ASYNC, launch_count, profile_enable,
-    profile_read, Server, autotune_enable, autotune_entries,
+    profile_read, Server, Batch, autotune_enable, autotune_entries,
 )
 
-__all__ = ["rthosvd", "rsthosvd", "decompose", "workspace_size", "TuckerError", "Server"]
+__all__ = ["rthosvd", "rsthosvd", "decompose", "workspace_size", "TuckerError", "Server", "Batch"]

@@ -87,6 +87,8 @@ _SIGS = {
     "tucker_server_wait": [_VP, _U64, _I64, _P(_INT)],
     "tucker_server_stats_get": [_VP, _P(ServerStats)],
     "tucker_server_destroy": [_VP],
+    "tucker_batch_workspace_size": [_INT, _VP, _P(Opts), _P(C.c_size_t)],
+    "tucker_batch_run": [_INT, _VP, _P(Opts)],
     "tucker_autotune_enable": [_INT],
     "tucker_autotune_count": [],
     "tucker_autotune_entry": [_I64],
@@ -467,3 +469,46 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Many independent decompositions launched as one CUDA graph
+    (tucker_batch_*). ``requests`` is a list of dicts with keys which ("T" or
+    "ST"), A (device tensor), dims, ranks and optionally P, q, c, prob, seed.
+    Outputs and the workspace are allocated here, once; ``run`` launches the
+    whole batch (captured on the first run, replayed afterwards) and returns the
+    list of (U, G). Inputs may be rewritten in place between runs."""
+
+    def __init__(self, requests, form="paper", prec="fp32"):
+        self._keep = []
+        self.outputs = []
+        arr = (Request * len(requests))()
+        for k, r in enumerate(requests):
+            A = r["A"]
+            dims = [int(d) for d in r["dims"]]
+            ranks = [int(x) for x in r["ranks"]]
+            if A.numel() != int(torch.tensor(dims).prod()):
+                raise ValueError("A.numel() must equal prod(dims)")
+            U = [factor_tensor(I, R, A.dtype, A.device) for I, R in zip(dims, ranks)]
+            G = torch.empty(int(torch.tensor(ranks).prod()), dtype=A.dtype, device=A.device)
+            d64, r32 = _i64(dims), _i32(ranks)
+            Up = (C.c_void_p * len(dims))(*[u.data_ptr() for u in U])
+            arr[k] = Request(C.sizeof(Request), 0 if r["which"] == "T" else 1, _dt(A), A.data_ptr(), d64, len(dims),
+                             r32, int(r.get("P", 5)), int(r.get("q", 1)), int(r.get("c", 0)),
+                             PROB[r.get("prob", "uniform")], int(r.get("seed", 0)) & (2**64 - 1), Up, G.data_ptr())
+            self._keep.append((A, d64, r32, Up))
+            self.outputs.append((U, G))
+        self._reqs = arr
+        self._n = len(requests)
+        self._form, self._prec = form, prec
+        n = C.c_size_t(0)
+        o = make_opts(form=form, prec=prec)
+        _check("tucker_batch_workspace_size",
+               lib().tucker_batch_workspace_size(self._n, C.cast(arr, C.c_void_p), C.byref(o), C.byref(n)))
+        self.workspace = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=requests[0]["A"].device)
+
+    def run(self, stream=None, sync=True):
+        o = make_opts(form=self._form, prec=self._prec, stream=stream, workspace=self.workspace,
+                      flags=0 if sync else FLAG_ASYNC)
+        _check("tucker_batch_run", lib().tucker_batch_run(self._n, C.cast(self._reqs, C.c_void_p), C.byref(o)))
+        return self.outputs

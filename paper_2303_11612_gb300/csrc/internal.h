@@ -113,6 +113,7 @@ int num_sms();
 enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKExtract = 4, kKSample = 5,
                    kKernelClasses = 6 };
 void note_launch();
+void note_launches(int64_t n);   // a graph replay's kernels
 void profile_drain();
 // Brackets one launch with CUDA events when profiling is on.
 class ProfScope {

@@ -44,6 +44,7 @@ cudaEvent_t get_event() {
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(int cls, double bytes, double flops, cudaStream_t s)
     : cls_(cls), bytes_(bytes), flops_(flops), s_(s) {
