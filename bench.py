@@ -44,6 +44,15 @@ VARIANTS = [
     dict(name="hilbert_q1_amm4000_uniform", tensor="hilbert", q=1, c=4000, prob="uniform"),
 ]
 BASELINE_METRIC = "decomps/s & sketch HBM GB/s, BF16 vs FP32 at equal rel err; serving p50/p99 ms"
+PROFILED = ("power", "power_bf16", "power_tf32", "ttm", "gather", "norms", "extract", "sample")
+# the dominant kernel of each form: (profiler class, name, source file, traffic.json key)
+DOMINANT = {
+    "tf32": ("power_tf32", "power_tf32_kernel (fused A(A^T X) pass, tcgen05 kind::tf32, TMA-fed, fp32 accumulate)",
+             "kernels_tf32.cu", "power_tf32_kernel_400cubed"),
+    "bf16": ("power_bf16", "power_tc_kernel (fused A(A^T X) pass, tcgen05 split bf16, fp32 accumulate)",
+             "kernels_tc.cu", "power_tc_kernel_400cubed"),
+    "fp32": ("power", "power_kernel (fused A(A^T X) pass, FP32 FFMA)", "kernels_sketch.cu", "power_kernel_400cubed"),
+}
 WORKLOAD = ("randomized ST-HOSVD, 400x400x400 FP32 (Tucker core 20^3 + 1e-2 noise, and Hilbert), "
             "R=20 P=10, variants: q=1; q=1 AMM c=4000 nearly-optimal; Hilbert q=2; Hilbert q=1 AMM c=4000 uniform")
 
@@ -269,8 +278,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prec", default="both", choices=["both", "bf16", "fp32"],
-                    help="sketch arithmetic to time (both: bf16 is the headline when its RE matches)")
+    ap.add_argument("--prec", default="all", choices=["all", "tf32", "bf16", "fp32"],
+                    help="sketch arithmetic to time (all: the headline is the fastest form whose relative "
+                         "errors are within 1e-3 of FP32's)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel configurations (no tuning in the synchronous warm-up calls)")
@@ -299,7 +309,7 @@ def main():
     if args.single:
         v = next(x for x in VARIANTS if x["name"] == args.single)
         A = torch.from_numpy(host[v["tensor"]]).cuda()
-        prec = "fp32" if args.prec == "fp32" else "bf16"
+        prec = "tf32" if args.prec == "all" else args.prec
         for _ in range(2):
             tk.rsthosvd(A, DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED, prec=prec)
         torch.cuda.synchronize()
@@ -307,13 +317,12 @@ def main():
         return 0
     if not args.no_autotune:
         # the synchronous accuracy checks below meet every shape class first and
-        # tune it; the graph-captured steps then reuse the kept choices
+        # tune it; the graph-captured batch steps then reuse the kept choices
         tk.autotune_enable(True)
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
     main_s = torch.cuda.Stream()
     batch = [v for v in VARIANTS for _ in range(args.copies)]
-    side = [torch.cuda.Stream() for _ in batch]
 
     def barrier():
         rank_barrier(dist, torch, cuda=True)
@@ -326,103 +335,76 @@ def main():
 
     def measure(prec):
         """Graph-timed throughput of the batch with one sketch arithmetic."""
-        # one stream, workspace and output set per variant: the four decompositions of
-        # a step run concurrently (fork from the main stream, join back into it)
-        wss = [torch.empty(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"], prec=prec),
-                           dtype=torch.uint8, device="cuda") for v in batch]
-        outs = [([tk.factor_tensor(I, R, torch.float32, "cuda") for I, R in zip(DIMS, RANKS)],
-                 torch.empty(int(np.prod(RANKS)), dtype=torch.float32, device="cuda")) for _ in batch]
-
-        def enqueue_step():
-            for st in side:
-                st.wait_stream(main_s)
-            for v, st, ws, out in zip(batch, side, wss, outs):
-                tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
-                            workspace=ws, stream=st, out=out, flags=tk.FLAG_ASYNC, prec=prec)
-            for st in side:
-                main_s.wait_stream(st)
-
         # accuracy of what is timed: explicit relative error of every variant
         res = {}
         for v in VARIANTS:
             U, G = tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
                                prec=prec)
             res[v["name"]] = tk.relative_error(dev[v["tensor"]], DIMS, RANKS, U, G)
-        with torch.cuda.stream(main_s):
-            for _ in range(args.warmup):
-                enqueue_step()
+        # the timed path: the library's batch call, which captures the whole step
+        # (every decomposition on its own stream) into one CUDA graph on its first
+        # run and replays it afterwards
+        bt = tk.Batch([dict(which="ST", A=dev[v["tensor"]], dims=DIMS, ranks=RANKS, P=P, q=v["q"], c=v["c"],
+                            prob=v["prob"], seed=SEED) for v in batch], prec=prec)
+        for _ in range(args.warmup):
+            bt.run(stream=main_s, sync=False)
         main_s.synchronize()
-        if tk.last_device_status() != 0:
-            raise RuntimeError("device status not OK after warm-up")
-        n0 = tk.launch_count()
-        with torch.cuda.stream(main_s):
-            enqueue_step()
-        main_s.synchronize()
-        per_step = tk.launch_count() - n0
-        graph = None
-        try:
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=main_s):
-                enqueue_step()
-            graph = g
-            with torch.cuda.stream(main_s):
-                graph.replay()
-            main_s.synchronize()
-        except Exception as exc:  # noqa: BLE001
-            print(f"graph capture unavailable ({exc}); timing eager launches", file=sys.stderr)
-            graph = None
+        bt.run(stream=main_s)                               # synchronous: raises on a device status
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         n0 = tk.launch_count()
-        with torch.cuda.stream(main_s):
-            ev0.record(main_s)
-            for _ in range(args.steps):
-                if graph is not None:
-                    graph.replay()
-                else:
-                    enqueue_step()
-            ev1.record(main_s)
+        ev0.record(main_s)
+        for _ in range(args.steps):
+            bt.run(stream=main_s, sync=False)
+        ev1.record(main_s)
         main_s.synchronize()
         n1 = tk.launch_count()
         barrier()
-        if tk.last_device_status() != 0:
+        if any(bt.status()):
             raise RuntimeError("device status not OK in the timed region")
         ms = max_over_ranks(ev0.elapsed_time(ev1))
+        del bt
         # per-kernel durations: event pairs inside a graph carry no timings, so they
-        # come from eager steps run right after the timed region (same streams)
+        # come from eager decompositions run right after the timed region, one at a
+        # time on one stream (each kernel has the GPU to itself, as in a serialised
+        # launch list)
+        wss = [torch.empty(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"], prec=prec),
+                           dtype=torch.uint8, device="cuda") for v in VARIANTS]
+        outs = [([tk.factor_tensor(I, R, torch.float32, "cuda") for I, R in zip(DIMS, RANKS)],
+                 torch.empty(int(np.prod(RANKS)), dtype=torch.float32, device="cuda")) for _ in VARIANTS]
         tk.profile_enable(True)
-        with torch.cuda.stream(main_s):
-            for _ in range(max(3, args.steps // 10)):
-                enqueue_step()
+        for _ in range(max(3, args.steps // 10)):
+            for v, ws, out in zip(VARIANTS, wss, outs):
+                tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
+                            workspace=ws, stream=main_s, out=out, flags=tk.FLAG_ASYNC, prec=prec)
         main_s.synchronize()
-        prof = {k: tk.profile_read(k) for k in ("power", "ttm", "gather", "norms", "extract", "sample")}
+        prof = {k: tk.profile_read(k) for k in PROFILED}
         tk.profile_enable(False)
-        del graph
+        if tk.last_device_status() != 0:
+            raise RuntimeError("device status not OK in the profiled decompositions")
         return {"prec": prec, "ms": ms, "value": whole_job_rate(len(batch) * args.steps, world, ms / 1e3),
-                "gpu_launches": (n1 - n0) if n1 - n0 > 0 else per_step * args.steps,
-                "graph": True, "rel_error": res, "prof": prof}
+                "gpu_launches": n1 - n0, "graph": True, "rel_error": res, "prof": prof}
 
     forms = {}
-    for prec in (["bf16", "fp32"] if args.prec == "both" else [args.prec]):
+    for prec in (["tf32", "bf16", "fp32"] if args.prec == "all" else [args.prec]):
         forms[prec] = measure(prec)
     clk = clocks.stop()
+    # headline: the fastest form whose relative error matches FP32's within 1e-3 on every variant
+    def matches(f):
+        return "fp32" not in forms or all(abs(f["rel_error"][k] - forms["fp32"]["rel_error"][k]) <= 1e-3
+                                          for k in forms["fp32"]["rel_error"])
+    equal = {p: matches(f) for p, f in forms.items()}
+    head = max((f for p, f in forms.items() if equal[p]), key=lambda f: f["value"])
     serving = None
     if not args.no_serving:
         reqs = serving_requests(torch)
-        serving = {p: serving_bench(tk, torch, reqs, p) for p in (["bf16", "fp32"] if args.prec == "both"
-                                                                  else [args.prec])}
+        serving = {p: serving_bench(tk, torch, reqs, p) for p in dict.fromkeys([head["prec"], "fp32"])
+                   if p in forms}
         serving["sample"] = (f"{len(reqs)} randomized ST-HOSVD requests (P=5, q=1), orders 3/4, extents U{{32..256}} "
                              f"(order 3) / U{{32..96}} (order 4), ranks U{{4..32}}, low-rank + 1e-2 noise, device-"
                              f"resident; budget {SERVE_BUDGET >> 30} GB, 16 streams; latencies at 0.7x the "
                              f"saturation throughput, Poisson arrivals")
         del reqs
-    if "bf16" in forms and "fp32" in forms:
-        equal = all(abs(forms["bf16"]["rel_error"][k] - forms["fp32"]["rel_error"][k]) <= 1e-3
-                    for k in forms["fp32"]["rel_error"])
-        head = forms["bf16"] if equal else forms["fp32"]
-    else:
-        equal = None
-        head = next(iter(forms.values()))
 
     # end to end through the public API with pinned host buffers, headline arithmetic:
     # every step submits the whole batch to the library's request loop, which
@@ -457,25 +439,21 @@ def main():
         e2e = {"value": None, "unit": "decomps/s", "error": str(exc)}
 
     peaks, peak_kind = load_peaks()
-    pw_n, pw_ms, pw_bytes, pw_flops = head["prof"]["power"]
+    pclass, pname, src_file, tkey = DOMINANT[head["prec"]]
+    pw_n, pw_ms, pw_bytes, pw_flops = head["prof"][pclass]
     achieved_gbs = pw_bytes / (pw_ms / 1e3) / 1e9 if pw_ms > 0 else 0.0
     achieved_tflops = pw_flops / (pw_ms / 1e3) / 1e12 if pw_ms > 0 else 0.0
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if head["prec"] == "bf16":
+    if head["prec"] in ("bf16", "tf32"):
         # bandwidth-bound: 4 L flops per 4-byte element is ~30 flops/byte, far below the
-        # bf16 tensor ridge (~285 flops/byte), so the bound is HBM
+        # tensor ridge (bf16 ~285, tf32 ~140 flops/byte), so the bound is HBM
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved_gbs / peaks["hbm_gbs"],
-                    "kernel": "power_tc_kernel (fused A(A^T X) pass, tcgen05 bf16, fp32 accumulate)",
-                    "tensor_tflops": achieved_tflops}
-        src_file, tkey = "kernels_tc.cu", "power_tc_kernel_400cubed"
+                    "frac": achieved_gbs / peaks["hbm_gbs"], "kernel": pname, "tensor_tflops": achieved_tflops}
     else:
         fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": achieved_tflops / fp32_peak,
-                    "kernel": "power_kernel (fused A(A^T X) pass, FP32 FFMA)",
+                    "frac": achieved_tflops / fp32_peak, "kernel": pname,
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz", "hbm_gbs": achieved_gbs}
-        src_file, tkey = "kernels_sketch.cu", "power_kernel_400cubed"
     traffic = None
     try:
         import hashlib
@@ -489,10 +467,12 @@ def main():
         traffic = None
     roofline.update({"traffic": traffic, "launches": pw_n, "ms_per_launch": pw_ms / max(pw_n, 1),
                      "algorithmic_bytes_per_launch": pw_bytes / max(pw_n, 1), "peak_kind": peak_kind,
-                     "timing": "eager profiled steps right after the graph-timed region, same streams and "
-                               "concurrency (CUDA-graph event nodes carry no timings)"})
+                     "timing": "CUDA events around each launch in eager decompositions run one at a time on "
+                               "one stream right after the graph-timed region (graph event nodes carry no timings)"})
     kernels = {}
-    for k in ("ttm", "gather", "norms", "extract", "sample"):
+    for k in PROFILED:
+        if k == pclass:
+            continue
         n, kms, b, f = head["prof"][k]
         if n:
             kernels[k] = {"launches": n, "ms_per_launch": kms / n}
@@ -506,15 +486,18 @@ def main():
                        "l2": "inputs larger than L2 (256 MB per tensor), no flush",
                        "parallelism": "replicas (each rank decomposes its own batch)" if world > 1 else "single GPU",
                        "sketch": f"paper form, {head['prec']} power steps "
-                                 + ("(tcgen05 tensor cores, fp32 accumulate)" if head["prec"] == "bf16"
-                                    else "(FP32 FFMA)"),
-                       "execution": f"CUDA graph of one step: {len(batch)} decompositions ({args.copies} of each "
-                                    f"variant, inputs shared read-only) on {len(batch)} streams"},
+                                 + {"tf32": "(tcgen05 kind::tf32 on mode 1, split bf16 on modes 2-3, fp32 "
+                                            "accumulate)",
+                                    "bf16": "(tcgen05 split bf16, fp32 accumulate)",
+                                    "fp32": "(FP32 FFMA)"}[head["prec"]],
+                       "execution": f"tucker_batch_run per step: one CUDA graph (captured by the library on its "
+                                    f"first run, replayed after) of {len(batch)} decompositions ({args.copies} of "
+                                    f"each variant, inputs shared read-only) on {len(batch)} streams"},
             "e2e": e2e, "gpu_launches": head["gpu_launches"], "roofline": roofline, "kernels": kernels,
             "sketch_hbm_gbs": achieved_gbs,
             "forms": {p: {"value": f["value"], "ms_per_step": f["ms"] / args.steps, "rel_error": f["rel_error"]}
                       for p, f in forms.items()},
-            "bf16_matches_fp32_rel_err_within_1e-3": equal,
+            "matches_fp32_rel_err_within_1e-3": equal,
             "serving": serving,
             "autotune": tk.autotune_entries(),
             "clocks": clk}

@@ -84,11 +84,18 @@ typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1 } tucker_form;
 
 /* Arithmetic of the sketch / power products.
  *  FP32: exact FP32 FMA on the CUDA cores.
- *  TF32: not built (TUCKER_ERR_UNSUPPORTED).
+ *  TF32: tcgen05 tensor cores, kind::tf32, FP32 accumulation: A is read once by
+ *    TMA, in FP32, straight into the tensor cores' operand layout, which use its
+ *    top 19 bits (TF32, about 2^-11 relative), as for X and A^T X. Used for
+ *    contiguous fibers (mode 1, or an AMM sample) with I_n % 4 == 0,
+ *    I_n <= 512, L_n <= 32 and A 16-byte aligned; other modes take the BF16
+ *    form where it fits, else FP32. tucker_power_step returns
+ *    TUCKER_ERR_UNSUPPORTED outside those limits.
  *  BF16: tcgen05 tensor cores with FP32 accumulation, split form: A and the
  *    intermediate A^T X are each held as a bf16 high part plus a bf16 low part
  *    (about 16 significant bits), so the sketch is of A itself; A is still read
- *    once, in FP32. Used where I_n <= 512 and L_n <= 64; other modes run FP32. */
+ *    once, in FP32. Used where I_n <= 512 and L_n <= 64; other modes run FP32.
+ * The tensor-core forms need FP32 data (TUCKER_ERR_UNSUPPORTED for FP64). */
 typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2 } tucker_sketch_prec;
 
 #define TUCKER_FLAG_ASYNC 0x1u
@@ -96,7 +103,7 @@ typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2 } tuck
 typedef struct {
     uint32_t struct_size;   /* sizeof(tucker_opts) */
     int32_t form;           /* tucker_form */
-    int32_t prec;           /* tucker_sketch_prec (TUCKER_SK_FP32 when not built) */
+    int32_t prec;           /* tucker_sketch_prec */
     uint32_t flags;         /* TUCKER_FLAG_* */
     double alpha;           /* T_n = ceil(alpha J_n) when c == 0 and alpha > 0 (Section 3.3) */
     void* stream;           /* cudaStream_t; NULL = legacy default stream */
@@ -361,12 +368,14 @@ int64_t tucker_launch_count(void);
 
 /* Kernel classes timed by the profiler. */
 typedef enum {
-    TUCKER_KERNEL_POWER = 0,   /* fused power step / range sketch (one pass over the unfolding) */
+    TUCKER_KERNEL_POWER = 0,   /* fused power step / range sketch on FP32/FP64 FMA (one pass over the unfolding) */
     TUCKER_KERNEL_TTM = 1,     /* mode-n product */
     TUCKER_KERNEL_GATHER = 2,  /* AMM rescaled gather */
     TUCKER_KERNEL_NORMS = 3,   /* squared fiber norms */
     TUCKER_KERNEL_EXTRACT = 4, /* a mode's whole orthonormalisation + extraction sequence */
-    TUCKER_KERNEL_SAMPLE = 5   /* a mode's weights, scan and draws */
+    TUCKER_KERNEL_SAMPLE = 5,  /* a mode's weights, scan and draws */
+    TUCKER_KERNEL_POWER_BF16 = 6, /* fused power step on the tensor cores, split-bf16 operands */
+    TUCKER_KERNEL_POWER_TF32 = 7  /* fused power step on the tensor cores, tf32 operands */
 } tucker_kernel_class;
 
 /* on != 0: clear the accumulators and bracket every launch of the classes

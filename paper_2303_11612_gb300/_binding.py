@@ -99,7 +99,8 @@ _SIGS = {
 _RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int64,
              "tucker_last_cuda_error": C.c_char_p, "tucker_autotune_count": C.c_int64,
              "tucker_autotune_entry": C.c_char_p}
-KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3, "extract": 4, "sample": 5}
+KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3, "extract": 4, "sample": 5, "power_bf16": 6,
+                  "power_tf32": 7}
 
 
 def lib():
@@ -482,6 +483,8 @@ class Batch:
     def __init__(self, requests, form="paper", prec="fp32"):
         self._keep = []
         self.outputs = []
+        self._offsets = []
+        off = 0
         arr = (Request * len(requests))()
         for k, r in enumerate(requests):
             A = r["A"]
@@ -498,6 +501,9 @@ class Batch:
                              PROB[r.get("prob", "uniform")], int(r.get("seed", 0)) & (2**64 - 1), Up, G.data_ptr())
             self._keep.append((A, d64, r32, Up))
             self.outputs.append((U, G))
+            self._offsets.append(off)
+            off += (workspace_size(r["which"], dims, ranks, P=int(r.get("P", 5)), q=int(r.get("q", 1)),
+                                   c=int(r.get("c", 0)), dtype=A.dtype, form=form, prec=prec) + 255) // 256 * 256
         self._reqs = arr
         self._n = len(requests)
         self._form, self._prec = form, prec
@@ -512,3 +518,10 @@ class Batch:
                       flags=0 if sync else FLAG_ASYNC)
         _check("tucker_batch_run", lib().tucker_batch_run(self._n, C.cast(self._reqs, C.c_void_p), C.byref(o)))
         return self.outputs
+
+    def status(self):
+        """Each request's device status word (0 = success; bit 0 numerical
+        failure, bit 1 a bounded wait timed out) as left by the last run; read
+        once that run has completed."""
+        w = self.workspace
+        return [int(w[o:o + 4].view(torch.int32).item()) for o in self._offsets]

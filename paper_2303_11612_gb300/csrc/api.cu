@@ -87,7 +87,6 @@ tucker_status read_opts(const tucker_opts* o, Opts& out) {
     if (out.form != TUCKER_FORM_PAPER && out.form != TUCKER_FORM_RANGE) return TUCKER_ERR_INVALID_ARG;
     if (out.prec < TUCKER_SK_FP32 || out.prec > TUCKER_SK_BF16) return TUCKER_ERR_INVALID_ARG;
     if (!(out.alpha >= 0.0) || out.alpha > 1.0) return TUCKER_ERR_INVALID_ARG;
-    if (out.prec == TUCKER_SK_TF32) return TUCKER_ERR_UNSUPPORTED;
     return TUCKER_OK;
 }
 
@@ -109,7 +108,8 @@ struct ModePlan {
     int L;
     int R;
     int64_t T;         // AMM samples (0 = none)
-    bool tc;           // power steps on the tensor cores (bf16 operands)
+    bool tc;           // power steps on the tensor cores (split-bf16 operands)
+    bool tf32;         // power steps on the tensor cores (tf32 operands, contiguous fibers)
     PowerPlan pp;
     OrthPlan op;
 };
@@ -155,9 +155,12 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         if (d[n] > kMaxI || mp.L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
         if (elem == 8 && d[n] > 512) return TUCKER_ERR_UNSUPPORTED;
         mp.pp = power_plan(mp.mv, mp.L, elem, sms);
-        // bf16 tensor-core power steps where the tile fits; the FP32 kernel elsewhere
-        mp.tc = o.prec == TUCKER_SK_BF16 && elem == 4 && power_tc_supported(mp.mv, mp.L);
-        if (mp.tc)
+        // tensor-core power steps where the tile fits: TF32 on contiguous fibers, split
+        // BF16 (also the TF32 form's choice for strided fibers); the FP32 kernel elsewhere
+        mp.tf32 = o.prec == TUCKER_SK_TF32 && elem == 4 && power_tf32_supported(mp.mv, mp.L);
+        mp.tc = (o.prec == TUCKER_SK_BF16 || o.prec == TUCKER_SK_TF32) && elem == 4 &&
+                power_tc_supported(mp.mv, mp.L);
+        if (mp.tc || mp.tf32)
             p.max_partials = std::max(p.max_partials, power_tc_partials_bytes(mp.mv, mp.L, sms));
         mp.op = orth_plan(d[n], mp.L, sms);
         if (!orth_supported(mp.op, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
@@ -227,10 +230,15 @@ void carve(const Plan& p, Arena& a, Work& w) {
         if (_e != cudaSuccess) return _e;           \
     } while (0)
 
-// X_out = M M^T X_in on the tensor cores (bf16) or with FP32/FP64 FMA.
+// X_out = M M^T X_in on the tensor cores (tf32 or split bf16) or with FP32/FP64 FMA.
 template <typename T>
 cudaError_t power_step(const T* M, const ModePlan& mp, const T* X_in, T* X_out, const Work& w, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+        if (mp.tf32) {
+            // cudaErrorNotSupported: M not 16-byte aligned for TMA; the next form runs
+            const cudaError_t e = launch_power_tf32(M, mp.mv, X_in, mp.L, X_out, w.partials, w.status, num_sms(), s);
+            if (e != cudaErrorNotSupported) return e;
+        }
         if (mp.tc)
             return launch_power_tc(M, mp.mv, X_in, mp.L, X_out, w.partials, w.status, num_sms(), s);
     }
@@ -352,7 +360,7 @@ tucker_status driver(bool st, const void* A, tucker_dtype dt, const int64_t* dim
     if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
     if (prob != TUCKER_PROB_NEARLY_OPTIMAL && prob != TUCKER_PROB_UNIFORM) return TUCKER_ERR_INVALID_ARG;
     if (!A || !U || !G) return TUCKER_ERR_INVALID_ARG;
-    if (o.prec == TUCKER_SK_BF16 && dt != TUCKER_F32) return TUCKER_ERR_UNSUPPORTED;
+    if ((o.prec == TUCKER_SK_BF16 || o.prec == TUCKER_SK_TF32) && dt != TUCKER_F32) return TUCKER_ERR_UNSUPPORTED;
     for (int n = 0; n < N && n < kMaxOrder; ++n)
         if (!U[n]) return TUCKER_ERR_INVALID_ARG;
     const int elem = dt == TUCKER_F64 ? 8 : 4;
@@ -566,6 +574,19 @@ tucker_status tucker_power_step(const void* A, tucker_dtype dt, const int64_t* d
     const int elem = dt == TUCKER_F64 ? 8 : 4;
     if (v.i > kMaxI || L > 4096 || (elem == 8 && v.i > 512)) return TUCKER_ERR_UNSUPPORTED;
     const PowerPlan pp = power_plan(v, (int)L, elem, num_sms());
+    if (o.prec == TUCKER_SK_TF32) {
+        if (elem != 4 || !power_tf32_supported(v, (int)L)) return TUCKER_ERR_UNSUPPORTED;
+        Scratch sc;
+        if ((rs = sc.get(power_tc_partials_bytes(v, (int)L, num_sms()) + 256, o.stream)) != TUCKER_OK) return rs;
+        int* status = reinterpret_cast<int*>(sc.p);
+        cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
+        if (e == cudaSuccess)
+            e = launch_power_tf32((const float*)A, v, (const float*)X_in, (int)L, (float*)X_out,
+                                  reinterpret_cast<char*>(sc.p) + 256, status, num_sms(), o.stream);
+        if (e == cudaErrorNotSupported) return TUCKER_ERR_UNSUPPORTED;
+        if (e != cudaSuccess) return from_cuda(e);
+        return sync_status(o.stream, status);
+    }
     if (o.prec == TUCKER_SK_BF16) {
         if (elem != 4 || !power_tc_supported(v, (int)L)) return TUCKER_ERR_UNSUPPORTED;
         Scratch sc;

@@ -57,6 +57,14 @@ size_t power_tc_partials_bytes(const ModeView& v, int L, int num_sms);
 cudaError_t launch_power_tc(const float* A, const ModeView& v, const float* X_in, int L, float* X_out, void* partials,
                             int* status, int num_sms, cudaStream_t s);
 
+// ---- tensor-core power step, tf32 operands / fp32 accumulation, contiguous
+// fibers (kernels_tf32.cu). Returns cudaErrorNotSupported (nothing launched)
+// when the shape is outside power_tf32_supported or A is not 16-byte aligned;
+// partials as for launch_power_tc.
+bool power_tf32_supported(const ModeView& v, int L);
+cudaError_t launch_power_tf32(const float* A, const ModeView& v, const float* X_in, int L, float* X_out,
+                              void* partials, int* status, int num_sms, cudaStream_t s);
+
 // ---- sampling (kernels_amm.cu)
 template <typename T>
 cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStream_t s);
@@ -111,7 +119,7 @@ int num_sms();
 
 // ---- launch counting and profiling (profile.cu)
 enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKExtract = 4, kKSample = 5,
-                   kKernelClasses = 6 };
+                   kKPowerBf16 = 6, kKPowerTf32 = 7, kKernelClasses = 8 };
 void note_launch();
 void note_launches(int64_t n);   // a graph replay's kernels
 void profile_drain();

@@ -334,7 +334,7 @@ cudaError_t launch_power_tc(const float* A, const ModeView& v, const float* X_in
     const double elems = (double)v.i * (double)v.fibers();
     cudaError_t e;
     {
-        ProfScope prof(kKPower, elems * sizeof(float), 4.0 * elems * L, s);
+        ProfScope prof(kKPowerBf16, elems * sizeof(float), 4.0 * elems * L, s);
         switch (LP) {
             case 16: e = contig ? launch_tc_t<true, 16>(A, v, X_in, L, part, grid, tiles, status, s)
                                 : launch_tc_t<false, 16>(A, v, X_in, L, part, grid, tiles, status, s); break;
