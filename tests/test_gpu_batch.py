@@ -75,13 +75,13 @@ def test_batch_equals_requests_alone_and_replays(tk, prec):
             assert same(got, w)
     # every kernel of the graph is counted once per launch
     assert tk.launch_count() - n1 == 2 * (n1 - n0) > 0
-    # the status word of each request's workspace slice is clear
+    # the status word of each request's workspace slice is clear, at the offsets
+    # the library's workspace sizes give
     sizes = [tk.workspace_size(r["which"], r["dims"], r["ranks"], P=r["P"], q=r["q"], c=r["c"], prec=prec)
              for r in reqs]
-    off = 0
-    for sz in sizes:
-        assert int(b.workspace[off:off + 4].view(torch.int32).item()) == 0
-        off += (sz + 255) // 256 * 256
+    offs = np.concatenate([[0], np.cumsum([(sz + 255) // 256 * 256 for sz in sizes])])
+    assert b.workspace.numel() >= offs[-1] and b._offsets == [int(o) for o in offs[:-1]]
+    assert b.status() == [0] * len(reqs)
 
 
 def test_replay_reads_inputs_rewritten_in_place(tk):
