@@ -44,7 +44,7 @@ VARIANTS = [
     dict(name="hilbert_q1_amm4000_uniform", tensor="hilbert", q=1, c=4000, prob="uniform"),
 ]
 BASELINE_METRIC = "decomps/s & sketch HBM GB/s, BF16 vs FP32 at equal rel err; serving p50/p99 ms"
-PROFILED = ("power", "power_bf16", "power_tf32", "ttm", "gather", "norms", "extract", "sample")
+PROFILED = ("power", "power_bf16", "power_tf32", "ttm", "ttm_bf16", "gather", "norms", "extract", "sample")
 # the dominant kernel of each form: (profiler class, name, source file, traffic.json key)
 DOMINANT = {
     "tf32": ("power_tf32", "power_tf32_kernel (fused A(A^T X) pass, tcgen05 kind::tf32, TMA-fed, fp32 accumulate)",
@@ -487,9 +487,10 @@ def main():
                        "parallelism": "replicas (each rank decomposes its own batch)" if world > 1 else "single GPU",
                        "sketch": f"paper form, {head['prec']} power steps "
                                  + {"tf32": "(tcgen05 kind::tf32 on mode 1, split bf16 on modes 2-3, fp32 "
-                                            "accumulate)",
-                                    "bf16": "(tcgen05 split bf16, fp32 accumulate)",
-                                    "fp32": "(FP32 FFMA)"}[head["prec"]],
+                                            "accumulate; mode-1 product split bf16 on tcgen05)",
+                                    "bf16": "(tcgen05 split bf16, fp32 accumulate; mode-1 product split bf16 "
+                                            "on tcgen05)",
+                                    "fp32": "(FP32 FFMA; exact FP32 mode products)"}[head["prec"]],
                        "execution": f"tucker_batch_run per step: one CUDA graph (captured by the library on its "
                                     f"first run, replayed after) of {len(batch)} decompositions ({args.copies} of "
                                     f"each variant, inputs shared read-only) on {len(batch)} streams"},

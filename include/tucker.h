@@ -219,7 +219,12 @@ tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, i
  * matrix: transpose == 0: M is K x I_n (out has K in mode n);
  *         transpose == 1: M_ptr holds I_n x K and M is its transpose
  *         (out = A x_n M_ptr^T, the truncation B x_n U^T of Algorithm 2).
- * Exact FP32 / FP64 FMA. */
+ * opts->prec FP32 (default): exact FP32 / FP64 FMA. BF16 or TF32: tcgen05 tensor
+ * cores with A and M each split into bf16 high and low parts, A_hi M_hi +
+ * A_lo M_hi + A_hi M_lo accumulated in FP32 (about 2^-16 relative, unbiased);
+ * contiguous fibers only (mode 0), FP32, I_n % 4 == 0, I_n <= 512, K <= 32, A
+ * 16-byte aligned, else TUCKER_ERR_UNSUPPORTED. The drivers use this form for
+ * the mode-0 product when their prec is BF16 or TF32 (FP32 FMA elsewhere). */
 tucker_status tucker_ttm(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode,
                          const void* M_ptr, int64_t K, int transpose, void* out,
                          const tucker_opts* opts);
@@ -375,7 +380,8 @@ typedef enum {
     TUCKER_KERNEL_EXTRACT = 4, /* a mode's whole orthonormalisation + extraction sequence */
     TUCKER_KERNEL_SAMPLE = 5,  /* a mode's weights, scan and draws */
     TUCKER_KERNEL_POWER_BF16 = 6, /* fused power step on the tensor cores, split-bf16 operands */
-    TUCKER_KERNEL_POWER_TF32 = 7  /* fused power step on the tensor cores, tf32 operands */
+    TUCKER_KERNEL_POWER_TF32 = 7, /* fused power step on the tensor cores, tf32 operands */
+    TUCKER_KERNEL_TTM_BF16 = 8    /* mode-n product on the tensor cores, split-bf16 operands */
 } tucker_kernel_class;
 
 /* on != 0: clear the accumulators and bracket every launch of the classes

@@ -100,7 +100,7 @@ _RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int6
              "tucker_last_cuda_error": C.c_char_p, "tucker_autotune_count": C.c_int64,
              "tucker_autotune_entry": C.c_char_p}
 KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3, "extract": 4, "sample": 5, "power_bf16": 6,
-                  "power_tf32": 7}
+                  "power_tf32": 7, "ttm_bf16": 8}
 
 
 def lib():
@@ -335,9 +335,10 @@ def leading_factor(Cm, R, stream=None):
     return U
 
 
-def ttm(A, dims, mode, M, transpose=False, stream=None):
+def ttm(A, dims, mode, M, transpose=False, stream=None, prec="fp32"):
     """A x_n M (transpose=False, M is K x I_n) or A x_n M^T (transpose=True, M is I_n x K);
-    M must have column-major strides."""
+    M must have column-major strides. prec "bf16"/"tf32": split-bf16 tensor cores
+    (contiguous fibers only)."""
     K = M.shape[1] if transpose else M.shape[0]
     if M.stride(0) != 1:
         M = M.t().contiguous().t()
@@ -347,7 +348,7 @@ def ttm(A, dims, mode, M, transpose=False, stream=None):
     for d in out_dims:
         n *= d
     out = torch.empty(n, dtype=A.dtype, device=A.device)
-    o = make_opts(stream=stream)
+    o = make_opts(stream=stream, prec=prec)
     _check("tucker_ttm", lib().tucker_ttm(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode, M.data_ptr(), K,
                                           int(transpose), out.data_ptr(), C.byref(o)))
     return out

@@ -116,6 +116,7 @@ struct ModePlan {
 
 struct Plan {
     int N = 0;
+    int prec = TUCKER_SK_FP32;
     bool st = false;
     int elem = 4;
     int form = 0;
@@ -139,6 +140,7 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
     p.st = st;
     p.elem = elem;
     p.form = o.form;
+    p.prec = o.prec;
     p.q = q;
     const int sms = num_sms();
     int64_t d[kMaxOrder];
@@ -290,6 +292,20 @@ cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, 
     return launch_extract<T>(X1, Q, mp.op, w.factors, 0, mp.R, U, w.orth, w.status, s);
 }
 
+// Mode-n product of the TTM chain: on the tensor cores (split bf16) for
+// contiguous fibers when the plan's arithmetic is BF16 or TF32, else FP32/FP64 FMA.
+template <typename T>
+cudaError_t mode_product(const Plan& p, const T* A, const ModeView& v, const T* U, int64_t K, T* out,
+                         const Work& w, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (p.prec != TUCKER_SK_FP32) {
+            const cudaError_t e = launch_ttm_tc(A, v, U, K, 1, v.i, out, w.status, num_sms(), s);
+            if (e != cudaErrorNotSupported) return e;
+        }
+    }
+    return launch_ttm<T>(A, v, U, K, 1, v.i, out, s, w.status);
+}
+
 template <typename T>
 cudaError_t run_driver(const Plan& p, const T* A, const int32_t* ranks, int q, int prob, uint64_t seed, T* const* U,
                        T* G, const Work& w, int64_t* const* sample_out, bool want_re, cudaStream_t s) {
@@ -302,7 +318,7 @@ cudaError_t run_driver(const Plan& p, const T* A, const int32_t* ranks, int q, i
             TK_TRY(factor_mode<T>(cur, mp, n, q, prob, seed, p.form, U[n], w,
                                   sample_out ? sample_out[n] : nullptr, s));
             T* out = n == N - 1 ? G : (T*)w.inter[n & 1];
-            TK_TRY(launch_ttm<T>(cur, mp.v, U[n], ranks[n], 1, mp.v.i, out, s, w.status));
+            TK_TRY(mode_product<T>(p, cur, mp.v, U[n], ranks[n], out, w, s));
             cur = out;
         }
     } else {
@@ -315,7 +331,7 @@ cudaError_t run_driver(const Plan& p, const T* A, const int32_t* ranks, int q, i
         for (int n = 0; n < N; ++n) {
             const ModeView v = view_of(e, N, n);
             T* out = n == N - 1 ? G : (T*)w.inter[n & 1];
-            TK_TRY(launch_ttm<T>(cur, v, U[n], ranks[n], 1, v.i, out, s, w.status));
+            TK_TRY(mode_product<T>(p, cur, v, U[n], ranks[n], out, w, s));
             e[n] = ranks[n];
             cur = out;
         }
@@ -738,6 +754,14 @@ tucker_status tucker_ttm(const void* A, tucker_dtype dt, const int64_t* dims, in
     Scratch sc;
     if ((rs = sc.get(256, o.stream)) != TUCKER_OK) return rs;
     if (cudaMemsetAsync(sc.p, 0, sizeof(int), o.stream) != cudaSuccess) return from_cuda(cudaGetLastError());
+    if (o.prec != TUCKER_SK_FP32) {
+        if (dt != TUCKER_F32) return TUCKER_ERR_UNSUPPORTED;
+        const cudaError_t e = launch_ttm_tc((const float*)A, v, (const float*)M_ptr, K, ld_i, ld_k, (float*)out,
+                                            (int*)sc.p, num_sms(), o.stream);
+        if (e == cudaErrorNotSupported) return TUCKER_ERR_UNSUPPORTED;
+        if (e != cudaSuccess) return from_cuda(e);
+        return sync_status(o.stream, (const int*)sc.p);
+    }
     cudaError_t e = dt == TUCKER_F32 ? launch_ttm<float>((const float*)A, v, (const float*)M_ptr, K, ld_i, ld_k,
                                                          (float*)out, o.stream, (int*)sc.p)
                   : dt == TUCKER_F64 ? launch_ttm<double>((const double*)A, v, (const double*)M_ptr, K, ld_i, ld_k,

@@ -65,6 +65,14 @@ bool power_tf32_supported(const ModeView& v, int L);
 cudaError_t launch_power_tf32(const float* A, const ModeView& v, const float* X_in, int L, float* X_out,
                               void* partials, int* status, int num_sms, cudaStream_t s);
 
+// ---- mode-n product on the tensor cores, split-bf16 operands / fp32
+// accumulation, contiguous fibers (kernels_ttm_tc.cu); M(i, o) = Mp[i ld_i + o ld_k],
+// out as launch_ttm. Returns cudaErrorNotSupported (nothing launched) outside
+// ttm_tc_supported or when A is not 16-byte aligned.
+bool ttm_tc_supported(const ModeView& v, int64_t K_out);
+cudaError_t launch_ttm_tc(const float* A, const ModeView& v, const float* Mp, int64_t K_out, int64_t ld_i,
+                          int64_t ld_k, float* out, int* status, int num_sms, cudaStream_t s);
+
 // ---- sampling (kernels_amm.cu)
 template <typename T>
 cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStream_t s);
@@ -119,7 +127,7 @@ int num_sms();
 
 // ---- launch counting and profiling (profile.cu)
 enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKExtract = 4, kKSample = 5,
-                   kKPowerBf16 = 6, kKPowerTf32 = 7, kKernelClasses = 8 };
+                   kKPowerBf16 = 6, kKPowerTf32 = 7, kKTtmBf16 = 8, kKernelClasses = 9 };
 void note_launch();
 void note_launches(int64_t n);   // a graph replay's kernels
 void profile_drain();

@@ -2,10 +2,11 @@
 // operands, FP32 accumulation in tensor memory): X_out = A_(n) (A_(n)^T X_in).
 //
 // Split-BF16 arithmetic: each FP32 entry a of A is held as a_hi + a_lo with
-// a_hi = bf16(a) and a_lo = bf16(a - a_hi), which represents a to about 2^-17
-// relative, and the FP32 product W = T^T X is split the same way. The products
+// a_hi = bf16(a) and a_lo = bf16(a - a_hi), which represents a to 2^-16
+// relative (bf16 keeps 8 significant bits, rounded to nearest), and the FP32
+// product W = T^T X is split the same way. The products
 //   W    = T_hi X + T_lo X
-//   Xacc += T_hi W_hi + T_lo W_hi + T_hi W_lo          (T_lo W_lo, ~2^-18, dropped)
+//   Xacc += T_hi W_hi + T_lo W_hi + T_hi W_lo          (T_lo W_lo, <= 2^-16, dropped)
 // therefore sketch A itself rather than its BF16 rounding (which alone would
 // set a relative-error floor near 1e-3), at the same HBM traffic: A is read
 // once, in FP32, and the extra tensor-core work stays far below the ridge.
