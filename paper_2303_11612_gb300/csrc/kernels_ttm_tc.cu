@@ -11,15 +11,15 @@
 //
 // A tile is 128 fibers (M of the product, one fiber per accumulator lane); it
 // streams through units of 64 values i. TMA loads a unit as two FP32 boxes of
-// 32 values x 128 fibers in the 128-byte-swizzled layout; eight converter warps
+// 32 values x 128 fibers in the 128-byte-swizzled layout; sixteen converter warps
 // rewrite it as bf16 high and low parts in the K-major swizzled layout of the
 // product (one 128-byte row of 64 values per fiber); the MMA thread issues
 // 4 K-steps x 3 products per unit into the tile's accumulator (N = 32 columns
 // for the K_out <= 32 outputs, double-buffered), and four warps read finished
 // accumulators back and store the tile's outputs.
 //
-// Warp roles: warp 0 TMA, warp 1 MMA (and tensor-memory allocation), warps 2-9
-// conversion, warps 10-13 read-back. Every mbarrier wait is bounded: on a
+// Warp roles: warp 0 TMA, warp 1 MMA (and tensor-memory allocation), warps 2-17
+// conversion, warps 18-21 read-back. Every mbarrier wait is bounded: on a
 // timeout the kernel records kStatTimeout, lets the copies and products it
 // issued finish (with the same bound), frees its tensor memory and returns.
 #include <climits>
@@ -31,19 +31,21 @@
 namespace tk {
 namespace {
 
-constexpr int kGThreads = 448;
+constexpr int kGThreads = 64 + 32 * 16 + 32 * 4;  // TMA, MMA, 16 converter and 4 read-back warps
 constexpr int kGJB = 128;                  // fibers per tile
 constexpr int kGBox = kGJB * 128;          // FP32 box: 32 values i x 128 fibers
 constexpr int kGUnit = 2 * kGBox;          // FP32 unit: 64 values i
 constexpr int kGHalf = kGJB * 128;         // one bf16 part of a unit: 64 values i x 128 fibers
 constexpr int kGFStages = 3;               // FP32 units in the TMA ring
 constexpr int kGCStages = 2;               // converted units
-constexpr int kGConv = 8;                  // converter warps 2 .. 9
+constexpr int kGConv = (kGThreads - 64 - 128) / 32;   // converter warps 2 .. 2 + kGConv - 1
 constexpr int kGEpi = 4;                   // read-back warps 10 .. 13
 constexpr int kGUChunk = 32 * 128;         // one unit of one part of M^T: 32 rows o x 128 bytes
 constexpr int kGWaitIters = 1 << 22;
 constexpr size_t kGSmemMax = 227 * 1024;
 constexpr uint32_t kGTmemCols = 64;
+constexpr int kGBars = 2 * kGFStages + 2 * kGCStages + 5;    // 8 bytes each, 256 reserved
+static_assert(kGBars * 8 + 8 <= 256, "barrier area");
 
 struct TtmTcLayout {
     int nu = 0;                // units of 64 values i
@@ -98,14 +100,14 @@ __global__ void __launch_bounds__(kGThreads, 1)
     unsigned char* Cb = smem + (size_t)kGFStages * kGUnit;              // [2] (hi, lo) bf16 units
     unsigned char* Us = Cb + (size_t)kGCStages * 2 * kGHalf;            // M^T hi [nu], then lo [nu]
     uint64_t* bar = reinterpret_cast<uint64_t*>(Us + (size_t)2 * nu * kGUChunk);
-    uint64_t* f_full = bar;            // [3] FP32 unit loaded (TMA bytes)
-    uint64_t* f_empty = bar + 3;       // [3] FP32 unit converted (8 warps)
-    uint64_t* c_full = bar + 6;        // [2] bf16 unit written (8 warps)
-    uint64_t* c_empty = bar + 8;       // [2] bf16 unit consumed by the products
-    uint64_t* d_full = bar + 10;       // [2] tile accumulated
-    uint64_t* d_empty = bar + 12;      // [2] tile read back (4 warps)
-    uint64_t* done = bar + 14;         // every product done
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 15);
+    uint64_t* f_full = bar;                          // FP32 unit loaded (TMA bytes)
+    uint64_t* f_empty = f_full + kGFStages;          // FP32 unit converted (converter warps)
+    uint64_t* c_full = f_empty + kGFStages;          // bf16 unit written (converter warps)
+    uint64_t* c_empty = c_full + kGCStages;          // bf16 unit consumed by the products
+    uint64_t* d_full = c_empty + kGCStages;          // [2] tile accumulated
+    uint64_t* d_empty = d_full + 2;                  // [2] tile read back (4 warps)
+    uint64_t* done = d_empty + 2;                    // every product done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t nloc = tiles > (int64_t)blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -127,12 +129,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
         *reinterpret_cast<uint4*>(Us + (size_t)nu * kGUChunk + off) = lo;
     }
     if (tid == 0) {
-        for (int k = 0; k < 15; ++k) {
-            uint32_t count = 1;
-            if ((k >= 3 && k < 6) || (k >= 6 && k < 8)) count = kGConv;   // f_empty, c_full
-            if (k >= 12 && k < 14) count = kGEpi;                         // d_empty
-            tc::mbar_init(&bar[k], count);
-        }
+        for (int k = 0; k < kGBars; ++k) tc::mbar_init(&bar[k], 1);
+        for (int k = 0; k < kGFStages; ++k) tc::mbar_init(&f_empty[k], kGConv);
+        for (int k = 0; k < kGCStages; ++k) tc::mbar_init(&c_full[k], kGConv);
+        for (int k = 0; k < 2; ++k) tc::mbar_init(&d_empty[k], kGEpi);
         *flag = 0;
         tma::fence_barrier_init();
     }
