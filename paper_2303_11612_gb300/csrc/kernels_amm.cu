@@ -26,33 +26,80 @@ template <> struct NormAcc<double> {
     __device__ double value() const { return s; }
 };
 
-// Contiguous fibers (mode 1): one warp per fiber.
+// Contiguous fibers (mode 1): one warp per fiber; each lane issues its loads in
+// predicated batches of 16 (coalesced 128-byte rows) before summing them.
 template <typename T>
 __global__ void __launch_bounds__(kT) norms_contig_kernel(const T* __restrict__ A, int64_t I, int64_t J,
                                                           double* __restrict__ w) {
+    constexpr int kB = 16;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)kT + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kT) >> 5;
     for (int64_t j = warp; j < J; j += nwarps) {
         NormAcc<T> acc;
         const T* f = A + j * I;
-        for (int64_t i = lane; i < I; i += 32) acc.add(__ldg(f + i));
+        for (int64_t i0 = 0; i0 < I; i0 += 32 * kB) {
+            T x[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int64_t i = i0 + lane + 32 * u;
+                x[u] = i < I ? __ldg(f + i) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) acc.add(x[u]);
+        }
         acc.warp_reduce();
         if (lane == 0) w[j] = acc.value();
     }
 }
 
-// Strided fibers: one thread per fiber; consecutive threads read consecutive
-// addresses because neighbouring fibers differ in the fastest index.
-template <typename T>
+// Strided fibers: 32 FW consecutive fibers per block (consecutive lanes read
+// consecutive addresses: neighbouring fibers differ in the fastest index; FW
+// warps side by side read 128 FW contiguous bytes), the fiber's I_n values
+// split over the block's kT / (32 FW) warp groups (group w takes
+// i = w, w + groups, ...); the per-group sums are combined in group order.
+template <typename T> struct NormPart;
+template <> struct NormPart<float> {
+    static __device__ void merge(NormAcc<float>& a, const NormAcc<float>& b) { pair_add(a.s, b.s); }
+};
+template <> struct NormPart<double> {
+    static __device__ void merge(NormAcc<double>& a, const NormAcc<double>& b) { a.s += b.s; }
+};
+
+template <typename T, int FW>
 __global__ void __launch_bounds__(kT) norms_strided_kernel(const T* __restrict__ A, ModeView v,
                                                            double* __restrict__ w) {
+    constexpr int kG = kT / (32 * FW);          // warp groups along i
+    constexpr int kF = 32 * FW;                 // fibers per block
+    __shared__ __align__(16) unsigned char part_raw[kG * kF * sizeof(NormAcc<T>)];
+    NormAcc<T>(*part)[kF] = reinterpret_cast<NormAcc<T>(*)[kF]>(part_raw);
+    const int f = threadIdx.x % kF, grp = threadIdx.x / kF;
     const int64_t J = v.fibers();
-    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < J; j += (int64_t)gridDim.x * kT) {
+    for (int64_t j0 = (int64_t)blockIdx.x * kF; j0 < J; j0 += (int64_t)gridDim.x * kF) {
+        const int64_t j = j0 + f;
         NormAcc<T> acc;
-        const T* f = A + v.base(j);
-        for (int64_t i = 0; i < v.i; ++i) acc.add(__ldg(f + i * v.lf));
-        w[j] = acc.value();
+        if (j < J) {
+            const T* p = A + v.base(j);
+            constexpr int kB = 8;
+            for (int64_t i0 = grp; i0 < v.i; i0 += (int64_t)kB * kG) {
+                T x[kB];
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int64_t i = i0 + (int64_t)u * kG;
+                    x[u] = i < v.i ? __ldg(p + i * v.lf) : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < kB; ++u) acc.add(x[u]);
+            }
+        }
+        part[grp][f] = acc;
+        __syncthreads();
+        if (grp == 0 && j < J) {
+            NormAcc<T> tot = part[0][f];
+            for (int q = 1; q < kG; ++q) NormPart<T>::merge(tot, part[q][f]);
+            w[j] = tot.value();
+        }
+        __syncthreads();
     }
 }
 
@@ -209,10 +256,14 @@ cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStr
     const int64_t J = v.fibers();
     if (J == 0) return cudaSuccess;
     ProfScope prof(kKNorms, (double)v.i * (double)J * sizeof(T), 2.0 * (double)v.i * (double)J, s);
-    if (v.lf == 1)
+    // a warp per fiber for long contiguous fibers; otherwise a thread per fiber
+    // (for short contiguous fibers the block's fibers still cover one contiguous range)
+    if (v.lf == 1 && v.i >= 64)
         norms_contig_kernel<T><<<grid_for(J, kT / 32, 8192), kT, 0, s>>>(A, v.i, J, w);
+    else if (v.lf >= 128 && J >= 128 * 152)
+        norms_strided_kernel<T, 4><<<grid_for(J, 128, 8192), kT, 0, s>>>(A, v, w);
     else
-        norms_strided_kernel<T><<<grid_for(J, kT, 8192), kT, 0, s>>>(A, v, w);
+        norms_strided_kernel<T, 1><<<grid_for(J, 32, 8192), kT, 0, s>>>(A, v, w);
     note_launch();
     return cudaGetLastError();
 }

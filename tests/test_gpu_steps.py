@@ -96,7 +96,8 @@ def test_range_sketch(tk, dims, L):
         assert rel(got, M @ Om) < 2e-5
 
 
-@pytest.mark.parametrize("dims", [(33, 20, 17), (5, 300, 7), (1000, 3, 4), (6, 5, 4, 3)])
+@pytest.mark.parametrize("dims", [(33, 20, 17), (5, 300, 7), (1000, 3, 4), (6, 5, 4, 3), (20, 400, 50), (7, 9, 1100),
+                                  (132, 140, 160), (30, 7, 5), (20, 60, 70)])
 def test_fiber_norms(tk, dims):
     A = synth.lowrank_noise(dims, [2] * len(dims), rel_noise=0.5, seed=4)
     At = flat_dev(A)
