@@ -80,13 +80,21 @@ __device__ __forceinline__ uint32_t bf2(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&p);
 }
 
+// Two FP32 values -> their bf16 high parts (packed, round to nearest) and the
+// bf16 low parts of the remainders x - hi (exact in FP32); a packed bf16 value
+// widens to FP32 by a 16-bit shift.
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    hi = bf2(a, b);
+    const float ha = __uint_as_float(hi << 16), hb = __uint_as_float(hi & 0xFFFF0000u);
+    lo = bf2(a - ha, b - hb);
+}
+
 // Eight FP32 values -> bf16 high parts and bf16 low parts (x - hi), packed in order.
 __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
-    float r[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) r[k] = x[k] - __bfloat162float(__float2bfloat16_rn(x[k]));
-    hi = make_uint4(bf2(x[0], x[1]), bf2(x[2], x[3]), bf2(x[4], x[5]), bf2(x[6], x[7]));
-    lo = make_uint4(bf2(r[0], r[1]), bf2(r[2], r[3]), bf2(r[4], r[5]), bf2(r[6], r[7]));
+    split2(x[0], x[1], hi.x, lo.x);
+    split2(x[2], x[3], hi.y, lo.y);
+    split2(x[4], x[5], hi.z, lo.z);
+    split2(x[6], x[7], hi.w, lo.w);
 }
 
 __global__ void __launch_bounds__(kGThreads, 1)
@@ -224,15 +232,17 @@ __global__ void __launch_bounds__(kGThreads, 1)
         for (int64_t k = 0; k < nloc && ok; ++k) {
             for (int u = 0; u < nu; ++u, ++g) {
                 const int fs = (int)(g % kGFStages), cs = (int)(g % kGCStages);
-                if (!wait_bar(&f_full[fs], (uint32_t)((g / kGFStages) & 1), flag) ||
-                    (g >= kGCStages && !wait_bar(&c_empty[cs], (uint32_t)((g / kGCStages - 1) & 1), flag))) {
+                if (!wait_bar(&f_full[fs], (uint32_t)((g / kGFStages) & 1), flag)) {
                     ok = false;
                     break;
                 }
+                // split into registers first (this consumes the loads), release the
+                // FP32 slot to the TMA at once, then store once a bf16 slot is free
+                constexpr int kTasks = (kGJB * 8) / (kGConv * 32);
                 const unsigned char* src = F + (size_t)fs * kGUnit;
-                unsigned char* dhi = Cb + (size_t)cs * 2 * kGHalf;
+                uint4 hi[kTasks], lo[kTasks];
 #pragma unroll
-                for (int r = 0; r < (kGJB * 8) / (kGConv * 32); ++r) {
+                for (int r = 0; r < kTasks; ++r) {
                     const int t = ct + kGConv * 32 * r;
                     const int j = t >> 3, p = t & 7;
                     const int q0 = (p & 3) * 2;
@@ -240,18 +250,26 @@ __global__ void __launch_bounds__(kGThreads, 1)
                     const float4 a = *reinterpret_cast<const float4*>(row + ((q0 ^ (j & 7)) << 4));
                     const float4 c = *reinterpret_cast<const float4*>(row + (((q0 + 1) ^ (j & 7)) << 4));
                     const float x[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
-                    uint4 hi, lo;
-                    split8(x, hi, lo);
+                    split8(x, hi[r], lo[r]);
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&f_empty[fs]);
+                if (g >= kGCStages && !wait_bar(&c_empty[cs], (uint32_t)((g / kGCStages - 1) & 1), flag)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* dhi = Cb + (size_t)cs * 2 * kGHalf;
+#pragma unroll
+                for (int r = 0; r < kTasks; ++r) {
+                    const int t = ct + kGConv * 32 * r;
+                    const int j = t >> 3, p = t & 7;
                     const int off = j * 128 + ((p ^ (j & 7)) << 4);
-                    *reinterpret_cast<uint4*>(dhi + off) = hi;
-                    *reinterpret_cast<uint4*>(dhi + kGHalf + off) = lo;
+                    *reinterpret_cast<uint4*>(dhi + off) = hi[r];
+                    *reinterpret_cast<uint4*>(dhi + kGHalf + off) = lo[r];
                 }
                 tc::fence_async_smem();
                 __syncwarp();
-                if (lane == 0) {
-                    tc::mbar_arrive(&f_empty[fs]);
-                    tc::mbar_arrive(&c_full[cs]);
-                }
+                if (lane == 0) tc::mbar_arrive(&c_full[cs]);
             }
         }
         if (!ok) fail(flag, status);
