@@ -66,7 +66,7 @@ def bench_tensors():
     return dims, ranks, low, hil
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
 def test_benchmark_workload_400cubed(tk, bench_tensors, prec):
     dims, ranks, low, hil = bench_tensors
     variants = [
@@ -93,7 +93,9 @@ def test_benchmark_workload_400cubed(tk, bench_tensors, prec):
                 for u, uo in zip(U, Uo):
                     assert np.linalg.norm(u @ u.T - uo @ uo.T, 2) <= 1e-4
             else:
-                assert abs(re - reo) <= 1e-3, (kw, re, reo)
+                # tensor-core forms: the sketch's rounding moves RE only to second
+                # order and the mode-1 product (split bf16, ~2^-16) to about 1e-6
+                assert abs(re - reo) <= 1e-4, (kw, re, reo)
         else:
             # Hilbert: its mode-n singular values fall by orders of magnitude per
             # index, so a power-step output (singular values sigma_i^2) loses every
@@ -129,7 +131,7 @@ def test_fourth_order_96(tk):
     A64 = A.astype(np.float64)
     Uo, Go = ot.rsthosvd(A64, ranks, P=8, q=2, seed=0)
     reo = ot.relative_error(A64, Uo, Go)
-    for prec, bar in (("fp32", 1e-5), ("bf16", 1e-3)):
+    for prec, bar in (("fp32", 1e-5), ("bf16", 1e-3), ("tf32", 1e-3)):
         (res,) = in_flight(tk, [(dev(A), dims, ranks, dict(P=8, q=2, c=0, prob="uniform", seed=0))], prec)
         U = [u.double().cpu().numpy() for u in res[0]]
         G = synth.from_flat(res[1].double().cpu().numpy(), ranks)
