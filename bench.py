@@ -469,6 +469,26 @@ def main():
                      "algorithmic_bytes_per_launch": pw_bytes / max(pw_n, 1), "peak_kind": peak_kind,
                      "timing": "CUDA events around each launch in eager decompositions run one at a time on "
                                "one stream right after the graph-timed region (graph event nodes carry no timings)"})
+    # the dominant launch alone: the mode-1 power step on one 400^3 tensor (the
+    # class above also averages the launches on the 4000-fiber AMM samples)
+    if head["prec"] in ("tf32", "bf16"):
+        X = torch.randn(30, DIMS[0], device="cuda").t()
+        for _ in range(3):
+            tk.power_step(dev["lowrank"], DIMS, 0, X, prec=head["prec"])
+        torch.cuda.synchronize()
+        tk.profile_enable(True)
+        for _ in range(10):
+            tk.power_step(dev["lowrank"], DIMS, 0, X, prec=head["prec"])
+        torch.cuda.synchronize()
+        n1, ms1, b1, _ = tk.profile_read(pclass)
+        tk.profile_enable(False)
+        if n1:
+            g1 = b1 / (ms1 / 1e3) / 1e9
+            roofline["mode1_full_tensor"] = {"launches": n1, "ms_per_launch": ms1 / n1, "achieved": g1,
+                                             "frac": g1 / peaks["hbm_gbs"], "unit": "GB/s",
+                                             "algorithmic_bytes_per_launch": b1 / n1,
+                                             "timing": "CUDA events around 10 back-to-back launches of the "
+                                                       "mode-1 power step on the 256 MB tensor (L = 30)"}
     kernels = {}
     for k in PROFILED:
         if k == pclass:

@@ -267,11 +267,13 @@ def gaussian(rows, cols, seed, stream_id, dtype=torch.float32, device="cuda", st
     return out
 
 
-def power_step(A, dims, mode, X, stream=None):
+def power_step(A, dims, mode, X, stream=None, prec="fp32"):
+    """X_out = A_(n) (A_(n)^T X) (one power step of Strategy A); prec "tf32" /
+    "bf16" run it on the tensor cores (see tucker_power_step)."""
     I = dims[mode]
     L = X.shape[1]
     out = factor_tensor(I, L, A.dtype, A.device)
-    o = make_opts(stream=stream)
+    o = make_opts(stream=stream, prec=prec)
     _check("tucker_power_step", lib().tucker_power_step(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode,
                                                         X.data_ptr(), L, out.data_ptr(), C.byref(o)))
     return out
