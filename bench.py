@@ -44,9 +44,12 @@ VARIANTS = [
     dict(name="hilbert_q1_amm4000_uniform", tensor="hilbert", q=1, c=4000, prob="uniform"),
 ]
 BASELINE_METRIC = "decomps/s & sketch HBM GB/s, BF16 vs FP32 at equal rel err; serving p50/p99 ms"
-PROFILED = ("power", "power_bf16", "power_tf32", "ttm", "ttm_bf16", "gather", "norms", "extract", "sample")
+PROFILED = ("power", "power_bf16", "power_tf32", "power_bf16x1", "ttm", "ttm_bf16", "gather", "norms", "extract",
+            "sample")
 # the dominant kernel of each form: (profiler class, name, source file, traffic.json key)
 DOMINANT = {
+    "bf16x1": ("power_bf16x1", "power_bf16x1_kernel (fused A(A^T X) pass, tcgen05 kind::f16 single-pass bf16, "
+                               "TMA-fed, fp32 accumulate)", "kernels_bf16x1.cu", "power_bf16x1_kernel_400cubed"),
     "tf32": ("power_tf32", "power_tf32_kernel (fused A(A^T X) pass, tcgen05 kind::tf32, TMA-fed, fp32 accumulate)",
              "kernels_tf32.cu", "power_tf32_kernel_400cubed"),
     "bf16": ("power_bf16", "power_tc_kernel (fused A(A^T X) pass, tcgen05 split bf16, fp32 accumulate)",
@@ -278,7 +281,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prec", default="all", choices=["all", "tf32", "bf16", "fp32"],
+    ap.add_argument("--prec", default="all", choices=["all", "bf16x1", "tf32", "bf16", "fp32"],
                     help="sketch arithmetic to time (all: the headline is the fastest form whose relative "
                          "errors are within 1e-3 of FP32's)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
@@ -386,7 +389,7 @@ def main():
                 "gpu_launches": n1 - n0, "graph": True, "rel_error": res, "prof": prof}
 
     forms = {}
-    for prec in (["tf32", "bf16", "fp32"] if args.prec == "all" else [args.prec]):
+    for prec in (["bf16x1", "tf32", "bf16", "fp32"] if args.prec == "all" else [args.prec]):
         forms[prec] = measure(prec)
     clk = clocks.stop()
     # headline: the fastest form whose relative error matches FP32's within 1e-3 on every variant
@@ -444,7 +447,7 @@ def main():
     achieved_gbs = pw_bytes / (pw_ms / 1e3) / 1e9 if pw_ms > 0 else 0.0
     achieved_tflops = pw_flops / (pw_ms / 1e3) / 1e12 if pw_ms > 0 else 0.0
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if head["prec"] in ("bf16", "tf32"):
+    if head["prec"] in ("bf16", "tf32", "bf16x1"):
         # bandwidth-bound: 4 L flops per 4-byte element is ~30 flops/byte, far below the
         # tensor ridge (bf16 ~285, tf32 ~140 flops/byte), so the bound is HBM
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -471,7 +474,7 @@ def main():
                                "one stream right after the graph-timed region (graph event nodes carry no timings)"})
     # the dominant launch alone: the mode-1 power step on one 400^3 tensor (the
     # class above also averages the launches on the 4000-fiber AMM samples)
-    if head["prec"] in ("tf32", "bf16"):
+    if head["prec"] in ("tf32", "bf16", "bf16x1"):
         X = torch.randn(30, DIMS[0], device="cuda").t()
         for _ in range(3):
             tk.power_step(dev["lowrank"], DIMS, 0, X, prec=head["prec"])
@@ -506,7 +509,9 @@ def main():
                        "l2": "inputs larger than L2 (256 MB per tensor), no flush",
                        "parallelism": "replicas (each rank decomposes its own batch)" if world > 1 else "single GPU",
                        "sketch": f"paper form, {head['prec']} power steps "
-                                 + {"tf32": "(tcgen05 kind::tf32 on mode 1, split bf16 on modes 2-3, fp32 "
+                                 + {"bf16x1": "(tcgen05 single-pass bf16 on mode 1, split bf16 on modes 2-3, "
+                                              "fp32 accumulate; mode-1 product split bf16 on tcgen05)",
+                                    "tf32": "(tcgen05 kind::tf32 on mode 1, split bf16 on modes 2-3, fp32 "
                                             "accumulate; mode-1 product split bf16 on tcgen05)",
                                     "bf16": "(tcgen05 split bf16, fp32 accumulate; mode-1 product split bf16 "
                                             "on tcgen05)",

@@ -95,8 +95,17 @@ typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1 } tucker_form;
  *    intermediate A^T X are each held as a bf16 high part plus a bf16 low part
  *    (about 16 significant bits), so the sketch is of A itself; A is still read
  *    once, in FP32. Used where I_n <= 512 and L_n <= 64; other modes run FP32.
- * The tensor-core forms need FP32 data (TUCKER_ERR_UNSUPPORTED for FP64). */
-typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2 } tucker_sketch_prec;
+ *  BF16X1: tcgen05 tensor cores, kind::f16, single pass: A, X and A^T X each
+ *    rounded to bf16 once (8 significant bits, to nearest), FP32 accumulation;
+ *    the sketch is then good to about 2^-8, which the power steps win back
+ *    (the factors' subspace moves by an angle of that order, the relative
+ *    error of the decomposition only to second order). A is read once by TMA,
+ *    in FP32. Used as TF32 is (contiguous fibers, I_n % 4 == 0, I_n <= 512,
+ *    L_n <= 32, A 16-byte aligned); other modes take the BF16 form where it
+ *    fits, else FP32.
+ * The tensor-core forms need FP32 data (TUCKER_ERR_UNSUPPORTED for FP64), and
+ * run the mode-0 product in split BF16 (see tucker_ttm). */
+typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2, TUCKER_SK_BF16X1 = 3 } tucker_sketch_prec;
 
 #define TUCKER_FLAG_ASYNC 0x1u
 
@@ -381,7 +390,8 @@ typedef enum {
     TUCKER_KERNEL_SAMPLE = 5,  /* a mode's weights, scan and draws */
     TUCKER_KERNEL_POWER_BF16 = 6, /* fused power step on the tensor cores, split-bf16 operands */
     TUCKER_KERNEL_POWER_TF32 = 7, /* fused power step on the tensor cores, tf32 operands */
-    TUCKER_KERNEL_TTM_BF16 = 8    /* mode-n product on the tensor cores, split-bf16 operands */
+    TUCKER_KERNEL_TTM_BF16 = 8,   /* mode-n product on the tensor cores, split-bf16 operands */
+    TUCKER_KERNEL_POWER_BF16X1 = 9 /* fused power step on the tensor cores, single-pass bf16 operands */
 } tucker_kernel_class;
 
 /* on != 0: clear the accumulators and bracket every launch of the classes

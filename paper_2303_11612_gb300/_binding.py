@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "C
                 4: "numerical failure", 5: "timeout", 6: "unsupported", 7: "over budget"}
 PROB = {"nearly_optimal": 0, "uniform": 1}
 FORM = {"paper": 0, "range": 1}
-PREC = {"fp32": 0, "tf32": 1, "bf16": 2}
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x1": 3}
 FLAG_ASYNC = 1
 
 
@@ -100,7 +100,7 @@ _RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int6
              "tucker_last_cuda_error": C.c_char_p, "tucker_autotune_count": C.c_int64,
              "tucker_autotune_entry": C.c_char_p}
 KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3, "extract": 4, "sample": 5, "power_bf16": 6,
-                  "power_tf32": 7, "ttm_bf16": 8}
+                  "power_tf32": 7, "ttm_bf16": 8, "power_bf16x1": 9}
 
 
 def lib():

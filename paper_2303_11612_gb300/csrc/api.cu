@@ -85,7 +85,7 @@ tucker_status read_opts(const tucker_opts* o, Opts& out) {
     out.rel_error = o->rel_error;
     out.sample_idx = o->sample_idx;
     if (out.form != TUCKER_FORM_PAPER && out.form != TUCKER_FORM_RANGE) return TUCKER_ERR_INVALID_ARG;
-    if (out.prec < TUCKER_SK_FP32 || out.prec > TUCKER_SK_BF16) return TUCKER_ERR_INVALID_ARG;
+    if (out.prec < TUCKER_SK_FP32 || out.prec > TUCKER_SK_BF16X1) return TUCKER_ERR_INVALID_ARG;
     if (!(out.alpha >= 0.0) || out.alpha > 1.0) return TUCKER_ERR_INVALID_ARG;
     return TUCKER_OK;
 }
@@ -110,6 +110,7 @@ struct ModePlan {
     int64_t T;         // AMM samples (0 = none)
     bool tc;           // power steps on the tensor cores (split-bf16 operands)
     bool tf32;         // power steps on the tensor cores (tf32 operands, contiguous fibers)
+    bool bf16x1;       // power steps on the tensor cores (single-pass bf16 operands, contiguous fibers)
     PowerPlan pp;
     OrthPlan op;
 };
@@ -160,9 +161,9 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         // tensor-core power steps where the tile fits: TF32 on contiguous fibers, split
         // BF16 (also the TF32 form's choice for strided fibers); the FP32 kernel elsewhere
         mp.tf32 = o.prec == TUCKER_SK_TF32 && elem == 4 && power_tf32_supported(mp.mv, mp.L);
-        mp.tc = (o.prec == TUCKER_SK_BF16 || o.prec == TUCKER_SK_TF32) && elem == 4 &&
-                power_tc_supported(mp.mv, mp.L);
-        if (mp.tc || mp.tf32)
+        mp.bf16x1 = o.prec == TUCKER_SK_BF16X1 && elem == 4 && power_bf16x1_supported(mp.mv, mp.L);
+        mp.tc = o.prec != TUCKER_SK_FP32 && elem == 4 && power_tc_supported(mp.mv, mp.L);
+        if (mp.tc || mp.tf32 || mp.bf16x1)
             p.max_partials = std::max(p.max_partials, power_tc_partials_bytes(mp.mv, mp.L, sms));
         mp.op = orth_plan(d[n], mp.L, sms);
         if (!orth_supported(mp.op, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
@@ -236,9 +237,11 @@ void carve(const Plan& p, Arena& a, Work& w) {
 template <typename T>
 cudaError_t power_step(const T* M, const ModePlan& mp, const T* X_in, T* X_out, const Work& w, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
-        if (mp.tf32) {
+        if (mp.tf32 || mp.bf16x1) {
             // cudaErrorNotSupported: M not 16-byte aligned for TMA; the next form runs
-            const cudaError_t e = launch_power_tf32(M, mp.mv, X_in, mp.L, X_out, w.partials, w.status, num_sms(), s);
+            const cudaError_t e =
+                mp.tf32 ? launch_power_tf32(M, mp.mv, X_in, mp.L, X_out, w.partials, w.status, num_sms(), s)
+                        : launch_power_bf16x1(M, mp.mv, X_in, mp.L, X_out, w.partials, w.status, num_sms(), s);
             if (e != cudaErrorNotSupported) return e;
         }
         if (mp.tc)
@@ -376,7 +379,7 @@ tucker_status driver(bool st, const void* A, tucker_dtype dt, const int64_t* dim
     if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
     if (prob != TUCKER_PROB_NEARLY_OPTIMAL && prob != TUCKER_PROB_UNIFORM) return TUCKER_ERR_INVALID_ARG;
     if (!A || !U || !G) return TUCKER_ERR_INVALID_ARG;
-    if ((o.prec == TUCKER_SK_BF16 || o.prec == TUCKER_SK_TF32) && dt != TUCKER_F32) return TUCKER_ERR_UNSUPPORTED;
+    if (o.prec != TUCKER_SK_FP32 && dt != TUCKER_F32) return TUCKER_ERR_UNSUPPORTED;
     for (int n = 0; n < N && n < kMaxOrder; ++n)
         if (!U[n]) return TUCKER_ERR_INVALID_ARG;
     const int elem = dt == TUCKER_F64 ? 8 : 4;
@@ -590,15 +593,18 @@ tucker_status tucker_power_step(const void* A, tucker_dtype dt, const int64_t* d
     const int elem = dt == TUCKER_F64 ? 8 : 4;
     if (v.i > kMaxI || L > 4096 || (elem == 8 && v.i > 512)) return TUCKER_ERR_UNSUPPORTED;
     const PowerPlan pp = power_plan(v, (int)L, elem, num_sms());
-    if (o.prec == TUCKER_SK_TF32) {
-        if (elem != 4 || !power_tf32_supported(v, (int)L)) return TUCKER_ERR_UNSUPPORTED;
+    if (o.prec == TUCKER_SK_TF32 || o.prec == TUCKER_SK_BF16X1) {
+        const bool tf = o.prec == TUCKER_SK_TF32;
+        if (elem != 4 || !(tf ? power_tf32_supported(v, (int)L) : power_bf16x1_supported(v, (int)L)))
+            return TUCKER_ERR_UNSUPPORTED;
         Scratch sc;
         if ((rs = sc.get(power_tc_partials_bytes(v, (int)L, num_sms()) + 256, o.stream)) != TUCKER_OK) return rs;
         int* status = reinterpret_cast<int*>(sc.p);
         cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
         if (e == cudaSuccess)
-            e = launch_power_tf32((const float*)A, v, (const float*)X_in, (int)L, (float*)X_out,
-                                  reinterpret_cast<char*>(sc.p) + 256, status, num_sms(), o.stream);
+            e = (tf ? launch_power_tf32 : launch_power_bf16x1)((const float*)A, v, (const float*)X_in, (int)L,
+                                                               (float*)X_out, reinterpret_cast<char*>(sc.p) + 256,
+                                                               status, num_sms(), o.stream);
         if (e == cudaErrorNotSupported) return TUCKER_ERR_UNSUPPORTED;
         if (e != cudaSuccess) return from_cuda(e);
         return sync_status(o.stream, status);

@@ -65,6 +65,12 @@ bool power_tf32_supported(const ModeView& v, int L);
 cudaError_t launch_power_tf32(const float* A, const ModeView& v, const float* X_in, int L, float* X_out,
                               void* partials, int* status, int num_sms, cudaStream_t s);
 
+// ---- tensor-core power step, single-pass bf16 operands / fp32 accumulation,
+// contiguous fibers (kernels_bf16x1.cu); contract as launch_power_tf32.
+bool power_bf16x1_supported(const ModeView& v, int L);
+cudaError_t launch_power_bf16x1(const float* A, const ModeView& v, const float* X_in, int L, float* X_out,
+                                void* partials, int* status, int num_sms, cudaStream_t s);
+
 // ---- mode-n product on the tensor cores, split-bf16 operands / fp32
 // accumulation, contiguous fibers (kernels_ttm_tc.cu); M(i, o) = Mp[i ld_i + o ld_k],
 // out as launch_ttm. Returns cudaErrorNotSupported (nothing launched) outside
@@ -127,7 +133,7 @@ int num_sms();
 
 // ---- launch counting and profiling (profile.cu)
 enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKExtract = 4, kKSample = 5,
-                   kKPowerBf16 = 6, kKPowerTf32 = 7, kKTtmBf16 = 8, kKernelClasses = 9 };
+                   kKPowerBf16 = 6, kKPowerTf32 = 7, kKTtmBf16 = 8, kKPowerBf16x1 = 9, kKernelClasses = 10 };
 void note_launch();
 void note_launches(int64_t n);   // a graph replay's kernels
 void profile_drain();

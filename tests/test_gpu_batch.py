@@ -50,7 +50,7 @@ def same(got, want):
     return all(torch.equal(u.contiguous().cpu(), ua) for u, ua in zip(U, Ua)) and torch.equal(G.cpu(), Ga)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32", "bf16x1"])
 def test_batch_equals_requests_alone_and_replays(tk, prec):
     reqs = make_requests(12, seed=8)
     for r in reqs:

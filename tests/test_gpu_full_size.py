@@ -66,7 +66,7 @@ def bench_tensors():
     return dims, ranks, low, hil
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32", "bf16x1"])
 def test_benchmark_workload_400cubed(tk, bench_tensors, prec):
     dims, ranks, low, hil = bench_tensors
     variants = [
@@ -94,16 +94,20 @@ def test_benchmark_workload_400cubed(tk, bench_tensors, prec):
                     assert np.linalg.norm(u @ u.T - uo @ uo.T, 2) <= 1e-4
             else:
                 # tensor-core forms: the sketch's rounding moves RE only to second
-                # order and the mode-1 product (split bf16, ~2^-16) to about 1e-6
-                assert abs(re - reo) <= 1e-4, (kw, re, reo)
+                # order and the mode-1 product (split bf16, ~2^-16) to about 1e-6;
+                # the single-pass bf16 sketch (2^-8) is held to the 1e-3 bar
+                bar = 1e-3 if prec == "bf16x1" else 1e-4
+                assert abs(re - reo) <= bar, (kw, re, reo)
         else:
             # Hilbert: its mode-n singular values fall by orders of magnitude per
             # index, so a power-step output (singular values sigma_i^2) loses every
             # direction with sigma_i / sigma_1 below ~2.4e-4 to FP32 rounding. The
             # FP64 oracle reaches RE 9.1e-5 at q = 2 and 2.3e-4 with AMM at q = 1;
             # FP32 arithmetic reaches ~2e-4 and ~1.5e-3; the FP64 data path is at
-            # least as accurate as the oracle (test below).
-            assert re <= 2e-3, (kw, re, reo)
+            # least as accurate as the oracle (test below). The single-pass bf16
+            # sketch keeps only directions whose sigma_i^2 / sigma_1^2 exceeds its
+            # rounding (2^-8): RE ~2.2e-3 with AMM at q = 1 (bar 3e-3)
+            assert re <= (3e-3 if prec == "bf16x1" else 2e-3), (kw, re, reo)
         if kw["c"]:
             # mode 1 samples the input tensor itself: identical weights, identical draws
             assert np.array_equal(res[2][0].cpu().numpy(), info["idx"][0]), kw
@@ -131,7 +135,7 @@ def test_fourth_order_96(tk):
     A64 = A.astype(np.float64)
     Uo, Go = ot.rsthosvd(A64, ranks, P=8, q=2, seed=0)
     reo = ot.relative_error(A64, Uo, Go)
-    for prec, bar in (("fp32", 1e-5), ("bf16", 1e-3), ("tf32", 1e-3)):
+    for prec, bar in (("fp32", 1e-5), ("bf16", 1e-3), ("tf32", 1e-3), ("bf16x1", 1e-3)):
         (res,) = in_flight(tk, [(dev(A), dims, ranks, dict(P=8, q=2, c=0, prob="uniform", seed=0))], prec)
         U = [u.double().cpu().numpy() for u in res[0]]
         G = synth.from_flat(res[1].double().cpu().numpy(), ranks)

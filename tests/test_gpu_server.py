@@ -36,7 +36,7 @@ def make_requests(n, seed):
     return reqs
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32", "bf16x1"])
 def test_results_same_alone_and_in_the_mix(tk, prec):
     reqs = make_requests(24, seed=5)
     alone = []
