@@ -53,13 +53,15 @@ constexpr int kHBSub = 2 * kHBChunk;       // bf16 sub-stage (128 values i) = 16
 constexpr int kHCStages = 2;               // bf16 sub-stages
 constexpr int kHXChunk = 4096;             // X^T bf16 chunk: 32 rows l x 128 bytes (64 values i)
 constexpr int kHWBytes = 4096;             // W^T bf16: 32 rows l x 128 bytes (64 fibers)
+constexpr int kHWBufs = 2;                 // W^T buffers
 constexpr int kHTransposers = 8;           // warps 4 .. 11
 constexpr int kHWaitIters = 1 << 22;
 constexpr size_t kHSmemMax = 227 * 1024;
 constexpr uint32_t kHTmemCols = 512;
 constexpr uint32_t kHD1Col = 128;          // D1: 2 x 64 columns
 constexpr uint32_t kHTpCol = 256;          // T': 2 x (4 blocks x 32 columns)
-constexpr int kHBars = 25;
+constexpr int kHBars = 2 * kHStages + 17;        // 8 bytes each; 256 reserved
+static_assert(kHBars * 8 + 8 <= 256, "barrier area");
 
 struct HLayout {
     int nc = 0;     // FP32 chunks of 32 values
@@ -76,7 +78,7 @@ HLayout h_layout(int I) {
     t.c_off = (size_t)kHStages * kHSub;
     t.x_off = t.c_off + (size_t)kHCStages * kHBSub;
     t.w_off = t.x_off + (size_t)t.nbc * kHXChunk;
-    t.bar_off = t.w_off + 2 * kHWBytes;
+    t.bar_off = t.w_off + (size_t)kHWBufs * kHWBytes;
     t.bytes = t.bar_off + 256 + 1024;
     return t;
 }
@@ -108,18 +110,18 @@ __global__ void __launch_bounds__(kHThreads, 1)
     unsigned char* Cb = smem + (size_t)kHStages * kHSub;               // bf16 sub-stages
     unsigned char* Xs = Cb + (size_t)kHCStages * kHBSub;               // X^T bf16
     unsigned char* Ws = Xs + (size_t)nbc * kHXChunk;                   // W^T bf16 [2]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(Ws + 2 * kHWBytes);
-    uint64_t* f_full = bar;            // [4] FP32 sub-stage loaded (TMA bytes)
-    uint64_t* f_empty = bar + 4;       // [4] FP32 sub-stage read (8 warps)
-    uint64_t* c_full = bar + 8;        // [2] bf16 sub-stage written (8 warps)
-    uint64_t* c_empty = bar + 10;      // [2] bf16 sub-stage consumed by the first product
-    uint64_t* d1_full = bar + 12;      // [2] first product done
-    uint64_t* d1_empty = bar + 14;     // [2] first product read back (2 warps)
-    uint64_t* w_full = bar + 16;       // [2] W written (2 warps)
-    uint64_t* w_empty = bar + 18;      // [2] second product done with W
-    uint64_t* tp_full = bar + 20;      // [2] T' of a tile written (8 warps)
-    uint64_t* tp_empty = bar + 22;     // [2] second product done with T'
-    uint64_t* done = bar + 24;         // every product done
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Ws + kHWBufs * kHWBytes);
+    uint64_t* f_full = bar;                    // FP32 sub-stage loaded (TMA bytes)
+    uint64_t* f_empty = f_full + kHStages;     // FP32 sub-stage read (8 warps)
+    uint64_t* c_full = f_empty + kHStages;     // [2] bf16 sub-stage written (8 warps)
+    uint64_t* c_empty = c_full + 2;            // [2] bf16 sub-stage consumed by the first product
+    uint64_t* d1_full = c_empty + 2;           // [2] first product done
+    uint64_t* d1_empty = d1_full + 2;          // [2] first product read back (2 warps)
+    uint64_t* w_full = d1_empty + 2;           // [kHWBufs] W written (2 warps)
+    uint64_t* w_empty = w_full + 2;            // [kHWBufs] second product done with W
+    uint64_t* tp_full = w_empty + 2;           // [2] T' of a tile written (8 warps)
+    uint64_t* tp_empty = tp_full + 2;          // [2] second product done with T'
+    uint64_t* done = tp_empty + 2;             // every product done
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + kHBars);
     volatile int* flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -139,10 +141,12 @@ __global__ void __launch_bounds__(kHThreads, 1)
     }
     if (tid == 0) {
         for (int k = 0; k < kHBars; ++k) {
+            const uint64_t* b = &bar[k];
             uint32_t count = 1;                                            // TMA, commits, done
-            if ((k >= 4 && k < 8) || (k >= 8 && k < 10) || (k >= 20 && k < 22))
-                count = kHTransposers;                                     // f_empty, c_full, tp_full
-            if ((k >= 14 && k < 16) || (k >= 16 && k < 18)) count = 2;     // d1_empty, w_full
+            if ((b >= f_empty && b < f_empty + kHStages) || (b >= c_full && b < c_full + 2) ||
+                (b >= tp_full && b < tp_full + 2))
+                count = kHTransposers;
+            if ((b >= d1_empty && b < d1_empty + 2) || (b >= w_full && b < w_full + 2)) count = 2;
             tc::mbar_init(&bar[k], count);
         }
         *flag = 0;
@@ -192,11 +196,12 @@ __global__ void __launch_bounds__(kHThreads, 1)
             const uint64_t c_desc = tc::desc_sw128(tc::smem_u32(Cb), 16, 1024);
             const uint64_t w_desc = tc::desc_sw128(tc::smem_u32(Ws), 16, 1024);
             auto second = [&](int64_t k) -> bool {
-                const int b = (int)(k & 1);
-                const uint32_t par = (uint32_t)((k >> 1) & 1);
-                if (!wait_bar(&w_full[b], par, flag) || !wait_bar(&tp_full[b], par, flag)) return false;
+                const int b = (int)(k & 1), bw = (int)(k % kHWBufs);
+                if (!wait_bar(&w_full[bw], (uint32_t)((k / kHWBufs) & 1), flag) ||
+                    !wait_bar(&tp_full[b], (uint32_t)((k >> 1) & 1), flag))
+                    return false;
                 tc::fence_after_sync();
-                const uint64_t wb = w_desc + (uint64_t)((b * kHWBytes) >> 4);
+                const uint64_t wb = w_desc + (uint64_t)((bw * kHWBytes) >> 4);
                 const uint32_t tb = tmem + kHTpCol + (uint32_t)(b * 128);
                 for (int mb = 0; mb < nsub; ++mb) {
 #pragma unroll
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(kHThreads, 1)
                                         wb + (uint64_t)(ks * 2), id2, k > 0 || ks > 0);
                 }
                 tc::commit(&tp_empty[b]);
-                tc::commit(&w_empty[b]);
+                tc::commit(&w_empty[bw]);
                 return true;
             };
             bool ok = true;
@@ -266,14 +271,15 @@ __global__ void __launch_bounds__(kHThreads, 1)
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&d1_empty[b]);
-            if (k >= 2 && !wait_bar(&w_empty[b], (uint32_t)(((k >> 1) - 1) & 1), flag)) {
+            const int bw = (int)(k % kHWBufs);
+            if (k >= kHWBufs && !wait_bar(&w_empty[bw], (uint32_t)((k / kHWBufs - 1) & 1), flag)) {
                 fail(flag, status);
                 break;
             }
             if (lane < 16) {
                 // row l of W^T in bf16: fibers 8 q .. 8 q + 7 in 16-byte group q
                 const int l = quarter * 16 + lane;
-                unsigned char* row = Ws + b * kHWBytes + (l >> 3) * 1024 + (l & 7) * 128;
+                unsigned char* row = Ws + bw * kHWBytes + (l >> 3) * 1024 + (l & 7) * 128;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const float* f = reinterpret_cast<const float*>(&r[8 * q]);
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(kHThreads, 1)
             }
             tc::fence_async_smem();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&w_full[b]);
+            if (lane == 0) tc::mbar_arrive(&w_full[bw]);
         }
     } else {
         // transposers: warp w reads FP32 chunk 4 u + w % 4 (rows i = its lanes) of
