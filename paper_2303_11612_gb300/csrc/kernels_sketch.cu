@@ -162,13 +162,41 @@ __global__ void __launch_bounds__(kT) power_kernel(const T* __restrict__ A, Mode
     }
 }
 
+// out[e] = sum over parts of partial[p * count + e]: 32 consecutive outputs per
+// block (coalesced), the parts split over the block's warps (warp w sums parts
+// w, w + warps, ... in increasing order), the warps' sums combined in warp
+// order, so the result does not depend on scheduling.
 template <typename T>
 __global__ void __launch_bounds__(kT) reduce_partials_kernel(const T* __restrict__ partial, int parts,
                                                              int64_t count, T* __restrict__ out) {
-    for (int64_t e = blockIdx.x * (int64_t)kT + threadIdx.x; e < count; e += (int64_t)gridDim.x * kT) {
+    constexpr int kG = kT / 32;
+    __shared__ T sh[kG][32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < count; e0 += (int64_t)gridDim.x * 32) {
+        const int64_t e = e0 + lane;
         T s = T(0);
-        for (int p = 0; p < parts; ++p) s += partial[(int64_t)p * count + e];
-        out[e] = s;
+        if (e < count) {
+            int p = g;
+            for (; p + 3 * kG < parts; p += 4 * kG) {
+                const T x0 = partial[(int64_t)p * count + e], x1 = partial[(int64_t)(p + kG) * count + e];
+                const T x2 = partial[(int64_t)(p + 2 * kG) * count + e];
+                const T x3 = partial[(int64_t)(p + 3 * kG) * count + e];
+                s += x0;
+                s += x1;
+                s += x2;
+                s += x3;
+            }
+            for (; p < parts; p += kG) s += partial[(int64_t)p * count + e];
+        }
+        sh[g][lane] = s;
+        __syncthreads();
+        if (g == 0 && e < count) {
+            T t = sh[0][lane];
+#pragma unroll
+            for (int q = 1; q < kG; ++q) t += sh[q][lane];
+            out[e] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -344,8 +372,8 @@ cudaError_t launch_power_plan(const T* A, const ModeView& v, const T* X_in, int 
 
 template <typename T>
 cudaError_t launch_reduce_partials(const T* partial, int parts, int64_t count, T* out, cudaStream_t s) {
-    int64_t blocks = (count + kT - 1) / kT;
-    if (blocks > 2048) blocks = 2048;
+    int64_t blocks = (count + 31) / 32;
+    if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
     reduce_partials_kernel<T><<<(unsigned)blocks, kT, 0, s>>>(partial, parts, count, out);
     note_launch();
