@@ -179,7 +179,11 @@ tucker_status tucker_gaussian(void* out, tucker_dtype dt, int64_t rows, int64_t 
                               uint64_t seed, uint32_t stream_id, const tucker_opts* opts);
 
 /* One power step of Strategy A fused into a single pass over the tensor:
- * X_out = A_(n) (A_(n)^T X_in), X_in and X_out I_n x L column-major. */
+ * X_out = A_(n) (A_(n)^T X_in), X_in and X_out I_n x L column-major.
+ * opts->prec selects the arithmetic (see tucker_sketch_prec): FP32 for every
+ * mode view; TF32 and BF16X1 for contiguous fibers (mode 0) within their
+ * limits; BF16 (split) for I_n <= 512 and L <= 64. Outside a form's limits the
+ * call returns TUCKER_ERR_UNSUPPORTED (it never substitutes another form). */
 tucker_status tucker_power_step(const void* A, tucker_dtype dt, const int64_t* dims, int N,
                                 int mode, const void* X_in, int64_t L, void* X_out,
                                 const tucker_opts* opts);
