@@ -100,9 +100,10 @@ typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1 } tucker_form;
  *    the sketch is then good to about 2^-8, which the power steps win back
  *    (the factors' subspace moves by an angle of that order, the relative
  *    error of the decomposition only to second order). A is read once by TMA,
- *    in FP32. Used as TF32 is (contiguous fibers, I_n % 4 == 0, I_n <= 512,
- *    L_n <= 32, A 16-byte aligned); other modes take the BF16 form where it
- *    fits, else FP32.
+ *    in FP32. Used for contiguous fibers (mode 0, or an AMM sample) and for
+ *    strided fibers with Lf = I_1 ... I_{n-1} >= 64 and Lf % 4 == 0, where
+ *    I_n % 4 == 0, I_n <= 512, L_n <= 32 and A is 16-byte aligned; other
+ *    modes take the BF16 form where it fits, else FP32.
  * The tensor-core forms need FP32 data (TUCKER_ERR_UNSUPPORTED for FP64), and
  * run the mode-0 product in split BF16 (see tucker_ttm). */
 typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2, TUCKER_SK_BF16X1 = 3 } tucker_sketch_prec;
@@ -181,8 +182,9 @@ tucker_status tucker_gaussian(void* out, tucker_dtype dt, int64_t rows, int64_t 
 /* One power step of Strategy A fused into a single pass over the tensor:
  * X_out = A_(n) (A_(n)^T X_in), X_in and X_out I_n x L column-major.
  * opts->prec selects the arithmetic (see tucker_sketch_prec): FP32 for every
- * mode view; TF32 and BF16X1 for contiguous fibers (mode 0) within their
- * limits; BF16 (split) for I_n <= 512 and L <= 64. Outside a form's limits the
+ * mode view; TF32 for contiguous fibers (mode 0) and BF16X1 for contiguous or
+ * wide-strided fibers, within their limits; BF16 (split) for I_n <= 512 and
+ * L <= 64. Outside a form's limits the
  * call returns TUCKER_ERR_UNSUPPORTED (it never substitutes another form). */
 tucker_status tucker_power_step(const void* A, tucker_dtype dt, const int64_t* dims, int N,
                                 int mode, const void* X_in, int64_t L, void* X_out,

@@ -26,6 +26,11 @@
 // the CTA's tiles and is written once as its partial; the partials are summed
 // in a fixed order afterwards.
 //
+// Strided fibers (modes 2..N, stride Lf >= 64): TMA loads 3-D boxes of 32
+// fibers x 32 values (fibers contiguous, one 128-byte row per value i), a tile
+// being 64 consecutive fibers of one slab (columns past Lf load as zeros), and a
+// transposer lane reads its own row instead of a column; the rest is the same.
+//
 // Warp roles (one CTA per SM, persistent over tiles j = blockIdx.x + k gridDim.x):
 // warps 0-1 read W back (tensor-memory lane quarters 0 and 1), warp 2 issues
 // the TMA loads, warp 3 the MMAs (first product of tile k, then the second
@@ -101,9 +106,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&p);
 }
 
+template <bool STRIDED>
 __global__ void __launch_bounds__(kHThreads, 1)
     power_bf16x1_kernel(const __grid_constant__ CUtensorMap map, int I, const float* __restrict__ X, int L,
-                        float* __restrict__ partial, int64_t tiles, int nc, int nbc, int* status) {
+                        float* __restrict__ partial, int64_t tiles, int64_t tiles_per_slab, int nc, int nbc,
+                        int* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // swizzled buffers start on 1024-byte boundaries (the launch adds 1 KB of slack)
     unsigned char* smem = smem_raw + ((1024 - (tma::smem_addr(smem_raw) & 1023)) & 1023);
@@ -164,7 +171,11 @@ __global__ void __launch_bounds__(kHThreads, 1)
             int64_t g = 0;
             bool ok = true;
             for (int64_t k = 0; k < nloc && ok; ++k) {
-                const int j0 = (int)((blockIdx.x + k * gridDim.x) * kHJB);
+                const int64_t tile = blockIdx.x + k * gridDim.x;
+                // contiguous: fibers tile * 64 ..; strided: slab r, fibers a0 .. a0 + 63 of it
+                const int j0 = (int)(tile * kHJB);
+                const int r = STRIDED ? (int)(tile / tiles_per_slab) : 0;
+                const int a0 = STRIDED ? (int)((tile % tiles_per_slab) * kHJB) : 0;
                 for (int u = 0; u < nsub; ++u, ++g) {
                     const int slot = (int)(g % kHStages);
                     if (g >= kHStages && !wait_bar(&f_empty[slot], (uint32_t)((g / kHStages - 1) & 1), flag)) {
@@ -175,8 +186,16 @@ __global__ void __launch_bounds__(kHThreads, 1)
                     const int nch = min(kHSubChunks, nc - u * kHSubChunks);
                     tma::expect_tx(&f_full[slot], (uint32_t)(nch * kHBox));
                     unsigned char* dst = smem + (size_t)slot * kHSub;
-                    for (int cc = 0; cc < nch; ++cc)
-                        tma::load_2d(dst + cc * kHBox, &map, (u * kHSubChunks + cc) * 32, j0, &f_full[slot]);
+                    for (int cc = 0; cc < nch; ++cc) {
+                        const int i0 = (u * kHSubChunks + cc) * 32;
+                        if (STRIDED) {
+                            // chunk cc: values i0 .. i0 + 31 (rows) x fibers a0 .. a0 + 31, then a0 + 32 ..
+                            tma::load_3d(dst + cc * kHBox, &map, a0, i0, r, &f_full[slot]);
+                            tma::load_3d(dst + cc * kHBox + kHBox / 2, &map, a0 + 32, i0, r, &f_full[slot]);
+                        } else {
+                            tma::load_2d(dst + cc * kHBox, &map, i0, j0, &f_full[slot]);
+                        }
+                    }
                 }
             }
             if (*flag) {
@@ -310,7 +329,17 @@ __global__ void __launch_bounds__(kHThreads, 1)
                 }
                 const int c = u * kHSubChunks + quarter;
                 float v[32];
-                if (c < nc) {
+                if (c < nc && STRIDED) {
+                    // row i = this lane of the chunk: fibers 32 half .. + 31 in 16-byte pieces
+                    const unsigned char* row = smem + (size_t)slot * kHSub + quarter * kHBox + half * (kHBox / 2) +
+                                               lane * 128;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 x = *reinterpret_cast<const float4*>(row + ((q ^ (lane & 7)) << 4));
+                        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+                    }
+                } else if (c < nc) {
+                    // fiber j's row of the chunk: value i = this lane
                     const unsigned char* src = smem + (size_t)slot * kHSub + quarter * kHBox +
                                                half * 32 * 128 + (lane & 3) * 4;
 #pragma unroll
@@ -382,8 +411,10 @@ __global__ void __launch_bounds__(kHThreads, 1)
 }  // namespace
 
 bool power_bf16x1_supported(const ModeView& v, int L) {
-    return v.lf == 1 && v.i >= 1 && v.i % 4 == 0 && v.i <= 512 && L >= 1 && L <= 32 &&
-           v.fibers() <= (int64_t)INT_MAX - kHJB && h_layout((int)v.i).bytes <= kHSmemMax;
+    const bool layout = v.lf == 1 || (v.lf >= kHJB && v.lf % 4 == 0);
+    return layout && v.i >= 1 && v.i % 4 == 0 && v.i <= 512 && L >= 1 && L <= 32 &&
+           v.fibers() <= (int64_t)INT_MAX - kHJB && v.rt <= (int64_t)INT_MAX &&
+           h_layout((int)v.i).bytes <= kHSmemMax;
 }
 
 cudaError_t launch_power_bf16x1(const float* A, const ModeView& v, const float* X_in, int L, float* X_out,
@@ -391,21 +422,34 @@ cudaError_t launch_power_bf16x1(const float* A, const ModeView& v, const float* 
     if (!power_bf16x1_supported(v, L) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
     const int I = (int)v.i;
     const int64_t J = v.fibers();
+    const bool strided = v.lf > 1;
     CUtensorMap map;
-    const uint64_t dims[2] = {(uint64_t)I, (uint64_t)J};
-    const uint64_t strides[1] = {(uint64_t)I * sizeof(float)};
-    const uint32_t box[2] = {32, (uint32_t)kHJB};
-    if (!tma::make_map_f32(&map, A, 2, dims, strides, box, true)) return cudaErrorNotSupported;
+    int64_t tiles, per_slab = 1;
+    if (!strided) {
+        const uint64_t dims[2] = {(uint64_t)I, (uint64_t)J};
+        const uint64_t strides[1] = {(uint64_t)I * sizeof(float)};
+        const uint32_t box[2] = {32, (uint32_t)kHJB};
+        if (!tma::make_map_f32(&map, A, 2, dims, strides, box, true)) return cudaErrorNotSupported;
+        tiles = (J + kHJB - 1) / kHJB;
+    } else {
+        // (Lf, I, Rt) with Lf fastest; a box is 32 fibers x 32 values of one slab
+        const uint64_t dims[3] = {(uint64_t)v.lf, (uint64_t)I, (uint64_t)v.rt};
+        const uint64_t strides[2] = {(uint64_t)v.lf * sizeof(float), (uint64_t)v.lf * I * sizeof(float)};
+        const uint32_t box[3] = {32, 32, 1};
+        if (!tma::make_map_f32(&map, A, 3, dims, strides, box, true)) return cudaErrorNotSupported;
+        per_slab = (v.lf + kHJB - 1) / kHJB;
+        tiles = per_slab * v.rt;
+    }
     const HLayout t = h_layout(I);
-    const int64_t tiles = (J + kHJB - 1) / kHJB;
     int grid = (int)(tiles < num_sms ? tiles : num_sms);
     if (grid < 1) grid = 1;
     float* part = reinterpret_cast<float*>(partials);
     const double elems = (double)I * (double)J;
     {
         ProfScope prof(kKPowerBf16x1, elems * sizeof(float), 4.0 * elems * L, s);
-        cudaFuncSetAttribute(power_bf16x1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.bytes);
-        power_bf16x1_kernel<<<grid, kHThreads, t.bytes, s>>>(map, I, X_in, L, part, tiles, t.nc, t.nbc, status);
+        auto k = strided ? power_bf16x1_kernel<true> : power_bf16x1_kernel<false>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.bytes);
+        k<<<grid, kHThreads, t.bytes, s>>>(map, I, X_in, L, part, tiles, per_slab, t.nc, t.nbc, status);
         note_launch();
     }
     const cudaError_t e = cudaGetLastError();

@@ -66,13 +66,21 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("dims,L", CASES)
-def test_bf16x1_power_step(tk, dims, L):
+STRIDED = [
+    ((64, 100, 70), 30, 1),       # stride 64: one full tile per slab, 70 slabs
+    ((100, 132, 60), 24, 1),      # stride 100: a second, partly zero-filled tile per slab
+    ((80, 40, 400), 30, 2),       # stride 3200, one slab: 50 tiles
+    ((64, 8, 36, 20), 17, 2),     # 4th order, stride 512, I_n = 36
+]
+
+
+@pytest.mark.parametrize("dims,L,mode", [(d, l, 0) for d, l in CASES] + STRIDED)
+def test_bf16x1_power_step(tk, dims, L, mode):
     A = synth.lowrank_noise(dims, [min(4, d) for d in dims], rel_noise=0.3, seed=5)
     At = torch.from_numpy(np.ascontiguousarray(synth.flat(A))).cuda()
-    M = ot.unfold(A.astype(np.float64), 0)
-    X = np.random.default_rng(1).standard_normal((dims[0], L)).astype(np.float32).astype(np.float64)
-    st, out = power_bf16x1(tk, At, dims, 0, X)
+    M = ot.unfold(A.astype(np.float64), mode)
+    X = np.random.default_rng(1).standard_normal((dims[mode], L)).astype(np.float32).astype(np.float64)
+    st, out = power_bf16x1(tk, At, dims, mode, X)
     assert st == 0
     got = out.double().cpu().numpy()
     exact = M @ (M.T @ X)
@@ -86,7 +94,7 @@ def test_bf16x1_power_step_rejects_unsupported(tk):
     dims = (40, 36, 32)
     A = torch.randn(40 * 36 * 32, device="cuda")
     X = np.zeros((36, 8))
-    assert power_bf16x1(tk, A, dims, 1, X)[0] == 6               # strided fibers
+    assert power_bf16x1(tk, A, dims, 1, X)[0] == 6               # strided fibers, stride 40 < 64
     assert power_bf16x1(tk, A, dims, 0, np.zeros((40, 40)))[0] == 6   # L > 32
     dims = (42, 36, 32)
     A = torch.randn(42 * 36 * 32, device="cuda")
