@@ -409,6 +409,36 @@ def main():
                              f"saturation throughput, Poisson arrivals")
         del reqs
 
+    # randomized T-HOSVD (Algorithm 1) on the same low-rank tensor in the headline
+    # arithmetic, as a secondary line: every mode sketches the full tensor (modes 2
+    # and 3 through strided fibers), 32 decompositions per batch call
+    thosvd = None
+    try:
+        tb = tk.Batch([dict(which="T", A=dev["lowrank"], dims=DIMS, ranks=RANKS, P=P, q=1, c=0, prob="uniform",
+                            seed=SEED + k) for k in range(len(batch))], prec=head["prec"])
+        for _ in range(args.warmup):
+            tb.run(stream=main_s, sync=False)
+        tb.run(stream=main_s)
+        t_steps = max(3, args.steps // 10)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main_s)
+        for _ in range(t_steps):
+            tb.run(stream=main_s, sync=False)
+        e1.record(main_s)
+        main_s.synchronize()
+        barrier()
+        if any(tb.status()):
+            raise RuntimeError("device status not OK")
+        t_ms = max_over_ranks(e0.elapsed_time(e1))
+        thosvd = {"value": whole_job_rate(len(batch) * t_steps, world, t_ms / 1e3), "unit": "decomps/s",
+                  "prec": head["prec"], "steps": t_steps,
+                  "workload": "randomized T-HOSVD of the 400^3 low-rank tensor, R=20 P=10 q=1, "
+                              f"{len(batch)} per tucker_batch_run call"}
+        del tb
+    except Exception as exc:  # noqa: BLE001
+        thosvd = {"value": None, "error": str(exc)}
+
     # end to end through the public API with pinned host buffers, headline arithmetic:
     # every step submits the whole batch to the library's request loop, which
     # stages each input host->device and each result device->host on the
@@ -525,6 +555,7 @@ def main():
                       for p, f in forms.items()},
             "matches_fp32_rel_err_within_1e-3": equal,
             "serving": serving,
+            "thosvd": thosvd,
             "autotune": tk.autotune_entries(),
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

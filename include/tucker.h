@@ -100,10 +100,12 @@ typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1 } tucker_form;
  *    the sketch is then good to about 2^-8, which the power steps win back
  *    (the factors' subspace moves by an angle of that order, the relative
  *    error of the decomposition only to second order). A is read once by TMA,
- *    in FP32. Used for contiguous fibers (mode 0, or an AMM sample) and for
- *    strided fibers with Lf = I_1 ... I_{n-1} >= 64 and Lf % 4 == 0, where
- *    I_n % 4 == 0, I_n <= 512, L_n <= 32 and A is 16-byte aligned; other
- *    modes take the BF16 form where it fits, else FP32.
+ *    in FP32. Used for sketches of the input tensor (every mode of T-HOSVD,
+ *    the first of ST-HOSVD) on contiguous fibers (mode 0, or an AMM sample)
+ *    and on strided fibers with Lf = I_1 ... I_{n-1} >= 64 and Lf % 4 == 0,
+ *    where I_n % 4 == 0, I_n <= 512, L_n <= 32 and A is 16-byte aligned;
+ *    ST-HOSVD's later modes (on the truncated tensor, small by then) and other
+ *    shapes take the BF16 form where it fits, else FP32.
  * The tensor-core forms need FP32 data (TUCKER_ERR_UNSUPPORTED for FP64), and
  * run the mode-0 product in split BF16 (see tucker_ttm). */
 typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2, TUCKER_SK_BF16X1 = 3 } tucker_sketch_prec;

@@ -159,9 +159,13 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         if (elem == 8 && d[n] > 512) return TUCKER_ERR_UNSUPPORTED;
         mp.pp = power_plan(mp.mv, mp.L, elem, sms);
         // tensor-core power steps where the tile fits: TF32 on contiguous fibers, split
-        // BF16 (also the TF32 form's choice for strided fibers); the FP32 kernel elsewhere
+        // BF16 (also the TF32 form's choice for strided fibers); the FP32 kernel elsewhere.
+        // Single-pass BF16 sketches the input tensor only (every mode of T-HOSVD, the
+        // first of ST-HOSVD): ST-HOSVD's later modes see the truncated tensor, small by
+        // then, where the split form's accuracy costs little.
         mp.tf32 = o.prec == TUCKER_SK_TF32 && elem == 4 && power_tf32_supported(mp.mv, mp.L);
-        mp.bf16x1 = o.prec == TUCKER_SK_BF16X1 && elem == 4 && power_bf16x1_supported(mp.mv, mp.L);
+        mp.bf16x1 = o.prec == TUCKER_SK_BF16X1 && elem == 4 && (!st || n == 0) &&
+                    power_bf16x1_supported(mp.mv, mp.L);
         mp.tc = o.prec != TUCKER_SK_FP32 && elem == 4 && power_tc_supported(mp.mv, mp.L);
         if (mp.tc || mp.tf32 || mp.bf16x1)
             p.max_partials = std::max(p.max_partials, power_tc_partials_bytes(mp.mv, mp.L, sms));
