@@ -14,7 +14,7 @@ Notation (paper -> here): mu_n -> R_n (target rank), K -> P (oversampling),
 T_n -> T (AMM sample count), G_n (Gaussian) -> Omega, Q_n -> U_n, core -> G.
 Tensors are numpy arrays of shape (I_1, ..., I_N), i_1 fastest (Fortran order).
 
-Readings where the paper is silent or ambiguous (each also listed in the design doc):
+Readings where the paper is silent or ambiguous:
   * L_n = min(R_n + P, I_n) columns in the sketch.
   * T_n = min(c, J_n) when c > 0; T_n = ceil(alpha J_n) when c == 0 and alpha > 0
     (the parameter rule of Section 3.3); no AMM otherwise.
