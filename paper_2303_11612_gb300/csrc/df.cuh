@@ -62,13 +62,20 @@ template <> struct Sc<df> {
     static __device__ __forceinline__ df fma(df a, df b, df c) { return c + a * b; }
     static __device__ __forceinline__ bool gt(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
     static __device__ __forceinline__ bool finite(df a) { return isfinite(a.hi); }
-    // 1/sqrt(a) for a > 0: FP32 estimate, one Newton step in double-float
-    // (y1 = y0 + y0 (1 - a y0^2) / 2 doubles the ~23 correct bits)
+    // 1/sqrt(a) for a > 0: FP32 estimate y0, one Newton step
+    // y1 = y0 + y0 h / 2 with h = 1 - a y0^2 (doubles the ~22 correct bits).
+    // y0^2 = p + pe exactly (FMA), and h is of the order of 2^-22, so forming
+    // h = 1 - a_hi p - a_hi pe - a_lo p with FMAs in FP32 carries it to about
+    // 2^-46 absolute (a_lo pe, below 2^-47, is dropped): a short dependent
+    // chain, since this sits on the Cholesky's serial path.
     static __device__ __forceinline__ df rsqrt(df a) {
         const float y0 = rsqrtf(a.hi);
-        const df y = {y0, 0.f};
-        const df r = df{1.f, 0.f} - a * (y * y);
-        return y + y * (df{0.5f, 0.f} * r);
+        const float p = y0 * y0;
+        const float pe = fmaf(y0, y0, -p);
+        float h = fmaf(-a.hi, p, 1.f);
+        h = fmaf(-a.hi, pe, h);
+        h = fmaf(-a.lo, p, h);
+        return fast_two_sum(y0, y0 * (0.5f * h));
     }
 };
 template <> struct Sc<double> {

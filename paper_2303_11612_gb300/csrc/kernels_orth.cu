@@ -43,6 +43,8 @@ namespace {
 constexpr int kT = kThreads;
 constexpr int kXT = 256;                 // threads of the extraction kernel (any SM can host it)
 constexpr int kGramRows = 64;            // fewest rows per Gram CTA (few partials to reduce)
+constexpr int kBsCols = 4;               // columns per warp in the extraction's back-substitution
+constexpr int kBsRows = 4;               // rows per lane there: L <= 32 kBsRows
 
 __host__ __device__ __forceinline__ int packed_index(int a, int b, int L) {
     return a * L - (a * (a - 1)) / 2 + (b - a);
@@ -56,6 +58,12 @@ template <typename S, typename T> __device__ __forceinline__ S to_s(T x) {
     if constexpr (sizeof(T) == 4) return Sc<S>::from_float((float)x);
     else return Sc<S>::from_double((double)x);
 }
+
+// Broadcast of a small-matrix scalar from lane src of the warp.
+__device__ __forceinline__ df shfl_s(df v, int src) {
+    return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+__device__ __forceinline__ double shfl_s(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 // Load that bypasses L1 (data written by other CTAs of the same launch).
 __device__ __forceinline__ df ld_cg(const df* p) {
@@ -111,20 +119,34 @@ __device__ bool last_cta(unsigned* ticket) {
     return last;
 }
 
+// Entry number e of the trailing triangle, counted from the bottom row up:
+// row i = L - 1 - r holds numbers T(r) .. T(r + 1) - 1, T(r) = r (r + 1) / 2,
+// and number T(r) + c is column j = i + c. Rows k + 1 .. L - 1 are then the
+// first T(L - 1 - k) numbers, for every k.
+__device__ __forceinline__ void trailing_entry(int e, int L, int& i, int& j) {
+    int r = (int)((sqrtf((float)(8 * e + 1)) - 1.f) * 0.5f);
+    if ((r + 1) * (r + 2) / 2 <= e) ++r;
+    if (r * (r + 1) / 2 > e) --r;
+    i = L - 1 - r;
+    j = i + (e - r * (r + 1) / 2);
+}
+
 // Sum the partials in block order into G and factor G = R^T R (all packed;
 // R in W, 1/R_kk in dinv). A pivot below 8u of its diagonal entry restarts once
 // with G + s I, s = 11 (I L + L (L + 1)) u tr(G), u the Gram's unit roundoff.
 // Returns false if that also fails (then R = I).
 //
-// Right-looking, one barrier per column: in the phase of column k every warp
-// updates whole trailing rows from the unscaled row k (W_ij -= W_ki W_kj / d_k),
-// the thread that updates W_{k+1,k+1} takes the next pivot at once, and row
-// k - 1 is scaled by 1/R_{k-1,k-1} alongside.
+// Right-looking, one barrier per column: in the phase of column k every
+// thread updates its entries of the trailing rows from the unscaled row k
+// (W_ij -= W_ki W_kj / d_k; at most a few entries a thread, numbered as in
+// trailing_entry), the thread that updates W_{k+1,k+1} takes the next pivot at
+// once (its threshold formed alongside the update), and row k - 1 is scaled by
+// 1/R_{k-1,k-1} alongside.
 template <typename T, typename S>
 __device__ bool reduce_cholesky(const S* __restrict__ partial, int nparts, int L, int64_t I, S* G, S* W, S* dinv,
                                 unsigned* ticket, int* status) {
     using F = Sc<S>;
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int np = (int)packed_size(L);
     const double u = gram_unit<T>();
     __shared__ int bad;
@@ -139,15 +161,14 @@ __device__ bool reduce_cholesky(const S* __restrict__ partial, int nparts, int L
     __syncthreads();
     const S thr = F::from_double(8.0 * u);
     S shift = F::zero();
-    // pivot k from the updated W_kk: false when numerically singular
-    auto pivot = [&](int k) {
-        const int kk = packed_index(k, k, L);
-        const S d = W[kk];
-        if (!F::gt(d, (G[kk] + shift) * thr) || !F::finite(d)) {
+    // pivot k from the updated W_kk = d against lim = (G_kk + shift) 8u;
+    // sets bad when numerically singular
+    auto pivot = [&](int k, S d, S lim) {
+        if (!F::gt(d, lim) || !F::finite(d)) {
             bad = 1;
         } else {
             const S y = F::rsqrt(d);
-            W[kk] = d * y;
+            W[packed_index(k, k, L)] = d * y;
             dinv[k] = y;
             inv2[k & 1] = y * y;
         }
@@ -158,7 +179,7 @@ __device__ bool reduce_cholesky(const S* __restrict__ partial, int nparts, int L
         for (int k = tid; k < L; k += nt) W[packed_index(k, k, L)] = G[packed_index(k, k, L)] + shift;
         if (tid == 0) bad = 0;
         __syncthreads();
-        if (tid == 0) pivot(0);
+        if (tid == 0) pivot(0, W[0], (G[0] + shift) * thr);
         __syncthreads();
         for (int k = 0; k < L && !bad; ++k) {
             if (k > 0) {                                  // scale row k - 1
@@ -168,13 +189,17 @@ __device__ bool reduce_cholesky(const S* __restrict__ partial, int nparts, int L
             }
             const S y2 = inv2[k & 1];
             const S* rk = W + packed_index(k, k, L);      // rk[j - k] = W_kj
-            for (int i = k + 1 + warp; i < L; i += nw) {
-                const S cki = rk[i - k] * y2;
-                S* ri = W + packed_index(i, i, L);        // ri[j - i] = W_ij
-                for (int j = i + lane; j < L; j += 32) {
-                    ri[j - i] = ri[j - i] - cki * rk[j - k];
-                    if (j == k + 1) pivot(k + 1);         // i == j == k + 1: warp 0, lane 0
-                }
+            const int ne = (L - 1 - k) * (L - k) / 2;     // entries of rows k + 1 .. L - 1
+            for (int e = tid; e < ne; e += nt) {
+                int i, j;
+                trailing_entry(e, L, i, j);
+                const bool piv = j == k + 1;              // then i == k + 1 as well
+                S lim = F::zero();
+                if (piv) lim = (G[packed_index(k + 1, k + 1, L)] + shift) * thr;
+                S* w = W + packed_index(i, j, L);
+                const S v = *w - (rk[i - k] * y2) * rk[j - k];
+                *w = v;
+                if (piv) pivot(k + 1, v, lim);
             }
             __syncthreads();
         }
@@ -206,36 +231,34 @@ __device__ bool reduce_cholesky(const S* __restrict__ partial, int nparts, int L
 }
 
 // Inverse of the packed upper-triangular R (1/R_kk in dinv) into Ri (packed),
-// with RT a scratch packed lower triangle. Row i of R^-1 solves y R = e_i by
-// forward substitution (one thread per row, four partial sums), so the computed
-// inverse has a small residual R^-1 R - I: X R^-1 R stays close to X, which is
-// what Q R = X needs. The substitution walks columns of R, so R is first
-// transposed into RT (row j of RT = column j of R, contiguous).
+// with Acc a packed scratch of the same size. Row i of R^-1 solves x R = e_i,
+// x_ij = (delta_ij - sum_{k<j} x_ik R_kj) / R_jj, so the computed inverse has a
+// small residual R^-1 R - I: X R^-1 R stays close to X, which is what Q R = X
+// needs. The columns are solved in order, right-looking: once column j is
+// known, every pair (row i <= j, column k > j) adds x_ij R_jk to its running
+// sum Acc_ik, so a column costs one dependent step and one barrier for all
+// rows together (each thread recomputes the x_ij its pairs need).
 template <typename S>
-__device__ void upper_inverse(const S* R, const S* dinv, int L, S* RT, S* Ri) {
+__device__ void upper_inverse(const S* R, const S* dinv, int L, S* Acc, S* Ri) {
     using F = Sc<S>;
-    for (int p = threadIdx.x; p < L * L; p += blockDim.x) {
-        const int a = p / L, b = p % L;
-        if (b >= a) RT[b * (b + 1) / 2 + a] = R[packed_index(a, b, L)];
-    }
+    const int np = (int)packed_size(L);
+    for (int p = threadIdx.x; p < np; p += blockDim.x) Acc[p] = F::zero();
     __syncthreads();
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        S* y = Ri + packed_index(i, i, L) - i;            // y[j] = Ri_ij, j >= i
-        for (int j = i; j < L; ++j) {
-            const S* col = RT + j * (j + 1) / 2;          // col[k] = R_kj
-            S a0 = (i == j) ? F::one() : F::zero(), a1 = F::zero(), a2 = F::zero(), a3 = F::zero();
-            int k = i;
-            for (; k + 3 < j; k += 4) {
-                a0 = F::fma(-y[k], col[k], a0);
-                a1 = F::fma(-y[k + 1], col[k + 1], a1);
-                a2 = F::fma(-y[k + 2], col[k + 2], a2);
-                a3 = F::fma(-y[k + 3], col[k + 3], a3);
+    for (int j = 0; j < L; ++j) {
+        const int rows = j + 1, cols = L - 1 - j;
+        const int n = rows * (cols > 0 ? cols : 1);
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int i = e % rows, c = e / rows;
+            const int ij = packed_index(i, j, L);
+            const S x = ((i == j ? F::one() : F::zero()) - Acc[ij]) * dinv[j];
+            if (c == 0) Ri[ij] = x;
+            if (cols > 0) {
+                const int ik = packed_index(i, j + 1 + c, L);
+                Acc[ik] = F::fma(x, R[packed_index(j, j + 1 + c, L)], Acc[ik]);
             }
-            for (; k < j; ++k) a0 = F::fma(-y[k], col[k], a0);
-            y[j] = ((a0 + a1) + (a2 + a3)) * dinv[j];
         }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // ---------------------------------------------------------------- one CholeskyQR pass
@@ -631,23 +654,41 @@ __global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, i
         for (int a = tid; a < L; a += kXT) u[a] *= f;
         __syncthreads();
     }
-    // W(:, r) = R2^-1 U_M(:, r): back-substitution, one thread per column (row l
-    // of R2 is contiguous in the packed layout)
-    for (int r = tid; r < R; r += kXT) {
-        const T* u = UM + (size_t)r * L;
-        S* w = Wout + (size_t)r * L;
-        for (int l = L - 1; l >= 0; --l) {
-            const S* row = Rf + packed_index(l, l, L) - l;      // row[k] = R2_lk
-            S a0 = F::zero(), a1 = F::zero(), a2 = F::zero(), a3 = F::zero();
-            int k = l + 1;
-            for (; k + 3 < L; k += 4) {
-                a0 = F::fma(row[k], w[k], a0);
-                a1 = F::fma(row[k + 1], w[k + 1], a1);
-                a2 = F::fma(row[k + 2], w[k + 2], a2);
-                a3 = F::fma(row[k + 3], w[k + 3], a3);
+    // W(:, r) = R2^-1 U_M(:, r): back-substitution, one warp per group of
+    // kBsCols columns. Lane q keeps u_k - sum_{l' > l} R2_kl' w_l' for the rows
+    // k = q + 32 m (m < kBsRows, so L <= 128); row l is finished by its lane,
+    // broadcast, and subtracted from every row above it, so each row costs one
+    // dependent step, with the group's columns in flight together.
+    for (int c0 = warp * kBsCols; c0 < R; c0 += nwarps * kBsCols) {
+        S acc[kBsCols][kBsRows];
+#pragma unroll
+        for (int c = 0; c < kBsCols; ++c)
+#pragma unroll
+            for (int m = 0; m < kBsRows; ++m) {
+                const int k = lane + 32 * m;
+                acc[c][m] = (c0 + c < R && k < L) ? to_s<S>(UM[(size_t)(c0 + c) * L + k]) : F::zero();
             }
-            for (; k < L; ++k) a0 = F::fma(row[k], w[k], a0);
-            w[l] = (to_s<S>(u[l]) - ((a0 + a1) + (a2 + a3))) * dinv[l];
+        for (int l = L - 1; l >= 0; --l) {
+            const int src = l & 31, ml = l >> 5;
+            const S d = dinv[l];
+            S rkl[kBsRows];                                      // R2_kl for this lane's rows above l
+#pragma unroll
+            for (int m = 0; m < kBsRows; ++m) {
+                const int k = lane + 32 * m;
+                rkl[m] = k < l ? Rf[packed_index(k, l, L)] : F::zero();
+            }
+#pragma unroll
+            for (int c = 0; c < kBsCols; ++c) {
+                S v = acc[c][0];
+#pragma unroll
+                for (int m = 1; m < kBsRows; ++m)
+                    if (ml == m) v = acc[c][m];
+                const S w = shfl_s(v * d, src);
+                if (lane == src && c0 + c < R) Wout[(size_t)(c0 + c) * L + l] = w;
+#pragma unroll
+                for (int m = 0; m < kBsRows; ++m)
+                    if (lane + 32 * m < l) acc[c][m] = F::fma(-rkl[m], w, acc[c][m]);
+            }
         }
     }
 }
@@ -717,8 +758,11 @@ __host__ __device__ inline FLayout flayout(int R, int elem, int64_t I) {
 //      against every valid column. The squared residuals of e_0 .. e_{I-1}
 //      average (I - d) / I for d valid columns, so accepting one above half
 //      that average always succeeds.
+// With staged set, U is copied into shared memory after the layout's other
+// regions (the host checks that it fits), worked on there and copied back at
+// the end, which keeps the loops over U off the global-memory latency.
 template <typename T>
-__global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I, int R) {
+__global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t I, int R, int staged) {
     using S = typename SmallScalar<T>::type;
     using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -736,6 +780,9 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I
     T* coef = reinterpret_cast<T*>(smem_raw + lay.w);     // [R][R] projection coefficients (W and RT)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kT / 32;
     const int np = (int)packed_size(R);
+    T* U = staged ? reinterpret_cast<T*>(smem_raw + lay.total) : Ug;
+    if (staged)
+        for (int64_t e = tid; e < I * R; e += kT) U[e] = Ug[e];
     __shared__ int offdiag, ndrop;
     __shared__ double red[kT / 32];
     __shared__ double bcast;
@@ -1003,6 +1050,10 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ U, int64_t I
             __syncthreads();
         }
     }
+    if (staged) {
+        __syncthreads();
+        for (int64_t e = tid; e < I * R; e += kT) Ug[e] = U[e];
+    }
 }
 
 }  // namespace
@@ -1037,9 +1088,14 @@ static size_t extract_smem(const OrthPlan& p, int R, int elem) {
     return std::max(xlayout(p.L, R, elem).total, (size_t)elem * (size_t)gram_rows(p) * p.L);
 }
 static size_t finish_smem(int R, int elem, int64_t I) { return flayout(R, elem, I).total; }
+// The final pass's shared memory with U staged in it, or 0 when that does not fit.
+static size_t finish_staged_smem(int R, int elem, int64_t I) {
+    const size_t b = flayout(R, elem, I).total + up16((size_t)elem * (size_t)I * (size_t)R);
+    return b <= kSmemCap ? b : 0;
+}
 
 bool orth_supported(const OrthPlan& p, int R, int elem) {
-    return gram_chol_smem(p, elem) <= kSmemCap && extract_smem(p, R, elem) <= kSmemCap &&
+    return p.L <= 32 * kBsRows && gram_chol_smem(p, elem) <= kSmemCap && extract_smem(p, R, elem) <= kSmemCap &&
            8 * packed_size(p.L) <= kSmemCap && finish_smem(R, elem, p.I) <= kSmemCap;
 }
 
@@ -1116,9 +1172,10 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
     if (ublocks > 4 * 1024) ublocks = 4 * 1024;
     form_u_kernel<T><<<(unsigned)ublocks, kT, 0, s>>>(Q1, p.I, L, R, (const S*)sc.W, U);
     note_launch();
-    const size_t fsm = finish_smem(R, sizeof(T), p.I);
+    const size_t staged = finish_staged_smem(R, sizeof(T), p.I);
+    const size_t fsm = staged ? staged : finish_smem(R, sizeof(T), p.I);
     cudaFuncSetAttribute(finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-    finish_kernel<T><<<1, kT, fsm, s>>>(U, p.I, R);
+    finish_kernel<T><<<1, kT, fsm, s>>>(U, p.I, R, staged ? 1 : 0);
     note_launch();
     return cudaGetLastError();
 }
