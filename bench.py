@@ -33,6 +33,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# A batch runs its decompositions on 32 streams of one CUDA graph. CUDA maps
+# streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware work queues (8 unless set),
+# and work of different streams sharing a queue is dispatched in order, so
+# with 8 a decomposition waiting on its own chain holds up others queued behind
+# it. 32 queues give every stream its own; the variable is read when the CUDA
+# context is created, so it is set before anything touches the GPU.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 DIMS = (400, 400, 400)
 RANKS = (20, 20, 20)
 P = 10
@@ -548,7 +556,8 @@ def main():
                                     "fp32": "(FP32 FFMA; exact FP32 mode products)"}[head["prec"]],
                        "execution": f"tucker_batch_run per step: one CUDA graph (captured by the library on its "
                                     f"first run, replayed after) of {len(batch)} decompositions ({args.copies} of "
-                                    f"each variant, inputs shared read-only) on {len(batch)} streams"},
+                                    f"each variant, inputs shared read-only) on {len(batch)} streams",
+                       "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")},
             "e2e": e2e, "gpu_launches": head["gpu_launches"], "roofline": roofline, "kernels": kernels,
             "sketch_hbm_gbs": achieved_gbs,
             "forms": {p: {"value": f["value"], "ms_per_step": f["ms"] / args.steps, "rel_error": f["rel_error"]}
