@@ -417,7 +417,9 @@ class Server:
     ``submit`` takes the tensor (device or host, pinned for overlap) and returns
     a ticket; the output tensors are created here on ``out_device`` unless given.
     The binding keeps every tensor of a request alive until ``wait`` has seen it
-    complete."""
+    complete. Requests overlap only as far as CUDA's hardware work queues allow:
+    set ``CUDA_DEVICE_MAX_CONNECTIONS`` (8 by default) to at least
+    ``max_inflight`` before the process first uses the GPU."""
 
     def __init__(self, budget_bytes: int, max_inflight: int = 8, form="paper", prec="fp32"):
         o = ServerOpts(C.sizeof(ServerOpts), int(max_inflight), int(budget_bytes), FORM[form], PREC[prec])
@@ -481,7 +483,11 @@ class Batch:
     "ST"), A (device tensor), dims, ranks and optionally P, q, c, prob, seed.
     Outputs and the workspace are allocated here, once; ``run`` launches the
     whole batch (captured on the first run, replayed afterwards) and returns the
-    list of (U, G). Inputs may be rewritten in place between runs."""
+    list of (U, G). Inputs may be rewritten in place between runs. Each request
+    runs on its own stream of the graph; with CUDA's default of 8 hardware work
+    queues (``CUDA_DEVICE_MAX_CONNECTIONS``, read when the process first uses
+    the GPU) streams sharing a queue wait on one another, so set it to 32 for
+    batches of more than 8 requests."""
 
     def __init__(self, requests, form="paper", prec="fp32"):
         self._keep = []

@@ -150,7 +150,13 @@ tucker_status tucker_batch_run(int n, const tucker_request* reqs, const tucker_o
         }
         std::vector<cudaEvent_t> ev(n + 1, nullptr);
         for (auto& x : ev)
-            if (cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) return TUCKER_ERR_CUDA;
+            if (cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) {
+                x = nullptr;
+                for (auto& y : ev)
+                    if (y) cudaEventDestroy(y);
+                cudaGetLastError();
+                return TUCKER_ERR_CUDA;
+            }
         cudaGraph_t graph = nullptr;
         const int64_t k0 = tucker_launch_count();
         e = cudaStreamBeginCapture(g_origin, cudaStreamCaptureModeThreadLocal);
