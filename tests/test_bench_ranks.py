@@ -51,3 +51,18 @@ def test_two_ranks_gloo(tmp_path):
 def test_single_rank_helpers():
     assert bench.rank_max(None, torch, 3.5, "cpu") == 3.5
     assert bench.whole_job_rate(10, 1, 2.0) == 5.0
+
+
+def test_bench_sets_hardware_queues_before_cuda():
+    """Importing bench.py sets CUDA_DEVICE_MAX_CONNECTIONS (32 queues for the
+    32-stream batch graph) without importing torch, so the value is in place
+    before any CUDA context exists; a value set by the caller is kept."""
+    import subprocess
+    code = ("import os, sys; sys.path.insert(0, sys.argv[1]); import bench; "
+            "print(os.environ['CUDA_DEVICE_MAX_CONNECTIONS'], 'torch' in sys.modules)")
+    env = {k: v for k, v in os.environ.items() if k != "CUDA_DEVICE_MAX_CONNECTIONS"}
+    out = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True, text=True, check=True)
+    assert out.stdout.split() == ["32", "False"]
+    env["CUDA_DEVICE_MAX_CONNECTIONS"] = "16"
+    out = subprocess.run([sys.executable, "-c", code, ROOT], env=env, capture_output=True, text=True, check=True)
+    assert out.stdout.split() == ["16", "False"]
