@@ -82,3 +82,66 @@ def test_drivers_reject_bad_arguments_without_touching_memory(lib):
     st = lib.tucker_rsthosvd(C.c_void_p(1), 0, B._i64((10, 10, 10)), 3, B._i32((2, 2, 2)), 5, 1, 0, 1,
                              C.c_uint64(0), U, C.c_void_p(1), C.byref(o))
     assert st == 1
+
+
+def _request(dims, ranks, which=1, N=None, P=10, q=1, c=0):
+    from paper_2303_11612_gb300 import _binding as B
+    r = B.Request()
+    r.struct_size = C.sizeof(B.Request)
+    r.which, r.dt, r.A, r.G = which, 0, 1, 1
+    d, rk = B._i64(dims or (1,)), B._i32(ranks or (1,))
+    U = (C.c_void_p * max(1, len(dims)))(*([1] * max(1, len(dims))))
+    r.dims = C.cast(d, C.POINTER(C.c_int64))
+    r.ranks = C.cast(rk, C.POINTER(C.c_int32))
+    r.U = C.cast(U, C.POINTER(C.c_void_p))
+    r.N = len(dims) if N is None else N
+    r.P, r.q, r.c, r.prob, r.seed = P, q, c, 1, 0
+    return r, (d, rk, U)
+
+
+def test_batch_sizes_and_argument_checks(lib):
+    """tucker_batch_workspace_size sums each request's workspace rounded up to
+    256 bytes and rejects malformed requests; tucker_batch_run refuses missing
+    options or workspace before any CUDA call."""
+    from paper_2303_11612_gb300 import _binding as B
+    a, ka = _request((400, 400, 400), (20, 20, 20))
+    b, kb = _request((64, 48, 40, 36), (8, 6, 5, 4), which=0, c=300)
+    arr = (B.Request * 2)(a, b)
+    n = C.c_size_t(0)
+    assert lib.tucker_batch_workspace_size(2, arr, None, C.byref(n)) == 0
+    wa = _ws(lib, (400, 400, 400), (20, 20, 20))[1]
+    wb = _ws(lib, (64, 48, 40, 36), (8, 6, 5, 4), which=0, c=300)[1]
+    up = lambda x: (x + 255) // 256 * 256
+    assert n.value == up(wa) + up(wb)
+    assert lib.tucker_batch_workspace_size(0, arr, None, C.byref(n)) == 1
+    assert lib.tucker_batch_workspace_size(2, None, None, C.byref(n)) == 1
+    assert lib.tucker_batch_workspace_size(2, arr, None, None) == 1
+    for bad in (dict(which=2), dict(N=0), dict(q=0), dict(P=-1)):
+        r, keep = _request((40, 36, 32), (4, 4, 4), **bad)
+        one = (B.Request * 1)(r)
+        assert lib.tucker_batch_workspace_size(1, one, None, C.byref(n)) == 1, bad
+    r, keep = _request((40, 36, 32), (41, 4, 4))                     # R > I
+    assert lib.tucker_batch_workspace_size(1, (B.Request * 1)(r), None, C.byref(n)) == 1
+    assert lib.tucker_batch_run(2, arr, None) == 1                     # options (and workspace) required
+    o = B.make_opts()
+    assert lib.tucker_batch_run(2, arr, C.byref(o)) == 1               # no workspace
+    o.prec = 9
+    assert lib.tucker_batch_workspace_size(2, arr, C.byref(o), C.byref(n)) == 1
+
+
+def test_options_and_server_argument_checks(lib):
+    """Out-of-range options and server settings are rejected on the host."""
+    from paper_2303_11612_gb300 import _binding as B
+    for field, value in (("prec", 4), ("prec", -1), ("form", 2), ("alpha", 1.5), ("alpha", -0.1)):
+        o = B.make_opts()
+        setattr(o, field, value)
+        st = lib.tucker_workspace_size(1, 0, B._i64((40, 36, 32)), 3, B._i32((4, 4, 4)), 5, 1, 0, C.byref(o),
+                                       C.byref(C.c_size_t()))
+        assert st == 1, (field, value)
+    h = C.c_void_p()
+    assert lib.tucker_server_create(None, C.byref(h)) == 1
+    for field, value in (("max_inflight", 0), ("max_inflight", 257), ("budget_bytes", 0), ("form", 3),
+                         ("prec", 4)):
+        so = B.ServerOpts(C.sizeof(B.ServerOpts), 8, 1 << 30, 0, 0)
+        setattr(so, field, value)
+        assert lib.tucker_server_create(C.byref(so), C.byref(h)) == 1, (field, value)
