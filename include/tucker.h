@@ -282,7 +282,10 @@ tucker_status tucker_power_step_noalloc(const void* A, tucker_dtype dt, const in
  * decomposition on its own stream, so the work of admitted requests overlaps
  * on the device, and a request that arrives while others run is admitted as
  * soon as a stream and memory free up. Results do not depend on what else runs:
- * every kernel reduces in a fixed order. */
+ * every kernel reduces in a fixed order. How far the streams overlap depends on
+ * CUDA's hardware work queues: CUDA_DEVICE_MAX_CONNECTIONS (8 when unset, read
+ * when the process creates its CUDA context) should be at least max_inflight,
+ * or requests sharing a queue wait on one another. */
 typedef struct tucker_server tucker_server;
 
 typedef struct {
@@ -346,7 +349,10 @@ tucker_status tucker_server_destroy(tucker_server* srv);
  * graph; a later call with the same signature replays that graph with one
  * launch (the 16 most recently used graphs are kept). The graph runs after the
  * work already on opts->stream and before what is enqueued there next. Each
- * request's results are bitwise those of the same request run alone. */
+ * request's results are bitwise those of the same request run alone. The
+ * requests overlap as far as CUDA's hardware work queues allow: with more than
+ * 8 requests, set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) before the process
+ * creates its CUDA context. */
 
 /* Device workspace bytes (256-byte aligned per request) a batch needs; opts
  * may be NULL (paper form, FP32). */
