@@ -1,7 +1,6 @@
 // Power step of Strategy A on the 5th-generation tensor cores with single-pass
 // BF16 operands (tcgen05 kind::f16, FP32 accumulation in tensor memory):
-// X_out = A_(n) (A_(n)^T X_in) for contiguous mode-n fibers (mode 1) and for
-// strided fibers of stride Lf >= 64 (described below). A, X_in
+// X_out = A_(n) (A_(n)^T X_in) for contiguous mode-n fibers (mode 1). A, X_in
 // and W = A^T X are each rounded to bf16 (8 significant bits, to nearest) once;
 // the sums are FP32. This is the form whose rounding the power steps win back:
 // a relative error of order 2^-8 in the sketch moves the captured subspace by
