@@ -145,3 +145,22 @@ def test_options_and_server_argument_checks(lib):
         so = B.ServerOpts(C.sizeof(B.ServerOpts), 8, 1 << 30, 0, 0)
         setattr(so, field, value)
         assert lib.tucker_server_create(C.byref(so), C.byref(h)) == 1, (field, value)
+
+
+def test_measurement_entry_points_without_gpu(lib):
+    """Launch counter, per-class profile counters (zero before any launch, one
+    slot per kernel class the binding names) and the last-CUDA-error string
+    answer without a GPU; an unknown class is an argument error."""
+    from paper_2303_11612_gb300 import _binding as B
+    assert lib.tucker_launch_count() >= 0
+    assert lib.tucker_profile_enable(1) == 0
+    n, ms, by, fl = C.c_int64(-1), C.c_double(-1), C.c_double(-1), C.c_double(-1)
+    classes = sorted(B.KERNEL_CLASSES.values())
+    assert classes == list(range(len(classes)))
+    for k in classes:
+        assert lib.tucker_profile_read(k, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)) == 0
+        assert (n.value, ms.value, by.value, fl.value) == (0, 0.0, 0.0, 0.0)
+    assert lib.tucker_profile_read(len(classes), None, None, None, None) == 1
+    assert lib.tucker_profile_read(-1, None, None, None, None) == 1
+    assert lib.tucker_profile_enable(0) == 0
+    assert lib.tucker_last_cuda_error() is not None
