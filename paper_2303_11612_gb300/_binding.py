@@ -186,12 +186,54 @@ def _ptr(t: torch.Tensor) -> int:
     return t.data_ptr()
 
 
+def _problem(which: str, A: torch.Tensor, dims, ranks):
+    """Checks one decomposition's arguments before they reach the C ABI, which
+    reads N extents and N ranks and the tensor as dense memory, i_1 fastest.
+    Returns (dims, ranks) as int lists."""
+    if which not in ("T", "ST"):
+        raise ValueError(f"which must be 'T' or 'ST', not {which!r}")
+    dims = [int(d) for d in dims]
+    ranks = [int(r) for r in ranks]
+    if not dims or len(ranks) != len(dims):
+        raise ValueError("dims and ranks must be non-empty and of equal length")
+    _dt(A)
+    if not A.is_contiguous():
+        raise ValueError("A must be contiguous (dense, i_1 fastest)")
+    if A.numel() != int(torch.tensor(dims).prod()):
+        raise ValueError("A.numel() must equal prod(dims)")
+    return dims, ranks
+
+
+def _outputs(out, A: torch.Tensor, dims, ranks, device):
+    """Caller-supplied (U list, G) checked against the ABI's layouts (U_n
+    column-major I_n x R_n, G dense with prod(ranks) entries, A's dtype), or
+    new tensors on device."""
+    if out is None:
+        U = [factor_tensor(I, R, A.dtype, device) for I, R in zip(dims, ranks)]
+        G = torch.empty(int(torch.tensor(ranks).prod()), dtype=A.dtype, device=device)
+        return U, G
+    U, G = out
+    if len(U) != len(dims):
+        raise ValueError("out must hold one factor per mode")
+    for u, I, R in zip(U, dims, ranks):
+        if tuple(u.shape) != (I, R) or u.dtype != A.dtype or (R > 1 and u.stride(0) != 1) or \
+                (I > 1 and R > 1 and u.stride(1) != I):
+            raise ValueError("each U_n must be a column-major I_n x R_n tensor of A's dtype")
+    if G.numel() != int(torch.tensor(ranks).prod()) or G.dtype != A.dtype or not G.is_contiguous():
+        raise ValueError("G must be a contiguous tensor of prod(ranks) entries of A's dtype")
+    return list(U), G
+
+
 def factor_tensor(I: int, R: int, dtype, device) -> torch.Tensor:
     """An (I, R) tensor with column-major strides (the ABI's matrix layout)."""
     return torch.empty((R, I), dtype=dtype, device=device).t()
 
 
 def workspace_size(which: str, dims, ranks, P=10, q=1, c=0, dtype=torch.float32, **kw) -> int:
+    if which not in ("T", "ST"):
+        raise ValueError(f"which must be 'T' or 'ST', not {which!r}")
+    if len(ranks) != len(dims):
+        raise ValueError("dims and ranks must be of equal length")
     n = C.c_size_t(0)
     o = make_opts(**kw)
     st = lib().tucker_workspace_size(0 if which == "T" else 1, 0 if dtype == torch.float32 else 1,
@@ -206,17 +248,10 @@ def decompose(which: str, A: torch.Tensor, dims: Sequence[int], ranks: Sequence[
               want_rel_error=False, want_samples=False, out=None, flags=0):
     """Randomized T-HOSVD (which='T', Algorithms 1/4) or ST-HOSVD (which='ST',
     Algorithms 2/5). Returns (U list, G flat[, rel_error][, sample indices])."""
-    dims = [int(d) for d in dims]
-    ranks = [int(r) for r in ranks]
+    dims, ranks = _problem(which, A, dims, ranks)
     N = len(dims)
-    if A.numel() != int(torch.tensor(dims).prod()):
-        raise ValueError("A.numel() must equal prod(dims)")
     dev = A.device
-    if out is None:
-        U = [factor_tensor(I, R, A.dtype, dev) for I, R in zip(dims, ranks)]
-        G = torch.empty(int(torch.tensor(ranks).prod()), dtype=A.dtype, device=dev)
-    else:
-        U, G = out
+    U, G = _outputs(out, A, dims, ranks, dev)
     re = C.c_double(float("nan")) if want_rel_error else None
     samples = None
     if want_samples:
@@ -430,17 +465,10 @@ class Server:
 
     def submit(self, which: str, A: torch.Tensor, dims, ranks, P=5, q=1, c=0, prob="uniform", seed=0,
                out=None, out_device=None):
-        dims = [int(d) for d in dims]
-        ranks = [int(r) for r in ranks]
+        dims, ranks = _problem(which, A, dims, ranks)
         N = len(dims)
-        if A.numel() != int(torch.tensor(dims).prod()):
-            raise ValueError("A.numel() must equal prod(dims)")
         dev = A.device if out_device is None else torch.device(out_device)
-        if out is None:
-            U = [factor_tensor(I, R, A.dtype, dev) for I, R in zip(dims, ranks)]
-            G = torch.empty(int(torch.tensor(ranks).prod()), dtype=A.dtype, device=dev)
-        else:
-            U, G = out
+        U, G = _outputs(out, A, dims, ranks, dev)
         d64, r32 = _i64(dims), _i32(ranks)
         Up = (C.c_void_p * N)(*[u.data_ptr() for u in U])
         req = Request(C.sizeof(Request), 0 if which == "T" else 1, _dt(A), A.data_ptr(), d64, N, r32, int(P), int(q),
@@ -497,12 +525,8 @@ class Batch:
         arr = (Request * len(requests))()
         for k, r in enumerate(requests):
             A = r["A"]
-            dims = [int(d) for d in r["dims"]]
-            ranks = [int(x) for x in r["ranks"]]
-            if A.numel() != int(torch.tensor(dims).prod()):
-                raise ValueError("A.numel() must equal prod(dims)")
-            U = [factor_tensor(I, R, A.dtype, A.device) for I, R in zip(dims, ranks)]
-            G = torch.empty(int(torch.tensor(ranks).prod()), dtype=A.dtype, device=A.device)
+            dims, ranks = _problem(r["which"], A, r["dims"], r["ranks"])
+            U, G = _outputs(None, A, dims, ranks, A.device)
             d64, r32 = _i64(dims), _i32(ranks)
             Up = (C.c_void_p * len(dims))(*[u.data_ptr() for u in U])
             arr[k] = Request(C.sizeof(Request), 0 if r["which"] == "T" else 1, _dt(A), A.data_ptr(), d64, len(dims),
