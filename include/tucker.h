@@ -217,7 +217,9 @@ tucker_status tucker_sample_fibers(const uint64_t* W, int64_t J, int64_t T, uint
                                    const tucker_opts* opts);
 
 /* C' = A_(n) S (Algorithms 4/5): column t of C' (I_n x T, column-major, dt) is
- * scale[t] times fiber idx[t]. */
+ * scale[t] times fiber idx[t]. idx and scale are device arrays of T entries;
+ * every idx[t] must lie in [0, J_n) (tucker_sample_fibers' indices always do):
+ * the kernel reads fiber idx[t] without checking it. */
 tucker_status tucker_gather_fibers(const void* A, tucker_dtype dt, const int64_t* dims, int N,
                                    int mode, const int64_t* idx, const double* scale, int64_t T,
                                    void* Cp, const tucker_opts* opts);

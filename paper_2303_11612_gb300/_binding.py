@@ -204,6 +204,28 @@ def _problem(which: str, A: torch.Tensor, dims, ranks):
     return dims, ranks
 
 
+def _view(A: torch.Tensor, dims, mode: int):
+    """Checks a mode view (dense tensor, N extents, 0 <= mode < N) before the C
+    ABI reads prod(dims) entries; returns dims as ints."""
+    dims = [int(d) for d in dims]
+    _dt(A)
+    if not dims or not 0 <= int(mode) < len(dims):
+        raise ValueError("mode must index one of the N extents")
+    if not A.is_contiguous() or A.numel() != int(torch.tensor(dims).prod()):
+        raise ValueError("A must be a dense tensor (i_1 fastest) of prod(dims) entries")
+    return dims
+
+
+def _colmajor_rows(X: torch.Tensor, rows: int, dtype, name: str) -> torch.Tensor:
+    """X as a column-major 2-D matrix with `rows` rows and the given dtype (a
+    copy when its strides are not column-major)."""
+    if X.dim() != 2 or X.shape[0] != rows or X.dtype != dtype:
+        raise ValueError(f"{name} must be a {rows} x k matrix of dtype {dtype}")
+    if X.shape[1] > 1 and X.stride(0) != 1 or X.shape[1] > 1 and rows > 1 and X.stride(1) != rows:
+        X = X.t().contiguous().t()
+    return X
+
+
 def _outputs(out, A: torch.Tensor, dims, ranks, device):
     """Caller-supplied (U list, G) checked against the ABI's layouts (U_n
     column-major I_n x R_n, G dense with prod(ranks) entries, A's dtype), or
@@ -305,7 +327,9 @@ def gaussian(rows, cols, seed, stream_id, dtype=torch.float32, device="cuda", st
 def power_step(A, dims, mode, X, stream=None, prec="fp32"):
     """X_out = A_(n) (A_(n)^T X) (one power step of Strategy A); prec "tf32" /
     "bf16" run it on the tensor cores (see tucker_power_step)."""
+    dims = _view(A, dims, mode)
     I = dims[mode]
+    X = _colmajor_rows(X, I, A.dtype, "X")
     L = X.shape[1]
     out = factor_tensor(I, L, A.dtype, A.device)
     o = make_opts(stream=stream, prec=prec)
@@ -315,6 +339,7 @@ def power_step(A, dims, mode, X, stream=None, prec="fp32"):
 
 
 def range_sketch(A, dims, mode, L, seed, stream=None):
+    dims = _view(A, dims, mode)
     out = factor_tensor(dims[mode], L, A.dtype, A.device)
     o = make_opts(stream=stream)
     _check("tucker_range_sketch", lib().tucker_range_sketch(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode, L,
@@ -323,6 +348,7 @@ def range_sketch(A, dims, mode, L, seed, stream=None):
 
 
 def fiber_norms(A, dims, mode, stream=None):
+    dims = _view(A, dims, mode)
     J = 1
     for m, d in enumerate(dims):
         if m != mode:
@@ -335,6 +361,8 @@ def fiber_norms(A, dims, mode, stream=None):
 
 
 def quantize_weights(w, prob="nearly_optimal", stream=None):
+    if w.dtype != torch.float64 or not w.is_contiguous():
+        raise ValueError("w must be a contiguous float64 vector")
     W = torch.empty(w.numel(), dtype=torch.int64, device=w.device)   # uint64 bits
     o = make_opts(stream=stream)
     _check("tucker_quantize_weights", lib().tucker_quantize_weights(w.data_ptr(), w.numel(), PROB[prob],
@@ -343,6 +371,8 @@ def quantize_weights(w, prob="nearly_optimal", stream=None):
 
 
 def sample_fibers(W, T, seed, mode, stream=None):
+    if W.dtype != torch.int64 or not W.is_contiguous():
+        raise ValueError("W must be a contiguous int64 vector (the uint64 weights' bits)")
     idx = torch.empty(max(T, 1), dtype=torch.int64, device=W.device)
     scale = torch.empty(max(T, 1), dtype=torch.float64, device=W.device)
     o = make_opts(stream=stream)
@@ -352,6 +382,12 @@ def sample_fibers(W, T, seed, mode, stream=None):
 
 
 def gather_fibers(A, dims, mode, idx, scale, stream=None):
+    """C' = A_(n) S: column t is scale[t] times fiber idx[t]; every idx[t] must
+    be below J_n (tucker_sample_fibers' indices always are)."""
+    dims = _view(A, dims, mode)
+    if idx.dtype != torch.int64 or scale.dtype != torch.float64 or idx.numel() != scale.numel() or \
+            not idx.is_contiguous() or not scale.is_contiguous():
+        raise ValueError("idx (int64) and scale (float64) must be contiguous vectors of equal length")
     T = idx.numel()
     out = factor_tensor(dims[mode], max(T, 1), A.dtype, A.device)
     o = make_opts(stream=stream)
@@ -376,6 +412,9 @@ def ttm(A, dims, mode, M, transpose=False, stream=None, prec="fp32"):
     """A x_n M (transpose=False, M is K x I_n) or A x_n M^T (transpose=True, M is I_n x K);
     M must have column-major strides. prec "bf16"/"tf32": split-bf16 tensor cores
     (contiguous fibers only)."""
+    dims = _view(A, dims, mode)
+    if M.dim() != 2 or M.dtype != A.dtype or M.shape[0 if transpose else 1] != dims[mode]:
+        raise ValueError("M must be I_n x K (transpose) or K x I_n, of A's dtype")
     K = M.shape[1] if transpose else M.shape[0]
     if M.stride(0) != 1:
         M = M.t().contiguous().t()
@@ -392,6 +431,8 @@ def ttm(A, dims, mode, M, transpose=False, stream=None, prec="fp32"):
 
 
 def relative_error(A, dims, ranks, U, G, stream=None):
+    dims, ranks = _problem("T", A, dims, ranks)
+    U, G = _outputs((U, G), A, dims, ranks, A.device)
     re = C.c_double(0.0)
     o = make_opts(stream=stream)
     Up = (C.c_void_p * len(U))(*[u.data_ptr() for u in U])
@@ -434,7 +475,9 @@ def profile_read(kernel: str):
 def power_step_noalloc(A, dims, mode, X, stream=None):
     """tucker_power_step_noalloc: the power step with the library's fixed scratch
     block instead of an allocation (see include/tucker.h)."""
+    dims = _view(A, dims, mode)
     I = dims[mode]
+    X = _colmajor_rows(X, I, A.dtype, "X")
     L = X.shape[1]
     out = factor_tensor(I, L, A.dtype, A.device)
     o = make_opts(stream=stream)

@@ -51,3 +51,40 @@ def test_public_calls_refuse_bad_arguments_before_the_library():
         B.workspace_size("Q", (4, 5, 6), (2, 2, 2))
     with pytest.raises(ValueError):
         B.Batch([dict(which="ST", A=A, dims=(4, 5, 6), ranks=(2, 2))])
+
+
+def test_step_wrappers_refuse_mis_shaped_operands():
+    """Every step wrapper checks the shapes the C ABI will read (an X with fewer
+    than I_n rows, an M of the wrong extent, index/scale vectors of other
+    types) before calling it."""
+    dims = (4, 5, 6)
+    A = torch.zeros(120)
+    with pytest.raises(ValueError):
+        B.power_step(A, dims, 3, torch.zeros(4, 2))                 # mode out of range
+    with pytest.raises(ValueError):
+        B.power_step(A, dims, 1, torch.zeros(4, 2).t().contiguous().t())   # 4 rows, I_n = 5
+    with pytest.raises(ValueError):
+        B.power_step(A, dims, 0, torch.zeros(4, 2, dtype=torch.float64))   # dtype differs from A's
+    with pytest.raises(ValueError):
+        B.power_step_noalloc(A[:119], dims, 0, torch.zeros(4, 2))   # numel mismatch
+    with pytest.raises(ValueError):
+        B.ttm(A, dims, 1, torch.zeros(3, 4), transpose=False)       # K x I_n needs I_n = 5 columns
+    with pytest.raises(ValueError):
+        B.ttm(A, dims, 1, torch.zeros(4, 3), transpose=True)        # I_n x K needs I_n = 5 rows
+    with pytest.raises(ValueError):
+        B.gather_fibers(A, dims, 0, torch.zeros(3), torch.zeros(3, dtype=torch.float64))   # float indices
+    with pytest.raises(ValueError):
+        B.gather_fibers(A, dims, 0, torch.zeros(3, dtype=torch.int64), torch.zeros(2, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        B.fiber_norms(A, dims, -1)
+    with pytest.raises(ValueError):
+        B.range_sketch(A.view(6, 5, 4).transpose(0, 2), dims, 0, 3, seed=0)   # not dense
+    with pytest.raises(ValueError):
+        B.quantize_weights(torch.zeros(10, dtype=torch.float32))
+    with pytest.raises(ValueError):
+        B.sample_fibers(torch.zeros(10, dtype=torch.float64), 4, seed=0, mode=0)
+    U = [B.factor_tensor(I, 2, torch.float32, "cpu") for I in dims]
+    with pytest.raises(ValueError):
+        B.relative_error(A, dims, (2, 2, 2), U[:2], torch.zeros(8))
+    with pytest.raises(ValueError):
+        B.relative_error(A, dims, (2, 2, 2), U, torch.zeros(7))
