@@ -164,3 +164,71 @@ def test_measurement_entry_points_without_gpu(lib):
     assert lib.tucker_profile_read(-1, None, None, None, None) == 1
     assert lib.tucker_profile_enable(0) == 0
     assert lib.tucker_last_cuda_error() is not None
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "tucker.h"
+
+int main(void) {
+    int64_t dims[3] = {400, 400, 400};
+    int32_t ranks[3] = {20, 20, 20}, bad[3] = {401, 20, 20};
+    size_t bytes = 0;
+    if (tucker_workspace_size(1, TUCKER_F32, dims, 3, ranks, 10, 1, 0, NULL, &bytes) != TUCKER_OK || bytes == 0)
+        return 1;
+    if (tucker_workspace_size(1, TUCKER_F32, dims, 3, bad, 10, 1, 0, NULL, &bytes) != TUCKER_ERR_INVALID_ARG)
+        return 2;
+    void* U[3] = {NULL, NULL, NULL};
+    if (tucker_rsthosvd(NULL, TUCKER_F32, dims, 3, ranks, 10, 1, 0, TUCKER_PROB_UNIFORM, 0, U, NULL, NULL) !=
+        TUCKER_ERR_INVALID_ARG)
+        return 3;
+    tucker_request req;
+    memset(&req, 0, sizeof(req));
+    req.struct_size = sizeof(req);
+    req.which = 1;
+    req.dt = TUCKER_F32;
+    req.A = dims;                       /* never read: sizing only */
+    req.dims = dims;
+    req.N = 3;
+    req.ranks = ranks;
+    req.P = 10;
+    req.q = 1;
+    req.prob = TUCKER_PROB_UNIFORM;
+    req.U = U;
+    req.G = dims;
+    size_t batch = 0;
+    if (tucker_batch_workspace_size(1, &req, NULL, &batch) != TUCKER_OK || batch < bytes) return 4;
+    tucker_server_opts so;
+    memset(&so, 0, sizeof(so));
+    so.struct_size = sizeof(so);
+    tucker_server* srv = NULL;
+    if (tucker_server_create(&so, &srv) != TUCKER_ERR_INVALID_ARG || srv) return 5;   /* max_inflight 0 */
+    printf("%s %zu %zu %lld\n", tucker_status_string(TUCKER_OK), bytes, batch, (long long)tucker_launch_count());
+    return 0;
+}
+"""
+
+
+def test_plain_c_caller(tmp_path):
+    """include/tucker.h is plain C (C99, -pedantic, no warnings) and a C program
+    links against the library and gets the documented answers from the host-side
+    entry points."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_2303_11612_gb300 import _binding as B
+    B.lib()
+    libdir = os.path.join(ROOT, "paper_2303_11612_gb300", "_lib")
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    cc = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                         str(src), "-L", libdir, "-ltucker", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                        capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
+    assert run.stdout.split()[0] == "ok"
