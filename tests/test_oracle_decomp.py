@@ -68,6 +68,28 @@ def test_tendiag_closed_form():
         assert abs(ot.relative_error(A, Us, G) - want) < 1e-8
 
 
+def test_tendiag_with_the_papers_spectrum_shape():
+    """Section 6.3's v, scaled from 600 to 48 entries: a flat block of ones
+    (50 there, 8 here) followed by (i - 49)^-2 (here (i - 7)^-2). For mu at or
+    beyond the flat block the leading directions are unique, and deterministic
+    T- and ST-HOSVD reach the closed-form error of the tail of v, which no
+    multilinear rank-(mu, mu, mu) approximation beats; the randomized
+    algorithms with two power steps stay within 1.5 times it (the gap at
+    mu = 20 is only v_20 / v_21 = 1.16)."""
+    k, n = 8, 48
+    i = np.arange(1, n + 1)
+    v = np.where(i <= k, 1.0, np.maximum(i - (k - 1), 1).astype(float) ** -2.0)
+    A = synth.tendiag(v, (n, n, n), seed=5)
+    for mu in (k, 12, 20):
+        want = np.sqrt(np.sum(v[mu:] ** 2) / np.sum(v ** 2))
+        for alg in (ot.thosvd, ot.sthosvd):
+            Us, G = alg(A, (mu,) * 3)
+            assert abs(ot.relative_error(A, Us, G) - want) < 1e-12, (alg.__name__, mu)
+        for alg in (ot.rthosvd, ot.rsthosvd):
+            re = ot.relative_error(A, *alg(A, (mu,) * 3, P=5, q=2))
+            assert want - 1e-12 <= re <= 1.5 * want, (alg.__name__, mu, re, want)
+
+
 def test_matrix_case_is_eckart_young():
     """N = 2: T-HOSVD is the truncated SVD; compare with eigenvalues of A A^T from
     a symmetric eigensolver (a different routine from the oracle's SVD)."""
