@@ -160,6 +160,20 @@ tucker_status tucker_workspace_size(int which, tucker_dtype dt, const int64_t* d
                                     const int32_t* ranks, int32_t P, int32_t q, int64_t c,
                                     const tucker_opts* opts, size_t* bytes);
 
+/* The arithmetic a driver call with these arguments takes in each mode, as
+ * text, without running it (host only; no GPU needed): one line per mode,
+ *   "mode n: I=.. L=.. J=.. T=.. sketch=contiguous|strided power=F ttm=F"
+ * (plus " range-sketch=F" in the range form), F one of bf16x1, tf32,
+ * split-bf16, fp32, fp64 - the choice made for a 16-byte aligned tensor (a
+ * misaligned one falls back to the next form; see tucker_sketch_prec). I, J:
+ * extent and fibers of the tensor the mode works on; T: AMM samples (0 = none),
+ * whose I x T gather is then the sketched matrix. Writes a zero-terminated
+ * string into buf (256 bytes per mode suffice); returns the drivers' argument
+ * errors, and TUCKER_ERR_INVALID_ARG when buf is too small. */
+tucker_status tucker_plan_describe(int which, tucker_dtype dt, const int64_t* dims, int N,
+                                   const int32_t* ranks, int32_t P, int32_t q, int64_t c,
+                                   const tucker_opts* opts, char* buf, size_t buf_bytes);
+
 const char* tucker_status_string(tucker_status s);
 
 /* Name and description of the last CUDA error that made a call on this host

@@ -68,6 +68,8 @@ _SIGS = {
     "tucker_rthosvd": [_VP, _INT, _P(_I64), _INT, _P(_I32), _I32, _I32, _I64, _INT, _U64, _P(_VP), _VP, _P(Opts)],
     "tucker_rsthosvd": [_VP, _INT, _P(_I64), _INT, _P(_I32), _I32, _I32, _I64, _INT, _U64, _P(_VP), _VP, _P(Opts)],
     "tucker_workspace_size": [_INT, _INT, _P(_I64), _INT, _P(_I32), _I32, _I32, _I64, _P(Opts), _P(C.c_size_t)],
+    "tucker_plan_describe": [_INT, _INT, _P(_I64), _INT, _P(_I32), _I32, _I32, _I64, _P(Opts), C.c_char_p,
+                             C.c_size_t],
     "tucker_status_string": [_INT],
     "tucker_last_cuda_error": [],
     "tucker_last_device_status": [],
@@ -263,6 +265,22 @@ def workspace_size(which: str, dims, ranks, P=10, q=1, c=0, dtype=torch.float32,
                                      C.byref(n))
     _check("tucker_workspace_size", st)
     return int(n.value)
+
+
+def plan_describe(which: str, dims, ranks, P=10, q=1, c=0, dtype=torch.float32, **kw) -> str:
+    """The arithmetic each mode of a driver call takes (tucker_plan_describe),
+    one line per mode; host only."""
+    if which not in ("T", "ST"):
+        raise ValueError(f"which must be 'T' or 'ST', not {which!r}")
+    if len(ranks) != len(dims):
+        raise ValueError("dims and ranks must be of equal length")
+    buf = C.create_string_buffer(256 * max(1, len(dims)) + 1)
+    o = make_opts(**kw)
+    _check("tucker_plan_describe",
+           lib().tucker_plan_describe(0 if which == "T" else 1, 0 if dtype == torch.float32 else 1, _i64(dims),
+                                      len(dims), _i32(ranks), int(P), int(q), int(c), C.byref(o), buf,
+                                      len(buf)))
+    return buf.value.decode()
 
 
 def decompose(which: str, A: torch.Tensor, dims: Sequence[int], ranks: Sequence[int], P=10, q=1, c=0,

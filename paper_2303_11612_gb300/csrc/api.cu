@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -544,6 +545,46 @@ tucker_status tucker_workspace_size(int which, tucker_dtype dt, const int64_t* d
     Work w;
     carve(p, a, w);
     *bytes = a.used;
+    return TUCKER_OK;
+}
+
+tucker_status tucker_plan_describe(int which, tucker_dtype dt, const int64_t* dims, int N, const int32_t* ranks,
+                                   int32_t P, int32_t q, int64_t c, const tucker_opts* opts, char* buf,
+                                   size_t buf_bytes) {
+    if (!buf || buf_bytes == 0 || (which != 0 && which != 1)) return TUCKER_ERR_INVALID_ARG;
+    buf[0] = 0;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    Plan p;
+    rs = make_plan(which == 1, dt == TUCKER_F64 ? 8 : 4, dims, N, ranks, P, q, c, o, p);
+    if (rs != TUCKER_OK) return rs;
+    // the same choices power_step() and mode_product() make, for 16-byte aligned tensors
+    std::string text;
+    int64_t e[kMaxOrder];
+    for (int n = 0; n < N; ++n) e[n] = p.dims[n];
+    for (int n = 0; n < N; ++n) {
+        const ModePlan& mp = p.m[n];
+        const char* power = p.elem == 8 ? "fp64"
+                            : mp.tf32   ? "tf32"
+                            : mp.bf16x1 ? "bf16x1"
+                            : mp.tc     ? "split-bf16"
+                                        : "fp32";
+        const ModeView tv = p.st ? mp.v : view_of(e, N, n);
+        const char* ttm = p.elem == 8 ? "fp64"
+                          : (p.prec != TUCKER_SK_FP32 && ttm_tc_supported(tv, ranks[n])) ? "split-bf16"
+                                                                                         : "fp32";
+        const char* range = p.form != TUCKER_FORM_RANGE ? "" : p.elem == 8 ? " range-sketch=fp64" : " range-sketch=fp32";
+        char line[256];
+        snprintf(line, sizeof(line), "mode %d: I=%lld L=%d J=%lld T=%lld sketch=%s power=%s ttm=%s%s\n", n,
+                 (long long)mp.v.i, mp.L, (long long)mp.v.fibers(), (long long)mp.T,
+                 mp.mv.lf == 1 ? "contiguous" : "strided", power, ttm, range);
+        text += line;
+        if (!p.st) e[n] = ranks[n];
+    }
+    if (text.size() >= buf_bytes) return TUCKER_ERR_INVALID_ARG;
+    memcpy(buf, text.c_str(), text.size() + 1);
     return TUCKER_OK;
 }
 

@@ -232,3 +232,48 @@ def test_plain_c_caller(tmp_path):
     run = subprocess.run([str(exe)], capture_output=True, text=True)
     assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
     assert run.stdout.split()[0] == "ok"
+
+
+def _modes(text):
+    """{mode: {key: value}} from tucker_plan_describe's lines."""
+    out = {}
+    for line in text.strip().splitlines():
+        head, rest = line.split(":", 1)
+        out[int(head.split()[1])] = dict(kv.split("=") for kv in rest.split())
+    return out
+
+
+def test_plan_describe_pins_the_dispatch_rules():
+    """The arithmetic of each mode, decided on the host: single-pass BF16
+    sketches only the input tensor (every T-HOSVD mode, ST-HOSVD's first),
+    ST-HOSVD's later (truncated) modes and the TF32 form's strided modes take
+    split BF16, the mode product runs split BF16 on contiguous fibers in every
+    tensor-core form and FP32 FMA elsewhere, and FP64 data stays FP64."""
+    import torch
+    from paper_2303_11612_gb300 import _binding as B
+    dims, ranks = (400, 400, 400), (20, 20, 20)
+    st = _modes(B.plan_describe("ST", dims, ranks, prec="bf16x1"))
+    assert [st[n]["power"] for n in range(3)] == ["bf16x1", "split-bf16", "split-bf16"]
+    assert [st[n]["ttm"] for n in range(3)] == ["split-bf16", "fp32", "fp32"]
+    assert [int(st[n]["J"]) for n in range(3)] == [160000, 20 * 400, 20 * 20]     # ST truncates
+    t = _modes(B.plan_describe("T", dims, ranks, prec="bf16x1"))
+    assert [t[n]["power"] for n in range(3)] == ["bf16x1"] * 3
+    assert [t[n]["sketch"] for n in range(3)] == ["contiguous", "strided", "strided"]
+    assert [int(t[n]["J"]) for n in range(3)] == [160000] * 3
+    tf = _modes(B.plan_describe("T", dims, ranks, prec="tf32"))
+    assert [tf[n]["power"] for n in range(3)] == ["tf32", "split-bf16", "split-bf16"]
+    fp = _modes(B.plan_describe("ST", dims, ranks, prec="fp32"))
+    assert all(fp[n]["power"] == "fp32" and fp[n]["ttm"] == "fp32" for n in range(3))
+    amm = _modes(B.plan_describe("ST", dims, ranks, c=4000, prec="bf16x1"))
+    assert [int(amm[n]["T"]) for n in range(3)] == [4000, 4000, 400]               # T_n = min(c, J_n)
+    assert all(amm[n]["sketch"] == "contiguous" for n in range(3))                 # the I x T gather
+    f64 = _modes(B.plan_describe("ST", (100, 100, 100), (10, 10, 10), P=5, dtype=torch.float64))
+    assert all(f64[n]["power"] == "fp64" and f64[n]["ttm"] == "fp64" for n in range(3))
+    assert all(int(f64[n]["L"]) == 15 for n in range(3))
+    rng = _modes(B.plan_describe("ST", dims, ranks, form="range", prec="bf16x1"))
+    assert all(rng[n]["range-sketch"] == "fp32" for n in range(3))
+    lib = B.lib()
+    small = C.create_string_buffer(16)
+    assert lib.tucker_plan_describe(1, 0, B._i64(dims), 3, B._i32(ranks), 10, 1, 0, None, small, 16) == 1
+    assert lib.tucker_plan_describe(1, 0, B._i64(dims), 3, B._i32((401, 20, 20)), 10, 1, 0, None,
+                                    C.create_string_buffer(1024), 1024) == 1
