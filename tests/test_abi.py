@@ -277,3 +277,18 @@ def test_plan_describe_pins_the_dispatch_rules():
     assert lib.tucker_plan_describe(1, 0, B._i64(dims), 3, B._i32(ranks), 10, 1, 0, None, small, 16) == 1
     assert lib.tucker_plan_describe(1, 0, B._i64(dims), 3, B._i32((401, 20, 20)), 10, 1, 0, None,
                                     C.create_string_buffer(1024), 1024) == 1
+
+
+def test_planner_sketch_width_follows_the_oracles_reading():
+    """L_n = min(R_n + P, I_n), the reading the oracle takes, in the C planner
+    too (for ST-HOSVD on the truncated extents of the earlier modes)."""
+    from paper_2303_11612_gb300 import _binding as B
+    from oracle import tucker as ot
+    dims, ranks, P = (16, 40, 40), (12, 5, 30), 10
+    got = _modes(B.plan_describe("ST", dims, ranks, P=P))
+    assert [int(got[n]["L"]) for n in range(3)] == [min(r + P, d) for r, d in zip(ranks, dims)] == [16, 15, 40]
+    import numpy as np
+    A = np.random.default_rng(0).standard_normal(dims)
+    info = {}
+    ot.rsthosvd(A, ranks, P=P, q=1, info=info)
+    assert [info["L"][n] for n in range(3)] == [16, 15, 40]
