@@ -292,3 +292,25 @@ def test_planner_sketch_width_follows_the_oracles_reading():
     info = {}
     ot.rsthosvd(A, ranks, P=P, q=1, info=info)
     assert [info["L"][n] for n in range(3)] == [16, 15, 40]
+
+
+def test_planner_sample_counts_follow_the_oracle():
+    """T_n = min(c, J_n) for c > 0 and ceil(alpha J_n) for c = 0, alpha > 0 (the
+    parameter rule of Section 3.3), in the C planner as in the oracle, on the
+    tensor each mode works on."""
+    from paper_2303_11612_gb300 import _binding as B
+    from oracle import tucker as ot
+    dims, ranks = (30, 40, 50), (5, 6, 7)
+    for which in ("T", "ST"):
+        for c, alpha in ((1000, 0.0), (10, 0.0), (0, 0.05), (0, 0.3333), (0, 0.0)):
+            got = _modes(B.plan_describe(which, dims, ranks, P=3, c=c, alpha=alpha))
+            cur = list(dims)
+            for n in range(3):
+                J = 1
+                for m in range(3):
+                    if m != n:
+                        J *= cur[m]
+                assert int(got[n]["J"]) == J
+                assert int(got[n]["T"]) == ot.sample_count(c, alpha, J), (which, c, alpha, n)
+                if which == "ST":
+                    cur[n] = ranks[n]
