@@ -152,14 +152,17 @@ def test_randomized_close_to_deterministic_on_noisy_lowrank(kind, c, prob):
     assert ot.relative_error(A, Us, G) <= 1.5 * det + 1e-6
 
 
-def test_power_scheme_converges_to_deterministic_subspace():
+@pytest.mark.parametrize("form", [ot.FORM_PAPER, ot.FORM_RANGE])
+def test_power_scheme_converges_to_deterministic_subspace(form):
     """More power steps sharpen the sketch: the distance between the randomized
-    and the deterministic leading subspace falls as q grows (gapped spectrum)."""
+    and the deterministic leading subspace falls as q grows (gapped spectrum),
+    for the paper's (A A^T)^q Omega and for the range form's subspace
+    iteration alike."""
     A = synth.lowrank_noise((40, 30, 20), (6, 6, 6), rel_noise=0.3, seed=8, dtype=np.float64)
     Ud, _ = ot.thosvd(A, (6, 6, 6))
     d = []
     for q in (1, 2, 3, 4):
-        Us, _ = ot.rthosvd(A, (6, 6, 6), P=2, q=q, seed=1)
+        Us, _ = ot.rthosvd(A, (6, 6, 6), P=2, q=q, seed=1, form=form)
         d.append(_proj_dist(Us[0], Ud[0]))
     assert all(d[i + 1] < d[i] for i in range(3))
     assert d[-1] < 1e-3
