@@ -115,3 +115,13 @@ def test_wrong_gaussian_angle_is_caught(monkeypatch):
         return np.abs(z)            # e.g. a dropped sign from the angle term
     monkeypatch.setattr(philox, "gaussian_elements", bad)
     assert _caught(tphilox.test_gaussian_moments_and_ks)
+
+
+def test_unsquared_fiber_norms_are_caught(monkeypatch):
+    def bad(M, prob):
+        if prob == ot.PROB_UNIFORM:
+            return np.ones(M.shape[1])
+        return np.sqrt(np.sum(M.astype(np.float64) ** 2, axis=0))
+    monkeypatch.setattr(ot, "fiber_weights", bad)
+    assert _caught(tsamp.test_fiber_weights_hand_values)
+    assert _caught(tsamp.test_nearly_optimal_weights_minimise_the_enumerated_amm_error)

@@ -110,3 +110,51 @@ def test_nearly_optimal_beats_uniform_on_skewed_fibers():
             e.append(np.linalg.norm(ref - C @ C.T))
         out[prob] = np.mean(e)
     assert out[ot.PROB_NEARLY_OPTIMAL] < out[ot.PROB_UNIFORM]
+
+
+def test_fiber_weights_hand_values():
+    """Nearly-optimal weights are the squared fiber norms (remark after
+    Algorithm 3 with B = A^T): columns (3, 4), (0, 0), (1, 1) of a 2 x 3
+    unfolding have squared norms 25, 0 and 2; uniform weights are all one."""
+    M = np.array([[3.0, 0.0, 1.0],
+                  [4.0, 0.0, 1.0]])
+    assert ot.fiber_weights(M, ot.PROB_NEARLY_OPTIMAL).tolist() == [25.0, 0.0, 2.0]
+    assert ot.fiber_weights(M, ot.PROB_UNIFORM).tolist() == [1.0, 1.0, 1.0]
+    # quantised: the largest weight maps to 2^24, 2/25 of it rounds up
+    W = ot.quantize_weights(ot.fiber_weights(M, ot.PROB_NEARLY_OPTIMAL))
+    assert W.tolist() == [1 << 24, 0, math.ceil(2 / 25 * (1 << 24))]
+
+
+def _expected_amm_error(M, p):
+    """E ||M M^T - C' C'^T||_F^2 for one sample (T = 1) with probabilities p,
+    by enumerating the J outcomes; with T samples the error is this over T."""
+    ref = M @ M.T
+    e = 0.0
+    for j in range(M.shape[1]):
+        if p[j] == 0:
+            continue
+        c = M[:, j:j + 1] / math.sqrt(p[j])
+        e += p[j] * float(np.sum((ref - c @ c.T) ** 2))
+    return e
+
+
+def test_nearly_optimal_weights_minimise_the_enumerated_amm_error():
+    """The probabilities the oracle derives for the nearly-optimal scheme are
+    the minimiser of the AMM estimator's expected squared error (Lemma 5 and
+    the remark after Algorithm 3 with B = A^T: p_j proportional to the squared
+    fiber norm). Enumerated, not from a closed form: every random perturbation
+    of p, and the unsquared-norm probabilities, give a larger error."""
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((3, 6)) * np.array([0.2, 1.0, 3.0, 0.5, 1.5, 0.05])[None, :]
+    W = ot.quantize_weights(ot.fiber_weights(M, ot.PROB_NEARLY_OPTIMAL))
+    p = W.astype(np.float64) / float(W.sum())
+    best = _expected_amm_error(M, p)
+    for k in range(40):
+        d = rng.standard_normal(p.shape)
+        q = p * np.exp(0.05 * d)
+        q /= q.sum()
+        assert _expected_amm_error(M, q) > best
+    norms = np.linalg.norm(M, axis=0)
+    assert _expected_amm_error(M, norms / norms.sum()) > best * 1.01
+    u = np.full(p.shape, 1.0 / p.size)
+    assert _expected_amm_error(M, u) > best * 1.01
