@@ -69,8 +69,13 @@ typedef enum {
  * probabilities for A_(n) A_(n)^T), or uniform p_j = 1 / J_n. */
 typedef enum { TUCKER_PROB_NEARLY_OPTIMAL = 0, TUCKER_PROB_UNIFORM = 1 } tucker_prob;
 
-/* Element type of tensors, factors and the core. The sketch and the mode-n
- * products compute in this type; Gram matrices and Cholesky factors in FP64. */
+/* Element type of tensors, factors and the core. With TUCKER_F64 every step
+ * computes in FP64. With TUCKER_F32 the sketch and the mode-n products compute
+ * in FP32 (or the tensor-core form opts->prec selects); the orthonormalisation
+ * sums its Gram matrices of exact FP32 products in FP32 pairs and does the small
+ * triangular algebra (Cholesky, inverses) in double-float, two FP32 words
+ * (about 2^-47); the small SVD is a one-sided Jacobi in FP32 with its coupling
+ * sums in FP32 pairs (tucker_leading_factor). */
 typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
 
 /* Which sketch is taken.
@@ -273,13 +278,17 @@ tucker_status tucker_relative_error(const void* A, tucker_dtype dt, const int64_
  * cannot allocate device memory while they run (memory reserved once at start,
  * or hosts where cudaMalloc/cudaFree would stall other work).
  *
- * tucker_power_step_noalloc computes exactly what tucker_power_step computes
- * (X_out = A_(n) (A_(n)^T X_in), same arguments and layouts) but takes its
- * partial sums from a fixed block of TUCKER_NOALLOC_SCRATCH_BYTES of device
- * memory that belongs to the library (held on every GPU that loads it until
- * the process exits) and calls no allocator. The first call on a device looks
- * up that block's address and should come before any stream capture. Calls
- * share the block, so calls whose GPU work overlaps race; order them. Returns
+ * tucker_power_step_noalloc computes what tucker_power_step computes with
+ * opts->prec TUCKER_SK_FP32 (X_out = A_(n) (A_(n)^T X_in) in exact FP32 or FP64
+ * FMA arithmetic, same arguments and layouts) but takes its partial sums from a
+ * fixed block of TUCKER_NOALLOC_SCRATCH_BYTES of device memory that belongs to
+ * the library (held on every GPU that loads it until the process exits) and
+ * calls no allocator. Only that arithmetic is served: another opts->prec gives
+ * TUCKER_ERR_UNSUPPORTED; invalid options give TUCKER_ERR_INVALID_ARG as for
+ * tucker_power_step. The first call on a device looks up the block's address
+ * there (again after the device's context was recreated, e.g. by
+ * cudaDeviceReset) and should come before any stream capture. Calls share the
+ * block, so calls whose GPU work overlaps race; order them. Returns
  * TUCKER_ERR_UNSUPPORTED when one I_n x L partial (I_n * L * element size
  * bytes) exceeds the block, and otherwise the statuses of tucker_power_step;
  * it synchronises opts->stream before returning. */

@@ -513,6 +513,9 @@ bool mode_args_ok(const void* A, const int64_t* dims, int N, int mode) {
 }
 
 }  // namespace
+
+tucker_status status_from_cuda(cudaError_t e) { return from_cuda(e); }
+
 }  // namespace tk
 
 using namespace tk;

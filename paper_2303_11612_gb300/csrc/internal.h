@@ -131,6 +131,9 @@ cudaError_t launch_sumsq(const T* a, const T* b, int64_t n, double* out, void* s
 
 int num_sms();
 
+// The status a CUDA error maps to; records the error for tucker_last_cuda_error.
+tucker_status status_from_cuda(cudaError_t e);
+
 // ---- launch counting and profiling (profile.cu)
 enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKExtract = 4, kKSample = 5,
                    kKPowerBf16 = 6, kKPowerTf32 = 7, kKTtmBf16 = 8, kKPowerBf16x1 = 9, kKernelClasses = 10 };

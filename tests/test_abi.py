@@ -147,6 +147,28 @@ def test_options_and_server_argument_checks(lib):
         assert lib.tucker_server_create(C.byref(so), C.byref(h)) == 1, (field, value)
 
 
+def test_noalloc_power_step_checks_options_like_the_power_step(lib):
+    """The allocation-free power step answers option errors before any CUDA
+    call, with the statuses of tucker_power_step, and refuses the tensor-core
+    forms (it serves only the exact FMA arithmetic)."""
+    from paper_2303_11612_gb300 import _binding as B
+    dims = B._i64((64, 8, 8))
+    fake = 0x1000                    # never dereferenced: every case returns before any launch
+    bad_form = B.make_opts()
+    bad_form.form = 7
+    bad_prec = B.make_opts()
+    bad_prec.prec = 9
+    bad_alpha = B.make_opts(alpha=2.0)
+    short = B.make_opts()
+    short.struct_size = 8
+    for o in (bad_form, bad_prec, bad_alpha, short):
+        assert lib.tucker_power_step_noalloc(fake, 0, dims, 3, 0, fake, 8, fake, C.byref(o)) == 1
+        assert lib.tucker_power_step(fake, 0, dims, 3, 0, fake, 8, fake, C.byref(o)) == 1
+    for prec in ("tf32", "bf16", "bf16x1"):
+        o = B.make_opts(prec=prec)
+        assert lib.tucker_power_step_noalloc(fake, 0, dims, 3, 0, fake, 8, fake, C.byref(o)) == 6
+
+
 def test_measurement_entry_points_without_gpu(lib):
     """Launch counter, per-class profile counters (zero before any launch, one
     slot per kernel class the binding names) and the last-CUDA-error string
