@@ -1,28 +1,35 @@
 #!/usr/bin/env python
-"""Benchmark of the randomized ST-HOSVD path on GB300.
+"""Benchmark of the randomized (ST-)HOSVD path on GB300.
 
-Workload (one "step" = one batch covering every step of the path): randomized
-ST-HOSVD (Algorithms 2 and 5) with R_n = 20, P = 10 on two synthetic
-400 x 400 x 400 FP32 tensors, a Tucker tensor with a 20^3 N(0,1) core plus
-noise at 1e-2 relative Frobenius norm and the Hilbert tensor
-1 / (i + j + k - 2):
-  1. low-rank, q = 1, no sampling               (Algorithm 2)
-  2. low-rank, q = 1, c = 4000, nearly-optimal  (Algorithm 5)
-  3. Hilbert,  q = 2, no sampling               (Algorithm 2)
-  4. Hilbert,  q = 1, c = 4000, uniform         (Algorithm 5)
-value = decompositions per second with the tensors resident in HBM;
-e2e = the same through the C ABI with pinned host buffers (host->device copy of
-each input and device->host copy of the factors and core inside the timed
-region). Each tensor is 256 MB, larger than the 129 MB L2, so no flush is
-needed between steps.
+Headline workload (one "step" = one batch covering every step of the path):
+randomized ST-HOSVD (Algorithm 2, and Algorithm 5 with AMM) of 1024 x 1024 x 512
+FP32 video-like tensors (a sum of 50 separable sinusoids plus N(0, 1e-2) noise,
+2.15 GB each), ranks (64, 64, 32), P = 16, q = 1, variants
+  1. q = 1, no sampling                        (Algorithm 2)
+  2. q = 1, c = 20000 fibers, uniform p        (Algorithm 5)
+two decompositions of each variant per step, each on its own tensor (four
+distinct 2.15 GB tensors, larger than the 129 MB L2, so no flush is needed),
+in every sketch arithmetic (single-pass BF16, TF32, split BF16, FP32).
+value = decompositions per second with the tensors resident in HBM, for the
+fastest arithmetic whose relative error (Eq. 8) is within 1e-3 of the FP64
+oracle's on every variant; the oracle runs on the host on the same bytes (the
+first tensor), which also gives the CPU baseline. e2e = the same through the
+library's request loop with pinned host buffers (host->device copy of each
+input and device->host copy of the factors and core inside the timed region).
 
---impl reference times the FP64 CPU oracle on the same workload (one
-decomposition per step, cycling through the four variants).
+Secondary lines, each with its own oracle check: the 400^3 batch (low-rank
+and Hilbert tensors, q = 1 / 2, AMM c = 4000; 32 distinct buffers), the 96^4
+decaying-core tensor (q = 2), the FP64 100^3 T-HOSVD, randomized T-HOSVD,
+and a serving sample.
+
+--impl reference times the FP64 CPU oracle on the headline workload (one
+decomposition per step, cycling through the variants).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -33,47 +40,91 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# A batch runs its decompositions on 32 streams of one CUDA graph. CUDA maps
-# streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware work queues (8 unless set),
-# and work of different streams sharing a queue is dispatched in order, so
-# with 8 a decomposition waiting on its own chain holds up others queued behind
-# it. 32 queues give every stream its own; the variable is read when the CUDA
-# context is created, so it is set before anything touches the GPU.
+# A batch runs its decompositions on up to 32 streams of one CUDA graph. CUDA
+# maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware work queues (8 unless
+# set), and work of different streams sharing a queue is dispatched in order,
+# so with 8 a decomposition waiting on its own chain holds up others queued
+# behind it. 32 queues give every stream its own; the variable is read when the
+# CUDA context is created, so it is set before anything touches the GPU.
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
-DIMS = (400, 400, 400)
-RANKS = (20, 20, 20)
-P = 10
 SEED = 0
-VARIANTS = [
-    dict(name="lowrank_q1", tensor="lowrank", q=1, c=0, prob="uniform"),
-    dict(name="lowrank_q1_amm4000_nearly_optimal", tensor="lowrank", q=1, c=4000, prob="nearly_optimal"),
-    dict(name="hilbert_q2", tensor="hilbert", q=2, c=0, prob="uniform"),
-    dict(name="hilbert_q1_amm4000_uniform", tensor="hilbert", q=1, c=4000, prob="uniform"),
-]
 BASELINE_METRIC = "decomps/s & sketch HBM GB/s, BF16 vs FP32 at equal rel err; serving p50/p99 ms"
-PROFILED = ("power", "power_bf16", "power_tf32", "power_bf16x1", "ttm", "ttm_bf16", "gather", "norms", "extract",
-            "sample")
-# the dominant kernel of each form: (profiler class, name, source file, traffic.json key)
-DOMINANT = {
-    "bf16x1": ("power_bf16x1", "power_bf16x1_kernel (fused A(A^T X) pass, tcgen05 kind::f16 single-pass bf16, "
-                               "TMA-fed, fp32 accumulate)", "kernels_bf16x1.cu", "power_bf16x1_kernel_400cubed"),
-    "tf32": ("power_tf32", "power_tf32_kernel (fused A(A^T X) pass, tcgen05 kind::tf32, TMA-fed, fp32 accumulate)",
-             "kernels_tf32.cu", "power_tf32_kernel_400cubed"),
-    "bf16": ("power_bf16", "power_tc_kernel (fused A(A^T X) pass, tcgen05 split bf16, fp32 accumulate)",
-             "kernels_tc.cu", "power_tc_kernel_400cubed"),
-    "fp32": ("power", "power_kernel (fused A(A^T X) pass, FP32 FFMA)", "kernels_sketch.cu", "power_kernel_400cubed"),
+FORMS = ["bf16x1", "tf32", "bf16", "fp32"]
+RE_GATE = 1e-3            # reduced-precision forms: |RE - RE_oracle|
+FP32_RE_BAR = 1e-5        # exact FP32 form, where the sketch is not rank-deficient
+
+WORKLOADS = {
+    "video1024": dict(
+        desc="randomized ST-HOSVD of 1024x1024x512 FP32 video-like tensors (sum of 50 separable sinusoids + "
+             "N(0,1e-2) noise, 2.15 GB each), R=(64,64,32) P=16 q=1; variants: Algorithm 2; Algorithm 5 with "
+             "c=20000 uniform",
+        which="ST", dims=(1024, 1024, 512), ranks=(64, 64, 32), P=16, dtype="f32", copies=2,
+        variants=[dict(name="q1", gen="video", q=1, c=0, prob="uniform"),
+                  dict(name="q1_amm20000_uniform", gen="video", q=1, c=20000, prob="uniform")]),
+    "cube400": dict(
+        desc="randomized ST-HOSVD of 400^3 FP32 tensors (Tucker core 20^3 + 1e-2 noise, and the Hilbert tensor "
+             "1/(i+j+k-2)), R=20 P=10; variants: q=1; q=1 AMM c=4000 nearly-optimal; Hilbert q=2; Hilbert q=1 "
+             "AMM c=4000 uniform",
+        which="ST", dims=(400, 400, 400), ranks=(20, 20, 20), P=10, dtype="f32", copies=8,
+        variants=[dict(name="lowrank_q1", gen="lowrank", q=1, c=0, prob="uniform"),
+                  dict(name="lowrank_q1_amm4000_nearly_optimal", gen="lowrank", q=1, c=4000, prob="nearly_optimal"),
+                  dict(name="hilbert_q2", gen="hilbert", q=2, c=0, prob="uniform", rank_deficient=True),
+                  dict(name="hilbert_q1_amm4000_uniform", gen="hilbert", q=1, c=4000, prob="uniform",
+                       rank_deficient=True)]),
+    "quartic96": dict(
+        desc="randomized ST-HOSVD of 96^4 FP32 tensors with a decaying 16^4 core (entries N(0,1) 0.8^(i1+i2+i3+i4), "
+             "no noise), R=16 P=8 q=2",
+        which="ST", dims=(96, 96, 96, 96), ranks=(16, 16, 16, 16), P=8, dtype="f32", copies=16,
+        variants=[dict(name="q2", gen="decaying", q=2, c=0, prob="uniform")]),
+    "fp64cube100": dict(
+        desc="randomized T-HOSVD of 100^3 FP64 tensors (Tucker core 10^3 + 1e-3 noise), R=10 P=5 q=1",
+        which="T", dims=(100, 100, 100), ranks=(10, 10, 10), P=5, dtype="f64", copies=32, forms=["fp32"],
+        flush_l2=True,
+        variants=[dict(name="q1", gen="lowrank64", q=1, c=0, prob="uniform")]),
 }
-WORKLOAD = ("randomized ST-HOSVD, 400x400x400 FP32 (Tucker core 20^3 + 1e-2 noise, and Hilbert), "
-            "R=20 P=10, variants: q=1; q=1 AMM c=4000 nearly-optimal; Hilbert q=2; Hilbert q=1 AMM c=4000 uniform")
+HEADLINE = "video1024"
 
 
-def tensors():
+# ---------------------------------------------------------------- inputs
+def reference_tensor(gen, dims):
+    """The first tensor of a generator (seed 0), built on the host with numpy:
+    the bytes both the GPU path and the oracle decompose."""
     import numpy as np
     import synth
-    lowrank = synth.lowrank_noise(DIMS, RANKS, rel_noise=1e-2, seed=SEED, dtype=np.float32)
-    hilbert = synth.hilbert(DIMS, dtype=np.float32)
-    return {"lowrank": synth.flat(lowrank), "hilbert": synth.flat(hilbert)}
+    if gen == "video":
+        return synth.flat(synth.video_like(dims, seed=SEED))
+    if gen == "lowrank":
+        return synth.flat(synth.lowrank_noise(dims, (20,) * len(dims), rel_noise=1e-2, seed=SEED))
+    if gen == "hilbert":
+        return synth.flat(synth.hilbert(dims))
+    if gen == "decaying":
+        return synth.flat(synth.decaying_core(dims, 16, ratio=0.8, seed=SEED))
+    if gen == "lowrank64":
+        return synth.flat(synth.lowrank_noise(dims, (10,) * len(dims), rel_noise=1e-3, seed=SEED, dtype=np.float64))
+    raise ValueError(gen)
+
+
+def slot_tensor(torch, gen, dims, k, ref_dev):
+    """Tensor k >= 1 of a generator, built on the device with the same recipe
+    (distinct values; the Hilbert tensor is deterministic, so its slots hold
+    copies in distinct buffers)."""
+    import numpy as np
+    import synth
+    from synth import device as sd
+    if gen == "video":
+        return sd.video_like(torch, dims, seed=SEED + k)
+    if gen == "lowrank":
+        return sd.tucker_tensor(torch, dims, (20,) * len(dims), 1e-2, seed=SEED + k)
+    if gen == "hilbert":
+        return ref_dev.clone()
+    if gen == "decaying":
+        idx = np.meshgrid(*[np.arange(16)] * len(dims), indexing="ij")
+        return sd.tucker_tensor(torch, dims, (16,) * len(dims), 0.0, seed=SEED + k, core_scale=0.8 ** sum(idx))
+    if gen == "lowrank64":
+        return torch.from_numpy(synth.flat(synth.lowrank_noise(dims, (10,) * len(dims), rel_noise=1e-3,
+                                                               seed=SEED + k, dtype=np.float64))).cuda()
+    raise ValueError(gen)
 
 
 def load_peaks():
@@ -94,6 +145,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.active = False
 
     def start(self):
         try:
@@ -107,7 +159,8 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            if self.active:
+                self.lines.append(line.strip())
 
     def stop(self):
         if not self.proc:
@@ -132,16 +185,24 @@ class ClockSampler:
                 if val.lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "samples taken while timed regions ran"}
 
 
-# ---------------------------------------------------------------- CPU baseline (oracle)
-def oracle_decomposition(host, v):
+# ---------------------------------------------------------------- oracle (CPU baseline and accuracy reference)
+def oracle_run(W, v, host_ref):
+    """One oracle decomposition of variant v on the reference tensor: (Us, G, RE, seconds)."""
     import numpy as np
     import synth
     from oracle import tucker as ot
-    A = synth.from_flat(host[v["tensor"]], DIMS).astype(np.float64)
-    return ot.rsthosvd(A, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED)
+    A = synth.from_flat(host_ref, W["dims"]).astype(np.float64)
+    t0 = time.perf_counter()
+    fn = ot.rsthosvd if W["which"] == "ST" else ot.rthosvd
+    Us, G = fn(A, W["ranks"], P=W["P"], q=v["q"], c=v["c"], prob=v["prob"], seed=SEED)
+    dt = time.perf_counter() - t0
+    re = ot.relative_error(A, Us, G) if A.size <= 100_000_000 else \
+        math.sqrt(max(0.0, 1.0 - ot.frobenius(G) ** 2 / ot.frobenius(A) ** 2))
+    return Us, np.asarray(G).reshape(-1, order="F"), re, dt
 
 
 def cpu_cores():
@@ -151,43 +212,50 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(host, budget_s=20.0):
-    """The oracle as it stands, on this host's cores, over whole decompositions of
-    the batch (in order) until the time budget is used (at least one)."""
-    done, t0 = 0, time.perf_counter()
-    names = []
-    while True:
-        v = VARIANTS[done % len(VARIANTS)]
-        oracle_decomposition(host, v)
-        names.append(v["name"])
-        done += 1
-        if time.perf_counter() - t0 > budget_s or done >= 2 * len(VARIANTS):
-            break
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "decomps/s", "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"{done} whole 400^3 decompositions of the batch ({', '.join(names)}) in {dt:.1f} s, "
-                      f"numpy FP64 with its BLAS on all host cores"}
+def oracle_one_thread(workload, variant, timeout_s=120):
+    """The oracle on one host thread (the paper's setting, maxNumCompThreads = 1),
+    one decomposition of a variant, timed in a fresh process whose BLAS is held
+    to one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, sys.argv[1]); import bench; "
+            "W = bench.WORKLOADS[sys.argv[2]]; v = next(x for x in W['variants'] if x['name'] == sys.argv[3]); "
+            "ref = bench.reference_tensor(v['gen'], W['dims']); _, _, re, dt = bench.oracle_run(W, v, ref); "
+            "print(json.dumps({'seconds': dt, 're': re}))")
+    try:
+        out = subprocess.run([sys.executable, "-c", code, ROOT, workload, variant], env=env, capture_output=True,
+                             text=True, timeout=timeout_s)
+        r = json.loads(out.stdout.strip().splitlines()[-1])
+        return {"value": 1.0 / r["seconds"], "unit": "decomps/s", "cores": 1, "kind": "oracle",
+                "sample": f"one {workload} {variant} decomposition on one thread ({r['seconds']:.1f} s)"}
+    except Exception as exc:  # noqa: BLE001
+        return {"value": None, "unit": "decomps/s", "cores": 1, "kind": "oracle", "error": str(exc)[:200]}
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank):
     if rank != 0:
         return 0
-    host = tensors()
+    W = WORKLOADS[HEADLINE]
+    refs = {}
+    for v in W["variants"]:
+        if v["gen"] not in refs:
+            refs[v["gen"]] = reference_tensor(v["gen"], W["dims"])
+    vs = W["variants"]
     for k in range(args.warmup):
-        oracle_decomposition(host, VARIANTS[k % len(VARIANTS)])
+        oracle_run(W, vs[k % len(vs)], refs[vs[k % len(vs)]["gen"]])
     t0 = time.perf_counter()
     for k in range(args.steps):
-        oracle_decomposition(host, VARIANTS[k % len(VARIANTS)])
+        oracle_run(W, vs[k % len(vs)], refs[vs[k % len(vs)]["gen"]])
     dt = time.perf_counter() - t0
     val = args.steps / dt
     line = {"impl": "reference", "metric": "decomps/s", "value": val, "unit": "decomps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "baseline_metric": BASELINE_METRIC,
-            "config": {"workload": WORKLOAD + " (reference: FP64 CPU oracle, one decomposition per step)"},
+            "config": {"workload": W["desc"] + " (reference: FP64 CPU oracle, one decomposition per step)"},
             "cpu_baseline": {"value": val, "unit": "decomps/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": f"{args.steps} decompositions cycling through the 4 variants"},
+                             "sample": f"{args.steps} decompositions cycling through the {len(vs)} variants"},
             "e2e": {"value": val, "unit": "decomps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -205,21 +273,14 @@ def serving_requests(torch, n=SERVE_N, seed=0):
     full stream's order-4 requests reach 256^4 = 17 GB each; the sample keeps
     the whole set resident)."""
     import numpy as np
+    from synth import device as sd
     rng = np.random.default_rng(seed)
-    g = torch.Generator(device="cuda")
-    g.manual_seed(seed)
     out = []
     for k in range(n):
         N = 3 if rng.random() < 0.5 else 4
         dims = [int(x) for x in rng.integers(32, (256 if N == 3 else 96) + 1, size=N)]
         ranks = [int(min(d, r)) for d, r in zip(dims, rng.integers(4, 33, size=N))]
-        X = torch.randn(*reversed(ranks), device="cuda", generator=g)
-        for m in range(N):                 # X x_m U_m, i_1 fastest: torch axis N-1-m
-            Um = torch.linalg.qr(torch.randn(dims[m], ranks[m], device="cuda", generator=g))[0]
-            X = torch.movedim(torch.tensordot(X, Um, dims=([N - 1 - m], [1])), -1, N - 1 - m)
-        X = X / X.norm()
-        E = torch.randn(X.shape, device="cuda", generator=g)
-        X = (X + 1e-2 * E / E.norm()).contiguous().view(-1)
+        X = sd.tucker_tensor(torch, dims, ranks, 1e-2, seed=1000 + k)
         out.append(dict(A=X, dims=dims, ranks=ranks, seed=k))
     torch.cuda.synchronize()
     return out
@@ -281,24 +342,181 @@ def whole_job_rate(units_per_rank, world, seconds):
     return units_per_rank * world / seconds
 
 
+# ---------------------------------------------------------------- accuracy against the oracle
+def projector_distance(U, Uo):
+    """||U U^T - Uo Uo^T||_2 for orthonormal I x R bases: the sine of the largest
+    principal angle, sqrt(1 - sigma_min(U^T Uo)^2)."""
+    import numpy as np
+    s = np.linalg.svd(U.T @ Uo, compute_uv=False)
+    return float(math.sqrt(max(0.0, 1.0 - float(np.min(s)) ** 2)))
+
+
 # ---------------------------------------------------------------- GPU arm
+class Bench:
+    def __init__(self, args, torch, tk, dist, world):
+        self.args, self.torch, self.tk, self.dist, self.world = args, torch, tk, dist, world
+        self.main_s = torch.cuda.Stream()
+        self.clocks = None
+
+    def barrier(self):
+        rank_barrier(self.dist, self.torch, cuda=True)
+
+    def max_over_ranks(self, x):
+        return rank_max(self.dist, self.torch, x, "cuda")
+
+    def prepare(self, name):
+        """Reference tensors (host, seed 0) with their oracle results, and one
+        distinct device tensor per batch slot."""
+        import numpy as np
+        torch = self.torch
+        W = WORKLOADS[name]
+        refs, oracle = {}, {}
+        t_oracle = 0.0
+        for v in W["variants"]:
+            if v["gen"] not in refs:
+                refs[v["gen"]] = reference_tensor(v["gen"], W["dims"])
+            Us, G, re, dt = oracle_run(W, v, refs[v["gen"]])
+            oracle[v["name"]] = dict(U=Us, G=G, re=re, seconds=dt)
+            t_oracle += dt
+        ref_dev = {g: torch.from_numpy(h).cuda() for g, h in refs.items()}
+        slots, counts = [], {}
+        for v in W["variants"]:
+            for _ in range(W["copies"]):
+                k = counts.get(v["gen"], 0)
+                counts[v["gen"]] = k + 1
+                A = ref_dev[v["gen"]] if k == 0 else slot_tensor(torch, v["gen"], W["dims"], k, ref_dev[v["gen"]])
+                slots.append((v, A))
+        torch.cuda.synchronize()
+        return dict(W=W, refs=refs, ref_dev=ref_dev, oracle=oracle, slots=slots, oracle_seconds=t_oracle,
+                    distinct=sum(counts.values()))
+
+    def accuracy(self, P, prec):
+        """RE (explicit reconstruction on the device) of every variant on the
+        reference tensor, with its distance to the oracle's, projector distances
+        per mode and the core's relative error."""
+        import numpy as np
+        tk, W = self.tk, P["W"]
+        out = {}
+        for v in W["variants"]:
+            A = P["ref_dev"][v["gen"]]
+            U, G = tk.decompose(W["which"], A, W["dims"], W["ranks"], P=W["P"], q=v["q"], c=v["c"], prob=v["prob"],
+                                seed=SEED, prec=prec)
+            re = tk.relative_error(A, W["dims"], W["ranks"], U, G)
+            o = P["oracle"][v["name"]]
+            Uh = [u.double().cpu().numpy() for u in U]
+            Gh = G.double().cpu().numpy()
+            out[v["name"]] = {
+                "rel_error": re, "oracle_rel_error": o["re"], "abs_diff": abs(re - o["re"]),
+                "projector_dist": [projector_distance(u, uo) for u, uo in zip(Uh, o["U"])],
+                "core_rel_err": float(np.linalg.norm(Gh - o["G"]) / max(np.linalg.norm(o["G"]), 1e-300))}
+        return out
+
+    def timed(self, P, prec, steps):
+        """Graph-timed throughput of the batch (every slot its own tensor)."""
+        torch, tk, W = self.torch, self.tk, P["W"]
+        bt = tk.Batch([dict(which=W["which"], A=A, dims=W["dims"], ranks=W["ranks"], P=W["P"], q=v["q"], c=v["c"],
+                            prob=v["prob"], seed=SEED) for v, A in P["slots"]], prec=prec)
+        for _ in range(self.args.warmup):
+            bt.run(stream=self.main_s, sync=False)
+        self.main_s.synchronize()
+        bt.run(stream=self.main_s)                               # synchronous: raises on a device status
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if W.get("flush_l2") else None
+        self.barrier()
+        self.clocks.active = True
+        n0 = tk.launch_count()
+        ms = 0.0
+        if flush is None:
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(self.main_s)
+            for _ in range(steps):
+                bt.run(stream=self.main_s, sync=False)
+            ev1.record(self.main_s)
+            self.main_s.synchronize()
+            ms = ev0.elapsed_time(ev1)
+        else:
+            # small tensors: the L2 is flushed between steps, outside the timed events
+            evs = []
+            with torch.cuda.stream(self.main_s):
+                for _ in range(steps):
+                    flush.fill_(1)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(self.main_s)
+                    bt.run(stream=self.main_s, sync=False)
+                    e1.record(self.main_s)
+                    evs.append((e0, e1))
+            self.main_s.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in evs)
+        n1 = tk.launch_count()
+        self.clocks.active = False
+        self.barrier()
+        if any(bt.status()):
+            raise RuntimeError("device status not OK in the timed region")
+        ms = self.max_over_ranks(ms)
+        del bt
+        return {"ms": ms, "value": whole_job_rate(len(P["slots"]) * steps, self.world, ms / 1e3),
+                "gpu_launches": n1 - n0}
+
+    def profile(self, P, prec, reps):
+        """Per-kernel-class launch counts, times and algorithmic bytes/flops from
+        eager decompositions run one at a time on one stream (graph-captured
+        event pairs carry no timings)."""
+        import numpy as np
+        torch, tk, W = self.torch, self.tk, P["W"]
+        wss, outs = [], []
+        for v in W["variants"]:
+            dt = P["ref_dev"][v["gen"]].dtype
+            wss.append(torch.empty(tk.workspace_size(W["which"], W["dims"], W["ranks"], P=W["P"], q=v["q"], c=v["c"],
+                                                     dtype=dt, prec=prec), dtype=torch.uint8, device="cuda"))
+            outs.append(([tk.factor_tensor(I, R, dt, "cuda") for I, R in zip(W["dims"], W["ranks"])],
+                         torch.empty(int(np.prod(W["ranks"])), dtype=dt, device="cuda")))
+        tk.profile_enable(True)
+        for _ in range(reps):
+            for v, ws, out in zip(W["variants"], wss, outs):
+                tk.decompose(W["which"], P["ref_dev"][v["gen"]], W["dims"], W["ranks"], P=W["P"], q=v["q"], c=v["c"],
+                             prob=v["prob"], seed=SEED, workspace=ws, stream=self.main_s, out=out,
+                             flags=tk.FLAG_ASYNC, prec=prec)
+        self.main_s.synchronize()
+        from paper_2303_11612_gb300 import _binding as B
+        prof = {k: tk.profile_read(k) for k in B.KERNEL_CLASSES}
+        tk.profile_enable(False)
+        if tk.last_device_status() != 0:
+            raise RuntimeError("device status not OK in the profiled decompositions")
+        return prof
+
+    def workload_line(self, name, forms, steps):
+        """Every form of one workload: accuracy against the oracle, timed batch,
+        and the gates."""
+        P = self.prepare(name)
+        W = P["W"]
+        res = {}
+        for prec in forms:
+            acc = self.accuracy(P, prec)
+            t = self.timed(P, prec, steps)
+            gate = all(a["abs_diff"] <= RE_GATE for a in acc.values())
+            fp32_bar = {k: a["abs_diff"] <= FP32_RE_BAR for k, a in acc.items()
+                        if not next(v for v in W["variants"] if v["name"] == k).get("rank_deficient")}
+            res[prec] = dict(t, accuracy=acc, re_within_1e_3_of_oracle=gate,
+                             re_within_1e_5_of_oracle=fp32_bar if prec == "fp32" else None)
+        return P, res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prec", default="all", choices=["all", "bf16x1", "tf32", "bf16", "fp32"],
+    ap.add_argument("--prec", default="all", choices=["all"] + FORMS,
                     help="sketch arithmetic to time (all: the headline is the fastest form whose relative "
-                         "errors are within 1e-3 of FP32's)")
+                         "errors are within 1e-3 of the oracle's)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-secondary", action="store_true", help="headline workload only")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel configurations (no tuning in the synchronous warm-up calls)")
-    ap.add_argument("--copies", type=int, default=8,
-                    help="decompositions of each variant in flight per step (each on its own stream)")
-    ap.add_argument("--single", default=None, choices=[v["name"] for v in VARIANTS],
-                    help="run one decomposition of one variant after one warm-up and exit (profiling case)")
+    ap.add_argument("--single", default=None,
+                    help="WORKLOAD:VARIANT -- run one decomposition of one variant after one warm-up and exit "
+                         "(profiling case)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -316,259 +534,206 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    host = tensors()
     if args.single:
-        v = next(x for x in VARIANTS if x["name"] == args.single)
-        A = torch.from_numpy(host[v["tensor"]]).cuda()
-        prec = "tf32" if args.prec == "all" else args.prec
+        wname, vname = args.single.split(":") if ":" in args.single else ("cube400", args.single)
+        W = WORKLOADS[wname]
+        v = next(x for x in W["variants"] if x["name"] == vname)
+        A = torch.from_numpy(reference_tensor(v["gen"], W["dims"])).cuda()
+        prec = "bf16x1" if args.prec == "all" else args.prec
         for _ in range(2):
-            tk.rsthosvd(A, DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED, prec=prec)
+            tk.decompose(W["which"], A, W["dims"], W["ranks"], P=W["P"], q=v["q"], c=v["c"], prob=v["prob"],
+                         seed=SEED, prec=prec)
         torch.cuda.synchronize()
-        print(json.dumps({"single": v["name"], "prec": prec, "ok": True}))
+        print(json.dumps({"single": args.single, "prec": prec, "ok": True}))
         return 0
     if not args.no_autotune:
-        # the synchronous accuracy checks below meet every shape class first and
-        # tune it; the graph-captured batch steps then reuse the kept choices
+        # the synchronous accuracy checks meet every shape class first and tune it;
+        # the graph-captured batch steps then reuse the kept choices
         tk.autotune_enable(True)
-    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
-    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
-    main_s = torch.cuda.Stream()
-    batch = [v for v in VARIANTS for _ in range(args.copies)]
+    b = Bench(args, torch, tk, dist, world)
+    b.clocks = ClockSampler(local)
+    b.clocks.start()
+    forms = FORMS if args.prec == "all" else [args.prec]
 
-    def barrier():
-        rank_barrier(dist, torch, cuda=True)
-
-    def max_over_ranks(x):
-        return rank_max(dist, torch, x, "cuda")
-
-    clocks = ClockSampler(local)
-    clocks.start()
-
-    def measure(prec):
-        """Graph-timed throughput of the batch with one sketch arithmetic."""
-        # accuracy of what is timed: explicit relative error of every variant
-        res = {}
-        for v in VARIANTS:
-            U, G = tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
-                               prec=prec)
-            res[v["name"]] = tk.relative_error(dev[v["tensor"]], DIMS, RANKS, U, G)
-        # the timed path: the library's batch call, which captures the whole step
-        # (every decomposition on its own stream) into one CUDA graph on its first
-        # run and replays it afterwards
-        bt = tk.Batch([dict(which="ST", A=dev[v["tensor"]], dims=DIMS, ranks=RANKS, P=P, q=v["q"], c=v["c"],
-                            prob=v["prob"], seed=SEED) for v in batch], prec=prec)
-        for _ in range(args.warmup):
-            bt.run(stream=main_s, sync=False)
-        main_s.synchronize()
-        bt.run(stream=main_s)                               # synchronous: raises on a device status
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        n0 = tk.launch_count()
-        ev0.record(main_s)
-        for _ in range(args.steps):
-            bt.run(stream=main_s, sync=False)
-        ev1.record(main_s)
-        main_s.synchronize()
-        n1 = tk.launch_count()
-        barrier()
-        if any(bt.status()):
-            raise RuntimeError("device status not OK in the timed region")
-        ms = max_over_ranks(ev0.elapsed_time(ev1))
-        del bt
-        # per-kernel durations: event pairs inside a graph carry no timings, so they
-        # come from eager decompositions run right after the timed region, one at a
-        # time on one stream (each kernel has the GPU to itself, as in a serialised
-        # launch list)
-        wss = [torch.empty(tk.workspace_size("ST", DIMS, RANKS, P=P, q=v["q"], c=v["c"], prec=prec),
-                           dtype=torch.uint8, device="cuda") for v in VARIANTS]
-        outs = [([tk.factor_tensor(I, R, torch.float32, "cuda") for I, R in zip(DIMS, RANKS)],
-                 torch.empty(int(np.prod(RANKS)), dtype=torch.float32, device="cuda")) for _ in VARIANTS]
-        tk.profile_enable(True)
-        for _ in range(max(3, args.steps // 10)):
-            for v, ws, out in zip(VARIANTS, wss, outs):
-                tk.rsthosvd(dev[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"], seed=SEED,
-                            workspace=ws, stream=main_s, out=out, flags=tk.FLAG_ASYNC, prec=prec)
-        main_s.synchronize()
-        prof = {k: tk.profile_read(k) for k in PROFILED}
-        tk.profile_enable(False)
-        if tk.last_device_status() != 0:
-            raise RuntimeError("device status not OK in the profiled decompositions")
-        return {"prec": prec, "ms": ms, "value": whole_job_rate(len(batch) * args.steps, world, ms / 1e3),
-                "gpu_launches": n1 - n0, "graph": True, "rel_error": res, "prof": prof}
-
-    forms = {}
-    for prec in (["bf16x1", "tf32", "bf16", "fp32"] if args.prec == "all" else [args.prec]):
-        forms[prec] = measure(prec)
-    clk = clocks.stop()
-    # headline: the fastest form whose relative error matches FP32's within 1e-3 on every variant
-    def matches(f):
-        return "fp32" not in forms or all(abs(f["rel_error"][k] - forms["fp32"]["rel_error"][k]) <= 1e-3
-                                          for k in forms["fp32"]["rel_error"])
-    equal = {p: matches(f) for p, f in forms.items()}
-    head = max((f for p, f in forms.items() if equal[p]), key=lambda f: f["value"])
-    serving = None
-    if not args.no_serving:
-        reqs = serving_requests(torch)
-        serving = {p: serving_bench(tk, torch, reqs, p) for p in dict.fromkeys([head["prec"], "fp32"])
-                   if p in forms}
-        serving["sample"] = (f"{len(reqs)} randomized ST-HOSVD requests (P=5, q=1), orders 3/4, extents U{{32..256}} "
-                             f"(order 3) / U{{32..96}} (order 4), ranks U{{4..32}}, low-rank + 1e-2 noise, device-"
-                             f"resident; budget {SERVE_BUDGET >> 30} GB, 16 streams; latencies at 0.7x the "
-                             f"saturation throughput, Poisson arrivals")
-        del reqs
-
-    # randomized T-HOSVD (Algorithm 1) on the same low-rank tensor in the headline
-    # arithmetic, as a secondary line: every mode sketches the full tensor (modes 2
-    # and 3 through strided fibers), 32 decompositions per batch call
-    thosvd = None
-    try:
-        tb = tk.Batch([dict(which="T", A=dev["lowrank"], dims=DIMS, ranks=RANKS, P=P, q=1, c=0, prob="uniform",
-                            seed=SEED + k) for k in range(len(batch))], prec=head["prec"])
-        for _ in range(args.warmup):
-            tb.run(stream=main_s, sync=False)
-        tb.run(stream=main_s)
-        t_steps = max(3, args.steps // 10)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(main_s)
-        for _ in range(t_steps):
-            tb.run(stream=main_s, sync=False)
-        e1.record(main_s)
-        main_s.synchronize()
-        barrier()
-        if any(tb.status()):
-            raise RuntimeError("device status not OK")
-        t_ms = max_over_ranks(e0.elapsed_time(e1))
-        thosvd = {"value": whole_job_rate(len(batch) * t_steps, world, t_ms / 1e3), "unit": "decomps/s",
-                  "prec": head["prec"], "steps": t_steps,
-                  "workload": "randomized T-HOSVD of the 400^3 low-rank tensor, R=20 P=10 q=1, "
-                              f"{len(batch)} per tucker_batch_run call"}
-        del tb
-    except Exception as exc:  # noqa: BLE001
-        thosvd = {"value": None, "error": str(exc)}
-
-    # end to end through the public API with pinned host buffers, headline arithmetic:
-    # every step submits the whole batch to the library's request loop, which
-    # stages each input host->device and each result device->host on the
-    # request's own stream, so copies of one request overlap work of others
-    houts = [([torch.empty((R, I), dtype=torch.float32).pin_memory().t() for I, R in zip(DIMS, RANKS)],
-              torch.empty(int(np.prod(RANKS)), dtype=torch.float32).pin_memory()) for _ in batch]
-
-    e2e = None
-    try:
-        with tk.Server(budget_bytes=64 << 30, max_inflight=len(batch), prec=head["prec"]) as srv:
-            def step_e2e():
-                ts = [srv.submit("ST", pinned[v["tensor"]], DIMS, RANKS, P=P, q=v["q"], c=v["c"], prob=v["prob"],
-                                 seed=SEED, out=out) for v, out in zip(batch, houts)]
-                for t in ts:
-                    srv.wait(t)
-
-            step_e2e()
-            barrier()
-            e2e_steps = max(3, args.steps // 10)
-            t0 = time.perf_counter()
-            for _ in range(e2e_steps):
-                step_e2e()
-            e2e_s = max_over_ranks(time.perf_counter() - t0)
-        h2d = sum(host[v["tensor"]].nbytes for v in batch)
-        d2h = sum((sum(I * R for I, R in zip(DIMS, RANKS)) + int(np.prod(RANKS))) * 4 for _ in batch)
-        e2e = {"value": whole_job_rate(len(batch) * e2e_steps, world, e2e_s), "unit": "decomps/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "path": f"tucker_server_* request loop, {len(batch)} requests per step, pinned host input and "
-                       f"output buffers, host clock around the steps"}
-    except Exception as exc:  # noqa: BLE001
-        e2e = {"value": None, "unit": "decomps/s", "error": str(exc)}
+    # ---- headline
+    P, res = b.workload_line(HEADLINE, forms, args.steps)
+    W = P["W"]
+    ok = {p: r["re_within_1e_3_of_oracle"] for p, r in res.items()}
+    cands = [p for p in res if ok[p]] or list(res)
+    head = max(cands, key=lambda p: res[p]["value"])
+    prof = b.profile(P, head, reps=max(2, args.steps // 10))
 
     peaks, peak_kind = load_peaks()
-    pclass, pname, src_file, tkey = DOMINANT[head["prec"]]
-    pw_n, pw_ms, pw_bytes, pw_flops = head["prof"][pclass]
+    power_classes = [k for k in prof if k.startswith("power")]
+    pclass = max(power_classes, key=lambda k: prof[k][1])
+    pw_n, pw_ms, pw_bytes, pw_flops = prof[pclass]
     achieved_gbs = pw_bytes / (pw_ms / 1e3) / 1e9 if pw_ms > 0 else 0.0
     achieved_tflops = pw_flops / (pw_ms / 1e3) / 1e12 if pw_ms > 0 else 0.0
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if head["prec"] in ("bf16", "tf32", "bf16x1"):
-        # bandwidth-bound: 4 L flops per 4-byte element is ~30 flops/byte, far below the
-        # tensor ridge (bf16 ~285, tf32 ~140 flops/byte), so the bound is HBM
+    if pclass != "power":
+        # bandwidth-bound: 4 L flops per 4-byte element (80 flops/byte at L = 80) is far
+        # below the bf16 tensor ridge (~280 flops/byte), so the bound is HBM
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved_gbs / peaks["hbm_gbs"], "kernel": pname, "tensor_tflops": achieved_tflops}
+                    "frac": achieved_gbs / peaks["hbm_gbs"], "kernel_class": pclass, "tensor_tflops": achieved_tflops}
     else:
         fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": achieved_tflops / fp32_peak, "kernel": pname,
+                    "frac": achieved_tflops / fp32_peak, "kernel_class": pclass,
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz", "hbm_gbs": achieved_gbs}
     traffic = None
     try:
         import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            tr = json.load(f).get(tkey)
-        src = open(os.path.join(ROOT, "paper_2303_11612_gb300", "csrc", src_file), "rb").read()
-        if tr and tr.get("source_sha256") == hashlib.sha256(src).hexdigest():
-            # DRAM bytes per algorithmic byte from one ncu capture, times this run's bytes per launch
-            traffic = tr["dram_bytes_per_algorithmic_byte"] * pw_bytes / max(pw_n, 1)
+            tr = json.load(f).get(f"{pclass}@{HEADLINE}")
+        if tr:
+            src = open(os.path.join(ROOT, "paper_2303_11612_gb300", "csrc", tr["source"]), "rb").read()
+            if tr.get("source_sha256") == hashlib.sha256(src).hexdigest():
+                traffic = tr["dram_bytes_per_algorithmic_byte"] * pw_bytes / max(pw_n, 1)
     except Exception:
         traffic = None
     roofline.update({"traffic": traffic, "launches": pw_n, "ms_per_launch": pw_ms / max(pw_n, 1),
                      "algorithmic_bytes_per_launch": pw_bytes / max(pw_n, 1), "peak_kind": peak_kind,
-                     "timing": "CUDA events around each launch in eager decompositions run one at a time on "
-                               "one stream right after the graph-timed region (graph event nodes carry no timings)"})
-    # the dominant launch alone: the mode-1 power step on one 400^3 tensor (the
-    # class above also averages the launches on the 4000-fiber AMM samples)
-    if head["prec"] in ("tf32", "bf16", "bf16x1"):
-        X = torch.randn(30, DIMS[0], device="cuda").t()
-        for _ in range(3):
-            tk.power_step(dev["lowrank"], DIMS, 0, X, prec=head["prec"])
-        torch.cuda.synchronize()
-        tk.profile_enable(True)
-        for _ in range(10):
-            tk.power_step(dev["lowrank"], DIMS, 0, X, prec=head["prec"])
-        torch.cuda.synchronize()
-        n1, ms1, b1, _ = tk.profile_read(pclass)
-        tk.profile_enable(False)
-        if n1:
-            g1 = b1 / (ms1 / 1e3) / 1e9
-            roofline["mode1_full_tensor"] = {"launches": n1, "ms_per_launch": ms1 / n1, "achieved": g1,
-                                             "frac": g1 / peaks["hbm_gbs"], "unit": "GB/s",
-                                             "algorithmic_bytes_per_launch": b1 / n1,
-                                             "timing": "CUDA events around 10 back-to-back launches of the "
-                                                       "mode-1 power step on the 256 MB tensor (L = 30)"}
+                     "timing": "CUDA events on the launching stream around each launch, in eager decompositions "
+                               "run one at a time right after the graph-timed region (graph event nodes carry "
+                               "no timings)"})
     kernels = {}
-    for k in PROFILED:
-        if k == pclass:
-            continue
-        n, kms, b, f = head["prof"][k]
+    for k, (n, kms, by, fl) in prof.items():
         if n:
-            kernels[k] = {"launches": n, "ms_per_launch": kms / n}
-            if b:
-                kernels[k].update({"gbs": b / (kms / 1e3) / 1e9, "hbm_frac": b / (kms / 1e3) / 1e9 / peaks["hbm_gbs"]})
-    line = {"metric": "decomps/s", "value": head["value"], "unit": "decomps/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps,
+            kernels[k] = {"launches": n, "ms_per_launch": kms / n, "share_of_kernel_time":
+                          kms / max(sum(x[1] for x in prof.values()), 1e-12)}
+            if by:
+                kernels[k].update({"gbs": by / (kms / 1e3) / 1e9,
+                                   "hbm_frac": by / (kms / 1e3) / 1e9 / peaks["hbm_gbs"]})
+
+    # ---- end to end through the request loop with pinned host buffers, headline arithmetic
+    e2e = None
+    try:
+        host_in = [torch.empty(A.numel(), dtype=A.dtype).pin_memory() for _, A in P["slots"]]
+        for h, (_, A) in zip(host_in, P["slots"]):
+            h.copy_(A)
+        houts = [([torch.empty((R, I), dtype=torch.float32).pin_memory().t() for I, R in zip(W["dims"], W["ranks"])],
+                  torch.empty(int(np.prod(W["ranks"])), dtype=torch.float32).pin_memory()) for _ in P["slots"]]
+        budget = sum(h.numel() * 4 for h in host_in) + (24 << 30)
+        with tk.Server(budget_bytes=budget, max_inflight=len(P["slots"]), prec=head) as srv:
+            def step_e2e():
+                ts = [srv.submit(W["which"], h, W["dims"], W["ranks"], P=W["P"], q=v["q"], c=v["c"], prob=v["prob"],
+                                 seed=SEED, out=out) for (v, _), h, out in zip(P["slots"], host_in, houts)]
+                for t in ts:
+                    srv.wait(t)
+
+            step_e2e()
+            b.barrier()
+            e2e_steps = max(3, args.steps // 4)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                step_e2e()
+            e2e_s = b.max_over_ranks(time.perf_counter() - t0)
+        h2d = sum(h.numel() * h.element_size() for h in host_in)
+        d2h = len(P["slots"]) * (sum(I * R for I, R in zip(W["dims"], W["ranks"])) + int(np.prod(W["ranks"]))) * 4
+        e2e = {"value": whole_job_rate(len(P["slots"]) * e2e_steps, world, e2e_s), "unit": "decomps/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "path": f"tucker_server_* request loop, {len(P['slots'])} requests per step, pinned host input and "
+                       f"output buffers, host clock around the steps"}
+        del host_in, houts
+    except Exception as exc:  # noqa: BLE001
+        e2e = {"value": None, "unit": "decomps/s", "error": str(exc)}
+
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_or = len(P["oracle"])
+        secs = sum(o["seconds"] for o in P["oracle"].values())
+        cpu_baseline = {"value": n_or / secs, "unit": "decomps/s", "cores": cpu_cores(), "kind": "oracle",
+                        "sample": f"{n_or} whole {HEADLINE} decompositions ({', '.join(P['oracle'])}) of the first "
+                                  f"tensor in {secs:.1f} s, numpy FP64 with its BLAS on all host cores (the same "
+                                  f"runs give the oracle's relative errors)"}
+    head_line = {p: {"value": r["value"], "ms_per_step": r["ms"] / args.steps, "gpu_launches": r["gpu_launches"],
+                     "accuracy": r["accuracy"], "re_within_1e_3_of_oracle": r["re_within_1e_3_of_oracle"],
+                     "re_within_1e_5_of_oracle": r["re_within_1e_5_of_oracle"]} for p, r in res.items()}
+    del P
+    torch.cuda.empty_cache()
+
+    # ---- secondary workloads
+    secondary = {}
+    if not args.no_secondary:
+        for name in ("cube400", "quartic96", "fp64cube100"):
+            try:
+                Wn = WORKLOADS[name]
+                Pn, rn = b.workload_line(name, Wn.get("forms", forms), max(3, args.steps // 2))
+                okn = [p for p in rn if rn[p]["re_within_1e_3_of_oracle"]] or list(rn)
+                hn = max(okn, key=lambda p: rn[p]["value"])
+                secondary[name] = {
+                    "workload": Wn["desc"], "headline_form": hn, "value": rn[hn]["value"], "unit": "decomps/s",
+                    "distinct_tensors": Pn["distinct"], "slots": len(Pn["slots"]),
+                    "oracle_decomps_per_s": len(Pn["oracle"]) / Pn["oracle_seconds"],
+                    "forms": {p: {"value": r["value"], "ms_per_step": r["ms"] / max(3, args.steps // 2),
+                                  "accuracy": r["accuracy"], "re_within_1e_3_of_oracle": r["re_within_1e_3_of_oracle"],
+                                  "re_within_1e_5_of_oracle": r["re_within_1e_5_of_oracle"]} for p, r in rn.items()}}
+                if name == "cube400":
+                    # randomized T-HOSVD (Algorithm 1) of the low-rank tensors in the headline form
+                    low = [A for v, A in Pn["slots"] if v["gen"] == "lowrank"]
+                    tb = tk.Batch([dict(which="T", A=A, dims=Wn["dims"], ranks=Wn["ranks"], P=Wn["P"], q=1, c=0,
+                                        prob="uniform", seed=SEED + k) for k, A in enumerate(low + low)], prec=hn)
+                    for _ in range(args.warmup):
+                        tb.run(stream=b.main_s, sync=False)
+                    tb.run(stream=b.main_s)
+                    ts = max(3, args.steps // 4)
+                    b.barrier()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(b.main_s)
+                    for _ in range(ts):
+                        tb.run(stream=b.main_s, sync=False)
+                    e1.record(b.main_s)
+                    b.main_s.synchronize()
+                    b.barrier()
+                    secondary["thosvd400"] = {
+                        "value": whole_job_rate(2 * len(low) * ts, world, b.max_over_ranks(e0.elapsed_time(e1)) / 1e3),
+                        "unit": "decomps/s", "prec": hn,
+                        "workload": f"randomized T-HOSVD of {len(low)} distinct 400^3 low-rank tensors (each twice, "
+                                    f"different seeds), R=20 P=10 q=1, one tucker_batch_run call per step"}
+                    del tb
+                del Pn
+                torch.cuda.empty_cache()
+            except Exception as exc:  # noqa: BLE001
+                secondary[name] = {"error": str(exc)[:300]}
+
+    serving = None
+    if not args.no_serving:
+        try:
+            reqs = serving_requests(torch)
+            serving = {p: serving_bench(tk, torch, reqs, p) for p in dict.fromkeys([head, "fp32"]) if p in forms}
+            serving["sample"] = (f"{len(reqs)} randomized ST-HOSVD requests (P=5, q=1), orders 3/4, extents "
+                                 f"U{{32..256}} (order 3) / U{{32..96}} (order 4), ranks U{{4..32}}, low-rank + 1e-2 "
+                                 f"noise, device-resident; budget {SERVE_BUDGET >> 30} GB, 16 streams; latencies at "
+                                 f"0.7x the saturation throughput, Poisson arrivals")
+            del reqs
+        except Exception as exc:  # noqa: BLE001
+            serving = {"error": str(exc)[:300]}
+    clk = b.clocks.stop()
+
+    line = {"metric": "decomps/s", "value": res[head]["value"], "unit": "decomps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res[head]["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "baseline_metric": BASELINE_METRIC,
-            "config": {"workload": WORKLOAD, "tensor_bytes": 256_000_000,
-                       "l2": "inputs larger than L2 (256 MB per tensor), no flush",
+            "config": {"workload": W["desc"], "headline_form": head, "slots_per_step": len(W["variants"]) * W["copies"],
+                       "tensor_bytes": int(np.prod(W["dims"])) * 4,
+                       "l2": "inputs larger than L2 (2.15 GB per tensor), no flush",
                        "parallelism": "replicas (each rank decomposes its own batch)" if world > 1 else "single GPU",
-                       "sketch": f"paper form, {head['prec']} power steps "
-                                 + {"bf16x1": "(tcgen05 single-pass bf16 on mode 1, split bf16 on modes 2-3, "
-                                              "fp32 accumulate; mode-1 product split bf16 on tcgen05)",
-                                    "tf32": "(tcgen05 kind::tf32 on mode 1, split bf16 on modes 2-3, fp32 "
-                                            "accumulate; mode-1 product split bf16 on tcgen05)",
-                                    "bf16": "(tcgen05 split bf16, fp32 accumulate; mode-1 product split bf16 "
-                                            "on tcgen05)",
-                                    "fp32": "(FP32 FFMA; exact FP32 mode products)"}[head["prec"]],
                        "execution": f"tucker_batch_run per step: one CUDA graph (captured by the library on its "
-                                    f"first run, replayed after) of {len(batch)} decompositions ({args.copies} of "
-                                    f"each variant, inputs shared read-only) on {len(batch)} streams",
+                                    f"first run, replayed after) of {len(W['variants']) * W['copies']} "
+                                    f"decompositions on as many streams, distinct inputs (one tensor per slot)",
+                       "headline_rule": "fastest form whose relative error is within 1e-3 of the FP64 oracle's on "
+                                        "every variant (oracle on the same bytes, this run)",
                        "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")},
-            "e2e": e2e, "gpu_launches": head["gpu_launches"], "roofline": roofline, "kernels": kernels,
+            "e2e": e2e, "gpu_launches": res[head]["gpu_launches"], "roofline": roofline, "kernels": kernels,
             "sketch_hbm_gbs": achieved_gbs,
-            "forms": {p: {"value": f["value"], "ms_per_step": f["ms"] / args.steps, "rel_error": f["rel_error"]}
-                      for p, f in forms.items()},
-            "matches_fp32_rel_err_within_1e-3": equal,
+            "forms": head_line,
+            "secondary": secondary,
             "serving": serving,
-            "thosvd": thosvd,
             "autotune": tk.autotune_entries(),
             "clocks": clk}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(host)
+    if cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline
+        line["cpu_baseline_1thread"] = oracle_one_thread(HEADLINE, W["variants"][0]["name"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
