@@ -102,7 +102,8 @@ _RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int6
              "tucker_last_cuda_error": C.c_char_p, "tucker_autotune_count": C.c_int64,
              "tucker_autotune_entry": C.c_char_p}
 KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3, "extract": 4, "sample": 5, "power_bf16": 6,
-                  "power_tf32": 7, "ttm_bf16": 8, "power_bf16x1": 9}
+                  "power_tf32": 7, "ttm_bf16": 8, "power_bf16x1": 9, "ttm_wide": 10, "power_wide1": 11,
+                  "power_wide2": 12, "range_wide": 13}
 
 
 def lib():
@@ -356,10 +357,12 @@ def power_step(A, dims, mode, X, stream=None, prec="fp32"):
     return out
 
 
-def range_sketch(A, dims, mode, L, seed, stream=None):
+def range_sketch(A, dims, mode, L, seed, stream=None, prec="fp32"):
+    """Y = A_(n) Omega, Omega J_n x L Gaussian from the Philox stream; prec other
+    than "fp32" runs it on the tensor cores (contiguous fibers)."""
     dims = _view(A, dims, mode)
     out = factor_tensor(dims[mode], L, A.dtype, A.device)
-    o = make_opts(stream=stream)
+    o = make_opts(stream=stream, prec=prec)
     _check("tucker_range_sketch", lib().tucker_range_sketch(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode, L,
                                                             C.c_uint64(seed), out.data_ptr(), C.byref(o)))
     return out

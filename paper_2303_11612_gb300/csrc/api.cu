@@ -112,6 +112,9 @@ struct ModePlan {
     bool tc;           // power steps on the tensor cores (split-bf16 operands)
     bool tf32;         // power steps on the tensor cores (tf32 operands, contiguous fibers)
     bool bf16x1;       // power steps on the tensor cores (single-pass bf16 operands, contiguous fibers)
+    bool wide;         // power steps as two tensor-core passes (contiguous fibers beyond the fused tiles)
+    bool wide_split;   //   with split-bf16 operands (else single-pass bf16)
+    bool wide_range;   // range form: first pass Y = A Omega on the tensor cores, Omega generated in-kernel
     PowerPlan pp;
     OrthPlan op;
 };
@@ -170,6 +173,19 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         mp.tc = o.prec != TUCKER_SK_FP32 && elem == 4 && power_tc_supported(mp.mv, mp.L);
         if (mp.tc || mp.tf32 || mp.bf16x1)
             p.max_partials = std::max(p.max_partials, power_tc_partials_bytes(mp.mv, mp.L, sms));
+        // beyond the fused kernels' tiles (I_n > 512 or wide sketches, contiguous fibers or
+        // the gathered AMM sample): two tensor-core passes, single-pass bf16 where the
+        // form sketches in single-pass BF16, split bf16 elsewhere
+        mp.wide_split = !(o.prec == TUCKER_SK_BF16X1 && (!st || n == 0));
+        mp.wide = o.prec != TUCKER_SK_FP32 && elem == 4 && !mp.tc && !mp.tf32 && !mp.bf16x1 &&
+                  wide_supported(mp.mv, mp.L);
+        mp.wide_range = o.form == TUCKER_FORM_RANGE && o.prec != TUCKER_SK_FP32 && elem == 4 &&
+                        wide_supported(mp.mv, mp.L);
+        if (mp.wide || mp.wide_range)
+            p.max_partials = std::max(p.max_partials, wide_power_scratch_bytes(mp.mv, mp.L, sms));
+        if (o.prec != TUCKER_SK_FP32 && elem == 4 && st && !ttm_tc_supported(mp.v, mp.R) &&
+            wide_supported(mp.v, mp.R))
+            p.max_partials = std::max(p.max_partials, wide_ttm_scratch_bytes(mp.v, mp.R));
         mp.op = orth_plan(d[n], mp.L, sms);
         if (!orth_supported(mp.op, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
         p.maxI = std::max(p.maxI, d[n]);
@@ -185,7 +201,12 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
     if (!st) {
         int64_t e[kMaxOrder];
         for (int n = 0; n < N; ++n) e[n] = dims[n];
-        for (int n = 0; n < N - 1; ++n) {
+        for (int n = 0; n < N; ++n) {
+            const ModeView tv = view_of(e, N, n);
+            if (o.prec != TUCKER_SK_FP32 && elem == 4 && !ttm_tc_supported(tv, ranks[n]) &&
+                wide_supported(tv, ranks[n]))
+                p.max_partials = std::max(p.max_partials, wide_ttm_scratch_bytes(tv, ranks[n]));
+            if (n == N - 1) break;
             e[n] = ranks[n];
             p.inter_elems = std::max(p.inter_elems, prod(e, N));
         }
@@ -251,6 +272,11 @@ cudaError_t power_step(const T* M, const ModePlan& mp, const T* X_in, T* X_out, 
         }
         if (mp.tc)
             return launch_power_tc(M, mp.mv, X_in, mp.L, X_out, w.partials, w.status, num_sms(), s);
+        if (mp.wide) {
+            const cudaError_t e = launch_power_wide(M, mp.mv, X_in, mp.L, X_out, mp.wide_split, false, 0, 0,
+                                                    w.partials, w.status, num_sms(), s);
+            if (e != cudaErrorNotSupported) return e;
+        }
     }
     return launch_power<T>(M, mp.mv, X_in, mp.L, X_out, w.partials, mp.pp, false, 0, 0, s);
 }
@@ -291,7 +317,15 @@ cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, 
         ProfScope prof(kKExtract, 0.0, 0.0, s);
         return launch_extract<T>(X1, Q, mp.op, w.factors, q - 1, mp.R, U, w.orth, w.status, s);
     }
-    TK_TRY(launch_power<T>(M, mp.mv, nullptr, L, X1, w.partials, mp.pp, true, seed, stream_id(0, n), s));
+    cudaError_t first = cudaErrorNotSupported;
+    if constexpr (sizeof(T) == 4) {
+        if (mp.wide_range)
+            first = launch_power_wide(M, mp.mv, nullptr, L, X1, mp.wide_split, true, seed, stream_id(0, n),
+                                      w.partials, w.status, num_sms(), s);
+    }
+    if (first == cudaErrorNotSupported)
+        first = launch_power<T>(M, mp.mv, nullptr, L, X1, w.partials, mp.pp, true, seed, stream_id(0, n), s);
+    TK_TRY(first);
     for (int k = 0; k < q; ++k) {
         TK_TRY(launch_cholqr<T>(X1, Q, mp.op, w.factors, w.orth, w.status, s));
         TK_TRY(power_step<T>(M, mp, Q, X1, w, s));
@@ -307,7 +341,9 @@ cudaError_t mode_product(const Plan& p, const T* A, const ModeView& v, const T* 
                          const Work& w, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (p.prec != TUCKER_SK_FP32) {
-            const cudaError_t e = launch_ttm_tc(A, v, U, K, 1, v.i, out, w.status, num_sms(), s);
+            cudaError_t e = launch_ttm_tc(A, v, U, K, 1, v.i, out, w.status, num_sms(), s);
+            if (e == cudaErrorNotSupported && wide_supported(v, K))
+                e = launch_ttm_wide(A, v, U, K, 1, v.i, out, w.partials, w.status, num_sms(), s);
             if (e != cudaErrorNotSupported) return e;
         }
     }
@@ -573,12 +609,18 @@ tucker_status tucker_plan_describe(int which, tucker_dtype dt, const int64_t* di
                             : mp.tf32   ? "tf32"
                             : mp.bf16x1 ? "bf16x1"
                             : mp.tc     ? "split-bf16"
+                            : mp.wide   ? (mp.wide_split ? "wide-split-bf16" : "wide-bf16x1")
                                         : "fp32";
         const ModeView tv = p.st ? mp.v : view_of(e, N, n);
-        const char* ttm = p.elem == 8 ? "fp64"
-                          : (p.prec != TUCKER_SK_FP32 && ttm_tc_supported(tv, ranks[n])) ? "split-bf16"
-                                                                                         : "fp32";
-        const char* range = p.form != TUCKER_FORM_RANGE ? "" : p.elem == 8 ? " range-sketch=fp64" : " range-sketch=fp32";
+        const bool tc_ttm = p.elem == 4 && p.prec != TUCKER_SK_FP32;
+        const char* ttm = p.elem == 8                                       ? "fp64"
+                          : (tc_ttm && ttm_tc_supported(tv, ranks[n]))     ? "split-bf16"
+                          : (tc_ttm && wide_supported(tv, ranks[n]))       ? "wide-split-bf16"
+                                                                           : "fp32";
+        const char* range = p.form != TUCKER_FORM_RANGE ? ""
+                            : p.elem == 8               ? " range-sketch=fp64"
+                            : mp.wide_range ? (mp.wide_split ? " range-sketch=wide-split-bf16" : " range-sketch=wide-bf16x1")
+                                            : " range-sketch=fp32";
         char line[256];
         snprintf(line, sizeof(line), "mode %d: I=%lld L=%d J=%lld T=%lld sketch=%s power=%s ttm=%s%s\n", n,
                  (long long)mp.v.i, mp.L, (long long)mp.v.fibers(), (long long)mp.T,
@@ -641,6 +683,23 @@ tucker_status tucker_power_step(const void* A, tucker_dtype dt, const int64_t* d
     const int elem = dt == TUCKER_F64 ? 8 : 4;
     if (v.i > kMaxI || L > 4096 || (elem == 8 && v.i > 512)) return TUCKER_ERR_UNSUPPORTED;
     const PowerPlan pp = power_plan(v, (int)L, elem, num_sms());
+    if (o.prec != TUCKER_SK_FP32 && elem == 4 && wide_supported(v, L) &&
+        !(o.prec == TUCKER_SK_TF32 ? power_tf32_supported(v, (int)L)
+          : o.prec == TUCKER_SK_BF16X1 ? power_bf16x1_supported(v, (int)L)
+                                       : power_tc_supported(v, (int)L))) {
+        // beyond the fused kernels' tiles: two tensor-core passes
+        Scratch sc;
+        if ((rs = sc.get(wide_power_scratch_bytes(v, (int)L, num_sms()) + 256, o.stream)) != TUCKER_OK) return rs;
+        int* status = reinterpret_cast<int*>(sc.p);
+        cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
+        if (e == cudaSuccess)
+            e = launch_power_wide((const float*)A, v, (const float*)X_in, (int)L, (float*)X_out,
+                                  o.prec != TUCKER_SK_BF16X1, false, 0, 0, reinterpret_cast<char*>(sc.p) + 256,
+                                  status, num_sms(), o.stream);
+        if (e == cudaErrorNotSupported) return TUCKER_ERR_UNSUPPORTED;
+        if (e != cudaSuccess) return from_cuda(e);
+        return sync_status(o.stream, status);
+    }
     if (o.prec == TUCKER_SK_TF32 || o.prec == TUCKER_SK_BF16X1) {
         const bool tf = o.prec == TUCKER_SK_TF32;
         if (elem != 4 || !(tf ? power_tf32_supported(v, (int)L) : power_bf16x1_supported(v, (int)L)))
@@ -689,10 +748,24 @@ tucker_status tucker_range_sketch(const void* A, tucker_dtype dt, const int64_t*
     const ModeView v = view_of(dims, N, mode);
     const int elem = dt == TUCKER_F64 ? 8 : 4;
     if (v.i > kMaxI || L > 4096 || (elem == 8 && v.i > 512)) return TUCKER_ERR_UNSUPPORTED;
+    const uint32_t sid = stream_id(0, mode);
+    if (o.prec != TUCKER_SK_FP32) {
+        // Y = A_(n) Omega on the tensor cores, Omega generated inside the kernel
+        if (elem != 4 || !wide_supported(v, L)) return TUCKER_ERR_UNSUPPORTED;
+        Scratch sc;
+        if ((rs = sc.get(wide_power_scratch_bytes(v, (int)L, num_sms()) + 256, o.stream)) != TUCKER_OK) return rs;
+        int* status = reinterpret_cast<int*>(sc.p);
+        cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
+        if (e == cudaSuccess)
+            e = launch_power_wide((const float*)A, v, nullptr, (int)L, (float*)Y, o.prec != TUCKER_SK_BF16X1, true,
+                                  seed, sid, reinterpret_cast<char*>(sc.p) + 256, status, num_sms(), o.stream);
+        if (e == cudaErrorNotSupported) return TUCKER_ERR_UNSUPPORTED;
+        if (e != cudaSuccess) return from_cuda(e);
+        return sync_status(o.stream, status);
+    }
     const PowerPlan pp = power_plan(v, (int)L, elem, num_sms());
     Scratch sc;
     if ((rs = sc.get(power_partials_bytes(pp, v, (int)L, elem), o.stream)) != TUCKER_OK) return rs;
-    const uint32_t sid = stream_id(0, mode);
     cudaError_t e = elem == 4 ? launch_power<float>((const float*)A, v, nullptr, (int)L, (float*)Y, sc.p, pp, true,
                                                     seed, sid, o.stream)
                               : launch_power<double>((const double*)A, v, nullptr, (int)L, (double*)Y, sc.p, pp,
@@ -806,12 +879,16 @@ tucker_status tucker_ttm(const void* A, tucker_dtype dt, const int64_t* dims, in
     const int64_t ld_i = transpose ? 1 : K, ld_k = transpose ? v.i : 1;
     TuneAllow tune(true);
     Scratch sc;
-    if ((rs = sc.get(256, o.stream)) != TUCKER_OK) return rs;
+    const bool wide = o.prec != TUCKER_SK_FP32 && dt == TUCKER_F32 && !ttm_tc_supported(v, K) && wide_supported(v, K);
+    if ((rs = sc.get(256 + (wide ? wide_ttm_scratch_bytes(v, K) : 0), o.stream)) != TUCKER_OK) return rs;
     if (cudaMemsetAsync(sc.p, 0, sizeof(int), o.stream) != cudaSuccess) return from_cuda(cudaGetLastError());
     if (o.prec != TUCKER_SK_FP32) {
         if (dt != TUCKER_F32) return TUCKER_ERR_UNSUPPORTED;
-        const cudaError_t e = launch_ttm_tc((const float*)A, v, (const float*)M_ptr, K, ld_i, ld_k, (float*)out,
-                                            (int*)sc.p, num_sms(), o.stream);
+        const cudaError_t e =
+            wide ? launch_ttm_wide((const float*)A, v, (const float*)M_ptr, K, ld_i, ld_k, (float*)out,
+                                   reinterpret_cast<char*>(sc.p) + 256, (int*)sc.p, num_sms(), o.stream)
+                 : launch_ttm_tc((const float*)A, v, (const float*)M_ptr, K, ld_i, ld_k, (float*)out, (int*)sc.p,
+                                 num_sms(), o.stream);
         if (e == cudaErrorNotSupported) return TUCKER_ERR_UNSUPPORTED;
         if (e != cudaSuccess) return from_cuda(e);
         return sync_status(o.stream, (const int*)sc.p);

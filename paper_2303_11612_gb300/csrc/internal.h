@@ -79,6 +79,22 @@ bool ttm_tc_supported(const ModeView& v, int64_t K_out);
 cudaError_t launch_ttm_tc(const float* A, const ModeView& v, const float* Mp, int64_t K_out, int64_t ld_i,
                           int64_t ld_k, float* out, int* status, int num_sms, cudaStream_t s);
 
+// ---- tensor-core passes for contiguous fibers at large shapes (kernels_wide.cu):
+// I_n % 4 == 0, columns (L or K_out) <= 128. Return cudaErrorNotSupported (nothing
+// launched) outside wide_supported or when A is not 16-byte aligned.
+bool wide_supported(const ModeView& v, int64_t cols);
+size_t wide_ttm_scratch_bytes(const ModeView& v, int64_t K_out);
+size_t wide_power_scratch_bytes(const ModeView& v, int L, int num_sms);
+// out = A x_n M (split bf16, FP32 accumulate), out[j K_out + o] as launch_ttm.
+cudaError_t launch_ttm_wide(const float* A, const ModeView& v, const float* Mp, int64_t K_out, int64_t ld_i,
+                            int64_t ld_k, float* out, void* scratch, int* status, int num_sms, cudaStream_t s);
+// X_out = A_(n) (A_(n)^T X_in) in two passes (range == false), or Y = A_(n) Omega
+// with Omega J_n x L from the Philox stream (range == true, X_in unused); split:
+// split-bf16 operands, else single-pass bf16.
+cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_in, int L, float* X_out, bool split,
+                              bool range, uint64_t seed, uint32_t stream_id, void* scratch, int* status, int num_sms,
+                              cudaStream_t s);
+
 // ---- sampling (kernels_amm.cu)
 template <typename T>
 cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStream_t s);
@@ -136,7 +152,8 @@ tucker_status status_from_cuda(cudaError_t e);
 
 // ---- launch counting and profiling (profile.cu)
 enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKExtract = 4, kKSample = 5,
-                   kKPowerBf16 = 6, kKPowerTf32 = 7, kKTtmBf16 = 8, kKPowerBf16x1 = 9, kKernelClasses = 10 };
+                   kKPowerBf16 = 6, kKPowerTf32 = 7, kKTtmBf16 = 8, kKPowerBf16x1 = 9, kKTtmWide = 10,
+                   kKPowerWide1 = 11, kKPowerWide2 = 12, kKRangeWide = 13, kKernelClasses = 14 };
 void note_launch();
 void note_launches(int64_t n);   // a graph replay's kernels
 void profile_drain();

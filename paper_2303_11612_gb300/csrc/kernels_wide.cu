@@ -1,0 +1,797 @@
+// Tensor-core kernels for contiguous mode-n fibers (mode 1) at shapes beyond
+// the tiles of the fused kernels: extents I_n in the thousands and sketch widths
+// or output ranks up to 128 (the 1024 x 1024 x 512 workload's mode 1 has
+// I_1 = 1024, L_1 = 80, R_1 = 64). tcgen05 kind::f16 with FP32 accumulation in
+// tensor memory; operands are bf16, either the single rounding of each FP32
+// value (the single-pass BF16 form) or its split a = a_hi + a_lo with the three
+// products hi.hi + lo.hi + hi.lo (about 2^-16 relative, the FP32-class forms).
+//
+// Two contractions, each a plain streaming pass over the tensor:
+//
+//   wide_ttm_kernel     D[j, o] = sum_i A_(n)[i, j] M[i, o]     (contracts I_n)
+//     Tiles of 128 fibers (M of the product, one fiber per accumulator lane),
+//     units of 64 values i. TMA loads a unit as two FP32 boxes (128-byte
+//     swizzled); sixteen converter warps round or split it into the K-major
+//     swizzled bf16 operand; M^T, prepared once per call as a swizzled bf16
+//     image in global memory (image_kernel), streams through a small ring
+//     by untiled bulk copies, one unit beside each tensor unit (at I_n = 1024
+//     the whole M^T does not fit in shared memory beside the rings). N = K_out
+//     padded to 16; the accumulator is double-buffered so a tile's read-back
+//     overlaps the next tile's products. Outputs: the mode-n product (FP32,
+//     fiber-major: out[j K_out + o], the truncation B x_n U^T of Algorithm 2),
+//     or W = A_(n)^T X as the bf16 operand image wide_power2_kernel reads.
+//
+//   wide_power2_kernel  P[i, l] = sum_j A_(n)[i, j] B[j, l]     (contracts J_n)
+//     B = W from the kernel above (second half of a power step of Strategy A,
+//     X_out = A_(n) W), or the range form's Gaussian Omega (J_n x L), generated
+//     per 64-fiber chunk from the Philox stream inside the kernel, so that it
+//     never touches HBM. A CTA owns up to 4 blocks of 128 rows i (its row group)
+//     and a strided set of 64-fiber chunks; its accumulators (rows on lanes, L
+//     padded to 16 columns per block) stay in tensor memory across its chunks
+//     and are written once as its partial; partials are summed in a fixed order
+//     afterwards. TMA loads a 128-row x 64-fiber unit as four FP32 boxes; eight
+//     converter warps write it in the no-swizzle core-matrix layout with i
+//     contiguous (the MN-major A operand), B arrives by bulk copy (or is
+//     generated) in the same layout with l contiguous (MN-major B).
+//
+// A power step is therefore two passes over the tensor (W is written between
+// them, 2 x L bytes per fiber per part) instead of the fused single pass of
+// kernels_bf16x1.cu / kernels_tc.cu, whose tiles stop at I_n = 512 and L <= 64:
+// an I_n x L FP32 accumulator of 1024 x 80 needs 320 KB of tensor memory, more
+// than one SM has (256 KB), so here the rows are split over CTAs instead.
+//
+// Every mbarrier wait is bounded: on a timeout the kernel records kStatTimeout,
+// lets the copies and products it issued finish (with the same bound), frees its
+// tensor memory and returns.
+#include <algorithm>
+#include <climits>
+
+#include "internal.h"
+#include "tc.cuh"
+#include "tma.cuh"
+
+namespace tk {
+namespace {
+
+constexpr int kWWaitIters = 1 << 22;
+constexpr size_t kWSmemMax = 227 * 1024;
+
+__device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, volatile int* flag) {
+    for (int it = 0; it < kWWaitIters; ++it) {
+        if (tc::mbar_try(b, parity)) return true;
+        if ((it & 255) == 255 && *flag) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fail(volatile int* flag, int* status) {
+    *flag = 1;
+    set_status(status, kStatTimeout);
+}
+
+__device__ __forceinline__ void drain(uint64_t* b, uint32_t parity) {
+    for (int it = 0; it < kWWaitIters; ++it)
+        if (tc::mbar_try(b, parity)) break;
+}
+
+__device__ __forceinline__ uint32_t bf2(float a, float b) {
+    __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&p);
+}
+
+// Eight FP32 values -> bf16 (round to nearest), and for SPLIT the bf16 of the
+// remainders x - bf16(x) (exact in FP32).
+template <bool SPLIT>
+__device__ __forceinline__ void cvt8(const float (&x)[8], uint4& hi, uint4& lo) {
+    hi = make_uint4(bf2(x[0], x[1]), bf2(x[2], x[3]), bf2(x[4], x[5]), bf2(x[6], x[7]));
+    if (SPLIT) {
+        const uint32_t h[4] = {hi.x, hi.y, hi.z, hi.w};
+        uint32_t l[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            l[k] = bf2(x[2 * k] - __uint_as_float(h[k] << 16), x[2 * k + 1] - __uint_as_float(h[k] & 0xFFFF0000u));
+        lo = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// ------------------------------------------------------------------ M^T image
+// K-major swizzled bf16 image of M^T (M(i, o) = Mp[i ld_i + o ld_k]) for the B
+// operand of wide_ttm_kernel: unit u (values i = 64 u ..), part p (hi, lo), row o
+// at u * ubytes + p * Np * 128 + (o / 8) 1024 + (o % 8) 128, its 16-byte group q
+// (values 64 u + 8 q .. + 7) at group position q ^ (o % 8); zero beyond K_out, I.
+template <bool SPLIT>
+__global__ void image_kernel(const float* __restrict__ Mp, int I, int K_out, int64_t ld_i, int64_t ld_k, int Np,
+                             int nu, unsigned char* __restrict__ img) {
+    const int parts = SPLIT ? 2 : 1;
+    const size_t ubytes = (size_t)parts * Np * 128;
+    const int64_t total = (int64_t)nu * Np * 8;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int u = (int)(e / (Np * 8));
+        const int rem = (int)(e - (int64_t)u * Np * 8);
+        const int o = rem >> 3, q = rem & 7;
+        float x[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int i = 64 * u + 8 * q + w;
+            x[w] = (o < K_out && i < I) ? __ldg(Mp + (int64_t)i * ld_i + (int64_t)o * ld_k) : 0.f;
+        }
+        uint4 hi, lo;
+        cvt8<SPLIT>(x, hi, lo);
+        unsigned char* row = img + (size_t)u * ubytes + (o >> 3) * 1024 + (o & 7) * 128 + ((q ^ (o & 7)) << 4);
+        *reinterpret_cast<uint4*>(row) = hi;
+        if (SPLIT) *reinterpret_cast<uint4*>(row + (size_t)Np * 128) = lo;
+    }
+}
+
+// ------------------------------------------------------------------ wide_ttm_kernel
+constexpr int kAJB = 128;                  // fibers per tile
+constexpr int kABox = kAJB * 128;          // FP32 box: 32 values i x 128 fibers = 16 KB
+constexpr int kAUnit = 2 * kABox;          // FP32 unit: 64 values i
+constexpr int kAHalf = kAJB * 128;         // one bf16 part of a unit: 64 values i x 128 fibers
+constexpr int kAFStages = 3;
+constexpr int kACStages = 2;
+constexpr int kAUStages = 2;
+constexpr int kAConv = 16;                 // converter warps 2 .. 17
+constexpr int kAEpi = 4;                   // read-back warps 18 .. 21
+constexpr int kAThreads = 64 + 32 * kAConv + 32 * kAEpi;
+constexpr int kABars = 2 * kAFStages + 2 * kACStages + 2 * kAUStages + 5;
+static_assert(kABars * 8 + 8 <= 256, "barrier area");
+
+struct WideALayout {
+    int nu = 0, Np = 0, parts = 1;
+    size_t ubytes = 0, c_off = 0, u_off = 0, bar_off = 0, bytes = 0;
+    uint32_t tmem_cols = 0;
+};
+
+WideALayout wide_a_layout(int I, int K_out, bool split) {
+    WideALayout t;
+    t.nu = (I + 63) / 64;
+    t.Np = (K_out + 15) / 16 * 16;
+    t.parts = split ? 2 : 1;
+    t.ubytes = (size_t)t.parts * t.Np * 128;
+    t.c_off = (size_t)kAFStages * kAUnit;
+    t.u_off = t.c_off + (size_t)kACStages * t.parts * kAHalf;
+    t.bar_off = t.u_off + (size_t)kAUStages * t.ubytes;
+    t.bytes = t.bar_off + 256 + 1024;
+    uint32_t c = 32;
+    while (c < (uint32_t)(2 * t.Np)) c <<= 1;
+    t.tmem_cols = c;
+    return t;
+}
+
+// OUT 0: out[j K_out + o] (FP32). OUT 1: W image for wide_power2_kernel's B
+// operand: 64-fiber chunk c = j / 64 at c * Np * 128 bytes of each part's array,
+// element (l, jj = j % 64) at (jj / 8) (Np / 8) 128 + (l / 8) 128 + (jj % 8) 16 +
+// (l % 8) 2 (core matrices of 8 fibers x 8 columns, columns contiguous).
+template <bool SPLIT, int OUT>
+__global__ void __launch_bounds__(kAThreads, 1)
+    wide_ttm_kernel(const __grid_constant__ CUtensorMap map, int I, int64_t J, const unsigned char* __restrict__ uimg,
+                    int K_out, int Np, float* __restrict__ out, unsigned char* __restrict__ w_hi,
+                    unsigned char* __restrict__ w_lo, int64_t tiles, int nu, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024 - (tma::smem_addr(smem_raw) & 1023)) & 1023);
+    constexpr int parts = SPLIT ? 2 : 1;
+    const uint32_t ubytes = (uint32_t)(parts * Np * 128);
+    unsigned char* F = smem;
+    unsigned char* Cb = smem + (size_t)kAFStages * kAUnit;
+    unsigned char* Us = Cb + (size_t)kACStages * parts * kAHalf;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Us + (size_t)kAUStages * ubytes);
+    uint64_t* f_full = bar;
+    uint64_t* f_empty = f_full + kAFStages;
+    uint64_t* c_full = f_empty + kAFStages;
+    uint64_t* c_empty = c_full + kACStages;
+    uint64_t* u_full = c_empty + kACStages;
+    uint64_t* u_empty = u_full + kAUStages;
+    uint64_t* d_full = u_empty + kAUStages;
+    uint64_t* d_empty = d_full + 2;
+    uint64_t* done = d_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t nloc = tiles > (int64_t)blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    uint32_t tcols = 32;
+    while (tcols < (uint32_t)(2 * Np)) tcols <<= 1;
+
+    if (tid == 0) {
+        for (int k = 0; k < kABars; ++k) tc::mbar_init(&bar[k], 1);
+        for (int k = 0; k < kAFStages; ++k) tc::mbar_init(&f_empty[k], kAConv);
+        for (int k = 0; k < kACStages; ++k) tc::mbar_init(&c_full[k], kAConv);
+        for (int k = 0; k < 2; ++k) tc::mbar_init(&d_empty[k], kAEpi);
+        *flag = 0;
+        tma::fence_barrier_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tmem_slot, tcols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int64_t g = 0;
+            bool ok = true;
+            for (int64_t k = 0; k < nloc && ok; ++k) {
+                const int j0 = (int)((blockIdx.x + k * gridDim.x) * kAJB);
+                for (int u = 0; u < nu; ++u, ++g) {
+                    const int fs = (int)(g % kAFStages), us = (int)(g % kAUStages);
+                    if ((g >= kAFStages && !wait_bar(&f_empty[fs], (uint32_t)((g / kAFStages - 1) & 1), flag)) ||
+                        (g >= kAUStages && !wait_bar(&u_empty[us], (uint32_t)((g / kAUStages - 1) & 1), flag))) {
+                        fail(flag, status);
+                        ok = false;
+                        break;
+                    }
+                    tma::expect_tx(&f_full[fs], (uint32_t)kAUnit);
+                    unsigned char* dst = F + (size_t)fs * kAUnit;
+                    // a box wholly beyond I_n loads zeros
+                    tma::load_2d(dst, &map, 64 * u, j0, &f_full[fs]);
+                    tma::load_2d(dst + kABox, &map, 64 * u + 32, j0, &f_full[fs]);
+                    tma::expect_tx(&u_full[us], ubytes);
+                    tma::bulk_load(Us + (size_t)us * ubytes, uimg + (size_t)u * ubytes, ubytes, &u_full[us]);
+                }
+            }
+            if (*flag) {
+                // the copies issued so far land before the kernel returns
+                const int64_t f0 = g > kAFStages ? g - kAFStages : 0;
+                for (int64_t gg = f0; gg < g; ++gg) drain(&f_full[gg % kAFStages], (uint32_t)((gg / kAFStages) & 1));
+                const int64_t u0 = g > kAUStages ? g - kAUStages : 0;
+                for (int64_t gg = u0; gg < g; ++gg) drain(&u_full[gg % kAUStages], (uint32_t)((gg / kAUStages) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id = tc::idesc_bf16(128, Np, false, false);
+            const uint64_t c_desc = tc::desc_sw128(tc::smem_u32(Cb), 16, 1024);
+            const uint64_t u_desc = tc::desc_sw128(tc::smem_u32(Us), 16, 1024);
+            const uint64_t lo_step = (uint64_t)(kAHalf >> 4), ulo_step = (uint64_t)((Np * 128) >> 4);
+            bool ok = true;
+            int64_t g = 0;
+            for (int64_t k = 0; k < nloc && ok; ++k) {
+                const int b = (int)(k & 1);
+                if (k >= 2 && !wait_bar(&d_empty[b], (uint32_t)(((k >> 1) - 1) & 1), flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)(b * Np);
+                for (int u = 0; u < nu; ++u, ++g) {
+                    const int cs = (int)(g % kACStages), us = (int)(g % kAUStages);
+                    if (!wait_bar(&c_full[cs], (uint32_t)((g / kACStages) & 1), flag) ||
+                        !wait_bar(&u_full[us], (uint32_t)((g / kAUStages) & 1), flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint64_t ahi = c_desc + (uint64_t)((cs * parts * kAHalf) >> 4);
+                    const uint64_t bhi = u_desc + (uint64_t)((us * ubytes) >> 4);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t s2 = (uint64_t)(ks * 2);
+                        tc::mma_bf16(d, ahi + s2, bhi + s2, id, u > 0 || ks > 0);
+                        if (SPLIT) {
+                            tc::mma_bf16(d, ahi + lo_step + s2, bhi + s2, id, true);
+                            tc::mma_bf16(d, ahi + s2, bhi + ulo_step + s2, id, true);
+                        }
+                    }
+                    tc::commit(&c_empty[cs]);
+                    tc::commit(&u_empty[us]);
+                }
+                if (!ok) break;
+                tc::commit(&d_full[b]);
+            }
+            tc::commit(done);
+            if (!ok) {
+                fail(flag, status);
+                drain(done, 0);
+            }
+        }
+    } else if (warp < 2 + kAConv) {
+        // conversion: task t = (fiber j, group p of 8 values i of the unit), two
+        // 16-byte pieces of FP32 box p / 4 in, one 16-byte piece per bf16 part out
+        const int ct = tid - 64;
+        bool ok = true;
+        int64_t g = 0;
+        constexpr int kTasks = (kAJB * 8) / (kAConv * 32);
+        for (int64_t k = 0; k < nloc && ok; ++k) {
+            for (int u = 0; u < nu; ++u, ++g) {
+                const int fs = (int)(g % kAFStages), cs = (int)(g % kACStages);
+                if (!wait_bar(&f_full[fs], (uint32_t)((g / kAFStages) & 1), flag)) {
+                    ok = false;
+                    break;
+                }
+                const unsigned char* src = F + (size_t)fs * kAUnit;
+                uint4 hi[kTasks], lo[kTasks];
+#pragma unroll
+                for (int r = 0; r < kTasks; ++r) {
+                    const int t = ct + kAConv * 32 * r;
+                    const int j = t >> 3, p = t & 7;
+                    const int q0 = (p & 3) * 2;
+                    const unsigned char* row = src + (p >> 2) * kABox + j * 128;
+                    const float4 a = *reinterpret_cast<const float4*>(row + ((q0 ^ (j & 7)) << 4));
+                    const float4 c = *reinterpret_cast<const float4*>(row + (((q0 + 1) ^ (j & 7)) << 4));
+                    const float x[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+                    cvt8<SPLIT>(x, hi[r], lo[r]);
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&f_empty[fs]);
+                if (g >= kACStages && !wait_bar(&c_empty[cs], (uint32_t)((g / kACStages - 1) & 1), flag)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* dhi = Cb + (size_t)cs * parts * kAHalf;
+#pragma unroll
+                for (int r = 0; r < kTasks; ++r) {
+                    const int t = ct + kAConv * 32 * r;
+                    const int j = t >> 3, p = t & 7;
+                    const int off = j * 128 + ((p ^ (j & 7)) << 4);
+                    *reinterpret_cast<uint4*>(dhi + off) = hi[r];
+                    if (SPLIT) *reinterpret_cast<uint4*>(dhi + kAHalf + off) = lo[r];
+                }
+                tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&c_full[cs]);
+            }
+        }
+        if (!ok) fail(flag, status);
+    } else {
+        // read-back: warp w reaches lanes 32 (w % 4) .. + 31 = fibers of the tile
+        const int quarter = warp & 3;
+        for (int64_t k = 0; k < nloc; ++k) {
+            const int b = (int)(k & 1);
+            if (!wait_bar(&d_full[b], (uint32_t)((k >> 1) & 1), flag)) {
+                if (!*flag) fail(flag, status);
+                break;
+            }
+            tc::fence_after_sync();
+            const int64_t j = (blockIdx.x + k * gridDim.x) * kAJB + quarter * 32 + lane;
+            const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * Np);
+            // the W image covers whole 64-fiber chunks: fibers J .. of the last one
+            // are written too (as zeros: their tensor columns load as zeros)
+            const int64_t jend = OUT == 0 ? J : (J + 63) / 64 * 64;
+            for (int c0 = 0; c0 < Np; c0 += 16) {
+                uint32_t r[16];
+                tc::tmem_ld16(ta + (uint32_t)c0, r);
+                if (j >= jend) continue;
+                if (OUT == 0) {
+                    float* o = out + j * K_out;
+                    if ((K_out & 3) == 0 && c0 + 16 <= K_out) {
+#pragma unroll
+                        for (int c = 0; c < 16; c += 4)
+                            *reinterpret_cast<float4*>(o + c0 + c) =
+                                make_float4(__uint_as_float(r[c]), __uint_as_float(r[c + 1]),
+                                            __uint_as_float(r[c + 2]), __uint_as_float(r[c + 3]));
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            if (c0 + c < K_out) o[c0 + c] = __uint_as_float(r[c]);
+                    }
+                } else {
+                    // columns l >= K_out of the accumulator are zero (M^T's image is)
+                    const int64_t ch = j >> 6;
+                    const int jj = (int)(j & 63);
+                    const size_t base = (size_t)ch * Np * 128 + (size_t)(jj >> 3) * (Np / 8) * 128 + (jj & 7) * 16;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float x[8];
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) x[w] = __uint_as_float(r[8 * h + w]);
+                        uint4 hi, lo;
+                        cvt8<SPLIT>(x, hi, lo);
+                        const size_t off = base + (size_t)((c0 + 8 * h) >> 3) * 128;
+                        *reinterpret_cast<uint4*>(w_hi + off) = hi;
+                        if (SPLIT) *reinterpret_cast<uint4*>(w_lo + off) = lo;
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&d_empty[b]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, tcols);
+}
+
+// ------------------------------------------------------------------ wide_power2_kernel
+constexpr int kBJB = 64;                   // fibers per chunk (K of the product)
+constexpr int kBBox = kBJB * 128;          // FP32 box: 32 values i x 64 fibers = 8 KB
+constexpr int kBUnit = 4 * kBBox;          // FP32 unit: 128 rows i x 64 fibers = 32 KB
+constexpr int kBHalf = 128 * kBJB * 2;     // one bf16 part of a unit: 16 KB
+constexpr int kBFStages = 3;
+constexpr int kBCStages = 2;
+constexpr int kBWStages = 2;
+constexpr int kBConv = 8;                  // converter (and generator, read-back) warps 2 .. 9
+constexpr int kBThreads = 64 + 32 * kBConv;
+constexpr int kBMaxBlocks = 4;             // 128-row blocks per CTA
+constexpr int kBTail = 20 * 1024;
+constexpr int kBBars = 2 * kBFStages + 2 * kBCStages + 2 * kBWStages + 1;
+static_assert(kBBars * 8 + 8 <= 256, "barrier area");
+
+struct WideBLayout {
+    int Np = 0, parts = 1, nb = 0, groups = 0;
+    size_t wbytes = 0, c_off = 0, w_off = 0, bar_off = 0, bytes = 0;
+};
+
+WideBLayout wide_b_layout(int I, int L, bool split) {
+    WideBLayout t;
+    t.Np = (L + 15) / 16 * 16;
+    t.parts = split ? 2 : 1;
+    const int blocks = (I + 127) / 128;
+    t.nb = std::min(kBMaxBlocks, std::min(blocks, 512 / t.Np));
+    t.groups = (blocks + t.nb - 1) / t.nb;
+    t.wbytes = (size_t)t.parts * t.Np * 128;
+    t.c_off = (size_t)kBFStages * kBUnit;
+    t.w_off = t.c_off + (size_t)kBCStages * t.parts * kBHalf;
+    t.bar_off = t.w_off + (size_t)kBWStages * t.wbytes;
+    // the tail keeps every operand read of the descriptors inside the allocation
+    // even for the largest strides the layout could be read with
+    t.bytes = t.bar_off + 256 + 1024 + kBTail;
+    return t;
+}
+
+// partial[r (I L) + l I + i] = sum over the CTA's chunks of A_(n)[i, j] B[j, l]
+// for the rows of its group; r = blockIdx.x / groups.
+template <bool SPLIT, bool RANGE>
+__global__ void __launch_bounds__(kBThreads, 1)
+    wide_power2_kernel(const __grid_constant__ CUtensorMap map, int I, int64_t J, int L, int Np,
+                       const unsigned char* __restrict__ w_hi, const unsigned char* __restrict__ w_lo, uint64_t seed,
+                       uint32_t stream_id, float* __restrict__ partial, int groups, int nb, int64_t chunks,
+                       int* status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024 - (tma::smem_addr(smem_raw) & 1023)) & 1023);
+    constexpr int parts = SPLIT ? 2 : 1;
+    const uint32_t wbytes = (uint32_t)(parts * Np * 128);
+    unsigned char* F = smem;
+    unsigned char* Cb = smem + (size_t)kBFStages * kBUnit;
+    unsigned char* Ws = Cb + (size_t)kBCStages * parts * kBHalf;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Ws + (size_t)kBWStages * wbytes);
+    uint64_t* f_full = bar;
+    uint64_t* f_empty = f_full + kBFStages;
+    uint64_t* c_full = f_empty + kBFStages;
+    uint64_t* c_empty = c_full + kBCStages;
+    uint64_t* w_full = c_empty + kBCStages;
+    uint64_t* w_empty = w_full + kBWStages;
+    uint64_t* done = w_empty + kBWStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = (int)(blockIdx.x % groups);
+    const int64_t r = blockIdx.x / groups, R = gridDim.x / groups;
+    const int64_t nloc = chunks > r ? (chunks - 1 - r) / R + 1 : 0;
+    const int blocks_total = (I + 127) / 128;
+    const int nbg = min(nb, blocks_total - grp * nb);     // row blocks of this CTA
+    const int row0 = grp * nb * 128;
+
+    if (tid == 0) {
+        for (int k = 0; k < kBBars; ++k) tc::mbar_init(&bar[k], 1);
+        for (int k = 0; k < kBFStages; ++k) tc::mbar_init(&f_empty[k], kBConv);
+        for (int k = 0; k < kBCStages; ++k) tc::mbar_init(&c_full[k], kBConv);
+        if (RANGE)
+            for (int k = 0; k < kBWStages; ++k) tc::mbar_init(&w_full[k], kBConv);
+        *flag = 0;
+        tma::fence_barrier_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int64_t g = 0, wc = 0;
+            bool ok = true;
+            for (int64_t kk = 0; kk < nloc && ok; ++kk) {
+                const int64_t ch = r + kk * R;
+                const int j0 = (int)(ch * kBJB);
+                if (!RANGE) {
+                    const int ws = (int)(wc % kBWStages);
+                    if (wc >= kBWStages && !wait_bar(&w_empty[ws], (uint32_t)((wc / kBWStages - 1) & 1), flag)) {
+                        fail(flag, status);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t pb = (uint32_t)(Np * 128);
+                    tma::expect_tx(&w_full[ws], wbytes);
+                    tma::bulk_load(Ws + (size_t)ws * wbytes, w_hi + (size_t)ch * pb, pb, &w_full[ws]);
+                    if (SPLIT) tma::bulk_load(Ws + (size_t)ws * wbytes + pb, w_lo + (size_t)ch * pb, pb, &w_full[ws]);
+                    ++wc;
+                }
+                for (int b = 0; b < nbg; ++b, ++g) {
+                    const int fs = (int)(g % kBFStages);
+                    if (g >= kBFStages && !wait_bar(&f_empty[fs], (uint32_t)((g / kBFStages - 1) & 1), flag)) {
+                        fail(flag, status);
+                        ok = false;
+                        break;
+                    }
+                    tma::expect_tx(&f_full[fs], (uint32_t)kBUnit);
+                    unsigned char* dst = F + (size_t)fs * kBUnit;
+                    const int i0 = row0 + b * 128;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) tma::load_2d(dst + s * kBBox, &map, i0 + 32 * s, j0, &f_full[fs]);
+                }
+            }
+            if (*flag) {
+                const int64_t f0 = g > kBFStages ? g - kBFStages : 0;
+                for (int64_t gg = f0; gg < g; ++gg) drain(&f_full[gg % kBFStages], (uint32_t)((gg / kBFStages) & 1));
+                if (!RANGE) {
+                    const int64_t w0 = wc > kBWStages ? wc - kBWStages : 0;
+                    for (int64_t gg = w0; gg < wc; ++gg)
+                        drain(&w_full[gg % kBWStages], (uint32_t)((gg / kBWStages) & 1));
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id = tc::idesc_bf16(128, Np, true, true);
+            // no-swizzle core matrices: A (rows i x 64 fibers) LBO = K step 2048, SBO = M step 128;
+            // B (64 fibers x Np columns) LBO = K step Np 16, SBO = N step 128
+            const uint64_t a_desc = tc::desc(tc::smem_u32(Cb), 2048, 128);
+            const uint64_t b_desc = tc::desc(tc::smem_u32(Ws), (uint32_t)(Np * 16), 128);
+            const uint64_t alo = (uint64_t)(kBHalf >> 4), blo = (uint64_t)((Np * 128) >> 4);
+            bool ok = true;
+            int64_t g = 0;
+            for (int64_t kk = 0; kk < nloc && ok; ++kk) {
+                const int ws = (int)(kk % kBWStages);
+                if (!wait_bar(&w_full[ws], (uint32_t)((kk / kBWStages) & 1), flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                for (int b = 0; b < nbg; ++b, ++g) {
+                    const int cs = (int)(g % kBCStages);
+                    if (!wait_bar(&c_full[cs], (uint32_t)((g / kBCStages) & 1), flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t d = tmem + (uint32_t)(b * Np);
+                    const uint64_t a0 = a_desc + (uint64_t)((cs * parts * kBHalf) >> 4);
+                    const uint64_t b0 = b_desc + (uint64_t)((ws * wbytes) >> 4);
+#pragma unroll
+                    for (int ks = 0; ks < kBJB / 16; ++ks) {
+                        const uint64_t sa = (uint64_t)((ks * 2 * 2048) >> 4), sb = (uint64_t)((ks * 2 * Np * 16) >> 4);
+                        tc::mma_bf16(d, a0 + sa, b0 + sb, id, kk > 0 || ks > 0);
+                        if (SPLIT) {
+                            tc::mma_bf16(d, a0 + alo + sa, b0 + sb, id, true);
+                            tc::mma_bf16(d, a0 + sa, b0 + blo + sb, id, true);
+                        }
+                    }
+                    tc::commit(&c_empty[cs]);
+                }
+                if (!ok) break;
+                tc::commit(&w_empty[ws]);
+            }
+            tc::commit(done);
+            if (!ok) {
+                fail(flag, status);
+                drain(done, 0);
+            }
+        }
+    } else {
+        const int ct = tid - 64;
+        bool ok = true;
+        int64_t g = 0;
+        constexpr int kTasks = (128 / 8) * kBJB / (kBConv * 32);   // 4
+        for (int64_t kk = 0; kk < nloc && ok; ++kk) {
+            const int64_t ch = r + kk * R;
+            if (RANGE) {
+                // Omega rows j of the chunk (Gaussian element j L + l of the stream),
+                // l contiguous in 16-byte groups of 8; zero for l >= L and j >= J
+                const int ws = (int)(kk % kBWStages);
+                if (kk >= kBWStages && !wait_bar(&w_empty[ws], (uint32_t)((kk / kBWStages - 1) & 1), flag)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* dst = Ws + (size_t)ws * wbytes;
+                const int ng = Np / 8;
+                for (int t = ct; t < kBJB * ng; t += kBConv * 32) {
+                    const int jj = t % kBJB, lg = t / kBJB;
+                    const int64_t j = ch * kBJB + jj;
+                    float x[8];
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) {
+                        const int l = 8 * lg + w;
+                        x[w] = (j < J && l < L) ? gaussian_at<float>(seed, stream_id, (uint64_t)(j * L + l)) : 0.f;
+                    }
+                    uint4 hi, lo;
+                    cvt8<SPLIT>(x, hi, lo);
+                    const size_t off = (size_t)(jj >> 3) * ng * 128 + (size_t)lg * 128 + (jj & 7) * 16;
+                    *reinterpret_cast<uint4*>(dst + off) = hi;
+                    if (SPLIT) *reinterpret_cast<uint4*>(dst + Np * 128 + off) = lo;
+                }
+                tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&w_full[ws]);
+            }
+            for (int b = 0; b < nbg; ++b, ++g) {
+                const int fs = (int)(g % kBFStages), cs = (int)(g % kBCStages);
+                if (!wait_bar(&f_full[fs], (uint32_t)((g / kBFStages) & 1), flag)) {
+                    ok = false;
+                    break;
+                }
+                // task t: fiber jj = 8 (t / 128) + t % 8, rows i = 8 ((t / 8) % 16) .. + 7 of the block
+                const unsigned char* src = F + (size_t)fs * kBUnit;
+                uint4 hi[kTasks], lo[kTasks];
+#pragma unroll
+                for (int q = 0; q < kTasks; ++q) {
+                    const int t = ct + kBConv * 32 * q;
+                    const int jlo = t & 7, ig = (t >> 3) & 15, jhi = t >> 7;
+                    const int jj = jhi * 8 + jlo;
+                    const int c0 = (ig & 3) * 2;
+                    const unsigned char* row = src + (ig >> 2) * kBBox + jj * 128;
+                    const float4 a = *reinterpret_cast<const float4*>(row + ((c0 ^ (jj & 7)) << 4));
+                    const float4 c = *reinterpret_cast<const float4*>(row + (((c0 + 1) ^ (jj & 7)) << 4));
+                    const float x[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+                    cvt8<SPLIT>(x, hi[q], lo[q]);
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&f_empty[fs]);
+                if (g >= kBCStages && !wait_bar(&c_empty[cs], (uint32_t)((g / kBCStages - 1) & 1), flag)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* dst = Cb + (size_t)cs * parts * kBHalf;
+#pragma unroll
+                for (int q = 0; q < kTasks; ++q) {
+                    const int t = ct + kBConv * 32 * q;
+                    const int jlo = t & 7, ig = (t >> 3) & 15, jhi = t >> 7;
+                    const int off = jhi * 2048 + ig * 128 + jlo * 16;
+                    *reinterpret_cast<uint4*>(dst + off) = hi[q];
+                    if (SPLIT) *reinterpret_cast<uint4*>(dst + kBHalf + off) = lo[q];
+                }
+                tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&c_full[cs]);
+            }
+        }
+        if (!ok) fail(flag, status);
+        // the CTA's partial: block b row i on lane i % 128, columns l
+        if (ok && wait_bar(done, 0, flag) && !*flag) {
+            tc::fence_after_sync();
+            const int quarter = warp & 3, half = (warp - 2) >> 2;
+            float* out = partial + r * ((int64_t)I * L);
+            for (int b = half; b < nbg; b += 2) {
+                const int i = row0 + b * 128 + quarter * 32 + lane;
+                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * Np);
+                for (int c0 = 0; c0 < Np; c0 += 16) {
+                    uint32_t v[16];
+                    tc::tmem_ld16(ta + (uint32_t)c0, v);
+                    if (i < I)
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            if (c0 + c < L) out[(int64_t)(c0 + c) * I + i] = __uint_as_float(v[c]);
+                }
+            }
+        } else if (!*flag) {
+            fail(flag, status);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+bool make_fiber_map(CUtensorMap* map, const float* A, int I, int64_t J, uint32_t box_fibers) {
+    const uint64_t dims[2] = {(uint64_t)I, (uint64_t)J};
+    const uint64_t strides[1] = {(uint64_t)I * sizeof(float)};
+    const uint32_t box[2] = {32, box_fibers};
+    return tma::make_map_f32(map, A, 2, dims, strides, box, true);
+}
+
+int grid_for(int64_t units, int num_sms) {
+    int g = (int)(units < num_sms ? units : num_sms);
+    return g < 1 ? 1 : g;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+bool wide_supported(const ModeView& v, int64_t cols) {
+    return v.lf == 1 && v.i >= 1 && v.i % 4 == 0 && v.i <= 16384 && cols >= 1 && cols <= 128 &&
+           v.fibers() <= (int64_t)INT_MAX - 256 && wide_a_layout((int)v.i, (int)cols, true).bytes <= kWSmemMax &&
+           wide_b_layout((int)v.i, (int)cols, true).bytes <= kWSmemMax;
+}
+
+size_t wide_ttm_scratch_bytes(const ModeView& v, int64_t K_out) {
+    const WideALayout a = wide_a_layout((int)v.i, (int)K_out, true);
+    return round256((size_t)a.nu * a.ubytes);
+}
+
+size_t wide_power_scratch_bytes(const ModeView& v, int L, int num_sms) {
+    const WideALayout a = wide_a_layout((int)v.i, L, true);
+    const WideBLayout b = wide_b_layout((int)v.i, L, true);
+    const int64_t chunks = (v.fibers() + kBJB - 1) / kBJB;
+    const int64_t R = std::max<int64_t>(1, std::min<int64_t>(chunks, num_sms / b.groups));
+    return round256((size_t)a.nu * a.ubytes) + 2 * round256((size_t)chunks * a.Np * 128) +
+           round256((size_t)R * v.i * L * sizeof(float));
+}
+
+cudaError_t launch_ttm_wide(const float* A, const ModeView& v, const float* Mp, int64_t K_out, int64_t ld_i,
+                            int64_t ld_k, float* out, void* scratch, int* status, int num_sms, cudaStream_t s) {
+    if (!wide_supported(v, K_out) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
+    const int I = (int)v.i;
+    const int64_t J = v.fibers();
+    const WideALayout t = wide_a_layout(I, (int)K_out, true);
+    CUtensorMap map;
+    if (!make_fiber_map(&map, A, I, J, kAJB)) return cudaErrorNotSupported;
+    unsigned char* img = reinterpret_cast<unsigned char*>(scratch);
+    image_kernel<true><<<grid_for(((int64_t)t.nu * t.Np * 8 + 255) / 256, 4 * num_sms), 256, 0, s>>>(
+        Mp, I, (int)K_out, ld_i, ld_k, t.Np, t.nu, img);
+    note_launch();
+    const int64_t tiles = (J + kAJB - 1) / kAJB;
+    const double elems = (double)I * (double)J;
+    {
+        ProfScope prof(kKTtmWide, (elems + (double)J * K_out) * sizeof(float), 2.0 * elems * K_out, s);
+        auto k = wide_ttm_kernel<true, 0>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.bytes);
+        k<<<grid_for(tiles, num_sms), kAThreads, t.bytes, s>>>(map, I, J, img, (int)K_out, t.Np, out, nullptr,
+                                                                 nullptr, tiles, t.nu, status);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_in, int L, float* X_out, bool split,
+                              bool range, uint64_t seed, uint32_t stream_id, void* scratch, int* status, int num_sms,
+                              cudaStream_t s) {
+    if (!wide_supported(v, L) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
+    const int I = (int)v.i;
+    const int64_t J = v.fibers();
+    const WideALayout ta = wide_a_layout(I, L, split);
+    const WideBLayout tb = wide_b_layout(I, L, split);
+    const int64_t chunks = (J + kBJB - 1) / kBJB;
+    const int64_t R = std::max<int64_t>(1, std::min<int64_t>(chunks, num_sms / tb.groups));
+    // scratch carve: M^T image | W hi | W lo | partials (sizes as wide_power_scratch_bytes, split)
+    const WideALayout tmax = wide_a_layout(I, L, true);
+    unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
+    unsigned char* img = p;
+    p += round256((size_t)tmax.nu * tmax.ubytes);
+    unsigned char* whi = p;
+    p += round256((size_t)chunks * ta.Np * 128);
+    unsigned char* wlo = p;
+    p += round256((size_t)chunks * ta.Np * 128);
+    float* part = reinterpret_cast<float*>(p);
+    const double elems = (double)I * (double)J;
+    if (!range) {
+        CUtensorMap map;
+        if (!make_fiber_map(&map, A, I, J, kAJB)) return cudaErrorNotSupported;
+        if (split)
+            image_kernel<true><<<grid_for(((int64_t)ta.nu * ta.Np * 8 + 255) / 256, 4 * num_sms), 256, 0, s>>>(
+                X_in, I, L, 1, I, ta.Np, ta.nu, img);
+        else
+            image_kernel<false><<<grid_for(((int64_t)ta.nu * ta.Np * 8 + 255) / 256, 4 * num_sms), 256, 0, s>>>(
+                X_in, I, L, 1, I, ta.Np, ta.nu, img);
+        note_launch();
+        const int64_t tiles = (J + kAJB - 1) / kAJB;
+        ProfScope prof(kKPowerWide1, elems * sizeof(float) + (double)J * ta.Np * 2 * ta.parts, 2.0 * elems * L, s);
+        auto k = split ? wide_ttm_kernel<true, 1> : wide_ttm_kernel<false, 1>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ta.bytes);
+        k<<<grid_for(tiles, num_sms), kAThreads, ta.bytes, s>>>(map, I, J, img, L, ta.Np, nullptr, whi, wlo, tiles,
+                                                                  ta.nu, status);
+        note_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    {
+        CUtensorMap map;
+        if (!make_fiber_map(&map, A, I, J, kBJB)) return cudaErrorNotSupported;
+        ProfScope prof(range ? kKRangeWide : kKPowerWide2,
+                       elems * sizeof(float) + (range ? 0.0 : (double)J * tb.Np * 2 * tb.parts * tb.groups),
+                       2.0 * elems * L, s);
+        auto k = split ? (range ? wide_power2_kernel<true, true> : wide_power2_kernel<true, false>)
+                       : (range ? wide_power2_kernel<false, true> : wide_power2_kernel<false, false>);
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb.bytes);
+        k<<<(int)(R * tb.groups), kBThreads, tb.bytes, s>>>(map, I, J, L, tb.Np, whi, wlo, seed, stream_id, part,
+                                                              tb.groups, tb.nb, chunks, status);
+        note_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return launch_reduce_partials<float>(part, (int)R, (int64_t)I * L, X_out, s);
+}
+
+}  // namespace tk

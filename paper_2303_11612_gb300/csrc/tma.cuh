@@ -47,6 +47,15 @@ __device__ __forceinline__ void load_3d(void* dst, const CUtensorMap* map, int x
         : "memory");
 }
 
+// Untiled bulk copy global -> shared of `bytes` (both addresses 16-byte aligned,
+// bytes a multiple of 16), completing on an mbarrier that expects the bytes.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(mbar))
+        : "memory");
+}
+
 // Makes mbarrier initialisation visible to the asynchronous (TMA) proxy.
 __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 

@@ -270,7 +270,9 @@ def test_plan_describe_pins_the_dispatch_rules():
     sketches only the input tensor (every T-HOSVD mode, ST-HOSVD's first),
     ST-HOSVD's later (truncated) modes and the TF32 form's strided modes take
     split BF16, the mode product runs split BF16 on contiguous fibers in every
-    tensor-core form and FP32 FMA elsewhere, and FP64 data stays FP64."""
+    tensor-core form and FP32 FMA elsewhere, shapes beyond the fused tiles take
+    the two-pass tensor-core kernels on contiguous fibers, and FP64 data stays
+    FP64."""
     import torch
     from paper_2303_11612_gb300 import _binding as B
     dims, ranks = (400, 400, 400), (20, 20, 20)
@@ -293,7 +295,23 @@ def test_plan_describe_pins_the_dispatch_rules():
     assert all(f64[n]["power"] == "fp64" and f64[n]["ttm"] == "fp64" for n in range(3))
     assert all(int(f64[n]["L"]) == 15 for n in range(3))
     rng = _modes(B.plan_describe("ST", dims, ranks, form="range", prec="bf16x1"))
-    assert all(rng[n]["range-sketch"] == "fp32" for n in range(3))
+    # the range form's first pass Y = A Omega: tensor cores on contiguous fibers
+    assert [rng[n]["range-sketch"] for n in range(3)] == ["wide-bf16x1", "fp32", "fp32"]
+    # beyond the fused tiles (I_n = 1024, L = 80, R = 64): two tensor-core passes on
+    # contiguous fibers and the gathered samples, single-pass BF16 on the input tensor only
+    big, bigr = (1024, 1024, 512), (64, 64, 32)
+    w1 = _modes(B.plan_describe("ST", big, bigr, P=16, prec="bf16x1"))
+    assert [w1[n]["power"] for n in range(3)] == ["wide-bf16x1", "fp32", "split-bf16"]
+    assert [w1[n]["ttm"] for n in range(3)] == ["wide-split-bf16", "fp32", "fp32"]
+    assert [int(w1[n]["L"]) for n in range(3)] == [80, 80, 48]
+    for prec in ("bf16", "tf32"):
+        w2 = _modes(B.plan_describe("ST", big, bigr, P=16, prec=prec))
+        assert [w2[n]["power"] for n in range(3)] == ["wide-split-bf16", "fp32", "split-bf16"]
+    wa = _modes(B.plan_describe("ST", big, bigr, P=16, c=20000, prec="bf16x1"))
+    assert [wa[n]["power"] for n in range(3)] == ["wide-bf16x1", "wide-split-bf16", "split-bf16"]
+    assert [int(wa[n]["T"]) for n in range(3)] == [20000, 20000, 64 * 64]
+    wf = _modes(B.plan_describe("ST", big, bigr, P=16, prec="fp32"))
+    assert all(wf[n]["power"] == "fp32" and wf[n]["ttm"] == "fp32" for n in range(3))
     lib = B.lib()
     small = C.create_string_buffer(16)
     assert lib.tucker_plan_describe(1, 0, B._i64(dims), 3, B._i32(ranks), 10, 1, 0, None, small, 16) == 1

@@ -79,13 +79,13 @@ def test_tc_power_step(tk, dims, L):
 def test_tc_power_step_rejects_unsupported_sizes(tk):
     from paper_2303_11612_gb300 import _binding as B
     import ctypes as C
-    dims = (600, 4, 4)
+    dims = (4, 600, 4)
     A = torch.zeros(600 * 16, device="cuda")
     X = torch.zeros((8, 600), device="cuda").t()
     out = torch.zeros((8, 600), device="cuda").t()
     o = B.make_opts(prec="bf16")
-    st = B.lib().tucker_power_step(A.data_ptr(), 0, B._i64(dims), 3, 0, X.data_ptr(), 8, out.data_ptr(), C.byref(o))
-    assert st == 6                                   # I_n > 512: unsupported on the bf16 path
+    st = B.lib().tucker_power_step(A.data_ptr(), 0, B._i64(dims), 3, 1, X.data_ptr(), 8, out.data_ptr(), C.byref(o))
+    assert st == 6                     # strided fibers with I_n > 512: no tensor-core pass takes them
 
 
 DRIVER_CASES = [

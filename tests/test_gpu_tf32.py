@@ -91,7 +91,7 @@ def test_tf32_power_step_rejects_unsupported(tk):
     A = torch.randn(40 * 36 * 32, device="cuda")
     X = np.zeros((36, 8))
     assert power_tf32(tk, A, dims, 1, X)[0] == 6               # strided fibers
-    assert power_tf32(tk, A, dims, 0, np.zeros((40, 40)))[0] == 6   # L > 32
+    assert power_tf32(tk, A, dims, 0, np.zeros((40, 130)))[0] == 6  # L > 128 (no tensor-core pass)
     dims = (42, 36, 32)
     A = torch.randn(42 * 36 * 32, device="cuda")
     assert power_tf32(tk, A, dims, 0, np.zeros((42, 8)))[0] == 6    # I_n not a multiple of 4

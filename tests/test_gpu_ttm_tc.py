@@ -87,7 +87,7 @@ def test_split_bf16_mode_product_rejects_unsupported(tk):
     with pytest.raises(tk.TuckerError):
         tk.ttm(A, dims, 1, torch.randn(8, 36, device="cuda").t(), transpose=True, prec="bf16")   # strided
     with pytest.raises(tk.TuckerError):
-        tk.ttm(A, dims, 0, torch.randn(40, 40, device="cuda").t(), transpose=True, prec="bf16")  # K > 32
+        tk.ttm(A, dims, 0, torch.randn(130, 40, device="cuda").t(), transpose=True, prec="bf16")  # K > 128
     with pytest.raises(tk.TuckerError):                                   # not 16-byte aligned for TMA
         tk.ttm(A[1:1 + 40 * 36 * 31], (40, 36, 31), 0, torch.randn(8, 40, device="cuda").t(), transpose=True,
                prec="bf16")
