@@ -184,7 +184,7 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         if (mp.wide || mp.wide_range)
             p.max_partials = std::max(p.max_partials, wide_power_scratch_bytes(mp.mv, mp.L, sms));
         if (o.prec != TUCKER_SK_FP32 && elem == 4 && st && !ttm_tc_supported(mp.v, mp.R) &&
-            wide_supported(mp.v, mp.R))
+            wide_ttm_supported(mp.v, mp.R))
             p.max_partials = std::max(p.max_partials, wide_ttm_scratch_bytes(mp.v, mp.R));
         mp.op = orth_plan(d[n], mp.L, sms);
         if (!orth_supported(mp.op, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
@@ -204,7 +204,7 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         for (int n = 0; n < N; ++n) {
             const ModeView tv = view_of(e, N, n);
             if (o.prec != TUCKER_SK_FP32 && elem == 4 && !ttm_tc_supported(tv, ranks[n]) &&
-                wide_supported(tv, ranks[n]))
+                wide_ttm_supported(tv, ranks[n]))
                 p.max_partials = std::max(p.max_partials, wide_ttm_scratch_bytes(tv, ranks[n]));
             if (n == N - 1) break;
             e[n] = ranks[n];
@@ -342,7 +342,7 @@ cudaError_t mode_product(const Plan& p, const T* A, const ModeView& v, const T* 
     if constexpr (sizeof(T) == 4) {
         if (p.prec != TUCKER_SK_FP32) {
             cudaError_t e = launch_ttm_tc(A, v, U, K, 1, v.i, out, w.status, num_sms(), s);
-            if (e == cudaErrorNotSupported && wide_supported(v, K))
+            if (e == cudaErrorNotSupported && wide_ttm_supported(v, K))
                 e = launch_ttm_wide(A, v, U, K, 1, v.i, out, w.partials, w.status, num_sms(), s);
             if (e != cudaErrorNotSupported) return e;
         }
@@ -615,7 +615,7 @@ tucker_status tucker_plan_describe(int which, tucker_dtype dt, const int64_t* di
         const bool tc_ttm = p.elem == 4 && p.prec != TUCKER_SK_FP32;
         const char* ttm = p.elem == 8                                       ? "fp64"
                           : (tc_ttm && ttm_tc_supported(tv, ranks[n]))     ? "split-bf16"
-                          : (tc_ttm && wide_supported(tv, ranks[n]))       ? "wide-split-bf16"
+                          : (tc_ttm && wide_ttm_supported(tv, ranks[n]))   ? "wide-split-bf16"
                                                                            : "fp32";
         const char* range = p.form != TUCKER_FORM_RANGE ? ""
                             : p.elem == 8               ? " range-sketch=fp64"
@@ -879,7 +879,8 @@ tucker_status tucker_ttm(const void* A, tucker_dtype dt, const int64_t* dims, in
     const int64_t ld_i = transpose ? 1 : K, ld_k = transpose ? v.i : 1;
     TuneAllow tune(true);
     Scratch sc;
-    const bool wide = o.prec != TUCKER_SK_FP32 && dt == TUCKER_F32 && !ttm_tc_supported(v, K) && wide_supported(v, K);
+    const bool wide =
+        o.prec != TUCKER_SK_FP32 && dt == TUCKER_F32 && !ttm_tc_supported(v, K) && wide_ttm_supported(v, K);
     if ((rs = sc.get(256 + (wide ? wide_ttm_scratch_bytes(v, K) : 0), o.stream)) != TUCKER_OK) return rs;
     if (cudaMemsetAsync(sc.p, 0, sizeof(int), o.stream) != cudaSuccess) return from_cuda(cudaGetLastError());
     if (o.prec != TUCKER_SK_FP32) {

@@ -82,7 +82,8 @@ cudaError_t launch_ttm_tc(const float* A, const ModeView& v, const float* Mp, in
 // ---- tensor-core passes for contiguous fibers at large shapes (kernels_wide.cu):
 // I_n % 4 == 0, columns (L or K_out) <= 128. Return cudaErrorNotSupported (nothing
 // launched) outside wide_supported or when A is not 16-byte aligned.
-bool wide_supported(const ModeView& v, int64_t cols);
+bool wide_supported(const ModeView& v, int64_t cols);          // power step (both passes)
+bool wide_ttm_supported(const ModeView& v, int64_t K_out);      // mode product
 size_t wide_ttm_scratch_bytes(const ModeView& v, int64_t K_out);
 size_t wide_power_scratch_bytes(const ModeView& v, int L, int num_sms);
 // out = A x_n M (split bf16, FP32 accumulate), out[j K_out + o] as launch_ttm.

@@ -404,7 +404,6 @@ constexpr int kBWStages = 2;
 constexpr int kBConv = 8;                  // converter (and generator, read-back) warps 2 .. 9
 constexpr int kBThreads = 64 + 32 * kBConv;
 constexpr int kBMaxBlocks = 4;             // 128-row blocks per CTA
-constexpr int kBTail = 20 * 1024;
 constexpr int kBBars = 2 * kBFStages + 2 * kBCStages + 2 * kBWStages + 1;
 static_assert(kBBars * 8 + 8 <= 256, "barrier area");
 
@@ -424,9 +423,7 @@ WideBLayout wide_b_layout(int I, int L, bool split) {
     t.c_off = (size_t)kBFStages * kBUnit;
     t.w_off = t.c_off + (size_t)kBCStages * t.parts * kBHalf;
     t.bar_off = t.w_off + (size_t)kBWStages * t.wbytes;
-    // the tail keeps every operand read of the descriptors inside the allocation
-    // even for the largest strides the layout could be read with
-    t.bytes = t.bar_off + 256 + 1024 + kBTail;
+    t.bytes = t.bar_off + 256 + 1024;
     return t;
 }
 
@@ -690,10 +687,13 @@ size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+bool wide_ttm_supported(const ModeView& v, int64_t K_out) {
+    return v.lf == 1 && v.i >= 1 && v.i % 4 == 0 && v.i <= 16384 && K_out >= 1 && K_out <= 128 &&
+           v.fibers() <= (int64_t)INT_MAX - 256 && wide_a_layout((int)v.i, (int)K_out, true).bytes <= kWSmemMax;
+}
+
 bool wide_supported(const ModeView& v, int64_t cols) {
-    return v.lf == 1 && v.i >= 1 && v.i % 4 == 0 && v.i <= 16384 && cols >= 1 && cols <= 128 &&
-           v.fibers() <= (int64_t)INT_MAX - 256 && wide_a_layout((int)v.i, (int)cols, true).bytes <= kWSmemMax &&
-           wide_b_layout((int)v.i, (int)cols, true).bytes <= kWSmemMax;
+    return wide_ttm_supported(v, cols) && wide_b_layout((int)v.i, (int)cols, true).bytes <= kWSmemMax;
 }
 
 size_t wide_ttm_scratch_bytes(const ModeView& v, int64_t K_out) {
@@ -712,7 +712,7 @@ size_t wide_power_scratch_bytes(const ModeView& v, int L, int num_sms) {
 
 cudaError_t launch_ttm_wide(const float* A, const ModeView& v, const float* Mp, int64_t K_out, int64_t ld_i,
                             int64_t ld_k, float* out, void* scratch, int* status, int num_sms, cudaStream_t s) {
-    if (!wide_supported(v, K_out) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
+    if (!wide_ttm_supported(v, K_out) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
     const int I = (int)v.i;
     const int64_t J = v.fibers();
     const WideALayout t = wide_a_layout(I, (int)K_out, true);

@@ -72,7 +72,7 @@ POWER = [
     ((1024, 40, 30), 80),     # the 1024^2 x 512 workload's I_1 and L_1 on 1200 fibers (ragged chunk and tile)
     ((1020, 33, 17), 70),     # I_n not a multiple of 64: partial row blocks and zero-filled boxes
     ((600, 100, 50), 48),     # five row blocks: two row groups of 4 and 1
-    ((256, 300, 10), 16),     # one row group, 3000 fibers: the rings wrap many times
+    ((520, 300, 10), 16),     # just past the fused tiles (I_n > 512), 3000 fibers: the rings wrap many times
     ((64, 50, 50), 128),      # the widest sketch
     ((1024, 8, 8), 1),        # one column
     ((1024, 20000, 1), 80),   # the shape of the gathered AMM sample (c = 20000)
@@ -81,6 +81,8 @@ POWER = [
 
 @pytest.mark.parametrize("dims,L", POWER)
 def test_wide_power_step_split(tk, dims, L):
+    """Every case lies beyond the fused kernels' tiles (I_n > 512 or L > 64),
+    where the two passes run (the fused split kernel rounds X to bf16 once)."""
     A, At = tensor(dims, 3)
     X = np.random.default_rng(L).standard_normal((dims[0], L)).astype(np.float32)
     M = ot.unfold(A.astype(np.float64), 0)
@@ -105,7 +107,8 @@ def test_wide_power_step_single(tk, dims, L):
     assert rel(got, Mb @ bf16(W)) < 5e-4
 
 
-TTM = [((1024, 40, 30), 64), ((1020, 33, 17), 50), ((600, 100, 50), 128), ((256, 300, 10), 1), ((64, 50, 50), 100)]
+# every case lies beyond the fused mode product (I_n > 512 or K_out > 32)
+TTM = [((1024, 40, 30), 64), ((1020, 33, 17), 50), ((600, 100, 50), 128), ((520, 300, 10), 1), ((64, 50, 50), 100)]
 
 
 @pytest.mark.parametrize("dims,K", TTM)
