@@ -41,9 +41,13 @@ namespace tk {
 namespace {
 
 constexpr int kT = kThreads;
-constexpr int kXT = 256;                 // threads of the extraction kernel (any SM can host it)
+// threads of the kernels whose last CTA runs the serial small-matrix algebra
+// (Cholesky, triangular inverse, Jacobi, final pass): their steps are chains of
+// barriers, so each step is spread over as many threads as a CTA has
+constexpr int kST = 1024;
+constexpr int kXT = kST;
 constexpr int kGramRows = 64;            // fewest rows per Gram CTA (few partials to reduce)
-constexpr int kBsCols = 4;               // columns per warp in the extraction's back-substitution
+constexpr int kBsCols = 2;               // columns per warp in the extraction's back-substitution
 constexpr int kBsRows = 4;               // rows per lane there: L <= 32 kBsRows
 
 __host__ __device__ __forceinline__ int packed_index(int a, int b, int L) {
@@ -264,7 +268,7 @@ __device__ void upper_inverse(const S* R, const S* dinv, int L, S* Acc, S* Ri) {
 // ---------------------------------------------------------------- one CholeskyQR pass
 // R and R^-1 (packed, scalar S) of X^T X = R^T R.
 template <typename T>
-__global__ void __launch_bounds__(kT) gram_chol_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
+__global__ void __launch_bounds__(kST) gram_chol_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
                                                        typename SmallScalar<T>::type* __restrict__ partial,
                                                        unsigned* ticket, typename SmallScalar<T>::type* __restrict__ R,
                                                        typename SmallScalar<T>::type* __restrict__ Rinv, int* status) {
@@ -381,14 +385,13 @@ __device__ __forceinline__ void rotation(double a, double b, double g, double& c
 }
 
 // One cyclic sweep of one-sided Jacobi on the columns of Mc (column-major,
-// column c at Mc + c * L, L <= 4 * GS); pairs handled by groups of GS lanes,
-// each lane holding up to 4 entries of both columns in registers. The squared
+// column c at Mc + c * L, L <= NE * GS); pairs handled by groups of GS lanes,
+// each lane holding up to NE entries of both columns in registers. The squared
 // norms a, b are plain sums (they only set the angle and the threshold); the
 // coupling g, which cancels, is summed in paired precision. Returns the number
 // of rotations.
-template <typename T, int GS>
+template <typename T, int GS, int NE>
 __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot) {
-    constexpr int NE = 4;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kGroupsPerWarp = 32 / GS;
     const int groups = ((int)blockDim.x >> 5) * kGroupsPerWarp, gl = lane % GS;
@@ -589,9 +592,10 @@ __global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, i
     const T tiny = eps * eps * fro2;
     for (int sweep = 0; sweep < 20; ++sweep) {
         int n;
-        if (L <= 32) n = jacobi_sweep<T, 8>(Mc, L, Lp, tol, tiny, &nrot);
-        else if (L <= 64) n = jacobi_sweep<T, 16>(Mc, L, Lp, tol, tiny, &nrot);
-        else n = jacobi_sweep<T, 32>(Mc, L, Lp, tol, tiny, &nrot);     // L <= 128
+        // groups of GS lanes, one pair each: every pair of a round in flight at once
+        if (L <= 32) n = jacobi_sweep<T, 8, 4>(Mc, L, Lp, tol, tiny, &nrot);
+        else if (L <= 64) n = jacobi_sweep<T, 16, 4>(Mc, L, Lp, tol, tiny, &nrot);
+        else n = jacobi_sweep<T, 16, 8>(Mc, L, Lp, tol, tiny, &nrot);     // L <= 128
         if (n == 0) break;
     }
     // singular values (column norms), decreasing order, lower index first on ties
@@ -762,7 +766,7 @@ __host__ __device__ inline FLayout flayout(int R, int elem, int64_t I) {
 // regions (the host checks that it fits), worked on there and copied back at
 // the end, which keeps the loops over U off the global-memory latency.
 template <typename T>
-__global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t I, int R, int staged) {
+__global__ void __launch_bounds__(kST) finish_kernel(T* __restrict__ Ug, int64_t I, int R, int staged) {
     using S = typename SmallScalar<T>::type;
     using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -778,23 +782,23 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
     int* cand = drop + R;                                      // [R] their candidate rows
     T* lev = reinterpret_cast<T*>(smem_raw + lay.lev);    // [I]
     T* coef = reinterpret_cast<T*>(smem_raw + lay.w);     // [R][R] projection coefficients (W and RT)
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kST / 32;
     const int np = (int)packed_size(R);
     T* U = staged ? reinterpret_cast<T*>(smem_raw + lay.total) : Ug;
     if (staged)
-        for (int64_t e = tid; e < I * R; e += kT) U[e] = Ug[e];
+        for (int64_t e = tid; e < I * R; e += kST) U[e] = Ug[e];
     __shared__ int offdiag, ndrop;
-    __shared__ double red[kT / 32];
+    __shared__ double red[kST / 32];
     __shared__ double bcast;
-    __shared__ T bvs[kT / 32];
-    __shared__ int64_t bis[kT / 32];
+    __shared__ T bvs[kST / 32];
+    __shared__ int64_t bis[kST / 32];
 
     const double eps = sizeof(T) == 4 ? (double)FLT_EPSILON : DBL_EPSILON;
     for (int pass = 0; pass < 2; ++pass) {
     // 1. Gram (FP32 data: Pair sums; FP64 data: the Pair slots hold one double)
     double* GD = reinterpret_cast<double*>(smem_raw + lay.g);
     __syncthreads();
-    for (int p = tid; p < np; p += kT) {
+    for (int p = tid; p < np; p += kST) {
         if constexpr (sizeof(T) == 4) GP[p] = Pair{0.f, 0.f};
         else GD[p] = 0.0;
     }
@@ -802,28 +806,40 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
     for (int64_t r0 = 0; r0 < I; r0 += kFRows) {
         const int nr = (int)min((int64_t)kFRows, I - r0);
         __syncthreads();
-        for (int e = tid; e < nr * R; e += kT) {
+        for (int e = tid; e < nr * R; e += kST) {
             const int r = e % nr, c = e / nr;
             xs[r * R + c] = U[(int64_t)c * I + r0 + r];
         }
         __syncthreads();
-        for (int p = tid; p < np; p += kT) {
+        for (int p = tid; p < np; p += kST) {
             int a = 0, rem = p;
             while (rem >= R - a) { rem -= R - a; ++a; }
             const int b = a + rem;
+            // two interleaved chains (even and odd rows), combined in a fixed order
             if constexpr (sizeof(T) == 4) {
-                Pair acc = GP[p];
-                for (int r = 0; r < nr; ++r) pair_add_prod(acc, xs[r * R + a], xs[r * R + b]);
+                Pair acc = GP[p], acc2{0.f, 0.f};
+                int r = 0;
+                for (; r + 1 < nr; r += 2) {
+                    pair_add_prod(acc, xs[r * R + a], xs[r * R + b]);
+                    pair_add_prod(acc2, xs[(r + 1) * R + a], xs[(r + 1) * R + b]);
+                }
+                if (r < nr) pair_add_prod(acc, xs[r * R + a], xs[r * R + b]);
+                pair_add(acc, acc2);
                 GP[p] = acc;
             } else {
-                double acc = GD[p];
-                for (int r = 0; r < nr; ++r) acc = fma(xs[r * R + a], xs[r * R + b], acc);
-                GD[p] = acc;
+                double acc = GD[p], acc2 = 0.0;
+                int r = 0;
+                for (; r + 1 < nr; r += 2) {
+                    acc = fma(xs[r * R + a], xs[r * R + b], acc);
+                    acc2 = fma(xs[(r + 1) * R + a], xs[(r + 1) * R + b], acc2);
+                }
+                if (r < nr) acc = fma(xs[r * R + a], xs[r * R + b], acc);
+                GD[p] = acc + acc2;
             }
         }
     }
     __syncthreads();
-    for (int p = tid; p < np; p += kT) {
+    for (int p = tid; p < np; p += kST) {
         int a = 0, rem = p;
         while (rem >= R - a) { rem -= R - a; ++a; }
         S g;
@@ -833,12 +849,12 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
         const double dev = fabs(F::to_double(g) - (rem == 0 ? 1.0 : 0.0));
         if (!(dev <= 8.0 * eps)) offdiag = 1;
     }
-    for (int k = tid; k < R; k += kT) valid[k] = 1;
+    for (int k = tid; k < R; k += kST) valid[k] = 1;
     __syncthreads();
     if (!offdiag) break;
     {
         // 2. Cholesky with column dropping (G kept in RT for the reference norms)
-        for (int p = tid; p < np; p += kT) RT[p] = W[p];
+        for (int p = tid; p < np; p += kST) RT[p] = W[p];
         __syncthreads();
         for (int k = 0; k < R; ++k) {
             if (tid == 0) {
@@ -858,12 +874,12 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
             __syncthreads();
             const int kk = packed_index(k, k, R);
             if (!valid[k]) {
-                for (int j = k + 1 + tid; j < R; j += kT) W[kk + (j - k)] = F::zero();
+                for (int j = k + 1 + tid; j < R; j += kST) W[kk + (j - k)] = F::zero();
                 __syncthreads();
                 continue;
             }
             const S y = dinv[k];
-            for (int j = k + 1 + tid; j < R; j += kT) W[kk + (j - k)] = W[kk + (j - k)] * y;
+            for (int j = k + 1 + tid; j < R; j += kST) W[kk + (j - k)] = W[kk + (j - k)] * y;
             __syncthreads();
             for (int i = k + 1 + warp; i < R; i += nw) {
                 const S cki = W[kk + (i - k)];
@@ -874,7 +890,7 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
         }
         upper_inverse<S>(W, dinv, R, RT, Ri);
         // U <- U R_U^-1, one thread per row, columns from the last (in place)
-        for (int64_t i = tid; i < I; i += kT) {
+        for (int64_t i = tid; i < I; i += kST) {
             for (int l = R - 1; l >= 0; --l) {
                 T v = T(0);
                 if (valid[l]) {
@@ -907,7 +923,7 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
     if (m == 0 || pass == 1) break;
     // 3. candidates: the first m rows k (increasing) whose unit vector keeps a
     //    long residual, 1 - leverage_k > (I - valid columns) / (2 I)
-    for (int64_t i = tid; i < I; i += kT) {
+    for (int64_t i = tid; i < I; i += kST) {
         T a = T(0);
         for (int r = 0; r < R; ++r)
             if (valid[r]) a = fma(U[(int64_t)r * I + i], U[(int64_t)r * I + i], a);
@@ -927,7 +943,7 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
     }
     __syncthreads();
     // first projection, from the candidate rows of the valid columns
-    for (int64_t e = tid; e < I * m; e += kT) {
+    for (int64_t e = tid; e < I * m; e += kST) {
         const int t = (int)(e / I);
         const int64_t i = e - (int64_t)t * I;
         const int k = cand[t];
@@ -950,7 +966,7 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
         if (lane == 0) coef[r * m + t] = c;
     }
     __syncthreads();
-    for (int64_t e = tid; e < I * m; e += kT) {
+    for (int64_t e = tid; e < I * m; e += kST) {
         const int t = (int)(e / I);
         const int64_t i = e - (int64_t)t * I;
         T v = U[(int64_t)drop[t] * I + i];
@@ -989,13 +1005,13 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
         if (valid[r]) continue;
         T* v = U + (int64_t)r * I;
         for (; k < I; ++k) {
-            for (int64_t i = tid; i < I; i += kT) v[i] = (i == k) ? T(1) : T(0);
+            for (int64_t i = tid; i < I; i += kST) v[i] = (i == k) ? T(1) : T(0);
             __syncthreads();
             for (int pass = 0; pass < 2; ++pass) {
                 for (int j = 0; j < R; ++j) {
                     if (!valid[j]) continue;
                     double s = 0.0;
-                    for (int64_t i = tid; i < I; i += kT) s = fma((double)U[(int64_t)j * I + i], (double)v[i], s);
+                    for (int64_t i = tid; i < I; i += kST) s = fma((double)U[(int64_t)j * I + i], (double)v[i], s);
                     s = warp_sum(s);
                     if (lane == 0) red[warp] = s;
                     __syncthreads();
@@ -1006,14 +1022,14 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
                     }
                     __syncthreads();
                     const double d = bcast;
-                    for (int64_t i = tid; i < I; i += kT) v[i] = (T)((double)v[i] - d * (double)U[(int64_t)j * I + i]);
+                    for (int64_t i = tid; i < I; i += kST) v[i] = (T)((double)v[i] - d * (double)U[(int64_t)j * I + i]);
                     __syncthreads();
                 }
             }
             double s = 0.0;
             T bv = T(-1);
             int64_t bi = 0;
-            for (int64_t i = tid; i < I; i += kT) {
+            for (int64_t i = tid; i < I; i += kST) {
                 s = fma((double)v[i], (double)v[i], s);
                 if (fabs(v[i]) > bv) { bv = fabs(v[i]); bi = i; }
             }
@@ -1039,7 +1055,7 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
             __syncthreads();
             const double f = bcast;
             if (f != 0.0) {
-                for (int64_t i = tid; i < I; i += kT) v[i] = (T)((double)v[i] * f);
+                for (int64_t i = tid; i < I; i += kST) v[i] = (T)((double)v[i] * f);
                 __syncthreads();
                 if (tid == 0) valid[r] = 1;
                 __syncthreads();
@@ -1052,7 +1068,7 @@ __global__ void __launch_bounds__(kT) finish_kernel(T* __restrict__ Ug, int64_t 
     }
     if (staged) {
         __syncthreads();
-        for (int64_t e = tid; e < I * R; e += kT) Ug[e] = U[e];
+        for (int64_t e = tid; e < I * R; e += kST) Ug[e] = U[e];
     }
 }
 
@@ -1142,7 +1158,7 @@ cudaError_t launch_cholqr(const T* X, T* Q, const OrthPlan& p, double* factor, v
     int64_t ablocks = (p.I * L + kT - 1) / kT;
     if (ablocks > 4 * 1024) ablocks = 4 * 1024;
     // R^-1 goes to the W block, which the extraction writes only after this pass
-    gram_chol_kernel<T><<<p.gram_blocks, kT, gsm, s>>>(X, p.I, L, rows, (S*)sc.partial, sc.ticket, (S*)factor,
+    gram_chol_kernel<T><<<p.gram_blocks, kST, gsm, s>>>(X, p.I, L, rows, (S*)sc.partial, sc.ticket, (S*)factor,
                                                         (S*)sc.W, status);
     note_launch();
     apply_rinv_kernel<T><<<(unsigned)ablocks, kT, asm_, s>>>(X, p.I, L, (const S*)sc.W, Q);
@@ -1175,7 +1191,7 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
     const size_t staged = finish_staged_smem(R, sizeof(T), p.I);
     const size_t fsm = staged ? staged : finish_smem(R, sizeof(T), p.I);
     cudaFuncSetAttribute(finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-    finish_kernel<T><<<1, kT, fsm, s>>>(U, p.I, R, staged ? 1 : 0);
+    finish_kernel<T><<<1, kST, fsm, s>>>(U, p.I, R, staged ? 1 : 0);
     note_launch();
     return cudaGetLastError();
 }
