@@ -170,15 +170,16 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         mp.tf32 = o.prec == TUCKER_SK_TF32 && elem == 4 && power_tf32_supported(mp.mv, mp.L);
         mp.bf16x1 = o.prec == TUCKER_SK_BF16X1 && elem == 4 && (!st || n == 0) &&
                     power_bf16x1_supported(mp.mv, mp.L);
-        mp.tc = o.prec != TUCKER_SK_FP32 && elem == 4 && power_tc_supported(mp.mv, mp.L);
+        // beyond the fused kernels' tiles (I_n > 512 or wide sketches; contiguous fibers, the
+        // gathered AMM sample, or strides that are multiples of 32): two tensor-core passes,
+        // single-pass bf16 where the form sketches in single-pass BF16 (preferred there over
+        // the fused split kernel), split bf16 elsewhere
+        mp.wide_split = !(o.prec == TUCKER_SK_BF16X1 && (!st || n == 0));
+        mp.wide = o.prec != TUCKER_SK_FP32 && elem == 4 && !mp.tf32 && !mp.bf16x1 &&
+                  wide_supported(mp.mv, mp.L) && (!mp.wide_split || !power_tc_supported(mp.mv, mp.L));
+        mp.tc = o.prec != TUCKER_SK_FP32 && elem == 4 && !mp.wide && power_tc_supported(mp.mv, mp.L);
         if (mp.tc || mp.tf32 || mp.bf16x1)
             p.max_partials = std::max(p.max_partials, power_tc_partials_bytes(mp.mv, mp.L, sms));
-        // beyond the fused kernels' tiles (I_n > 512 or wide sketches, contiguous fibers or
-        // the gathered AMM sample): two tensor-core passes, single-pass bf16 where the
-        // form sketches in single-pass BF16, split bf16 elsewhere
-        mp.wide_split = !(o.prec == TUCKER_SK_BF16X1 && (!st || n == 0));
-        mp.wide = o.prec != TUCKER_SK_FP32 && elem == 4 && !mp.tc && !mp.tf32 && !mp.bf16x1 &&
-                  wide_supported(mp.mv, mp.L);
         mp.wide_range = o.form == TUCKER_FORM_RANGE && o.prec != TUCKER_SK_FP32 && elem == 4 &&
                         wide_supported(mp.mv, mp.L);
         if (mp.wide || mp.wide_range)

@@ -163,11 +163,15 @@ WideALayout wide_a_layout(int I, int K_out, bool split) {
 // operand: 64-fiber chunk c = j / 64 at c * Np * 128 bytes of each part's array,
 // element (l, jj = j % 64) at (jj / 8) (Np / 8) 128 + (l / 8) 128 + (jj % 8) 16 +
 // (l % 8) 2 (core matrices of 8 fibers x 8 columns, columns contiguous).
-template <bool SPLIT, int OUT>
+// STRIDED: fibers of modes 2..N (stride Lf, a multiple of 32) in the unfolding's
+// order j = l + r Lf; a tile is 128 consecutive fibers, four groups of 32 that
+// each lie in one slab r; TMA loads a group as 3-D boxes of 32 fibers x 32
+// values (fibers contiguous) and the converters transpose them.
+template <bool SPLIT, int OUT, bool STRIDED>
 __global__ void __launch_bounds__(kAThreads, 1)
     wide_ttm_kernel(const __grid_constant__ CUtensorMap map, int I, int64_t J, const unsigned char* __restrict__ uimg,
                     int K_out, int Np, float* __restrict__ out, unsigned char* __restrict__ w_hi,
-                    unsigned char* __restrict__ w_lo, int64_t tiles, int nu, int* status) {
+                    unsigned char* __restrict__ w_lo, int64_t tiles, int nu, int64_t lf, int* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024 - (tma::smem_addr(smem_raw) & 1023)) & 1023);
     constexpr int parts = SPLIT ? 2 : 1;
@@ -222,9 +226,19 @@ __global__ void __launch_bounds__(kAThreads, 1)
                     }
                     tma::expect_tx(&f_full[fs], (uint32_t)kAUnit);
                     unsigned char* dst = F + (size_t)fs * kAUnit;
-                    // a box wholly beyond I_n loads zeros
-                    tma::load_2d(dst, &map, 64 * u, j0, &f_full[fs]);
-                    tma::load_2d(dst + kABox, &map, 64 * u + 32, j0, &f_full[fs]);
+                    // a box wholly beyond I_n (or, strided, beyond the last slab) loads zeros
+                    if (STRIDED) {
+#pragma unroll
+                        for (int gq = 0; gq < 4; ++gq) {
+                            const int64_t jg = (int64_t)j0 + 32 * gq;
+                            const int r = (int)(jg / lf), l = (int)(jg - (int64_t)r * lf);
+                            tma::load_3d(dst + (2 * gq) * 4096, &map, l, 64 * u, r, &f_full[fs]);
+                            tma::load_3d(dst + (2 * gq + 1) * 4096, &map, l, 64 * u + 32, r, &f_full[fs]);
+                        }
+                    } else {
+                        tma::load_2d(dst, &map, 64 * u, j0, &f_full[fs]);
+                        tma::load_2d(dst + kABox, &map, 64 * u + 32, j0, &f_full[fs]);
+                    }
                     tma::expect_tx(&u_full[us], ubytes);
                     tma::bulk_load(Us + (size_t)us * ubytes, uimg + (size_t)u * ubytes, ubytes, &u_full[us]);
                 }
@@ -303,12 +317,26 @@ __global__ void __launch_bounds__(kAThreads, 1)
 #pragma unroll
                 for (int r = 0; r < kTasks; ++r) {
                     const int t = ct + kAConv * 32 * r;
-                    const int j = t >> 3, p = t & 7;
-                    const int q0 = (p & 3) * 2;
-                    const unsigned char* row = src + (p >> 2) * kABox + j * 128;
-                    const float4 a = *reinterpret_cast<const float4*>(row + ((q0 ^ (j & 7)) << 4));
-                    const float4 c = *reinterpret_cast<const float4*>(row + (((q0 + 1) ^ (j & 7)) << 4));
-                    const float x[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+                    float x[8];
+                    if (STRIDED) {
+                        // task: fiber f of the tile (lanes: 32 consecutive fibers), values
+                        // 8 p .. 8 p + 7 of the unit, read down rows of box (f / 32, p / 4)
+                        const int f = t & 127, p = t >> 7;
+                        const unsigned char* box = src + (2 * (f >> 5) + (p >> 2)) * 4096;
+                        const int c = (f & 31) >> 2, e = (f & 3) * 4;
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) {
+                            const int row = (p & 3) * 8 + w;
+                            x[w] = *reinterpret_cast<const float*>(box + row * 128 + ((c ^ (row & 7)) << 4) + e);
+                        }
+                    } else {
+                        const int j = t >> 3, p = t & 7;
+                        const int q0 = (p & 3) * 2;
+                        const unsigned char* row = src + (p >> 2) * kABox + j * 128;
+                        const float4 a = *reinterpret_cast<const float4*>(row + ((q0 ^ (j & 7)) << 4));
+                        const float4 c = *reinterpret_cast<const float4*>(row + (((q0 + 1) ^ (j & 7)) << 4));
+                        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = c.x; x[5] = c.y; x[6] = c.z; x[7] = c.w;
+                    }
                     cvt8<SPLIT>(x, hi[r], lo[r]);
                 }
                 __syncwarp();
@@ -321,7 +349,7 @@ __global__ void __launch_bounds__(kAThreads, 1)
 #pragma unroll
                 for (int r = 0; r < kTasks; ++r) {
                     const int t = ct + kAConv * 32 * r;
-                    const int j = t >> 3, p = t & 7;
+                    const int j = STRIDED ? (t & 127) : (t >> 3), p = STRIDED ? (t >> 7) : (t & 7);
                     const int off = j * 128 + ((p ^ (j & 7)) << 4);
                     *reinterpret_cast<uint4*>(dhi + off) = hi[r];
                     if (SPLIT) *reinterpret_cast<uint4*>(dhi + kAHalf + off) = lo[r];
@@ -351,7 +379,14 @@ __global__ void __launch_bounds__(kAThreads, 1)
                 uint32_t r[16];
                 tc::tmem_ld16(ta + (uint32_t)c0, r);
                 if (j >= jend) continue;
-                if (OUT == 0) {
+                if (OUT == 0 && STRIDED) {
+                    // out(l, o, r) = out[l + o Lf + r Lf K_out]: lanes write consecutive l
+                    const int64_t rr = j / lf, l = j - rr * lf;
+                    float* o = out + l + rr * lf * K_out;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        if (c0 + c < K_out) o[(int64_t)(c0 + c) * lf] = __uint_as_float(r[c]);
+                } else if (OUT == 0) {
                     float* o = out + j * K_out;
                     if ((K_out & 3) == 0 && c0 + 16 <= K_out) {
 #pragma unroll
@@ -429,12 +464,15 @@ WideBLayout wide_b_layout(int I, int L, bool split) {
 
 // partial[r (I L) + l I + i] = sum over the CTA's chunks of A_(n)[i, j] B[j, l]
 // for the rows of its group; r = blockIdx.x / groups.
-template <bool SPLIT, bool RANGE>
+// STRIDED: a 64-fiber chunk is two groups of 32 fibers, each in one slab,
+// loaded as 3-D boxes of 32 fibers x 32 rows; the A operand is then K-major
+// (fibers contiguous in each row) in the no-swizzle core-matrix layout.
+template <bool SPLIT, bool RANGE, bool STRIDED>
 __global__ void __launch_bounds__(kBThreads, 1)
     wide_power2_kernel(const __grid_constant__ CUtensorMap map, int I, int64_t J, int L, int Np,
                        const unsigned char* __restrict__ w_hi, const unsigned char* __restrict__ w_lo, uint64_t seed,
                        uint32_t stream_id, float* __restrict__ partial, int groups, int nb, int64_t chunks,
-                       int* status) {
+                       int64_t lf, int* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024 - (tma::smem_addr(smem_raw) & 1023)) & 1023);
     constexpr int parts = SPLIT ? 2 : 1;
@@ -505,8 +543,19 @@ __global__ void __launch_bounds__(kBThreads, 1)
                     tma::expect_tx(&f_full[fs], (uint32_t)kBUnit);
                     unsigned char* dst = F + (size_t)fs * kBUnit;
                     const int i0 = row0 + b * 128;
+                    if (STRIDED) {
 #pragma unroll
-                    for (int s = 0; s < 4; ++s) tma::load_2d(dst + s * kBBox, &map, i0 + 32 * s, j0, &f_full[fs]);
+                        for (int gq = 0; gq < 2; ++gq) {
+                            const int64_t jg = (int64_t)j0 + 32 * gq;
+                            const int r = (int)(jg / lf), l = (int)(jg - (int64_t)r * lf);
+#pragma unroll
+                            for (int s = 0; s < 4; ++s)
+                                tma::load_3d(dst + (4 * gq + s) * 4096, &map, l, i0 + 32 * s, r, &f_full[fs]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < 4; ++s) tma::load_2d(dst + s * kBBox, &map, i0 + 32 * s, j0, &f_full[fs]);
+                    }
                 }
             }
             if (*flag) {
@@ -521,10 +570,12 @@ __global__ void __launch_bounds__(kBThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t id = tc::idesc_bf16(128, Np, true, true);
-            // no-swizzle core matrices: A (rows i x 64 fibers) LBO = K step 2048, SBO = M step 128;
-            // B (64 fibers x Np columns) LBO = K step Np 16, SBO = N step 128
-            const uint64_t a_desc = tc::desc(tc::smem_u32(Cb), 2048, 128);
+            const uint32_t id = tc::idesc_bf16(128, Np, !STRIDED, true);
+            // no-swizzle core matrices, LBO the K step, SBO the M/N step: A (rows i x 64
+            // fibers) MN-major 2048 / 128 (contiguous), K-major 128 / 1024 (strided);
+            // B (64 fibers x Np columns) MN-major, Np 16 / 128
+            const uint64_t a_desc = STRIDED ? tc::desc(tc::smem_u32(Cb), 128, 1024) : tc::desc(tc::smem_u32(Cb), 2048, 128);
+            const uint32_t a_kstep = STRIDED ? 2 * 128 : 2 * 2048;            // bytes per 16 fibers
             const uint64_t b_desc = tc::desc(tc::smem_u32(Ws), (uint32_t)(Np * 16), 128);
             const uint64_t alo = (uint64_t)(kBHalf >> 4), blo = (uint64_t)((Np * 128) >> 4);
             bool ok = true;
@@ -548,7 +599,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
                     const uint64_t b0 = b_desc + (uint64_t)((ws * wbytes) >> 4);
 #pragma unroll
                     for (int ks = 0; ks < kBJB / 16; ++ks) {
-                        const uint64_t sa = (uint64_t)((ks * 2 * 2048) >> 4), sb = (uint64_t)((ks * 2 * Np * 16) >> 4);
+                        const uint64_t sa = (uint64_t)((ks * a_kstep) >> 4), sb = (uint64_t)((ks * 2 * Np * 16) >> 4);
                         tc::mma_bf16(d, a0 + sa, b0 + sb, id, kk > 0 || ks > 0);
                         if (SPLIT) {
                             tc::mma_bf16(d, a0 + alo + sa, b0 + sb, id, true);
@@ -608,18 +659,28 @@ __global__ void __launch_bounds__(kBThreads, 1)
                     ok = false;
                     break;
                 }
-                // task t: fiber jj = 8 (t / 128) + t % 8, rows i = 8 ((t / 8) % 16) .. + 7 of the block
+                // contiguous, task t: fiber jj = 8 (t / 128) + t % 8, rows i = 8 ((t / 8) % 16) .. + 7;
+                // strided, task t: row i = t % 8 + 8 (t / 64), fibers 8 q .. 8 q + 7, q = (t / 8) % 8
                 const unsigned char* src = F + (size_t)fs * kBUnit;
                 uint4 hi[kTasks], lo[kTasks];
 #pragma unroll
                 for (int q = 0; q < kTasks; ++q) {
                     const int t = ct + kBConv * 32 * q;
-                    const int jlo = t & 7, ig = (t >> 3) & 15, jhi = t >> 7;
-                    const int jj = jhi * 8 + jlo;
-                    const int c0 = (ig & 3) * 2;
-                    const unsigned char* row = src + (ig >> 2) * kBBox + jj * 128;
-                    const float4 a = *reinterpret_cast<const float4*>(row + ((c0 ^ (jj & 7)) << 4));
-                    const float4 c = *reinterpret_cast<const float4*>(row + (((c0 + 1) ^ (jj & 7)) << 4));
+                    float4 a, c;
+                    if (STRIDED) {
+                        const int i = (t & 7) + 8 * (t >> 6), g8 = (t >> 3) & 7;
+                        const unsigned char* row = src + (4 * (g8 >> 2) + (i >> 5)) * 4096 + (i & 31) * 128;
+                        const int c0 = (g8 & 3) * 2;
+                        a = *reinterpret_cast<const float4*>(row + ((c0 ^ (i & 7)) << 4));
+                        c = *reinterpret_cast<const float4*>(row + (((c0 + 1) ^ (i & 7)) << 4));
+                    } else {
+                        const int jlo = t & 7, ig = (t >> 3) & 15, jhi = t >> 7;
+                        const int jj = jhi * 8 + jlo;
+                        const int c0 = (ig & 3) * 2;
+                        const unsigned char* row = src + (ig >> 2) * kBBox + jj * 128;
+                        a = *reinterpret_cast<const float4*>(row + ((c0 ^ (jj & 7)) << 4));
+                        c = *reinterpret_cast<const float4*>(row + (((c0 + 1) ^ (jj & 7)) << 4));
+                    }
                     const float x[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
                     cvt8<SPLIT>(x, hi[q], lo[q]);
                 }
@@ -633,8 +694,9 @@ __global__ void __launch_bounds__(kBThreads, 1)
 #pragma unroll
                 for (int q = 0; q < kTasks; ++q) {
                     const int t = ct + kBConv * 32 * q;
-                    const int jlo = t & 7, ig = (t >> 3) & 15, jhi = t >> 7;
-                    const int off = jhi * 2048 + ig * 128 + jlo * 16;
+                    // strided: core matrix (i / 8, fibers g8) at (i / 8) 1024 + g8 128, row i % 8
+                    const int off = STRIDED ? ((t >> 6) * 1024 + ((t >> 3) & 7) * 128 + (t & 7) * 16)
+                                            : ((t >> 7) * 2048 + ((t >> 3) & 15) * 128 + (t & 7) * 16);
                     *reinterpret_cast<uint4*>(dst + off) = hi[q];
                     if (SPLIT) *reinterpret_cast<uint4*>(dst + kBHalf + off) = lo[q];
                 }
@@ -671,11 +733,19 @@ __global__ void __launch_bounds__(kBThreads, 1)
     if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
-bool make_fiber_map(CUtensorMap* map, const float* A, int I, int64_t J, uint32_t box_fibers) {
-    const uint64_t dims[2] = {(uint64_t)I, (uint64_t)J};
-    const uint64_t strides[1] = {(uint64_t)I * sizeof(float)};
-    const uint32_t box[2] = {32, box_fibers};
-    return tma::make_map_f32(map, A, 2, dims, strides, box, true);
+// Tensor map of the fibers: contiguous (I, J) with boxes of 32 values x `box_fibers`;
+// strided (Lf, I, Rt) with boxes of 32 fibers x 32 values x 1 slab.
+bool make_fiber_map(CUtensorMap* map, const float* A, const ModeView& v, uint32_t box_fibers) {
+    if (v.lf == 1) {
+        const uint64_t dims[2] = {(uint64_t)v.i, (uint64_t)v.fibers()};
+        const uint64_t strides[1] = {(uint64_t)v.i * sizeof(float)};
+        const uint32_t box[2] = {32, box_fibers};
+        return tma::make_map_f32(map, A, 2, dims, strides, box, true);
+    }
+    const uint64_t dims[3] = {(uint64_t)v.lf, (uint64_t)v.i, (uint64_t)v.rt};
+    const uint64_t strides[2] = {(uint64_t)v.lf * sizeof(float), (uint64_t)v.lf * v.i * sizeof(float)};
+    const uint32_t box[3] = {32, 32, 1};
+    return tma::make_map_f32(map, A, 3, dims, strides, box, true);
 }
 
 int grid_for(int64_t units, int num_sms) {
@@ -685,10 +755,17 @@ int grid_for(int64_t units, int num_sms) {
 
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// contiguous fibers (I_n % 4 == 0 for the row stride), or strided ones whose
+// stride is a multiple of 32 (a 32-fiber group never crosses a slab)
+bool layout_ok(const ModeView& v) {
+    if (v.lf == 1) return v.i % 4 == 0;
+    return v.lf % 32 == 0 && v.lf <= (int64_t)INT_MAX && v.rt <= (int64_t)INT_MAX;
+}
+
 }  // namespace
 
 bool wide_ttm_supported(const ModeView& v, int64_t K_out) {
-    return v.lf == 1 && v.i >= 1 && v.i % 4 == 0 && v.i <= 16384 && K_out >= 1 && K_out <= 128 &&
+    return layout_ok(v) && v.i >= 1 && v.i <= 16384 && K_out >= 1 && K_out <= 128 &&
            v.fibers() <= (int64_t)INT_MAX - 256 && wide_a_layout((int)v.i, (int)K_out, true).bytes <= kWSmemMax;
 }
 
@@ -715,9 +792,10 @@ cudaError_t launch_ttm_wide(const float* A, const ModeView& v, const float* Mp, 
     if (!wide_ttm_supported(v, K_out) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
     const int I = (int)v.i;
     const int64_t J = v.fibers();
+    const bool strided = v.lf > 1;
     const WideALayout t = wide_a_layout(I, (int)K_out, true);
     CUtensorMap map;
-    if (!make_fiber_map(&map, A, I, J, kAJB)) return cudaErrorNotSupported;
+    if (!make_fiber_map(&map, A, v, kAJB)) return cudaErrorNotSupported;
     unsigned char* img = reinterpret_cast<unsigned char*>(scratch);
     image_kernel<true><<<grid_for(((int64_t)t.nu * t.Np * 8 + 255) / 256, 4 * num_sms), 256, 0, s>>>(
         Mp, I, (int)K_out, ld_i, ld_k, t.Np, t.nu, img);
@@ -726,10 +804,10 @@ cudaError_t launch_ttm_wide(const float* A, const ModeView& v, const float* Mp, 
     const double elems = (double)I * (double)J;
     {
         ProfScope prof(kKTtmWide, (elems + (double)J * K_out) * sizeof(float), 2.0 * elems * K_out, s);
-        auto k = wide_ttm_kernel<true, 0>;
+        auto k = strided ? wide_ttm_kernel<true, 0, true> : wide_ttm_kernel<true, 0, false>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.bytes);
         k<<<grid_for(tiles, num_sms), kAThreads, t.bytes, s>>>(map, I, J, img, (int)K_out, t.Np, out, nullptr,
-                                                                 nullptr, tiles, t.nu, status);
+                                                                 nullptr, tiles, t.nu, v.lf, status);
         note_launch();
     }
     return cudaGetLastError();
@@ -741,6 +819,7 @@ cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_
     if (!wide_supported(v, L) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
     const int I = (int)v.i;
     const int64_t J = v.fibers();
+    const bool strided = v.lf > 1;
     const WideALayout ta = wide_a_layout(I, L, split);
     const WideBLayout tb = wide_b_layout(I, L, split);
     const int64_t chunks = (J + kBJB - 1) / kBJB;
@@ -758,7 +837,7 @@ cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_
     const double elems = (double)I * (double)J;
     if (!range) {
         CUtensorMap map;
-        if (!make_fiber_map(&map, A, I, J, kAJB)) return cudaErrorNotSupported;
+        if (!make_fiber_map(&map, A, v, kAJB)) return cudaErrorNotSupported;
         if (split)
             image_kernel<true><<<grid_for(((int64_t)ta.nu * ta.Np * 8 + 255) / 256, 4 * num_sms), 256, 0, s>>>(
                 X_in, I, L, 1, I, ta.Np, ta.nu, img);
@@ -768,25 +847,31 @@ cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_
         note_launch();
         const int64_t tiles = (J + kAJB - 1) / kAJB;
         ProfScope prof(kKPowerWide1, elems * sizeof(float) + (double)J * ta.Np * 2 * ta.parts, 2.0 * elems * L, s);
-        auto k = split ? wide_ttm_kernel<true, 1> : wide_ttm_kernel<false, 1>;
+        auto k = split ? (strided ? wide_ttm_kernel<true, 1, true> : wide_ttm_kernel<true, 1, false>)
+                       : (strided ? wide_ttm_kernel<false, 1, true> : wide_ttm_kernel<false, 1, false>);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ta.bytes);
         k<<<grid_for(tiles, num_sms), kAThreads, ta.bytes, s>>>(map, I, J, img, L, ta.Np, nullptr, whi, wlo, tiles,
-                                                                  ta.nu, status);
+                                                                  ta.nu, v.lf, status);
         note_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     {
         CUtensorMap map;
-        if (!make_fiber_map(&map, A, I, J, kBJB)) return cudaErrorNotSupported;
+        if (!make_fiber_map(&map, A, v, kBJB)) return cudaErrorNotSupported;
         ProfScope prof(range ? kKRangeWide : kKPowerWide2,
                        elems * sizeof(float) + (range ? 0.0 : (double)J * tb.Np * 2 * tb.parts * tb.groups),
                        2.0 * elems * L, s);
-        auto k = split ? (range ? wide_power2_kernel<true, true> : wide_power2_kernel<true, false>)
-                       : (range ? wide_power2_kernel<false, true> : wide_power2_kernel<false, false>);
+        decltype(&wide_power2_kernel<true, true, true>) k;
+        if (strided)
+            k = split ? (range ? wide_power2_kernel<true, true, true> : wide_power2_kernel<true, false, true>)
+                      : (range ? wide_power2_kernel<false, true, true> : wide_power2_kernel<false, false, true>);
+        else
+            k = split ? (range ? wide_power2_kernel<true, true, false> : wide_power2_kernel<true, false, false>)
+                      : (range ? wide_power2_kernel<false, true, false> : wide_power2_kernel<false, false, false>);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb.bytes);
         k<<<(int)(R * tb.groups), kBThreads, tb.bytes, s>>>(map, I, J, L, tb.Np, whi, wlo, seed, stream_id, part,
-                                                              tb.groups, tb.nb, chunks, status);
+                                                              tb.groups, tb.nb, chunks, v.lf, status);
         note_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

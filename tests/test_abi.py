@@ -300,13 +300,16 @@ def test_plan_describe_pins_the_dispatch_rules():
     # beyond the fused tiles (I_n = 1024, L = 80, R = 64): two tensor-core passes on
     # contiguous fibers and the gathered samples, single-pass BF16 on the input tensor only
     big, bigr = (1024, 1024, 512), (64, 64, 32)
+    # (strided fibers too where the stride is a multiple of 32: modes 2 and 3 here)
     w1 = _modes(B.plan_describe("ST", big, bigr, P=16, prec="bf16x1"))
-    assert [w1[n]["power"] for n in range(3)] == ["wide-bf16x1", "fp32", "split-bf16"]
-    assert [w1[n]["ttm"] for n in range(3)] == ["wide-split-bf16", "fp32", "fp32"]
+    assert [w1[n]["power"] for n in range(3)] == ["wide-bf16x1", "wide-split-bf16", "split-bf16"]
+    assert [w1[n]["ttm"] for n in range(3)] == ["wide-split-bf16"] * 3
     assert [int(w1[n]["L"]) for n in range(3)] == [80, 80, 48]
     for prec in ("bf16", "tf32"):
         w2 = _modes(B.plan_describe("ST", big, bigr, P=16, prec=prec))
-        assert [w2[n]["power"] for n in range(3)] == ["wide-split-bf16", "fp32", "split-bf16"]
+        assert [w2[n]["power"] for n in range(3)] == ["wide-split-bf16", "wide-split-bf16", "split-bf16"]
+    wt = _modes(B.plan_describe("T", big, bigr, P=16, prec="bf16x1"))
+    assert [wt[n]["power"] for n in range(3)] == ["wide-bf16x1"] * 3          # every mode sketches the input
     wa = _modes(B.plan_describe("ST", big, bigr, P=16, c=20000, prec="bf16x1"))
     assert [wa[n]["power"] for n in range(3)] == ["wide-bf16x1", "wide-split-bf16", "split-bf16"]
     assert [int(wa[n]["T"]) for n in range(3)] == [20000, 20000, 64 * 64]

@@ -148,19 +148,84 @@ def test_wide_range_sketch(tk, dims, L):
     assert rel(got1, bf16(M) @ bf16(Om)) < 5e-4
 
 
+def step_mode(tk, At, dims, n, X, prec):
+    from paper_2303_11612_gb300 import _binding as B
+    L = X.shape[1]
+    out = tk.factor_tensor(dims[n], L, torch.float32, "cuda")
+    o = B.make_opts(prec=prec)
+    st = B.lib().tucker_power_step(At.data_ptr(), 0, B._i64(dims), len(dims), n, colmajor(X).data_ptr(), L,
+                                   out.data_ptr(), C.byref(o))
+    return st, out.double().cpu().numpy()
+
+
+# strided fibers (modes 2..N) with a stride that is a multiple of 32
+STRIDED = [
+    ((64, 1024, 40), 1, 80),      # the 1024^2 x 512 workload's second mode (after truncation) on 40 slabs
+    ((96, 600, 20), 1, 48),       # stride 96: groups of 32 fibers, chunks straddling slabs
+    ((32, 40, 60, 30), 2, 16),    # 4th order, stride 1280, I_n = 60 (zero-filled boxes)
+    ((32, 520, 9), 1, 70),        # 288 fibers: ragged last tile and chunk, beyond the last slab
+]
+
+
+@pytest.mark.parametrize("dims,n,L", STRIDED)
+def test_wide_power_step_strided(tk, dims, n, L):
+    A, At = tensor(dims, 7)
+    X = np.random.default_rng(L).standard_normal((dims[n], L)).astype(np.float32)
+    M = ot.unfold(A.astype(np.float64), n)
+    exact = M @ (M.T @ X.astype(np.float64))
+    prec = "bf16" if dims[n] > 512 or L > 64 else None
+    if prec:                                   # beyond the fused split kernel: the two passes run
+        st, got = step_mode(tk, At, dims, n, X, "bf16")
+        assert st == 0 and rel(got, exact) < 2e-4
+    st, got = step_mode(tk, At, dims, n, X, "bf16x1")
+    assert st == 0
+    assert rel(got, exact) < 3e-2
+    Mb = bf16(M)
+    assert rel(got, Mb @ bf16((Mb.T @ bf16(X)).astype(np.float32))) < 5e-4
+
+
+@pytest.mark.parametrize("dims,n,K", [((64, 1024, 40), 1, 64), ((96, 600, 20), 1, 50), ((32, 40, 60, 30), 2, 40),
+                                      ((32, 520, 9), 1, 128)])
+def test_wide_mode_product_strided(tk, dims, n, K):
+    """out(l, o, r) = sum_i A(l, i, r) M(i, o): the output keeps the tensor's layout
+    (mode n replaced by K), written by lanes of consecutive l."""
+    A, At = tensor(dims, 8)
+    U = np.random.default_rng(K).standard_normal((dims[n], K)).astype(np.float32)
+    Ut = torch.from_numpy(np.ascontiguousarray(U.T)).cuda().t()
+    got = tk.ttm(At, dims, n, Ut, transpose=True, prec="bf16").double().cpu().numpy()
+    M = ot.unfold(A.astype(np.float64), n)
+    outdims = list(dims)
+    outdims[n] = K
+    got = ot.unfold(synth.from_flat(got, outdims), n).T                   # J x K
+    exact = M.T @ U.astype(np.float64)
+    absprod = np.abs(M.T) @ np.abs(U.astype(np.float64))
+    I = dims[n]
+    assert np.all(np.abs(got - exact) <= (4 * 2.0 ** -16 + 4 * I * 2.0 ** -24) * absprod + 1e-30)
+
+
+def test_wide_range_sketch_strided(tk):
+    dims, L = (64, 600, 30), 70
+    A, At = tensor(dims, 9)
+    M = ot.unfold(A.astype(np.float64), 1)
+    Om = philox.gaussian_matrix(5, 1, M.shape[1], L)
+    got = tk.range_sketch(At, dims, 1, L, seed=5, prec="bf16").double().cpu().numpy()
+    assert rel(got, M @ Om) < 2e-4
+
+
 def test_wide_rejects_what_it_cannot_take(tk):
     from paper_2303_11612_gb300 import _binding as B
     dims = (1024, 4, 4)
     A = torch.zeros(1024 * 16 + 1, device="cuda")[1:]                   # not 16-byte aligned for TMA
     st, _ = step(tk, A, dims, np.zeros((1024, 80), np.float32), "bf16")
     assert st == 6
-    with pytest.raises(tk.TuckerError):
-        tk.range_sketch(torch.zeros(40 * 36 * 32, device="cuda"), (40, 36, 32), 1, 8, seed=1, prec="bf16")  # strided
+    with pytest.raises(tk.TuckerError):                                   # stride 40: not a multiple of 32
+        tk.range_sketch(torch.zeros(40 * 36 * 32, device="cuda"), (40, 36, 32), 1, 8, seed=1, prec="bf16")
 
 
 DRIVER = [
     ((1024, 96, 40), (64, 16, 8), 16),
     ((600, 80, 60), (40, 10, 12), 10),
+    ((640, 600, 8), (32, 32, 4), 16),       # the second mode strided (stride 32) with I_n = 600
 ]
 FORMS = ["bf16x1", "bf16", "tf32"]
 
