@@ -45,9 +45,11 @@ constexpr int kT = kThreads;
 // (Cholesky, triangular inverse, Jacobi, final pass): their steps are chains of
 // barriers, so each step is spread over as many threads as a CTA has
 constexpr int kST = 1024;
-constexpr int kXT = kST;
+// the extraction kernel holds two columns' entries per Jacobi lane: 512 threads
+// leave it 128 registers and still give every pair of a round (L <= 128) its group
+constexpr int kXT = 512;
 constexpr int kGramRows = 64;            // fewest rows per Gram CTA (few partials to reduce)
-constexpr int kBsCols = 2;               // columns per warp in the extraction's back-substitution
+constexpr int kBsCols = 4;               // columns per warp in the extraction's back-substitution
 constexpr int kBsRows = 4;               // rows per lane there: L <= 32 kBsRows
 
 __host__ __device__ __forceinline__ int packed_index(int a, int b, int L) {
@@ -504,7 +506,7 @@ __host__ __device__ inline XLayout xlayout(int L, int R, int elem) {
 // (scalar S, L x R, column-major). A column with no direction left gets W = 0
 // (the final pass completes it).
 template <typename T>
-__global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
+__global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
                                                       typename SmallScalar<T>::type* __restrict__ partial,
                                                       unsigned* ticket,
                                                       const typename SmallScalar<T>::type* __restrict__ prev,
@@ -592,10 +594,14 @@ __global__ void __launch_bounds__(kXT) extract_kernel(const T* __restrict__ X, i
     const T tiny = eps * eps * fro2;
     for (int sweep = 0; sweep < 20; ++sweep) {
         int n;
-        // groups of GS lanes, one pair each: every pair of a round in flight at once
+        // groups of 8 lanes, one pair each, every pair of a round in flight at once;
+        // each lane holds NE >= L / 8 entries of both columns (a round is bound by
+        // instruction issue, so lanes do not repeat the reductions needlessly)
         if (L <= 32) n = jacobi_sweep<T, 8, 4>(Mc, L, Lp, tol, tiny, &nrot);
-        else if (L <= 64) n = jacobi_sweep<T, 16, 4>(Mc, L, Lp, tol, tiny, &nrot);
-        else n = jacobi_sweep<T, 16, 8>(Mc, L, Lp, tol, tiny, &nrot);     // L <= 128
+        else if (L <= 64) n = jacobi_sweep<T, 8, 8>(Mc, L, Lp, tol, tiny, &nrot);
+        else if (L <= 80) n = jacobi_sweep<T, 8, 10>(Mc, L, Lp, tol, tiny, &nrot);
+        else if (L <= 96) n = jacobi_sweep<T, 8, 12>(Mc, L, Lp, tol, tiny, &nrot);
+        else n = jacobi_sweep<T, 8, 16>(Mc, L, Lp, tol, tiny, &nrot);     // L <= 128
         if (n == 0) break;
     }
     // singular values (column norms), decreasing order, lower index first on ties
@@ -765,8 +771,41 @@ __host__ __device__ inline FLayout flayout(int R, int elem, int64_t I) {
 // With staged set, U is copied into shared memory after the layout's other
 // regions (the host checks that it fits), worked on there and copied back at
 // the end, which keeps the loops over U off the global-memory latency.
+// Partial Grams of U's rows by a grid of CTAs; the last one sums them in block
+// order and records in *ok whether U^T U is within 8 eps of I, in which case
+// the final pass keeps U and only applies the sign rule.
 template <typename T>
-__global__ void __launch_bounds__(kST) finish_kernel(T* __restrict__ Ug, int64_t I, int R, int staged) {
+__global__ void __launch_bounds__(kST) ugram_check_kernel(const T* __restrict__ U, int64_t I, int R, int rows,
+                                                          typename SmallScalar<T>::type* __restrict__ partial,
+                                                          unsigned* ticket, int* ok) {
+    using S = typename SmallScalar<T>::type;
+    using F = Sc<S>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    gram_partial<T, S>(U, I, R, rows, partial, smem_raw);
+    if (!last_cta(ticket)) return;
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    const int np = (int)packed_size(R);
+    const double eps = sizeof(T) == 4 ? (double)FLT_EPSILON : DBL_EPSILON;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        S acc = ld_cg(partial + p);
+        for (int b = 1; b < (int)gridDim.x; ++b) acc = acc + ld_cg(partial + (int64_t)b * np + p);
+        int a = 0, rem = p;
+        while (rem >= R - a) { rem -= R - a; ++a; }
+        const double dev = fabs(F::to_double(acc) - (rem == 0 ? 1.0 : 0.0));
+        if (!(dev <= 8.0 * eps)) bad = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *ok = !bad;
+        *ticket = 0;                                     // ready for the next use
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kST) finish_kernel(T* __restrict__ Ug, int64_t I, int R, int staged,
+                                                     const int* __restrict__ pre_ok) {
     using S = typename SmallScalar<T>::type;
     using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -794,7 +833,14 @@ __global__ void __launch_bounds__(kST) finish_kernel(T* __restrict__ Ug, int64_t
     __shared__ int64_t bis[kST / 32];
 
     const double eps = sizeof(T) == 4 ? (double)FLT_EPSILON : DBL_EPSILON;
-    for (int pass = 0; pass < 2; ++pass) {
+    // U^T U already checked within 8 eps of I by the grid of ugram_check_kernel:
+    // nothing to repair, only the sign rule
+    const bool checked_ok = *pre_ok != 0;
+    if (checked_ok) {
+        for (int k = tid; k < R; k += kST) valid[k] = 1;
+        __syncthreads();
+    }
+    for (int pass = 0; pass < 2 && !checked_ok; ++pass) {
     // 1. Gram (FP32 data: Pair sums; FP64 data: the Pair slots hold one double)
     double* GD = reinterpret_cast<double*>(smem_raw + lay.g);
     __syncthreads();
@@ -1188,10 +1234,17 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
     if (ublocks > 4 * 1024) ublocks = 4 * 1024;
     form_u_kernel<T><<<(unsigned)ublocks, kT, 0, s>>>(Q1, p.I, L, R, (const S*)sc.W, U);
     note_launch();
+    // U^T U by a grid of CTAs (the final pass repairs U only when it is not
+    // orthonormal to 8 eps, which a one-CTA Gram over I rows would take long to tell)
+    int* ok = sc.flag + 8;
+    const size_t usm = (size_t)sizeof(T) * (size_t)rows * R;
+    cudaFuncSetAttribute(ugram_check_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usm);
+    ugram_check_kernel<T><<<p.gram_blocks, kST, usm, s>>>(U, p.I, R, rows, (S*)sc.partial, sc.ticket, ok);
+    note_launch();
     const size_t staged = finish_staged_smem(R, sizeof(T), p.I);
     const size_t fsm = staged ? staged : finish_smem(R, sizeof(T), p.I);
     cudaFuncSetAttribute(finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-    finish_kernel<T><<<1, kST, fsm, s>>>(U, p.I, R, staged ? 1 : 0);
+    finish_kernel<T><<<1, kST, fsm, s>>>(U, p.I, R, staged ? 1 : 0, ok);
     note_launch();
     return cudaGetLastError();
 }
