@@ -115,6 +115,8 @@ struct ModePlan {
     bool wide;         // power steps as two tensor-core passes (contiguous fibers beyond the fused tiles)
     bool wide_split;   //   with split-bf16 operands (else single-pass bf16)
     bool wide_range;   // range form: first pass Y = A Omega on the tensor cores, Omega generated in-kernel
+    bool half;         // AMM, paper form: power steps on C' as two orthonormalised half steps
+    OrthPlan opT;      //   orthonormalisation of the T x L half-step product
     PowerPlan pp;
     OrthPlan op;
 };
@@ -129,7 +131,8 @@ struct Plan {
     int64_t dims[kMaxOrder];
     int64_t cur[kMaxOrder][kMaxOrder];   // dims of the tensor each mode works on (ST shrinks)
     ModePlan m[kMaxOrder];
-    int64_t maxI = 0, maxL = 0, maxJ = 0, maxT = 0, maxIT = 0;
+    int64_t maxI = 0, maxL = 0, maxJ = 0, maxT = 0, maxIT = 0, maxTL = 0;
+    bool half = false;
     size_t max_partials = 0, max_orth = 0;
     int64_t inter_elems = 0;             // largest intermediate tensor of the TTM chain
 };
@@ -189,6 +192,17 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
             p.max_partials = std::max(p.max_partials, wide_ttm_scratch_bytes(mp.v, mp.R));
         mp.op = orth_plan(d[n], mp.L, sms);
         if (!orth_supported(mp.op, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
+        // AMM in the paper form: C_n = (C' C'^T)^q Omega evaluated in half steps (Y = C'^T Q,
+        // Y = Q_Y R_Y, X = C' Q_Y), every stored product orthonormalised, so that FP32 keeps
+        // the sample's directions down to sigma_i / sigma_1 ~ 2^-24 rather than 2^-12
+        mp.half = mp.T > 0 && o.form == TUCKER_FORM_PAPER && mp.T >= mp.L && half_supported(mp.L);
+        if (mp.half) {
+            mp.opT = orth_plan(mp.T, mp.L, sms);
+            p.half = true;
+            p.maxTL = std::max(p.maxTL, mp.T * (int64_t)mp.L);
+            p.max_orth = std::max(p.max_orth, orth_scratch_bytes(mp.opT, elem));
+            p.max_partials = std::max(p.max_partials, half_partials_bytes(d[n], mp.L, mp.T, sms, elem));
+        }
         p.maxI = std::max(p.maxI, d[n]);
         p.maxL = std::max<int64_t>(p.maxL, mp.L);
         p.maxJ = std::max(p.maxJ, J);
@@ -223,13 +237,15 @@ struct Work {
     void* orth;
     double* w; uint64_t* W; void* samp; int64_t* idx; double* scale; void* Cp;
     void* inter[2];
+    void* Y; void* QY;     // half steps: T x L product and its orthonormal factor
     void* sumsq;
     double* norms;     // [2]: ||A||^2, ||G||^2
 };
 
 void carve(const Plan& p, Arena& a, Work& w) {
     const size_t IL = (size_t)p.maxI * p.maxL * p.elem;
-    const int slots = p.form == TUCKER_FORM_PAPER ? p.q : 1;
+    // factor slots: paper form q (2q with half steps: one per half step and per step), range form 1
+    const int slots = p.form == TUCKER_FORM_PAPER ? (p.half ? 2 * p.q : p.q) : 1;
     w.status = (int*)a.take(sizeof(int) * 64);
     w.X0 = a.take(IL);
     w.X1 = a.take(IL);
@@ -248,6 +264,8 @@ void carve(const Plan& p, Arena& a, Work& w) {
     } else {
         w.w = nullptr; w.W = nullptr; w.samp = nullptr; w.idx = nullptr; w.scale = nullptr; w.Cp = nullptr;
     }
+    w.Y = p.maxTL ? a.take((size_t)p.maxTL * p.elem) : nullptr;
+    w.QY = p.maxTL ? a.take((size_t)p.maxTL * p.elem) : nullptr;
     w.inter[0] = a.take((size_t)p.inter_elems * p.elem);
     w.inter[1] = a.take((size_t)p.inter_elems * p.elem);
     w.sumsq = a.take(sumsq_scratch_bytes());
@@ -302,6 +320,29 @@ cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, 
     const int L = mp.L;
     T* X0 = (T*)w.X0; T* X1 = (T*)w.X1; T* Q = (T*)w.Q;
     const size_t LL = (size_t)L * L;
+    if (form == TUCKER_FORM_PAPER && mp.half) {
+        // C = (C' C'^T)^q Omega in half steps: from Q_{k-1} (Q_0 = Omega), Y_k = C'^T Q_{k-1}
+        // = Q_Y R_Y and X_k = C' Q_Y, so C' C'^T Q_{k-1} = X_k R_Y; between steps X_k = Q_k F_k.
+        // Hence C = X_q R_Y,q F_{q-1} R_Y,q-1 ... F_1 R_Y,1, the factors kept in that order.
+        TK_TRY(launch_gaussian<T>(X0, mp.v.i, L, seed, stream_id(0, n), s));
+        T* Y = (T*)w.Y;
+        T* QY = (T*)w.QY;
+        int f = 0;
+        const T* xin = X0;
+        for (int k = 0; k < q; ++k) {
+            if (k > 0) {
+                TK_TRY(launch_cholqr<T>(X1, Q, mp.op, w.factors + (size_t)f * LL, w.orth, w.status, s));
+                ++f;
+                xin = Q;
+            }
+            TK_TRY(launch_gemm_tn<T>(M, mp.v.i, mp.T, xin, L, Y, s));
+            TK_TRY(launch_cholqr<T>(Y, QY, mp.opT, w.factors + (size_t)f * LL, w.orth, w.status, s));
+            ++f;
+            TK_TRY(launch_gemm_nn<T>(M, mp.v.i, mp.T, QY, L, X1, w.partials, num_sms(), s));
+        }
+        ProfScope prof(kKExtract, 0.0, 0.0, s);
+        return launch_extract<T>(X1, Q, mp.op, w.factors, f, mp.R, U, w.orth, w.status, s);
+    }
     if (form == TUCKER_FORM_PAPER) {
         // C = (M M^T)^q Omega in factored form: after each step X_k = Q_k F_k and
         // the next step multiplies Q_k, so C = X_q F_{q-1} ... F_1 with no overflow
@@ -623,9 +664,10 @@ tucker_status tucker_plan_describe(int which, tucker_dtype dt, const int64_t* di
                             : mp.wide_range ? (mp.wide_split ? " range-sketch=wide-split-bf16" : " range-sketch=wide-bf16x1")
                                             : " range-sketch=fp32";
         char line[256];
-        snprintf(line, sizeof(line), "mode %d: I=%lld L=%d J=%lld T=%lld sketch=%s power=%s ttm=%s%s\n", n,
+        snprintf(line, sizeof(line), "mode %d: I=%lld L=%d J=%lld T=%lld sketch=%s power=%s ttm=%s%s%s\n", n,
                  (long long)mp.v.i, mp.L, (long long)mp.v.fibers(), (long long)mp.T,
-                 mp.mv.lf == 1 ? "contiguous" : "strided", power, ttm, range);
+                 mp.mv.lf == 1 ? "contiguous" : "strided", mp.half ? (p.elem == 8 ? "fp64" : "fp32") : power, ttm,
+                 range, mp.half ? " amm=half-steps" : "");
         text += line;
         if (!p.st) e[n] = ranks[n];
     }

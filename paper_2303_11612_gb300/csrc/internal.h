@@ -96,6 +96,17 @@ cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_
                               bool range, uint64_t seed, uint32_t stream_id, void* scratch, int* status, int num_sms,
                               cudaStream_t s);
 
+// ---- half steps of the power scheme on the gathered AMM sample (kernels_half.cu)
+bool half_supported(int L);
+size_t half_partials_bytes(int64_t I, int L, int64_t Tn, int num_sms, int elem_size);
+// Y (Tn x L) = M^T X with M I x Tn, X I x L (all column-major).
+template <typename T>
+cudaError_t launch_gemm_tn(const T* M, int64_t I, int64_t Tn, const T* X, int L, T* Y, cudaStream_t s);
+// X (I x L) = M Q with Q Tn x L, split over Tn (partials of half_partials_bytes).
+template <typename T>
+cudaError_t launch_gemm_nn(const T* M, int64_t I, int64_t Tn, const T* Q, int L, T* X, void* partials, int num_sms,
+                           cudaStream_t s);
+
 // ---- sampling (kernels_amm.cu)
 template <typename T>
 cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStream_t s);

@@ -426,16 +426,28 @@ __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot) {
                 x[e] = in ? cp[r] : T(0);
                 y[e] = in ? cq[r] : T(0);
             }
-            T a = T(0), b = T(0), g;
+            // two independent chains per sum (even and odd entries), combined in a
+            // fixed order: the sums are the dependent chains of a round
+            T a = T(0), b = T(0), a2 = T(0), b2 = T(0), g;
 #pragma unroll
-            for (int e = 0; e < NE; ++e) {
+            for (int e = 0; e < NE; e += 2) {
                 a = fma(x[e], x[e], a);
                 b = fma(y[e], y[e], b);
+                if (e + 1 < NE) {
+                    a2 = fma(x[e + 1], x[e + 1], a2);
+                    b2 = fma(y[e + 1], y[e + 1], b2);
+                }
             }
+            a += a2;
+            b += b2;
             if constexpr (sizeof(T) == 4) {
-                Pair ga{0.f, 0.f};
+                Pair ga{0.f, 0.f}, gb{0.f, 0.f};
 #pragma unroll
-                for (int e = 0; e < NE; ++e) pair_add_prod(ga, x[e], y[e]);
+                for (int e = 0; e < NE; e += 2) {
+                    pair_add_prod(ga, x[e], y[e]);
+                    if (e + 1 < NE) pair_add_prod(gb, x[e + 1], y[e + 1]);
+                }
+                pair_add(ga, gb);
 #pragma unroll
                 for (int o = GS / 2; o > 0; o >>= 1) {
                     const float ta = __shfl_xor_sync(0xffffffffu, a, o);

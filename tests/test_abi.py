@@ -310,9 +310,15 @@ def test_plan_describe_pins_the_dispatch_rules():
         assert [w2[n]["power"] for n in range(3)] == ["wide-split-bf16", "wide-split-bf16", "split-bf16"]
     wt = _modes(B.plan_describe("T", big, bigr, P=16, prec="bf16x1"))
     assert [wt[n]["power"] for n in range(3)] == ["wide-bf16x1"] * 3          # every mode sketches the input
+    # AMM in the paper form: the gathered sample is sketched in half steps in the
+    # data's precision (FMA), in every form
     wa = _modes(B.plan_describe("ST", big, bigr, P=16, c=20000, prec="bf16x1"))
-    assert [wa[n]["power"] for n in range(3)] == ["wide-bf16x1", "wide-split-bf16", "split-bf16"]
+    assert [wa[n]["power"] for n in range(3)] == ["fp32"] * 3
+    assert [wa[n]["amm"] for n in range(3)] == ["half-steps"] * 3
     assert [int(wa[n]["T"]) for n in range(3)] == [20000, 20000, 64 * 64]
+    # no half steps where the sample has fewer fibers than the sketch has columns
+    few = _modes(B.plan_describe("ST", (40, 36, 32), (8, 6, 7), P=5, c=10, prec="bf16x1"))
+    assert all("amm" not in few[n] for n in range(3))
     wf = _modes(B.plan_describe("ST", big, bigr, P=16, prec="fp32"))
     assert all(wf[n]["power"] == "fp32" and wf[n]["ttm"] == "fp32" for n in range(3))
     lib = B.lib()

@@ -179,12 +179,15 @@ def test_video_like_1024_against_the_oracle(tk, video, video_oracle, prec):
     jobs = [(Ad, dims, ranks, kw) for kw in VIDEO_VARIANTS]
     got = in_flight(tk, jobs, prec)
     for kw, res, (Uo, Go, reo, info) in zip(VIDEO_VARIANTS, got, video_oracle):
-        re_dev = tk.relative_error(Ad, dims, ranks, res[0], res[1])
+        re = tk.relative_error(Ad, dims, ranks, res[0], res[1])              # explicit, on the device
         U = [u.double().cpu().numpy() for u in res[0]]
         G = res[1].double().cpu().numpy()
-        re = np.sqrt(max(0.0, 1.0 - float(np.sum(G * G)) / float(np.sum(A.astype(np.float64) ** 2))))
+        re_id = np.sqrt(max(0.0, 1.0 - float(np.sum(G * G)) / float(np.sum(A.astype(np.float64) ** 2))))
         assert abs(re - reo) <= (1e-5 if prec == "fp32" else 1e-3), (prec, kw["c"], re, reo)
-        assert abs(re - re_dev) <= 1e-4, (re, re_dev)
+        # the identity is as accurate as the core: a relative error d of ||G||^2
+        # moves it by about d / (2 RE); the tensor-core forms' mode products are
+        # split bf16 (d ~ 2^-15), the FP32 form's exact FP32
+        assert abs(re_id - re) <= (1e-4 if prec == "fp32" else 2.0 ** -15 / (2 * re) + 1e-5), (re_id, re)
         for n, (u, uo) in enumerate(zip(U, Uo)):
             assert np.linalg.norm(u.T @ u - np.eye(u.shape[1])) < 10 * u.shape[1] * 1.19e-7
             s = info["sigma_C"][n]
