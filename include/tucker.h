@@ -273,6 +273,57 @@ tucker_status tucker_relative_error(const void* A, tucker_dtype dt, const int64_
                                     const int32_t* ranks, void* const* U, const void* G,
                                     double* re, const tucker_opts* opts);
 
+/* ---------------------------------------------------------------- steps of a sharded call
+ * The tensor partitioned into slabs along its last mode N, one slab per rank
+ * (slab-sharded ST-HOSVD): for every mode n < N the sketch is the sum over the
+ * slabs of their power-step outputs, and AMM samples the fibers of all slabs
+ * together (Algorithm 5, RANDSAMPLE of Section 3.2). A slab's mode-n fibers are
+ * consecutive global fibers (mode N is the most significant part of the fiber
+ * index), so the global multinomial draws can be resolved slab by slab. These
+ * entry points are the steps such a call needs beyond those above; the package's
+ * sharded driver combines them with torch.distributed collectives. */
+
+/* W_j = ceil(w_j / wmax * 2^24) for w_j > 0, else 0 (all ones when wmax is 0):
+ * the integer weights of RANDSAMPLE (remark after Algorithm 3) with the largest
+ * weight wmax taken over every slab. w, W: device arrays of J entries. */
+tucker_status tucker_quantize_weights_max(const double* w, int64_t J, double wmax, uint64_t* W,
+                                          const tucker_opts* opts);
+
+/* The draws of RANDSAMPLE (Section 3.2) that fall in one slab: this slab holds
+ * global fibers fiber_offset .. fiber_offset + J - 1 with weights W (device, J
+ * entries) covering the range [S_offset, S_offset + sum W) of the global weight
+ * total S_total. Draw t (same Philox word as tucker_sample_fibers) owned by
+ * this slab gets its global fiber index in idx[t] and 1/sqrt(T p) in scale[t];
+ * draws owned by other slabs get idx[t] = -1 and scale[t] = 0 (device arrays of
+ * T entries). Over all slabs the result equals tucker_sample_fibers on the
+ * concatenated weights, bit for bit. */
+tucker_status tucker_sample_fibers_slab(const uint64_t* W, int64_t J, int64_t T, uint64_t seed, int mode,
+                                        uint64_t S_offset, uint64_t S_total, int64_t fiber_offset, int64_t* idx,
+                                        double* scale, const tucker_opts* opts);
+
+/* One CholeskyQR pass X = Q F (X, Q: I x L column-major device arrays, I >= L,
+ * not aliased): the orthonormalisation between power steps of the factored
+ * power scheme (C_n = X_q F_{q-1} ... F_1, remark after Algorithm 1, Strategy
+ * A). F: device array of L*L doubles receiving the packed upper triangle (FP64
+ * for F64 data, double-float pairs for F32 data) as tucker_leading_factor_chain reads it. */
+tucker_status tucker_cholqr(const void* X, tucker_dtype dt, int64_t I, int64_t L, void* Q, double* F,
+                            const tucker_opts* opts);
+
+/* U (I x R) = the R leading left singular vectors of C = X F_{nf-1} ... F_0
+ * (remark after Algorithm 5), with the factors as written by tucker_cholqr
+ * (device, nfactors slots of L*L doubles, F_0 first), sign-fixed as
+ * tucker_leading_factor. */
+tucker_status tucker_leading_factor_chain(const void* X, tucker_dtype dt, int64_t I, int64_t L, int64_t R,
+                                          const double* factors, int nfactors, void* U, const tucker_opts* opts);
+
+/* The factor of Algorithms 4/5 from a gathered sample: U (I x R) = the R
+ * leading left singular vectors of (C' C'^T)^q Omega, C' (I x T, column-major
+ * device array) the rescaled sampled fibers, Omega the mode's Gaussian
+ * (L = min(R + P, I) columns, Philox stream of `mode`), evaluated as the drivers
+ * evaluate it (in orthonormalised half steps when T >= L). Paper form only. */
+tucker_status tucker_sample_factor(const void* Cp, tucker_dtype dt, int64_t I, int64_t T, int64_t R, int32_t P,
+                                   int32_t q, uint64_t seed, int mode, void* U, const tucker_opts* opts);
+
 /* ---------------------------------------------------------------- allocation-free variant
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot allocate device memory while they run (memory reserved once at start,

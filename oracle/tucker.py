@@ -86,11 +86,13 @@ def fiber_weights(M: np.ndarray, prob: str) -> np.ndarray:
     return np.sum(M.astype(np.float64) ** 2, axis=0)
 
 
-def quantize_weights(w: np.ndarray) -> np.ndarray:
+def quantize_weights(w: np.ndarray, wmax: float = None) -> np.ndarray:
     """Integer weights W_j = ceil(w_j / max(w) * 2^24) (0 for w_j = 0); all ones
-    when every w_j is zero."""
+    when every w_j is zero. With `wmax` given, that value replaces max(w): the
+    largest weight over every part of a partitioned set of fibers."""
     w = np.asarray(w, dtype=np.float64)
-    wmax = float(np.max(w)) if w.size else 0.0
+    if wmax is None:
+        wmax = float(np.max(w)) if w.size else 0.0
     if wmax <= 0.0:
         return np.ones(w.shape, dtype=np.uint64)
     W = np.ceil((w / wmax) * float(1 << QUANT_BITS))
@@ -123,6 +125,40 @@ def randsample(W: np.ndarray, T: int, seed: int, mode: int):
                 lo = mid + 1
         idx[t] = lo
         p = float(int(W[lo])) / float(S)
+        scale[t] = 1.0 / math.sqrt(float(T) * p)
+    return idx, scale
+
+
+def randsample_slab(W: np.ndarray, T: int, seed: int, mode: int, S_offset: int, S_total: int,
+                    fiber_offset: int):
+    """RANDSAMPLE (Section 3.2) resolved by one part of a partition of the
+    fibers: this part holds global fibers fiber_offset .. fiber_offset + len(W) - 1
+    whose weights W cover [S_offset, S_offset + sum W) of the total S_total.
+    Draw t lands here when S_offset <= v_t < S_offset + sum W, v_t as in
+    randsample; it then gets its global index and 1/sqrt(T p); other draws get
+    index -1 and scale 0 (another part resolves them)."""
+    W = np.asarray(W, dtype=np.uint64)
+    cdf, acc = [], 0
+    for wj in W.tolist():
+        acc += int(wj)
+        cdf.append(acc)
+    words = philox.sampling_words(seed, mode, T)
+    idx = np.full(T, -1, dtype=np.int64)
+    scale = np.zeros(T, dtype=np.float64)
+    for t, r in enumerate(words):
+        v = (r * S_total) >> 64
+        if not (S_offset <= v < S_offset + acc):
+            continue
+        u = v - S_offset
+        lo, hi = 0, len(cdf) - 1
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if cdf[mid] > u:
+                hi = mid
+            else:
+                lo = mid + 1
+        idx[t] = lo + fiber_offset
+        p = float(int(W[lo])) / float(S_total)
         scale[t] = 1.0 / math.sqrt(float(T) * p)
     return idx, scale
 

@@ -84,6 +84,11 @@ _SIGS = {
     "tucker_ttm": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _INT, _VP, _P(Opts)],
     "tucker_relative_error": [_VP, _INT, _P(_I64), _INT, _P(_I32), _P(_VP), _VP, _P(_DBL), _P(Opts)],
     "tucker_power_step_noalloc": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _VP, _P(Opts)],
+    "tucker_quantize_weights_max": [_VP, _I64, _DBL, _VP, _P(Opts)],
+    "tucker_sample_fibers_slab": [_VP, _I64, _I64, _U64, _INT, _U64, _U64, _I64, _VP, _VP, _P(Opts)],
+    "tucker_cholqr": [_VP, _INT, _I64, _I64, _VP, _VP, _P(Opts)],
+    "tucker_leading_factor_chain": [_VP, _INT, _I64, _I64, _I64, _VP, _INT, _VP, _P(Opts)],
+    "tucker_sample_factor": [_VP, _INT, _I64, _I64, _I64, _I32, _I32, _U64, _INT, _VP, _P(Opts)],
     "tucker_server_create": [_P(ServerOpts), _P(_VP)],
     "tucker_server_submit": [_VP, _P(Request), _P(_U64)],
     "tucker_server_wait": [_VP, _U64, _I64, _P(_INT)],
@@ -416,6 +421,69 @@ def gather_fibers(A, dims, mode, idx, scale, stream=None):
                                                               idx.data_ptr(), scale.data_ptr(), T, out.data_ptr(),
                                                               C.byref(o)))
     return out[:, :T]
+
+
+def quantize_weights_max(w, wmax, stream=None):
+    """tucker_quantize_weights_max: integer weights against a given largest weight."""
+    if w.dtype != torch.float64 or not w.is_contiguous():
+        raise ValueError("w must be a contiguous float64 vector")
+    W = torch.empty(w.numel(), dtype=torch.int64, device=w.device)   # uint64 bits
+    o = make_opts(stream=stream)
+    _check("tucker_quantize_weights_max", lib().tucker_quantize_weights_max(w.data_ptr(), w.numel(), float(wmax),
+                                                                            W.data_ptr(), C.byref(o)))
+    return W
+
+
+def sample_fibers_slab(W, T, seed, mode, S_offset, S_total, fiber_offset, stream=None):
+    """tucker_sample_fibers_slab: the draws of one slab (idx -1 / scale 0 elsewhere)."""
+    if W.dtype != torch.int64 or not W.is_contiguous():
+        raise ValueError("W must be a contiguous int64 vector (the uint64 weights' bits)")
+    idx = torch.empty(max(T, 1), dtype=torch.int64, device=W.device)
+    scale = torch.empty(max(T, 1), dtype=torch.float64, device=W.device)
+    o = make_opts(stream=stream)
+    _check("tucker_sample_fibers_slab", lib().tucker_sample_fibers_slab(
+        W.data_ptr(), W.numel(), T, C.c_uint64(seed), mode, C.c_uint64(S_offset), C.c_uint64(S_total),
+        int(fiber_offset), idx.data_ptr(), scale.data_ptr(), C.byref(o)))
+    return idx[:T], scale[:T]
+
+
+def cholqr(X, stream=None):
+    """tucker_cholqr: (Q, F) with X = Q F, F the packed triangular factor (L*L doubles)."""
+    I, L = X.shape
+    if X.stride(0) != 1:
+        X = X.t().contiguous().t()
+    Q = factor_tensor(I, L, X.dtype, X.device)
+    F = torch.empty(L * L, dtype=torch.float64, device=X.device)
+    o = make_opts(stream=stream)
+    _check("tucker_cholqr", lib().tucker_cholqr(X.data_ptr(), _dt(X), I, L, Q.data_ptr(), F.data_ptr(), C.byref(o)))
+    return Q, F
+
+
+def leading_factor_chain(X, R, factors, stream=None):
+    """tucker_leading_factor_chain: U of C = X F_{k-1} ... F_0 (factors from cholqr, F_0 first)."""
+    I, L = X.shape
+    if X.stride(0) != 1:
+        X = X.t().contiguous().t()
+    U = factor_tensor(I, R, X.dtype, X.device)
+    Fs = torch.cat([f.reshape(-1) for f in factors]) if factors else torch.empty(1, dtype=torch.float64,
+                                                                                   device=X.device)
+    o = make_opts(stream=stream)
+    _check("tucker_leading_factor_chain", lib().tucker_leading_factor_chain(
+        X.data_ptr(), _dt(X), I, L, R, Fs.data_ptr(), len(factors), U.data_ptr(), C.byref(o)))
+    return U
+
+
+def sample_factor(Cp, R, P, q, seed, mode, stream=None):
+    """tucker_sample_factor: the factor of Algorithms 4/5 from a gathered sample C' (I x T)."""
+    I, T = Cp.shape
+    if Cp.stride(0) != 1:
+        Cp = Cp.t().contiguous().t()
+    U = factor_tensor(I, R, Cp.dtype, Cp.device)
+    o = make_opts(stream=stream)
+    _check("tucker_sample_factor", lib().tucker_sample_factor(Cp.data_ptr(), _dt(Cp), I, T, R, int(P), int(q),
+                                                              C.c_uint64(int(seed) & (2**64 - 1)), int(mode),
+                                                              U.data_ptr(), C.byref(o)))
+    return U
 
 
 def leading_factor(Cm, R, stream=None):

@@ -300,6 +300,10 @@ cudaError_t power_step(const T* M, const ModePlan& mp, const T* X_in, T* X_out, 
     return launch_power<T>(M, mp.mv, X_in, mp.L, X_out, w.partials, mp.pp, false, 0, 0, s);
 }
 
+template <typename T>
+cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t seed, int form, T* U,
+                          const Work& w, cudaStream_t s);
+
 // One mode's factor U (I_n x R_n) from the tensor B (view mp.v).
 template <typename T>
 cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, uint64_t seed, int form, T* U,
@@ -317,6 +321,14 @@ cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, 
         if (sample_out) TK_TRY(cudaMemcpyAsync(sample_out, w.idx, sizeof(int64_t) * mp.T, cudaMemcpyDefault, s));
         M = (const T*)w.Cp;
     }
+    return sketch_factor<T>(M, mp, n, q, seed, form, U, w, s);
+}
+
+// U from the sketch of M: the tensor's unfolding, or the gathered AMM sample
+// C' (I_n x T) when mp.T > 0.
+template <typename T>
+cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t seed, int form, T* U,
+                          const Work& w, cudaStream_t s) {
     const int L = mp.L;
     T* X0 = (T*)w.X0; T* X1 = (T*)w.X1; T* Q = (T*)w.Q;
     const size_t LL = (size_t)L * L;
@@ -873,6 +885,134 @@ tucker_status tucker_gather_fibers(const void* A, tucker_dtype dt, const int64_t
     if (e == cudaErrorInvalidValue) return TUCKER_ERR_INVALID_ARG;
     if (e != cudaSuccess) return from_cuda(e);
     return sync_status(o.stream, nullptr);
+}
+
+// ------------------------------------------------------------------ steps of a sharded call
+tucker_status tucker_quantize_weights_max(const double* w, int64_t J, double wmax, uint64_t* W,
+                                          const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!w || !W || J < 1 || !(wmax >= 0.0)) return TUCKER_ERR_INVALID_ARG;
+    cudaError_t e = launch_quantize_max(w, J, wmax, W, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_sample_fibers_slab(const uint64_t* W, int64_t J, int64_t T, uint64_t seed, int mode,
+                                        uint64_t S_offset, uint64_t S_total, int64_t fiber_offset, int64_t* idx,
+                                        double* scale, const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!W || J < 1 || T < 0 || (T > 0 && (!idx || !scale)) || mode < 0 || mode > 255 || S_total == 0 ||
+        S_offset >= S_total || fiber_offset < 0)
+        return TUCKER_ERR_INVALID_ARG;
+    Scratch sc;
+    if ((rs = sc.get(sample_scratch_bytes(J), o.stream)) != TUCKER_OK) return rs;
+    cudaError_t e = launch_sample_slab(W, J, T, seed, stream_id(1, mode), S_offset, S_total, fiber_offset, idx, scale,
+                                       sc.p, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_cholqr(const void* X, tucker_dtype dt, int64_t I, int64_t L, void* Q, double* F,
+                            const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!X || !Q || !F || X == Q || I < 1 || L < 1 || L > I) return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    if (L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
+    const int elem = dt == TUCKER_F64 ? 8 : 4;
+    const OrthPlan op = orth_plan(I, (int)L, num_sms());
+    Scratch sc;
+    if ((rs = sc.get(256 + orth_scratch_bytes(op, elem), o.stream)) != TUCKER_OK) return rs;
+    int* status = (int*)sc.p;
+    void* orth = (char*)sc.p + 256;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
+    if (e == cudaSuccess)
+        e = elem == 4 ? launch_cholqr<float>((const float*)X, (float*)Q, op, F, orth, status, o.stream)
+                      : launch_cholqr<double>((const double*)X, (double*)Q, op, F, orth, status, o.stream);
+    if (e == cudaErrorInvalidValue) return TUCKER_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, status);
+}
+
+tucker_status tucker_leading_factor_chain(const void* X, tucker_dtype dt, int64_t I, int64_t L, int64_t R,
+                                          const double* factors, int nfactors, void* U, const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!X || !U || I < 1 || L < 1 || R < 1 || R > L || L > I || nfactors < 0 || nfactors > 64 ||
+        (nfactors > 0 && !factors))
+        return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    if (L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
+    const int elem = dt == TUCKER_F64 ? 8 : 4;
+    const OrthPlan op = orth_plan(I, (int)L, num_sms());
+    if (!orth_supported(op, (int)R, elem)) return TUCKER_ERR_UNSUPPORTED;
+    const size_t slot = (size_t)L * L;
+    Arena a;
+    a.take(sizeof(int) * 64);
+    a.take(orth_scratch_bytes(op, elem));
+    a.take((size_t)I * L * elem);
+    a.take(sizeof(double) * slot * (size_t)(nfactors + 1));
+    Scratch sc;
+    if ((rs = sc.get(a.used, o.stream)) != TUCKER_OK) return rs;
+    Arena b;
+    b.base = (char*)sc.p;
+    b.cap = a.used;
+    int* status = (int*)b.take(sizeof(int) * 64);
+    void* orth = b.take(orth_scratch_bytes(op, elem));
+    void* Q1 = b.take((size_t)I * L * elem);
+    double* F = (double*)b.take(sizeof(double) * slot * (size_t)(nfactors + 1));
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
+    if (e == cudaSuccess && nfactors > 0)
+        e = cudaMemcpyAsync(F, factors, sizeof(double) * slot * (size_t)nfactors, cudaMemcpyDeviceToDevice, o.stream);
+    if (e == cudaSuccess)
+        e = elem == 4 ? launch_extract<float>((const float*)X, (float*)Q1, op, F, nfactors, (int)R, (float*)U, orth,
+                                              status, o.stream)
+                      : launch_extract<double>((const double*)X, (double*)Q1, op, F, nfactors, (int)R, (double*)U,
+                                               orth, status, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, status);
+}
+
+tucker_status tucker_sample_factor(const void* Cp, tucker_dtype dt, int64_t I, int64_t T, int64_t R, int32_t P,
+                                   int32_t q, uint64_t seed, int mode, void* U, const tucker_opts* opts) {
+    cudaGetLastError();
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!Cp || !U || I < 1 || T < 1 || R < 1 || R > I || P < 0 || q < 1 || mode < 0 || mode > 255)
+        return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    if (o.form != TUCKER_FORM_PAPER) return TUCKER_ERR_UNSUPPORTED;
+    // the sample as the unfolding of an I x T matrix whose T fibers are all sampled
+    const int elem = dt == TUCKER_F64 ? 8 : 4;
+    const int64_t dims[2] = {I, T};
+    const int32_t ranks[2] = {(int32_t)R, 1};
+    Plan p;
+    rs = make_plan(false, elem, dims, 2, ranks, P, q, T, o, p);
+    if (rs != TUCKER_OK) return rs;
+    Arena a;
+    Work w;
+    carve(p, a, w);
+    Scratch sc;
+    if ((rs = sc.get(a.used, o.stream)) != TUCKER_OK) return rs;
+    Arena b;
+    b.base = (char*)sc.p;
+    b.cap = a.used;
+    carve(p, b, w);
+    cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(int), o.stream);
+    if (e == cudaSuccess)
+        e = elem == 4 ? sketch_factor<float>((const float*)Cp, p.m[0], mode, q, seed, TUCKER_FORM_PAPER, (float*)U, w,
+                                             o.stream)
+                      : sketch_factor<double>((const double*)Cp, p.m[0], mode, q, seed, TUCKER_FORM_PAPER,
+                                              (double*)U, w, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, w.status);
 }
 
 tucker_status tucker_leading_factor(const void* C, tucker_dtype dt, int64_t I, int64_t L, int64_t R, void* U,

@@ -119,6 +119,11 @@ cudaError_t launch_sample(const uint64_t* W, int64_t J, int64_t T, uint64_t seed
 template <typename T>
 cudaError_t launch_gather(const T* A, const ModeView& v, const int64_t* idx, const double* scale,
                           int64_t T_, T* Cp, cudaStream_t s);
+// sharded calls: quantisation against a given maximum, and one slab's draws
+cudaError_t launch_quantize_max(const double* w, int64_t J, double wmax, uint64_t* W, cudaStream_t s);
+cudaError_t launch_sample_slab(const uint64_t* W, int64_t J, int64_t T_, uint64_t seed, uint32_t stream_id,
+                               uint64_t S_offset, uint64_t S_total, int64_t fiber_offset, int64_t* idx, double* scale,
+                               void* scratch, cudaStream_t s);
 
 // ---- orthonormalisation and extraction (kernels_orth.cu)
 struct OrthPlan {

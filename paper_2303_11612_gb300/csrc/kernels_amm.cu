@@ -129,6 +129,20 @@ __global__ void __launch_bounds__(kT) quantize_kernel(const double* __restrict__
     }
 }
 
+// W_j = ceil(w_j / wmax 2^24) with wmax given (the largest weight over every
+// slab of a sharded call); 0 for w_j = 0, all ones if wmax is 0.
+__global__ void __launch_bounds__(kT) quantize_value_kernel(const double* __restrict__ w, int64_t J, double wmax,
+                                                            uint64_t* __restrict__ W) {
+    for (int64_t j = blockIdx.x * (int64_t)kT + threadIdx.x; j < J; j += (int64_t)gridDim.x * kT) {
+        uint64_t q = 1;
+        if (wmax > 0.0) {
+            const double x = w[j];
+            q = x > 0.0 ? (uint64_t)ceil((x / wmax) * 16777216.0) : 0;
+        }
+        W[j] = q;
+    }
+}
+
 // ---------------------------------------------------------------- inclusive scan
 __device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t x, uint64_t* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -224,6 +238,38 @@ __global__ void __launch_bounds__(kT) sample_kernel(const uint64_t* __restrict__
     }
 }
 
+// The draws of one slab of a sharded call: the slab's fibers are global fibers
+// fiber_offset .. fiber_offset + J - 1 and its weights the CDF range
+// [S_offset, S_offset + S_slab) of the whole S_total. Draw t falls in this slab
+// when S_offset <= v_t < S_offset + S_slab; then idx[t] is its global index and
+// scale[t] its scale, else idx[t] = -1 and scale[t] = 0 (the owning slab sets them).
+__global__ void __launch_bounds__(kT) sample_slab_kernel(const uint64_t* __restrict__ cdf,
+                                                         const uint64_t* __restrict__ W, int64_t J, int64_t T_,
+                                                         uint64_t seed, uint32_t stream_id, uint64_t S_offset,
+                                                         uint64_t S_total, int64_t fiber_offset,
+                                                         int64_t* __restrict__ idx, double* __restrict__ scale) {
+    const uint64_t S_slab = cdf[J - 1];
+    for (int64_t t = blockIdx.x * (int64_t)kT + threadIdx.x; t < T_; t += (int64_t)gridDim.x * kT) {
+        const uint4 x = philox_block(seed, stream_id, (uint64_t)(t >> 1));
+        const uint64_t r = (t & 1) ? ((uint64_t)x.w << 32 | x.z) : ((uint64_t)x.y << 32 | x.x);
+        const uint64_t v = __umul64hi(r, S_total);
+        if (v < S_offset || v - S_offset >= S_slab) {
+            idx[t] = -1;
+            scale[t] = 0.0;
+            continue;
+        }
+        const uint64_t u = v - S_offset;
+        int64_t lo = 0, hi = J - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cdf[mid] > u) hi = mid; else lo = mid + 1;
+        }
+        idx[t] = lo + fiber_offset;
+        const double p = (double)W[lo] / (double)S_total;
+        scale[t] = 1.0 / sqrt((double)T_ * p);
+    }
+}
+
 // ---------------------------------------------------------------- rescaled gather
 template <typename T>
 __global__ void __launch_bounds__(kT) gather_kernel(const T* __restrict__ A, ModeView v,
@@ -283,6 +329,13 @@ cudaError_t launch_quantize(const double* w, int64_t J, int prob, uint64_t* W, v
     return cudaGetLastError();
 }
 
+cudaError_t launch_quantize_max(const double* w, int64_t J, double wmax, uint64_t* W, cudaStream_t s) {
+    if (J == 0) return cudaSuccess;
+    quantize_value_kernel<<<grid_for(J, kT, 8192), kT, 0, s>>>(w, J, wmax, W);
+    note_launch();
+    return cudaGetLastError();
+}
+
 size_t sample_scratch_bytes(int64_t J) {
     const int64_t nb = (J + kScanBlock - 1) / kScanBlock;
     return sizeof(uint64_t) * (size_t)J + sizeof(uint64_t) * (size_t)(nb + 1) + 512;
@@ -302,6 +355,26 @@ cudaError_t launch_sample(const uint64_t* W, int64_t J, int64_t T_, uint64_t see
     scan_final<<<(unsigned)nb, kT, 0, s>>>(W, J, bsum, cdf);
     note_launch();
     sample_kernel<<<grid_for(T_, kT, 4096), kT, 0, s>>>(cdf, W, J, T_, seed, stream_id, idx, scale);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_slab(const uint64_t* W, int64_t J, int64_t T_, uint64_t seed, uint32_t stream_id,
+                               uint64_t S_offset, uint64_t S_total, int64_t fiber_offset, int64_t* idx, double* scale,
+                               void* scratch, cudaStream_t s) {
+    if (T_ == 0 || J == 0) return cudaSuccess;
+    auto* cdf = reinterpret_cast<uint64_t*>(scratch);
+    auto* bsum = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(scratch) +
+                                             (((sizeof(uint64_t) * (size_t)J) + 255) & ~size_t(255)));
+    const int64_t nb = (J + kScanBlock - 1) / kScanBlock;
+    scan_block_sums<<<(unsigned)nb, kT, 0, s>>>(W, J, bsum);
+    note_launch();
+    scan_offsets<<<1, kT, 0, s>>>(bsum, nb);
+    note_launch();
+    scan_final<<<(unsigned)nb, kT, 0, s>>>(W, J, bsum, cdf);
+    note_launch();
+    sample_slab_kernel<<<grid_for(T_, kT, 4096), kT, 0, s>>>(cdf, W, J, T_, seed, stream_id, S_offset, S_total,
+                                                              fiber_offset, idx, scale);
     note_launch();
     return cudaGetLastError();
 }

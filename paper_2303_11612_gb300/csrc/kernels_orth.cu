@@ -91,26 +91,36 @@ template <> struct GramAcc<double> {
 };
 
 // Gram partial of this CTA's rows (packed upper triangle) -> partial[blockIdx.x].
+// Rows of X staged in shared memory per chunk of the Gram partial sums.
+constexpr int kGramChunk = 64;
+
 template <typename T, typename S>
 __device__ void gram_partial(const T* __restrict__ X, int64_t I, int L, int rows, S* __restrict__ partial,
                              unsigned char* smem) {
-    T* xs = reinterpret_cast<T*>(smem);   // [rows][L]
+    T* xs = reinterpret_cast<T*>(smem);   // [kGramChunk][L]
     const int64_t r0 = (int64_t)blockIdx.x * rows;
     const int nr = (int)max((int64_t)0, min((int64_t)rows, I - r0));
-    for (int e = threadIdx.x; e < nr * L; e += blockDim.x) {
-        const int r = e % nr, c = e / nr;
-        xs[r * L + c] = X[(int64_t)c * I + r0 + r];
-    }
-    __syncthreads();
     const int np = (int)packed_size(L);
     S* out = partial + (int64_t)blockIdx.x * np;
-    for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        int a = 0, rem = p;
-        while (rem >= L - a) { rem -= L - a; ++a; }
-        const int b = a + rem;
-        GramAcc<T> acc;
-        for (int r = 0; r < nr; ++r) acc.add(xs[r * L + a], xs[r * L + b]);
-        out[p] = acc.value();
+    // chunks of kGramChunk rows; each entry's chunk sums are added in chunk order
+    // by the thread that owns the entry
+    for (int c0 = 0; c0 < nr || c0 == 0; c0 += kGramChunk) {
+        const int cn = min(kGramChunk, nr - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cn * L; e += blockDim.x) {
+            const int r = e % cn, c = e / cn;
+            xs[r * L + c] = X[(int64_t)c * I + r0 + c0 + r];
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+            int a = 0, rem = p;
+            while (rem >= L - a) { rem -= L - a; ++a; }
+            const int b = a + rem;
+            GramAcc<T> acc;
+            for (int r = 0; r < cn; ++r) acc.add(xs[r * L + a], xs[r * L + b]);
+            out[p] = c0 == 0 ? acc.value() : out[p] + acc.value();
+        }
+        if (cn <= 0) break;
     }
 }
 
@@ -1154,12 +1164,15 @@ static int gram_rows(const OrthPlan& p) { return (int)((p.I + p.gram_blocks - 1)
 // Largest dynamic shared memory any orthonormalisation kernel may take.
 static constexpr size_t kSmemCap = 220 * 1024;
 
+static size_t gram_stage_bytes(const OrthPlan& p, int elem) {
+    return (size_t)elem * (size_t)std::min(gram_rows(p), kGramChunk) * p.L;
+}
 static size_t gram_chol_smem(const OrthPlan& p, int elem) {
     const size_t np = packed_size(p.L);
-    return std::max((size_t)elem * (size_t)gram_rows(p) * p.L, 8 * (3 * np + (size_t)p.L));
+    return std::max(gram_stage_bytes(p, elem), 8 * (3 * np + (size_t)p.L));
 }
 static size_t extract_smem(const OrthPlan& p, int R, int elem) {
-    return std::max(xlayout(p.L, R, elem).total, (size_t)elem * (size_t)gram_rows(p) * p.L);
+    return std::max(xlayout(p.L, R, elem).total, gram_stage_bytes(p, elem));
 }
 static size_t finish_smem(int R, int elem, int64_t I) { return flayout(R, elem, I).total; }
 // The final pass's shared memory with U staged in it, or 0 when that does not fit.
@@ -1249,7 +1262,7 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
     // U^T U by a grid of CTAs (the final pass repairs U only when it is not
     // orthonormal to 8 eps, which a one-CTA Gram over I rows would take long to tell)
     int* ok = sc.flag + 8;
-    const size_t usm = (size_t)sizeof(T) * (size_t)rows * R;
+    const size_t usm = (size_t)sizeof(T) * (size_t)std::min(rows, kGramChunk) * R;
     cudaFuncSetAttribute(ugram_check_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usm);
     ugram_check_kernel<T><<<p.gram_blocks, kST, usm, s>>>(U, p.I, R, rows, (S*)sc.partial, sc.ticket, ok);
     note_launch();

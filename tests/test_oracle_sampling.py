@@ -158,3 +158,29 @@ def test_nearly_optimal_weights_minimise_the_enumerated_amm_error():
     assert _expected_amm_error(M, norms / norms.sum()) > best * 1.01
     u = np.full(p.shape, 1.0 / p.size)
     assert _expected_amm_error(M, u) > best * 1.01
+
+
+@pytest.mark.parametrize("parts", [1, 2, 3, 5])
+def test_slab_draws_partition_the_global_draws(parts):
+    """RANDSAMPLE resolved part by part over a partition of the fibers (each
+    part quantised against the global largest weight, its CDF range offset by
+    the earlier parts' totals) gives, over the parts, exactly the single-call
+    indices and scales: the sharded sampler's definition."""
+    w = np.abs(np.random.default_rng(7).standard_normal(50)) ** 3
+    w[[3, 17]] = 0.0
+    T = 400
+    W = ot.quantize_weights(w)
+    idx, scale = ot.randsample(W, T, seed=9, mode=2)
+    bounds = np.linspace(0, w.size, parts + 1).astype(int)
+    Ws = [ot.quantize_weights(w[a:b], wmax=float(np.max(w))) for a, b in zip(bounds[:-1], bounds[1:])]
+    assert np.array_equal(np.concatenate(Ws), W)
+    totals = [int(x.sum()) for x in Ws]
+    got_i = np.full(T, -1, dtype=np.int64)
+    got_s = np.zeros(T)
+    for k, (a, b) in enumerate(zip(bounds[:-1], bounds[1:])):
+        i, s = ot.randsample_slab(Ws[k], T, 9, 2, sum(totals[:k]), sum(totals), a)
+        mine = i >= 0
+        assert not np.any(got_i[mine] >= 0)                 # every draw resolved by one part only
+        got_i[mine], got_s[mine] = i[mine], s[mine]
+    assert np.array_equal(got_i, idx)
+    assert np.array_equal(got_s, scale)
