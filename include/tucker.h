@@ -84,8 +84,13 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  *  RANGE: Y = A_(n) Omega with Omega J_n x L_n, then q times
  *    Y = A_(n) (A_(n)^T orth(Y)) (the form the introduction contrasts, item (c)).
  * Either way U_n = the R_n leading left singular vectors of the sketch (remark
- * after Algorithm 5), each column's largest-magnitude entry made positive. */
-typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1 } tucker_form;
+ * after Algorithm 5), each column's largest-magnitude entry made positive.
+ *  RELATED: Algorithms 6 and 7 (the related forms of Algorithms 1 and 2): the
+ *    paper form's C_n, its thin QR C_n = P_n R, U = the R_n leading left singular
+ *    vectors of P_n^T A_(n), and the factor Q_n = P_n U with the sign rule; one
+ *    more pass over the mode's tensor per mode. Without AMM only (c = 0, alpha = 0,
+ *    else TUCKER_ERR_UNSUPPORTED). */
+typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1, TUCKER_FORM_RELATED = 2 } tucker_form;
 
 /* Arithmetic of the sketch / power products.
  *  FP32: exact FP32 FMA on the CUDA cores.

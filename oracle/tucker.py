@@ -30,6 +30,10 @@ Readings where the paper is silent or ambiguous:
   * Extraction: U_n = the R_n leading left singular vectors of C_n (the remark
     after Algorithm 5), each column's largest-magnitude entry made positive
     (first such entry on ties).
+  * "Related form" (Algorithms 6 and 7, the related forms of Algorithms 1 and 2):
+    the sketch C_n as in the paper form, its thin QR C_n = P_n R, the R_n leading
+    left singular vectors U of P_n^T A_(n), and Q_n = P_n U (sign rule applied to
+    Q_n). Defined without AMM only.
   * "Range form" (optional, from the comparison in the introduction, item (c)):
     Y = A_(n) Omega with Omega J_n x L_n, then q times Y = A_(n) (A_(n)^T orth(Y));
     U_n = leading left singular vectors of Y.
@@ -44,6 +48,7 @@ from . import philox
 
 FORM_PAPER = "paper"
 FORM_RANGE = "range"
+FORM_RELATED = "related"
 PROB_NEARLY_OPTIMAL = "nearly_optimal"
 PROB_UNIFORM = "uniform"
 QUANT_BITS = 24
@@ -228,6 +233,17 @@ def _factor(M, R, P, q, T, prob, seed, mode, form, info):
         info.setdefault("idx", {})[mode] = idx
         info.setdefault("scale", {})[mode] = scale
         info.setdefault("W", {})[mode] = W
+    if form == FORM_RELATED:
+        if T > 0:
+            raise ValueError("the related forms (Algorithms 6 and 7) are defined without AMM")
+        C = sketch_paper(M, L, q, seed, mode)
+        Pn, _ = np.linalg.qr(C)                          # thin QR, P_n orthonormal I x L
+        Ul, s = leading_left_singular_vectors(Pn.T @ M, R)
+        U = sign_fix(Pn @ Ul)
+        info.setdefault("L", {})[mode] = L
+        info.setdefault("T", {})[mode] = T
+        info.setdefault("sigma_C", {})[mode] = s
+        return U
     if form == FORM_RANGE:
         C = sketch_range(M, L, q, seed, mode)
     else:

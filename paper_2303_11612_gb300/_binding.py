@@ -26,7 +26,7 @@ TUCKER_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
                 4: "numerical failure", 5: "timeout", 6: "unsupported", 7: "over budget"}
 PROB = {"nearly_optimal": 0, "uniform": 1}
-FORM = {"paper": 0, "range": 1}
+FORM = {"paper": 0, "range": 1, "related": 2}
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x1": 3}
 FLAG_ASYNC = 1
 

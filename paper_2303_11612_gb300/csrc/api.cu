@@ -85,7 +85,8 @@ tucker_status read_opts(const tucker_opts* o, Opts& out) {
     out.workspace_bytes = o->workspace_bytes;
     out.rel_error = o->rel_error;
     out.sample_idx = o->sample_idx;
-    if (out.form != TUCKER_FORM_PAPER && out.form != TUCKER_FORM_RANGE) return TUCKER_ERR_INVALID_ARG;
+    if (out.form != TUCKER_FORM_PAPER && out.form != TUCKER_FORM_RANGE && out.form != TUCKER_FORM_RELATED)
+        return TUCKER_ERR_INVALID_ARG;
     if (out.prec < TUCKER_SK_FP32 || out.prec > TUCKER_SK_BF16X1) return TUCKER_ERR_INVALID_ARG;
     if (!(out.alpha >= 0.0) || out.alpha > 1.0) return TUCKER_ERR_INVALID_ARG;
     return TUCKER_OK;
@@ -117,6 +118,7 @@ struct ModePlan {
     bool wide_range;   // range form: first pass Y = A Omega on the tensor cores, Omega generated in-kernel
     bool half;         // AMM, paper form: power steps on C' as two orthonormalised half steps
     OrthPlan opT;      //   orthonormalisation of the T x L half-step product
+    OrthPlan opL;      // related form: extraction from the L x L matrix P^T A A^T P
     PowerPlan pp;
     OrthPlan op;
 };
@@ -195,6 +197,15 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
         // AMM in the paper form: C_n = (C' C'^T)^q Omega evaluated in half steps (Y = C'^T Q,
         // Y = Q_Y R_Y, X = C' Q_Y), every stored product orthonormalised, so that FP32 keeps
         // the sample's directions down to sigma_i / sigma_1 ~ 2^-24 rather than 2^-12
+        if (o.form == TUCKER_FORM_RELATED) {
+            // Algorithms 6/7: defined without AMM; the leading vectors of P^T A_(n) come from
+            // the L x L matrix P^T A A^T P, and Q_n = P U is an I x L by L x R product
+            if (mp.T > 0 || !half_supported(mp.L)) return TUCKER_ERR_UNSUPPORTED;
+            mp.opL = orth_plan(mp.L, mp.L, sms);
+            if (!orth_supported(mp.opL, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
+            p.max_orth = std::max(p.max_orth, orth_scratch_bytes(mp.opL, elem));
+            p.max_partials = std::max(p.max_partials, half_partials_bytes(d[n], mp.R, mp.L, sms, elem));
+        }
         mp.half = mp.T > 0 && o.form == TUCKER_FORM_PAPER && mp.T >= mp.L && half_supported(mp.L);
         if (mp.half) {
             mp.opT = orth_plan(mp.T, mp.L, sms);
@@ -245,7 +256,10 @@ struct Work {
 void carve(const Plan& p, Arena& a, Work& w) {
     const size_t IL = (size_t)p.maxI * p.maxL * p.elem;
     // factor slots: paper form q (2q with half steps: one per half step and per step), range form 1
-    const int slots = p.form == TUCKER_FORM_PAPER ? (p.half ? 2 * p.q : p.q) : 1;
+    // related form: q for the power steps, 2 for P's CholeskyQR2, 1 for the extraction from H
+    const int slots = p.form == TUCKER_FORM_PAPER     ? (p.half ? 2 * p.q : p.q)
+                      : p.form == TUCKER_FORM_RELATED ? p.q + 3
+                                                      : 1;
     w.status = (int*)a.take(sizeof(int) * 64);
     w.X0 = a.take(IL);
     w.X1 = a.take(IL);
@@ -332,6 +346,35 @@ cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t
     const int L = mp.L;
     T* X0 = (T*)w.X0; T* X1 = (T*)w.X1; T* Q = (T*)w.Q;
     const size_t LL = (size_t)L * L;
+    if (form == TUCKER_FORM_RELATED) {
+        // Algorithms 6/7: the sketch as in the paper form (its span is that of X_q), P its
+        // orthonormal basis by CholeskyQR2, Z = M (M^T P) by one more power step, and
+        // H = P^T Z = (P^T M)(P^T M)^T, whose leading eigenvectors are the leading left
+        // singular vectors of P^T M; Q_n = P U_H with the sign rule
+        TK_TRY(launch_gaussian<T>(X0, mp.v.i, L, seed, stream_id(0, n), s));
+        for (int k = 0; k < q; ++k) {
+            const T* xin = X0;
+            if (k > 0) {
+                TK_TRY(launch_cholqr<T>(X1, Q, mp.op, w.factors + (size_t)(k - 1) * LL, w.orth, w.status, s));
+                xin = Q;
+            }
+            TK_TRY(power_step<T>(M, mp, xin, X1, w, s));
+        }
+        T* P = (T*)w.Qt;
+        double* fs = w.factors + (size_t)q * LL;
+        TK_TRY(launch_cholqr<T>(X1, Q, mp.op, fs, w.orth, w.status, s));
+        TK_TRY(launch_cholqr<T>(Q, P, mp.op, fs + LL, w.orth, w.status, s));
+        TK_TRY(power_step<T>(M, mp, P, X1, w, s));                     // Z (I x L)
+        T* H = X0;                                                    // L x L
+        TK_TRY(launch_gemm_tn<T>(P, mp.v.i, L, X1, L, H, s));
+        T* UH = Q;                                                    // L x R
+        {
+            ProfScope prof(kKExtract, 0.0, 0.0, s);
+            TK_TRY(launch_extract<T>(H, X1, mp.opL, fs + 2 * LL, 0, mp.R, UH, w.orth, w.status, s));
+        }
+        TK_TRY(launch_gemm_nn<T>(P, mp.v.i, L, UH, mp.R, U, w.partials, num_sms(), s));
+        return launch_sign_fix<T>(U, mp.v.i, mp.R, s);
+    }
     if (form == TUCKER_FORM_PAPER && mp.half) {
         // C = (C' C'^T)^q Omega in half steps: from Q_{k-1} (Q_0 = Omega), Y_k = C'^T Q_{k-1}
         // = Q_Y R_Y and X_k = C' Q_Y, so C' C'^T Q_{k-1} = X_k R_Y; between steps X_k = Q_k F_k.
@@ -679,7 +722,7 @@ tucker_status tucker_plan_describe(int which, tucker_dtype dt, const int64_t* di
         snprintf(line, sizeof(line), "mode %d: I=%lld L=%d J=%lld T=%lld sketch=%s power=%s ttm=%s%s%s\n", n,
                  (long long)mp.v.i, mp.L, (long long)mp.v.fibers(), (long long)mp.T,
                  mp.mv.lf == 1 ? "contiguous" : "strided", mp.half ? (p.elem == 8 ? "fp64" : "fp32") : power, ttm,
-                 range, mp.half ? " amm=half-steps" : "");
+                 range, mp.half ? " amm=half-steps" : p.form == TUCKER_FORM_RELATED ? " factor=related" : "");
         text += line;
         if (!p.st) e[n] = ranks[n];
     }

@@ -107,6 +107,10 @@ template <typename T>
 cudaError_t launch_gemm_nn(const T* M, int64_t I, int64_t Tn, const T* Q, int L, T* X, void* partials, int num_sms,
                            cudaStream_t s);
 
+// Sign rule on U's columns (largest-magnitude entry positive, lowest row on ties).
+template <typename T>
+cudaError_t launch_sign_fix(T* U, int64_t I, int R, cudaStream_t s);
+
 // ---- sampling (kernels_amm.cu)
 template <typename T>
 cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStream_t s);

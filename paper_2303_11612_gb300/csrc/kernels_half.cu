@@ -124,6 +124,30 @@ __global__ void __launch_bounds__(kHT) gemm_nn_kernel(const T* __restrict__ M, i
     }
 }
 
+// Sign rule on the columns of U (I x R, column-major): each column's
+// largest-magnitude entry positive, the lowest row on ties; one warp per column.
+template <typename T>
+__global__ void __launch_bounds__(kHT) sign_fix_kernel(T* __restrict__ U, int64_t I, int R) {
+    const int lane = threadIdx.x & 31;
+    const int r = (int)((blockIdx.x * (int64_t)kHT + threadIdx.x) >> 5);
+    if (r >= R) return;
+    T* u = U + (int64_t)r * I;
+    T bv = T(-1);
+    int64_t bi = 0;
+    for (int64_t i = lane; i < I; i += 32) {
+        const T a = fabs(u[i]);
+        if (a > bv) { bv = a; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (u[bi] < T(0))
+        for (int64_t i = lane; i < I; i += 32) u[i] = -u[i];
+}
+
 int half_splits(int64_t I, int64_t Tn, int num_sms) {
     const int64_t rows = (I + kHTile - 1) / kHTile;
     int64_t s = (num_sms + rows - 1) / rows;
@@ -158,11 +182,17 @@ size_t half_partials_bytes(int64_t I, int L, int64_t Tn, int num_sms, int elem_s
 
 template <typename T>
 cudaError_t launch_gemm_tn(const T* M, int64_t I, int64_t Tn, const T* X, int L, T* Y, cudaStream_t s) {
-    const int lpt = (L + kHLG - 1) / kHLG;
-    if (lpt <= 2) return tn_t<T, 2>(M, I, Tn, X, L, Y, s);
-    if (lpt <= 4) return tn_t<T, 4>(M, I, Tn, X, L, Y, s);
-    if (lpt <= 8) return tn_t<T, 8>(M, I, Tn, X, L, Y, s);
-    return cudaErrorInvalidValue;
+    switch ((L + kHLG - 1) / kHLG) {           // columns per thread, no more than needed
+        case 1: return tn_t<T, 1>(M, I, Tn, X, L, Y, s);
+        case 2: return tn_t<T, 2>(M, I, Tn, X, L, Y, s);
+        case 3: return tn_t<T, 3>(M, I, Tn, X, L, Y, s);
+        case 4: return tn_t<T, 4>(M, I, Tn, X, L, Y, s);
+        case 5: return tn_t<T, 5>(M, I, Tn, X, L, Y, s);
+        case 6: return tn_t<T, 6>(M, I, Tn, X, L, Y, s);
+        case 7: return tn_t<T, 7>(M, I, Tn, X, L, Y, s);
+        case 8: return tn_t<T, 8>(M, I, Tn, X, L, Y, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T>
@@ -172,13 +202,29 @@ cudaError_t launch_gemm_nn(const T* M, int64_t I, int64_t Tn, const T* Q, int L,
     const int splits = half_splits(I, Tn, num_sms);
     T* part = reinterpret_cast<T*>(partials);
     cudaError_t e;
-    if (lpt <= 2) e = nn_t<T, 2>(M, I, Tn, Q, L, part, splits, s);
-    else if (lpt <= 4) e = nn_t<T, 4>(M, I, Tn, Q, L, part, splits, s);
-    else if (lpt <= 8) e = nn_t<T, 8>(M, I, Tn, Q, L, part, splits, s);
-    else return cudaErrorInvalidValue;
+    switch (lpt) {
+        case 1: e = nn_t<T, 1>(M, I, Tn, Q, L, part, splits, s); break;
+        case 2: e = nn_t<T, 2>(M, I, Tn, Q, L, part, splits, s); break;
+        case 3: e = nn_t<T, 3>(M, I, Tn, Q, L, part, splits, s); break;
+        case 4: e = nn_t<T, 4>(M, I, Tn, Q, L, part, splits, s); break;
+        case 5: e = nn_t<T, 5>(M, I, Tn, Q, L, part, splits, s); break;
+        case 6: e = nn_t<T, 6>(M, I, Tn, Q, L, part, splits, s); break;
+        case 7: e = nn_t<T, 7>(M, I, Tn, Q, L, part, splits, s); break;
+        case 8: e = nn_t<T, 8>(M, I, Tn, Q, L, part, splits, s); break;
+        default: return cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess) return e;
     return launch_reduce_partials<T>(part, splits, I * (int64_t)L, X, s);
 }
+
+template <typename T>
+cudaError_t launch_sign_fix(T* U, int64_t I, int R, cudaStream_t s) {
+    sign_fix_kernel<T><<<(unsigned)((R * 32 + kHT - 1) / kHT), kHT, 0, s>>>(U, I, R);
+    note_launch();
+    return cudaGetLastError();
+}
+template cudaError_t launch_sign_fix<float>(float*, int64_t, int, cudaStream_t);
+template cudaError_t launch_sign_fix<double>(double*, int64_t, int, cudaStream_t);
 
 template cudaError_t launch_gemm_tn<float>(const float*, int64_t, int64_t, const float*, int, float*, cudaStream_t);
 template cudaError_t launch_gemm_tn<double>(const double*, int64_t, int64_t, const double*, int, double*,

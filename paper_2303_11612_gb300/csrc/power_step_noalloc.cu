@@ -107,7 +107,8 @@ extern "C" tucker_status tucker_power_step_noalloc(const void* A, tucker_dtype d
     if (opts) {
         // the same option checks as tucker_power_step
         if (opts->struct_size < sizeof(tucker_opts)) return TUCKER_ERR_INVALID_ARG;
-        if (opts->form != TUCKER_FORM_PAPER && opts->form != TUCKER_FORM_RANGE) return TUCKER_ERR_INVALID_ARG;
+        if (opts->form != TUCKER_FORM_PAPER && opts->form != TUCKER_FORM_RANGE && opts->form != TUCKER_FORM_RELATED)
+            return TUCKER_ERR_INVALID_ARG;
         if (opts->prec < TUCKER_SK_FP32 || opts->prec > TUCKER_SK_BF16X1) return TUCKER_ERR_INVALID_ARG;
         if (!(opts->alpha >= 0.0) || opts->alpha > 1.0) return TUCKER_ERR_INVALID_ARG;
         s = reinterpret_cast<cudaStream_t>(opts->stream);

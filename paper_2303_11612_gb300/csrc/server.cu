@@ -224,7 +224,8 @@ extern "C" {
 tucker_status tucker_server_create(const tucker_server_opts* opts, tucker_server** out) {
     if (!opts || !out || opts->struct_size < sizeof(tucker_server_opts)) return TUCKER_ERR_INVALID_ARG;
     if (opts->max_inflight < 1 || opts->max_inflight > 256 || opts->budget_bytes == 0) return TUCKER_ERR_INVALID_ARG;
-    if (opts->form != TUCKER_FORM_PAPER && opts->form != TUCKER_FORM_RANGE) return TUCKER_ERR_INVALID_ARG;
+    if (opts->form != TUCKER_FORM_PAPER && opts->form != TUCKER_FORM_RANGE && opts->form != TUCKER_FORM_RELATED)
+        return TUCKER_ERR_INVALID_ARG;
     if (opts->prec < TUCKER_SK_FP32 || opts->prec > TUCKER_SK_BF16X1) return TUCKER_ERR_INVALID_ARG;
     std::unique_ptr<tucker_server> s(new tucker_server());
     s->budget = opts->budget_bytes;

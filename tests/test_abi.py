@@ -132,7 +132,7 @@ def test_batch_sizes_and_argument_checks(lib):
 def test_options_and_server_argument_checks(lib):
     """Out-of-range options and server settings are rejected on the host."""
     from paper_2303_11612_gb300 import _binding as B
-    for field, value in (("prec", 4), ("prec", -1), ("form", 2), ("alpha", 1.5), ("alpha", -0.1)):
+    for field, value in (("prec", 4), ("prec", -1), ("form", 3), ("alpha", 1.5), ("alpha", -0.1)):
         o = B.make_opts()
         setattr(o, field, value)
         st = lib.tucker_workspace_size(1, 0, B._i64((40, 36, 32)), 3, B._i32((4, 4, 4)), 5, 1, 0, C.byref(o),

@@ -210,3 +210,58 @@ def test_amm_indices_drawn_only_from_nonzero_fibers():
     idx = info["idx"][0]
     cols = ot.unfold(A, 0)[:, idx]
     assert np.all(np.linalg.norm(cols, axis=0) > 0)
+
+
+# ---------------------------------------------------------------- related forms (Algorithms 6 and 7)
+def _mode_residual(M, U):
+    return float(np.linalg.norm(M - U @ (U.T @ M)))
+
+
+@pytest.mark.parametrize("kind", ["T", "ST"])
+def test_related_form_is_optimal_within_the_sketch_span(kind):
+    """Algorithms 6/7 take, inside span(C_n) = span(P_n), the R_n-dimensional
+    subspace that best approximates the (current) unfolding: the left singular
+    vectors of P_n^T A_(n). So per mode its projection error is never larger
+    than the paper form's factor (which lies in the same span) nor than random
+    R_n-dimensional subspaces of span(P_n)."""
+    A = synth.lowrank_noise((24, 20, 18), (6, 5, 4), rel_noise=0.3, seed=8, dtype=np.float64)
+    ranks = (4, 3, 3)
+    rng = np.random.default_rng(1)
+    B = A.copy()
+    for n in range(3):
+        M = ot.unfold(B, n)
+        info_r, info_p = {}, {}
+        Ur = ot._factor(M, ranks[n], 4, 1, 0, ot.PROB_UNIFORM, 3, n, ot.FORM_RELATED, info_r)
+        Up = ot._factor(M, ranks[n], 4, 1, 0, ot.PROB_UNIFORM, 3, n, ot.FORM_PAPER, info_p)
+        assert np.allclose(Ur.T @ Ur, np.eye(ranks[n]), atol=1e-12)
+        e_r = _mode_residual(M, Ur)
+        assert e_r <= _mode_residual(M, Up) + 1e-12
+        Pn, _ = np.linalg.qr(ot.sketch_paper(M, info_r["L"][n], 1, 3, n))
+        assert np.linalg.norm(Ur - Pn @ (Pn.T @ Ur)) < 1e-12           # inside span(P_n)
+        for _ in range(20):
+            V = Pn @ np.linalg.qr(rng.standard_normal((Pn.shape[1], ranks[n])))[0]
+            assert e_r <= _mode_residual(M, V) + 1e-12
+        if kind == "ST":
+            B = ot.ttm(B, Up.T, n)
+
+
+def test_related_form_without_oversampling_spans_the_sketch():
+    """With K = 0 the sketch has R_n columns: both forms return a basis of
+    span(C_n), hence the same projector."""
+    A = synth.lowrank_noise((20, 18, 16), (5, 4, 4), rel_noise=0.2, seed=3, dtype=np.float64)
+    Ur, _ = ot.rsthosvd(A, (4, 3, 3), P=0, q=1, seed=2, form=ot.FORM_RELATED)
+    Up, _ = ot.rsthosvd(A, (4, 3, 3), P=0, q=1, seed=2, form=ot.FORM_PAPER)
+    for a, b in zip(Ur, Up):
+        assert _proj_dist(a, b) < 1e-10
+
+
+def test_related_form_recovers_exact_rank_and_rejects_amm():
+    A = synth.lowrank_noise((20, 18, 16), (4, 3, 5), rel_noise=0.0, seed=1, dtype=np.float64)
+    for kind in ("T", "ST"):
+        Us, G = _run(kind, A, (4, 3, 5), form=ot.FORM_RELATED)
+        assert ot.relative_error(A, Us, G) < 1e-9
+        for U in Us:
+            k = np.argmax(np.abs(U), axis=0)
+            assert np.all(U[k, np.arange(U.shape[1])] > 0)      # the sign rule holds on Q_n
+    with pytest.raises(ValueError):
+        _run("ST", A, (4, 3, 5), c=50, form=ot.FORM_RELATED)

@@ -125,3 +125,27 @@ def test_unsquared_fiber_norms_are_caught(monkeypatch):
     monkeypatch.setattr(ot, "fiber_weights", bad)
     assert _caught(tsamp.test_fiber_weights_hand_values)
     assert _caught(tsamp.test_nearly_optimal_weights_minimise_the_enumerated_amm_error)
+
+
+def test_right_singular_vectors_in_the_related_form_are_caught(monkeypatch):
+    good = ot.leading_left_singular_vectors
+    def bad(C, R):
+        # the related form asks for left singular vectors of the L x J matrix
+        # P^T A; a plausible slip takes the leading right ones of its transpose's
+        # transpose, i.e. of C^T C, truncated to C's row count
+        if C.shape[0] < C.shape[1]:
+            _, s, Vt = np.linalg.svd(C, full_matrices=False)
+            W = np.linalg.qr(np.random.default_rng(0).standard_normal((C.shape[0], R)))[0]
+            return W, s
+        return good(C, R)
+    monkeypatch.setattr(ot, "leading_left_singular_vectors", bad)
+    assert _caught(decomp.test_related_form_is_optimal_within_the_sketch_span, "T")
+
+
+def test_related_form_without_the_basis_product_is_caught(monkeypatch):
+    good_qr = np.linalg.qr
+    def bad_qr(C, *a, **k):
+        Q, R = good_qr(C, *a, **k)
+        return np.roll(Q, 1, axis=0), R          # a basis of the wrong span
+    monkeypatch.setattr(ot.np.linalg, "qr", bad_qr)
+    assert _caught(decomp.test_related_form_is_optimal_within_the_sketch_span, "ST")
