@@ -117,6 +117,7 @@ struct ModePlan {
     bool wide_split;   //   with split-bf16 operands (else single-pass bf16)
     bool wide_range;   // range form: first pass Y = A Omega on the tensor cores, Omega generated in-kernel
     bool half;         // AMM, paper form: power steps on C' as two orthonormalised half steps
+    bool half_tc;      //   on the tensor cores (split bf16; the tensor-core forms, large samples)
     OrthPlan opT;      //   orthonormalisation of the T x L half-step product
     OrthPlan opL;      // related form: extraction from the L x L matrix P^T A A^T P
     PowerPlan pp;
@@ -207,6 +208,11 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
             p.max_partials = std::max(p.max_partials, half_partials_bytes(d[n], mp.R, mp.L, sms, elem));
         }
         mp.half = mp.T > 0 && o.form == TUCKER_FORM_PAPER && mp.T >= mp.L && half_supported(mp.L);
+        // the tensor-core forms run the half steps of large samples (beyond the fused
+        // kernels' tiles) on the tensor cores in split bf16, FP32-class like the FMA form
+        mp.half_tc = mp.half && o.prec != TUCKER_SK_FP32 && elem == 4 && wide_supported(mp.mv, mp.L) &&
+                     !power_tc_supported(mp.mv, mp.L);
+        if (mp.half_tc) p.max_partials = std::max(p.max_partials, wide_power_scratch_bytes(mp.mv, mp.L, sms));
         if (mp.half) {
             mp.opT = orth_plan(mp.T, mp.L, sms);
             p.half = true;
@@ -390,10 +396,20 @@ cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t
                 ++f;
                 xin = Q;
             }
-            TK_TRY(launch_gemm_tn<T>(M, mp.v.i, mp.T, xin, L, Y, s));
+            cudaError_t e = cudaErrorNotSupported;
+            if constexpr (sizeof(T) == 4) {
+                if (mp.half_tc) e = launch_wide_tn(M, mp.mv, xin, L, Y, w.partials, w.status, num_sms(), s);
+            }
+            if (e == cudaErrorNotSupported) e = launch_gemm_tn<T>(M, mp.v.i, mp.T, xin, L, Y, s);
+            TK_TRY(e);
             TK_TRY(launch_cholqr<T>(Y, QY, mp.opT, w.factors + (size_t)f * LL, w.orth, w.status, s));
             ++f;
-            TK_TRY(launch_gemm_nn<T>(M, mp.v.i, mp.T, QY, L, X1, w.partials, num_sms(), s));
+            e = cudaErrorNotSupported;
+            if constexpr (sizeof(T) == 4) {
+                if (mp.half_tc) e = launch_wide_nn(M, mp.mv, QY, L, X1, w.partials, w.status, num_sms(), s);
+            }
+            if (e == cudaErrorNotSupported) e = launch_gemm_nn<T>(M, mp.v.i, mp.T, QY, L, X1, w.partials, num_sms(), s);
+            TK_TRY(e);
         }
         ProfScope prof(kKExtract, 0.0, 0.0, s);
         return launch_extract<T>(X1, Q, mp.op, w.factors, f, mp.R, U, w.orth, w.status, s);
@@ -721,7 +737,8 @@ tucker_status tucker_plan_describe(int which, tucker_dtype dt, const int64_t* di
         char line[256];
         snprintf(line, sizeof(line), "mode %d: I=%lld L=%d J=%lld T=%lld sketch=%s power=%s ttm=%s%s%s\n", n,
                  (long long)mp.v.i, mp.L, (long long)mp.v.fibers(), (long long)mp.T,
-                 mp.mv.lf == 1 ? "contiguous" : "strided", mp.half ? (p.elem == 8 ? "fp64" : "fp32") : power, ttm,
+                 mp.mv.lf == 1 ? "contiguous" : "strided",
+                 mp.half ? (mp.half_tc ? "wide-split-bf16" : p.elem == 8 ? "fp64" : "fp32") : power, ttm,
                  range, mp.half ? " amm=half-steps" : p.form == TUCKER_FORM_RELATED ? " factor=related" : "");
         text += line;
         if (!p.st) e[n] = ranks[n];

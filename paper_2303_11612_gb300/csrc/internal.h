@@ -96,6 +96,13 @@ cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_
                               bool range, uint64_t seed, uint32_t stream_id, void* scratch, int* status, int num_sms,
                               cudaStream_t s);
 
+// half steps of the AMM sketch on the tensor cores (split bf16), scratch as launch_power_wide:
+// Y (J x L, column-major) = A_(n)^T X, and X_out = A_(n) Q with Q J x L column-major
+cudaError_t launch_wide_tn(const float* A, const ModeView& v, const float* X, int L, float* Y, void* scratch,
+                           int* status, int num_sms, cudaStream_t s);
+cudaError_t launch_wide_nn(const float* A, const ModeView& v, const float* Q, int L, float* X_out, void* scratch,
+                           int* status, int num_sms, cudaStream_t s);
+
 // ---- half steps of the power scheme on the gathered AMM sample (kernels_half.cu)
 bool half_supported(int L);
 size_t half_partials_bytes(int64_t I, int L, int64_t Tn, int num_sms, int elem_size);

@@ -123,6 +123,34 @@ __global__ void image_kernel(const float* __restrict__ Mp, int I, int K_out, int
     }
 }
 
+// B operand image of wide_power2_kernel from a column-major FP32 matrix Q (Tn x L):
+// chunk c of 64 rows t at c Np 128 bytes of each part, element (l, jj = t % 64) at
+// (jj / 8) (Np / 8) 128 + (l / 8) 128 + (jj % 8) 16 + (l % 8) 2; zero beyond Tn and L.
+template <bool SPLIT>
+__global__ void bimage_kernel(const float* __restrict__ Q, int64_t Tn, int L, int Np, int64_t chunks,
+                              unsigned char* __restrict__ hi, unsigned char* __restrict__ lo) {
+    const int ng = Np / 8;
+    const int64_t total = chunks * 64 * ng;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int jj = (int)(e % 64);
+        const int64_t rest = e / 64;
+        const int lg = (int)(rest % ng);
+        const int64_t ch = rest / ng;
+        const int64_t t = ch * 64 + jj;
+        float x[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int l = 8 * lg + w;
+            x[w] = (t < Tn && l < L) ? __ldg(Q + t + Tn * (int64_t)l) : 0.f;
+        }
+        uint4 h, lw;
+        cvt8<SPLIT>(x, h, lw);
+        const size_t off = (size_t)ch * Np * 128 + (size_t)(jj >> 3) * ng * 128 + (size_t)lg * 128 + (jj & 7) * 16;
+        *reinterpret_cast<uint4*>(hi + off) = h;
+        if (SPLIT) *reinterpret_cast<uint4*>(lo + off) = lw;
+    }
+}
+
 // ------------------------------------------------------------------ wide_ttm_kernel
 constexpr int kAJB = 128;                  // fibers per tile
 constexpr int kABox = kAJB * 128;          // FP32 box: 32 values i x 128 fibers = 16 KB
@@ -159,7 +187,8 @@ WideALayout wide_a_layout(int I, int K_out, bool split) {
     return t;
 }
 
-// OUT 0: out[j K_out + o] (FP32). OUT 1: W image for wide_power2_kernel's B
+// OUT 2: out[j + J o] (FP32, column-major J x K_out: the half-step product
+// Y = C'^T X of the AMM sketch). OUT 0: out[j K_out + o] (FP32). OUT 1: W image for wide_power2_kernel's B
 // operand: 64-fiber chunk c = j / 64 at c * Np * 128 bytes of each part's array,
 // element (l, jj = j % 64) at (jj / 8) (Np / 8) 128 + (l / 8) 128 + (jj % 8) 16 +
 // (l % 8) 2 (core matrices of 8 fibers x 8 columns, columns contiguous).
@@ -374,12 +403,16 @@ __global__ void __launch_bounds__(kAThreads, 1)
             const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * Np);
             // the W image covers whole 64-fiber chunks: fibers J .. of the last one
             // are written too (as zeros: their tensor columns load as zeros)
-            const int64_t jend = OUT == 0 ? J : (J + 63) / 64 * 64;
+            const int64_t jend = OUT == 1 ? (J + 63) / 64 * 64 : J;
             for (int c0 = 0; c0 < Np; c0 += 16) {
                 uint32_t r[16];
                 tc::tmem_ld16(ta + (uint32_t)c0, r);
                 if (j >= jend) continue;
-                if (OUT == 0 && STRIDED) {
+                if (OUT == 2) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        if (c0 + c < K_out) out[j + J * (int64_t)(c0 + c)] = __uint_as_float(r[c]);
+                } else if (OUT == 0 && STRIDED) {
                     // out(l, o, r) = out[l + o Lf + r Lf K_out]: lanes write consecutive l
                     const int64_t rr = j / lf, l = j - rr * lf;
                     float* o = out + l + rr * lf * K_out;
@@ -872,6 +905,73 @@ cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb.bytes);
         k<<<(int)(R * tb.groups), kBThreads, tb.bytes, s>>>(map, I, J, L, tb.Np, whi, wlo, seed, stream_id, part,
                                                               tb.groups, tb.nb, chunks, v.lf, status);
+        note_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return launch_reduce_partials<float>(part, (int)R, (int64_t)I * L, X_out, s);
+}
+
+}  // namespace tk
+
+namespace tk {
+
+// Y (J x L, column-major FP32) = A_(n)^T X: the first half of a half step of
+// the AMM sketch, on the tensor cores (split bf16). Scratch as launch_power_wide.
+cudaError_t launch_wide_tn(const float* A, const ModeView& v, const float* X, int L, float* Y, void* scratch,
+                           int* status, int num_sms, cudaStream_t s) {
+    if (!wide_supported(v, L) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
+    const int I = (int)v.i;
+    const int64_t J = v.fibers();
+    const WideALayout ta = wide_a_layout(I, L, true);
+    CUtensorMap map;
+    if (!make_fiber_map(&map, A, v, kAJB)) return cudaErrorNotSupported;
+    unsigned char* img = reinterpret_cast<unsigned char*>(scratch);
+    image_kernel<true><<<grid_for(((int64_t)ta.nu * ta.Np * 8 + 255) / 256, 4 * num_sms), 256, 0, s>>>(
+        X, I, L, 1, I, ta.Np, ta.nu, img);
+    note_launch();
+    const int64_t tiles = (J + kAJB - 1) / kAJB;
+    const double elems = (double)I * (double)J;
+    ProfScope prof(kKPowerWide1, (elems + (double)J * L) * sizeof(float), 2.0 * elems * L, s);
+    auto k = v.lf > 1 ? wide_ttm_kernel<true, 2, true> : wide_ttm_kernel<true, 2, false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ta.bytes);
+    k<<<grid_for(tiles, num_sms), kAThreads, ta.bytes, s>>>(map, I, J, img, L, ta.Np, Y, nullptr, nullptr, tiles,
+                                                              ta.nu, v.lf, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// X_out (I x L) = A_(n) Q with Q (J x L, column-major FP32): the second half of a
+// half step, on the tensor cores (split bf16). Scratch as launch_power_wide.
+cudaError_t launch_wide_nn(const float* A, const ModeView& v, const float* Q, int L, float* X_out, void* scratch,
+                           int* status, int num_sms, cudaStream_t s) {
+    if (!wide_supported(v, L) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
+    const int I = (int)v.i;
+    const int64_t J = v.fibers();
+    const WideALayout ta = wide_a_layout(I, L, true);
+    const WideBLayout tb = wide_b_layout(I, L, true);
+    const int64_t chunks = (J + kBJB - 1) / kBJB;
+    const int64_t R = std::max<int64_t>(1, std::min<int64_t>(chunks, num_sms / tb.groups));
+    unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
+    p += round256((size_t)ta.nu * ta.ubytes);
+    unsigned char* whi = p;
+    p += round256((size_t)chunks * ta.Np * 128);
+    unsigned char* wlo = p;
+    p += round256((size_t)chunks * ta.Np * 128);
+    float* part = reinterpret_cast<float*>(p);
+    bimage_kernel<true><<<grid_for((chunks * 64 * (ta.Np / 8) + 255) / 256, 4 * num_sms), 256, 0, s>>>(
+        Q, J, L, ta.Np, chunks, whi, wlo);
+    note_launch();
+    CUtensorMap map;
+    if (!make_fiber_map(&map, A, v, kBJB)) return cudaErrorNotSupported;
+    const double elems = (double)I * (double)J;
+    {
+        ProfScope prof(kKPowerWide2, elems * sizeof(float) + (double)J * tb.Np * 2 * tb.parts * tb.groups,
+                       2.0 * elems * L, s);
+        auto k = v.lf > 1 ? wide_power2_kernel<true, false, true> : wide_power2_kernel<true, false, false>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb.bytes);
+        k<<<(int)(R * tb.groups), kBThreads, tb.bytes, s>>>(map, I, J, L, tb.Np, whi, wlo, 0, 0, part, tb.groups,
+                                                              tb.nb, chunks, v.lf, status);
         note_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

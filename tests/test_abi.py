@@ -310,10 +310,13 @@ def test_plan_describe_pins_the_dispatch_rules():
         assert [w2[n]["power"] for n in range(3)] == ["wide-split-bf16", "wide-split-bf16", "split-bf16"]
     wt = _modes(B.plan_describe("T", big, bigr, P=16, prec="bf16x1"))
     assert [wt[n]["power"] for n in range(3)] == ["wide-bf16x1"] * 3          # every mode sketches the input
-    # AMM in the paper form: the gathered sample is sketched in half steps in the
-    # data's precision (FMA), in every form
+    # AMM in the paper form: the gathered sample is sketched in orthonormalised half
+    # steps, FP32-class: split bf16 on the tensor cores for samples beyond the fused
+    # tiles in the tensor-core forms, FMA otherwise
     wa = _modes(B.plan_describe("ST", big, bigr, P=16, c=20000, prec="bf16x1"))
-    assert [wa[n]["power"] for n in range(3)] == ["fp32"] * 3
+    assert [wa[n]["power"] for n in range(3)] == ["wide-split-bf16", "wide-split-bf16", "fp32"]
+    wf = _modes(B.plan_describe("ST", big, bigr, P=16, c=20000, prec="fp32"))
+    assert [wf[n]["power"] for n in range(3)] == ["fp32"] * 3
     assert [wa[n]["amm"] for n in range(3)] == ["half-steps"] * 3
     assert [int(wa[n]["T"]) for n in range(3)] == [20000, 20000, 64 * 64]
     # no half steps where the sample has fewer fibers than the sketch has columns
