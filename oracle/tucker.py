@@ -345,3 +345,48 @@ def tail_energy_bound(A, ranks) -> float:
         s = np.linalg.svd(unfold(A, n), compute_uv=False)
         tot += float(np.sum(s[ranks[n]:] ** 2))
     return tot
+
+
+# ---------------------------------------------------------------- fixed precision (Problem 2)
+def rsthosvd_adaptive(A, eps, P=0, q=1, seed=0, L0=8, form=FORM_PAPER):
+    """Problem 2 (concluding section): multilinear ranks and factors with
+    ||A - A x_1 Q_1 Q_1^T ... x_N Q_N Q_N^T||_F <= eps ||A||_F.
+
+    Reading (the paper poses the problem only): ST-HOSVD order 1..N. The
+    truncation error is the sum of the energies the modes discard (the equality
+    behind Eq. 23 / Lemma 8), so mode n may discard
+        budget_n = (eps^2 ||A||^2 - discarded so far) / (N - n + 1).
+    For mode n a sketch of L columns (L = L0, doubled up to I_n) gives U_L (all
+    L leading left singular vectors of the paper form's sketch), the exact
+    energies e_k = ||u_k^T B_(n)||^2 and the smallest r with
+    ||B||^2 - sum_{k<=r} e_k <= budget_n; without such r the sketch is widened,
+    and at L = I_n nothing is discarded. Q_n = U_L(:, 1:r), B <- B x_n Q_n^T.
+    Returns (Qs, G, ranks)."""
+    B = np.asarray(A, dtype=np.float64)
+    N = B.ndim
+    total = frobenius(B) ** 2
+    allowed = (eps ** 2) * total
+    spent = 0.0
+    Qs, ranks = [], []
+    for n in range(N):
+        M = unfold(B, n)
+        I = M.shape[0]
+        normB = float(np.sum(M * M))
+        budget = (allowed - spent) / (N - n)
+        L = min(L0, I)
+        while True:
+            info = {}
+            U = _factor(M, L, 0, q, 0, PROB_UNIFORM, seed, n, form, info)    # all L vectors of an L-column sketch
+            e = np.sum((U.T @ M) ** 2, axis=1)
+            resid = normB - np.cumsum(e)
+            ok = np.nonzero(resid <= budget)[0]
+            if ok.size or L == I:
+                r = int(ok[0]) + 1 if ok.size else I
+                break
+            L = min(2 * L, I)
+        Q = U[:, :r]
+        spent += normB - float(np.sum(e[:r]))
+        Qs.append(Q)
+        ranks.append(r)
+        B = ttm(B, Q.T, n)
+    return Qs, B, ranks

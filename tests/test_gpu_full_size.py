@@ -4,10 +4,11 @@ on side streams, several decompositions in flight).
 
 - 400^3 FP32 (the benchmark's tensors), randomized ST-HOSVD R = 20, P = 10:
   FP32 form |RE - RE_oracle| <= 1e-5 and projectors <= 1e-4 on the low-rank
-  tensor (gap at R), split-BF16 within 1e-3; on the Hilbert tensor FP32
-  arithmetic has a floor above the FP64 oracle (see the test), and the FP64
-  data path is never worse than the oracle by more than 1e-5; orthonormal
-  factors throughout; sampled fiber indices of mode 1 equal to the oracle's.
+  tensor (gap at R), split-BF16 within 1e-4 and single-pass BF16 within 1e-3;
+  on the Hilbert tensor per-form bars against the oracle (see the test), and
+  the FP64 data path never worse than the oracle by more than 1e-5;
+  orthonormal factors throughout; sampled fiber indices of mode 1 equal to the
+  oracle's.
 - 96^4 FP32 with a geometrically decaying core, ST-HOSVD R = 16, P = 8, q = 2.
 - 1024 x 1024 x 512 FP32 video-like tensor (2.1 GB), ST-HOSVD R = (64, 64, 32),
   P = 16, q = 1, with and without AMM (c = 20000): against the FP64 oracle run
@@ -98,14 +99,18 @@ def test_benchmark_workload_400cubed(tk, bench_tensors, prec):
                 assert abs(re - reo) <= bar, (kw, re, reo)
         else:
             # Hilbert: its mode-n singular values fall by orders of magnitude per
-            # index, so a power-step output (singular values sigma_i^2) loses every
-            # direction with sigma_i / sigma_1 below ~2.4e-4 to FP32 rounding. The
-            # FP64 oracle reaches RE 9.1e-5 at q = 2 and 2.3e-4 with AMM at q = 1;
-            # FP32 arithmetic reaches ~2e-4 and ~1.5e-3; the FP64 data path is at
-            # least as accurate as the oracle (test below). The single-pass bf16
-            # sketch keeps only directions whose sigma_i^2 / sigma_1^2 exceeds its
-            # rounding (2^-8): RE ~2.2e-3 with AMM at q = 1 (bar 3e-3)
-            assert re <= (3e-3 if prec == "bf16x1" else 2e-3), (kw, re, reo)
+            # index. Bars against the oracle, per form (measured in brackets):
+            #   q = 2, no sampling: a full power step carries sigma_i^2, so FP32
+            #   loses the directions with sigma_i / sigma_1 below ~2^-12 the FP64
+            #   oracle keeps: FP32 1.2e-4 (8e-5), tensor-core forms 2e-4 (1.2-1.4e-4);
+            #   q = 1 with AMM: the sample is sketched in orthonormalised half steps
+            #   and the factored extraction never forms C_n, so every form resolves
+            #   directions the oracle's explicit FP64 C_n loses: never worse than the
+            #   oracle, within 2.5e-4 of it (1.7e-4 better)
+            if kw["c"]:
+                assert re <= reo + 1e-5 and abs(re - reo) <= 2.5e-4, (prec, kw, re, reo)
+            else:
+                assert abs(re - reo) <= (1.2e-4 if prec == "fp32" else 2e-4), (prec, kw, re, reo)
         if kw["c"]:
             # mode 1 samples the input tensor itself: identical weights, identical draws
             assert np.array_equal(res[2][0].cpu().numpy(), info["idx"][0]), kw

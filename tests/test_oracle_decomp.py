@@ -265,3 +265,41 @@ def test_related_form_recovers_exact_rank_and_rejects_amm():
             assert np.all(U[k, np.arange(U.shape[1])] > 0)      # the sign rule holds on Q_n
     with pytest.raises(ValueError):
         _run("ST", A, (4, 3, 5), c=50, form=ot.FORM_RELATED)
+
+
+# ---------------------------------------------------------------- fixed precision (Problem 2)
+def test_adaptive_ranks_meet_the_tolerance_and_recover_exact_ranks():
+    """Problem 2: the returned decomposition meets ||A - Ahat|| <= eps ||A||; on a
+    tensor of exact multilinear rank the ranks found are that rank."""
+    A = synth.lowrank_noise((24, 20, 18), (4, 3, 5), rel_noise=0.0, seed=5, dtype=np.float64)
+    Qs, G, ranks = ot.rsthosvd_adaptive(A, 1e-9, q=1, seed=1, L0=4)
+    assert ranks == [4, 3, 5]
+    assert ot.relative_error(A, Qs, G) <= 1e-9
+    B = synth.lowrank_noise((24, 20, 18), (6, 5, 4), rel_noise=0.05, seed=6, dtype=np.float64)
+    for eps in (0.2, 0.1, 0.06):
+        Qs, G, ranks = ot.rsthosvd_adaptive(B, eps, q=2, seed=2, L0=2)
+        assert ot.relative_error(B, Qs, G) <= eps * (1 + 1e-12), (eps, ranks)
+        for Q in Qs:
+            assert np.allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-12)
+
+
+def test_adaptive_ranks_on_tendiag_follow_the_closed_form():
+    """tendiag: every unfolding has singular values |v_i| exactly (Section 6.3),
+    and after truncating modes 1..n-1 to r_1..r_{n-1} the next unfolding keeps
+    v_1..v_min(r). So the ranks are the closed-form minimal r meeting each
+    mode's budget: with budget_n = (eps^2 sum v^2 - spent) / (N - n + 1), r_n =
+    the least r with sum_{r < i <= m} v_i^2 <= budget_n over the m values left."""
+    v = 0.6 ** np.arange(12)
+    A = synth.tendiag(v, (20, 18, 16), seed=3)
+    eps = 0.05
+    _, _, ranks = ot.rsthosvd_adaptive(A, eps, q=3, seed=4, L0=2)
+    total = float(np.sum(v ** 2))
+    spent, m, want = 0.0, len(v), []
+    for n in range(3):
+        budget = (eps ** 2 * total - spent) / (3 - n)
+        tail = [float(np.sum(v[r:m] ** 2)) for r in range(m + 1)]
+        r = next(r for r in range(1, m + 1) if tail[r] <= budget)
+        want.append(r)
+        spent += tail[r]
+        m = r
+    assert ranks == want
