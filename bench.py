@@ -82,6 +82,13 @@ WORKLOADS = {
         which="T", dims=(100, 100, 100), ranks=(10, 10, 10), P=5, dtype="f64", copies=32, forms=["fp32"],
         flush_l2=True,
         variants=[dict(name="q1", gen="lowrank64", q=1, c=0, prob="uniform")]),
+    # a smaller tensor with the headline's mode-1 shapes (I_1 = 1024, L_1 = 80, R_1 = 64; 268 MB, still
+    # larger than L2): the case for profiler captures of the headline's kernels (--single only)
+    "video1024x256": dict(
+        desc="randomized ST-HOSVD of a 1024x256x256 FP32 video-like tensor, R=(64,64,32) P=16 q=1 (profiling case)",
+        which="ST", dims=(1024, 256, 256), ranks=(64, 64, 32), P=16, dtype="f32", copies=1, profile_only=True,
+        variants=[dict(name="q1", gen="video", q=1, c=0, prob="uniform"),
+                  dict(name="q1_amm20000_uniform", gen="video", q=1, c=20000, prob="uniform")]),
 }
 HEADLINE = "video1024"
 
@@ -512,6 +519,9 @@ def main():
                          "errors are within 1e-3 of the oracle's)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-secondary", action="store_true", help="headline workload only")
+    ap.add_argument("--copies", type=int, default=0,
+                    help="decompositions of each variant per step in the headline batch (0: the workload's "
+                         "default), every one on its own tensor")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel configurations (no tuning in the synchronous warm-up calls)")
     ap.add_argument("--single", default=None,
@@ -556,6 +566,8 @@ def main():
     forms = FORMS if args.prec == "all" else [args.prec]
 
     # ---- headline
+    if args.copies > 0:
+        WORKLOADS[HEADLINE]["copies"] = args.copies
     P, res = b.workload_line(HEADLINE, forms, args.steps)
     W = P["W"]
     ok = {p: r["re_within_1e_3_of_oracle"] for p, r in res.items()}

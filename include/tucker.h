@@ -165,6 +165,38 @@ tucker_status tucker_rsthosvd(const void* A, tucker_dtype dt, const int64_t* dim
                               tucker_prob prob, uint64_t seed, void* const* U, void* G,
                               const tucker_opts* opts);
 
+/* Fixed-precision problem (Problem 2, concluding section): multilinear ranks
+ * r_n and orthonormal factors Q_n with
+ *   ||A - A x_1 Q_1 Q_1^T ... x_N Q_N Q_N^T||_F <= eps ||A||_F,
+ * by randomized ST-HOSVD in processing order 1..N. The energies the modes
+ * discard add up exactly (each truncation projects the tensor the previous ones
+ * left), so mode n may discard (eps^2 ||A||^2 - energy discarded so far) / (N - n)
+ * (0-based n). Mode n sketches L columns (L = min(L0, I_n), doubled up to I_n)
+ * in the form opts->form with q power steps and no oversampling beyond L, takes
+ * all L leading left singular vectors U_L, the kept energies
+ * e_k = ||u_k^T B_(n)||^2 from Y = B x_n U_L^T, and the smallest r_n whose
+ * remainder ||B||^2 - (e_1 + ... + e_r) is within the mode's share; without one
+ * the sketch is widened, and at L = I_n nothing is discarded. Q_n = U_L(:, 1:r_n)
+ * and B becomes the first r_n slices of Y. Decisions are taken on the host in
+ * FP64 from energies summed in FP64 on the device; the call is synchronous.
+ *   A, dims, N, dt: the tensor (device memory)
+ *   eps   : relative tolerance, finite, >= 0
+ *   q     : power steps, >= 1; L0: first sketch width, >= 1
+ *   U     : host array of N device pointers, U[n] with room for I_n x I_n
+ *           elements; receives I_n x r_n (column-major)
+ *   G     : device buffer with room for I_1 ... I_N elements; receives the
+ *           r_1 x ... x r_N core (r_1 fastest)
+ *   ranks : host array of N, receives r_n
+ *   opts  : stream, prec, form, rel_error as for the drivers; the call
+ *           allocates its scratch itself (stream-ordered) and takes neither
+ *           opts->workspace nor TUCKER_FLAG_ASYNC (TUCKER_ERR_INVALID_ARG).
+ * Host pointers where device memory is required give
+ * TUCKER_ERR_INVALID_ARG; a sketch wider than the extraction supports (110
+ * columns) before the tolerance is met gives TUCKER_ERR_UNSUPPORTED. */
+tucker_status tucker_rsthosvd_adaptive(const void* A, tucker_dtype dt, const int64_t* dims, int N, double eps,
+                                       int32_t q, int32_t L0, uint64_t seed, void* const* U, void* G,
+                                       int32_t* ranks, const tucker_opts* opts);
+
 /* Scratch bytes a driver call needs. which = 0 (T-HOSVD) or 1 (ST-HOSVD). */
 tucker_status tucker_workspace_size(int which, tucker_dtype dt, const int64_t* dims, int N,
                                     const int32_t* ranks, int32_t P, int32_t q, int64_t c,
@@ -328,6 +360,15 @@ tucker_status tucker_leading_factor_chain(const void* X, tucker_dtype dt, int64_
  * evaluate it (in orthonormalised half steps when T >= L). Paper form only. */
 tucker_status tucker_sample_factor(const void* Cp, tucker_dtype dt, int64_t I, int64_t T, int64_t R, int32_t P,
                                    int32_t q, uint64_t seed, int mode, void* U, const tucker_opts* opts);
+
+/* Checks the bounded-wait path of the tensor-core kernels on the device (no
+ * counterpart in the paper): one CTA takes tensor memory, waits on an mbarrier
+ * that nothing completes for `iters` polls (1 .. 2^24), records the timeout in
+ * its status word exactly as the kernels do when a wait runs out, frees its
+ * tensor memory and returns; nothing is in flight, so nothing is drained.
+ * Returns TUCKER_ERR_TIMEOUT when that path works (the stream and the context
+ * stay usable), TUCKER_ERR_INVALID_ARG for iters out of range. */
+tucker_status tucker_check_wait_timeout(int32_t iters, const tucker_opts* opts);
 
 /* ---------------------------------------------------------------- allocation-free variant
  * The paper has no counterpart to this entry point; it exists for callers that

@@ -8,10 +8,10 @@ importing the binding builds the library if needed and raises if it cannot be
 loaded.
 """
 from ._binding import (  # noqa: F401
-    TuckerError, decompose, rthosvd, rsthosvd, workspace_size, plan_describe, factor_tensor, gaussian, power_step,
+    TuckerError, decompose, rthosvd, rsthosvd, rsthosvd_adaptive, workspace_size, plan_describe, factor_tensor, gaussian, power_step,
     range_sketch, fiber_norms, quantize_weights, sample_fibers, gather_fibers, leading_factor, ttm,
     relative_error, last_device_status, lib, exported_symbols, FLAG_ASYNC, launch_count, profile_enable,
     profile_read, Server, Batch, autotune_enable, autotune_entries,
 )
 
-__all__ = ["rthosvd", "rsthosvd", "decompose", "workspace_size", "plan_describe", "TuckerError", "Server", "Batch"]
+__all__ = ["rthosvd", "rsthosvd", "rsthosvd_adaptive", "decompose", "workspace_size", "plan_describe", "TuckerError", "Server", "Batch"]

@@ -13,6 +13,7 @@ core as a flat tensor in r_1-fastest order (``core.view(R_N, ..., R_1)``).
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 from typing import Optional, Sequence
 
@@ -89,6 +90,9 @@ _SIGS = {
     "tucker_cholqr": [_VP, _INT, _I64, _I64, _VP, _VP, _P(Opts)],
     "tucker_leading_factor_chain": [_VP, _INT, _I64, _I64, _I64, _VP, _INT, _VP, _P(Opts)],
     "tucker_sample_factor": [_VP, _INT, _I64, _I64, _I64, _I32, _I32, _U64, _INT, _VP, _P(Opts)],
+    "tucker_check_wait_timeout": [_I32, _P(Opts)],
+    "tucker_rsthosvd_adaptive": [_VP, _INT, _P(_I64), _INT, _DBL, _I32, _I32, _U64, _P(_VP), _VP, _P(_I32),
+                                 _P(Opts)],
     "tucker_server_create": [_P(ServerOpts), _P(_VP)],
     "tucker_server_submit": [_VP, _P(Request), _P(_U64)],
     "tucker_server_wait": [_VP, _U64, _I64, _P(_INT)],
@@ -333,6 +337,40 @@ def rthosvd(A, dims, ranks, **kw):
 
 def rsthosvd(A, dims, ranks, **kw):
     return decompose("ST", A, dims, ranks, **kw)
+
+
+def rsthosvd_adaptive(A, dims, eps, q=1, L0=8, seed=0, form="paper", prec="fp32", stream=None,
+                      want_rel_error=False):
+    """tucker_rsthosvd_adaptive (Problem 2): ranks chosen so that the relative
+    error is at most eps. A is a device tensor. Returns (U list of I_n x r_n,
+    G flat of prod(r_n), ranks[, rel_error])."""
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    if A.numel() != math.prod(dims):
+        raise ValueError("A must hold prod(dims) elements")
+    dev = A.device
+    Ubuf = [factor_tensor(I, I, A.dtype, dev) for I in dims]
+    Gbuf = torch.empty(math.prod(dims), dtype=A.dtype, device=dev)
+    ranks = (C.c_int32 * N)()
+    re = C.c_double(float("nan")) if want_rel_error else None
+    o = make_opts(form, prec, 0.0, stream, None, re, None, 0)
+    Uptrs = (C.c_void_p * N)(*[u.data_ptr() for u in Ubuf])
+    _check("tucker_rsthosvd_adaptive",
+           lib().tucker_rsthosvd_adaptive(A.data_ptr(), _dt(A), _i64(dims), N, float(eps), int(q), int(L0),
+                                          C.c_uint64(int(seed) & (2**64 - 1)), Uptrs, Gbuf.data_ptr(), ranks,
+                                          C.byref(o)))
+    r = [int(x) for x in ranks]
+    U = [u[:, :k] for u, k in zip(Ubuf, r)]
+    G = Gbuf[:math.prod(r)]
+    res = (U, G, r)
+    return res + (re.value,) if want_rel_error else res
+
+
+def check_wait_timeout(iters=1000, stream=None) -> int:
+    """tucker_check_wait_timeout: the status (an int, not raised) of a bounded
+    device wait that nothing completes; TUCKER_ERR_TIMEOUT (5) when the path works."""
+    o = make_opts(stream=stream)
+    return int(lib().tucker_check_wait_timeout(int(iters), C.byref(o)))
 
 
 def last_device_status() -> int:

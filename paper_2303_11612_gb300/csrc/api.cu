@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -140,6 +141,82 @@ struct Plan {
     int64_t inter_elems = 0;             // largest intermediate tensor of the TTM chain
 };
 
+// The plan of mode n of the tensor d (rank R, oversampling P, c samples): fills
+// p.m[n] and raises the plan's buffer maxima.
+tucker_status plan_mode(Plan& p, const int64_t* d, int N, int n, int64_t R, int32_t P, int64_t c, bool st, int elem,
+                        const Opts& o, int sms) {
+    ModePlan& mp = p.m[n];
+    mp.v = view_of(d, N, n);
+    mp.R = R;
+    mp.L = (int)std::min<int64_t>((int64_t)R + P, d[n]);
+    const int64_t J = mp.v.fibers();
+    mp.T = sample_count(c, o.alpha, J);
+    mp.mv = mp.T > 0 ? ModeView{1, d[n], mp.T} : mp.v;
+    if (d[n] > kMaxI || mp.L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
+    if (elem == 8 && d[n] > 512) return TUCKER_ERR_UNSUPPORTED;
+    mp.pp = power_plan(mp.mv, mp.L, elem, sms);
+    // tensor-core power steps where the tile fits: TF32 on contiguous fibers, split
+    // BF16 (also the TF32 form's choice for strided fibers); the FP32 kernel elsewhere.
+    // Single-pass BF16 sketches the input tensor only (every mode of T-HOSVD, the
+    // first of ST-HOSVD): ST-HOSVD's later modes see the truncated tensor, small by
+    // then, where the split form's accuracy costs little.
+    mp.tf32 = o.prec == TUCKER_SK_TF32 && elem == 4 && power_tf32_supported(mp.mv, mp.L);
+    mp.bf16x1 = o.prec == TUCKER_SK_BF16X1 && elem == 4 && (!st || n == 0) &&
+                power_bf16x1_supported(mp.mv, mp.L);
+    // beyond the fused kernels' tiles (I_n > 512 or wide sketches; contiguous fibers, the
+    // gathered AMM sample, or strides that are multiples of 32): two tensor-core passes,
+    // single-pass bf16 where the form sketches in single-pass BF16 (preferred there over
+    // the fused split kernel), split bf16 elsewhere
+    mp.wide_split = !(o.prec == TUCKER_SK_BF16X1 && (!st || n == 0));
+    mp.wide = o.prec != TUCKER_SK_FP32 && elem == 4 && !mp.tf32 && !mp.bf16x1 &&
+              wide_supported(mp.mv, mp.L) && (!mp.wide_split || !power_tc_supported(mp.mv, mp.L));
+    mp.tc = o.prec != TUCKER_SK_FP32 && elem == 4 && !mp.wide && power_tc_supported(mp.mv, mp.L);
+    if (mp.tc || mp.tf32 || mp.bf16x1)
+        p.max_partials = std::max(p.max_partials, power_tc_partials_bytes(mp.mv, mp.L, sms));
+    mp.wide_range = o.form == TUCKER_FORM_RANGE && o.prec != TUCKER_SK_FP32 && elem == 4 &&
+                    wide_supported(mp.mv, mp.L);
+    if (mp.wide || mp.wide_range)
+        p.max_partials = std::max(p.max_partials, wide_power_scratch_bytes(mp.mv, mp.L, sms));
+    if (o.prec != TUCKER_SK_FP32 && elem == 4 && st && !ttm_tc_supported(mp.v, mp.R) &&
+        wide_ttm_supported(mp.v, mp.R))
+        p.max_partials = std::max(p.max_partials, wide_ttm_scratch_bytes(mp.v, mp.R));
+    mp.op = orth_plan(d[n], mp.L, sms);
+    if (!orth_supported(mp.op, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
+    // AMM in the paper form: C_n = (C' C'^T)^q Omega evaluated in half steps (Y = C'^T Q,
+    // Y = Q_Y R_Y, X = C' Q_Y), every stored product orthonormalised, so that FP32 keeps
+    // the sample's directions down to sigma_i / sigma_1 ~ 2^-24 rather than 2^-12
+    if (o.form == TUCKER_FORM_RELATED) {
+        // Algorithms 6/7: defined without AMM; the leading vectors of P^T A_(n) come from
+        // the L x L matrix P^T A A^T P, and Q_n = P U is an I x L by L x R product
+        if (mp.T > 0 || !half_supported(mp.L)) return TUCKER_ERR_UNSUPPORTED;
+        mp.opL = orth_plan(mp.L, mp.L, sms);
+        if (!orth_supported(mp.opL, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
+        p.max_orth = std::max(p.max_orth, orth_scratch_bytes(mp.opL, elem));
+        p.max_partials = std::max(p.max_partials, half_partials_bytes(d[n], mp.R, mp.L, sms, elem));
+    }
+    mp.half = mp.T > 0 && o.form == TUCKER_FORM_PAPER && mp.T >= mp.L && half_supported(mp.L);
+    // the tensor-core forms run the half steps of large samples (beyond the fused
+    // kernels' tiles) on the tensor cores in split bf16, FP32-class like the FMA form
+    mp.half_tc = mp.half && o.prec != TUCKER_SK_FP32 && elem == 4 && wide_supported(mp.mv, mp.L) &&
+                 !power_tc_supported(mp.mv, mp.L);
+    if (mp.half_tc) p.max_partials = std::max(p.max_partials, wide_power_scratch_bytes(mp.mv, mp.L, sms));
+    if (mp.half) {
+        mp.opT = orth_plan(mp.T, mp.L, sms);
+        p.half = true;
+        p.maxTL = std::max(p.maxTL, mp.T * (int64_t)mp.L);
+        p.max_orth = std::max(p.max_orth, orth_scratch_bytes(mp.opT, elem));
+        p.max_partials = std::max(p.max_partials, half_partials_bytes(d[n], mp.L, mp.T, sms, elem));
+    }
+    p.maxI = std::max(p.maxI, d[n]);
+    p.maxL = std::max<int64_t>(p.maxL, mp.L);
+    p.maxJ = std::max(p.maxJ, J);
+    p.maxT = std::max(p.maxT, mp.T);
+    p.maxIT = std::max(p.maxIT, d[n] * mp.T);
+    p.max_partials = std::max(p.max_partials, power_partials_bytes(mp.pp, mp.mv, mp.L, elem));
+    p.max_orth = std::max(p.max_orth, orth_scratch_bytes(mp.op, elem));
+    return TUCKER_OK;
+}
+
 tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int32_t* ranks, int32_t P, int32_t q,
                         int64_t c, const Opts& o, Plan& p) {
     if (N < 1 || N > kMaxOrder || !dims || !ranks) return TUCKER_ERR_INVALID_ARG;
@@ -158,75 +235,8 @@ tucker_status make_plan(bool st, int elem, const int64_t* dims, int N, const int
     for (int n = 0; n < N; ++n) d[n] = p.dims[n] = dims[n];
     for (int n = 0; n < N; ++n) {
         for (int k = 0; k < N; ++k) p.cur[n][k] = d[k];
-        ModePlan& mp = p.m[n];
-        mp.v = view_of(d, N, n);
-        mp.R = ranks[n];
-        mp.L = (int)std::min<int64_t>((int64_t)ranks[n] + P, d[n]);
-        const int64_t J = mp.v.fibers();
-        mp.T = sample_count(c, o.alpha, J);
-        mp.mv = mp.T > 0 ? ModeView{1, d[n], mp.T} : mp.v;
-        if (d[n] > kMaxI || mp.L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
-        if (elem == 8 && d[n] > 512) return TUCKER_ERR_UNSUPPORTED;
-        mp.pp = power_plan(mp.mv, mp.L, elem, sms);
-        // tensor-core power steps where the tile fits: TF32 on contiguous fibers, split
-        // BF16 (also the TF32 form's choice for strided fibers); the FP32 kernel elsewhere.
-        // Single-pass BF16 sketches the input tensor only (every mode of T-HOSVD, the
-        // first of ST-HOSVD): ST-HOSVD's later modes see the truncated tensor, small by
-        // then, where the split form's accuracy costs little.
-        mp.tf32 = o.prec == TUCKER_SK_TF32 && elem == 4 && power_tf32_supported(mp.mv, mp.L);
-        mp.bf16x1 = o.prec == TUCKER_SK_BF16X1 && elem == 4 && (!st || n == 0) &&
-                    power_bf16x1_supported(mp.mv, mp.L);
-        // beyond the fused kernels' tiles (I_n > 512 or wide sketches; contiguous fibers, the
-        // gathered AMM sample, or strides that are multiples of 32): two tensor-core passes,
-        // single-pass bf16 where the form sketches in single-pass BF16 (preferred there over
-        // the fused split kernel), split bf16 elsewhere
-        mp.wide_split = !(o.prec == TUCKER_SK_BF16X1 && (!st || n == 0));
-        mp.wide = o.prec != TUCKER_SK_FP32 && elem == 4 && !mp.tf32 && !mp.bf16x1 &&
-                  wide_supported(mp.mv, mp.L) && (!mp.wide_split || !power_tc_supported(mp.mv, mp.L));
-        mp.tc = o.prec != TUCKER_SK_FP32 && elem == 4 && !mp.wide && power_tc_supported(mp.mv, mp.L);
-        if (mp.tc || mp.tf32 || mp.bf16x1)
-            p.max_partials = std::max(p.max_partials, power_tc_partials_bytes(mp.mv, mp.L, sms));
-        mp.wide_range = o.form == TUCKER_FORM_RANGE && o.prec != TUCKER_SK_FP32 && elem == 4 &&
-                        wide_supported(mp.mv, mp.L);
-        if (mp.wide || mp.wide_range)
-            p.max_partials = std::max(p.max_partials, wide_power_scratch_bytes(mp.mv, mp.L, sms));
-        if (o.prec != TUCKER_SK_FP32 && elem == 4 && st && !ttm_tc_supported(mp.v, mp.R) &&
-            wide_ttm_supported(mp.v, mp.R))
-            p.max_partials = std::max(p.max_partials, wide_ttm_scratch_bytes(mp.v, mp.R));
-        mp.op = orth_plan(d[n], mp.L, sms);
-        if (!orth_supported(mp.op, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
-        // AMM in the paper form: C_n = (C' C'^T)^q Omega evaluated in half steps (Y = C'^T Q,
-        // Y = Q_Y R_Y, X = C' Q_Y), every stored product orthonormalised, so that FP32 keeps
-        // the sample's directions down to sigma_i / sigma_1 ~ 2^-24 rather than 2^-12
-        if (o.form == TUCKER_FORM_RELATED) {
-            // Algorithms 6/7: defined without AMM; the leading vectors of P^T A_(n) come from
-            // the L x L matrix P^T A A^T P, and Q_n = P U is an I x L by L x R product
-            if (mp.T > 0 || !half_supported(mp.L)) return TUCKER_ERR_UNSUPPORTED;
-            mp.opL = orth_plan(mp.L, mp.L, sms);
-            if (!orth_supported(mp.opL, mp.R, elem)) return TUCKER_ERR_UNSUPPORTED;
-            p.max_orth = std::max(p.max_orth, orth_scratch_bytes(mp.opL, elem));
-            p.max_partials = std::max(p.max_partials, half_partials_bytes(d[n], mp.R, mp.L, sms, elem));
-        }
-        mp.half = mp.T > 0 && o.form == TUCKER_FORM_PAPER && mp.T >= mp.L && half_supported(mp.L);
-        // the tensor-core forms run the half steps of large samples (beyond the fused
-        // kernels' tiles) on the tensor cores in split bf16, FP32-class like the FMA form
-        mp.half_tc = mp.half && o.prec != TUCKER_SK_FP32 && elem == 4 && wide_supported(mp.mv, mp.L) &&
-                     !power_tc_supported(mp.mv, mp.L);
-        if (mp.half_tc) p.max_partials = std::max(p.max_partials, wide_power_scratch_bytes(mp.mv, mp.L, sms));
-        if (mp.half) {
-            mp.opT = orth_plan(mp.T, mp.L, sms);
-            p.half = true;
-            p.maxTL = std::max(p.maxTL, mp.T * (int64_t)mp.L);
-            p.max_orth = std::max(p.max_orth, orth_scratch_bytes(mp.opT, elem));
-            p.max_partials = std::max(p.max_partials, half_partials_bytes(d[n], mp.L, mp.T, sms, elem));
-        }
-        p.maxI = std::max(p.maxI, d[n]);
-        p.maxL = std::max<int64_t>(p.maxL, mp.L);
-        p.maxJ = std::max(p.maxJ, J);
-        p.maxT = std::max(p.maxT, mp.T);
-        p.maxIT = std::max(p.maxIT, d[n] * mp.T);
-        p.max_partials = std::max(p.max_partials, power_partials_bytes(mp.pp, mp.mv, mp.L, elem));
-        p.max_orth = std::max(p.max_orth, orth_scratch_bytes(mp.op, elem));
+        const tucker_status ms = plan_mode(p, d, N, n, ranks[n], P, c, st, elem, o, sms);
+        if (ms != TUCKER_OK) return ms;
         if (st) d[n] = ranks[n];
         if (st && n < N - 1) p.inter_elems = std::max(p.inter_elems, prod(d, N));
     }
@@ -661,6 +671,136 @@ bool mode_args_ok(const void* A, const int64_t* dims, int N, int mode) {
     return true;
 }
 
+// ------------------------------------------------------------------ fixed-precision ranks
+// Problem 2 (concluding section): ranks r_n and factors Q_n with
+// ||A - A x_1 Q_1 Q_1^T ... x_N Q_N Q_N^T||_F <= eps ||A||_F, in ST-HOSVD order.
+// The energies the modes discard add up exactly (each truncation is an
+// orthogonal projection of the tensor the previous ones left), so mode n
+// (0-based) may discard budget_n = (eps^2 ||A||^2 - discarded so far) / (N - n).
+// For mode n an L-column sketch (L = L0, doubled up to I_n) gives the L leading
+// left singular vectors U_L of the paper form's C_n; Y = B x_n U_L^T gives the
+// kept energies e_k = ||slice k of Y||^2, and r is the smallest count with
+// ||B||^2 - (e_1 + ... + e_r) <= budget_n. Without one the sketch is widened; at
+// L = I_n nothing is discarded. Q_n = U_L(:, 1:r) and the next B is the first r
+// slices of Y. The decisions are taken on the host, in FP64, from the device's
+// energies.
+template <typename T>
+tucker_status adaptive_run(const T* A, const int64_t* dims, int N, double eps, int q, int L0, uint64_t seed,
+                           const Opts& o, T* const* U, T* G, int32_t* ranks) {
+    cudaStream_t s = o.stream;
+    const int elem = (int)sizeof(T);
+    const int sms = num_sms();
+    const int64_t E = prod(dims, N);
+    int64_t maxI = 0;
+    for (int n = 0; n < N; ++n) maxI = std::max(maxI, dims[n]);
+    tucker_status rs;
+    Scratch bY, bB0, bB1, bU, bS;
+    if ((rs = bY.get((size_t)E * elem, s)) != TUCKER_OK) return rs;
+    if ((rs = bB0.get((size_t)E * elem, s)) != TUCKER_OK) return rs;
+    if ((rs = bB1.get((size_t)E * elem, s)) != TUCKER_OK) return rs;
+    if ((rs = bU.get((size_t)maxI * std::min<int64_t>(maxI, kMaxL) * elem, s)) != TUCKER_OK) return rs;
+    if ((rs = bS.get(sizeof(double) * 256 + sumsq_scratch_bytes(), s)) != TUCKER_OK) return rs;
+    T* Y = (T*)bY.p;
+    T* Bb[2] = {(T*)bB0.p, (T*)bB1.p};
+    T* UL = (T*)bU.p;
+    double* de = (double*)bS.p;              // [128] energies
+    double* dn = de + 128;                   // [1] a norm
+    void* sumsq_scr = de + 256;
+    auto sumsq_host = [&](const T* x, int64_t n, double* out) -> tucker_status {
+        cudaError_t e = launch_sumsq<T>(x, nullptr, n, dn, sumsq_scr, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, dn, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return from_cuda(e);
+    };
+    double total = 0.0;
+    if ((rs = sumsq_host(A, E, &total)) != TUCKER_OK) return rs;
+    const double allowed = eps * eps * total;
+    double spent = 0.0;
+    int64_t cd[kMaxOrder];
+    for (int n = 0; n < N; ++n) cd[n] = dims[n];
+    const T* cur = A;
+    for (int n = 0; n < N; ++n) {
+        const ModeView v = view_of(cd, N, n);
+        const int64_t I = cd[n];
+        double normB = total;
+        if (n > 0 && (rs = sumsq_host(cur, prod(cd, N), &normB)) != TUCKER_OK) return rs;
+        const double budget = (allowed - spent) / (double)(N - n);
+        int64_t L = std::min<int64_t>(L0, I);
+        int64_t r = 0;
+        double kept = 0.0;
+        for (;;) {
+            if (L > kMaxL) return TUCKER_ERR_UNSUPPORTED;
+            Plan p;
+            p.N = N;
+            p.st = true;
+            p.elem = elem;
+            p.form = o.form;
+            p.prec = o.prec;
+            p.q = q;
+            for (int k = 0; k < N; ++k) p.dims[k] = cd[k];
+            if ((rs = plan_mode(p, cd, N, n, L, 0, 0, true, elem, o, sms)) != TUCKER_OK) return rs;
+            Arena a;
+            Work w;
+            carve(p, a, w);
+            ModeView vy = v;
+            vy.i = L;
+            const size_t wbytes = (a.used + 255) & ~size_t(255);
+            Scratch ws;
+            if ((rs = ws.get(wbytes + slice_sumsq_scratch_bytes(vy, sms), s)) != TUCKER_OK) return rs;
+            Arena b;
+            b.base = (char*)ws.p;
+            b.cap = a.used;
+            carve(p, b, w);
+            double e[128];
+            int st = 0;
+            cudaError_t ce = cudaMemsetAsync(w.status, 0, sizeof(int), s);
+            if (ce == cudaSuccess)
+                ce = factor_mode<T>(cur, p.m[n], n, q, TUCKER_PROB_UNIFORM, seed, o.form, UL, w, nullptr, s);
+            if (ce == cudaSuccess) ce = mode_product<T>(p, cur, v, UL, L, Y, w, s);
+            if (ce == cudaSuccess) ce = launch_slice_sumsq<T>(Y, vy, de, (char*)ws.p + wbytes, sms, s);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(e, de, sizeof(double) * L, cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(&st, w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) return from_cuda(ce);
+            if (st & kStatTimeout) return TUCKER_ERR_TIMEOUT;
+            if (st & kStatNumerical) return TUCKER_ERR_NUMERICAL;
+            double acc = 0.0;
+            r = 0;
+            for (int64_t k = 0; k < L; ++k) {
+                acc += e[k];
+                if (normB - acc <= budget) {
+                    r = k + 1;
+                    break;
+                }
+            }
+            if (r > 0 || L == I) {
+                if (r == 0) r = L;
+                kept = 0.0;
+                for (int64_t k = 0; k < r; ++k) kept += e[k];
+                break;
+            }
+            L = std::min<int64_t>(2 * L, I);
+        }
+        ranks[n] = (int32_t)r;
+        spent += normB - kept;
+        T* dst = n == N - 1 ? G : Bb[n & 1];
+        const size_t run = (size_t)v.lf * elem;
+        cudaError_t ce = cudaMemcpyAsync(U[n], UL, (size_t)I * r * elem, cudaMemcpyDeviceToDevice, s);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy2DAsync(dst, run * r, Y, run * L, run * r, (size_t)v.rt, cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) return from_cuda(ce);
+        cur = dst;
+        cd[n] = r;
+    }
+    if (o.rel_error) {
+        double g2 = 0.0;
+        if ((rs = sumsq_host(G, prod(cd, N), &g2)) != TUCKER_OK) return rs;
+        const double r2 = total > 0.0 ? 1.0 - g2 / total : 0.0;
+        *o.rel_error = r2 > 0.0 ? sqrt(r2) : 0.0;
+    }
+    return from_cuda(cudaStreamSynchronize(s));
+}
+
 }  // namespace
 
 tucker_status status_from_cuda(cudaError_t e) { return from_cuda(e); }
@@ -1037,6 +1177,43 @@ tucker_status tucker_leading_factor_chain(const void* X, tucker_dtype dt, int64_
                                                orth, status, o.stream);
     if (e != cudaSuccess) return from_cuda(e);
     return sync_status(o.stream, status);
+}
+
+tucker_status tucker_check_wait_timeout(int32_t iters, const tucker_opts* opts) {
+    cudaGetLastError();
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (iters < 1 || iters > (1 << 24)) return TUCKER_ERR_INVALID_ARG;
+    Scratch sc;
+    if ((rs = sc.get(256, o.stream)) != TUCKER_OK) return rs;
+    cudaError_t e = cudaMemsetAsync(sc.p, 0, sizeof(int), o.stream);
+    if (e == cudaSuccess) e = launch_wait_timeout(iters, (int*)sc.p, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, (const int*)sc.p);
+}
+
+tucker_status tucker_rsthosvd_adaptive(const void* A, tucker_dtype dt, const int64_t* dims, int N, double eps,
+                                       int32_t q, int32_t L0, uint64_t seed, void* const* U, void* G, int32_t* ranks,
+                                       const tucker_opts* opts) {
+    cudaGetLastError();
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    if (!A || !dims || !U || !G || !ranks || N < 1 || N > kMaxOrder) return TUCKER_ERR_INVALID_ARG;
+    if (!(eps >= 0.0) || !std::isfinite(eps) || q < 1 || L0 < 1) return TUCKER_ERR_INVALID_ARG;
+    if ((o.flags & TUCKER_FLAG_ASYNC) || o.workspace) return TUCKER_ERR_INVALID_ARG;
+    for (int n = 0; n < N; ++n)
+        if (dims[n] < 1 || !U[n]) return TUCKER_ERR_INVALID_ARG;
+    if (o.prec != TUCKER_SK_FP32 && dt != TUCKER_F32) return TUCKER_ERR_UNSUPPORTED;
+    if (!on_device(A) || !on_device(G)) return TUCKER_ERR_INVALID_ARG;
+    for (int n = 0; n < N; ++n)
+        if (!on_device(U[n])) return TUCKER_ERR_INVALID_ARG;
+    if (dt == TUCKER_F32)
+        return adaptive_run<float>((const float*)A, dims, N, eps, q, L0, seed, o, (float* const*)U, (float*)G, ranks);
+    return adaptive_run<double>((const double*)A, dims, N, eps, q, L0, seed, o, (double* const*)U, (double*)G,
+                                ranks);
 }
 
 tucker_status tucker_sample_factor(const void* Cp, tucker_dtype dt, int64_t I, int64_t T, int64_t R, int32_t P,

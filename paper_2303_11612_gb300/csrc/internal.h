@@ -168,6 +168,14 @@ template <typename T>
 cudaError_t launch_ttm(const T* A, const ModeView& v, const T* Mp, int64_t K_out, int64_t ld_i,
                        int64_t ld_k, T* out, cudaStream_t s, int* status = nullptr);
 size_t sumsq_scratch_bytes();
+// One CTA whose bounded wait on an mbarrier nothing completes runs out after
+// `iters` polls: sets kStatTimeout in *status, frees its tensor memory, returns.
+cudaError_t launch_wait_timeout(int iters, int* status, cudaStream_t s);
+// Energies e_k = ||Y(slice k of mode n)||^2 (Y viewed through v with v.i = K slices).
+size_t slice_sumsq_scratch_bytes(const ModeView& v, int num_sms);
+template <typename T>
+cudaError_t launch_slice_sumsq(const T* Y, const ModeView& v, double* e, void* scratch, int num_sms,
+                               cudaStream_t s);
 // *out (device double) = sum (a - b)^2 (b may be null).
 template <typename T>
 cudaError_t launch_sumsq(const T* a, const T* b, int64_t n, double* out, void* scratch,

@@ -11,10 +11,11 @@
 //      Q1 = X R1^-1 with a row-oriented triangular inverse.
 //   2. A second Gram/Cholesky Q1^T Q1 = R2^T R2, so Q = Q1 R2^-1 is orthonormal
 //      and C = Q M with M = R2 R1 F (L x L, upper triangular).
-//   3. One-sided (Hestenes) Jacobi on the columns of M with paired-precision
-//      dot products: M V = U_M S, U_M = the rotated columns, normalised;
-//      columns at rounding level are re-orthogonalised (classical Gram-Schmidt,
-//      twice), so they keep the sketch's own weak directions.
+//   3. QR with column pivoting of M^T, M^T P = Q_h R, so M = P R^T Q_h^T, then
+//      one-sided (Hestenes) Jacobi on the columns of B = R^T with paired-precision
+//      dot products: B V = U_B S, U_B = the rotated columns, normalised, and
+//      U_M = P U_B; columns at rounding level are re-orthogonalised (classical
+//      Gram-Schmidt, twice), so they keep the sketch's own weak directions.
 //      U = Q U_M = Q1 W with W = R2^-1 U_M (back-substitution); Q is never formed.
 //   4. U = Q1 W in paired precision.
 //   5. A final pass keeps U orthonormal where the sketch is numerically
@@ -365,11 +366,124 @@ __device__ __forceinline__ Pair group_sum_pair(Pair s) {
     }
     return s;
 }
-template <int GS>
-__device__ __forceinline__ double group_sum(double s) {
+template <int GS, typename V>
+__device__ __forceinline__ V group_sum(V s) {
 #pragma unroll
     for (int o = GS / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
+}
+
+// Dot product of a group of 8 lanes' NE entries each (rows gl + 8 e), paired
+// precision for FP32 data; every lane of the group gets the sum.
+template <typename T, int NE>
+__device__ __forceinline__ T group8_dot(const T (&x)[NE], const T (&y)[NE]) {
+    if constexpr (sizeof(T) == 4) {
+        Pair a{0.f, 0.f}, b{0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < NE; e += 2) {
+            pair_add_prod(a, x[e], y[e]);
+            if (e + 1 < NE) pair_add_prod(b, x[e + 1], y[e + 1]);
+        }
+        pair_add(a, b);
+        a = group_sum_pair<8>(a);
+        return a.hi + a.lo;
+    } else {
+        T a = T(0);
+#pragma unroll
+        for (int e = 0; e < NE; ++e) a = fma(x[e], y[e], a);
+        return group_sum<8>(a);
+    }
+}
+
+// Householder QR with column pivoting of the L x L matrix A (column-major in
+// shared memory, column p at A + p L): A(:, cmap) = Q R, with Q not formed.
+// The strict upper triangle of R stays in A (R_ij, i < j, at A[cmap[j] L + i]),
+// its diagonal goes to rdiag and the column order to cmap + (L & 1) Lp.
+// Step k takes the remaining column of largest norm (lowest index on ties) and
+// the reflector H = I - beta v v^T with H x = alpha e_k, alpha = -sign(x_k) |x|,
+// beta = 1 / (alpha (alpha - x_k)) (no cancellation in either). One barrier per
+// step: every 8-lane group forms the reflector from the pivot column itself
+// (|x|^2 is the pivot's remaining norm, kept from the previous step in paired
+// precision), then updates its columns (rows k..) and their remaining norms
+// below row k; the norms and the order are double-buffered, since other warps
+// still read the previous step's while a group writes.
+template <typename T, int NE>
+__device__ void pivoted_qr(T* A, int L, int Lp, T* qnrm, T* rdiag, int* cmap) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = (int)blockDim.x >> 5;
+    const int gl = lane & 7, gw = lane >> 3;
+    const int ngroups = nwarps * 4;
+    for (int p = warp; p < L; p += nwarps) {
+        DotAcc<T> s2;
+        for (int r = lane; r < L; r += 32) s2.add(A[p * L + r], A[p * L + r]);
+        s2.reduce();
+        if (lane == 0) qnrm[p] = (T)s2.value();
+    }
+    for (int j = tid; j < L; j += blockDim.x) cmap[j] = j;
+    __syncthreads();
+    for (int k = 0; k < L; ++k) {
+        const int* cur = cmap + (k & 1) * Lp;
+        int* nxt = cmap + ((k + 1) & 1) * Lp;
+        const T* nin = qnrm + (k & 1) * Lp;
+        T* nout = qnrm + ((k + 1) & 1) * Lp;
+        T bv = T(-1);
+        int bj = L;
+        for (int j = k + lane; j < L; j += 32) {
+            const T v = nin[cur[j]];
+            if (v > bv) { bv = v; bj = j; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ov > bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
+        }
+        const int piv = bj < L ? bj : k;
+        const int pk = cur[k], pc = cur[piv];
+        if (warp == 0)
+            for (int j = lane; j < L; j += 32) nxt[j] = j == k ? pc : (j == piv ? pk : cur[j]);
+        const T n2 = nin[pc];
+        const T xk = A[pc * L + k];
+        T v[NE];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            const int r = gl + 8 * e;
+            v[e] = (r >= k && r < L) ? A[pc * L + r] : T(0);
+        }
+        const bool any = n2 > T(0);
+        const T alpha = any ? -copysign(sqrt(n2), xk) : T(0);
+        const T beta = any ? T(1) / (alpha * (alpha - xk)) : T(0);
+#pragma unroll
+        for (int e = 0; e < NE; ++e)
+            if (gl + 8 * e == k) v[e] -= alpha;
+        if (tid == 0) rdiag[k] = alpha;
+        // the loop bound is uniform across a warp (the group sums shuffle over all 32 lanes)
+        for (int base = k + 1 + warp * 4; base < L; base += ngroups) {
+            const int j = base + gw;
+            const bool live = j < L;
+            const int p = live ? (j == piv ? pk : cur[j]) : 0;
+            T y[NE];
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+                const int r = gl + 8 * e;
+                y[e] = (live && r >= k && r < L) ? A[p * L + r] : T(0);
+            }
+            const T d = beta * group8_dot<T, NE>(v, y);
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+                const int r = gl + 8 * e;
+                if (live && r >= k && r < L) {
+                    const T w = fma(-d, v[e], y[e]);
+                    A[p * L + r] = w;
+                    y[e] = r > k ? w : T(0);
+                } else {
+                    y[e] = T(0);
+                }
+            }
+            const T m2 = group8_dot<T, NE>(y, y);
+            if (live && gl == 0) nout[p] = m2;
+        }
+        __syncthreads();
+    }
 }
 
 // Rotation (c, s) that zeroes the coupling g of columns with squared norms a, b
@@ -396,21 +510,70 @@ __device__ __forceinline__ void rotation(double a, double b, double g, double& c
     s = c * t;
 }
 
+// Squared norms a, b and coupling g of the column pair x, y held by a group of
+// GS lanes (NE entries each): a, b are plain sums (they only set the angle and
+// the threshold); g, which cancels, is summed in paired precision.
+template <typename T, int GS, int NE>
+__device__ __forceinline__ void pair_sums(const T (&x)[NE], const T (&y)[NE], T& a, T& b, T& g) {
+    // two independent chains per sum (even and odd entries), combined in a
+    // fixed order: the sums are the dependent chains of a round
+    T a2 = T(0), b2 = T(0);
+    a = T(0);
+    b = T(0);
+#pragma unroll
+    for (int e = 0; e < NE; e += 2) {
+        a = fma(x[e], x[e], a);
+        b = fma(y[e], y[e], b);
+        if (e + 1 < NE) {
+            a2 = fma(x[e + 1], x[e + 1], a2);
+            b2 = fma(y[e + 1], y[e + 1], b2);
+        }
+    }
+    a += a2;
+    b += b2;
+    if constexpr (sizeof(T) == 4) {
+        Pair ga{0.f, 0.f}, gb{0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < NE; e += 2) {
+            pair_add_prod(ga, x[e], y[e]);
+            if (e + 1 < NE) pair_add_prod(gb, x[e + 1], y[e + 1]);
+        }
+        pair_add(ga, gb);
+#pragma unroll
+        for (int o = GS / 2; o > 0; o >>= 1) {
+            const float ta = __shfl_xor_sync(0xffffffffu, a, o);
+            const float tb = __shfl_xor_sync(0xffffffffu, b, o);
+            Pair t;
+            t.hi = __shfl_xor_sync(0xffffffffu, ga.hi, o);
+            t.lo = __shfl_xor_sync(0xffffffffu, ga.lo, o);
+            a += ta;
+            b += tb;
+            pair_add(ga, t);
+        }
+        g = ga.hi + ga.lo;
+    } else {
+        double ga = 0.0;
+#pragma unroll
+        for (int e = 0; e < NE; ++e) ga = fma(x[e], y[e], ga);
+        a = group_sum<GS>(a); b = group_sum<GS>(b); g = group_sum<GS>(ga);
+    }
+}
+
 // One cyclic sweep of one-sided Jacobi on the columns of Mc (column-major,
 // column c at Mc + c * L, L <= NE * GS); pairs handled by groups of GS lanes,
-// each lane holding up to NE entries of both columns in registers. The squared
-// norms a, b are plain sums (they only set the angle and the threshold); the
-// coupling g, which cancels, is summed in paired precision. Returns the number
-// of rotations.
+// each lane holding up to NE entries of both columns in registers. Returns the
+// number of rotations; *mxc2 receives the largest squared cosine g^2 / (a b)
+// among the rotated pairs (as the bits of a nonnegative float).
 template <typename T, int GS, int NE>
-__device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot) {
+__device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot, unsigned* mxc2) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kGroupsPerWarp = 32 / GS;
     const int groups = ((int)blockDim.x >> 5) * kGroupsPerWarp, gl = lane % GS;
     const int m = Lp - 1;
-    if (tid == 0) *nrot = 0;
+    if (tid == 0) { *nrot = 0; *mxc2 = 0u; }
     __syncthreads();
     int mine = 0;
+    float c2max = 0.f;
     for (int rnd = 0; rnd < m; ++rnd) {
         // the loop bound is uniform across a warp, so all 32 lanes reach every
         // shuffle below; groups without a pair take part with zeros
@@ -436,47 +599,10 @@ __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot) {
                 x[e] = in ? cp[r] : T(0);
                 y[e] = in ? cq[r] : T(0);
             }
-            // two independent chains per sum (even and odd entries), combined in a
-            // fixed order: the sums are the dependent chains of a round
-            T a = T(0), b = T(0), a2 = T(0), b2 = T(0), g;
-#pragma unroll
-            for (int e = 0; e < NE; e += 2) {
-                a = fma(x[e], x[e], a);
-                b = fma(y[e], y[e], b);
-                if (e + 1 < NE) {
-                    a2 = fma(x[e + 1], x[e + 1], a2);
-                    b2 = fma(y[e + 1], y[e + 1], b2);
-                }
-            }
-            a += a2;
-            b += b2;
-            if constexpr (sizeof(T) == 4) {
-                Pair ga{0.f, 0.f}, gb{0.f, 0.f};
-#pragma unroll
-                for (int e = 0; e < NE; e += 2) {
-                    pair_add_prod(ga, x[e], y[e]);
-                    if (e + 1 < NE) pair_add_prod(gb, x[e + 1], y[e + 1]);
-                }
-                pair_add(ga, gb);
-#pragma unroll
-                for (int o = GS / 2; o > 0; o >>= 1) {
-                    const float ta = __shfl_xor_sync(0xffffffffu, a, o);
-                    const float tb = __shfl_xor_sync(0xffffffffu, b, o);
-                    Pair t;
-                    t.hi = __shfl_xor_sync(0xffffffffu, ga.hi, o);
-                    t.lo = __shfl_xor_sync(0xffffffffu, ga.lo, o);
-                    a += ta;
-                    b += tb;
-                    pair_add(ga, t);
-                }
-                g = ga.hi + ga.lo;
-            } else {
-                double ga = 0.0;
-#pragma unroll
-                for (int e = 0; e < NE; ++e) ga = fma(x[e], y[e], ga);
-                a = group_sum<GS>(a); b = group_sum<GS>(b); g = group_sum<GS>(ga);
-            }
+            T a, b, g;
+            pair_sums<T, GS, NE>(x, y, a, b, g);
             if (live && fabs(g) > tiny && g * g > tol * tol * a * b) {
+                c2max = fmaxf(c2max, (float)((g / a) * (g / b)));
                 T c, s;
                 rotation(a, b, g, c, s);
 #pragma unroll
@@ -493,15 +619,57 @@ __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot) {
         __syncthreads();
     }
     if (mine) atomicAdd(nrot, mine);
+    if (c2max > 0.f) atomicMax(mxc2, __float_as_uint(c2max));
     __syncthreads();
     const int n = *nrot;
     __syncthreads();
     return n;
 }
 
+// True when some pair of the L columns would still rotate (the test of
+// jacobi_sweep on every pair at once, columns unchanged): what a sweep that
+// rotates nothing establishes, at the cost of one round's arithmetic per
+// L / 2 pairs and a single barrier.
+template <typename T, int GS, int NE>
+__device__ bool jacobi_pending(const T* Mc, int L, T tol, T tiny, int* flag) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int kGroupsPerWarp = 32 / GS;
+    const int groups = ((int)blockDim.x >> 5) * kGroupsPerWarp, gl = lane % GS;
+    const int npairs = L * (L - 1) / 2;
+    if (tid == 0) *flag = 0;
+    __syncthreads();
+    bool mine = false;
+    for (int base = warp * kGroupsPerWarp; base < npairs; base += groups) {
+        const int pi = base + lane / GS;
+        const bool live = pi < npairs;
+        // pair number pi -> (p, q), p < q: row p holds L - 1 - p pairs
+        int p = 0, rem = live ? pi : 0;
+        while (rem >= L - 1 - p) { rem -= L - 1 - p; ++p; }
+        const int q = p + 1 + rem;
+        const T* cp = Mc + p * L;
+        const T* cq = Mc + q * L;
+        T x[NE], y[NE];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            const int r = gl + e * GS;
+            const bool in = live && r < L;
+            x[e] = in ? cp[r] : T(0);
+            y[e] = in ? cq[r] : T(0);
+        }
+        T a, b, g;
+        pair_sums<T, GS, NE>(x, y, a, b, g);
+        if (live && fabs(g) > tiny && g * g > tol * tol * a * b) mine = true;
+    }
+    if (mine) *flag = 1;
+    __syncthreads();
+    const bool any = *flag != 0;
+    __syncthreads();
+    return any;
+}
+
 // Shared-memory layout of the extraction's last CTA (byte offsets).
 struct XLayout {
-    size_t rf, g, h, dinv, sig, inrm, dots, perm, total;
+    size_t rf, g, h, dinv, sig, inrm, dots, perm, qnrm, rdiag, cmap, total;
 };
 __host__ __device__ inline size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ inline size_t zmax(size_t a, size_t b) { return a > b ? a : b; }
@@ -510,21 +678,25 @@ __host__ __device__ inline XLayout xlayout(int L, int R, int elem) {
     const size_t np = packed_size(L);
     XLayout x;
     x.rf = 0;                                                       // packed R2
-    x.g = up16(8 * np);                                             // packed P / M, later U_M
-    x.h = x.g + up16(zmax(8 * np, (size_t)elem * R * L));           // packed products, later Mc
+    x.g = up16(8 * np);                                             // packed P / M, later B = R^T
+    x.h = x.g + up16(zmax(8 * np, (size_t)elem * Lp * L));          // packed products, M^T, later U_M
     x.dinv = x.h + up16(zmax(8 * np, (size_t)elem * Lp * L));
     x.sig = x.dinv + up16((size_t)8 * L);
     x.inrm = x.sig + up16((size_t)elem * Lp);
     x.dots = x.inrm + up16((size_t)elem * Lp);
     x.perm = x.dots + up16((size_t)elem * R);
-    x.total = x.perm + up16(sizeof(int) * Lp);
+    x.qnrm = x.perm + up16(sizeof(int) * Lp);                      // [2][Lp] pivoting norms
+    x.rdiag = x.qnrm + up16((size_t)elem * 2 * Lp);                 // [Lp] diagonal of R
+    x.cmap = x.rdiag + up16((size_t)elem * Lp);                     // [2][Lp] pivot order
+    x.total = x.cmap + up16(sizeof(int) * 2 * Lp);
     return x;
 }
 
 // Grid of Gram CTAs over Q1 (kXT threads each). The last CTA: Cholesky
 // Q1^T Q1 = R2^T R2, M = R2 P with P = prev[nprev-1] ... prev[0] (packed
-// factors fstride apart; prev[nprev-1] is R1), Jacobi on M, U_M (rounding-level
-// columns re-orthogonalised) and W = R2^-1 U_M for the R leading columns
+// factors fstride apart; prev[nprev-1] is R1), pivoted QR of M^T, Jacobi on
+// R^T, U_M (rounding-level columns re-orthogonalised) and W = R2^-1 U_M for the
+// R leading columns
 // (scalar S, L x R, column-major). A column with no direction left gets W = 0
 // (the final pass completes it).
 template <typename T>
@@ -552,9 +724,12 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
     T* inrm = reinterpret_cast<T*>(smem_raw + lay.inrm);   // [Lp] their reciprocals
     T* dots = reinterpret_cast<T*>(smem_raw + lay.dots);   // [R] Gram-Schmidt coefficients
     int* perm = reinterpret_cast<int*>(smem_raw + lay.perm);
-    T* Mc = reinterpret_cast<T*>(H);                       // column-major [Lp][L], once M is in G
-    T* UM = reinterpret_cast<T*>(G);                       // column-major [R][L], once Mc is formed
+    T* qnrm = reinterpret_cast<T*>(smem_raw + lay.qnrm);
+    T* rdiag = reinterpret_cast<T*>(smem_raw + lay.rdiag);
+    int* cmap = reinterpret_cast<int*>(smem_raw + lay.cmap);
+    T* Mt = reinterpret_cast<T*>(H);                       // M^T column-major [Lp][L], once M is in G
     __shared__ int nrot;
+    __shared__ int graded;
     __shared__ T fro2;
     __shared__ T nrm2;
     __shared__ unsigned long long mx_bits;
@@ -582,7 +757,7 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
         __syncthreads();
         src = dst;
     }
-    // M scaled by a power of two (largest entry in [1, 2)) and stored in T
+    // M^T scaled by a power of two (largest entry in [1, 2)) and stored in T
     if (tid == 0) { mx_bits = 0ull; fro2 = T(0); }
     __syncthreads();
     {
@@ -600,36 +775,89 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
         T s2 = T(0);
         for (int p = tid; p < Lp * L; p += kXT) {
             const int c = p / L, a = p % L;
-            const T v = (c < L && a <= c) ? (T)ldexp(F::to_double(G[packed_index(a, c, L)]), 1 - ex) : T(0);
-            Mc[p] = v;
+            const T v = (c < L && c <= a) ? (T)ldexp(F::to_double(G[packed_index(c, a, L)]), 1 - ex) : T(0);
+            Mt[p] = v;
             s2 += v * v;
         }
         s2 = warp_sum(s2);
         if (lane == 0) atomicAdd(&fro2, s2);
     }
     __syncthreads();
-    // rotate while a pair's cosine exceeds 4 eps and its coupling is above the
-    // rounding level of the whole matrix; the stored columns carry rounding of
-    // their own, so the sweep count is capped
+    // Preconditioning (Drmac and Veselic, 2008): M^T(:, cmap) = Q R by QR with
+    // column pivoting, so M = P R^T Q^T and the left singular vectors of M are
+    // those of B = R^T with rows permuted (row j of B is row cmap[j] of M's).
+    // The pivoted R is row-graded, B column-graded, and one-sided Jacobi on B's
+    // columns needs about half the sweeps it takes on M's. The reflectors are
+    // columnwise backward stable: each row of M is perturbed relative to its
+    // own norm, as rounding M to T already does.
+    if (L <= 32) pivoted_qr<T, 4>(Mt, L, Lp, qnrm, rdiag, cmap);
+    else if (L <= 64) pivoted_qr<T, 8>(Mt, L, Lp, qnrm, rdiag, cmap);
+    else if (L <= 80) pivoted_qr<T, 10>(Mt, L, Lp, qnrm, rdiag, cmap);
+    else if (L <= 96) pivoted_qr<T, 12>(Mt, L, Lp, qnrm, rdiag, cmap);
+    else pivoted_qr<T, 16>(Mt, L, Lp, qnrm, rdiag, cmap);
+    // A sketch that is numerically rank-deficient in T (its smallest pivot below
+    // 2^-20 of the largest, e.g. the Hilbert tensor's) keeps the unconditioned
+    // Jacobi on M's columns: there every column has the norm of M's leading rows,
+    // the rounding a rotation leaves lies along the strong directions, and the
+    // re-orthogonalisation below removes it from the weak columns, which gives
+    // better factors on such sketches than the graded B (measured). Otherwise B.
+    if (tid == 0) graded = !(fabs(rdiag[L - 1]) >= T(0x1p-20) * fabs(rdiag[0]));
+    __syncthreads();
+    int* fmap = cmap + (L & 1) * Lp;
+    T* Bc = graded ? Mt : reinterpret_cast<T*>(G);         // the matrix the Jacobi rotates, [Lp][L]
+    T* UM = graded ? reinterpret_cast<T*>(G) : Mt;         // U_M, column-major [R][L], once Bc is final
+    if (graded) {
+        for (int p = tid; p < Lp * L; p += kXT) {
+            const int c = p / L, a = p % L;
+            Bc[p] = (c < L && a <= c) ? (T)ldexp(F::to_double(G[packed_index(a, c, L)]), 1 - ex) : T(0);
+        }
+        for (int j = tid; j < L; j += kXT) fmap[j] = j;
+    } else {
+        for (int p = tid; p < Lp * L; p += kXT) {
+            const int c = p / L, a = p % L;
+            T v = T(0);
+            if (c < L) v = a == c ? rdiag[c] : (a > c ? Mt[fmap[a] * L + c] : T(0));
+            Bc[p] = v;
+        }
+    }
+    __syncthreads();
+    // rotate while a pair's cosine exceeds 4 eps, g^2 > tol^2 a b. B's columns
+    // are graded and carry rounding relative to their own norms (the reflectors
+    // are columnwise stable), so for B the test is relative to the pair alone
+    // (tiny only keeps underflowed couplings out; B's pivots lie within 2^20 of
+    // each other and the largest entry of M is in [1, 2), so tol^2 a b stays
+    // above the smallest normal); M's columns carry rounding of the whole
+    // matrix, so there a coupling must also exceed eps^2 ||M||_F^2. The stored columns carry rounding
+    // of their own, so the sweep count is capped. Once a sweep's largest rotated cosine is below 1e-3
+    // (Jacobi converges quadratically from there), all pairs are tested at once
+    // before another sweep is spent: when none would rotate, that sweep would
+    // have rotated nothing.
     const T eps = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
     const T tol = T(4) * eps;
-    const T tiny = eps * eps * fro2;
+    const T tiny = graded ? eps * eps * fro2 : (sizeof(T) == 4 ? (T)FLT_MIN : (T)DBL_MIN);
+    __shared__ unsigned mxc2;
     for (int sweep = 0; sweep < 20; ++sweep) {
         int n;
+        bool pending;
         // groups of 8 lanes, one pair each, every pair of a round in flight at once;
         // each lane holds NE >= L / 8 entries of both columns (a round is bound by
         // instruction issue, so lanes do not repeat the reductions needlessly)
-        if (L <= 32) n = jacobi_sweep<T, 8, 4>(Mc, L, Lp, tol, tiny, &nrot);
-        else if (L <= 64) n = jacobi_sweep<T, 8, 8>(Mc, L, Lp, tol, tiny, &nrot);
-        else if (L <= 80) n = jacobi_sweep<T, 8, 10>(Mc, L, Lp, tol, tiny, &nrot);
-        else if (L <= 96) n = jacobi_sweep<T, 8, 12>(Mc, L, Lp, tol, tiny, &nrot);
-        else n = jacobi_sweep<T, 8, 16>(Mc, L, Lp, tol, tiny, &nrot);     // L <= 128
-        if (n == 0) break;
+#define TK_JACOBI(NE)                                                                  \
+        n = jacobi_sweep<T, 8, NE>(Bc, L, Lp, tol, tiny, &nrot, &mxc2);                \
+        pending = n > 0 && (__uint_as_float(mxc2) >= 1e-6f ||                          \
+                            jacobi_pending<T, 8, NE>(Bc, L, tol, tiny, &nrot));
+        if (L <= 32) { TK_JACOBI(4) }
+        else if (L <= 64) { TK_JACOBI(8) }
+        else if (L <= 80) { TK_JACOBI(10) }
+        else if (L <= 96) { TK_JACOBI(12) }
+        else { TK_JACOBI(16) }                                                      // L <= 128
+#undef TK_JACOBI
+        if (!pending) break;
     }
     // singular values (column norms), decreasing order, lower index first on ties
     for (int c = warp; c < L; c += nwarps) {
         DotAcc<T> s;
-        for (int r = lane; r < L; r += 32) s.add(Mc[c * L + r], Mc[c * L + r]);
+        for (int r = lane; r < L; r += 32) s.add(Bc[c * L + r], Bc[c * L + r]);
         s.reduce();
         if (lane == 0) {
             const T sg = sqrt((T)s.value());
@@ -645,11 +873,11 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
     }
     __syncthreads();
     const T weak = T(64) * eps * sig[perm[0]];
-    // U_M: rotated columns in decreasing order, normalised
+    // U_M: B's rotated columns in decreasing order, normalised, rows in M's order
     for (int p = tid; p < L * R; p += kXT) {
-        const int r = p / L, a = p % L;
+        const int r = p / L, j = p % L;
         const int c = perm[r];
-        UM[p] = Mc[c * L + a] * inrm[c];
+        UM[(size_t)r * L + fmap[j]] = Bc[c * L + j] * inrm[c];
     }
     __syncthreads();
     // rounding-level columns: classical Gram-Schmidt against every earlier

@@ -7,6 +7,8 @@
 // indices; the fiber tile streams through shared memory in chunks of KC input
 // indices while the JB x OB block of results stays in registers, so the input
 // is read once per output block (one block whenever K_out <= 64).
+#include <algorithm>
+
 #include "internal.h"
 #include "tc.cuh"
 #include "tma.cuh"
@@ -391,6 +393,83 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int n, d
     }
 }
 
+// Energies of the mode-n slices of Y (viewed as [rt][K][lf], lf fastest):
+// e_k = sum of Y^2 over slice k, i.e. ||u_k^T B_(n)||^2 when Y = B x_n U^T.
+// Long runs (lf >= kT): block (k, c) reads chunk c of slice k, runs of lf
+// consecutive elements. Short runs: Y is the [rt][K lf] matrix and each thread
+// sums one column over a chunk of rows (consecutive threads, consecutive
+// columns). Partials are reduced in a fixed order: the result is deterministic.
+template <typename T>
+__global__ void __launch_bounds__(kT) slice_sumsq_runs_kernel(const T* __restrict__ Y, int64_t lf, int64_t K,
+                                                              int64_t rt, double* __restrict__ partial) {
+    __shared__ double sh[kT / 32];
+    const int64_t k = blockIdx.x;
+    const int chunks = (int)gridDim.y, c = (int)blockIdx.y;
+    const int64_t per = lf * rt;
+    double acc = 0.0;
+    for (int64_t e = (int64_t)c * kT + threadIdx.x; e < per; e += (int64_t)chunks * kT) {
+        const int64_t o = e / lf, i = e - o * lf;
+        const double v = (double)Y[(o * K + k) * lf + i];
+        acc = fma(v, v, acc);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kT / 32; ++w) t += sh[w];
+        partial[k * chunks + c] = t;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT) slice_sumsq_cols_kernel(const T* __restrict__ Y, int64_t W, int64_t rt,
+                                                              double* __restrict__ partial) {
+    const int64_t m = (int64_t)blockIdx.x * kT + threadIdx.x;
+    const int chunks = (int)gridDim.y, c = (int)blockIdx.y;
+    if (m >= W) return;
+    double acc = 0.0;
+    for (int64_t o = c; o < rt; o += chunks) {
+        const double v = (double)Y[o * W + m];
+        acc = fma(v, v, acc);
+    }
+    partial[(int64_t)c * W + m] = acc;
+}
+
+// e_k from the partials: runs layout [K][chunks], columns layout [chunks][K lf].
+__global__ void slice_sum_partials_kernel(const double* __restrict__ partial, int64_t K, int chunks, int64_t lf,
+                                          bool cols, double* __restrict__ e) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double t = 0.0;
+    if (!cols) {
+        for (int c = 0; c < chunks; ++c) t += partial[k * chunks + c];
+    } else {
+        for (int c = 0; c < chunks; ++c)
+            for (int64_t i = 0; i < lf; ++i) t += partial[(int64_t)c * K * lf + k * lf + i];
+    }
+    e[k] = t;
+}
+
+struct SliceSplit {
+    bool runs;
+    int chunks;
+};
+SliceSplit slice_split(const ModeView& v, int num_sms) {
+    SliceSplit sp;
+    sp.runs = v.lf >= kT;
+    const int64_t target = 4 * (int64_t)num_sms;
+    if (sp.runs) {
+        const int64_t c = (target + v.i - 1) / v.i;
+        sp.chunks = (int)std::max<int64_t>(1, std::min<int64_t>(c, 256));
+    } else {
+        const int64_t tiles = (v.i * v.lf + kT - 1) / kT;
+        const int64_t c = (target + tiles - 1) / tiles;
+        sp.chunks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(c, 64), std::max<int64_t>(v.rt, 1)));
+    }
+    return sp;
+}
+
 }  // namespace
 
 template <typename T>
@@ -480,5 +559,37 @@ template cudaError_t launch_ttm<double>(const double*, const ModeView&, const do
                                         double*, cudaStream_t, int*);
 template cudaError_t launch_sumsq<float>(const float*, const float*, int64_t, double*, void*, cudaStream_t);
 template cudaError_t launch_sumsq<double>(const double*, const double*, int64_t, double*, void*, cudaStream_t);
+
+size_t slice_sumsq_scratch_bytes(const ModeView& v, int num_sms) {
+    const SliceSplit sp = slice_split(v, num_sms);
+    const int64_t n = sp.runs ? v.i * sp.chunks : (int64_t)sp.chunks * v.i * v.lf;
+    return sizeof(double) * (size_t)n + 256;
+}
+
+template <typename T>
+cudaError_t launch_slice_sumsq(const T* Y, const ModeView& v, double* e, void* scratch, int num_sms,
+                               cudaStream_t s) {
+    if (v.i < 1 || v.fibers() < 1) return cudaSuccess;
+    if (v.i > 65535) return cudaErrorInvalidValue;
+    const SliceSplit sp = slice_split(v, num_sms);
+    double* partial = reinterpret_cast<double*>(scratch);
+    if (sp.runs) {
+        slice_sumsq_runs_kernel<T><<<dim3((unsigned)v.i, (unsigned)sp.chunks), kT, 0, s>>>(Y, v.lf, v.i, v.rt,
+                                                                                          partial);
+    } else {
+        const int64_t W = v.i * v.lf;
+        slice_sumsq_cols_kernel<T><<<dim3((unsigned)((W + kT - 1) / kT), (unsigned)sp.chunks), kT, 0, s>>>(
+            Y, W, v.rt, partial);
+    }
+    note_launch();
+    slice_sum_partials_kernel<<<(unsigned)((v.i + 127) / 128), 128, 0, s>>>(partial, v.i, sp.chunks,
+                                                                             sp.runs ? 1 : v.lf, !sp.runs, e);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_slice_sumsq<float>(const float*, const ModeView&, double*, void*, int, cudaStream_t);
+template cudaError_t launch_slice_sumsq<double>(const double*, const ModeView&, double*, void*, int,
+                                                cudaStream_t);
 
 }  // namespace tk

@@ -795,6 +795,37 @@ bool layout_ok(const ModeView& v) {
     return v.lf % 32 == 0 && v.lf <= (int64_t)INT_MAX && v.rt <= (int64_t)INT_MAX;
 }
 
+// A wait that nothing completes: one CTA takes tensor memory as the kernels
+// above do, initialises an mbarrier that no thread and no copy arrives at,
+// waits for it with the bound `iters`, records the timeout as every kernel here
+// does, frees its tensor memory and returns. No copy or product is in flight,
+// so nothing needs draining: it checks that a bounded wait ends, that its
+// status reaches the host and that the context stays usable.
+__global__ void __launch_bounds__(64) wait_timeout_kernel(int iters, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int flag;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        flag = 0;
+        tma::fence_barrier_init();
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_slot, 32);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x == 0) {
+        bool ok = false;
+        for (int it = 0; it < iters && !ok; ++it) ok = tc::mbar_try(&bar, 0);
+        if (!ok) fail(&flag, status);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem_slot, 32);
+}
+
 }  // namespace
 
 bool wide_ttm_supported(const ModeView& v, int64_t K_out) {
@@ -977,6 +1008,13 @@ cudaError_t launch_wide_nn(const float* A, const ModeView& v, const float* Q, in
         if (e != cudaSuccess) return e;
     }
     return launch_reduce_partials<float>(part, (int)R, (int64_t)I * L, X_out, s);
+}
+
+cudaError_t launch_wait_timeout(int iters, int* status, cudaStream_t s) {
+    if (iters < 1) return cudaErrorInvalidValue;
+    wait_timeout_kernel<<<1, 64, 0, s>>>(iters, status);
+    note_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace tk

@@ -211,3 +211,22 @@ def test_relative_error_explicit(tk):
     got = tk.relative_error(flat_dev(A), dims, ranks, [colmajor(U) for U in Us],
                             dev(synth.flat(G).astype(np.float32)))
     assert abs(got - want) < 1e-6
+
+
+def test_bounded_wait_times_out_and_the_context_survives(tk):
+    """A device wait that nothing completes ends after its bound with the
+    timeout status (as every tensor-core kernel's waits do), frees its tensor
+    memory, and the next decomposition on the same context is unaffected."""
+    from paper_2303_11612_gb300 import _binding as B
+    assert B.check_wait_timeout(1000) == 5                      # TUCKER_ERR_TIMEOUT
+    assert B.check_wait_timeout(1) == 5
+    assert B.check_wait_timeout(0) == 1                         # TUCKER_ERR_INVALID_ARG
+    dims, ranks = (48, 40, 36), (6, 5, 4)
+    A = synth.lowrank_noise(dims, ranks, rel_noise=1e-3, seed=1)
+    At = torch.from_numpy(np.ascontiguousarray(synth.flat(A))).cuda()
+    for prec in ("fp32", "bf16x1"):
+        U, G = tk.rsthosvd(At, dims, ranks, P=4, q=1, prec=prec)
+        assert tk.last_device_status() == 0
+        re = ot.relative_error(A.astype(np.float64), [u.double().cpu().numpy() for u in U],
+                               synth.from_flat(G.double().cpu().numpy(), ranks))
+        assert re < 2e-3
