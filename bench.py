@@ -7,7 +7,7 @@ FP32 video-like tensors (a sum of 50 separable sinusoids plus N(0, 1e-2) noise,
 2.15 GB each), ranks (64, 64, 32), P = 16, q = 1, variants
   1. q = 1, no sampling                        (Algorithm 2)
   2. q = 1, c = 20000 fibers, uniform p        (Algorithm 5)
-two decompositions of each variant per step, each on its own tensor (four
+four decompositions of each variant per step, each on its own tensor (eight
 distinct 2.15 GB tensors, larger than the 129 MB L2, so no flush is needed),
 in every sketch arithmetic (single-pass BF16, TF32, split BF16, FP32).
 value = decompositions per second with the tensors resident in HBM, for the
@@ -19,8 +19,10 @@ input and device->host copy of the factors and core inside the timed region).
 
 Secondary lines, each with its own oracle check: the 400^3 batch (low-rank
 and Hilbert tensors, q = 1 / 2, AMM c = 4000; 32 distinct buffers), the 96^4
-decaying-core tensor (q = 2), the FP64 100^3 T-HOSVD, randomized T-HOSVD,
-and a serving sample.
+decaying-core tensor (q = 2), the FP64 100^3 T-HOSVD, randomized T-HOSVD;
+and the serving stream (2000 requests of orders 3 and 4, extents up to 256,
+a 40 GB admission budget): saturation throughput and p50/p99 latency under
+Poisson arrivals, in the headline arithmetic and in FP32.
 
 --impl reference times the FP64 CPU oracle on the headline workload (one
 decomposition per step, cycling through the variants).
@@ -59,7 +61,7 @@ WORKLOADS = {
         desc="randomized ST-HOSVD of 1024x1024x512 FP32 video-like tensors (sum of 50 separable sinusoids + "
              "N(0,1e-2) noise, 2.15 GB each), R=(64,64,32) P=16 q=1; variants: Algorithm 2; Algorithm 5 with "
              "c=20000 uniform",
-        which="ST", dims=(1024, 1024, 512), ranks=(64, 64, 32), P=16, dtype="f32", copies=2,
+        which="ST", dims=(1024, 1024, 512), ranks=(64, 64, 32), P=16, dtype="f32", copies=4,
         variants=[dict(name="q1", gen="video", q=1, c=0, prob="uniform"),
                   dict(name="q1_amm20000_uniform", gen="video", q=1, c=20000, prob="uniform")]),
     "cube400": dict(
@@ -269,57 +271,88 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- serving
-SERVE_N = 300
+SERVE_N = 2000
 SERVE_BUDGET = 40 << 30
+SERVE_RESIDENT = 48 << 30
 
 
-def serving_requests(torch, n=SERVE_N, seed=0):
-    """A bounded sample of the serving stream: orders 3 and 4 (50/50), ranks
-    U{4..32} (at most the extent), P = 5, q = 1, low-rank + 1e-2 noise built on
-    the device. Extents U{32..256} for order 3 and U{32..96} for order 4 (the
-    full stream's order-4 requests reach 256^4 = 17 GB each; the sample keeps
-    the whole set resident)."""
+def serving_specs(n=SERVE_N, seed=0):
+    """The serving stream of the config: n randomized ST-HOSVD requests (P = 5, q = 1), order 3 or 4 with
+    equal odds, every extent uniform in 32..256, ranks uniform in 4..32 (at most the extent), each a
+    low-rank (core of the ranks) plus 1e-2 noise FP32 tensor; order-4 requests reach 256^4 = 17 GB."""
+    import synth
+    return synth.serving_requests(n, seed=seed, dim_range=(32, 256), rank_range=(4, 32), orders=(3, 4))
+
+
+def serving_batches(specs, resident=SERVE_RESIDENT):
+    """Consecutive groups of the stream whose inputs fit `resident` bytes of device memory together."""
     import numpy as np
-    from synth import device as sd
-    rng = np.random.default_rng(seed)
-    out = []
-    for k in range(n):
-        N = 3 if rng.random() < 0.5 else 4
-        dims = [int(x) for x in rng.integers(32, (256 if N == 3 else 96) + 1, size=N)]
-        ranks = [int(min(d, r)) for d, r in zip(dims, rng.integers(4, 33, size=N))]
-        X = sd.tucker_tensor(torch, dims, ranks, 1e-2, seed=1000 + k)
-        out.append(dict(A=X, dims=dims, ranks=ranks, seed=k))
-    torch.cuda.synchronize()
+    out, cur, used = [], [], 0
+    for r in specs:
+        b = 4 * int(np.prod(r["dims"]))
+        if cur and used + b > resident:
+            out.append(cur)
+            cur, used = [], 0
+        cur.append(r)
+        used += b
+    if cur:
+        out.append(cur)
     return out
 
 
-def serving_bench(tk, torch, reqs, prec, load=0.7):
-    """Saturation throughput (every request submitted at once), then p50/p99
-    latency under Poisson arrivals at `load` times that throughput."""
+def serving_inputs(torch, batch):
+    """The batch's tensors, generated on the device (untimed; they stand for data that has arrived in HBM)."""
+    from synth import device as sd
+    xs = [sd.tucker_tensor_lean(torch, r["dims"], r["ranks"], 1e-2, seed=1000 + r["id"]) for r in batch]
+    torch.cuda.synchronize()
+    return xs
+
+
+def serving_bench(tk, torch, specs, prec, load=0.7):
+    """The whole stream through one server per phase, in groups of requests whose inputs are generated on
+    the device before the group (outside the timed region). Saturation: each group submitted at once, the
+    rate over the groups' wall times. Latency: within each group arrivals are Poisson at `load` times the
+    saturation rate (the queue drains between groups); p50/p99 over every request, submission to
+    completion, as the server records them."""
     import numpy as np
+    batches = serving_batches(specs)
+    sat_s, n = 0.0, 0
     with tk.Server(budget_bytes=SERVE_BUDGET, max_inflight=16, prec=prec) as srv:
-        t0 = time.perf_counter()
-        ts = [srv.submit("ST", r["A"], r["dims"], r["ranks"], P=5, q=1, seed=r["seed"]) for r in reqs]
-        for t in ts:
-            srv.wait(t)
-        sat = len(reqs) / (time.perf_counter() - t0)
+        for batch in batches:
+            xs = serving_inputs(torch, batch)
+            t0 = time.perf_counter()
+            ts = [srv.submit("ST", x, r["dims"], r["ranks"], P=5, q=1, seed=r["seed"]) for x, r in zip(xs, batch)]
+            for t in ts:
+                srv.wait(t)
+            sat_s += time.perf_counter() - t0
+            n += len(batch)
+            del xs, ts
+        sat_peak = srv.stats()["peak_bytes"]
+    sat = n / sat_s
     rate = load * sat
-    gaps = np.random.default_rng(1).exponential(1.0 / rate, size=len(reqs))
+    rng = np.random.default_rng(1)
+    busy_s = 0.0
     with tk.Server(budget_bytes=SERVE_BUDGET, max_inflight=16, prec=prec) as srv:
-        t0 = time.perf_counter()
-        due = t0
-        ts = []
-        for r, gap in zip(reqs, gaps):
-            due += gap
-            while time.perf_counter() < due:
-                pass
-            ts.append(srv.submit("ST", r["A"], r["dims"], r["ranks"], P=5, q=1, seed=r["seed"]))
-        for t in ts:
-            srv.wait(t)
+        for batch in batches:
+            xs = serving_inputs(torch, batch)
+            gaps = rng.exponential(1.0 / rate, size=len(batch))
+            t0 = time.perf_counter()
+            due = t0
+            ts = []
+            for x, r, gap in zip(xs, batch, gaps):
+                due += gap
+                while time.perf_counter() < due:
+                    pass
+                ts.append(srv.submit("ST", x, r["dims"], r["ranks"], P=5, q=1, seed=r["seed"]))
+            for t in ts:
+                srv.wait(t)
+            busy_s += time.perf_counter() - t0
+            del xs, ts
         st = srv.stats()
-    return {"saturation_decomps_per_s": sat, "offered_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "mean_ms": st["mean_ms"], "max_ms": st["max_ms"], "decomps_per_s": st["throughput"],
-            "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"], "failed": st["failed"]}
+    return {"requests": n, "groups": len(batches), "saturation_decomps_per_s": sat, "offered_per_s": rate,
+            "decomps_per_s": n / busy_s, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "max_ms": st["max_ms"], "peak_inflight": st["peak_inflight"],
+            "peak_bytes": max(st["peak_bytes"], sat_peak), "failed": st["failed"]}
 
 
 # ---------------------------------------------------------------- ranks
@@ -490,6 +523,30 @@ class Bench:
             raise RuntimeError("device status not OK in the profiled decompositions")
         return prof
 
+    def full_tensor_profile(self, P, prec, reps=3):
+        """Per-class times of the headline's mode-1 launches on the full input tensor alone (one power step
+        and one mode product, eager, on one stream): the decomposition profile averages them with the
+        small launches on AMM samples and truncated tensors."""
+        torch, tk, W = self.torch, self.tk, P["W"]
+        from paper_2303_11612_gb300 import _binding as B
+        A = P["ref_dev"][W["variants"][0]["gen"]]
+        dims = W["dims"]
+        L = min(W["ranks"][0] + W["P"], dims[0])
+        X = B.gaussian(dims[0], L, SEED, 0, device="cuda", stream=self.main_s)
+        U = B.gaussian(dims[0], W["ranks"][0], SEED, 1, device="cuda", stream=self.main_s)
+        for _ in range(2):
+            B.power_step(A, dims, 0, X, stream=self.main_s, prec=prec)
+            B.ttm(A, dims, 0, U, transpose=True, stream=self.main_s, prec=prec)
+        self.main_s.synchronize()
+        tk.profile_enable(True)
+        for _ in range(reps):
+            B.power_step(A, dims, 0, X, stream=self.main_s, prec=prec)
+            B.ttm(A, dims, 0, U, transpose=True, stream=self.main_s, prec=prec)
+        self.main_s.synchronize()
+        prof = {k: tk.profile_read(k) for k in B.KERNEL_CLASSES}
+        tk.profile_enable(False)
+        return prof
+
     def workload_line(self, name, forms, steps):
         """Every form of one workload: accuracy against the oracle, timed batch,
         and the gates."""
@@ -525,8 +582,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel configurations (no tuning in the synchronous warm-up calls)")
     ap.add_argument("--single", default=None,
-                    help="WORKLOAD:VARIANT -- run one decomposition of one variant after one warm-up and exit "
-                         "(profiling case)")
+                    help="WORKLOAD:VARIANT[,VARIANT...] -- run one decomposition of each listed variant after one "
+                         "warm-up and exit (profiling case)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -545,14 +602,23 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.single:
-        wname, vname = args.single.split(":") if ":" in args.single else ("cube400", args.single)
+        wname, vnames = args.single.split(":") if ":" in args.single else ("cube400", args.single)
         W = WORKLOADS[wname]
-        v = next(x for x in W["variants"] if x["name"] == vname)
-        A = torch.from_numpy(reference_tensor(v["gen"], W["dims"])).cuda()
         prec = "bf16x1" if args.prec == "all" else args.prec
-        for _ in range(2):
-            tk.decompose(W["which"], A, W["dims"], W["ranks"], P=W["P"], q=v["q"], c=v["c"], prob=v["prob"],
-                         seed=SEED, prec=prec)
+        tensors = {}
+        for vname in vnames.split(","):
+            v = next(x for x in W["variants"] if x["name"] == vname)
+            if v["gen"] not in tensors:
+                tensors[v["gen"]] = torch.from_numpy(reference_tensor(v["gen"], W["dims"])).cuda()
+            # asynchronous calls with a caller workspace: the launch configuration of the timed batch
+            ws = torch.empty(tk.workspace_size(W["which"], W["dims"], W["ranks"], P=W["P"], q=v["q"], c=v["c"],
+                                               prec=prec), dtype=torch.uint8, device="cuda")
+            for _ in range(2):
+                tk.decompose(W["which"], tensors[v["gen"]], W["dims"], W["ranks"], P=W["P"], q=v["q"], c=v["c"],
+                             prob=v["prob"], seed=SEED, prec=prec, workspace=ws, flags=tk.FLAG_ASYNC)
+            torch.cuda.synchronize()
+            if tk.last_device_status() != 0:
+                raise RuntimeError("device status not OK")
         torch.cuda.synchronize()
         print(json.dumps({"single": args.single, "prec": prec, "ok": True}))
         return 0
@@ -575,16 +641,23 @@ def main():
     head = max(cands, key=lambda p: res[p]["value"])
     prof = b.profile(P, head, reps=max(2, args.steps // 10))
 
+    full = b.full_tensor_profile(P, head)
+
     peaks, peak_kind = load_peaks()
-    power_classes = [k for k in prof if k.startswith("power")]
-    pclass = max(power_classes, key=lambda k: prof[k][1])
+    # the dominant kernel: the streaming class (power steps, mode products) with the largest share of
+    # kernel time in the profiled decompositions; the extraction chain is latency-bound (one CTA per
+    # step) and overlaps other decompositions' passes in the batch
+    stream_classes = [k for k in prof if (k.startswith("power") or k.startswith("ttm") or k == "range_wide")
+                      and prof[k][0] > 0]
+    pclass = max(stream_classes, key=lambda k: prof[k][1])
     pw_n, pw_ms, pw_bytes, pw_flops = prof[pclass]
     achieved_gbs = pw_bytes / (pw_ms / 1e3) / 1e9 if pw_ms > 0 else 0.0
     achieved_tflops = pw_flops / (pw_ms / 1e3) / 1e12 if pw_ms > 0 else 0.0
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if pclass != "power":
-        # bandwidth-bound: 4 L flops per 4-byte element (80 flops/byte at L = 80) is far
-        # below the bf16 tensor ridge (~280 flops/byte), so the bound is HBM
+    if pclass not in ("power", "ttm"):
+        # bandwidth-bound: 2 L flops per 4-byte element and pass (40 flops/byte at L = 80, 32 for a mode
+        # product with K = 64; three products in split bf16) is below the bf16 tensor ridge (~280 flops/byte),
+        # so the bound is HBM
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved_gbs / peaks["hbm_gbs"], "kernel_class": pclass, "tensor_tflops": achieved_tflops}
     else:
@@ -603,6 +676,16 @@ def main():
                 traffic = tr["dram_bytes_per_algorithmic_byte"] * pw_bytes / max(pw_n, 1)
     except Exception:
         traffic = None
+    full_launch = {}
+    for k, (n, kms, by, fl) in full.items():
+        if n and by:
+            gbs = by / (kms / 1e3) / 1e9
+            full_launch[k] = {"launches": n, "ms_per_launch": kms / n, "algorithmic_bytes_per_launch": by / n,
+                              "achieved_gbs": gbs, "frac": gbs / peaks["hbm_gbs"]}
+    roofline["mode1_full_tensor"] = {
+        "what": "the headline's mode-1 launches on the full 2.15 GB input alone: one power step (two passes) and "
+                "one mode product, eager on one stream, CUDA events around each launch",
+        "classes": full_launch}
     roofline.update({"traffic": traffic, "launches": pw_n, "ms_per_launch": pw_ms / max(pw_n, 1),
                      "algorithmic_bytes_per_launch": pw_bytes / max(pw_n, 1), "peak_kind": peak_kind,
                      "timing": "CUDA events on the launching stream around each launch, in eager decompositions "
@@ -711,13 +794,14 @@ def main():
     serving = None
     if not args.no_serving:
         try:
-            reqs = serving_requests(torch)
-            serving = {p: serving_bench(tk, torch, reqs, p) for p in dict.fromkeys([head, "fp32"]) if p in forms}
-            serving["sample"] = (f"{len(reqs)} randomized ST-HOSVD requests (P=5, q=1), orders 3/4, extents "
-                                 f"U{{32..256}} (order 3) / U{{32..96}} (order 4), ranks U{{4..32}}, low-rank + 1e-2 "
-                                 f"noise, device-resident; budget {SERVE_BUDGET >> 30} GB, 16 streams; latencies at "
-                                 f"0.7x the saturation throughput, Poisson arrivals")
-            del reqs
+            specs = serving_specs()
+            serving = {p: serving_bench(tk, torch, specs, p) for p in dict.fromkeys([head, "fp32"]) if p in forms}
+            serving["stream"] = (f"{len(specs)} randomized ST-HOSVD requests (P=5, q=1), order 3 or 4, every extent "
+                                 f"U{{32..256}}, ranks U{{4..32}}, low-rank + 1e-2 noise FP32 (order 4 up to 17 GB); "
+                                 f"server budget {SERVE_BUDGET >> 30} GB, 16 streams; inputs generated on the device "
+                                 f"in groups of at most {SERVE_RESIDENT >> 30} GB before each group (untimed); "
+                                 f"saturation = each group at once; latency under Poisson arrivals at 0.7x the "
+                                 f"saturation rate within each group")
         except Exception as exc:  # noqa: BLE001
             serving = {"error": str(exc)[:300]}
     clk = b.clocks.stop()

@@ -267,6 +267,7 @@ struct Work {
     void* Y; void* QY;     // half steps: T x L product and its orthonormal factor
     void* sumsq;
     double* norms;     // [2]: ||A||^2, ||G||^2
+    int wide_stages = kWideStagesAlone;   // FP32 ring depth of the wide tensor-core kernels
 };
 
 void carve(const Plan& p, Arena& a, Work& w) {
@@ -323,7 +324,7 @@ cudaError_t power_step(const T* M, const ModePlan& mp, const T* X_in, T* X_out, 
             return launch_power_tc(M, mp.mv, X_in, mp.L, X_out, w.partials, w.status, num_sms(), s);
         if (mp.wide) {
             const cudaError_t e = launch_power_wide(M, mp.mv, X_in, mp.L, X_out, mp.wide_split, false, 0, 0,
-                                                    w.partials, w.status, num_sms(), s);
+                                                    w.partials, w.status, num_sms(), s, w.wide_stages);
             if (e != cudaErrorNotSupported) return e;
         }
     }
@@ -408,7 +409,8 @@ cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t
             }
             cudaError_t e = cudaErrorNotSupported;
             if constexpr (sizeof(T) == 4) {
-                if (mp.half_tc) e = launch_wide_tn(M, mp.mv, xin, L, Y, w.partials, w.status, num_sms(), s);
+                if (mp.half_tc) e = launch_wide_tn(M, mp.mv, xin, L, Y, w.partials, w.status, num_sms(), s,
+                                                   w.wide_stages);
             }
             if (e == cudaErrorNotSupported) e = launch_gemm_tn<T>(M, mp.v.i, mp.T, xin, L, Y, s);
             TK_TRY(e);
@@ -416,7 +418,8 @@ cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t
             ++f;
             e = cudaErrorNotSupported;
             if constexpr (sizeof(T) == 4) {
-                if (mp.half_tc) e = launch_wide_nn(M, mp.mv, QY, L, X1, w.partials, w.status, num_sms(), s);
+                if (mp.half_tc) e = launch_wide_nn(M, mp.mv, QY, L, X1, w.partials, w.status, num_sms(), s,
+                                                   w.wide_stages);
             }
             if (e == cudaErrorNotSupported) e = launch_gemm_nn<T>(M, mp.v.i, mp.T, QY, L, X1, w.partials, num_sms(), s);
             TK_TRY(e);
@@ -444,7 +447,7 @@ cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t
     if constexpr (sizeof(T) == 4) {
         if (mp.wide_range)
             first = launch_power_wide(M, mp.mv, nullptr, L, X1, mp.wide_split, true, seed, stream_id(0, n),
-                                      w.partials, w.status, num_sms(), s);
+                                      w.partials, w.status, num_sms(), s, w.wide_stages);
     }
     if (first == cudaErrorNotSupported)
         first = launch_power<T>(M, mp.mv, nullptr, L, X1, w.partials, mp.pp, true, seed, stream_id(0, n), s);
@@ -466,7 +469,7 @@ cudaError_t mode_product(const Plan& p, const T* A, const ModeView& v, const T* 
         if (p.prec != TUCKER_SK_FP32) {
             cudaError_t e = launch_ttm_tc(A, v, U, K, 1, v.i, out, w.status, num_sms(), s);
             if (e == cudaErrorNotSupported && wide_ttm_supported(v, K))
-                e = launch_ttm_wide(A, v, U, K, 1, v.i, out, w.partials, w.status, num_sms(), s);
+                e = launch_ttm_wide(A, v, U, K, 1, v.i, out, w.partials, w.status, num_sms(), s, w.wide_stages);
             if (e != cudaErrorNotSupported) return e;
         }
     }
@@ -596,6 +599,8 @@ tucker_status driver(bool st, const void* A, tucker_dtype dt, const int64_t* dim
     b.base = base;
     b.cap = need;
     carve(p, b, w);
+    // asynchronous calls run beside others (batches, the serving loop): keep the shallow rings
+    w.wide_stages = async ? kWideStagesShared : kWideStagesAlone;
 
     char* sp = (char*)stage_buf;
     const void* dA = A;

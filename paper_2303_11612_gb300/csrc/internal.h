@@ -87,21 +87,28 @@ bool wide_ttm_supported(const ModeView& v, int64_t K_out);      // mode product
 size_t wide_ttm_scratch_bytes(const ModeView& v, int64_t K_out);
 size_t wide_power_scratch_bytes(const ModeView& v, int L, int num_sms);
 // out = A x_n M (split bf16, FP32 accumulate), out[j K_out + o] as launch_ttm.
+// FP32 ring depth of the wide kernels: kWideStagesShared (3) keeps a wide CTA's
+// shared memory small enough that another decomposition's extraction CTA fits
+// on the same SM (batches and served requests run many decompositions at
+// once); a call that runs alone takes as many stages as shared memory holds.
+constexpr int kWideStagesShared = 3;
+constexpr int kWideStagesAlone = 6;
 cudaError_t launch_ttm_wide(const float* A, const ModeView& v, const float* Mp, int64_t K_out, int64_t ld_i,
-                            int64_t ld_k, float* out, void* scratch, int* status, int num_sms, cudaStream_t s);
+                            int64_t ld_k, float* out, void* scratch, int* status, int num_sms, cudaStream_t s,
+                            int max_stages = kWideStagesAlone);
 // X_out = A_(n) (A_(n)^T X_in) in two passes (range == false), or Y = A_(n) Omega
 // with Omega J_n x L from the Philox stream (range == true, X_in unused); split:
 // split-bf16 operands, else single-pass bf16.
 cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_in, int L, float* X_out, bool split,
                               bool range, uint64_t seed, uint32_t stream_id, void* scratch, int* status, int num_sms,
-                              cudaStream_t s);
+                              cudaStream_t s, int max_stages = kWideStagesAlone);
 
 // half steps of the AMM sketch on the tensor cores (split bf16), scratch as launch_power_wide:
 // Y (J x L, column-major) = A_(n)^T X, and X_out = A_(n) Q with Q J x L column-major
 cudaError_t launch_wide_tn(const float* A, const ModeView& v, const float* X, int L, float* Y, void* scratch,
-                           int* status, int num_sms, cudaStream_t s);
+                           int* status, int num_sms, cudaStream_t s, int max_stages = kWideStagesAlone);
 cudaError_t launch_wide_nn(const float* A, const ModeView& v, const float* Q, int L, float* X_out, void* scratch,
-                           int* status, int num_sms, cudaStream_t s);
+                           int* status, int num_sms, cudaStream_t s, int max_stages = kWideStagesAlone);
 
 // ---- half steps of the power scheme on the gathered AMM sample (kernels_half.cu)
 bool half_supported(int L);

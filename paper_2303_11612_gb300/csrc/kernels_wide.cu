@@ -156,28 +156,34 @@ constexpr int kAJB = 128;                  // fibers per tile
 constexpr int kABox = kAJB * 128;          // FP32 box: 32 values i x 128 fibers = 16 KB
 constexpr int kAUnit = 2 * kABox;          // FP32 unit: 64 values i
 constexpr int kAHalf = kAJB * 128;         // one bf16 part of a unit: 64 values i x 128 fibers
-constexpr int kAFStages = 3;
+constexpr int kAFMin = 3;                  // FP32 ring stages: as many as shared memory holds, 3 .. 6
+constexpr int kAFMax = 6;
 constexpr int kACStages = 2;
 constexpr int kAUStages = 2;
 constexpr int kAConv = 16;                 // converter warps 2 .. 17
 constexpr int kAEpi = 4;                   // read-back warps 18 .. 21
 constexpr int kAThreads = 64 + 32 * kAConv + 32 * kAEpi;
-constexpr int kABars = 2 * kAFStages + 2 * kACStages + 2 * kAUStages + 5;
+constexpr int kABars = 2 * kAFMax + 2 * kACStages + 2 * kAUStages + 5;
 static_assert(kABars * 8 + 8 <= 256, "barrier area");
 
 struct WideALayout {
-    int nu = 0, Np = 0, parts = 1;
+    int nu = 0, Np = 0, parts = 1, fst = kAFMin;
     size_t ubytes = 0, c_off = 0, u_off = 0, bar_off = 0, bytes = 0;
     uint32_t tmem_cols = 0;
 };
 
-WideALayout wide_a_layout(int I, int K_out, bool split) {
+WideALayout wide_a_layout(int I, int K_out, bool split, int max_stages = kAFMax) {
     WideALayout t;
     t.nu = (I + 63) / 64;
     t.Np = (K_out + 15) / 16 * 16;
     t.parts = split ? 2 : 1;
     t.ubytes = (size_t)t.parts * t.Np * 128;
-    t.c_off = (size_t)kAFStages * kAUnit;
+    // the FP32 ring takes what the converted ring, the image ring and the barriers leave
+    // (each stage keeps 32 KB of the tensor in flight per SM)
+    const size_t rest = (size_t)kACStages * t.parts * kAHalf + (size_t)kAUStages * t.ubytes + 256 + 1024;
+    if (rest + (size_t)kAFMin * kAUnit <= kWSmemMax)
+        t.fst = (int)std::max<size_t>(kAFMin, std::min<size_t>(std::min(kAFMax, max_stages), (kWSmemMax - rest) / kAUnit));
+    t.c_off = (size_t)t.fst * kAUnit;
     t.u_off = t.c_off + (size_t)kACStages * t.parts * kAHalf;
     t.bar_off = t.u_off + (size_t)kAUStages * t.ubytes;
     t.bytes = t.bar_off + 256 + 1024;
@@ -200,18 +206,18 @@ template <bool SPLIT, int OUT, bool STRIDED>
 __global__ void __launch_bounds__(kAThreads, 1)
     wide_ttm_kernel(const __grid_constant__ CUtensorMap map, int I, int64_t J, const unsigned char* __restrict__ uimg,
                     int K_out, int Np, float* __restrict__ out, unsigned char* __restrict__ w_hi,
-                    unsigned char* __restrict__ w_lo, int64_t tiles, int nu, int64_t lf, int* status) {
+                    unsigned char* __restrict__ w_lo, int64_t tiles, int nu, int64_t lf, int* status, int fst) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024 - (tma::smem_addr(smem_raw) & 1023)) & 1023);
     constexpr int parts = SPLIT ? 2 : 1;
     const uint32_t ubytes = (uint32_t)(parts * Np * 128);
     unsigned char* F = smem;
-    unsigned char* Cb = smem + (size_t)kAFStages * kAUnit;
+    unsigned char* Cb = smem + (size_t)fst * kAUnit;
     unsigned char* Us = Cb + (size_t)kACStages * parts * kAHalf;
     uint64_t* bar = reinterpret_cast<uint64_t*>(Us + (size_t)kAUStages * ubytes);
     uint64_t* f_full = bar;
-    uint64_t* f_empty = f_full + kAFStages;
-    uint64_t* c_full = f_empty + kAFStages;
+    uint64_t* f_empty = f_full + kAFMax;
+    uint64_t* c_full = f_empty + kAFMax;
     uint64_t* c_empty = c_full + kACStages;
     uint64_t* u_full = c_empty + kACStages;
     uint64_t* u_empty = u_full + kAUStages;
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(kAThreads, 1)
 
     if (tid == 0) {
         for (int k = 0; k < kABars; ++k) tc::mbar_init(&bar[k], 1);
-        for (int k = 0; k < kAFStages; ++k) tc::mbar_init(&f_empty[k], kAConv);
+        for (int k = 0; k < fst; ++k) tc::mbar_init(&f_empty[k], kAConv);
         for (int k = 0; k < kACStages; ++k) tc::mbar_init(&c_full[k], kAConv);
         for (int k = 0; k < 2; ++k) tc::mbar_init(&d_empty[k], kAEpi);
         *flag = 0;
@@ -240,15 +246,17 @@ __global__ void __launch_bounds__(kAThreads, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
+        // two producers: lane 0 streams the tensor as far ahead as the FP32 ring
+        // allows; lane 1 streams the operand image (from L2) one unit ahead of each
+        // product, so the short image ring never holds back the tensor's loads
         if (lane == 0) {
             int64_t g = 0;
-            bool ok = true;
-            for (int64_t k = 0; k < nloc && ok; ++k) {
+            for (int64_t k = 0; k < nloc; ++k) {
                 const int j0 = (int)((blockIdx.x + k * gridDim.x) * kAJB);
+                bool ok = true;
                 for (int u = 0; u < nu; ++u, ++g) {
-                    const int fs = (int)(g % kAFStages), us = (int)(g % kAUStages);
-                    if ((g >= kAFStages && !wait_bar(&f_empty[fs], (uint32_t)((g / kAFStages - 1) & 1), flag)) ||
-                        (g >= kAUStages && !wait_bar(&u_empty[us], (uint32_t)((g / kAUStages - 1) & 1), flag))) {
+                    const int fs = (int)(g % fst);
+                    if (g >= fst && !wait_bar(&f_empty[fs], (uint32_t)((g / fst - 1) & 1), flag)) {
                         fail(flag, status);
                         ok = false;
                         break;
@@ -268,14 +276,31 @@ __global__ void __launch_bounds__(kAThreads, 1)
                         tma::load_2d(dst, &map, 64 * u, j0, &f_full[fs]);
                         tma::load_2d(dst + kABox, &map, 64 * u + 32, j0, &f_full[fs]);
                     }
-                    tma::expect_tx(&u_full[us], ubytes);
-                    tma::bulk_load(Us + (size_t)us * ubytes, uimg + (size_t)u * ubytes, ubytes, &u_full[us]);
                 }
+                if (!ok) break;
             }
             if (*flag) {
                 // the copies issued so far land before the kernel returns
-                const int64_t f0 = g > kAFStages ? g - kAFStages : 0;
-                for (int64_t gg = f0; gg < g; ++gg) drain(&f_full[gg % kAFStages], (uint32_t)((gg / kAFStages) & 1));
+                const int64_t f0 = g > fst ? g - fst : 0;
+                for (int64_t gg = f0; gg < g; ++gg) drain(&f_full[gg % fst], (uint32_t)((gg / fst) & 1));
+            }
+        } else if (lane == 1) {
+            int64_t g = 0;
+            for (int64_t k = 0; k < nloc; ++k) {
+                bool ok = true;
+                for (int u = 0; u < nu; ++u, ++g) {
+                    const int us = (int)(g % kAUStages);
+                    if (g >= kAUStages && !wait_bar(&u_empty[us], (uint32_t)((g / kAUStages - 1) & 1), flag)) {
+                        fail(flag, status);
+                        ok = false;
+                        break;
+                    }
+                    tma::expect_tx(&u_full[us], ubytes);
+                    tma::bulk_load(Us + (size_t)us * ubytes, uimg + (size_t)u * ubytes, ubytes, &u_full[us]);
+                }
+                if (!ok) break;
+            }
+            if (*flag) {
                 const int64_t u0 = g > kAUStages ? g - kAUStages : 0;
                 for (int64_t gg = u0; gg < g; ++gg) drain(&u_full[gg % kAUStages], (uint32_t)((gg / kAUStages) & 1));
             }
@@ -336,8 +361,8 @@ __global__ void __launch_bounds__(kAThreads, 1)
         constexpr int kTasks = (kAJB * 8) / (kAConv * 32);
         for (int64_t k = 0; k < nloc && ok; ++k) {
             for (int u = 0; u < nu; ++u, ++g) {
-                const int fs = (int)(g % kAFStages), cs = (int)(g % kACStages);
-                if (!wait_bar(&f_full[fs], (uint32_t)((g / kAFStages) & 1), flag)) {
+                const int fs = (int)(g % fst), cs = (int)(g % kACStages);
+                if (!wait_bar(&f_full[fs], (uint32_t)((g / fst) & 1), flag)) {
                     ok = false;
                     break;
                 }
@@ -466,21 +491,22 @@ constexpr int kBJB = 64;                   // fibers per chunk (K of the product
 constexpr int kBBox = kBJB * 128;          // FP32 box: 32 values i x 64 fibers = 8 KB
 constexpr int kBUnit = 4 * kBBox;          // FP32 unit: 128 rows i x 64 fibers = 32 KB
 constexpr int kBHalf = 128 * kBJB * 2;     // one bf16 part of a unit: 16 KB
-constexpr int kBFStages = 3;
+constexpr int kBFMin = 3;                  // FP32 ring stages: as many as shared memory holds, 3 .. 6
+constexpr int kBFMax = 6;
 constexpr int kBCStages = 2;
 constexpr int kBWStages = 2;
 constexpr int kBConv = 8;                  // converter (and generator, read-back) warps 2 .. 9
 constexpr int kBThreads = 64 + 32 * kBConv;
 constexpr int kBMaxBlocks = 4;             // 128-row blocks per CTA
-constexpr int kBBars = 2 * kBFStages + 2 * kBCStages + 2 * kBWStages + 1;
+constexpr int kBBars = 2 * kBFMax + 2 * kBCStages + 2 * kBWStages + 1;
 static_assert(kBBars * 8 + 8 <= 256, "barrier area");
 
 struct WideBLayout {
-    int Np = 0, parts = 1, nb = 0, groups = 0;
+    int Np = 0, parts = 1, nb = 0, groups = 0, fst = kBFMin;
     size_t wbytes = 0, c_off = 0, w_off = 0, bar_off = 0, bytes = 0;
 };
 
-WideBLayout wide_b_layout(int I, int L, bool split) {
+WideBLayout wide_b_layout(int I, int L, bool split, int max_stages = kBFMax) {
     WideBLayout t;
     t.Np = (L + 15) / 16 * 16;
     t.parts = split ? 2 : 1;
@@ -488,7 +514,10 @@ WideBLayout wide_b_layout(int I, int L, bool split) {
     t.nb = std::min(kBMaxBlocks, std::min(blocks, 512 / t.Np));
     t.groups = (blocks + t.nb - 1) / t.nb;
     t.wbytes = (size_t)t.parts * t.Np * 128;
-    t.c_off = (size_t)kBFStages * kBUnit;
+    const size_t rest = (size_t)kBCStages * t.parts * kBHalf + (size_t)kBWStages * t.wbytes + 256 + 1024;
+    if (rest + (size_t)kBFMin * kBUnit <= kWSmemMax)
+        t.fst = (int)std::max<size_t>(kBFMin, std::min<size_t>(std::min(kBFMax, max_stages), (kWSmemMax - rest) / kBUnit));
+    t.c_off = (size_t)t.fst * kBUnit;
     t.w_off = t.c_off + (size_t)kBCStages * t.parts * kBHalf;
     t.bar_off = t.w_off + (size_t)kBWStages * t.wbytes;
     t.bytes = t.bar_off + 256 + 1024;
@@ -505,18 +534,18 @@ __global__ void __launch_bounds__(kBThreads, 1)
     wide_power2_kernel(const __grid_constant__ CUtensorMap map, int I, int64_t J, int L, int Np,
                        const unsigned char* __restrict__ w_hi, const unsigned char* __restrict__ w_lo, uint64_t seed,
                        uint32_t stream_id, float* __restrict__ partial, int groups, int nb, int64_t chunks,
-                       int64_t lf, int* status) {
+                       int64_t lf, int* status, int fst) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024 - (tma::smem_addr(smem_raw) & 1023)) & 1023);
     constexpr int parts = SPLIT ? 2 : 1;
     const uint32_t wbytes = (uint32_t)(parts * Np * 128);
     unsigned char* F = smem;
-    unsigned char* Cb = smem + (size_t)kBFStages * kBUnit;
+    unsigned char* Cb = smem + (size_t)fst * kBUnit;
     unsigned char* Ws = Cb + (size_t)kBCStages * parts * kBHalf;
     uint64_t* bar = reinterpret_cast<uint64_t*>(Ws + (size_t)kBWStages * wbytes);
     uint64_t* f_full = bar;
-    uint64_t* f_empty = f_full + kBFStages;
-    uint64_t* c_full = f_empty + kBFStages;
+    uint64_t* f_empty = f_full + kBFMax;
+    uint64_t* c_full = f_empty + kBFMax;
     uint64_t* c_empty = c_full + kBCStages;
     uint64_t* w_full = c_empty + kBCStages;
     uint64_t* w_empty = w_full + kBWStages;
@@ -533,7 +562,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
 
     if (tid == 0) {
         for (int k = 0; k < kBBars; ++k) tc::mbar_init(&bar[k], 1);
-        for (int k = 0; k < kBFStages; ++k) tc::mbar_init(&f_empty[k], kBConv);
+        for (int k = 0; k < fst; ++k) tc::mbar_init(&f_empty[k], kBConv);
         for (int k = 0; k < kBCStages; ++k) tc::mbar_init(&c_full[k], kBConv);
         if (RANGE)
             for (int k = 0; k < kBWStages; ++k) tc::mbar_init(&w_full[k], kBConv);
@@ -567,8 +596,8 @@ __global__ void __launch_bounds__(kBThreads, 1)
                     ++wc;
                 }
                 for (int b = 0; b < nbg; ++b, ++g) {
-                    const int fs = (int)(g % kBFStages);
-                    if (g >= kBFStages && !wait_bar(&f_empty[fs], (uint32_t)((g / kBFStages - 1) & 1), flag)) {
+                    const int fs = (int)(g % fst);
+                    if (g >= fst && !wait_bar(&f_empty[fs], (uint32_t)((g / fst - 1) & 1), flag)) {
                         fail(flag, status);
                         ok = false;
                         break;
@@ -592,8 +621,8 @@ __global__ void __launch_bounds__(kBThreads, 1)
                 }
             }
             if (*flag) {
-                const int64_t f0 = g > kBFStages ? g - kBFStages : 0;
-                for (int64_t gg = f0; gg < g; ++gg) drain(&f_full[gg % kBFStages], (uint32_t)((gg / kBFStages) & 1));
+                const int64_t f0 = g > fst ? g - fst : 0;
+                for (int64_t gg = f0; gg < g; ++gg) drain(&f_full[gg % fst], (uint32_t)((gg / fst) & 1));
                 if (!RANGE) {
                     const int64_t w0 = wc > kBWStages ? wc - kBWStages : 0;
                     for (int64_t gg = w0; gg < wc; ++gg)
@@ -687,8 +716,8 @@ __global__ void __launch_bounds__(kBThreads, 1)
                 if (lane == 0) tc::mbar_arrive(&w_full[ws]);
             }
             for (int b = 0; b < nbg; ++b, ++g) {
-                const int fs = (int)(g % kBFStages), cs = (int)(g % kBCStages);
-                if (!wait_bar(&f_full[fs], (uint32_t)((g / kBFStages) & 1), flag)) {
+                const int fs = (int)(g % fst), cs = (int)(g % kBCStages);
+                if (!wait_bar(&f_full[fs], (uint32_t)((g / fst) & 1), flag)) {
                     ok = false;
                     break;
                 }
@@ -852,12 +881,13 @@ size_t wide_power_scratch_bytes(const ModeView& v, int L, int num_sms) {
 }
 
 cudaError_t launch_ttm_wide(const float* A, const ModeView& v, const float* Mp, int64_t K_out, int64_t ld_i,
-                            int64_t ld_k, float* out, void* scratch, int* status, int num_sms, cudaStream_t s) {
+                            int64_t ld_k, float* out, void* scratch, int* status, int num_sms, cudaStream_t s,
+                            int max_stages) {
     if (!wide_ttm_supported(v, K_out) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
     const int I = (int)v.i;
     const int64_t J = v.fibers();
     const bool strided = v.lf > 1;
-    const WideALayout t = wide_a_layout(I, (int)K_out, true);
+    const WideALayout t = wide_a_layout(I, (int)K_out, true, max_stages);
     CUtensorMap map;
     if (!make_fiber_map(&map, A, v, kAJB)) return cudaErrorNotSupported;
     unsigned char* img = reinterpret_cast<unsigned char*>(scratch);
@@ -871,7 +901,7 @@ cudaError_t launch_ttm_wide(const float* A, const ModeView& v, const float* Mp, 
         auto k = strided ? wide_ttm_kernel<true, 0, true> : wide_ttm_kernel<true, 0, false>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.bytes);
         k<<<grid_for(tiles, num_sms), kAThreads, t.bytes, s>>>(map, I, J, img, (int)K_out, t.Np, out, nullptr,
-                                                                 nullptr, tiles, t.nu, v.lf, status);
+                                                                 nullptr, tiles, t.nu, v.lf, status, t.fst);
         note_launch();
     }
     return cudaGetLastError();
@@ -879,13 +909,13 @@ cudaError_t launch_ttm_wide(const float* A, const ModeView& v, const float* Mp, 
 
 cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_in, int L, float* X_out, bool split,
                               bool range, uint64_t seed, uint32_t stream_id, void* scratch, int* status, int num_sms,
-                              cudaStream_t s) {
+                              cudaStream_t s, int max_stages) {
     if (!wide_supported(v, L) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
     const int I = (int)v.i;
     const int64_t J = v.fibers();
     const bool strided = v.lf > 1;
-    const WideALayout ta = wide_a_layout(I, L, split);
-    const WideBLayout tb = wide_b_layout(I, L, split);
+    const WideALayout ta = wide_a_layout(I, L, split, max_stages);
+    const WideBLayout tb = wide_b_layout(I, L, split, max_stages);
     const int64_t chunks = (J + kBJB - 1) / kBJB;
     const int64_t R = std::max<int64_t>(1, std::min<int64_t>(chunks, num_sms / tb.groups));
     // scratch carve: M^T image | W hi | W lo | partials (sizes as wide_power_scratch_bytes, split)
@@ -915,7 +945,7 @@ cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_
                        : (strided ? wide_ttm_kernel<false, 1, true> : wide_ttm_kernel<false, 1, false>);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ta.bytes);
         k<<<grid_for(tiles, num_sms), kAThreads, ta.bytes, s>>>(map, I, J, img, L, ta.Np, nullptr, whi, wlo, tiles,
-                                                                  ta.nu, v.lf, status);
+                                                                  ta.nu, v.lf, status, ta.fst);
         note_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -935,7 +965,7 @@ cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_
                       : (range ? wide_power2_kernel<false, true, false> : wide_power2_kernel<false, false, false>);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb.bytes);
         k<<<(int)(R * tb.groups), kBThreads, tb.bytes, s>>>(map, I, J, L, tb.Np, whi, wlo, seed, stream_id, part,
-                                                              tb.groups, tb.nb, chunks, v.lf, status);
+                                                              tb.groups, tb.nb, chunks, v.lf, status, tb.fst);
         note_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -950,11 +980,11 @@ namespace tk {
 // Y (J x L, column-major FP32) = A_(n)^T X: the first half of a half step of
 // the AMM sketch, on the tensor cores (split bf16). Scratch as launch_power_wide.
 cudaError_t launch_wide_tn(const float* A, const ModeView& v, const float* X, int L, float* Y, void* scratch,
-                           int* status, int num_sms, cudaStream_t s) {
+                           int* status, int num_sms, cudaStream_t s, int max_stages) {
     if (!wide_supported(v, L) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
     const int I = (int)v.i;
     const int64_t J = v.fibers();
-    const WideALayout ta = wide_a_layout(I, L, true);
+    const WideALayout ta = wide_a_layout(I, L, true, max_stages);
     CUtensorMap map;
     if (!make_fiber_map(&map, A, v, kAJB)) return cudaErrorNotSupported;
     unsigned char* img = reinterpret_cast<unsigned char*>(scratch);
@@ -967,7 +997,7 @@ cudaError_t launch_wide_tn(const float* A, const ModeView& v, const float* X, in
     auto k = v.lf > 1 ? wide_ttm_kernel<true, 2, true> : wide_ttm_kernel<true, 2, false>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ta.bytes);
     k<<<grid_for(tiles, num_sms), kAThreads, ta.bytes, s>>>(map, I, J, img, L, ta.Np, Y, nullptr, nullptr, tiles,
-                                                              ta.nu, v.lf, status);
+                                                              ta.nu, v.lf, status, ta.fst);
     note_launch();
     return cudaGetLastError();
 }
@@ -975,12 +1005,12 @@ cudaError_t launch_wide_tn(const float* A, const ModeView& v, const float* X, in
 // X_out (I x L) = A_(n) Q with Q (J x L, column-major FP32): the second half of a
 // half step, on the tensor cores (split bf16). Scratch as launch_power_wide.
 cudaError_t launch_wide_nn(const float* A, const ModeView& v, const float* Q, int L, float* X_out, void* scratch,
-                           int* status, int num_sms, cudaStream_t s) {
+                           int* status, int num_sms, cudaStream_t s, int max_stages) {
     if (!wide_supported(v, L) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
     const int I = (int)v.i;
     const int64_t J = v.fibers();
     const WideALayout ta = wide_a_layout(I, L, true);
-    const WideBLayout tb = wide_b_layout(I, L, true);
+    const WideBLayout tb = wide_b_layout(I, L, true, max_stages);
     const int64_t chunks = (J + kBJB - 1) / kBJB;
     const int64_t R = std::max<int64_t>(1, std::min<int64_t>(chunks, num_sms / tb.groups));
     unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
@@ -1002,7 +1032,7 @@ cudaError_t launch_wide_nn(const float* A, const ModeView& v, const float* Q, in
         auto k = v.lf > 1 ? wide_power2_kernel<true, false, true> : wide_power2_kernel<true, false, false>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tb.bytes);
         k<<<(int)(R * tb.groups), kBThreads, tb.bytes, s>>>(map, I, J, L, tb.Np, whi, wlo, 0, 0, part, tb.groups,
-                                                              tb.nb, chunks, v.lf, status);
+                                                              tb.nb, chunks, v.lf, status, tb.fst);
         note_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -9,7 +9,11 @@
 // stream-ordered free), then admits from the head of the queue. Device memory
 // comes from a pool private to the server (stream-ordered allocation, kept
 // cached up to the budget). Head-of-line order is strict, so a large request
-// is never overtaken indefinitely by small ones.
+// is never overtaken indefinitely by small ones. Host inputs are staged by one
+// copy stream shared by all requests, in admission order: concurrent
+// host-to-device copies on many streams share the chip link badly (a third of
+// one stream's rate in eight, measured), while one stream keeps it busy and
+// each request's decomposition starts as soon as its own copy lands.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -64,6 +68,8 @@ struct Request {
 struct Slot {
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_alloc = nullptr;   // the request's block is allocated (on s)
+    cudaEvent_t ev_copy = nullptr;    // its input has landed (on the copy stream)
     int* h_status = nullptr;      // pinned word the request's device status is copied into
     Request* r = nullptr;
 };
@@ -77,6 +83,7 @@ struct tucker_server {
     std::vector<std::unique_ptr<Request>> reqs;      // index ticket - 1
     std::vector<Slot> slots;
     cudaMemPool_t pool = nullptr;
+    cudaStream_t copy_s = nullptr;    // host-to-device staging of every request's input
     int device = 0;
     size_t budget = 0, in_use = 0, peak = 0;
     int inflight = 0, peak_inflight = 0;
@@ -107,7 +114,11 @@ bool tucker_server::launch(Slot& sl, Request* r) {
     const void* dA = r->A;
     if (r->hostA) {
         dA = b;
-        cudaMemcpyAsync(b, r->A, r->a_bytes, cudaMemcpyHostToDevice, s);
+        cudaEventRecord(sl.ev_alloc, s);
+        cudaStreamWaitEvent(copy_s, sl.ev_alloc, 0);
+        cudaMemcpyAsync(b, r->A, r->a_bytes, cudaMemcpyHostToDevice, copy_s);
+        cudaEventRecord(sl.ev_copy, copy_s);
+        cudaStreamWaitEvent(s, sl.ev_copy, 0);
         b += up(r->a_bytes);
     }
     void* dU[kMaxN];
@@ -242,10 +253,13 @@ tucker_status tucker_server_create(const tucker_server_opts* opts, tucker_server
         uint64_t keep = s->budget;
         e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_s, cudaStreamNonBlocking);
     s->slots.resize(opts->max_inflight);
     for (Slot& sl : s->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_alloc, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_copy, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_status, sizeof(int));
         if (e == cudaSuccess) *sl.h_status = 0;
     }
@@ -254,8 +268,11 @@ tucker_status tucker_server_create(const tucker_server_opts* opts, tucker_server
         for (Slot& sl : s->slots) {
             if (sl.s) cudaStreamDestroy(sl.s);
             if (sl.ev) cudaEventDestroy(sl.ev);
+            if (sl.ev_alloc) cudaEventDestroy(sl.ev_alloc);
+            if (sl.ev_copy) cudaEventDestroy(sl.ev_copy);
             if (sl.h_status) cudaFreeHost(sl.h_status);
         }
+        if (s->copy_s) cudaStreamDestroy(s->copy_s);
         if (s->pool) cudaMemPoolDestroy(s->pool);
         return e == cudaErrorMemoryAllocation ? TUCKER_ERR_OOM : TUCKER_ERR_CUDA;
     }
@@ -385,8 +402,12 @@ tucker_status tucker_server_destroy(tucker_server* srv) {
         cudaStreamSynchronize(sl.s);
         cudaStreamDestroy(sl.s);
         cudaEventDestroy(sl.ev);
+        cudaEventDestroy(sl.ev_alloc);
+        cudaEventDestroy(sl.ev_copy);
         cudaFreeHost(sl.h_status);
     }
+    cudaStreamSynchronize(srv->copy_s);
+    cudaStreamDestroy(srv->copy_s);
     cudaMemPoolDestroy(srv->pool);
     delete srv;
     return TUCKER_OK;

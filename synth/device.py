@@ -60,3 +60,34 @@ def tucker_tensor(torch, dims, core_dims, rel_noise=1e-2, seed=0, core_scale=Non
         E = torch.randn(X.shape, device=device, generator=g)
         X = X + rel_noise * E / E.norm()
     return X.contiguous().view(-1)
+
+
+def tucker_tensor_lean(torch, dims, core_dims, rel_noise=1e-2, seed=0, device="cuda", chunk=1 << 27):
+    """The recipe of ``tucker_tensor`` for tensors of many GB: the mode products
+    are applied from the last mode to the first, so that the first lands on the
+    innermost axis and the result is built contiguous without a copy, and the
+    noise is drawn in chunks from per-chunk generators (one pass for its norm, a
+    second, re-seeded, to add it), so that the peak footprint is the tensor
+    itself plus one chunk. Flat FP32, i_1 fastest."""
+    g = _gen(torch, seed, device)
+    N = len(dims)
+    X = torch.randn(*reversed(core_dims), device=device, generator=g)
+    Us = [torch.linalg.qr(torch.randn(dims[m], core_dims[m], device=device, generator=g))[0] for m in range(N)]
+    for m in reversed(range(N)):                   # mode m is torch axis N-1-m
+        X = torch.tensordot(X, Us[m], dims=([N - 1 - m], [1]))
+        if m > 0:
+            X = torch.movedim(X, -1, N - 1 - m)
+    X = X.reshape(-1)
+    X /= X.norm()
+    if rel_noise > 0:
+        n = X.numel()
+        starts = range(0, n, chunk)
+        ss = 0.0
+        for k, a in enumerate(starts):
+            e = torch.randn(min(chunk, n - a), device=device, generator=_gen(torch, seed * 1_000_003 + k + 1, device))
+            ss += float(torch.dot(e, e))
+        scale = rel_noise / float(np.sqrt(ss))
+        for k, a in enumerate(starts):
+            e = torch.randn(min(chunk, n - a), device=device, generator=_gen(torch, seed * 1_000_003 + k + 1, device))
+            X[a:a + e.numel()].add_(e, alpha=scale)
+    return X
