@@ -73,9 +73,10 @@ typedef enum { TUCKER_PROB_NEARLY_OPTIMAL = 0, TUCKER_PROB_UNIFORM = 1 } tucker_
  * computes in FP64. With TUCKER_F32 the sketch and the mode-n products compute
  * in FP32 (or the tensor-core form opts->prec selects); the orthonormalisation
  * sums its Gram matrices of exact FP32 products in FP32 pairs and does the small
- * triangular algebra (Cholesky, inverses) in double-float, two FP32 words
- * (about 2^-47); the small SVD is a one-sided Jacobi in FP32 with its coupling
- * sums in FP32 pairs (tucker_leading_factor). */
+ * triangular algebra (Cholesky, inverses, triangle products) in double-float,
+ * two FP32 words (about 2^-47); the small SVD is a QR with column pivoting
+ * (Householder, FP32 with paired dot products) followed by a one-sided Jacobi
+ * in FP32 with its coupling sums in FP32 pairs (tucker_leading_factor). */
 typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
 
 /* Which sketch is taken.
@@ -104,7 +105,9 @@ typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1, TUCKER_FORM_RELATED
  *  BF16: tcgen05 tensor cores with FP32 accumulation, split form: A and the
  *    intermediate A^T X are each held as a bf16 high part plus a bf16 low part
  *    (about 16 significant bits), so the sketch is of A itself; A is still read
- *    once, in FP32. Used where I_n <= 512 and L_n <= 64; other modes run FP32.
+ *    once, in FP32. One fused pass where I_n <= 512 and L_n <= 64; beyond that
+ *    (I_n <= 1024, L_n <= 128) two passes, W = A^T X then A W, on contiguous
+ *    fibers or strides that are multiples of 32; other modes run FP32.
  *  BF16X1: tcgen05 tensor cores, kind::f16, single pass: A, X and A^T X each
  *    rounded to bf16 once (8 significant bits, to nearest), FP32 accumulation;
  *    the sketch is then good to about 2^-8, which the power steps win back
@@ -113,11 +116,15 @@ typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1, TUCKER_FORM_RELATED
  *    in FP32. Used for sketches of the input tensor (every mode of T-HOSVD,
  *    the first of ST-HOSVD) on contiguous fibers (mode 0, or an AMM sample)
  *    and on strided fibers with Lf = I_1 ... I_{n-1} >= 64 and Lf % 4 == 0,
- *    where I_n % 4 == 0, I_n <= 512, L_n <= 32 and A is 16-byte aligned;
+ *    where I_n % 4 == 0, I_n <= 512, L_n <= 32 and A is 16-byte aligned, and
+ *    in the two-pass kernels beyond (contiguous fibers, I_n <= 1024);
  *    ST-HOSVD's later modes (on the truncated tensor, small by then) and other
  *    shapes take the BF16 form where it fits, else FP32.
- * The tensor-core forms need FP32 data (TUCKER_ERR_UNSUPPORTED for FP64), and
- * run the mode-0 product in split BF16 (see tucker_ttm). */
+ * In every tensor-core form, q >= 2 power steps in the paper form on a mode with
+ * I_n <= 128 take Strategy B (tucker_gram: one pass for A_(n) A_(n)^T in split
+ * bf16, then its powers) where the tensor-core kernels take the layout, and the
+ * mode products run in split BF16 (see tucker_ttm). The tensor-core forms need
+ * FP32 data (TUCKER_ERR_UNSUPPORTED for FP64). */
 typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2, TUCKER_SK_BF16X1 = 3 } tucker_sketch_prec;
 
 #define TUCKER_FLAG_ASYNC 0x1u
@@ -360,6 +367,18 @@ tucker_status tucker_leading_factor_chain(const void* X, tucker_dtype dt, int64_
  * evaluate it (in orthonormalised half steps when T >= L). Paper form only. */
 tucker_status tucker_sample_factor(const void* Cp, tucker_dtype dt, int64_t I, int64_t T, int64_t R, int32_t P,
                                    int32_t q, uint64_t seed, int mode, void* U, const tucker_opts* opts);
+
+/* Strategy B of the remark after Algorithm 1: G (I_n x I_n, column-major device
+ * array) = A_(n) A_(n)^T in one pass over the tensor on the tensor cores, split
+ * bf16 operands with FP32 accumulation (about 2^-16 per product), the partial
+ * sums of a fixed set of CTAs added in a fixed order. FP32 data and a
+ * tensor-core opts->prec (any; the Gram is always split bf16), I_n <= 128,
+ * mode-1 fibers or strides that are multiples of 32, A 16-byte aligned;
+ * otherwise TUCKER_ERR_UNSUPPORTED. The drivers take this route in the paper
+ * form when q >= 2 and I_n <= 128 (one pass over the tensor instead of q), then
+ * C_n = G^q Omega_n in the factored form. */
+tucker_status tucker_gram(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode, void* G,
+                          const tucker_opts* opts);
 
 /* Checks the bounded-wait path of the tensor-core kernels on the device (no
  * counterpart in the paper): one CTA takes tensor memory, waits on an mbarrier

@@ -91,6 +91,7 @@ _SIGS = {
     "tucker_leading_factor_chain": [_VP, _INT, _I64, _I64, _I64, _VP, _INT, _VP, _P(Opts)],
     "tucker_sample_factor": [_VP, _INT, _I64, _I64, _I64, _I32, _I32, _U64, _INT, _VP, _P(Opts)],
     "tucker_check_wait_timeout": [_I32, _P(Opts)],
+    "tucker_gram": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _P(Opts)],
     "tucker_rsthosvd_adaptive": [_VP, _INT, _P(_I64), _INT, _DBL, _I32, _I32, _U64, _P(_VP), _VP, _P(_I32),
                                  _P(Opts)],
     "tucker_server_create": [_P(ServerOpts), _P(_VP)],
@@ -112,7 +113,7 @@ _RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int6
              "tucker_autotune_entry": C.c_char_p}
 KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3, "extract": 4, "sample": 5, "power_bf16": 6,
                   "power_tf32": 7, "ttm_bf16": 8, "power_bf16x1": 9, "ttm_wide": 10, "power_wide1": 11,
-                  "power_wide2": 12, "range_wide": 13}
+                  "power_wide2": 12, "range_wide": 13, "gram_wide": 14}
 
 
 def lib():
@@ -364,6 +365,17 @@ def rsthosvd_adaptive(A, dims, eps, q=1, L0=8, seed=0, form="paper", prec="fp32"
     G = Gbuf[:math.prod(r)]
     res = (U, G, r)
     return res + (re.value,) if want_rel_error else res
+
+
+def gram(A, dims, mode, stream=None, prec="bf16"):
+    """tucker_gram: G = A_(n) A_(n)^T (I_n x I_n) in one tensor-core pass (Strategy B)."""
+    dims = _view(A, dims, mode)
+    I = dims[mode]
+    G = factor_tensor(I, I, A.dtype, A.device)
+    o = make_opts(stream=stream, prec=prec)
+    _check("tucker_gram", lib().tucker_gram(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode, G.data_ptr(),
+                                            C.byref(o)))
+    return G
 
 
 def check_wait_timeout(iters=1000, stream=None) -> int:

@@ -119,6 +119,7 @@ struct ModePlan {
     bool wide_range;   // range form: first pass Y = A Omega on the tensor cores, Omega generated in-kernel
     bool half;         // AMM, paper form: power steps on C' as two orthonormalised half steps
     bool half_tc;      //   on the tensor cores (split bf16; the tensor-core forms, large samples)
+    bool gram;         // Strategy B: G = B_(n) B_(n)^T in one tensor-core pass, then G^q Omega
     OrthPlan opT;      //   orthonormalisation of the T x L half-step product
     OrthPlan opL;      // related form: extraction from the L x L matrix P^T A A^T P
     PowerPlan pp;
@@ -135,7 +136,7 @@ struct Plan {
     int64_t dims[kMaxOrder];
     int64_t cur[kMaxOrder][kMaxOrder];   // dims of the tensor each mode works on (ST shrinks)
     ModePlan m[kMaxOrder];
-    int64_t maxI = 0, maxL = 0, maxJ = 0, maxT = 0, maxIT = 0, maxTL = 0;
+    int64_t maxI = 0, maxL = 0, maxJ = 0, maxT = 0, maxIT = 0, maxTL = 0, maxGram = 0;
     bool half = false;
     size_t max_partials = 0, max_orth = 0;
     int64_t inter_elems = 0;             // largest intermediate tensor of the TTM chain
@@ -200,6 +201,17 @@ tucker_status plan_mode(Plan& p, const int64_t* d, int N, int n, int64_t R, int3
     mp.half_tc = mp.half && o.prec != TUCKER_SK_FP32 && elem == 4 && wide_supported(mp.mv, mp.L) &&
                  !power_tc_supported(mp.mv, mp.L);
     if (mp.half_tc) p.max_partials = std::max(p.max_partials, wide_power_scratch_bytes(mp.mv, mp.L, sms));
+    // Strategy B (remark after Algorithm 1) where it saves passes over the tensor: with q >= 2
+    // power steps and I_n <= 128, G = B_(n) B_(n)^T in one tensor-core pass (split bf16, FP32
+    // accumulation) and C_n = G^q Omega_n on the I_n x I_n matrix, where Strategy A reads the
+    // tensor q times; the same C_n, in the same factored form
+    mp.gram = o.form == TUCKER_FORM_PAPER && mp.T == 0 && p.q >= 2 && o.prec != TUCKER_SK_FP32 && elem == 4 &&
+              gram_wide_supported(mp.v);
+    if (mp.gram) {
+        p.maxGram = std::max(p.maxGram, d[n] * d[n]);
+        p.max_partials = std::max(p.max_partials, gram_wide_scratch_bytes(mp.v, sms));
+        p.max_partials = std::max(p.max_partials, half_partials_bytes(d[n], mp.L, d[n], sms, elem));
+    }
     if (mp.half) {
         mp.opT = orth_plan(mp.T, mp.L, sms);
         p.half = true;
@@ -265,6 +277,7 @@ struct Work {
     double* w; uint64_t* W; void* samp; int64_t* idx; double* scale; void* Cp;
     void* inter[2];
     void* Y; void* QY;     // half steps: T x L product and its orthonormal factor
+    void* Gn;              // Strategy B: the I_n x I_n Gram matrix (FP32)
     void* sumsq;
     double* norms;     // [2]: ||A||^2, ||G||^2
     int wide_stages = kWideStagesAlone;   // FP32 ring depth of the wide tensor-core kernels
@@ -297,6 +310,7 @@ void carve(const Plan& p, Arena& a, Work& w) {
     }
     w.Y = p.maxTL ? a.take((size_t)p.maxTL * p.elem) : nullptr;
     w.QY = p.maxTL ? a.take((size_t)p.maxTL * p.elem) : nullptr;
+    w.Gn = p.maxGram ? a.take((size_t)p.maxGram * sizeof(float)) : nullptr;
     w.inter[0] = a.take((size_t)p.inter_elems * p.elem);
     w.inter[1] = a.take((size_t)p.inter_elems * p.elem);
     w.sumsq = a.take(sumsq_scratch_bytes());
@@ -430,7 +444,17 @@ cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t
     if (form == TUCKER_FORM_PAPER) {
         // C = (M M^T)^q Omega in factored form: after each step X_k = Q_k F_k and
         // the next step multiplies Q_k, so C = X_q F_{q-1} ... F_1 with no overflow
-        // and no loss of the weaker directions to FP32 rounding.
+        // and no loss of the weaker directions to FP32 rounding. Strategy B forms
+        // G = M M^T once and multiplies it instead of passing over M each step.
+        const T* Gm = nullptr;
+        if constexpr (sizeof(T) == 4) {
+            if (mp.gram) {
+                const cudaError_t e = launch_gram_wide(M, mp.mv, (float*)w.Gn, true, w.partials, w.status, num_sms(),
+                                                       s, w.wide_stages);
+                if (e == cudaSuccess) Gm = (const T*)w.Gn;
+                else if (e != cudaErrorNotSupported) return e;
+            }
+        }
         TK_TRY(launch_gaussian<T>(X0, mp.v.i, L, seed, stream_id(0, n), s));
         for (int k = 0; k < q; ++k) {
             const T* xin = X0;
@@ -438,7 +462,8 @@ cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t
                 TK_TRY(launch_cholqr<T>(X1, Q, mp.op, w.factors + (size_t)(k - 1) * LL, w.orth, w.status, s));
                 xin = Q;
             }
-            TK_TRY(power_step<T>(M, mp, xin, X1, w, s));
+            if (Gm) TK_TRY(launch_gemm_nn<T>(Gm, mp.v.i, mp.v.i, xin, L, X1, w.partials, num_sms(), s));
+            else TK_TRY(power_step<T>(M, mp, xin, X1, w, s));
         }
         ProfScope prof(kKExtract, 0.0, 0.0, s);
         return launch_extract<T>(X1, Q, mp.op, w.factors, q - 1, mp.R, U, w.orth, w.status, s);
@@ -864,6 +889,7 @@ tucker_status tucker_plan_describe(int which, tucker_dtype dt, const int64_t* di
     for (int n = 0; n < N; ++n) {
         const ModePlan& mp = p.m[n];
         const char* power = p.elem == 8 ? "fp64"
+                            : mp.gram   ? "gram-split-bf16"
                             : mp.tf32   ? "tf32"
                             : mp.bf16x1 ? "bf16x1"
                             : mp.tc     ? "split-bf16"
@@ -1180,6 +1206,28 @@ tucker_status tucker_leading_factor_chain(const void* X, tucker_dtype dt, int64_
                                               status, o.stream)
                       : launch_extract<double>((const double*)X, (double*)Q1, op, F, nfactors, (int)R, (double*)U,
                                                orth, status, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, status);
+}
+
+tucker_status tucker_gram(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode, void* G,
+                          const tucker_opts* opts) {
+    cudaGetLastError();
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (!mode_args_ok(A, dims, N, mode) || !G) return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    const ModeView v = view_of(dims, N, mode);
+    if (dt != TUCKER_F32 || o.prec == TUCKER_SK_FP32 || !gram_wide_supported(v)) return TUCKER_ERR_UNSUPPORTED;
+    Scratch sc;
+    if ((rs = sc.get(gram_wide_scratch_bytes(v, num_sms()) + 256, o.stream)) != TUCKER_OK) return rs;
+    int* status = reinterpret_cast<int*>(sc.p);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), o.stream);
+    if (e == cudaSuccess)
+        e = launch_gram_wide((const float*)A, v, (float*)G, true, reinterpret_cast<char*>(sc.p) + 256, status,
+                             num_sms(), o.stream);
+    if (e == cudaErrorNotSupported) return TUCKER_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return from_cuda(e);
     return sync_status(o.stream, status);
 }

@@ -103,6 +103,13 @@ cudaError_t launch_power_wide(const float* A, const ModeView& v, const float* X_
                               bool range, uint64_t seed, uint32_t stream_id, void* scratch, int* status, int num_sms,
                               cudaStream_t s, int max_stages = kWideStagesAlone);
 
+// Strategy B: G = A_(n) A_(n)^T (I_n x I_n, column-major, I_n <= 128) in one tensor-core pass;
+// scratch of gram_wide_scratch_bytes (per-CTA partials, summed in a fixed order).
+bool gram_wide_supported(const ModeView& v);
+size_t gram_wide_scratch_bytes(const ModeView& v, int num_sms);
+cudaError_t launch_gram_wide(const float* A, const ModeView& v, float* G, bool split, void* scratch, int* status,
+                             int num_sms, cudaStream_t s, int max_stages = kWideStagesAlone);
+
 // half steps of the AMM sketch on the tensor cores (split bf16), scratch as launch_power_wide:
 // Y (J x L, column-major) = A_(n)^T X, and X_out = A_(n) Q with Q J x L column-major
 cudaError_t launch_wide_tn(const float* A, const ModeView& v, const float* X, int L, float* Y, void* scratch,
@@ -196,7 +203,8 @@ tucker_status status_from_cuda(cudaError_t e);
 // ---- launch counting and profiling (profile.cu)
 enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKExtract = 4, kKSample = 5,
                    kKPowerBf16 = 6, kKPowerTf32 = 7, kKTtmBf16 = 8, kKPowerBf16x1 = 9, kKTtmWide = 10,
-                   kKPowerWide1 = 11, kKPowerWide2 = 12, kKRangeWide = 13, kKernelClasses = 14 };
+                   kKPowerWide1 = 11, kKPowerWide2 = 12, kKRangeWide = 13,
+                   kKGramWide = 14, kKernelClasses = 15 };
 void note_launch();
 void note_launches(int64_t n);   // a graph replay's kernels
 void profile_drain();

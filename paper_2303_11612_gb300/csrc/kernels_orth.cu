@@ -158,10 +158,11 @@ __device__ __forceinline__ void trailing_entry(int e, int L, int& i, int& j) {
 // (W_ij -= W_ki W_kj / d_k; at most a few entries a thread, numbered as in
 // trailing_entry), the thread that updates W_{k+1,k+1} takes the next pivot at
 // once (its threshold formed alongside the update), and row k - 1 is scaled by
-// 1/R_{k-1,k-1} alongside.
+// 1/R_{k-1,k-1} alongside. The entries' (i, j) are decoded once into `tab`
+// ((L - 1) L / 2 ints of shared memory): their numbering does not depend on k.
 template <typename T, typename S>
 __device__ bool reduce_cholesky(const S* __restrict__ partial, int nparts, int L, int64_t I, S* G, S* W, S* dinv,
-                                unsigned* ticket, int* status) {
+                                int* tab, unsigned* ticket, int* status) {
     using F = Sc<S>;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int np = (int)packed_size(L);
@@ -173,6 +174,11 @@ __device__ bool reduce_cholesky(const S* __restrict__ partial, int nparts, int L
         S acc = ld_cg(partial + p);
         for (int b = 1; b < nparts; ++b) acc = acc + ld_cg(partial + (int64_t)b * np + p);
         G[p] = acc;
+    }
+    for (int e = tid; e < (L - 1) * L / 2; e += nt) {
+        int i, j;
+        trailing_entry(e, L, i, j);
+        tab[e] = (i << 16) | j;
     }
     if (tid == 0) *ticket = 0;                           // ready for the next use
     __syncthreads();
@@ -208,8 +214,8 @@ __device__ bool reduce_cholesky(const S* __restrict__ partial, int nparts, int L
             const S* rk = W + packed_index(k, k, L);      // rk[j - k] = W_kj
             const int ne = (L - 1 - k) * (L - k) / 2;     // entries of rows k + 1 .. L - 1
             for (int e = tid; e < ne; e += nt) {
-                int i, j;
-                trailing_entry(e, L, i, j);
+                const int ij = tab[e];
+                const int i = ij >> 16, j = ij & 0xffff;
                 const bool piv = j == k + 1;              // then i == k + 1 as well
                 S lim = F::zero();
                 if (piv) lim = (G[packed_index(k + 1, k + 1, L)] + shift) * thr;
@@ -294,7 +300,7 @@ __global__ void __launch_bounds__(kST) gram_chol_kernel(const T* __restrict__ X,
     S* W = G + np;
     S* RT = W + np;
     S* dinv = RT + np;
-    reduce_cholesky<T, S>(partial, gridDim.x, L, I, G, W, dinv, ticket, status);
+    reduce_cholesky<T, S>(partial, gridDim.x, L, I, G, W, dinv, reinterpret_cast<int*>(RT), ticket, status);
     upper_inverse<S>(W, dinv, L, RT, G);
     for (int p = threadIdx.x; p < np; p += blockDim.x) {
         R[p] = W[p];
@@ -564,6 +570,35 @@ __device__ __forceinline__ void pair_sums(const T (&x)[NE], const T (&y)[NE], T&
 // each lane holding up to NE entries of both columns in registers. Returns the
 // number of rotations; *mxc2 receives the largest squared cosine g^2 / (a b)
 // among the rotated pairs (as the bits of a nonnegative float).
+// The same three sums with the coupling summed plainly (a, b, g reduced together).
+template <typename T, int GS, int NE>
+__device__ __forceinline__ void pair_sums_plain(const T (&x)[NE], const T (&y)[NE], T& a, T& b, T& g) {
+    T a2 = T(0), b2 = T(0), g2 = T(0);
+    a = T(0);
+    b = T(0);
+    g = T(0);
+#pragma unroll
+    for (int e = 0; e < NE; e += 2) {
+        a = fma(x[e], x[e], a);
+        b = fma(y[e], y[e], b);
+        g = fma(x[e], y[e], g);
+        if (e + 1 < NE) {
+            a2 = fma(x[e + 1], x[e + 1], a2);
+            b2 = fma(y[e + 1], y[e + 1], b2);
+            g2 = fma(x[e + 1], y[e + 1], g2);
+        }
+    }
+    a += a2;
+    b += b2;
+    g += g2;
+#pragma unroll
+    for (int o = GS / 2; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        g += __shfl_xor_sync(0xffffffffu, g, o);
+    }
+}
+
 template <typename T, int GS, int NE>
 __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot, unsigned* mxc2) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -600,7 +635,17 @@ __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot, unsi
                 y[e] = in ? cq[r] : T(0);
             }
             T a, b, g;
-            pair_sums<T, GS, NE>(x, y, a, b, g);
+            if constexpr (sizeof(T) == 4) {
+                // the coupling summed plainly is good to about L eps |x| |y|: enough to
+                // rotate a pair whose cosine exceeds 2^-10; a warp with a pair below
+                // that sums its couplings again in paired precision (the test at 4 eps
+                // and the small rotations near convergence need it)
+                pair_sums_plain<T, GS, NE>(x, y, a, b, g);
+                const bool fine = live && g * g <= T(0x1p-20) * a * b;
+                if (__any_sync(0xffffffffu, fine)) pair_sums<T, GS, NE>(x, y, a, b, g);
+            } else {
+                pair_sums<T, GS, NE>(x, y, a, b, g);
+            }
             if (live && fabs(g) > tiny && g * g > tol * tol * a * b) {
                 c2max = fmaxf(c2max, (float)((g / a) * (g / b)));
                 T c, s;
@@ -734,7 +779,7 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
     __shared__ T nrm2;
     __shared__ unsigned long long mx_bits;
 
-    reduce_cholesky<T, S>(partial, gridDim.x, L, I, G, Rf, dinv, ticket, status);
+    reduce_cholesky<T, S>(partial, gridDim.x, L, I, G, Rf, dinv, reinterpret_cast<int*>(H), ticket, status);
 
     // M = R2 prev[nprev-1] ... prev[0]: products of packed upper triangles, one
     // thread per output entry, alternating between H and G so the last lands in G
@@ -746,12 +791,17 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
             const int a = p / L, c = p % L;
             if (c < a) continue;
             S acc0 = F::zero(), acc1 = F::zero();
+            // (a, b) and (b, c) for b = a, a + 1, ...: packed(b + 1, c) = packed(b, c) + L - b - 1
+            int ia = packed_index(a, a, L), ib = packed_index(a, c, L);
             int b = a;
             for (; b + 1 <= c; b += 2) {
-                acc0 = F::fma(Fm[packed_index(a, b, L)], src[packed_index(b, c, L)], acc0);
-                acc1 = F::fma(Fm[packed_index(a, b + 1, L)], src[packed_index(b + 1, c, L)], acc1);
+                const int ib1 = ib + L - b - 1;
+                acc0 = F::fma(Fm[ia], src[ib], acc0);
+                acc1 = F::fma(Fm[ia + 1], src[ib1], acc1);
+                ia += 2;
+                ib = ib1 + L - b - 2;
             }
-            if (b == c) acc0 = F::fma(Fm[packed_index(a, c, L)], src[packed_index(c, c, L)], acc0);
+            if (b == c) acc0 = F::fma(Fm[ia], src[ib], acc0);
             dst[packed_index(a, c, L)] = acc0 + acc1;
         }
         __syncthreads();
@@ -935,7 +985,7 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
 #pragma unroll
             for (int m = 0; m < kBsRows; ++m) {
                 const int k = lane + 32 * m;
-                rkl[m] = k < l ? Rf[packed_index(k, l, L)] : F::zero();
+                rkl[m] = (32 * m < l && k < l) ? Rf[packed_index(k, l, L)] : F::zero();
             }
 #pragma unroll
             for (int c = 0; c < kBsCols; ++c) {
@@ -946,8 +996,10 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
                 const S w = shfl_s(v * d, src);
                 if (lane == src && c0 + c < R) Wout[(size_t)(c0 + c) * L + l] = w;
 #pragma unroll
-                for (int m = 0; m < kBsRows; ++m)
+                for (int m = 0; m < kBsRows; ++m) {
+                    if (32 * m >= l) break;                        // the same for the whole warp
                     if (lane + 32 * m < l) acc[c][m] = F::fma(-rkl[m], w, acc[c][m]);
+                }
             }
         }
     }

@@ -824,6 +824,216 @@ bool layout_ok(const ModeView& v) {
     return v.lf % 32 == 0 && v.lf <= (int64_t)INT_MAX && v.rt <= (int64_t)INT_MAX;
 }
 
+// ------------------------------------------------------------------ gram_wide_kernel
+// Strategy B (remark after Algorithm 1): G = A_(n) A_(n)^T (I_n x I_n, I_n <= 128)
+// in one streaming pass, partial[r I^2 + i' I + i] = sum over the CTA's 64-fiber
+// chunks of A_(n)[i, j] A_(n)[i', j]. The units are loaded and converted exactly
+// as in wide_power2_kernel (one 128-row block, rows >= I_n load as zeros), and
+// the converted unit is both operands of D = T T^T: A = rows i x fibers and
+// B = fibers x columns i', the same core matrices read with the same strides
+// (i contiguous for contiguous fibers: MN-major A and B; fibers contiguous for
+// strided ones: K-major A and B). N = I_n padded to 16; split: hi.hi + lo.hi +
+// hi.lo.
+constexpr int kGBars = 2 * kBFMax + 2 * kBCStages + 1;
+static_assert(kGBars * 8 + 8 <= 256, "barrier area");
+
+struct GramLayout {
+    int Np = 0, parts = 1, fst = kBFMin;
+    size_t c_off = 0, bar_off = 0, bytes = 0;
+};
+
+GramLayout gram_layout(int I, bool split, int max_stages = kBFMax) {
+    GramLayout t;
+    t.Np = (I + 15) / 16 * 16;
+    t.parts = split ? 2 : 1;
+    const size_t rest = (size_t)kBCStages * t.parts * kBHalf + 256 + 1024;
+    if (rest + (size_t)kBFMin * kBUnit <= kWSmemMax)
+        t.fst = (int)std::max<size_t>(kBFMin, std::min<size_t>(std::min(kBFMax, max_stages), (kWSmemMax - rest) / kBUnit));
+    t.c_off = (size_t)t.fst * kBUnit;
+    t.bar_off = t.c_off + (size_t)kBCStages * t.parts * kBHalf;
+    t.bytes = t.bar_off + 256 + 1024;
+    return t;
+}
+
+template <bool SPLIT, bool STRIDED>
+__global__ void __launch_bounds__(kBThreads, 1)
+    gram_wide_kernel(const __grid_constant__ CUtensorMap map, int I, int64_t J, int Np, float* __restrict__ partial,
+                     int64_t chunks, int64_t lf, int* status, int fst) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024 - (tma::smem_addr(smem_raw) & 1023)) & 1023);
+    constexpr int parts = SPLIT ? 2 : 1;
+    unsigned char* F = smem;
+    unsigned char* Cb = smem + (size_t)fst * kBUnit;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Cb + (size_t)kBCStages * parts * kBHalf);
+    uint64_t* f_full = bar;
+    uint64_t* f_empty = f_full + kBFMax;
+    uint64_t* c_full = f_empty + kBFMax;
+    uint64_t* c_empty = c_full + kBCStages;
+    uint64_t* done = c_empty + kBCStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t r = blockIdx.x, R = gridDim.x;
+    const int64_t nloc = chunks > r ? (chunks - 1 - r) / R + 1 : 0;
+
+    if (tid == 0) {
+        for (int k = 0; k < kGBars; ++k) tc::mbar_init(&bar[k], 1);
+        for (int k = 0; k < fst; ++k) tc::mbar_init(&f_empty[k], kBConv);
+        for (int k = 0; k < kBCStages; ++k) tc::mbar_init(&c_full[k], kBConv);
+        *flag = 0;
+        tma::fence_barrier_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tmem_slot, 128);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int64_t g = 0;
+            for (int64_t kk = 0; kk < nloc; ++kk, ++g) {
+                const int64_t ch = r + kk * R;
+                const int j0 = (int)(ch * kBJB);
+                const int fs = (int)(g % fst);
+                if (g >= fst && !wait_bar(&f_empty[fs], (uint32_t)((g / fst - 1) & 1), flag)) {
+                    fail(flag, status);
+                    break;
+                }
+                tma::expect_tx(&f_full[fs], (uint32_t)kBUnit);
+                unsigned char* dst = F + (size_t)fs * kBUnit;
+                if (STRIDED) {
+#pragma unroll
+                    for (int gq = 0; gq < 2; ++gq) {
+                        const int64_t jg = (int64_t)j0 + 32 * gq;
+                        const int rr = (int)(jg / lf), l = (int)(jg - (int64_t)rr * lf);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            tma::load_3d(dst + (4 * gq + q) * 4096, &map, l, 32 * q, rr, &f_full[fs]);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) tma::load_2d(dst + q * kBBox, &map, 32 * q, j0, &f_full[fs]);
+                }
+            }
+            if (*flag) {
+                const int64_t f0 = g > fst ? g - fst : 0;
+                for (int64_t gg = f0; gg < g; ++gg) drain(&f_full[gg % fst], (uint32_t)((gg / fst) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id = tc::idesc_bf16(128, Np, !STRIDED, !STRIDED);
+            // the converted unit read as A (rows i x 64 fibers) and as B (64 fibers x columns i'):
+            // no-swizzle core matrices, LBO the fiber step, SBO the row step; MN-major 2048 / 128
+            // (contiguous), K-major 128 / 1024 (strided), the same for both operands
+            const uint64_t desc0 = STRIDED ? tc::desc(tc::smem_u32(Cb), 128, 1024) : tc::desc(tc::smem_u32(Cb), 2048, 128);
+            const uint32_t kstep = STRIDED ? 2 * 128 : 2 * 2048;                 // bytes per 16 fibers
+            const uint64_t lo = (uint64_t)(kBHalf >> 4);
+            bool ok = true;
+            for (int64_t kk = 0; kk < nloc; ++kk) {
+                const int cs = (int)(kk % kBCStages);
+                if (!wait_bar(&c_full[cs], (uint32_t)((kk / kBCStages) & 1), flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint64_t a0 = desc0 + (uint64_t)((cs * parts * kBHalf) >> 4);
+#pragma unroll
+                for (int ks = 0; ks < kBJB / 16; ++ks) {
+                    const uint64_t sk = (uint64_t)((ks * kstep) >> 4);
+                    tc::mma_bf16(tmem, a0 + sk, a0 + sk, id, kk > 0 || ks > 0);
+                    if (SPLIT) {
+                        tc::mma_bf16(tmem, a0 + lo + sk, a0 + sk, id, true);
+                        tc::mma_bf16(tmem, a0 + sk, a0 + lo + sk, id, true);
+                    }
+                }
+                tc::commit(&c_empty[cs]);
+            }
+            tc::commit(done);
+            if (!ok) {
+                fail(flag, status);
+                drain(done, 0);
+            }
+        }
+    } else {
+        const int ct = tid - 64;
+        bool ok = true;
+        constexpr int kTasks = (128 / 8) * kBJB / (kBConv * 32);   // 4
+        for (int64_t kk = 0; kk < nloc && ok; ++kk) {
+            const int fs = (int)(kk % fst), cs = (int)(kk % kBCStages);
+            if (!wait_bar(&f_full[fs], (uint32_t)((kk / fst) & 1), flag)) {
+                ok = false;
+                break;
+            }
+            const unsigned char* src = F + (size_t)fs * kBUnit;
+            uint4 hi[kTasks], lw[kTasks];
+#pragma unroll
+            for (int q = 0; q < kTasks; ++q) {
+                const int t = ct + kBConv * 32 * q;
+                float4 a, c;
+                if (STRIDED) {
+                    const int i = (t & 7) + 8 * (t >> 6), g8 = (t >> 3) & 7;
+                    const unsigned char* row = src + (4 * (g8 >> 2) + (i >> 5)) * 4096 + (i & 31) * 128;
+                    const int c0 = (g8 & 3) * 2;
+                    a = *reinterpret_cast<const float4*>(row + ((c0 ^ (i & 7)) << 4));
+                    c = *reinterpret_cast<const float4*>(row + (((c0 + 1) ^ (i & 7)) << 4));
+                } else {
+                    const int jlo = t & 7, ig = (t >> 3) & 15, jhi = t >> 7;
+                    const int jj = jhi * 8 + jlo;
+                    const int c0 = (ig & 3) * 2;
+                    const unsigned char* row = src + (ig >> 2) * kBBox + jj * 128;
+                    a = *reinterpret_cast<const float4*>(row + ((c0 ^ (jj & 7)) << 4));
+                    c = *reinterpret_cast<const float4*>(row + (((c0 + 1) ^ (jj & 7)) << 4));
+                }
+                const float x[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+                cvt8<SPLIT>(x, hi[q], lw[q]);
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&f_empty[fs]);
+            if (kk >= kBCStages && !wait_bar(&c_empty[cs], (uint32_t)((kk / kBCStages - 1) & 1), flag)) {
+                ok = false;
+                break;
+            }
+            unsigned char* dst = Cb + (size_t)cs * parts * kBHalf;
+#pragma unroll
+            for (int q = 0; q < kTasks; ++q) {
+                const int t = ct + kBConv * 32 * q;
+                const int off = STRIDED ? ((t >> 6) * 1024 + ((t >> 3) & 7) * 128 + (t & 7) * 16)
+                                        : ((t >> 7) * 2048 + ((t >> 3) & 15) * 128 + (t & 7) * 16);
+                *reinterpret_cast<uint4*>(dst + off) = hi[q];
+                if (SPLIT) *reinterpret_cast<uint4*>(dst + kBHalf + off) = lw[q];
+            }
+            tc::fence_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&c_full[cs]);
+        }
+        if (!ok) fail(flag, status);
+        // the CTA's partial: row i on lane i, columns i'; the first four converter warps
+        const bool ready = ok && warp < 6 && wait_bar(done, 0, flag);
+        if (ok && warp < 6 && !ready && !*flag) fail(flag, status);
+        if (ready && !*flag) {
+            tc::fence_after_sync();
+            const int quarter = warp & 3;
+            float* out = partial + r * ((int64_t)I * I);
+            const int i = quarter * 32 + lane;
+            const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16);
+            for (int c0 = 0; c0 < Np; c0 += 16) {
+                uint32_t v[16];
+                tc::tmem_ld16(ta + (uint32_t)c0, v);
+                if (i < I)
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        if (c0 + c < I) out[(int64_t)(c0 + c) * I + i] = __uint_as_float(v[c]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, 128);
+}
+
 // A wait that nothing completes: one CTA takes tensor memory as the kernels
 // above do, initialises an mbarrier that no thread and no copy arrives at,
 // waits for it with the bound `iters`, records the timeout as every kernel here
@@ -1045,6 +1255,43 @@ cudaError_t launch_wait_timeout(int iters, int* status, cudaStream_t s) {
     wait_timeout_kernel<<<1, 64, 0, s>>>(iters, status);
     note_launch();
     return cudaGetLastError();
+}
+
+bool gram_wide_supported(const ModeView& v) {
+    return layout_ok(v) && v.i >= 1 && v.i <= 128 && v.fibers() <= (int64_t)INT_MAX - 256;
+}
+
+size_t gram_wide_scratch_bytes(const ModeView& v, int num_sms) {
+    const int64_t chunks = (v.fibers() + kBJB - 1) / kBJB;
+    const int64_t R = std::max<int64_t>(1, std::min<int64_t>(chunks, num_sms));
+    return round256((size_t)R * v.i * v.i * sizeof(float));
+}
+
+cudaError_t launch_gram_wide(const float* A, const ModeView& v, float* G, bool split, void* scratch, int* status,
+                             int num_sms, cudaStream_t s, int max_stages) {
+    if (!gram_wide_supported(v) || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
+    const int I = (int)v.i;
+    const int64_t J = v.fibers();
+    const bool strided = v.lf > 1;
+    const GramLayout t = gram_layout(I, split, max_stages);
+    if (t.bytes > kWSmemMax) return cudaErrorNotSupported;
+    const int64_t chunks = (J + kBJB - 1) / kBJB;
+    const int64_t R = std::max<int64_t>(1, std::min<int64_t>(chunks, num_sms));
+    CUtensorMap map;
+    if (!make_fiber_map(&map, A, v, kBJB)) return cudaErrorNotSupported;
+    float* part = reinterpret_cast<float*>(scratch);
+    {
+        const double elems = (double)I * (double)J;
+        ProfScope prof(kKGramWide, elems * sizeof(float), 2.0 * elems * I, s);
+        auto k = split ? (strided ? gram_wide_kernel<true, true> : gram_wide_kernel<true, false>)
+                       : (strided ? gram_wide_kernel<false, true> : gram_wide_kernel<false, false>);
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.bytes);
+        k<<<(int)R, kBThreads, t.bytes, s>>>(map, I, J, t.Np, part, chunks, v.lf, status, t.fst);
+        note_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return launch_reduce_partials<float>(part, (int)R, (int64_t)I * I, G, s);
 }
 
 }  // namespace tk

@@ -318,6 +318,18 @@ def test_plan_describe_pins_the_dispatch_rules():
     wf = _modes(B.plan_describe("ST", big, bigr, P=16, c=20000, prec="fp32"))
     assert [wf[n]["power"] for n in range(3)] == ["fp32"] * 3
     assert [wa[n]["amm"] for n in range(3)] == ["half-steps"] * 3
+    # Strategy B: with q >= 2 in a tensor-core form, I_n <= 128 and a layout the tensor-core
+    # kernels take, G = A_(n) A_(n)^T in one pass replaces the q passes of Strategy A
+    qb = _modes(B.plan_describe("ST", (96, 96, 96, 96), (16,) * 4, P=8, q=2, prec="bf16x1"))
+    # (ST-HOSVD's mode 2 has the stride R_1 = 16, not a multiple of 32: Strategy A there)
+    assert [qb[n]["power"] for n in range(4)] == ["gram-split-bf16", "split-bf16", "gram-split-bf16",
+                                                  "gram-split-bf16"]
+    qt = _modes(B.plan_describe("T", (96, 96, 96, 96), (16,) * 4, P=8, q=2, prec="tf32"))
+    assert [qt[n]["power"] for n in range(4)] == ["gram-split-bf16"] * 4
+    q1 = _modes(B.plan_describe("T", (96, 96, 96, 96), (16,) * 4, P=8, q=1, prec="tf32"))
+    assert "gram-split-bf16" not in [q1[n]["power"] for n in range(4)]          # q = 1: one pass either way
+    qf = _modes(B.plan_describe("T", (96, 96, 96, 96), (16,) * 4, P=8, q=2, prec="fp32"))
+    assert [qf[n]["power"] for n in range(4)] == ["fp32"] * 4
     assert [int(wa[n]["T"]) for n in range(3)] == [20000, 20000, 64 * 64]
     # no half steps where the sample has fewer fibers than the sketch has columns
     few = _modes(B.plan_describe("ST", (40, 36, 32), (8, 6, 7), P=5, c=10, prec="bf16x1"))
