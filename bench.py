@@ -734,14 +734,17 @@ def main():
                 step_e2e()
             b.barrier()
             e2e_steps = max(3, args.steps // 4)
+            step_ms = []
             t0 = time.perf_counter()
             for _ in range(e2e_steps):
+                t1 = time.perf_counter()
                 step_e2e()
+                step_ms.append(round(1e3 * (time.perf_counter() - t1), 1))
             e2e_s = b.max_over_ranks(time.perf_counter() - t0)
         h2d = sum(h.numel() * h.element_size() for h in host_in)
         d2h = len(P["slots"]) * (sum(I * R for I, R in zip(W["dims"], W["ranks"])) + int(np.prod(W["ranks"]))) * 4
         e2e = {"value": whole_job_rate(len(P["slots"]) * e2e_steps, world, e2e_s), "unit": "decomps/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "step_ms": step_ms,
                "path": f"tucker_server_* request loop, {len(P['slots'])} requests per step, pinned host input and "
                        f"output buffers, host clock around the steps"}
         del host_in, houts

@@ -8,8 +8,9 @@ importing the binding builds the library if needed and raises if it cannot be
 loaded.
 """
 from ._binding import (  # noqa: F401
-    TuckerError, decompose, rthosvd, rsthosvd, rsthosvd_adaptive, workspace_size, plan_describe, factor_tensor, gaussian, power_step,
-    range_sketch, fiber_norms, quantize_weights, sample_fibers, gather_fibers, leading_factor, ttm,
+    TuckerError, decompose, rthosvd, rsthosvd, rsthosvd_adaptive, workspace_size, plan_describe, factor_tensor,
+    gaussian, power_step, range_sketch, fiber_norms, quantize_weights, sample_fibers, gather_fibers, leading_factor,
+    ttm, gram, cholqr, leading_factor_chain, sample_factor, quantize_weights_max, sample_fibers_slab,
     relative_error, last_device_status, lib, exported_symbols, FLAG_ASYNC, launch_count, profile_enable,
     profile_read, Server, Batch, autotune_enable, autotune_entries,
 )

@@ -379,18 +379,69 @@ __device__ __forceinline__ V group_sum(V s) {
     return s;
 }
 
+// Two FP32 values in one 64-bit register and the packed FP32 pipe's
+// operations on both halves at once (each half rounded as the scalar
+// operation rounds it): the even and odd entries' chains below run as one.
+using f2 = unsigned long long;
+__device__ __forceinline__ f2 pk2(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void up2(f2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// sum over e of x[e] y[e] in paired precision, the even and odd entries in two
+// chains (packed), combined: the per-lane part of a paired dot product
+template <int NE>
+__device__ __forceinline__ Pair paired_dot2(const float (&x)[NE], const float (&y)[NE]) {
+    static_assert(NE % 2 == 0, "entries in pairs");
+    f2 H = 0ull, Lo = 0ull;
+#pragma unroll
+    for (int e = 0; e < NE; e += 2) {
+        const f2 X = pk2(x[e], x[e + 1]), Y = pk2(y[e], y[e + 1]);
+        const f2 P = mul2(X, Y);
+        const f2 PE = fma2(X, Y, sub2(0ull, P));
+        const f2 Tt = add2(H, P);
+        const f2 Z = sub2(Tt, H);
+        const f2 E = add2(sub2(H, sub2(Tt, Z)), sub2(P, Z));
+        H = Tt;
+        Lo = add2(Lo, add2(E, PE));
+    }
+    Pair ga, gb;
+    up2(H, ga.hi, gb.hi);
+    up2(Lo, ga.lo, gb.lo);
+    pair_add(ga, gb);
+    return ga;
+}
+
 // Dot product of a group of 8 lanes' NE entries each (rows gl + 8 e), paired
 // precision for FP32 data; every lane of the group gets the sum.
 template <typename T, int NE>
 __device__ __forceinline__ T group8_dot(const T (&x)[NE], const T (&y)[NE]) {
     if constexpr (sizeof(T) == 4) {
-        Pair a{0.f, 0.f}, b{0.f, 0.f};
-#pragma unroll
-        for (int e = 0; e < NE; e += 2) {
-            pair_add_prod(a, x[e], y[e]);
-            if (e + 1 < NE) pair_add_prod(b, x[e + 1], y[e + 1]);
-        }
-        pair_add(a, b);
+        Pair a = paired_dot2<NE>(x, y);
         a = group_sum_pair<8>(a);
         return a.hi + a.lo;
     } else {
@@ -523,6 +574,36 @@ template <typename T, int GS, int NE>
 __device__ __forceinline__ void pair_sums(const T (&x)[NE], const T (&y)[NE], T& a, T& b, T& g) {
     // two independent chains per sum (even and odd entries), combined in a
     // fixed order: the sums are the dependent chains of a round
+    if constexpr (sizeof(T) == 4 && NE % 2 == 0) {
+        // both chains at once on the packed pipe: the same operations, in the same
+        // order, as the scalar form below (pair_add_prod per entry)
+        f2 A = 0ull, Bs = 0ull;
+#pragma unroll
+        for (int e = 0; e < NE; e += 2) {
+            const f2 X = pk2(x[e], x[e + 1]), Y = pk2(y[e], y[e + 1]);
+            A = fma2(X, X, A);
+            Bs = fma2(Y, Y, Bs);
+        }
+        float a0, a1, b0, b1;
+        up2(A, a0, a1);
+        up2(Bs, b0, b1);
+        a = a0 + a1;
+        b = b0 + b1;
+        Pair ga = paired_dot2<NE>(x, y);
+#pragma unroll
+        for (int o = GS / 2; o > 0; o >>= 1) {
+            const float ta = __shfl_xor_sync(0xffffffffu, a, o);
+            const float tb = __shfl_xor_sync(0xffffffffu, b, o);
+            Pair t;
+            t.hi = __shfl_xor_sync(0xffffffffu, ga.hi, o);
+            t.lo = __shfl_xor_sync(0xffffffffu, ga.lo, o);
+            a += ta;
+            b += tb;
+            pair_add(ga, t);
+        }
+        g = ga.hi + ga.lo;
+        return;
+    }
     T a2 = T(0), b2 = T(0);
     a = T(0);
     b = T(0);
@@ -570,35 +651,6 @@ __device__ __forceinline__ void pair_sums(const T (&x)[NE], const T (&y)[NE], T&
 // each lane holding up to NE entries of both columns in registers. Returns the
 // number of rotations; *mxc2 receives the largest squared cosine g^2 / (a b)
 // among the rotated pairs (as the bits of a nonnegative float).
-// The same three sums with the coupling summed plainly (a, b, g reduced together).
-template <typename T, int GS, int NE>
-__device__ __forceinline__ void pair_sums_plain(const T (&x)[NE], const T (&y)[NE], T& a, T& b, T& g) {
-    T a2 = T(0), b2 = T(0), g2 = T(0);
-    a = T(0);
-    b = T(0);
-    g = T(0);
-#pragma unroll
-    for (int e = 0; e < NE; e += 2) {
-        a = fma(x[e], x[e], a);
-        b = fma(y[e], y[e], b);
-        g = fma(x[e], y[e], g);
-        if (e + 1 < NE) {
-            a2 = fma(x[e + 1], x[e + 1], a2);
-            b2 = fma(y[e + 1], y[e + 1], b2);
-            g2 = fma(x[e + 1], y[e + 1], g2);
-        }
-    }
-    a += a2;
-    b += b2;
-    g += g2;
-#pragma unroll
-    for (int o = GS / 2; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        g += __shfl_xor_sync(0xffffffffu, g, o);
-    }
-}
-
 template <typename T, int GS, int NE>
 __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot, unsigned* mxc2) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -635,27 +687,33 @@ __device__ int jacobi_sweep(T* Mc, int L, int Lp, T tol, T tiny, int* nrot, unsi
                 y[e] = in ? cq[r] : T(0);
             }
             T a, b, g;
-            if constexpr (sizeof(T) == 4) {
-                // the coupling summed plainly is good to about L eps |x| |y|: enough to
-                // rotate a pair whose cosine exceeds 2^-10; a warp with a pair below
-                // that sums its couplings again in paired precision (the test at 4 eps
-                // and the small rotations near convergence need it)
-                pair_sums_plain<T, GS, NE>(x, y, a, b, g);
-                const bool fine = live && g * g <= T(0x1p-20) * a * b;
-                if (__any_sync(0xffffffffu, fine)) pair_sums<T, GS, NE>(x, y, a, b, g);
-            } else {
-                pair_sums<T, GS, NE>(x, y, a, b, g);
-            }
+            pair_sums<T, GS, NE>(x, y, a, b, g);
             if (live && fabs(g) > tiny && g * g > tol * tol * a * b) {
-                c2max = fmaxf(c2max, (float)((g / a) * (g / b)));
                 T c, s;
                 rotation(a, b, g, c, s);
+                if constexpr (sizeof(T) == 4 && NE % 2 == 0) {
+                    // the squared cosine only steers the test of all pairs: an approximate quotient
+                    c2max = fmaxf(c2max, __fdividef(g * g, a * b));
+                    const f2 C2 = pk2(c, c), S2 = pk2(s, s);
 #pragma unroll
-                for (int e = 0; e < NE; ++e) {
-                    const int r = gl + e * GS;
-                    if (r < L) {
-                        cp[r] = c * x[e] - s * y[e];
-                        cq[r] = s * x[e] + c * y[e];
+                    for (int e = 0; e < NE; e += 2) {
+                        const f2 X = pk2(x[e], x[e + 1]), Y = pk2(y[e], y[e + 1]);
+                        float u0, u1, v0, v1;
+                        up2(fma2(C2, X, sub2(0ull, mul2(S2, Y))), u0, u1);
+                        up2(fma2(S2, X, mul2(C2, Y)), v0, v1);
+                        const int r = gl + e * GS;
+                        if (r < L) { cp[r] = u0; cq[r] = v0; }
+                        if (r + GS < L) { cp[r + GS] = u1; cq[r + GS] = v1; }
+                    }
+                } else {
+                    c2max = fmaxf(c2max, (float)((g / a) * (g / b)));
+#pragma unroll
+                    for (int e = 0; e < NE; ++e) {
+                        const int r = gl + e * GS;
+                        if (r < L) {
+                            cp[r] = c * x[e] - s * y[e];
+                            cq[r] = s * x[e] + c * y[e];
+                        }
                     }
                 }
                 mine += gl == 0;

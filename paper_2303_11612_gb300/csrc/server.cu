@@ -8,7 +8,7 @@
 // requests (event query, device status word read back into pinned memory,
 // stream-ordered free), then admits from the head of the queue. Device memory
 // comes from a pool private to the server (stream-ordered allocation, kept
-// cached up to the budget). Head-of-line order is strict, so a large request
+// mapped for the server's lifetime). Head-of-line order is strict, so a large request
 // is never overtaken indefinitely by small ones. Host inputs are staged by one
 // copy stream shared by all requests, in admission order: concurrent
 // host-to-device copies on many streams share the chip link badly (a third of
@@ -250,7 +250,11 @@ tucker_status tucker_server_create(const tucker_server_opts* opts, tucker_server
     props.location.id = s->device;
     if (e == cudaSuccess) e = cudaMemPoolCreate(&s->pool, &props);
     if (e == cudaSuccess) {
-        uint64_t keep = s->budget;
+        // the pool keeps every block it has mapped until the server is destroyed: blocks of
+        // recurring request sizes are then reused instead of being unmapped at a
+        // synchronisation and mapped again (tens of milliseconds for GB-sized blocks); the
+        // budget, not the pool, bounds what is admitted
+        uint64_t keep = UINT64_MAX;
         e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_s, cudaStreamNonBlocking);
