@@ -128,6 +128,9 @@ typedef enum { TUCKER_FORM_PAPER = 0, TUCKER_FORM_RANGE = 1, TUCKER_FORM_RELATED
 typedef enum { TUCKER_SK_FP32 = 0, TUCKER_SK_TF32 = 1, TUCKER_SK_BF16 = 2, TUCKER_SK_BF16X1 = 3 } tucker_sketch_prec;
 
 #define TUCKER_FLAG_ASYNC 0x1u
+/* tucker_batch_run only: run the batch through the work-list kernel (see the
+ * batches section). */
+#define TUCKER_FLAG_WORKLIST 0x2u
 
 typedef struct {
     uint32_t struct_size;   /* sizeof(tucker_opts) */
@@ -386,7 +389,11 @@ tucker_status tucker_gram(const void* A, tucker_dtype dt, const int64_t* dims, i
  * its status word exactly as the kernels do when a wait runs out, frees its
  * tensor memory and returns; nothing is in flight, so nothing is drained.
  * Returns TUCKER_ERR_TIMEOUT when that path works (the stream and the context
- * stay usable), TUCKER_ERR_INVALID_ARG for iters out of range. */
+ * stay usable), TUCKER_ERR_INVALID_ARG for iters out of range. With
+ * TUCKER_FLAG_WORKLIST in opts->flags it checks the work-list kernel's
+ * dependency wait instead: one CTA runs a two-item list whose second item
+ * depends on an item that is never listed; its wait gives up after `iters`
+ * polls, records the timeout and the launch drains. */
 tucker_status tucker_check_wait_timeout(int32_t iters, const tucker_opts* opts);
 
 /* ---------------------------------------------------------------- allocation-free variant
@@ -493,7 +500,27 @@ tucker_status tucker_server_destroy(tucker_server* srv);
  * request's results are bitwise those of the same request run alone. The
  * requests overlap as far as CUDA's hardware work queues allow: with more than
  * 8 requests, set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) before the process
- * creates its CUDA context. */
+ * creates its CUDA context.
+ *
+ * With TUCKER_FLAG_WORKLIST in opts->flags the graph holds a work list instead
+ * of the requests' own launch sequences (many small tensors in few launches):
+ * every stage of every request - Gaussian test matrix, power-step partials and
+ * their fixed-order sum, mode products, status reset - becomes items, the
+ * blocks its own kernel would run, and one persistent kernel launch per step
+ * (mode n and power step k, with ST-HOSVD's truncation by U_{n-1} ahead of the
+ * power step it feeds; a last step for the cores) claims the items of all
+ * requests in list order, each CTA waiting (bounded, about a second, then
+ * TUCKER_ERR_TIMEOUT) until the stages an item depends on are done; the
+ * CholeskyQR passes and extractions of all requests run as one grouped launch
+ * per step. The requests are dealt to up to four lanes (streams of the graph),
+ * so that one lane's orthonormalisations overlap another's streaming steps. Each request's results are bitwise those of the request run alone
+ * (with autotuning off, which can pick other FP32 power-step tiles). The work
+ * list takes Algorithms 1 and 2 in the paper form with TUCKER_SK_FP32, no
+ * sampling (c = 0, alpha = 0), one element type across the batch, every extent
+ * I_n <= 256 and every rank R_n <= 32; other batches return
+ * TUCKER_ERR_UNSUPPORTED (from tucker_batch_workspace_size too, which with the
+ * flag includes the work list's descriptor area). Not part of the paper's
+ * method. */
 
 /* Device workspace bytes (256-byte aligned per request) a batch needs; opts
  * may be NULL (paper form, FP32). */
@@ -508,6 +535,21 @@ tucker_status tucker_batch_workspace_size(int n, const tucker_request* reqs, con
  * after enqueueing, and request k's status word is the first 4 bytes of its
  * workspace slice. Argument errors of any request return before any launch. */
 tucker_status tucker_batch_run(int n, const tucker_request* reqs, const tucker_opts* opts);
+
+/* Host only (no device work, no pointer checks): the work list a batch with
+ * TUCKER_FLAG_WORKLIST in opts->flags would run, as text in buf (len bytes,
+ * NUL-terminated; TUCKER_ERR_INVALID_ARG when it does not fit): one line per
+ * step ("step s lane l: items=... init=... gaussian=... power=... sum=...
+ * product=... smem=... heavy=..." counting tasks per stage) or grouped
+ * orthonormalisation ("cholqr lane l: jobs=..." / "extract lane l: jobs=..."),
+ * lane by lane, then "lanes=... tasks=... items=... area=...". Requests are
+ * dealt to lanes (request k to lane k mod lanes; one lane per four requests, at
+ * most four), each a sequence on its own stream of the graph. The
+ * planner checks that every dependency precedes its dependant in the same step
+ * (TUCKER_ERR_INVALID_ARG otherwise); unsupported batches return
+ * TUCKER_ERR_UNSUPPORTED. */
+tucker_status tucker_batch_describe(int n, const tucker_request* reqs, const tucker_opts* opts, char* buf,
+                                    size_t len);
 
 /* ---------------------------------------------------------------- autotuning
  * Not part of the paper's method. When enabled, the first synchronous call

@@ -30,6 +30,7 @@ PROB = {"nearly_optimal": 0, "uniform": 1}
 FORM = {"paper": 0, "range": 1, "related": 2}
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x1": 3}
 FLAG_ASYNC = 1
+FLAG_WORKLIST = 2
 
 
 class TuckerError(RuntimeError):
@@ -101,6 +102,7 @@ _SIGS = {
     "tucker_server_destroy": [_VP],
     "tucker_batch_workspace_size": [_INT, _VP, _P(Opts), _P(C.c_size_t)],
     "tucker_batch_run": [_INT, _VP, _P(Opts)],
+    "tucker_batch_describe": [_INT, _VP, _P(Opts), C.c_char_p, C.c_size_t],
     "tucker_autotune_enable": [_INT],
     "tucker_autotune_count": [],
     "tucker_autotune_entry": [_I64],
@@ -113,7 +115,7 @@ _RESTYPES = {"tucker_status_string": C.c_char_p, "tucker_launch_count": C.c_int6
              "tucker_autotune_entry": C.c_char_p}
 KERNEL_CLASSES = {"power": 0, "ttm": 1, "gather": 2, "norms": 3, "extract": 4, "sample": 5, "power_bf16": 6,
                   "power_tf32": 7, "ttm_bf16": 8, "power_bf16x1": 9, "ttm_wide": 10, "power_wide1": 11,
-                  "power_wide2": 12, "range_wide": 13, "gram_wide": 14}
+                  "power_wide2": 12, "range_wide": 13, "gram_wide": 14, "worklist": 15}
 
 
 def lib():
@@ -278,6 +280,28 @@ def workspace_size(which: str, dims, ranks, P=10, q=1, c=0, dtype=torch.float32,
     return int(n.value)
 
 
+def batch_describe(specs, dtype=torch.float32, form="paper", prec="fp32") -> str:
+    """The work list a batch would run (tucker_batch_describe with
+    TUCKER_FLAG_WORKLIST): one line per step or grouped orthonormalisation.
+    ``specs``: dicts with which, dims, ranks and optionally P, q, c, seed; host
+    only (no buffers are touched)."""
+    arr = (Request * len(specs))()
+    keep = []
+    for k, r in enumerate(specs):
+        dims, ranks = list(r["dims"]), list(r["ranks"])
+        d64, r32 = _i64(dims), _i32(ranks)
+        Up = (C.c_void_p * len(dims))(*([256] * len(dims)))
+        arr[k] = Request(C.sizeof(Request), 0 if r["which"] == "T" else 1, 0 if dtype == torch.float32 else 1, 256,
+                         d64, len(dims), r32, int(r.get("P", 5)), int(r.get("q", 1)), int(r.get("c", 0)),
+                         PROB[r.get("prob", "uniform")], int(r.get("seed", 0)), Up, 256)
+        keep.append((d64, r32, Up))
+    buf = C.create_string_buffer(1 << 16)
+    o = make_opts(form=form, prec=prec, flags=FLAG_WORKLIST)
+    _check("tucker_batch_describe", lib().tucker_batch_describe(len(specs), C.cast(arr, C.c_void_p), C.byref(o), buf,
+                                                                len(buf)))
+    return buf.value.decode()
+
+
 def plan_describe(which: str, dims, ranks, P=10, q=1, c=0, dtype=torch.float32, **kw) -> str:
     """The arithmetic each mode of a driver call takes (tucker_plan_describe),
     one line per mode; host only."""
@@ -378,10 +402,12 @@ def gram(A, dims, mode, stream=None, prec="bf16"):
     return G
 
 
-def check_wait_timeout(iters=1000, stream=None) -> int:
+def check_wait_timeout(iters=1000, stream=None, worklist=False) -> int:
     """tucker_check_wait_timeout: the status (an int, not raised) of a bounded
-    device wait that nothing completes; TUCKER_ERR_TIMEOUT (5) when the path works."""
-    o = make_opts(stream=stream)
+    device wait that nothing completes (the tensor-core kernels' mbarrier wait,
+    or with ``worklist`` the work-list kernel's dependency wait);
+    TUCKER_ERR_TIMEOUT (5) when the path works."""
+    o = make_opts(stream=stream, flags=FLAG_WORKLIST if worklist else 0)
     return int(lib().tucker_check_wait_timeout(int(iters), C.byref(o)))
 
 
@@ -697,9 +723,12 @@ class Batch:
     runs on its own stream of the graph; with CUDA's default of 8 hardware work
     queues (``CUDA_DEVICE_MAX_CONNECTIONS``, read when the process first uses
     the GPU) streams sharing a queue wait on one another, so set it to 32 for
-    batches of more than 8 requests."""
+    batches of more than 8 requests. ``worklist=True`` runs the batch through
+    the work-list kernel instead (TUCKER_FLAG_WORKLIST: one persistent launch
+    per step for every request, grouped orthonormalisations; Algorithms 1/2,
+    FP32 arithmetic, no sampling, extents <= 256, ranks <= 32)."""
 
-    def __init__(self, requests, form="paper", prec="fp32"):
+    def __init__(self, requests, form="paper", prec="fp32", worklist=False):
         self._keep = []
         self.outputs = []
         self._offsets = []
@@ -722,15 +751,16 @@ class Batch:
         self._reqs = arr
         self._n = len(requests)
         self._form, self._prec = form, prec
+        self._flags = FLAG_WORKLIST if worklist else 0
         n = C.c_size_t(0)
-        o = make_opts(form=form, prec=prec)
+        o = make_opts(form=form, prec=prec, flags=self._flags)
         _check("tucker_batch_workspace_size",
                lib().tucker_batch_workspace_size(self._n, C.cast(arr, C.c_void_p), C.byref(o), C.byref(n)))
         self.workspace = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=requests[0]["A"].device)
 
     def run(self, stream=None, sync=True):
         o = make_opts(form=self._form, prec=self._prec, stream=stream, workspace=self.workspace,
-                      flags=0 if sync else FLAG_ASYNC)
+                      flags=self._flags | (0 if sync else FLAG_ASYNC))
         _check("tucker_batch_run", lib().tucker_batch_run(self._n, C.cast(self._reqs, C.c_void_p), C.byref(o)))
         return self.outputs
 

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -835,6 +836,336 @@ tucker_status adaptive_run(const T* A, const int64_t* dims, int N, double eps, i
 
 tucker_status status_from_cuda(cudaError_t e) { return from_cuda(e); }
 
+// ------------------------------------------------------------------ work-list batches
+// The requests of a batch as steps of the work-list kernel and grouped
+// orthonormalisations, in the order of the drivers' own launches: for each mode
+// n (and each power step k) one step with every request's stage, then the
+// orthonormalisation of every request's sketch in one launch; a last step forms
+// the cores. ST-HOSVD's step for mode n carries the truncation by U_{n-1}
+// ahead of the power step it feeds. The requests are dealt to lanes (request k
+// to lane k mod lanes), each lane a sequence of its own on a stream of its own,
+// so one lane's orthonormalisations (a few CTAs each) overlap another lane's
+// streaming steps. Each request keeps its own workspace slice (the layout of an
+// asynchronous call), so its results are those of the request alone (FP32
+// power-step tiles as planned, without autotuning).
+tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts& opts, char* ws,
+                            const std::vector<size_t>& offsets, WorklistPlan& wp) {
+    wp = WorklistPlan();
+    Opts o;
+    tucker_status rs = read_opts(&opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (o.form != TUCKER_FORM_PAPER || o.prec != TUCKER_SK_FP32 || o.alpha != 0.0) return TUCKER_ERR_UNSUPPORTED;
+    if (n < 1 || (int)offsets.size() < n) return TUCKER_ERR_INVALID_ARG;
+    const int elem = reqs[0].dt == TUCKER_F64 ? 8 : 4;
+    wp.elem = elem;
+    std::vector<Plan> plans(n);
+    std::vector<Work> works(n);
+    for (int k = 0; k < n; ++k) {
+        const tucker_request& r = reqs[k];
+        if ((r.dt != TUCKER_F32 && r.dt != TUCKER_F64) || (r.dt == TUCKER_F64 ? 8 : 4) != elem) return TUCKER_ERR_UNSUPPORTED;
+        if (r.c != 0) return TUCKER_ERR_UNSUPPORTED;
+        rs = make_plan(r.which == 1, elem, r.dims, r.N, r.ranks, r.P, r.q, 0, o, plans[k]);
+        if (rs != TUCKER_OK) return rs;
+        const Plan& p = plans[k];
+        for (int m = 0; m < r.N; ++m) {
+            const ModePlan& mp = p.m[m];
+            if (mp.v.i > kThreads || r.dims[m] > kThreads || worklist_ttm_opt(r.ranks[m]) == 0 || mp.T != 0 ||
+                mp.gram || mp.half || mp.tc || mp.tf32 || mp.bf16x1 || mp.wide)
+                return TUCKER_ERR_UNSUPPORTED;
+            if (mp.pp.jb != (elem == 4 ? 32 : 16)) return TUCKER_ERR_UNSUPPORTED;
+        }
+        Arena a;
+        a.base = ws ? ws + offsets[k] : nullptr;
+        a.cap = ~size_t(0) >> 1;
+        carve(p, a, works[k]);
+    }
+    // every extent a block program will touch, checked against the buffer it
+    // targets (elements): what the items and jobs read and write stays inside
+    // the request's buffers whatever the shapes
+    bool fits = true;
+    auto need = [&](bool ok) { fits = fits && ok; };
+    std::vector<int64_t> cap_il(n), cap_part(n), cap_inter(n), cap_fac(n), cap_A(n), cap_G(n);
+    for (int k = 0; k < n; ++k) {
+        const Plan& p = plans[k];
+        const tucker_request& r = reqs[k];
+        cap_il[k] = p.maxI * p.maxL;
+        cap_part[k] = (int64_t)(p.max_partials / elem);
+        cap_inter[k] = p.inter_elems;
+        cap_fac[k] = (int64_t)r.q * p.maxL * p.maxL;        // paper form without half steps: q slots
+        cap_A[k] = prod(r.dims, r.N);
+        int64_t g = 1;
+        for (int m = 0; m < r.N; ++m) g *= r.ranks[m];
+        cap_G[k] = g;
+    }
+    // four requests or more per lane, at most four lanes
+    wp.lanes = std::max(1, std::min(4, n / 4));
+    std::vector<WTask>& tasks = wp.tasks;
+    std::vector<WItem>& items = wp.items;
+    auto add = [&](WTask t, int gx, int gy) -> int {
+        t.nitems = gx * gy;
+        const int id = (int)tasks.size();
+        tasks.push_back(t);
+        for (int x = 0; x < gx; ++x)
+            for (int y = 0; y < gy; ++y) items.push_back(WItem{id, x, y, 0});
+        return id;
+    };
+    auto base_task = [&](int kind, int k) {
+        WTask t{};
+        t.kind = kind;
+        t.dep[0] = t.dep[1] = -1;
+        t.status = works[k].status;
+        return t;
+    };
+    const int NF = elem == 4 ? 2 : 1;
+    for (int lane = 0; lane < wp.lanes; ++lane) {
+        std::vector<int> mem;
+        for (int k = lane; k < n; k += wp.lanes) mem.push_back(k);
+        int maxN = 0, maxq = 0;
+        for (int k : mem) {
+            maxN = std::max(maxN, reqs[k].N);
+            maxq = std::max(maxq, reqs[k].q);
+        }
+        size_t step_smem = 0;
+        int step_heavy = 0;
+        int step_begin = (int)items.size();
+        auto note = [&](const WTask& t, size_t smem) {
+            step_smem = std::max(step_smem, smem);
+            step_heavy |= worklist_heavy(t) ? 1 : 0;
+        };
+        auto close_step = [&]() {
+            if ((int)items.size() > step_begin)
+                wp.ops.push_back(
+                    WorklistOp{0, step_begin, (int)items.size(), wp.steps++, step_smem, 0, step_heavy, lane});
+            step_begin = (int)items.size();
+            step_smem = 0;
+            step_heavy = 0;
+        };
+        // the mode product out = in x_m U (fibers of view v), as one task
+        auto ttm_task = [&](int k, const void* in, const ModeView& v, const void* U, int64_t K, void* out, int dep,
+                            int64_t in_cap, int64_t out_cap) {
+            need(v.fibers() * v.i <= in_cap && v.fibers() * K <= out_cap && v.i <= kThreads);
+            WTask t = base_task(kWTtm, k);
+            t.in = in;
+            t.X = U;
+            t.out = out;
+            t.v = v;
+            t.K = K;
+            t.opt = worklist_ttm_opt(K);
+            t.dep[0] = dep;
+            note(t, worklist_ttm_smem(elem, t.opt));
+            const int64_t gx = (v.fibers() + 64 * NF - 1) / (64 * NF), gy = (K + 4 * t.opt - 1) / (4 * t.opt);
+            return add(t, (int)gx, (int)gy);
+        };
+        std::vector<const void*> cur(n);
+        for (int k : mem) cur[k] = reqs[k].A;
+        std::vector<int> init(n, -1), prev(n, -1);
+        for (int m = 0; m < maxN; ++m) {
+            // step: [truncation by U_{m-1}], [status reset], Omega_m, power step 1, its sum
+            std::vector<int> ttm(n, -1), gen(n, -1), pw(n, -1);
+            for (int k : mem) {
+                const tucker_request& r = reqs[k];
+                if (r.which == 1 && m > 0 && m < r.N) {
+                    void* out = (void*)works[k].inter[(m - 1) & 1];
+                    ttm[k] = ttm_task(k, cur[k], plans[k].m[m - 1].v, r.U[m - 1], r.ranks[m - 1], out, -1,
+                                      m == 1 ? cap_A[k] : cap_inter[k], cap_inter[k]);
+                    cur[k] = out;
+                }
+            }
+            for (int k : mem) {
+                const tucker_request& r = reqs[k];
+                if (m >= r.N) continue;
+                const ModePlan& mp = plans[k].m[m];
+                if (m == 0) init[k] = add(base_task(kWInit, k), 1, 1);
+                WTask t = base_task(kWGen, k);
+                t.out = works[k].X0;
+                t.rows = mp.v.i;
+                t.cols = mp.L;
+                t.seed = r.seed;
+                t.sid = stream_id(0, m);
+                t.dep[0] = m == 0 ? init[k] : -1;
+                const int64_t ne = mp.v.i * (int64_t)mp.L;
+                need(ne <= cap_il[k]);
+                gen[k] = add(t, (int)std::max<int64_t>(1, (ne + 4 * kThreads - 1) / (4 * kThreads)), 1);
+            }
+            for (int q = 0; q < maxq; ++q) {
+                if (q > 0) {
+                    // CholeskyQR of every sketch that takes another power step, in one launch
+                    const int j0 = (int)wp.jobs.size();
+                    for (int k : mem) {
+                        const tucker_request& r = reqs[k];
+                        if (m >= r.N || q >= r.q) continue;
+                        const ModePlan& mp = plans[k].m[m];
+                        OrthJob j = orth_job(mp.op, works[k].orth);
+                        j.X = works[k].X1;
+                        j.Q = works[k].Q;
+                        j.R = mp.R;
+                        j.factor = works[k].factors + (size_t)(q - 1) * mp.L * mp.L;
+                        j.fofs = 0;
+                        need(mp.v.i * (int64_t)mp.L <= cap_il[k] && (int64_t)q * mp.L * mp.L <= cap_fac[k]);
+                        j.status = works[k].status;
+                        wp.jobs.push_back(j);
+                    }
+                    if ((int)wp.jobs.size() > j0)
+                        wp.ops.push_back(WorklistOp{1, j0, (int)wp.jobs.size(), -1, 0, 0, 0, lane});
+                }
+                for (int k : mem) {
+                    const tucker_request& r = reqs[k];
+                    if (m >= r.N || q >= r.q) continue;
+                    const ModePlan& mp = plans[k].m[m];
+                    WTask t = base_task(kWPow, k);
+                    t.in = r.which == 1 ? cur[k] : r.A;
+                    t.v = mp.v;
+                    t.X = q == 0 ? works[k].X0 : works[k].Q;
+                    t.L = mp.L;
+                    t.out = works[k].partials;
+                    t.tiles = mp.pp.tiles;
+                    t.parts = mp.pp.parts;
+                    t.jb = mp.pp.jb;
+                    t.lg = mp.pp.lg;
+                    if (q == 0) {
+                        t.dep[0] = gen[k];
+                        t.dep[1] = ttm[k];
+                    }
+                    need(mp.v.fibers() * mp.v.i <= (r.which == 1 && m > 0 ? cap_inter[k] : cap_A[k]) &&
+                         mp.v.i * (int64_t)mp.L <= cap_il[k] &&
+                         (int64_t)mp.pp.parts * mp.v.i * mp.L <= cap_part[k] && mp.v.i <= kThreads &&
+                         mp.pp.tiles * mp.pp.jb >= mp.v.fibers() && mp.pp.groups * mp.pp.lg >= mp.L);
+                    note(t, worklist_pow_smem(elem, (int)mp.v.i, mp.pp.lg));
+                    pw[k] = add(t, mp.pp.groups, mp.pp.parts);
+                }
+                for (int k : mem) {
+                    const tucker_request& r = reqs[k];
+                    if (m >= r.N || q >= r.q) continue;
+                    const ModePlan& mp = plans[k].m[m];
+                    WTask t = base_task(kWRed, k);
+                    t.in = works[k].partials;
+                    t.out = works[k].X1;
+                    t.parts = mp.pp.parts;
+                    t.count = mp.v.i * (int64_t)mp.L;
+                    t.dep[0] = pw[k];
+                    need((int64_t)t.parts * t.count <= cap_part[k] && t.count <= cap_il[k]);
+                    add(t, (int)std::max<int64_t>(1, (t.count + 255) / 256), 1);
+                }
+                close_step();
+            }
+            // the leading factor of every sketch, in one launch
+            const int j0 = (int)wp.jobs.size();
+            for (int k : mem) {
+                const tucker_request& r = reqs[k];
+                if (m >= r.N) continue;
+                const ModePlan& mp = plans[k].m[m];
+                OrthJob j = orth_job(mp.op, works[k].orth);
+                j.X = works[k].X1;
+                j.Q = works[k].Q;
+                j.R = mp.R;
+                j.factor = works[k].factors;
+                j.nprev = r.q - 1;
+                j.fofs = (int64_t)(r.q - 1) * mp.L * mp.L;
+                j.U = r.U[m];
+                j.status = works[k].status;
+                j.staged = orth_group_staged(j, elem) ? 1 : 0;
+                need(mp.v.i * (int64_t)mp.L <= cap_il[k] && (int64_t)r.q * mp.L * mp.L <= cap_fac[k] &&
+                     mp.v.i == r.dims[m] && mp.R == r.ranks[m]);
+                wp.jobs.push_back(j);
+            }
+            wp.ops.push_back(WorklistOp{2, j0, (int)wp.jobs.size(), -1, 0, 0, 0, lane});
+        }
+        // the cores: ST-HOSVD's last truncation; T-HOSVD's chain x_1 U_1^T ... x_N U_N^T
+        for (int m = 0; m < maxN; ++m) {
+            for (int k : mem) {
+                const tucker_request& r = reqs[k];
+                if (r.which == 1) {
+                    if (m == r.N - 1)
+                        ttm_task(k, cur[k], plans[k].m[m].v, r.U[m], r.ranks[m], r.G, -1,
+                                 m == 0 ? cap_A[k] : cap_inter[k], cap_G[k]);
+                    continue;
+                }
+                if (m >= r.N) continue;
+                int64_t e[kMaxOrder];
+                for (int a = 0; a < r.N; ++a) e[a] = a < m ? r.ranks[a] : r.dims[a];
+                void* out = m == r.N - 1 ? r.G : works[k].inter[m & 1];
+                prev[k] = ttm_task(k, cur[k], view_of(e, r.N, m), r.U[m], r.ranks[m], out, prev[k],
+                                   m == 0 ? cap_A[k] : cap_inter[k], m == r.N - 1 ? cap_G[k] : cap_inter[k]);
+                cur[k] = out;
+            }
+        }
+        close_step();
+    }
+    if (!fits) return TUCKER_ERR_INVALID_ARG;
+    // every dependency is an earlier task whose items all come before the first
+    // item of its dependant, in the same step (what makes the waits end)
+    std::vector<int> first(tasks.size(), -1), last(tasks.size(), -1), step_of(items.size(), -1);
+    for (const WorklistOp& op : wp.ops)
+        if (op.kind == 0)
+            for (int i = op.a; i < op.b; ++i) step_of[i] = op.step;
+    for (int i = 0; i < (int)items.size(); ++i) {
+        const int t = items[i].task;
+        if (first[t] < 0) first[t] = i;
+        last[t] = i;
+    }
+    for (int t = 0; t < (int)tasks.size(); ++t)
+        for (int d : tasks[t].dep)
+            if (d >= 0 && (d >= t || last[d] >= first[t] || step_of[last[d]] != step_of[first[t]]))
+                return TUCKER_ERR_INVALID_ARG;
+    const size_t a256 = 255;
+    wp.tasks_off = 0;
+    wp.items_off = (sizeof(WTask) * tasks.size() + a256) & ~a256;
+    wp.jobs_off = wp.items_off + ((sizeof(WItem) * items.size() + a256) & ~a256);
+    wp.desc_bytes = wp.jobs_off + sizeof(OrthJob) * wp.jobs.size();
+    wp.counters_off = (wp.desc_bytes + a256) & ~a256;
+    wp.counter_bytes = sizeof(unsigned) * ((size_t)wp.steps + tasks.size() + 1);
+    wp.area_bytes = wp.counters_off + ((wp.counter_bytes + a256) & ~a256);
+    return TUCKER_OK;
+}
+
+void worklist_prepare(WorklistPlan& wp) {
+    for (WorklistOp& op : wp.ops)
+        if (op.kind == 0) op.grid = worklist_grid(wp.elem, op.heavy != 0, op.smem, op.b - op.a);
+}
+
+void worklist_pack(const WorklistPlan& wp, void* host) {
+    char* h = (char*)host;
+    std::memcpy(h + wp.tasks_off, wp.tasks.data(), sizeof(WTask) * wp.tasks.size());
+    std::memcpy(h + wp.items_off, wp.items.data(), sizeof(WItem) * wp.items.size());
+    if (!wp.jobs.empty()) std::memcpy(h + wp.jobs_off, wp.jobs.data(), sizeof(OrthJob) * wp.jobs.size());
+}
+
+cudaError_t worklist_enqueue(const WorklistPlan& wp, char* area, const void* host_desc,
+                             const std::vector<cudaStream_t>& lane_streams, cudaEvent_t uploaded) {
+    if ((int)lane_streams.size() < wp.lanes) return cudaErrorInvalidValue;
+    cudaStream_t s0 = lane_streams[0];
+    cudaError_t e = cudaMemcpyAsync(area, host_desc, wp.desc_bytes, cudaMemcpyHostToDevice, s0);
+    unsigned* counters = (unsigned*)(area + wp.counters_off);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, wp.counter_bytes, s0);
+    if (e == cudaSuccess) e = cudaEventRecord(uploaded, s0);
+    for (int l = 1; l < wp.lanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(lane_streams[l], uploaded, 0);
+    const WTask* tasks = (const WTask*)(area + wp.tasks_off);
+    const WItem* items = (const WItem*)(area + wp.items_off);
+    const OrthJob* jobs = (const OrthJob*)(area + wp.jobs_off);
+    unsigned* done = counters + wp.steps;
+    int* abort_flag = (int*)(done + wp.tasks.size());
+    for (const WorklistOp& op : wp.ops) {
+        if (e != cudaSuccess) break;
+        cudaStream_t s = lane_streams[op.lane];
+        if (op.kind == 0) {
+            e = wp.elem == 4 ? launch_worklist<float>(tasks, items, op.a, op.b, counters + op.step, done, abort_flag,
+                                                      op.heavy != 0, op.smem, op.grid, s)
+                             : launch_worklist<double>(tasks, items, op.a, op.b, counters + op.step, done, abort_flag,
+                                                       op.heavy != 0, op.smem, op.grid, s);
+        } else {
+            const std::vector<OrthJob> h(wp.jobs.begin() + op.a, wp.jobs.begin() + op.b);
+            ProfScope prof(kKExtract, 0.0, 0.0, s);
+            if (op.kind == 1)
+                e = wp.elem == 4 ? launch_cholqr_group<float>(jobs + op.a, h, s)
+                                 : launch_cholqr_group<double>(jobs + op.a, h, s);
+            else
+                e = wp.elem == 4 ? launch_extract_group<float>(jobs + op.a, h, s)
+                                 : launch_extract_group<double>(jobs + op.a, h, s);
+        }
+    }
+    return e;
+}
+
 }  // namespace tk
 
 using namespace tk;
@@ -1238,10 +1569,13 @@ tucker_status tucker_check_wait_timeout(int32_t iters, const tucker_opts* opts) 
     tucker_status rs = read_opts(opts, o);
     if (rs != TUCKER_OK) return rs;
     if (iters < 1 || iters > (1 << 24)) return TUCKER_ERR_INVALID_ARG;
+    const bool wl = (o.flags & TUCKER_FLAG_WORKLIST) != 0;
     Scratch sc;
-    if ((rs = sc.get(256, o.stream)) != TUCKER_OK) return rs;
+    if ((rs = sc.get(256 + (wl ? worklist_wait_check_bytes() : 0), o.stream)) != TUCKER_OK) return rs;
     cudaError_t e = cudaMemsetAsync(sc.p, 0, sizeof(int), o.stream);
-    if (e == cudaSuccess) e = launch_wait_timeout(iters, (int*)sc.p, o.stream);
+    if (e == cudaSuccess)
+        e = wl ? launch_worklist_wait_check(iters, (char*)sc.p + 256, (int*)sc.p, o.stream)
+               : launch_wait_timeout(iters, (int*)sc.p, o.stream);
     if (e != cudaSuccess) return from_cuda(e);
     return sync_status(o.stream, (const int*)sc.p);
 }

@@ -4,8 +4,13 @@
 // requests' asynchronous launch sequences, each on its own stream forked from an
 // origin stream, into one graph and instantiates it; later calls with the same
 // signature replay it with a single cudaGraphLaunch. Instantiated graphs are
-// kept in a small least-recently-used cache.
+// kept in a small least-recently-used cache. With TUCKER_FLAG_WORKLIST the
+// graph instead holds the batch's work-list steps and grouped
+// orthonormalisations (worklist.cu, api.cu: worklist_plan): one launch per step
+// for every request together.
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <list>
 #include <mutex>
 #include <vector>
@@ -23,7 +28,13 @@ struct Cached {
     cudaGraphExec_t exec;
     std::vector<size_t> offsets;       // each request's workspace offset
     int64_t kernels;                   // kernel launches one replay makes
+    void* desc = nullptr;              // work-list batches: pinned host image of the descriptors
 };
+
+void release(Cached& c) {
+    cudaGraphExecDestroy(c.exec);
+    if (c.desc) cudaFreeHost(c.desc);
+}
 
 std::mutex g_mu;
 std::list<Cached> g_cache;             // front = most recently used
@@ -52,6 +63,7 @@ std::vector<unsigned char> signature(int n, const tucker_request* r, const tucke
     put(s, o.prec);
     put(s, o.workspace);
     put(s, o.workspace_bytes);
+    put(s, o.flags & TUCKER_FLAG_WORKLIST);
     for (int k = 0; k < n; ++k) {
         put(s, r[k].which);
         put(s, r[k].dt);
@@ -72,8 +84,10 @@ std::vector<unsigned char> signature(int n, const tucker_request* r, const tucke
     return s;
 }
 
+// Each request's workspace offset and the total; work-list batches add the
+// descriptor area after the requests' slices (at area_off).
 tucker_status check(int n, const tucker_request* reqs, const tucker_opts* opts, bool check_ptrs,
-                    std::vector<size_t>& offsets, size_t& total) {
+                    std::vector<size_t>& offsets, size_t& total, size_t* area_off = nullptr) {
     if (n < 1 || !reqs) return TUCKER_ERR_INVALID_ARG;
     tucker_opts o;
     std::memset(&o, 0, sizeof(o));
@@ -100,6 +114,13 @@ tucker_status check(int n, const tucker_request* reqs, const tucker_opts* opts, 
         offsets[k] = total;
         total += up(ws);
     }
+    if (area_off) *area_off = total;
+    if (opts && (opts->flags & TUCKER_FLAG_WORKLIST)) {
+        tk::WorklistPlan wp;
+        const tucker_status st = tk::worklist_plan(n, reqs, *opts, nullptr, offsets, wp);
+        if (st != TUCKER_OK) return st;
+        total += up(wp.area_bytes);
+    }
     return TUCKER_OK;
 }
 
@@ -116,13 +137,59 @@ tucker_status tucker_batch_workspace_size(int n, const tucker_request* reqs, con
     return st;
 }
 
-tucker_status tucker_batch_run(int n, const tucker_request* reqs, const tucker_opts* opts) {
-    if (!opts || opts->struct_size < sizeof(tucker_opts) || !opts->workspace) return TUCKER_ERR_INVALID_ARG;
+tucker_status tucker_batch_describe(int n, const tucker_request* reqs, const tucker_opts* opts, char* buf,
+                                    size_t len) {
+    if (!opts || opts->struct_size < sizeof(tucker_opts) || !(opts->flags & TUCKER_FLAG_WORKLIST) || !buf || len < 1)
+        return TUCKER_ERR_INVALID_ARG;
     std::vector<size_t> offsets;
     size_t total = 0;
     tucker_status st = check(n, reqs, opts, false, offsets, total);
     if (st != TUCKER_OK) return st;
+    tk::WorklistPlan wp;
+    st = tk::worklist_plan(n, reqs, *opts, nullptr, offsets, wp);
+    if (st != TUCKER_OK) return st;
+    static const char* kNames[] = {"init", "gaussian", "power", "sum", "product"};
+    std::string out;
+    char line[256];
+    for (const tk::WorklistOp& op : wp.ops) {
+        if (op.kind == 0) {
+            int count[5] = {0, 0, 0, 0, 0};
+            int last = -1;
+            for (int i = op.a; i < op.b; ++i)
+                if (wp.items[i].task != last) {
+                    last = wp.items[i].task;
+                    ++count[wp.tasks[last].kind];
+                }
+            snprintf(line, sizeof line, "step %d lane %d: items=%d", op.step, op.lane, op.b - op.a);
+            out += line;
+            for (int k = 0; k < 5; ++k) {
+                snprintf(line, sizeof line, " %s=%d", kNames[k], count[k]);
+                out += line;
+            }
+            snprintf(line, sizeof line, " smem=%zu heavy=%d\n", op.smem, op.heavy);
+            out += line;
+        } else {
+            snprintf(line, sizeof line, "%s lane %d: jobs=%d\n", op.kind == 1 ? "cholqr" : "extract", op.lane,
+                     op.b - op.a);
+            out += line;
+        }
+    }
+    snprintf(line, sizeof line, "lanes=%d tasks=%zu items=%zu area=%zu\n", wp.lanes, wp.tasks.size(), wp.items.size(),
+             wp.area_bytes);
+    out += line;
+    if (out.size() + 1 > len) return TUCKER_ERR_INVALID_ARG;
+    std::memcpy(buf, out.c_str(), out.size() + 1);
+    return TUCKER_OK;
+}
+
+tucker_status tucker_batch_run(int n, const tucker_request* reqs, const tucker_opts* opts) {
+    if (!opts || opts->struct_size < sizeof(tucker_opts) || !opts->workspace) return TUCKER_ERR_INVALID_ARG;
+    std::vector<size_t> offsets;
+    size_t total = 0, area_off = 0;
+    tucker_status st = check(n, reqs, opts, false, offsets, total, &area_off);
+    if (st != TUCKER_OK) return st;
     if (opts->workspace_bytes < total) return TUCKER_ERR_INVALID_ARG;
+    const bool worklist = (opts->flags & TUCKER_FLAG_WORKLIST) != 0;
     cudaStream_t user = (cudaStream_t)opts->stream;
     const std::vector<unsigned char> sig = signature(n, reqs, *opts);
     std::lock_guard<std::mutex> g(g_mu);
@@ -158,10 +225,40 @@ tucker_status tucker_batch_run(int n, const tucker_request* reqs, const tucker_o
                 return TUCKER_ERR_CUDA;
             }
         cudaGraph_t graph = nullptr;
+        Cached c;
+        tk::WorklistPlan wp;
+        if (worklist) {
+            // the descriptors point into this workspace; their host image is pinned
+            // (the graph's upload node reads it on every replay)
+            st = tk::worklist_plan(n, reqs, *opts, (char*)opts->workspace, offsets, wp);
+            if (st == TUCKER_OK && cudaMallocHost(&c.desc, wp.desc_bytes ? wp.desc_bytes : 1) != cudaSuccess) {
+                c.desc = nullptr;
+                cudaGetLastError();
+                st = TUCKER_ERR_OOM;
+            }
+            if (st != TUCKER_OK) {
+                for (auto& x : ev) cudaEventDestroy(x);
+                return st;
+            }
+            tk::worklist_pack(wp, c.desc);
+            tk::worklist_prepare(wp);
+        }
         const int64_t k0 = tucker_launch_count();
         e = cudaStreamBeginCapture(g_origin, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess && worklist) {
+            // lane 0 on the origin stream, the others forked from it after the
+            // upload (ev[n]) and joined back through ev[1..]
+            std::vector<cudaStream_t> lanes(wp.lanes);
+            lanes[0] = g_origin;
+            for (int l = 1; l < wp.lanes; ++l) lanes[l] = g_side[l - 1];
+            e = tk::worklist_enqueue(wp, (char*)opts->workspace + area_off, c.desc, lanes, ev[n]);
+            for (int l = 1; l < wp.lanes && e == cudaSuccess; ++l) {
+                e = cudaEventRecord(ev[l - 1], lanes[l]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(g_origin, ev[l - 1], 0);
+            }
+        }
         if (e == cudaSuccess) e = cudaEventRecord(ev[n], g_origin);
-        for (int k = 0; k < n && st == TUCKER_OK && e == cudaSuccess; ++k) {
+        for (int k = 0; k < n && !worklist && st == TUCKER_OK && e == cudaSuccess; ++k) {
             const tucker_request& r = reqs[k];
             e = cudaStreamWaitEvent(g_side[k], ev[n], 0);
             if (e != cudaSuccess) break;
@@ -179,21 +276,21 @@ tucker_status tucker_batch_run(int n, const tucker_request* reqs, const tucker_o
         }
         const cudaError_t ee = cudaStreamEndCapture(g_origin, &graph);
         if (e == cudaSuccess) e = ee;
-        Cached c;
         c.offsets = offsets;
         c.sig = sig;
         c.kernels = tucker_launch_count() - k0;   // counted once, for the launch below
         if (e == cudaSuccess && st == TUCKER_OK) e = cudaGraphInstantiate(&c.exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         for (auto& x : ev) cudaEventDestroy(x);
-        if (st != TUCKER_OK) return st;
-        if (e != cudaSuccess) {
+        if (st != TUCKER_OK || e != cudaSuccess) {
+            if (c.desc) cudaFreeHost(c.desc);
+            if (st != TUCKER_OK) return st;
             cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? TUCKER_ERR_OOM : TUCKER_ERR_CUDA;
+            return tk::status_from_cuda(e);          // records the error for tucker_last_cuda_error
         }
         g_cache.push_front(std::move(c));
         if (g_cache.size() > kCacheSize) {
-            cudaGraphExecDestroy(g_cache.back().exec);
+            release(g_cache.back());
             g_cache.pop_back();
         }
         hit = g_cache.begin();

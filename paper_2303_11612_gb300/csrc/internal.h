@@ -174,6 +174,123 @@ template <typename T>
 cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors, int nprev, int R, T* U,
                            void* scratch, int* status, cudaStream_t s);
 
+// Grouped orthonormalisations (a batch's requests side by side in one launch,
+// job = blockIdx.y): the same block programs and results as launch_cholqr /
+// launch_extract of each job alone.
+struct OrthJob {
+    const void* X;          // I x L sketch
+    void* Q;                // I x L: the CholeskyQR output (cholqr), the extraction's Q1 (extract)
+    int64_t I;
+    int L, R;               // R: columns extracted
+    int rows, nblk;         // Gram rows per CTA, Gram CTAs (the plan's)
+    int nprev;              // extraction: earlier factors in the slots from `factor` on
+    int staged;             // extraction: the final pass keeps U in shared memory (orth_group_staged)
+    void* partial;          // orthonormalisation scratch (orth_job)
+    int* flag;
+    unsigned* ticket;
+    void* W;
+    double* factor;         // cholqr: the factor slot; extract: the first factor slot
+    int64_t fofs;           // doubles from `factor` to the slot this CholeskyQR pass writes (extract: nprev L^2)
+    void* U;                // extraction output, I x R
+    int* status;
+};
+// A job with the plan's sizes and the scratch regions filled in.
+OrthJob orth_job(const OrthPlan& p, void* scratch);
+bool orth_group_staged(const OrthJob& j, int elem_size);
+// d_jobs: the jobs in device memory; h_jobs: the same on the host (sizes of the launches).
+template <typename T>
+cudaError_t launch_cholqr_group(const OrthJob* d_jobs, const std::vector<OrthJob>& h_jobs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_extract_group(const OrthJob* d_jobs, const std::vector<OrthJob>& h_jobs, cudaStream_t s);
+
+// ---- work-list kernel of batched runs (worklist.cu)
+enum WKind : int { kWInit = 0, kWGen = 1, kWPow = 2, kWRed = 3, kWTtm = 4 };
+// One stage of one request's mode; its items are the blocks the stage's own
+// kernel would launch.
+struct WTask {
+    int kind;               // WKind
+    int nitems;             // items of this task
+    int dep[2];             // tasks whose items must all be done first (-1: none; always earlier in the list)
+    int* status;            // the request's status word
+    const void* in;         // kWPow, kWTtm: the tensor; kWRed: the partials
+    const void* X;          // kWPow: X_in (I x L); kWTtm: the factor U (I x K)
+    void* out;              // kWGen: Omega; kWPow: the partials; kWRed: X_out; kWTtm: the product
+    ModeView v;             // kWPow, kWTtm
+    int64_t tiles;          // kWPow: fiber tiles of jb fibers
+    int64_t count;          // kWRed: I L
+    int64_t K;              // kWTtm: outputs per fiber (R_n)
+    int64_t rows, cols;     // kWGen
+    uint64_t seed;
+    uint32_t sid;
+    int L, parts, jb, lg, opt;
+};
+// kWPow: x = column group, y = part; kWTtm: (x, y) = the product kernel's block;
+// kWGen, kWRed: x = block of the task's nitems.
+struct WItem {
+    int task, x, y, pad;
+};
+// Shared memory of a power-step item (jb fixed by the type: 32 FP32, 16 FP64), of
+// a mode-product item; the outputs-per-thread choice of a mode product with K
+// outputs (0 when K > 32, which the work list does not take).
+size_t worklist_pow_smem(int elem, int I, int lg);
+size_t worklist_ttm_smem(int elem, int opt);
+// Whether a task needs the kernel's heavy register class (column groups of 32, more than 16 outputs per block).
+bool worklist_heavy(const WTask& t);
+int worklist_ttm_opt(int64_t K);
+// The grid of a step with `items` items and `smem` bytes of dynamic shared
+// memory (the SMs times the CTAs that fit on one, at most one CTA per item);
+// also raises the kernel's shared-memory limit. Not for use under stream capture.
+int worklist_grid(int elem, bool heavy, size_t smem, int items);
+// A one-CTA work list whose second item waits for an item that is never listed:
+// the wait runs out after `iters` polls and sets kStatTimeout in *status.
+size_t worklist_wait_check_bytes();
+cudaError_t launch_worklist_wait_check(int iters, void* scratch, int* status, cudaStream_t s);
+// Items [begin, end) of one step; claim, done (one word per task) and abort_flag
+// zeroed before the batch's first step.
+template <typename T>
+cudaError_t launch_worklist(const WTask* tasks, const WItem* items, int begin, int end, unsigned* claim,
+                            unsigned* done, int* abort_flag, bool heavy, size_t smem, int grid, cudaStream_t s);
+
+// A batch as work-list steps and grouped orthonormalisations (api.cu).
+struct WorklistOp {
+    int kind;               // 0: work-list step over items [a, b); 1: CholeskyQR of jobs [a, b); 2: extraction of jobs [a, b)
+    int a, b;
+    int step;               // kind 0: the step's claim word
+    size_t smem;            // kind 0: dynamic shared memory
+    int grid = 0;           // kind 0: CTAs (worklist_prepare)
+    int heavy = 0;          // kind 0: a task needs the heavy register class
+    int lane = 0;           // the stream of the batch's graph it runs on
+};
+struct WorklistPlan {
+    int elem = 4;
+    std::vector<WTask> tasks;
+    std::vector<WItem> items;
+    std::vector<OrthJob> jobs;
+    std::vector<WorklistOp> ops;
+    int steps = 0;
+    int lanes = 1;          // requests k with k % lanes == l run their steps on stream l
+    // device area: tasks, items and jobs (uploaded from the host image), then the
+    // claim words (one per step), done words (one per task) and the abort flag
+    size_t tasks_off = 0, items_off = 0, jobs_off = 0, desc_bytes = 0;
+    size_t counters_off = 0, counter_bytes = 0, area_bytes = 0;
+};
+// The plan of n requests whose workspace slices start at ws + offsets[k] (ws may be
+// null: sizes only). TUCKER_ERR_UNSUPPORTED unless every request is Algorithm 1 or 2
+// in the paper form with the exact FMA arithmetic, no sampling, one element type,
+// every extent <= 256 and every rank <= 32.
+tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts& opts, char* ws,
+                            const std::vector<size_t>& offsets, WorklistPlan& wp);
+// Fills each step's grid (queries the device: call before stream capture).
+void worklist_prepare(WorklistPlan& wp);
+// The host image of the descriptors (wp.desc_bytes bytes at host).
+void worklist_pack(const WorklistPlan& wp, void* host);
+// Uploads the image to area (wp.area_bytes of device memory) and zeroes the
+// counters on lane_streams[0], then enqueues each lane's steps and grouped
+// launches on its stream (lane l on lane_streams[l], ordered after the upload;
+// the caller joins the lanes).
+cudaError_t worklist_enqueue(const WorklistPlan& wp, char* area, const void* host_desc,
+                             const std::vector<cudaStream_t>& lane_streams, cudaEvent_t uploaded);
+
 // ---- mode products and norms (kernels_ttm.cu)
 // out = A x_n M: M(k_out, i) read as Mp[i * ld_i + k_out * ld_k]. With a
 // device status word (FP32) the TMA-fed kernel is used where the shape allows;
@@ -204,7 +321,7 @@ tucker_status status_from_cuda(cudaError_t e);
 enum KernelClass { kKPower = 0, kKTtm = 1, kKGather = 2, kKNorms = 3, kKExtract = 4, kKSample = 5,
                    kKPowerBf16 = 6, kKPowerTf32 = 7, kKTtmBf16 = 8, kKPowerBf16x1 = 9, kKTtmWide = 10,
                    kKPowerWide1 = 11, kKPowerWide2 = 12, kKRangeWide = 13,
-                   kKGramWide = 14, kKernelClasses = 15 };
+                   kKGramWide = 14, kKWorklist = 15, kKernelClasses = 16 };
 void note_launch();
 void note_launches(int64_t n);   // a graph replay's kernels
 void profile_drain();

@@ -91,18 +91,18 @@ template <> struct GramAcc<double> {
     __device__ double value() const { return s; }
 };
 
-// Gram partial of this CTA's rows (packed upper triangle) -> partial[blockIdx.x].
+// Gram partial of block bid's rows (packed upper triangle) -> partial[bid].
 // Rows of X staged in shared memory per chunk of the Gram partial sums.
 constexpr int kGramChunk = 64;
 
 template <typename T, typename S>
 __device__ void gram_partial(const T* __restrict__ X, int64_t I, int L, int rows, S* __restrict__ partial,
-                             unsigned char* smem) {
+                             unsigned char* smem, int64_t bid) {
     T* xs = reinterpret_cast<T*>(smem);   // [kGramChunk][L]
-    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r0 = bid * rows;
     const int nr = (int)max((int64_t)0, min((int64_t)rows, I - r0));
     const int np = (int)packed_size(L);
-    S* out = partial + (int64_t)blockIdx.x * np;
+    S* out = partial + bid * np;
     // chunks of kGramChunk rows; each entry's chunk sums are added in chunk order
     // by the thread that owns the entry
     for (int c0 = 0; c0 < nr || c0 == 0; c0 += kGramChunk) {
@@ -126,11 +126,11 @@ __device__ void gram_partial(const T* __restrict__ X, int64_t I, int L, int rows
 }
 
 // True in exactly one CTA: the last to finish its partial (an atomic ticket, no waiting).
-__device__ bool last_cta(unsigned* ticket) {
+__device__ bool last_cta(unsigned* ticket, unsigned nblk) {
     __shared__ int last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == nblk - 1;
     __syncthreads();
     if (last) __threadfence();
     return last;
@@ -287,20 +287,21 @@ __device__ void upper_inverse(const S* R, const S* dinv, int L, S* Acc, S* Ri) {
 // ---------------------------------------------------------------- one CholeskyQR pass
 // R and R^-1 (packed, scalar S) of X^T X = R^T R.
 template <typename T>
-__global__ void __launch_bounds__(kST) gram_chol_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
-                                                       typename SmallScalar<T>::type* __restrict__ partial,
-                                                       unsigned* ticket, typename SmallScalar<T>::type* __restrict__ R,
-                                                       typename SmallScalar<T>::type* __restrict__ Rinv, int* status) {
+__device__ __forceinline__ void gram_chol_body(const T* __restrict__ X, int64_t I, int L, int rows,
+                                               typename SmallScalar<T>::type* __restrict__ partial, unsigned* ticket,
+                                               typename SmallScalar<T>::type* __restrict__ R,
+                                               typename SmallScalar<T>::type* __restrict__ Rinv, int* status,
+                                               int bid, int nblk) {
     using S = typename SmallScalar<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    gram_partial<T, S>(X, I, L, rows, partial, smem_raw);
-    if (!last_cta(ticket)) return;
+    gram_partial<T, S>(X, I, L, rows, partial, smem_raw, bid);
+    if (!last_cta(ticket, nblk)) return;
     const int np = (int)packed_size(L);
     S* G = reinterpret_cast<S*>(smem_raw);
     S* W = G + np;
     S* RT = W + np;
     S* dinv = RT + np;
-    reduce_cholesky<T, S>(partial, gridDim.x, L, I, G, W, dinv, reinterpret_cast<int*>(RT), ticket, status);
+    reduce_cholesky<T, S>(partial, nblk, L, I, G, W, dinv, reinterpret_cast<int*>(RT), ticket, status);
     upper_inverse<S>(W, dinv, L, RT, G);
     for (int p = threadIdx.x; p < np; p += blockDim.x) {
         R[p] = W[p];
@@ -326,9 +327,9 @@ template <> struct ApplyAcc<double> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kT) apply_rinv_kernel(const T* __restrict__ X, int64_t I, int L,
-                                                        const typename SmallScalar<T>::type* __restrict__ Rinv,
-                                                        T* __restrict__ Q) {
+__device__ __forceinline__ void apply_rinv_body(const T* __restrict__ X, int64_t I, int L,
+                                                const typename SmallScalar<T>::type* __restrict__ Rinv,
+                                                T* __restrict__ Q, int bid, int nblk) {
     using S = typename SmallScalar<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* Ri = reinterpret_cast<S*>(smem_raw);    // packed
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(kT) apply_rinv_kernel(const T* __restrict__ X,
     for (int p = threadIdx.x; p < np; p += kT) Ri[p] = Rinv[p];
     __syncthreads();
     const int64_t n = I * L;
-    for (int64_t e = (int64_t)blockIdx.x * kT + threadIdx.x; e < n; e += (int64_t)gridDim.x * kT) {
+    for (int64_t e = (int64_t)bid * kT + threadIdx.x; e < n; e += (int64_t)nblk * kT) {
         const int l = (int)(e / I);
         const int64_t i = e - (int64_t)l * I;
         ApplyAcc<T> acc;
@@ -803,18 +804,16 @@ __host__ __device__ inline XLayout xlayout(int L, int R, int elem) {
 // (scalar S, L x R, column-major). A column with no direction left gets W = 0
 // (the final pass completes it).
 template <typename T>
-__global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
-                                                      typename SmallScalar<T>::type* __restrict__ partial,
-                                                      unsigned* ticket,
-                                                      const typename SmallScalar<T>::type* __restrict__ prev,
-                                                      size_t fstride, int nprev, int R,
-                                                      typename SmallScalar<T>::type* __restrict__ Wout,
-                                                      int* status) {
+__device__ __forceinline__ void extract_body(const T* __restrict__ X, int64_t I, int L, int rows,
+                                             typename SmallScalar<T>::type* __restrict__ partial, unsigned* ticket,
+                                             const typename SmallScalar<T>::type* __restrict__ prev, size_t fstride,
+                                             int nprev, int R, typename SmallScalar<T>::type* __restrict__ Wout,
+                                             int* status, int bid, int nblk) {
     using S = typename SmallScalar<T>::type;
     using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    gram_partial<T, S>(X, I, L, rows, partial, smem_raw);
-    if (!last_cta(ticket)) return;
+    gram_partial<T, S>(X, I, L, rows, partial, smem_raw, bid);
+    if (!last_cta(ticket, nblk)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kXT / 32;
     const int Lp = L + (L & 1);
     const int np = (int)packed_size(L);
@@ -837,7 +836,7 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
     __shared__ T nrm2;
     __shared__ unsigned long long mx_bits;
 
-    reduce_cholesky<T, S>(partial, gridDim.x, L, I, G, Rf, dinv, reinterpret_cast<int*>(H), ticket, status);
+    reduce_cholesky<T, S>(partial, nblk, L, I, G, Rf, dinv, reinterpret_cast<int*>(H), ticket, status);
 
     // M = R2 prev[nprev-1] ... prev[0]: products of packed upper triangles, one
     // thread per output entry, alternating between H and G so the last lands in G
@@ -974,9 +973,15 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
         }
     }
     __syncthreads();
+    // (a total order: a NaN norm ranks below every number, so perm is a
+    // permutation whatever the data and every index taken from it stays in range)
     for (int c = tid; c < L; c += kXT) {
+        const T sc = sig[c] == sig[c] ? sig[c] : T(-1);
         int rank = 0;
-        for (int d = 0; d < L; ++d) rank += (sig[d] > sig[c]) || (sig[d] == sig[c] && d < c);
+        for (int d = 0; d < L; ++d) {
+            const T sd = sig[d] == sig[d] ? sig[d] : T(-1);
+            rank += (sd > sc) || (sd == sc && d < c);
+        }
         perm[rank] = c;
     }
     __syncthreads();
@@ -1065,11 +1070,11 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
 
 // U(:, r) = X W(:, r) in paired precision, one thread per entry of U.
 template <typename T>
-__global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ X, int64_t I, int L, int R,
-                                                    const typename SmallScalar<T>::type* __restrict__ W,
-                                                    T* __restrict__ U) {
+__device__ __forceinline__ void form_u_body(const T* __restrict__ X, int64_t I, int L, int R,
+                                            const typename SmallScalar<T>::type* __restrict__ W, T* __restrict__ U,
+                                            int bid, int nblk) {
     const int64_t n = I * R;
-    for (int64_t e = (int64_t)blockIdx.x * kT + threadIdx.x; e < n; e += (int64_t)gridDim.x * kT) {
+    for (int64_t e = (int64_t)bid * kT + threadIdx.x; e < n; e += (int64_t)nblk * kT) {
         const int r = (int)(e / I);
         const int64_t i = e - (int64_t)r * I;
         const auto* w = W + (int64_t)r * L;
@@ -1135,14 +1140,14 @@ __host__ __device__ inline FLayout flayout(int R, int elem, int64_t I) {
 // order and records in *ok whether U^T U is within 8 eps of I, in which case
 // the final pass keeps U and only applies the sign rule.
 template <typename T>
-__global__ void __launch_bounds__(kST) ugram_check_kernel(const T* __restrict__ U, int64_t I, int R, int rows,
-                                                          typename SmallScalar<T>::type* __restrict__ partial,
-                                                          unsigned* ticket, int* ok) {
+__device__ __forceinline__ void ugram_check_body(const T* __restrict__ U, int64_t I, int R, int rows,
+                                                 typename SmallScalar<T>::type* __restrict__ partial, unsigned* ticket,
+                                                 int* ok, int bid, int nblk) {
     using S = typename SmallScalar<T>::type;
     using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    gram_partial<T, S>(U, I, R, rows, partial, smem_raw);
-    if (!last_cta(ticket)) return;
+    gram_partial<T, S>(U, I, R, rows, partial, smem_raw, bid);
+    if (!last_cta(ticket, nblk)) return;
     __shared__ int bad;
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
@@ -1150,7 +1155,7 @@ __global__ void __launch_bounds__(kST) ugram_check_kernel(const T* __restrict__ 
     const double eps = sizeof(T) == 4 ? (double)FLT_EPSILON : DBL_EPSILON;
     for (int p = threadIdx.x; p < np; p += blockDim.x) {
         S acc = ld_cg(partial + p);
-        for (int b = 1; b < (int)gridDim.x; ++b) acc = acc + ld_cg(partial + (int64_t)b * np + p);
+        for (int b = 1; b < nblk; ++b) acc = acc + ld_cg(partial + (int64_t)b * np + p);
         int a = 0, rem = p;
         while (rem >= R - a) { rem -= R - a; ++a; }
         const double dev = fabs(F::to_double(acc) - (rem == 0 ? 1.0 : 0.0));
@@ -1164,8 +1169,8 @@ __global__ void __launch_bounds__(kST) ugram_check_kernel(const T* __restrict__ 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kST) finish_kernel(T* __restrict__ Ug, int64_t I, int R, int staged,
-                                                     const int* __restrict__ pre_ok) {
+__device__ __forceinline__ void finish_body(T* __restrict__ Ug, int64_t I, int R, int staged,
+                                            const int* __restrict__ pre_ok) {
     using S = typename SmallScalar<T>::type;
     using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1478,6 +1483,97 @@ __global__ void __launch_bounds__(kST) finish_kernel(T* __restrict__ Ug, int64_t
     }
 }
 
+// ---------------------------------------------------------------- kernels
+// One orthonormalisation per launch: the block programs above at blockIdx.x of gridDim.x.
+template <typename T>
+__global__ void __launch_bounds__(kST) gram_chol_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
+                                                       typename SmallScalar<T>::type* __restrict__ partial,
+                                                       unsigned* ticket, typename SmallScalar<T>::type* __restrict__ R,
+                                                       typename SmallScalar<T>::type* __restrict__ Rinv, int* status) {
+    gram_chol_body<T>(X, I, L, rows, partial, ticket, R, Rinv, status, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(kT) apply_rinv_kernel(const T* __restrict__ X, int64_t I, int L,
+                                                        const typename SmallScalar<T>::type* __restrict__ Rinv,
+                                                        T* __restrict__ Q) {
+    apply_rinv_body<T>(X, I, L, Rinv, Q, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
+                                                      typename SmallScalar<T>::type* __restrict__ partial,
+                                                      unsigned* ticket,
+                                                      const typename SmallScalar<T>::type* __restrict__ prev,
+                                                      size_t fstride, int nprev, int R,
+                                                      typename SmallScalar<T>::type* __restrict__ Wout,
+                                                      int* status) {
+    extract_body<T>(X, I, L, rows, partial, ticket, prev, fstride, nprev, R, Wout, status, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ X, int64_t I, int L, int R,
+                                                    const typename SmallScalar<T>::type* __restrict__ W,
+                                                    T* __restrict__ U) {
+    form_u_body<T>(X, I, L, R, W, U, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(kST) ugram_check_kernel(const T* __restrict__ U, int64_t I, int R, int rows,
+                                                          typename SmallScalar<T>::type* __restrict__ partial,
+                                                          unsigned* ticket, int* ok) {
+    ugram_check_body<T>(U, I, R, rows, partial, ticket, ok, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(kST) finish_kernel(T* __restrict__ Ug, int64_t I, int R, int staged,
+                                                     const int* __restrict__ pre_ok) {
+    finish_body<T>(Ug, I, R, staged, pre_ok);
+}
+
+// Grouped: the orthonormalisations of a batch's requests side by side, job
+// blockIdx.y with its own parameters; CTAs beyond a job's count return at once
+// (the Gram programs count their job's CTAs, not the grid's).
+__global__ void orth_reset_group_kernel(const OrthJob* __restrict__ jobs) {
+    const OrthJob j = jobs[blockIdx.x];
+    if (threadIdx.x < 32) j.flag[threadIdx.x] = 0;     // the flag and ticket words (128 bytes)
+}
+template <typename T>
+__global__ void __launch_bounds__(kST) gram_chol_group_kernel(const OrthJob* __restrict__ jobs) {
+    using S = typename SmallScalar<T>::type;
+    const OrthJob j = jobs[blockIdx.y];
+    if ((int)blockIdx.x >= j.nblk) return;
+    gram_chol_body<T>((const T*)j.X, j.I, j.L, j.rows, (S*)j.partial, j.ticket, (S*)(j.factor + j.fofs), (S*)j.W,
+                      j.status, blockIdx.x, j.nblk);
+}
+template <typename T>
+__global__ void __launch_bounds__(kT) apply_rinv_group_kernel(const OrthJob* __restrict__ jobs) {
+    using S = typename SmallScalar<T>::type;
+    const OrthJob j = jobs[blockIdx.y];
+    apply_rinv_body<T>((const T*)j.X, j.I, j.L, (const S*)j.W, (T*)j.Q, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(kXT, 1) extract_group_kernel(const OrthJob* __restrict__ jobs) {
+    using S = typename SmallScalar<T>::type;
+    const OrthJob j = jobs[blockIdx.y];
+    if ((int)blockIdx.x >= j.nblk) return;
+    extract_body<T>((const T*)j.Q, j.I, j.L, j.rows, (S*)j.partial, j.ticket, (const S*)j.factor,
+                    (size_t)j.L * j.L, j.nprev + 1, j.R, (S*)j.W, j.status, blockIdx.x, j.nblk);
+}
+template <typename T>
+__global__ void __launch_bounds__(kT) form_u_group_kernel(const OrthJob* __restrict__ jobs) {
+    using S = typename SmallScalar<T>::type;
+    const OrthJob j = jobs[blockIdx.y];
+    form_u_body<T>((const T*)j.Q, j.I, j.L, j.R, (const S*)j.W, (T*)j.U, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(kST) ugram_check_group_kernel(const OrthJob* __restrict__ jobs) {
+    using S = typename SmallScalar<T>::type;
+    const OrthJob j = jobs[blockIdx.y];
+    if ((int)blockIdx.x >= j.nblk) return;
+    ugram_check_body<T>((const T*)j.U, j.I, j.R, j.rows, (S*)j.partial, j.ticket, j.flag + 8, blockIdx.x, j.nblk);
+}
+template <typename T>
+__global__ void __launch_bounds__(kST) finish_group_kernel(const OrthJob* __restrict__ jobs) {
+    const OrthJob j = jobs[blockIdx.y];
+    finish_body<T>((T*)j.U, j.I, j.R, j.staged, j.flag + 8);
+}
+
 }  // namespace
 
 OrthPlan orth_plan(int64_t I, int L, int num_sms) {
@@ -1612,6 +1708,109 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
     return cudaGetLastError();
 }
 
+OrthJob orth_job(const OrthPlan& p, void* scratch) {
+    OrthJob j{};
+    const OrthScratch sc = carve(p, scratch);
+    j.I = p.I;
+    j.L = p.L;
+    j.rows = gram_rows(p);
+    j.nblk = p.gram_blocks;
+    j.partial = sc.partial;
+    j.flag = sc.flag;
+    j.ticket = sc.ticket;
+    j.W = sc.W;
+    return j;
+}
+
+namespace {
+int64_t elementwise_blocks(int64_t n) {
+    int64_t b = (n + kT - 1) / kT;
+    return b > 4 * 1024 ? 4 * 1024 : (b < 1 ? 1 : b);
+}
+OrthPlan plan_of(const OrthJob& j) {
+    OrthPlan p{};
+    p.I = j.I;
+    p.L = j.L;
+    p.gram_blocks = j.nblk;
+    return p;
+}
+// The CholeskyQR pass of every job (the factor at factor + fofs, R^-1 into W, Q = X R^-1).
+template <typename T>
+cudaError_t cholqr_group(const OrthJob* d, const std::vector<OrthJob>& h, cudaStream_t s) {
+    size_t gsm = 0, asm_ = 0;
+    int gx = 1;
+    int64_t ax = 1;
+    for (const OrthJob& j : h) {
+        const OrthPlan p = plan_of(j);
+        gsm = std::max(gsm, gram_chol_smem(p, sizeof(T)));
+        asm_ = std::max(asm_, 8 * packed_size(j.L));
+        gx = std::max(gx, j.nblk);
+        ax = std::max(ax, elementwise_blocks(j.I * j.L));
+    }
+    if (gsm > kSmemCap || asm_ > kSmemCap) return cudaErrorInvalidValue;
+    const unsigned ny = (unsigned)h.size();
+    cudaFuncSetAttribute(gram_chol_group_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    cudaFuncSetAttribute(apply_rinv_group_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    orth_reset_group_kernel<<<ny, 32, 0, s>>>(d);
+    note_launch();
+    gram_chol_group_kernel<T><<<dim3((unsigned)gx, ny), kST, gsm, s>>>(d);
+    note_launch();
+    apply_rinv_group_kernel<T><<<dim3((unsigned)ax, ny), kT, asm_, s>>>(d);
+    note_launch();
+    return cudaGetLastError();
+}
+}  // namespace
+
+template <typename T>
+cudaError_t launch_cholqr_group(const OrthJob* d_jobs, const std::vector<OrthJob>& h_jobs, cudaStream_t s) {
+    if (h_jobs.empty()) return cudaSuccess;
+    return cholqr_group<T>(d_jobs, h_jobs, s);
+}
+
+template <typename T>
+cudaError_t launch_extract_group(const OrthJob* d_jobs, const std::vector<OrthJob>& h_jobs, cudaStream_t s) {
+    if (h_jobs.empty()) return cudaSuccess;
+    for (const OrthJob& j : h_jobs)
+        if (!orth_supported(plan_of(j), j.R, sizeof(T)) || j.fofs != (int64_t)j.nprev * j.L * j.L)
+            return cudaErrorInvalidValue;
+    cudaError_t e = cholqr_group<T>(d_jobs, h_jobs, s);
+    if (e != cudaSuccess) return e;
+    size_t xsm = 0, usm = 0, fsm = 0;
+    int gx = 1;
+    int64_t ux = 1;
+    for (const OrthJob& j : h_jobs) {
+        const OrthPlan p = plan_of(j);
+        xsm = std::max(xsm, extract_smem(p, j.R, sizeof(T)));
+        usm = std::max(usm, (size_t)sizeof(T) * (size_t)std::min(j.rows, kGramChunk) * j.R);
+        const size_t staged = finish_staged_smem(j.R, sizeof(T), j.I);
+        if ((staged != 0) != (j.staged != 0)) return cudaErrorInvalidValue;
+        fsm = std::max(fsm, staged ? staged : finish_smem(j.R, sizeof(T), j.I));
+        gx = std::max(gx, j.nblk);
+        ux = std::max(ux, elementwise_blocks(j.I * j.R));
+    }
+    const unsigned ny = (unsigned)h_jobs.size();
+    cudaFuncSetAttribute(extract_group_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    cudaFuncSetAttribute(ugram_check_group_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    cudaFuncSetAttribute(finish_group_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    orth_reset_group_kernel<<<ny, 32, 0, s>>>(d_jobs);
+    note_launch();
+    extract_group_kernel<T><<<dim3((unsigned)gx, ny), kXT, xsm, s>>>(d_jobs);
+    note_launch();
+    form_u_group_kernel<T><<<dim3((unsigned)ux, ny), kT, 0, s>>>(d_jobs);
+    note_launch();
+    ugram_check_group_kernel<T><<<dim3((unsigned)gx, ny), kST, usm, s>>>(d_jobs);
+    note_launch();
+    finish_group_kernel<T><<<dim3(1, ny), kST, fsm, s>>>(d_jobs);
+    note_launch();
+    return cudaGetLastError();
+}
+
+bool orth_group_staged(const OrthJob& j, int elem_size) { return finish_staged_smem(j.R, elem_size, j.I) != 0; }
+
+template cudaError_t launch_cholqr_group<float>(const OrthJob*, const std::vector<OrthJob>&, cudaStream_t);
+template cudaError_t launch_cholqr_group<double>(const OrthJob*, const std::vector<OrthJob>&, cudaStream_t);
+template cudaError_t launch_extract_group<float>(const OrthJob*, const std::vector<OrthJob>&, cudaStream_t);
+template cudaError_t launch_extract_group<double>(const OrthJob*, const std::vector<OrthJob>&, cudaStream_t);
 template cudaError_t launch_cholqr<float>(const float*, float*, const OrthPlan&, double*, void*, int*, cudaStream_t);
 template cudaError_t launch_cholqr<double>(const double*, double*, const OrthPlan&, double*, void*, int*,
                                            cudaStream_t);

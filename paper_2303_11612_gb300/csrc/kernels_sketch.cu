@@ -13,6 +13,7 @@
 #include <utility>
 #include <vector>
 
+#include "blocks.cuh"
 #include "internal.h"
 
 namespace tk {
@@ -24,46 +25,10 @@ constexpr int kT = kThreads;
 template <typename T>
 __global__ void __launch_bounds__(kT) gaussian_kernel(T* __restrict__ out, int64_t rows, int64_t cols,
                                                       uint64_t seed, uint32_t stream_id) {
-    const int64_t n = rows * cols;
-    for (int64_t k = blockIdx.x * (int64_t)kT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kT) {
-        const int64_t l = k / rows, i = k - l * rows;      // column-major position
-        out[k] = gaussian_at<T>(seed, stream_id, (uint64_t)(i * cols + l));
-    }
+    blk::gaussian_block<T>(out, rows, cols, seed, stream_id, blockIdx.x, gridDim.x);
 }
 
-// Loads the JB x I tile of fibers j0 .. j0+JB-1 into Ts (row stride ldt).
-template <typename T, int JB>
-__device__ __forceinline__ void load_tile(const T* __restrict__ A, const ModeView& v, int64_t j0,
-                                          int64_t J, T* Ts, int ldt, int64_t* bases) {
-    const int I = (int)v.i;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (v.lf == 1) {
-        // fibers are contiguous runs of I elements
-        for (int jj = warp; jj < JB; jj += kT / 32) {
-            const int64_t j = j0 + jj;
-            T* dst = Ts + jj * ldt;
-            if (j < J) {
-                const T* src = A + j * (int64_t)I;
-                for (int i = lane; i < I; i += 32) dst[i] = __ldg(src + i);
-            } else {
-                for (int i = lane; i < I; i += 32) dst[i] = T(0);
-            }
-        }
-    } else {
-        if (tid < JB) {
-            const int64_t j = j0 + tid;
-            bases[tid] = j < J ? v.base(j) : -1;
-        }
-        __syncthreads();
-        const int64_t lf = v.lf;
-        for (int e = tid; e < JB * I; e += kT) {
-            const int jj = e % JB, i = e / JB;
-            const int64_t b = bases[jj];
-            Ts[jj * ldt + i] = b >= 0 ? __ldg(A + b + (int64_t)i * lf) : T(0);
-        }
-    }
-}
-
+// Block (l-group blockIdx.x, tiles blockIdx.y + k gridDim.y) of the power step;
 // RANGE == false: W = T X (phase 1). RANGE == true: W = Omega rows (Philox).
 template <typename T, int JB, int LG, int KR, bool RANGE>
 __global__ void __launch_bounds__(kT) power_kernel(const T* __restrict__ A, ModeView v,
@@ -71,140 +36,21 @@ __global__ void __launch_bounds__(kT) power_kernel(const T* __restrict__ A, Mode
                                                    T* __restrict__ partial, int64_t tiles,
                                                    uint64_t seed, uint32_t stream_id) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int KS = kT / JB;            // phase-1 split of the I dimension
-    const int I = (int)v.i;
-    const int64_t J = v.fibers();
-    const int l0 = blockIdx.x * LG;
-    const int lg = min(LG, L - l0);
-    const int ldt = I | 1;                 // odd row stride: conflict-free column reads
-    T* Xs = reinterpret_cast<T*>(smem_raw);               // [I][LG]
-    T* Ts = Xs + (RANGE ? 0 : I * LG);                     // [JB][ldt]
-    T* Wp = Ts + JB * ldt;                                 // [KS][JB][LG]
-    T* Ws = Wp + KS * JB * LG;                             // [JB][LG]
-    int64_t* bases = reinterpret_cast<int64_t*>(Ws + JB * LG);
-    const int tid = threadIdx.x;
-
-    if (!RANGE) {
-        for (int e = tid; e < I * LG; e += kT) {
-            const int i = e / LG, l = e % LG;
-            Xs[e] = l < lg ? X[(int64_t)(l0 + l) * I + i] : T(0);
-        }
-    }
-    T acc2[KR][LG];
-#pragma unroll
-    for (int k = 0; k < KR; ++k)
-#pragma unroll
-        for (int l = 0; l < LG; ++l) acc2[k][l] = T(0);
-
-    for (int64_t tile = blockIdx.y; tile < tiles; tile += gridDim.y) {
-        const int64_t j0 = tile * JB;
-        __syncthreads();                    // previous tile fully consumed
-        load_tile<T, JB>(A, v, j0, J, Ts, ldt, bases);
-        if (RANGE) {
-            for (int e = tid; e < JB * LG; e += kT) {
-                const int jj = e / LG, l = e % LG;
-                const int64_t j = j0 + jj;
-                Ws[e] = (j < J && l < lg)
-                            ? gaussian_at<T>(seed, stream_id, (uint64_t)(j * L + l0 + l))
-                            : T(0);
-            }
-            __syncthreads();
-        } else {
-            __syncthreads();
-            // phase 1: W(jj, :) partial over this thread's slice of I
-            const int jj = tid % JB, ks = tid / JB;
-            const int ib = (int)((int64_t)I * ks / KS), ie = (int)((int64_t)I * (ks + 1) / KS);
-            T acc[LG];
-#pragma unroll
-            for (int l = 0; l < LG; ++l) acc[l] = T(0);
-            const T* trow = Ts + jj * ldt;
-            for (int i = ib; i < ie; ++i) {
-                const T t = trow[i];
-                const T* xr = Xs + i * LG;
-#pragma unroll
-                for (int l = 0; l < LG; ++l) acc[l] = fma(t, xr[l], acc[l]);
-            }
-            T* wp = Wp + (ks * JB + jj) * LG;
-#pragma unroll
-            for (int l = 0; l < LG; ++l) wp[l] = acc[l];
-            __syncthreads();
-            for (int e = tid; e < JB * LG; e += kT) {
-                T s = T(0);
-#pragma unroll 4
-                for (int k = 0; k < KS; ++k) s += Wp[k * JB * LG + e];
-                Ws[e] = s;
-            }
-            __syncthreads();
-        }
-        // phase 2: X_acc(i, :) += sum_jj T(jj, i) W(jj, :)
-#pragma unroll
-        for (int k = 0; k < KR; ++k) {
-            const int i = tid + k * kT;
-            if (i < I) {
-                for (int jj = 0; jj < JB; ++jj) {
-                    const T t = Ts[jj * ldt + i];
-                    const T* w = Ws + jj * LG;
-#pragma unroll
-                    for (int l = 0; l < LG; ++l) acc2[k][l] = fma(t, w[l], acc2[k][l]);
-                }
-            }
-        }
-    }
-    T* out = partial + (int64_t)blockIdx.y * ((int64_t)I * L);
-#pragma unroll
-    for (int k = 0; k < KR; ++k) {
-        const int i = tid + k * kT;
-        if (i < I) {
-#pragma unroll
-            for (int l = 0; l < LG; ++l)
-                if (l < lg) out[(int64_t)(l0 + l) * I + i] = acc2[k][l];
-        }
-    }
+    blk::power_block<T, JB, LG, KR, RANGE, true>(A, v, X, L, partial, tiles, seed, stream_id, blockIdx.x, blockIdx.y,
+                                                 gridDim.y, smem_raw);
 }
 
-// out[e] = sum over parts of partial[p * count + e]: 32 consecutive outputs per
-// block (coalesced), the parts split over the block's warps (warp w sums parts
-// w, w + warps, ... in increasing order), the warps' sums combined in warp
-// order, so the result does not depend on scheduling.
+// out[e] = sum over parts of partial[p * count + e] in a fixed order (the block
+// program's), so the result does not depend on scheduling.
 template <typename T>
 __global__ void __launch_bounds__(kT) reduce_partials_kernel(const T* __restrict__ partial, int parts,
                                                              int64_t count, T* __restrict__ out) {
-    constexpr int kG = kT / 32;
-    __shared__ T sh[kG][32];
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < count; e0 += (int64_t)gridDim.x * 32) {
-        const int64_t e = e0 + lane;
-        T s = T(0);
-        if (e < count) {
-            int p = g;
-            for (; p + 3 * kG < parts; p += 4 * kG) {
-                const T x0 = partial[(int64_t)p * count + e], x1 = partial[(int64_t)(p + kG) * count + e];
-                const T x2 = partial[(int64_t)(p + 2 * kG) * count + e];
-                const T x3 = partial[(int64_t)(p + 3 * kG) * count + e];
-                s += x0;
-                s += x1;
-                s += x2;
-                s += x3;
-            }
-            for (; p < parts; p += kG) s += partial[(int64_t)p * count + e];
-        }
-        sh[g][lane] = s;
-        __syncthreads();
-        if (g == 0 && e < count) {
-            T t = sh[0][lane];
-#pragma unroll
-            for (int q = 1; q < kG; ++q) t += sh[q][lane];
-            out[e] = t;
-        }
-        __syncthreads();
-    }
+    blk::reduce_block<T, true>(partial, parts, count, out, blockIdx.x, gridDim.x);
 }
 
 template <typename T, int JB, int LG, int KR, bool RANGE>
 size_t power_smem(int I) {
-    const int ldt = I | 1;
-    return sizeof(T) * ((RANGE ? 0 : (size_t)I * LG) + (size_t)JB * ldt + (size_t)(kT / JB) * JB * LG +
-                        (size_t)JB * LG) + sizeof(int64_t) * JB + 16;
+    return blk::power_block_smem<T, JB, LG, RANGE>(I);
 }
 
 }  // namespace

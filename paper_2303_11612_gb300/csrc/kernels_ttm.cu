@@ -9,6 +9,7 @@
 // is read once per output block (one block whenever K_out <= 64).
 #include <algorithm>
 
+#include "blocks.cuh"
 #include "internal.h"
 #include "tc.cuh"
 #include "tma.cuh"
@@ -17,145 +18,13 @@ namespace tk {
 namespace {
 
 constexpr int kT = kThreads;
-constexpr int KC = 32, KP = KC + 4;   // rows padded to 36 elements: 16-byte aligned, conflict-free
-
-// four consecutive T values from 16-byte aligned shared memory
-__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
-    const float4 x = *reinterpret_cast<const float4*>(p);
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
-    const double2 x = *reinterpret_cast<const double2*>(p), y = *reinterpret_cast<const double2*>(p + 2);
-    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
-}
-
-// Thread (lane64 = tid % 64, og = tid / 64) owns fibers lane64 + 64 f (f < NF)
-// and outputs og * OPT .. og * OPT + OPT - 1. Both shared tiles keep the input
-// index contiguous, so stores are unit-stride and the inner loop reads four
-// input indices per 128-bit load; the M rows are the same across a warp
-// (broadcast) and each serves 4 NF multiply-adds. The next chunk's global
-// loads are issued into registers before the current chunk is multiplied.
+// Block (blockIdx.x, blockIdx.y) of the register-staged mode-n product: JB =
+// 64 NF fibers by OB = 4 OPT outputs (the block program's layout and order).
 template <typename T, int OPT, int NF>
 __global__ void __launch_bounds__(kT) ttm_kernel(const T* __restrict__ A, ModeView v, const T* __restrict__ Mp,
                                                  int64_t K_out, int64_t ld_i, int64_t ld_k, T* __restrict__ out) {
-    constexpr int JB = 64 * NF, OB = 4 * OPT;
-    constexpr int TPT = JB * KC / kT;                    // tile elements loaded per thread and chunk
-    constexpr int MPT = (OB * KC + kT - 1) / kT;         // M elements loaded per thread and chunk
-    constexpr size_t kTileBytes = sizeof(T) * (JB * KP + OB * KP);
-    constexpr size_t kOutBytes = sizeof(T) * JB * (OB + 1);
-    __shared__ __align__(16) unsigned char smem[kTileBytes > kOutBytes ? kTileBytes : kOutBytes];
-    auto Ts = reinterpret_cast<T(*)[KP]>(smem);                       // [JB][KP]
-    auto Ms = reinterpret_cast<T(*)[KP]>(smem + sizeof(T) * JB * KP);  // [OB][KP]
-    auto Os = reinterpret_cast<T(*)[OB + 1]>(smem);                   // [JB][OB + 1], after the products
-    __shared__ int64_t bases[JB];
-    const int tid = threadIdx.x;
-    const int64_t J = v.fibers();
-    const int64_t j0 = (int64_t)blockIdx.x * JB;
-    const int64_t o0 = (int64_t)blockIdx.y * OB;
-    const int I = (int)v.i;
-    const bool contig = v.lf == 1;
-    for (int r = tid; r < JB; r += kT) {
-        const int64_t j = j0 + r;
-        bases[r] = j < J ? v.base(j) : -1;
-    }
-    __syncthreads();
-    T tr[TPT], mr[MPT];
-    // element u of this thread's share of a chunk: (fiber, k) for the tile, (output, k) for M
-    auto load_chunk = [&](int i0) {
-#pragma unroll
-        for (int u = 0; u < TPT; ++u) {
-            const int e = tid + u * kT;
-            int r, c;
-            if (contig) { r = e / KC; c = e % KC; }      // a warp reads KC consecutive elements of a fiber
-            else { r = e % JB; c = e / JB; }             // a warp reads one element of 32 neighbouring fibers
-            const int64_t b = bases[r];
-            const int i = i0 + c;
-            tr[u] = (b >= 0 && i < I) ? __ldg(A + b + (int64_t)i * v.lf) : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < MPT; ++u) {
-            const int e = tid + u * kT;
-            int kk, oo;
-            if (ld_i == 1) { kk = e % KC; oo = e / KC; } // unit stride along the input index
-            else { oo = e % OB; kk = e / OB; }
-            const int i = i0 + kk;
-            const int64_t o = o0 + oo;
-            mr[u] = (e < OB * KC && i < I && o < K_out) ? __ldg(Mp + (int64_t)i * ld_i + o * ld_k) : T(0);
-        }
-    };
-    auto store_chunk = [&]() {
-#pragma unroll
-        for (int u = 0; u < TPT; ++u) {
-            const int e = tid + u * kT;
-            int r, c;
-            if (contig) { r = e / KC; c = e % KC; }
-            else { r = e % JB; c = e / JB; }
-            Ts[r][c] = tr[u];
-        }
-#pragma unroll
-        for (int u = 0; u < MPT; ++u) {
-            const int e = tid + u * kT;
-            int kk, oo;
-            if (ld_i == 1) { kk = e % KC; oo = e / KC; }
-            else { oo = e % OB; kk = e / OB; }
-            if (e < OB * KC) Ms[oo][kk] = mr[u];
-        }
-    };
-    const int jl = tid % 64, og = tid / 64;
-    T acc[NF][OPT];
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int u = 0; u < OPT; ++u) acc[f][u] = T(0);
-    load_chunk(0);
-    for (int i0 = 0; i0 < I; i0 += KC) {
-        store_chunk();
-        __syncthreads();
-        if (i0 + KC < I) load_chunk(i0 + KC);            // in flight during the products below
-#pragma unroll 2
-        for (int kk = 0; kk < KC; kk += 4) {
-            T t4[NF][4];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) ld4(&Ts[jl + 64 * f][kk], t4[f]);
-#pragma unroll
-            for (int u = 0; u < OPT; ++u) {
-                T m4[4];
-                ld4(&Ms[og * OPT + u][kk], m4);
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    acc[f][u] = fma(t4[f][0], m4[0], acc[f][u]);
-                    acc[f][u] = fma(t4[f][1], m4[1], acc[f][u]);
-                    acc[f][u] = fma(t4[f][2], m4[2], acc[f][u]);
-                    acc[f][u] = fma(t4[f][3], m4[3], acc[f][u]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // (the loop ends with a barrier, so every thread is done reading Ts and Ms)
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int u = 0; u < OPT; ++u) Os[jl + 64 * f][og * OPT + u] = acc[f][u];
-    __syncthreads();
-    if (contig) {
-        // out[o + j K_out]: consecutive threads -> consecutive o
-        for (int e = tid; e < JB * OB; e += kT) {
-            const int r = e / OB, oo = e % OB;
-            const int64_t j = j0 + r, o = o0 + oo;
-            if (j < J && o < K_out) out[j * K_out + o] = Os[r][oo];
-        }
-    } else {
-        // out[l + o Lf + t Lf K_out]: consecutive threads -> consecutive fibers
-        for (int e = tid; e < JB * OB; e += kT) {
-            const int r = e % JB, oo = e / JB;
-            const int64_t j = j0 + r, o = o0 + oo;
-            if (j < J && o < K_out) {
-                const int64_t t = j / v.lf, l = j - t * v.lf;
-                out[l + o * v.lf + t * v.lf * K_out] = Os[r][oo];
-            }
-        }
-    }
+    __shared__ __align__(16) unsigned char smem[blk::ttm_block_smem<T, OPT, NF>()];
+    blk::ttm_block<T, OPT, NF, true>(A, v, Mp, K_out, ld_i, ld_k, out, blockIdx.x, blockIdx.y, smem);
 }
 
 // TMA-fed FP32 mode-n product. Each CTA takes JB = 128 consecutive fibers
