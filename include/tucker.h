@@ -429,9 +429,13 @@ tucker_status tucker_power_step_noalloc(const void* A, tucker_dtype dt, const in
  * what the budget has left; each admitted request runs as a TUCKER_FLAG_ASYNC
  * decomposition on its own stream, so the work of admitted requests overlaps
  * on the device, and a request that arrives while others run is admitted as
- * soon as a stream and memory free up. Results do not depend on what else runs:
- * every kernel reduces in a fixed order. How far the streams overlap depends on
- * CUDA's hardware work queues: CUDA_DEVICE_MAX_CONNECTIONS (8 when unset, read
+ * soon as a stream and memory free up. With ticks (tucker_server_opts.tick_max),
+ * consecutive small requests at the head of the queue are admitted together as
+ * one work-list batch on one stream: each still has its own status and
+ * completion, and its results are bitwise those of the request run alone.
+ * Results do not depend on what else runs: every kernel reduces in a fixed
+ * order. How far the streams overlap depends on CUDA's hardware work queues:
+ * CUDA_DEVICE_MAX_CONNECTIONS (8 when unset, read
  * when the process creates its CUDA context) should be at least max_inflight,
  * or requests sharing a queue wait on one another. */
 typedef struct tucker_server tucker_server;
@@ -442,6 +446,12 @@ typedef struct {
     size_t budget_bytes;    /* device memory admitted requests may hold together */
     int32_t form;           /* tucker_form of every request */
     int32_t prec;           /* tucker_sketch_prec of every request */
+    int32_t tick_max;       /* 0 or 1: every request on its own stream; 2 .. 256: up to this many
+                               consecutive requests at the head of the queue that the work list
+                               takes (see the batches section) and whose tensors hold at most
+                               tick_elems elements run together as one work-list batch (a tick)
+                               on one stream; needs the paper form with TUCKER_SK_FP32 */
+    int64_t tick_elems;     /* the size limit of a tick's requests, elements (> 0 with ticks) */
 } tucker_server_opts;
 
 typedef struct {
@@ -466,6 +476,8 @@ typedef struct {
     double throughput;      /* completed / (last completion - first submission), per second */
     size_t peak_bytes;      /* largest device memory held by admitted requests together */
     int32_t peak_inflight;  /* largest number of requests on the device together */
+    uint64_t ticks;         /* work-list ticks launched */
+    uint64_t tick_requests; /* requests admitted in them */
 } tucker_server_stats;
 
 /* Creates a server on the calling thread's current device. */

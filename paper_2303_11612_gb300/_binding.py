@@ -48,7 +48,7 @@ class Opts(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("max_inflight", C.c_int32), ("budget_bytes", C.c_size_t),
-                ("form", C.c_int32), ("prec", C.c_int32)]
+                ("form", C.c_int32), ("prec", C.c_int32), ("tick_max", C.c_int32), ("tick_elems", C.c_int64)]
 
 
 class Request(C.Structure):
@@ -61,7 +61,8 @@ class Request(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
-                ("throughput", C.c_double), ("peak_bytes", C.c_size_t), ("peak_inflight", C.c_int32)]
+                ("throughput", C.c_double), ("peak_bytes", C.c_size_t), ("peak_inflight", C.c_int32),
+                ("ticks", C.c_uint64), ("tick_requests", C.c_uint64)]
 
 
 _VP, _I64, _I32, _U64, _U32, _INT, _DBL = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64, C.c_uint32, C.c_int, C.c_double
@@ -662,10 +663,15 @@ class Server:
     The binding keeps every tensor of a request alive until ``wait`` has seen it
     complete. Requests overlap only as far as CUDA's hardware work queues allow:
     set ``CUDA_DEVICE_MAX_CONNECTIONS`` (8 by default) to at least
-    ``max_inflight`` before the process first uses the GPU."""
+    ``max_inflight`` before the process first uses the GPU. ``tick_max`` > 1
+    (paper form, FP32 arithmetic) admits up to that many consecutive requests
+    of at most ``tick_elems`` tensor elements that the work list takes as one
+    work-list batch on one stream."""
 
-    def __init__(self, budget_bytes: int, max_inflight: int = 8, form="paper", prec="fp32"):
-        o = ServerOpts(C.sizeof(ServerOpts), int(max_inflight), int(budget_bytes), FORM[form], PREC[prec])
+    def __init__(self, budget_bytes: int, max_inflight: int = 8, form="paper", prec="fp32", tick_max: int = 0,
+                 tick_elems: int = 1 << 22):
+        o = ServerOpts(C.sizeof(ServerOpts), int(max_inflight), int(budget_bytes), FORM[form], PREC[prec],
+                       int(tick_max), int(tick_elems))
         h = C.c_void_p()
         _check("tucker_server_create", lib().tucker_server_create(C.byref(o), C.byref(h)))
         self._h = h

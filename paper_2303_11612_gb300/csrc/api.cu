@@ -849,7 +849,7 @@ tucker_status status_from_cuda(cudaError_t e) { return from_cuda(e); }
 // asynchronous call), so its results are those of the request alone (FP32
 // power-step tiles as planned, without autotuning).
 tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts& opts, char* ws,
-                            const std::vector<size_t>& offsets, WorklistPlan& wp) {
+                            const std::vector<size_t>& offsets, WorklistPlan& wp, int max_lanes) {
     wp = WorklistPlan();
     Opts o;
     tucker_status rs = read_opts(&opts, o);
@@ -898,7 +898,7 @@ tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts
         cap_G[k] = g;
     }
     // four requests or more per lane, at most four lanes
-    wp.lanes = std::max(1, std::min(4, n / 4));
+    wp.lanes = std::max(1, std::min(std::min(4, max_lanes), n / 4));
     std::vector<WTask>& tasks = wp.tasks;
     std::vector<WItem>& items = wp.items;
     auto add = [&](WTask t, int gx, int gy) -> int {

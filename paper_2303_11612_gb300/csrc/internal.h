@@ -279,7 +279,7 @@ struct WorklistPlan {
 // in the paper form with the exact FMA arithmetic, no sampling, one element type,
 // every extent <= 256 and every rank <= 32.
 tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts& opts, char* ws,
-                            const std::vector<size_t>& offsets, WorklistPlan& wp);
+                            const std::vector<size_t>& offsets, WorklistPlan& wp, int max_lanes = 4);
 // Fills each step's grid (queries the device: call before stream capture).
 void worklist_prepare(WorklistPlan& wp);
 // The host image of the descriptors (wp.desc_bytes bytes at host).
