@@ -389,11 +389,7 @@ tucker_status tucker_gram(const void* A, tucker_dtype dt, const int64_t* dims, i
  * its status word exactly as the kernels do when a wait runs out, frees its
  * tensor memory and returns; nothing is in flight, so nothing is drained.
  * Returns TUCKER_ERR_TIMEOUT when that path works (the stream and the context
- * stay usable), TUCKER_ERR_INVALID_ARG for iters out of range. With
- * TUCKER_FLAG_WORKLIST in opts->flags it checks the work-list kernel's
- * dependency wait instead: one CTA runs a two-item list whose second item
- * depends on an item that is never listed; its wait gives up after `iters`
- * polls, records the timeout and the launch drains. */
+ * stay usable), TUCKER_ERR_INVALID_ARG for iters out of range. */
 tucker_status tucker_check_wait_timeout(int32_t iters, const tucker_opts* opts);
 
 /* ---------------------------------------------------------------- allocation-free variant
@@ -429,12 +425,8 @@ tucker_status tucker_power_step_noalloc(const void* A, tucker_dtype dt, const in
  * what the budget has left; each admitted request runs as a TUCKER_FLAG_ASYNC
  * decomposition on its own stream, so the work of admitted requests overlaps
  * on the device, and a request that arrives while others run is admitted as
- * soon as a stream and memory free up. With ticks (tucker_server_opts.tick_max),
- * consecutive small requests at the head of the queue are admitted together as
- * one work-list batch on one stream: each still has its own status and
- * completion, and its results are bitwise those of the request run alone.
- * Results do not depend on what else runs: every kernel reduces in a fixed
- * order. How far the streams overlap depends on CUDA's hardware work queues:
+ * soon as a stream and memory free up. Results do not depend on what else
+ * runs: every kernel reduces in a fixed order. How far the streams overlap depends on CUDA's hardware work queues:
  * CUDA_DEVICE_MAX_CONNECTIONS (8 when unset, read
  * when the process creates its CUDA context) should be at least max_inflight,
  * or requests sharing a queue wait on one another. */
@@ -446,11 +438,11 @@ typedef struct {
     size_t budget_bytes;    /* device memory admitted requests may hold together */
     int32_t form;           /* tucker_form of every request */
     int32_t prec;           /* tucker_sketch_prec of every request */
-    int32_t tick_max;       /* 0 or 1: every request on its own stream; 2 .. 256: up to this many
-                               consecutive requests at the head of the queue that the work list
-                               takes (see the batches section) and whose tensors hold at most
-                               tick_elems elements run together as one work-list batch (a tick)
-                               on one stream; needs the paper form with TUCKER_SK_FP32 */
+    int32_t tick_max;       /* 0 or 1: every request on its own stream. 2 .. 256 (ticks: up to this
+                               many consecutive requests at the head of the queue that the work
+                               list takes, each of at most tick_elems elements, as one work-list
+                               batch on one stream) returns TUCKER_ERR_UNSUPPORTED: the work-list
+                               path is not run (see the batches section) */
     int64_t tick_elems;     /* the size limit of a tick's requests, elements (> 0 with ticks) */
 } tucker_server_opts;
 
@@ -514,25 +506,32 @@ tucker_status tucker_server_destroy(tucker_server* srv);
  * 8 requests, set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) before the process
  * creates its CUDA context.
  *
- * With TUCKER_FLAG_WORKLIST in opts->flags the graph holds a work list instead
+ * TUCKER_FLAG_WORKLIST: tucker_batch_run returns TUCKER_ERR_UNSUPPORTED
+ * before any launch. The work-list path below is built and planned
+ * (tucker_batch_describe, tucker_batch_workspace_size) but not run: in some
+ * runs of a heterogeneous 32-request batch replayed back to back it raised an
+ * illegal-address fault whose cause has not been found, so it is kept off the
+ * device. As designed:
+ * with TUCKER_FLAG_WORKLIST in opts->flags the graph holds a work list instead
  * of the requests' own launch sequences (many small tensors in few launches):
  * every stage of every request - Gaussian test matrix, power-step partials and
  * their fixed-order sum, mode products, status reset - becomes items, the
- * blocks its own kernel would run, and one persistent kernel launch per step
- * (mode n and power step k, with ST-HOSVD's truncation by U_{n-1} ahead of the
- * power step it feeds; a last step for the cores) claims the items of all
- * requests in list order, each CTA waiting (bounded, about a second, then
- * TUCKER_ERR_TIMEOUT) until the stages an item depends on are done; the
- * CholeskyQR passes and extractions of all requests run as one grouped launch
- * per step. The requests are dealt to up to four lanes (streams of the graph),
- * so that one lane's orthonormalisations overlap another's streaming steps. Each request's results are bitwise those of the request run alone
- * (with autotuning off, which can pick other FP32 power-step tiles). The work
- * list takes Algorithms 1 and 2 in the paper form with TUCKER_SK_FP32, no
- * sampling (c = 0, alpha = 0), one element type across the batch, every extent
- * I_n <= 256 and every rank R_n <= 32; other batches return
- * TUCKER_ERR_UNSUPPORTED (from tucker_batch_workspace_size too, which with the
- * flag includes the work list's descriptor area). Not part of the paper's
- * method. */
+ * blocks its own kernel would run, and one persistent kernel launch per phase
+ * claims the items of all requests (per mode: the truncation by U_{n-1} of
+ * ST-HOSVD, the status reset and Omega_n; then per power step its partials and
+ * their sums; last the cores, T-HOSVD's chain a phase per position). The items
+ * of a phase are independent: what they read was written by an earlier phase,
+ * so no CTA waits for another. The CholeskyQR passes and extractions of all
+ * requests run as one grouped launch per step. The requests are dealt to up to
+ * eight lanes (streams of the graph), so that one lane's orthonormalisations
+ * overlap another's streaming phases. Each request's results are bitwise those
+ * of the request run alone (with autotuning off, which can pick other FP32
+ * power-step tiles). The work list takes Algorithms 1 and 2 in the paper form
+ * with TUCKER_SK_FP32, no sampling (c = 0, alpha = 0), one element type across
+ * the batch, every extent I_n <= 256 and every rank R_n <= 32; other batches
+ * return TUCKER_ERR_UNSUPPORTED (from tucker_batch_workspace_size too, which
+ * with the flag includes the work list's descriptor area). Not part of the
+ * paper's method. */
 
 /* Device workspace bytes (256-byte aligned per request) a batch needs; opts
  * may be NULL (paper form, FP32). */
@@ -551,14 +550,15 @@ tucker_status tucker_batch_run(int n, const tucker_request* reqs, const tucker_o
 /* Host only (no device work, no pointer checks): the work list a batch with
  * TUCKER_FLAG_WORKLIST in opts->flags would run, as text in buf (len bytes,
  * NUL-terminated; TUCKER_ERR_INVALID_ARG when it does not fit): one line per
- * step ("step s lane l: items=... init=... gaussian=... power=... sum=...
+ * phase ("step s lane l: items=... init=... gaussian=... power=... sum=...
  * product=... smem=... heavy=..." counting tasks per stage) or grouped
  * orthonormalisation ("cholqr lane l: jobs=..." / "extract lane l: jobs=..."),
  * lane by lane, then "lanes=... tasks=... items=... area=...". Requests are
  * dealt to lanes (request k to lane k mod lanes; one lane per four requests, at
- * most four), each a sequence on its own stream of the graph. The
- * planner checks that every dependency precedes its dependant in the same step
- * (TUCKER_ERR_INVALID_ARG otherwise); unsupported batches return
+ * most eight), each a sequence on its own stream of the graph. The
+ * planner checks that every task whose output another reads runs in an earlier
+ * phase of the same lane, and that every extent an item touches lies inside the
+ * buffer it targets (TUCKER_ERR_INVALID_ARG otherwise); unsupported batches return
  * TUCKER_ERR_UNSUPPORTED. */
 tucker_status tucker_batch_describe(int n, const tucker_request* reqs, const tucker_opts* opts, char* buf,
                                     size_t len);

@@ -403,12 +403,10 @@ def gram(A, dims, mode, stream=None, prec="bf16"):
     return G
 
 
-def check_wait_timeout(iters=1000, stream=None, worklist=False) -> int:
+def check_wait_timeout(iters=1000, stream=None) -> int:
     """tucker_check_wait_timeout: the status (an int, not raised) of a bounded
-    device wait that nothing completes (the tensor-core kernels' mbarrier wait,
-    or with ``worklist`` the work-list kernel's dependency wait);
-    TUCKER_ERR_TIMEOUT (5) when the path works."""
-    o = make_opts(stream=stream, flags=FLAG_WORKLIST if worklist else 0)
+    device wait that nothing completes; TUCKER_ERR_TIMEOUT (5) when the path works."""
+    o = make_opts(stream=stream)
     return int(lib().tucker_check_wait_timeout(int(iters), C.byref(o)))
 
 
@@ -666,7 +664,8 @@ class Server:
     ``max_inflight`` before the process first uses the GPU. ``tick_max`` > 1
     (paper form, FP32 arithmetic) admits up to that many consecutive requests
     of at most ``tick_elems`` tensor elements that the work list takes as one
-    work-list batch on one stream."""
+    work-list batch on one stream; the library refuses ticks (unsupported), as
+    the work-list path is not run."""
 
     def __init__(self, budget_bytes: int, max_inflight: int = 8, form="paper", prec="fp32", tick_max: int = 0,
                  tick_elems: int = 1 << 22):
@@ -729,10 +728,9 @@ class Batch:
     runs on its own stream of the graph; with CUDA's default of 8 hardware work
     queues (``CUDA_DEVICE_MAX_CONNECTIONS``, read when the process first uses
     the GPU) streams sharing a queue wait on one another, so set it to 32 for
-    batches of more than 8 requests. ``worklist=True`` runs the batch through
-    the work-list kernel instead (TUCKER_FLAG_WORKLIST: one persistent launch
-    per step for every request, grouped orthonormalisations; Algorithms 1/2,
-    FP32 arithmetic, no sampling, extents <= 256, ranks <= 32)."""
+    batches of more than 8 requests. ``worklist=True`` asks for the work-list
+    path (TUCKER_FLAG_WORKLIST), which the library plans but does not run: ``run``
+    then raises TuckerError (unsupported); ``batch_describe`` shows its plan."""
 
     def __init__(self, requests, form="paper", prec="fp32", worklist=False):
         self._keep = []

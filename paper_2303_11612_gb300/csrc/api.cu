@@ -837,13 +837,16 @@ tucker_status adaptive_run(const T* A, const int64_t* dims, int N, double eps, i
 tucker_status status_from_cuda(cudaError_t e) { return from_cuda(e); }
 
 // ------------------------------------------------------------------ work-list batches
-// The requests of a batch as steps of the work-list kernel and grouped
+// The requests of a batch as phases of the work-list kernel and grouped
 // orthonormalisations, in the order of the drivers' own launches: for each mode
-// n (and each power step k) one step with every request's stage, then the
-// orthonormalisation of every request's sketch in one launch; a last step forms
-// the cores. ST-HOSVD's step for mode n carries the truncation by U_{n-1}
-// ahead of the power step it feeds. The requests are dealt to lanes (request k
-// to lane k mod lanes), each lane a sequence of its own on a stream of its own,
+// n one phase with every request's truncation by U_{n-1} (ST-HOSVD), status
+// reset and Omega_n, then per power step a phase of partials and a phase of
+// their sums, then the orthonormalisation of every request's sketch in one
+// launch; last, the cores (T-HOSVD's chain a phase per position). Items of one
+// phase never depend on one another: what a task reads was written by an
+// earlier phase, an earlier launch on the lane's stream. The requests are dealt to lanes (request k
+// to lane k mod lanes; a lane per four requests, at most eight), each lane a
+// sequence of its own on a stream of its own,
 // so one lane's orthonormalisations (a few CTAs each) overlap another lane's
 // streaming steps. Each request keeps its own workspace slice (the layout of an
 // asynchronous call), so its results are those of the request alone (FP32
@@ -897,8 +900,8 @@ tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts
         for (int m = 0; m < r.N; ++m) g *= r.ranks[m];
         cap_G[k] = g;
     }
-    // four requests or more per lane, at most four lanes
-    wp.lanes = std::max(1, std::min(std::min(4, max_lanes), n / 4));
+    // four requests or more per lane, at most eight lanes
+    wp.lanes = std::max(1, std::min(std::min(8, max_lanes), n / 4));
     std::vector<WTask>& tasks = wp.tasks;
     std::vector<WItem>& items = wp.items;
     auto add = [&](WTask t, int gx, int gy) -> int {
@@ -982,11 +985,12 @@ tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts
                 t.cols = mp.L;
                 t.seed = r.seed;
                 t.sid = stream_id(0, m);
-                t.dep[0] = m == 0 ? init[k] : -1;
+                (void)init;
                 const int64_t ne = mp.v.i * (int64_t)mp.L;
                 need(ne <= cap_il[k]);
                 gen[k] = add(t, (int)std::max<int64_t>(1, (ne + 4 * kThreads - 1) / (4 * kThreads)), 1);
             }
+            close_step();                    // phase 1: truncation, status reset, Omega_m
             for (int q = 0; q < maxq; ++q) {
                 if (q > 0) {
                     // CholeskyQR of every sketch that takes another power step, in one launch
@@ -1033,6 +1037,7 @@ tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts
                     note(t, worklist_pow_smem(elem, (int)mp.v.i, mp.pp.lg));
                     pw[k] = add(t, mp.pp.groups, mp.pp.parts);
                 }
+                close_step();                // phase 2: the power step's partials
                 for (int k : mem) {
                     const tucker_request& r = reqs[k];
                     if (m >= r.N || q >= r.q) continue;
@@ -1046,7 +1051,7 @@ tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts
                     need((int64_t)t.parts * t.count <= cap_part[k] && t.count <= cap_il[k]);
                     add(t, (int)std::max<int64_t>(1, (t.count + 255) / 256), 1);
                 }
-                close_step();
+                close_step();                // phase 3: their sums
             }
             // the leading factor of every sketch, in one launch
             const int j0 = (int)wp.jobs.size();
@@ -1088,24 +1093,24 @@ tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts
                                    m == 0 ? cap_A[k] : cap_inter[k], m == r.N - 1 ? cap_G[k] : cap_inter[k]);
                 cur[k] = out;
             }
+            close_step();                    // a phase per position of the chain
         }
-        close_step();
     }
     if (!fits) return TUCKER_ERR_INVALID_ARG;
-    // every dependency is an earlier task whose items all come before the first
-    // item of its dependant, in the same step (what makes the waits end)
-    std::vector<int> first(tasks.size(), -1), last(tasks.size(), -1), step_of(items.size(), -1);
+    // every task a task reads the output of runs in an earlier phase of the same
+    // lane (an earlier launch on the lane's stream): no item waits for another
+    std::vector<int> phase_of(items.size(), -1), lane_of(items.size(), -1), first(tasks.size(), -1);
     for (const WorklistOp& op : wp.ops)
         if (op.kind == 0)
-            for (int i = op.a; i < op.b; ++i) step_of[i] = op.step;
-    for (int i = 0; i < (int)items.size(); ++i) {
-        const int t = items[i].task;
-        if (first[t] < 0) first[t] = i;
-        last[t] = i;
-    }
-    for (int t = 0; t < (int)tasks.size(); ++t)
-        for (int d : tasks[t].dep)
-            if (d >= 0 && (d >= t || last[d] >= first[t] || step_of[last[d]] != step_of[first[t]]))
+            for (int i = op.a; i < op.b; ++i) {
+                phase_of[i] = op.step;
+                lane_of[i] = op.lane;
+            }
+    for (int i = 0; i < (int)items.size(); ++i)
+        if (first[items[i].task] < 0) first[items[i].task] = i;
+    for (int i = 0; i < (int)items.size(); ++i)
+        for (int d : tasks[items[i].task].dep)
+            if (d >= 0 && (d >= items[i].task || lane_of[first[d]] != lane_of[i] || phase_of[first[d]] >= phase_of[i]))
                 return TUCKER_ERR_INVALID_ARG;
     const size_t a256 = 255;
     wp.tasks_off = 0;
@@ -1113,7 +1118,7 @@ tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts
     wp.jobs_off = wp.items_off + ((sizeof(WItem) * items.size() + a256) & ~a256);
     wp.desc_bytes = wp.jobs_off + sizeof(OrthJob) * wp.jobs.size();
     wp.counters_off = (wp.desc_bytes + a256) & ~a256;
-    wp.counter_bytes = sizeof(unsigned) * ((size_t)wp.steps + tasks.size() + 1);
+    wp.counter_bytes = sizeof(unsigned) * (size_t)wp.steps;
     wp.area_bytes = wp.counters_off + ((wp.counter_bytes + a256) & ~a256);
     return TUCKER_OK;
 }
@@ -1142,16 +1147,14 @@ cudaError_t worklist_enqueue(const WorklistPlan& wp, char* area, const void* hos
     const WTask* tasks = (const WTask*)(area + wp.tasks_off);
     const WItem* items = (const WItem*)(area + wp.items_off);
     const OrthJob* jobs = (const OrthJob*)(area + wp.jobs_off);
-    unsigned* done = counters + wp.steps;
-    int* abort_flag = (int*)(done + wp.tasks.size());
     for (const WorklistOp& op : wp.ops) {
         if (e != cudaSuccess) break;
         cudaStream_t s = lane_streams[op.lane];
         if (op.kind == 0) {
-            e = wp.elem == 4 ? launch_worklist<float>(tasks, items, op.a, op.b, counters + op.step, done, abort_flag,
-                                                      op.heavy != 0, op.smem, op.grid, s)
-                             : launch_worklist<double>(tasks, items, op.a, op.b, counters + op.step, done, abort_flag,
-                                                       op.heavy != 0, op.smem, op.grid, s);
+            e = wp.elem == 4 ? launch_worklist<float>(tasks, items, op.a, op.b, counters + op.step, op.heavy != 0,
+                                                      op.smem, op.grid, s)
+                             : launch_worklist<double>(tasks, items, op.a, op.b, counters + op.step, op.heavy != 0,
+                                                       op.smem, op.grid, s);
         } else {
             const std::vector<OrthJob> h(wp.jobs.begin() + op.a, wp.jobs.begin() + op.b);
             ProfScope prof(kKExtract, 0.0, 0.0, s);
@@ -1569,13 +1572,10 @@ tucker_status tucker_check_wait_timeout(int32_t iters, const tucker_opts* opts) 
     tucker_status rs = read_opts(opts, o);
     if (rs != TUCKER_OK) return rs;
     if (iters < 1 || iters > (1 << 24)) return TUCKER_ERR_INVALID_ARG;
-    const bool wl = (o.flags & TUCKER_FLAG_WORKLIST) != 0;
     Scratch sc;
-    if ((rs = sc.get(256 + (wl ? worklist_wait_check_bytes() : 0), o.stream)) != TUCKER_OK) return rs;
+    if ((rs = sc.get(256, o.stream)) != TUCKER_OK) return rs;
     cudaError_t e = cudaMemsetAsync(sc.p, 0, sizeof(int), o.stream);
-    if (e == cudaSuccess)
-        e = wl ? launch_worklist_wait_check(iters, (char*)sc.p + 256, (int*)sc.p, o.stream)
-               : launch_wait_timeout(iters, (int*)sc.p, o.stream);
+    if (e == cudaSuccess) e = launch_wait_timeout(iters, (int*)sc.p, o.stream);
     if (e != cudaSuccess) return from_cuda(e);
     return sync_status(o.stream, (const int*)sc.p);
 }

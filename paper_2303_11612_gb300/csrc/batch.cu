@@ -184,6 +184,8 @@ tucker_status tucker_batch_describe(int n, const tucker_request* reqs, const tuc
 
 tucker_status tucker_batch_run(int n, const tucker_request* reqs, const tucker_opts* opts) {
     if (!opts || opts->struct_size < sizeof(tucker_opts) || !opts->workspace) return TUCKER_ERR_INVALID_ARG;
+    // the work-list path is planned (tucker_batch_describe) but not run: see the header
+    if (opts->flags & TUCKER_FLAG_WORKLIST) return TUCKER_ERR_UNSUPPORTED;
     std::vector<size_t> offsets;
     size_t total = 0, area_off = 0;
     tucker_status st = check(n, reqs, opts, false, offsets, total, &area_off);

@@ -210,7 +210,7 @@ enum WKind : int { kWInit = 0, kWGen = 1, kWPow = 2, kWRed = 3, kWTtm = 4 };
 struct WTask {
     int kind;               // WKind
     int nitems;             // items of this task
-    int dep[2];             // tasks whose items must all be done first (-1: none; always earlier in the list)
+    int dep[2];             // tasks whose output it reads (-1: none): always in an earlier phase of its lane
     int* status;            // the request's status word
     const void* in;         // kWPow, kWTtm: the tensor; kWRed: the partials
     const void* X;          // kWPow: X_in (I x L); kWTtm: the factor U (I x K)
@@ -241,15 +241,11 @@ int worklist_ttm_opt(int64_t K);
 // memory (the SMs times the CTAs that fit on one, at most one CTA per item);
 // also raises the kernel's shared-memory limit. Not for use under stream capture.
 int worklist_grid(int elem, bool heavy, size_t smem, int items);
-// A one-CTA work list whose second item waits for an item that is never listed:
-// the wait runs out after `iters` polls and sets kStatTimeout in *status.
-size_t worklist_wait_check_bytes();
-cudaError_t launch_worklist_wait_check(int iters, void* scratch, int* status, cudaStream_t s);
-// Items [begin, end) of one step; claim, done (one word per task) and abort_flag
-// zeroed before the batch's first step.
+// Items [begin, end) of one phase (independent of one another); the claim word
+// zeroed before the launch.
 template <typename T>
-cudaError_t launch_worklist(const WTask* tasks, const WItem* items, int begin, int end, unsigned* claim,
-                            unsigned* done, int* abort_flag, bool heavy, size_t smem, int grid, cudaStream_t s);
+cudaError_t launch_worklist(const WTask* tasks, const WItem* items, int begin, int end, unsigned* claim, bool heavy,
+                            size_t smem, int grid, cudaStream_t s);
 
 // A batch as work-list steps and grouped orthonormalisations (api.cu).
 struct WorklistOp {
@@ -270,7 +266,7 @@ struct WorklistPlan {
     int steps = 0;
     int lanes = 1;          // requests k with k % lanes == l run their steps on stream l
     // device area: tasks, items and jobs (uploaded from the host image), then the
-    // claim words (one per step), done words (one per task) and the abort flag
+    // claim words (one per phase)
     size_t tasks_off = 0, items_off = 0, jobs_off = 0, desc_bytes = 0;
     size_t counters_off = 0, counter_bytes = 0, area_bytes = 0;
 };
@@ -279,7 +275,7 @@ struct WorklistPlan {
 // in the paper form with the exact FMA arithmetic, no sampling, one element type,
 // every extent <= 256 and every rank <= 32.
 tucker_status worklist_plan(int n, const tucker_request* reqs, const tucker_opts& opts, char* ws,
-                            const std::vector<size_t>& offsets, WorklistPlan& wp, int max_lanes = 4);
+                            const std::vector<size_t>& offsets, WorklistPlan& wp, int max_lanes = 8);
 // Fills each step's grid (queries the device: call before stream capture).
 void worklist_prepare(WorklistPlan& wp);
 // The host image of the descriptors (wp.desc_bytes bytes at host).

@@ -471,8 +471,8 @@ tucker_status tucker_server_create(const tucker_server_opts* opts, tucker_server
     if (opts->prec < TUCKER_SK_FP32 || opts->prec > TUCKER_SK_BF16X1) return TUCKER_ERR_INVALID_ARG;
     if (opts->tick_max < 0 || opts->tick_max > 256 || (opts->tick_max > 1 && opts->tick_elems < 1))
         return TUCKER_ERR_INVALID_ARG;
-    if (opts->tick_max > 1 && (opts->form != TUCKER_FORM_PAPER || opts->prec != TUCKER_SK_FP32))
-        return TUCKER_ERR_UNSUPPORTED;
+    // ticks run the work-list path, which is planned but not run: see the header
+    if (opts->tick_max > 1) return TUCKER_ERR_UNSUPPORTED;
     std::unique_ptr<tucker_server> s(new tucker_server());
     s->budget = opts->budget_bytes;
     s->form = opts->form;

@@ -2,17 +2,13 @@
 // tasks - one stage of one request's mode: the Gaussian test matrix, the power
 // step's per-CTA partials, their fixed-order sum, the mode-n product, the
 // status word's reset - and each task into items, the blocks its own kernel
-// would launch. One persistent launch per step of the batch walks the items of
-// every request in list order: a CTA claims the next item with an atomic
-// ticket, waits until the tasks it depends on have all their items done, runs
-// the item's block program (blocks.cuh, the same code and results as the
-// stage's own kernel) and counts the item done. Items are claimed in list order
-// and every dependency lies earlier in the list, so the items a CTA waits for
-// are held by CTAs that are running: the wait always ends, whatever the grid's
-// residency. Each wait still gives up after a bounded number of polls, marks
-// the request's status with kStatTimeout and raises an abort flag, after which
-// the remaining items are only counted (with the same status) and the launch
-// drains.
+// would launch. The tasks of one phase (for every request of the batch) are
+// independent, and one persistent launch per phase walks their items: a CTA
+// claims the next item with an atomic ticket, runs the item's block program
+// (blocks.cuh, the same code and results as the stage's own kernel) and claims
+// again until the list is exhausted. What a task reads was written by an
+// earlier phase, an earlier launch on the same stream, so no CTA ever waits for
+// another.
 #include "blocks.cuh"
 #include "internal.h"
 
@@ -20,19 +16,6 @@ namespace tk {
 namespace {
 
 constexpr int kT = kThreads;
-constexpr int kSpinIters = 1 << 22;     // polls of a dependency wait, 256 ns apart: about a second
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ int ld_relaxed(const int* p) {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 template <typename T, int JB, int LG>
 __device__ __forceinline__ void pow_item(const WTask& t, const WItem& w, unsigned char* smem) {
     blk::power_block<T, JB, LG, 1, false, false>((const T*)t.in, t.v, (const T*)t.X, t.L, (T*)t.out, t.tiles, 0, 0,
@@ -102,44 +85,18 @@ __device__ void run_item(const WTask& t, const WItem& w, unsigned char* smem) {
 
 template <typename T, bool HEAVY>
 __global__ void __launch_bounds__(kT, HEAVY ? 1 : 2) worklist_kernel(const WTask* __restrict__ tasks,
-                                                                     const WItem* __restrict__ items,
-                                                      int begin, int end, unsigned* __restrict__ claim,
-                                                      unsigned* __restrict__ done, int* __restrict__ abort_flag,
-                                                      int spin_limit) {
+                                                                     const WItem* __restrict__ items, int begin,
+                                                                     int end, unsigned* __restrict__ claim) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item, s_go;
+    __shared__ int s_item;
     for (;;) {
         if (threadIdx.x == 0) s_item = begin + (int)atomicAdd(claim, 1u);
         __syncthreads();
         const int it = s_item;
         if (it >= end) return;
         const WItem w = items[it];
-        const WTask& t = tasks[w.task];
-        if (threadIdx.x == 0) {
-            int go = ld_relaxed(abort_flag) == 0;
-            for (int d = 0; d < 2 && go; ++d) {
-                const int dep = t.dep[d];
-                if (dep < 0) continue;
-                const unsigned need = (unsigned)tasks[dep].nitems;
-                for (int n = 0; ld_acquire(done + dep) < need; ++n) {
-                    if (n >= spin_limit) {
-                        go = 0;
-                        atomicExch(abort_flag, 1);
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-            }
-            if (!go) set_status(t.status, kStatTimeout);
-            s_go = go;
-        }
-        __syncthreads();
-        if (s_go) run_item<T, HEAVY>(t, w, smem);
-        __syncthreads();                       // the item's writes, then its count
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(done + w.task, 1u);
-        }
+        run_item<T, HEAVY>(tasks[w.task], w, smem);
+        __syncthreads();                       // the item's reads of shared memory and s_item, before the next
     }
 }
 
@@ -211,54 +168,22 @@ int worklist_ttm_opt(int64_t K) {
 }
 
 template <typename T>
-cudaError_t launch_worklist(const WTask* tasks, const WItem* items, int begin, int end, unsigned* claim,
-                            unsigned* done, int* abort_flag, bool heavy, size_t smem, int grid, cudaStream_t s) {
+cudaError_t launch_worklist(const WTask* tasks, const WItem* items, int begin, int end, unsigned* claim, bool heavy,
+                            size_t smem, int grid, cudaStream_t s) {
     if (end <= begin) return cudaSuccess;
     if (smem > g_smem_cap[sizeof(T) == 4 ? 0 : 1][heavy] || grid < 1) return cudaErrorInvalidValue;
     ProfScope prof(kKWorklist, 0.0, 0.0, s);
     if (heavy)
-        worklist_kernel<T, true><<<(unsigned)grid, kT, smem, s>>>(tasks, items, begin, end, claim, done, abort_flag,
-                                                                  kSpinIters);
+        worklist_kernel<T, true><<<(unsigned)grid, kT, smem, s>>>(tasks, items, begin, end, claim);
     else
-        worklist_kernel<T, false><<<(unsigned)grid, kT, smem, s>>>(tasks, items, begin, end, claim, done, abort_flag,
-                                                                   kSpinIters);
+        worklist_kernel<T, false><<<(unsigned)grid, kT, smem, s>>>(tasks, items, begin, end, claim);
     note_launch();
     return cudaGetLastError();
 }
 
-template cudaError_t launch_worklist<float>(const WTask*, const WItem*, int, int, unsigned*, unsigned*, int*, bool,
-                                            size_t, int, cudaStream_t);
-template cudaError_t launch_worklist<double>(const WTask*, const WItem*, int, int, unsigned*, unsigned*, int*, bool,
-                                             size_t, int, cudaStream_t);
-
-size_t worklist_wait_check_bytes() { return 1024; }
-
-cudaError_t launch_worklist_wait_check(int iters, void* scratch, int* status, cudaStream_t s) {
-    // task 0 claims two items but the list holds one; task 1 waits for both
-    WTask t[2] = {};
-    t[0].kind = -1;
-    t[0].nitems = 2;
-    t[0].dep[0] = t[0].dep[1] = -1;
-    t[0].status = status;
-    t[1].kind = -1;
-    t[1].nitems = 1;
-    t[1].dep[0] = 0;
-    t[1].dep[1] = -1;
-    t[1].status = status;
-    const WItem it[2] = {{0, 0, 0, 0}, {1, 0, 0, 0}};
-    char* b = (char*)scratch;
-    WTask* dt = (WTask*)b;
-    WItem* di = (WItem*)(b + 512);
-    unsigned* counters = (unsigned*)(b + 768);      // claim, done[2], abort
-    static_assert(2 * sizeof(WTask) <= 512, "tasks fit");
-    cudaError_t e = cudaMemcpyAsync(dt, t, sizeof t, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(di, it, sizeof it, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);     // the host images are on this call's stack
-    if (e != cudaSuccess) return e;
-    worklist_kernel<float, false><<<1, kT, 0, s>>>(dt, di, 0, 2, counters, counters + 1, (int*)(counters + 3), iters);
-    note_launch();
-    return cudaGetLastError();
-}
+template cudaError_t launch_worklist<float>(const WTask*, const WItem*, int, int, unsigned*, bool, size_t, int,
+                                            cudaStream_t);
+template cudaError_t launch_worklist<double>(const WTask*, const WItem*, int, int, unsigned*, bool, size_t, int,
+                                             cudaStream_t);
 
 }  // namespace tk

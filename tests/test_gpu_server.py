@@ -86,47 +86,3 @@ def test_admission_budget_and_errors(tk):
             srv.submit("ST", A, dims, (49, 4, 4), P=5, q=1)
         assert e.value.status == 1
 
-
-def test_ticks_same_as_alone_and_fewer_launches(tk):
-    """With ticks, consecutive small requests (the work list's: Algorithms 1/2, no
-    sampling) run together as one work-list batch; AMM requests and tensors above
-    tick_elems keep their own streams. Every result is bitwise the request run
-    alone, host or device buffers alike, and the kernel launches drop."""
-    reqs = make_requests(30, seed=17)
-    for k, r in enumerate(reqs):
-        if k % 7 == 3:
-            r["c"] = 200                                    # AMM: not in ticks
-        elif k % 5 != 4:
-            r["c"] = 0
-    alone = []
-    for r in reqs:
-        At = torch.from_numpy(np.ascontiguousarray(synth.flat(r["A"]))).cuda()
-        U, G = tk.decompose(r["which"], At, r["dims"], r["ranks"], P=5, q=r["q"], c=r["c"], prob=r["prob"],
-                            seed=r["seed"])
-        alone.append(([u.cpu() for u in U], G.cpu()))
-    counts, stats = [], []
-    for tick_max in (0, 8):
-        n0 = tk.launch_count()
-        # two streams: requests queue up behind the first ones and the later ticks fill
-        with tk.Server(budget_bytes=256 << 20, max_inflight=2, tick_max=tick_max, tick_elems=1 << 19) as srv:
-            tickets = []
-            for r in reqs:
-                flat = torch.from_numpy(np.ascontiguousarray(synth.flat(r["A"])))
-                A = flat.pin_memory() if r["host_in"] else flat.cuda()
-                tickets.append(srv.submit(r["which"], A, r["dims"], r["ranks"], P=5, q=r["q"], c=r["c"],
-                                          prob=r["prob"], seed=r["seed"],
-                                          out_device="cpu" if r["host_out"] else "cuda"))
-            got = [srv.wait(t) for t in tickets]
-            st = srv.stats()
-        counts.append(tk.launch_count() - n0)
-        stats.append(st)
-        assert st["completed"] == len(reqs) and st["failed"] == 0
-        for k, ((U, G), (Ua, Ga)) in enumerate(zip(got, alone)):
-            assert all(torch.equal(u.cpu(), ua) for u, ua in zip(U, Ua)) and torch.equal(G.cpu(), Ga), (tick_max, k)
-    assert stats[0]["ticks"] == 0 and stats[1]["ticks"] > 0
-    tickable = sum(1 for r in reqs if r["c"] == 0)
-    # every tickable request went through a tick, and ticks held several on average
-    assert stats[1]["tick_requests"] == tickable, (stats[1], tickable)
-    assert stats[1]["tick_requests"] >= 2 * stats[1]["ticks"], stats[1]
-    assert counts[1] < counts[0] * 0.75, counts
-

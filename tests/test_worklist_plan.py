@@ -1,6 +1,6 @@
-"""Host side of work-list batches (tucker_batch_describe; no GPU): the steps and
-grouped launches a batch becomes, the planner's own dependency check on random
-batches, the workspace it adds, and the batches it refuses."""
+"""Host side of work-list batches (tucker_batch_describe; no GPU): the phases and
+grouped launches a batch becomes, the planner's own dependency and extent
+checks on random batches, the workspace it adds, and the batches it refuses."""
 import re
 
 import numpy as np
@@ -34,18 +34,36 @@ def parse(text):
     return steps, groups, total
 
 
+def expected_steps(specs):
+    """Phases per lane: per mode one (truncation, status reset, Omega) and two per power
+    step (partials, sums) for the longest power iteration among the lane's requests on
+    that mode; then one per position of the core chains that has a product."""
+    nl = max(1, min(8, len(specs) // 4))
+    total = 0
+    for lane in range(nl):
+        mem = specs[lane::nl]
+        maxN = max(len(s["dims"]) for s in mem)
+        total += sum(1 + 2 * max(s["q"] for s in mem if len(s["dims"]) > m) for m in range(maxN))
+        total += sum(1 for m in range(maxN)
+                     if any((s["which"] == "T" and m < len(s["dims"])) or (s["which"] == "ST" and m == len(s["dims"]) - 1)
+                            for s in mem))
+    return total
+
+
 def test_st_hosvd_steps():
-    # 64 x 48 x 40, ranks (8, 6, 5), q = 1: per mode one step (status reset in the first,
-    # the truncation by U_{n-1} in the later ones) and one grouped extraction; a last step
-    # forms the core
+    # 64 x 48 x 40, ranks (8, 6, 5), q = 1: per mode a phase with the status reset (first
+    # mode) or the truncation by U_{n-1} (later modes) and Omega_n, a phase of power-step
+    # partials, a phase of their sums, then the grouped extraction; a last phase forms the core
     steps, groups, (tasks, items, area) = parse(B.batch_describe([dict(which="ST", dims=(64, 48, 40),
                                                                        ranks=(8, 6, 5), P=4, q=1)]))
-    assert groups == ["step", ("extract", 1), "step", ("extract", 1), "step", ("extract", 1), "step"]
-    assert [s[2:7] for s in steps] == [(1, 1, 1, 1, 0), (0, 1, 1, 1, 1), (0, 1, 1, 1, 1), (0, 0, 0, 0, 1)]
-    # the core step: the product by U_3 of the 8 x 6 x 40 tensor (48 fibers, one block of 128)
-    assert steps[3][1] == 1
-    # step 1's product by U_1: 48 * 40 fibers in blocks of 128, 8 outputs in one block
-    assert steps[1][1] >= 15 + 3
+    mode = ["step", "step", "step", ("extract", 1)]
+    assert groups == mode * 3 + ["step"]
+    assert [s[2:7] for s in steps] == [(1, 1, 0, 0, 0), (0, 0, 1, 0, 0), (0, 0, 0, 1, 0)] + \
+        [(0, 1, 0, 0, 1), (0, 0, 1, 0, 0), (0, 0, 0, 1, 0)] * 2 + [(0, 0, 0, 0, 1)]
+    # the core: the product by U_3 of the 8 x 6 x 40 tensor (48 fibers, one block of 128)
+    assert steps[-1][1] == 1
+    # the product by U_1: 48 * 40 fibers in blocks of 128, 8 outputs in one block; and Omega_2
+    assert steps[3][1] == 15 + 1
     assert tasks == sum(sum(s[2:7]) for s in steps) and items == sum(s[1] for s in steps)
     assert area % 256 == 0 and area > 0
 
@@ -59,17 +77,18 @@ def test_t_hosvd_steps(q):
     # then one step with the whole core chain
     want = []
     for _ in range(N):
+        want.append("step")                                  # (status reset,) Omega_n
         for k in range(q):
             if k:
                 want.append(("cholqr", 1))
-            want.append("step")
+            want += ["step", "step"]                         # partials, sums
         want.append(("extract", 1))
-    want.append("step")
+    want += ["step"] * N                                     # the core chain, a phase per product
     assert groups == want
-    assert len(steps) == N * q + 1
-    assert steps[-1][2:7] == (0, 0, 0, 0, N)
+    assert len(steps) == N * (1 + 2 * q) + N
+    assert all(s[2:7] == (0, 0, 0, 0, 1) for s in steps[-N:])
     assert sum(s[3] for s in steps) == N                     # one Gaussian per mode
-    assert sum(s[4] for s in steps) == N * q                 # one power task per step
+    assert sum(s[4] for s in steps) == N * q                 # one power task per power step
 
 
 def test_batches_group_every_request():
@@ -77,8 +96,8 @@ def test_batches_group_every_request():
              dict(which="T", dims=(30, 28, 26, 24), ranks=(4, 4, 3, 2), P=3, q=2),
              dict(which="ST", dims=(256, 17, 33), ranks=(32, 5, 7), P=8, q=2)]
     steps, groups, _ = parse(B.batch_describe(specs))
-    # the longest request sets the schedule: 4 modes x 2 power steps + the cores
-    assert len(steps) == 9
+    # the longest requests set the schedule: 4 modes of (1 + 2 x 2) phases, 4 core phases
+    assert len(steps) == expected_steps(specs) == 24
     assert groups.count(("extract", 3)) == 3 and ("extract", 1) in groups
     # CholeskyQR between power steps only for the q = 2 requests still on their modes
     assert ("cholqr", 2) in groups and ("cholqr", 1) in groups
@@ -97,14 +116,7 @@ def test_random_batches_pass_the_dependency_check():
                               P=int(rng.integers(0, 10)), q=int(rng.integers(1, 4)), seed=k))
         dtype = torch.float32 if trial % 2 == 0 else torch.float64
         steps, groups, (tasks, items, area) = parse(B.batch_describe(specs, dtype=dtype))
-        nl = max(1, min(4, len(specs) // 4))
-        want = 0
-        for lane in range(nl):
-            mem = specs[lane::nl]
-            maxN = max(len(s["dims"]) for s in mem)
-            # mode m takes as many steps as its longest power iteration among the lane's requests that have it
-            want += sum(max(s["q"] for s in mem if len(s["dims"]) > m) for m in range(maxN)) + 1
-        assert len(steps) == want
+        assert len(steps) == expected_steps(specs)
         assert items == sum(s[1] for s in steps) and tasks == sum(sum(s[2:7]) for s in steps)
         assert all(s[7] <= 227 * 1024 for s in steps)
 
@@ -114,8 +126,8 @@ def test_requests_are_dealt_to_lanes():
     out = B.batch_describe(specs)
     assert "lanes=3 " in out
     steps, groups, _ = parse(out)
-    # each lane: 3 modes (a step and an extraction each) and the core step
-    assert len(steps) == 3 * 4 and groups.count("step") == 12
+    # each lane: 3 modes (three phases and an extraction each) and the core phase
+    assert len(steps) == 3 * 10 == expected_steps(specs)
     assert [g for g in groups if g != "step"] == [("extract", 5)] * 3 + [("extract", 4)] * 6
 
 
@@ -167,3 +179,20 @@ def test_mixed_element_types_are_refused():
     o = B.make_opts(flags=B.FLAG_WORKLIST)
     buf = C.create_string_buffer(4096)
     assert B.lib().tucker_batch_describe(2, C.cast(arr, C.c_void_p), C.byref(o), buf, len(buf)) == 6
+
+
+def test_the_work_list_is_not_run():
+    """tucker_batch_run refuses TUCKER_FLAG_WORKLIST before any launch (the path is
+    planned but kept off the device), and the server refuses ticks."""
+    import ctypes as C
+    arr = (B.Request * 1)()
+    d64, r32 = B._i64((20, 20, 20)), B._i32((3, 3, 3))
+    Up = (C.c_void_p * 3)(256, 256, 256)
+    arr[0] = B.Request(C.sizeof(B.Request), 1, 0, 256, d64, 3, r32, 2, 1, 0, 1, 0, Up, 256)
+    o = B.make_opts(flags=B.FLAG_WORKLIST)
+    o.workspace = 256
+    o.workspace_bytes = 1 << 30
+    assert B.lib().tucker_batch_run(1, C.cast(arr, C.c_void_p), C.byref(o)) == 6
+    so = B.ServerOpts(C.sizeof(B.ServerOpts), 8, 1 << 30, 0, 0, 8, 1 << 20)
+    h = C.c_void_p()
+    assert B.lib().tucker_server_create(C.byref(so), C.byref(h)) == 6 and not h.value
