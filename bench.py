@@ -747,6 +747,26 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "step_ms": step_ms,
                "path": f"tucker_server_* request loop, {len(P['slots'])} requests per step, pinned host input and "
                        f"output buffers, host clock around the steps"}
+        # the host link that bounds it: one pinned tensor copied to the device, CUDA events around it
+        try:
+            dev = torch.empty_like(host_in[0], device="cuda")
+            rates = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(b.main_s)
+                with torch.cuda.stream(b.main_s):
+                    dev.copy_(host_in[0], non_blocking=True)
+                e1.record(b.main_s)
+                b.main_s.synchronize()
+                rates.append(host_in[0].numel() * host_in[0].element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+            link = max(rates)
+            bound = len(P["slots"]) / ((h2d + d2h) / (link * 1e9))
+            e2e["h2d_link_gbs"] = link
+            e2e["copy_bound_decomps_per_s"] = bound
+            e2e["frac_of_copy_bound"] = e2e["value"] / bound
+            del dev
+        except Exception as exc:  # noqa: BLE001
+            e2e["h2d_link_error"] = str(exc)[:200]
         del host_in, houts
     except Exception as exc:  # noqa: BLE001
         e2e = {"value": None, "unit": "decomps/s", "error": str(exc)}
