@@ -729,11 +729,13 @@ def main():
 
             # the first passes of the DMA engines over freshly pinned host buffers run at a third of the
             # link's rate (measured: 64, 81, then 211 GB/s over three passes), so the buffers, which a
-            # serving process keeps for its lifetime, are warmed by three untimed steps
-            for _ in range(3):
+            # serving process keeps for its lifetime, are warmed by untimed steps; the timed steps are
+            # many enough (10 at the default 20) that a step slowed by the shared host moves the rate
+            # little (single steps of 124 to 243 ms against 86.5 were seen)
+            for _ in range(5):
                 step_e2e()
             b.barrier()
-            e2e_steps = max(3, args.steps // 4)
+            e2e_steps = max(5, args.steps // 2)
             step_ms = []
             t0 = time.perf_counter()
             for _ in range(e2e_steps):
