@@ -15,12 +15,14 @@ fastest arithmetic whose relative error (Eq. 8) is within 1e-3 of the FP64
 oracle's on every variant; the oracle runs on the host on the same bytes (the
 first tensor), which also gives the CPU baseline. e2e = the same through the
 library's request loop with pinned host buffers (host->device copy of each
-input and device->host copy of the factors and core inside the timed region).
+input and device->host copy of the factors and core inside the timed region),
+beside the host link's measured rate and the rate it bounds.
 
 Secondary lines, each with its own oracle check: the 400^3 batch (low-rank
 and Hilbert tensors, q = 1 / 2, AMM c = 4000; 32 distinct buffers), the 96^4
 decaying-core tensor (q = 2), the FP64 100^3 T-HOSVD, randomized T-HOSVD;
-and the serving stream (2000 requests of orders 3 and 4, extents up to 256,
+the latency of one decomposition alone (headline tensor and 400^3, headline
+arithmetic and FP32); and the serving stream (2000 requests of orders 3 and 4, extents up to 256,
 a 40 GB admission budget): saturation throughput and p50/p99 latency under
 Poisson arrivals, in the headline arithmetic and in FP32.
 
@@ -361,6 +363,47 @@ def serving_bench(tk, torch, specs, prec, load=0.7):
             "decomps_per_s": n / busy_s, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
             "max_ms": st["max_ms"], "peak_inflight": st["peak_inflight"],
             "peak_bytes": max(st["peak_bytes"], sat_peak), "failed": st["failed"]}
+
+
+# ---------------------------------------------------------------- latency
+def latency_bench(tk, torch, stream, precs):
+    """One decomposition alone, as a caller waiting for its result sees it: randomized ST-HOSVD (q = 1) of the
+    headline's 1024 x 1024 x 512 video-like tensor (R = (64, 64, 32), P = 16) and of a 400^3 low-rank tensor
+    (R = 20, P = 10), input resident in HBM, asynchronous call into a preallocated workspace on one stream,
+    CUDA events around it; 2 warm-up calls, then the median and minimum of 5."""
+    import numpy as np
+    import synth
+    from synth import device as sd
+    cases = {"video1024": ((1024, 1024, 512), (64, 64, 32), 16,
+                           lambda: sd.video_like(torch, (1024, 1024, 512), seed=SEED)),
+             "cube400": ((400, 400, 400), (20, 20, 20), 10,
+                         lambda: torch.from_numpy(synth.flat(synth.lowrank_noise((400,) * 3, (20,) * 3, rel_noise=1e-2,
+                                                                                  seed=SEED))).cuda())}
+    out = {}
+    for name, (dims, ranks, P, make) in cases.items():
+        A = make()
+        res = {"workload": f"randomized ST-HOSVD of {'x'.join(map(str, dims))}, R={ranks}, P={P}, q=1"}
+        for prec in precs:
+            ws = torch.empty(tk.workspace_size("ST", dims, ranks, P=P, q=1, prec=prec), dtype=torch.uint8,
+                             device="cuda")
+            ms = []
+            for k in range(7):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tk.decompose("ST", A, dims, ranks, P=P, q=1, seed=SEED, prec=prec, stream=stream, workspace=ws,
+                             flags=tk.FLAG_ASYNC)
+                e1.record(stream)
+                stream.synchronize()
+                if k >= 2:
+                    ms.append(e0.elapsed_time(e1))
+            if tk.last_device_status() != 0:
+                raise RuntimeError("device status not OK")
+            res[prec] = {"median_ms": float(np.median(ms)), "min_ms": float(min(ms))}
+            del ws
+        out[name] = res
+        del A
+        torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- ranks
@@ -831,6 +874,13 @@ def main():
             except Exception as exc:  # noqa: BLE001
                 secondary[name] = {"error": str(exc)[:300]}
 
+    latency = None
+    if not args.no_secondary:
+        try:
+            latency = latency_bench(tk, torch, b.main_s, list(dict.fromkeys([head, "fp32"])))
+        except Exception as exc:  # noqa: BLE001
+            latency = {"error": str(exc)[:300]}
+
     serving = None
     if not args.no_serving:
         try:
@@ -864,6 +914,7 @@ def main():
             "sketch_hbm_gbs": achieved_gbs,
             "forms": head_line,
             "secondary": secondary,
+            "latency": latency,
             "serving": serving,
             "autotune": tk.autotune_entries(),
             "clocks": clk}
