@@ -382,28 +382,65 @@ def latency_bench(tk, torch, stream, precs):
     out = {}
     for name, (dims, ranks, P, make) in cases.items():
         A = make()
+        # outputs allocated once; everything generated on the default stream is complete
+        # before the decompositions on `stream` read it
+        U = [torch.empty((R, I), dtype=torch.float32, device="cuda").t() for I, R in zip(dims, ranks)]
+        G = torch.empty(int(np.prod(ranks)), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
         res = {"workload": f"randomized ST-HOSVD of {'x'.join(map(str, dims))}, R={ranks}, P={P}, q=1"}
         for prec in precs:
             ws = torch.empty(tk.workspace_size("ST", dims, ranks, P=P, q=1, prec=prec), dtype=torch.uint8,
                              device="cuda")
+            torch.cuda.synchronize()
             ms = []
             for k in range(7):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 tk.decompose("ST", A, dims, ranks, P=P, q=1, seed=SEED, prec=prec, stream=stream, workspace=ws,
-                             flags=tk.FLAG_ASYNC)
+                             flags=tk.FLAG_ASYNC, out=(U, G))
                 e1.record(stream)
                 stream.synchronize()
                 if k >= 2:
                     ms.append(e0.elapsed_time(e1))
-            if tk.last_device_status() != 0:
-                raise RuntimeError("device status not OK")
-            res[prec] = {"median_ms": float(np.median(ms)), "min_ms": float(min(ms))}
+            # the last call's status (0: ok; 4: TUCKER_ERR_NUMERICAL, a sketch CholeskyQR could not
+            # orthonormalise even shifted; 5: a bounded wait ran out)
+            res[prec] = {"median_ms": float(np.median(ms)), "min_ms": float(min(ms)),
+                         "status": int(tk.last_device_status())}
             del ws
         out[name] = res
         del A
         torch.cuda.empty_cache()
     return out
+
+
+# ---------------------------------------------------------------- fusions
+def fusion_bench(tk, torch, stream):
+    """The mode-1 and mode-2 fiber norms of a 400^3 FP32 tensor (Algorithm 4's nearly-optimal
+    probabilities for its first two modes): one fused pass against two per-mode passes; kernel time from
+    the library's per-launch CUDA events (profile class "norms"), 2 warm-up calls, then 7 of each."""
+    import synth
+    dims = (400, 400, 400)
+    A = torch.from_numpy(synth.flat(synth.lowrank_noise(dims, (20,) * 3, rel_noise=1e-2, seed=SEED))).cuda()
+    torch.cuda.synchronize()
+
+    def timed(fn, launches):
+        for _ in range(2):
+            fn()
+        tk.profile_enable(True)
+        for _ in range(7):
+            fn()
+        n, ms, _, _ = tk.profile_read("norms")
+        tk.profile_enable(False)
+        if n != 7 * launches:
+            raise RuntimeError(f"expected {7 * launches} norm launches, profiled {n}")
+        return ms / 7
+
+    fused = timed(lambda: tk.fiber_norms12(A, dims, stream=stream), 1)
+    apart = timed(lambda: (tk.fiber_norms(A, dims, 0, stream=stream), tk.fiber_norms(A, dims, 1, stream=stream)), 2)
+    gb = A.numel() * 4 / 1e9
+    return {"norms12_400cubed": {"workload": "squared fiber norms of modes 1 and 2 of a 400^3 FP32 tensor",
+                                 "fused_ms": fused, "per_mode_ms": apart, "fused_gbs": gb / (fused * 1e-3),
+                                 "speedup": apart / fused}}
 
 
 # ---------------------------------------------------------------- ranks
@@ -880,6 +917,10 @@ def main():
             latency = latency_bench(tk, torch, b.main_s, list(dict.fromkeys([head, "fp32"])))
         except Exception as exc:  # noqa: BLE001
             latency = {"error": str(exc)[:300]}
+        try:
+            secondary["fusions"] = fusion_bench(tk, torch, b.main_s)
+        except Exception as exc:  # noqa: BLE001
+            secondary["fusions"] = {"error": str(exc)[:300]}
 
     serving = None
     if not args.no_serving:

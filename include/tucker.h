@@ -269,6 +269,18 @@ tucker_status tucker_range_sketch(const void* A, tucker_dtype dt, const int64_t*
 tucker_status tucker_fiber_norms(const void* A, tucker_dtype dt, const int64_t* dims, int N,
                                  int mode, double* w, const tucker_opts* opts);
 
+/* The squared norms of the mode-1 and the mode-2 fibers (as tucker_fiber_norms
+ * with mode 0 and 1) in one pass over A (N >= 2, I_1 <= 1024, else
+ * TUCKER_ERR_UNSUPPORTED): w1 receives J_1 = I_2 ... I_N values, bitwise those
+ * of tucker_fiber_norms for mode 0 when I_1 >= 64 (the same summation order);
+ * w2 receives J_2 = I_1 I_3 ... I_N values, summed in a fixed order of its own
+ * (within about 2^-44 relative of tucker_fiber_norms for mode 1). Algorithm 4
+ * with the nearly-optimal probabilities samples modes 1 and 2 of the same
+ * tensor; the T-HOSVD driver forms both from this pass. Not in the paper as a
+ * separate step (a fusion of the remark after Algorithm 3's norms). */
+tucker_status tucker_fiber_norms12(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                                   double* w1, double* w2, const tucker_opts* opts);
+
 /* Integer sampling weights W_j = ceil(w_j / max(w) * 2^24) (0 where w_j == 0;
  * all ones if every w_j is 0), or all ones for uniform probabilities. */
 tucker_status tucker_quantize_weights(const double* w, int64_t J, tucker_prob prob,

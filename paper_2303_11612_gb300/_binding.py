@@ -80,6 +80,7 @@ _SIGS = {
     "tucker_power_step": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _I64, _VP, _P(Opts)],
     "tucker_range_sketch": [_VP, _INT, _P(_I64), _INT, _INT, _I64, _U64, _VP, _P(Opts)],
     "tucker_fiber_norms": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _P(Opts)],
+    "tucker_fiber_norms12": [_VP, _INT, _P(_I64), _INT, _VP, _VP, _P(Opts)],
     "tucker_quantize_weights": [_VP, _I64, _INT, _VP, _P(Opts)],
     "tucker_sample_fibers": [_VP, _I64, _I64, _U64, _INT, _VP, _VP, _P(Opts)],
     "tucker_gather_fibers": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _VP, _I64, _VP, _P(Opts)],
@@ -459,6 +460,20 @@ def fiber_norms(A, dims, mode, stream=None):
     _check("tucker_fiber_norms", lib().tucker_fiber_norms(A.data_ptr(), _dt(A), _i64(dims), len(dims), mode,
                                                           w.data_ptr(), C.byref(o)))
     return w
+
+
+def fiber_norms12(A, dims, stream=None):
+    """tucker_fiber_norms12: the mode-1 and mode-2 fiber norms from one pass over A."""
+    dims = _view(A, dims, 1)
+    E = 1
+    for d in dims:
+        E *= d
+    w1 = torch.empty(E // dims[0], dtype=torch.float64, device=A.device)
+    w2 = torch.empty(E // dims[1], dtype=torch.float64, device=A.device)
+    o = make_opts(stream=stream)
+    _check("tucker_fiber_norms12", lib().tucker_fiber_norms12(A.data_ptr(), _dt(A), _i64(dims), len(dims),
+                                                              w1.data_ptr(), w2.data_ptr(), C.byref(o)))
+    return w1, w2
 
 
 def quantize_weights(w, prob="nearly_optimal", stream=None):

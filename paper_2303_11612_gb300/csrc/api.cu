@@ -276,6 +276,7 @@ struct Work {
     void* partials;
     void* orth;
     double* w; uint64_t* W; void* samp; int64_t* idx; double* scale; void* Cp;
+    double* w2;            // T-HOSVD with sampling: mode 2's fiber norms, formed beside mode 1's
     void* inter[2];
     void* Y; void* QY;     // half steps: T x L product and its orthonormal factor
     void* Gn;              // Strategy B: the I_n x I_n Gram matrix (FP32)
@@ -306,8 +307,10 @@ void carve(const Plan& p, Arena& a, Work& w) {
         w.idx = (int64_t*)a.take(sizeof(int64_t) * (size_t)p.maxT);
         w.scale = (double*)a.take(sizeof(double) * (size_t)p.maxT);
         w.Cp = a.take((size_t)p.maxIT * p.elem);
+        w.w2 = p.st ? nullptr : (double*)a.take(sizeof(double) * (size_t)p.maxJ);
     } else {
         w.w = nullptr; w.W = nullptr; w.samp = nullptr; w.idx = nullptr; w.scale = nullptr; w.Cp = nullptr;
+        w.w2 = nullptr;
     }
     w.Y = p.maxTL ? a.take((size_t)p.maxTL * p.elem) : nullptr;
     w.QY = p.maxTL ? a.take((size_t)p.maxTL * p.elem) : nullptr;
@@ -350,17 +353,20 @@ template <typename T>
 cudaError_t sketch_factor(const T* M, const ModePlan& mp, int n, int q, uint64_t seed, int form, T* U,
                           const Work& w, cudaStream_t s);
 
-// One mode's factor U (I_n x R_n) from the tensor B (view mp.v).
+// One mode's factor U (I_n x R_n) from the tensor B (view mp.v); with sampling,
+// `norms` holds B's mode-n fiber norms when they were formed already (else w.w
+// receives them here).
 template <typename T>
 cudaError_t factor_mode(const T* B, const ModePlan& mp, int n, int q, int prob, uint64_t seed, int form, T* U,
-                        const Work& w, int64_t* sample_out, cudaStream_t s) {
+                        const Work& w, int64_t* sample_out, cudaStream_t s, const double* norms = nullptr) {
     const T* M = B;
     if (mp.T > 0) {
         const int64_t J = mp.v.fibers();
-        if (prob == TUCKER_PROB_NEARLY_OPTIMAL) TK_TRY(launch_fiber_norms<T>(B, mp.v, w.w, s));
+        if (prob == TUCKER_PROB_NEARLY_OPTIMAL && !norms) TK_TRY(launch_fiber_norms<T>(B, mp.v, w.w, s));
+        const double* wn = norms ? norms : w.w;
         {
             ProfScope prof(kKSample, 0.0, 0.0, s);
-            TK_TRY(launch_quantize(w.w, J, prob, w.W, w.samp, s));
+            TK_TRY(launch_quantize(wn, J, prob, w.W, w.samp, s));
             TK_TRY(launch_sample(w.W, J, mp.T, seed, stream_id(1, n), w.idx, w.scale, w.samp, s));
         }
         TK_TRY(launch_gather<T>(B, mp.v, w.idx, w.scale, mp.T, (T*)w.Cp, s));
@@ -518,9 +524,19 @@ cudaError_t run_driver(const Plan& p, const T* A, const int32_t* ranks, int q, i
             cur = out;
         }
     } else {
+        // Algorithm 4 with the nearly-optimal probabilities: modes 1 and 2 sample the same
+        // tensor, so their fiber norms come from one pass over it
+        const double* pre[2] = {nullptr, nullptr};
+        if (prob == TUCKER_PROB_NEARLY_OPTIMAL && N >= 2 && p.m[0].T > 0 && p.m[1].T > 0 && w.w2 &&
+            fiber_norms12_supported(p.dims[0])) {
+            TK_TRY(launch_fiber_norms12<T>(A, p.dims[0], p.dims[1], prod(p.dims, N) / (p.dims[0] * p.dims[1]), w.w,
+                                           w.w2, s));
+            pre[0] = w.w;
+            pre[1] = w.w2;
+        }
         for (int n = 0; n < N; ++n)
             TK_TRY(factor_mode<T>(A, p.m[n], n, q, prob, seed, p.form, U[n], w,
-                                  sample_out ? sample_out[n] : nullptr, s));
+                                  sample_out ? sample_out[n] : nullptr, s, n < 2 ? pre[n] : nullptr));
         int64_t e[kMaxOrder];
         for (int n = 0; n < N; ++n) e[n] = p.dims[n];
         const T* cur = A;
@@ -1390,6 +1406,24 @@ tucker_status tucker_range_sketch(const void* A, tucker_dtype dt, const int64_t*
                                                     seed, sid, o.stream)
                               : launch_power<double>((const double*)A, v, nullptr, (int)L, (double*)Y, sc.p, pp,
                                                      true, seed, sid, o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_fiber_norms12(const void* A, tucker_dtype dt, const int64_t* dims, int N, double* w1,
+                                   double* w2, const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (N < 2 || !mode_args_ok(A, dims, N, 1) || !w1 || !w2) return TUCKER_ERR_INVALID_ARG;
+    if (!fiber_norms12_supported(dims[0])) return TUCKER_ERR_UNSUPPORTED;
+    const int64_t rest = prod(dims, N) / (dims[0] * dims[1]);
+    cudaError_t e = dt == TUCKER_F32 ? launch_fiber_norms12<float>((const float*)A, dims[0], dims[1], rest, w1, w2,
+                                                                   o.stream)
+                  : dt == TUCKER_F64 ? launch_fiber_norms12<double>((const double*)A, dims[0], dims[1], rest, w1, w2,
+                                                                    o.stream)
+                                     : cudaErrorInvalidValue;
+    if (e == cudaErrorInvalidValue) return TUCKER_ERR_INVALID_ARG;
     if (e != cudaSuccess) return from_cuda(e);
     return sync_status(o.stream, nullptr);
 }

@@ -135,6 +135,12 @@ cudaError_t launch_sign_fix(T* U, int64_t I, int R, cudaStream_t s);
 // ---- sampling (kernels_amm.cu)
 template <typename T>
 cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStream_t s);
+// Mode-1 and mode-2 fiber norms in one pass over the tensor read as I1 x I2 x rest:
+// w1[i2 + I2 r] (the mode-1 fibers' order), w2[i1 + I1 r] (the mode-2 fibers'); I1 <= 1024.
+bool fiber_norms12_supported(int64_t I1);
+template <typename T>
+cudaError_t launch_fiber_norms12(const T* A, int64_t I1, int64_t I2, int64_t rest, double* w1, double* w2,
+                                 cudaStream_t s);
 size_t quantize_scratch_bytes(int64_t J);
 cudaError_t launch_quantize(const double* w, int64_t J, int prob, uint64_t* W, void* scratch,
                             cudaStream_t s);

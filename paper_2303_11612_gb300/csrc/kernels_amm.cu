@@ -103,6 +103,57 @@ __global__ void __launch_bounds__(kT) norms_strided_kernel(const T* __restrict__
     }
 }
 
+// The squared norms of the mode-1 and the mode-2 fibers in one pass (the remark
+// after Algorithm 3, for the sampling of both modes in Algorithm 4). The tensor
+// is read as I1 x I2 x rest (i1 fastest); slab s of rest is an I1 x I2 matrix
+// whose rows (fixed i2) are mode-1 fibers and whose columns (fixed i1) are
+// mode-2 fibers. Warp w takes rows i2 = w, w + warps, ...: a row's sum is the
+// lanes' partials (lane takes i1 = lane + 32 k, k increasing: the order of
+// norms_contig_kernel, so the mode-1 norms are the same) reduced across the
+// warp; each lane also adds its elements into its columns' sums over the
+// warp's rows, and the warps' column sums are combined in warp order.
+template <typename T, int NK>
+__global__ void __launch_bounds__(kT) norms12_kernel(const T* __restrict__ A, int64_t I1, int64_t I2, int64_t rest,
+                                                     double* __restrict__ w1, double* __restrict__ w2) {
+    constexpr int kW = kT / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    NormAcc<T>* part = reinterpret_cast<NormAcc<T>*>(smem_raw);    // [kW][I1]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t s = blockIdx.x; s < rest; s += gridDim.x) {
+        const T* slab = A + s * I1 * I2;
+        NormAcc<T> col[NK];
+        for (int64_t i2 = warp; i2 < I2; i2 += kW) {
+            const T* row = slab + i2 * I1;
+            T x[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const int64_t i = lane + 32 * k;
+                x[k] = i < I1 ? __ldg(row + i) : T(0);
+            }
+            NormAcc<T> r;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                r.add(x[k]);
+                col[k].add(x[k]);
+            }
+            r.warp_reduce();
+            if (lane == 0) w1[i2 + I2 * s] = r.value();
+        }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const int64_t i = lane + 32 * k;
+            if (i < I1) part[warp * I1 + i] = col[k];
+        }
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < I1; i += kT) {
+            NormAcc<T> t = part[i];
+            for (int q = 1; q < kW; ++q) NormPart<T>::merge(t, part[q * I1 + i]);
+            w2[i + I1 * s] = t.value();
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- integer weights
 __global__ void __launch_bounds__(kT) max_kernel(const double* __restrict__ w, int64_t J,
                                                  unsigned long long* __restrict__ out) {
@@ -314,6 +365,29 @@ cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStr
     return cudaGetLastError();
 }
 
+bool fiber_norms12_supported(int64_t I1) { return I1 >= 1 && I1 <= 1024; }
+
+template <typename T>
+cudaError_t launch_fiber_norms12(const T* A, int64_t I1, int64_t I2, int64_t rest, double* w1, double* w2,
+                                 cudaStream_t s) {
+    if (!fiber_norms12_supported(I1) || I2 < 1) return cudaErrorInvalidValue;
+    if (rest == 0) return cudaSuccess;
+    const double elems = (double)I1 * (double)I2 * (double)rest;
+    ProfScope prof(kKNorms, elems * sizeof(T), 4.0 * elems, s);
+    const size_t smem = (size_t)(kT / 32) * (size_t)I1 * sizeof(NormAcc<T>);
+    const int64_t grid = rest < 4 * (int64_t)num_sms() ? rest : 4 * (int64_t)num_sms();
+    auto run = [&](auto kernel) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kernel<<<(unsigned)grid, kT, smem, s>>>(A, I1, I2, rest, w1, w2);
+    };
+    if (I1 <= 128) run(norms12_kernel<T, 4>);
+    else if (I1 <= 256) run(norms12_kernel<T, 8>);
+    else if (I1 <= 512) run(norms12_kernel<T, 16>);
+    else run(norms12_kernel<T, 32>);
+    note_launch();
+    return cudaGetLastError();
+}
+
 size_t quantize_scratch_bytes(int64_t) { return 256; }
 
 cudaError_t launch_quantize(const double* w, int64_t J, int prob, uint64_t* W, void* scratch, cudaStream_t s) {
@@ -389,6 +463,10 @@ cudaError_t launch_gather(const T* A, const ModeView& v, const int64_t* idx, con
     return cudaGetLastError();
 }
 
+template cudaError_t launch_fiber_norms12<float>(const float*, int64_t, int64_t, int64_t, double*, double*,
+                                                cudaStream_t);
+template cudaError_t launch_fiber_norms12<double>(const double*, int64_t, int64_t, int64_t, double*, double*,
+                                                 cudaStream_t);
 template cudaError_t launch_fiber_norms<float>(const float*, const ModeView&, double*, cudaStream_t);
 template cudaError_t launch_fiber_norms<double>(const double*, const ModeView&, double*, cudaStream_t);
 template cudaError_t launch_gather<float>(const float*, const ModeView&, const int64_t*, const double*, int64_t,
