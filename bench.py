@@ -846,6 +846,22 @@ def main():
             e2e["h2d_link_gbs"] = link
             e2e["copy_bound_decomps_per_s"] = bound
             e2e["frac_of_copy_bound"] = e2e["value"] / bound
+            # the same steps with the copies alone (every slot's input to the device, host clock
+            # around each step): single copies on this host's link now and then take 2.5x their
+            # usual time, in a copy loop without any decomposition as well as in the request loop,
+            # and this loop meets those stalls over as many steps as the timed ones
+            loop_ms = []
+            for _ in range(e2e_steps):
+                t1 = time.perf_counter()
+                with torch.cuda.stream(b.main_s):
+                    for h in host_in:
+                        dev.copy_(h, non_blocking=True)
+                b.main_s.synchronize()
+                loop_ms.append(round(1e3 * (time.perf_counter() - t1), 1))
+            loop_rate = len(P["slots"]) * e2e_steps / (sum(loop_ms) / 1e3)
+            e2e["copy_loop"] = {"decomps_per_s": loop_rate, "step_ms": loop_ms,
+                                "what": "the timed steps' host-to-device copies alone, one stream, host clock"}
+            e2e["frac_of_copy_loop"] = e2e["value"] / loop_rate
             del dev
         except Exception as exc:  # noqa: BLE001
             e2e["h2d_link_error"] = str(exc)[:200]

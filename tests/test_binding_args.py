@@ -88,3 +88,13 @@ def test_step_wrappers_refuse_mis_shaped_operands():
         B.relative_error(A, dims, (2, 2, 2), U[:2], torch.zeros(8))
     with pytest.raises(ValueError):
         B.relative_error(A, dims, (2, 2, 2), U, torch.zeros(7))
+
+
+def test_binding_flags_match_the_header():
+    """The binding's TUCKER_FLAG_* values are the header's."""
+    import re
+    from pathlib import Path
+    from paper_2303_11612_gb300 import _binding as B
+    text = (Path(__file__).resolve().parents[1] / "include" / "tucker.h").read_text()
+    flags = {m.group(1): int(m.group(2), 16) for m in re.finditer(r"#define TUCKER_FLAG_(\w+) (0x[0-9a-fA-F]+)u", text)}
+    assert flags == {"ASYNC": B.FLAG_ASYNC, "WORKLIST": B.FLAG_WORKLIST}
