@@ -420,9 +420,10 @@ def latency_bench(tk, torch, stream, precs):
 
 # ---------------------------------------------------------------- fusions
 def fusion_bench(tk, torch, stream):
-    """The mode-1 and mode-2 fiber norms of a 400^3 FP32 tensor (Algorithm 4's nearly-optimal
-    probabilities for its first two modes): one fused pass against two per-mode passes; kernel time from
-    the library's per-launch CUDA events (profile class "norms"), 2 warm-up calls, then 7 of each."""
+    """The fiber norms of a 400^3 FP32 tensor (Algorithm 4's nearly-optimal probabilities): modes 1 and 2
+    in one fused pass against two per-mode passes, and all three modes in one pass (plus the sums of its
+    partials) against three; kernel time from the library's per-launch CUDA events (profile class
+    "norms"), 2 warm-up calls, then 7 of each."""
     import synth
     dims = (400, 400, 400)
     A = torch.from_numpy(synth.flat(synth.lowrank_noise(dims, (20,) * 3, rel_noise=1e-2, seed=SEED))).cuda()
@@ -442,10 +443,17 @@ def fusion_bench(tk, torch, stream):
 
     fused = timed(lambda: tk.fiber_norms12(A, dims, stream=stream), 1)
     apart = timed(lambda: (tk.fiber_norms(A, dims, 0, stream=stream), tk.fiber_norms(A, dims, 1, stream=stream)), 2)
+    ws = torch.empty(tk.fiber_norms123_workspace_size(dims), dtype=torch.uint8, device="cuda")
+    all3 = timed(lambda: tk.fiber_norms123(A, dims, stream=stream, workspace=ws), 1)
+    apart3 = timed(lambda: [tk.fiber_norms(A, dims, n, stream=stream) for n in range(3)], 3)
     gb = A.numel() * 4 / 1e9
     return {"norms12_400cubed": {"workload": "squared fiber norms of modes 1 and 2 of a 400^3 FP32 tensor",
                                  "fused_ms": fused, "per_mode_ms": apart, "fused_gbs": gb / (fused * 1e-3),
-                                 "speedup": apart / fused}}
+                                 "speedup": apart / fused},
+            "norms123_400cubed": {"workload": "squared fiber norms of all three modes of a 400^3 FP32 tensor "
+                                              "(one pass over the tensor, then the partials summed)",
+                                  "fused_ms": all3, "per_mode_ms": apart3, "fused_gbs": gb / (all3 * 1e-3),
+                                  "speedup": apart3 / all3}}
 
 
 # ---------------------------------------------------------------- ranks

@@ -281,6 +281,23 @@ tucker_status tucker_fiber_norms(const void* A, tucker_dtype dt, const int64_t* 
 tucker_status tucker_fiber_norms12(const void* A, tucker_dtype dt, const int64_t* dims, int N,
                                    double* w1, double* w2, const tucker_opts* opts);
 
+/* All three modes' squared fiber norms of an order-3 tensor (N == 3, else
+ * TUCKER_ERR_INVALID_ARG; I_1 <= 1024, else TUCKER_ERR_UNSUPPORTED) in one pass
+ * over A: w1 (J_1 = I_2 I_3 values) bitwise those of tucker_fiber_norms for
+ * mode 0 when I_1 >= 64; w2 (J_2 = I_1 I_3) and w3 (J_3 = I_1 I_2) summed from
+ * partials over bands of rows and chunks of slabs in a fixed order (within
+ * about 2^-44 relative of tucker_fiber_norms for modes 1 and 2). The partials
+ * go to opts->workspace when it is set (device memory of
+ * tucker_fiber_norms123_workspace_size bytes; fewer is TUCKER_ERR_INVALID_ARG),
+ * else to a block the call allocates on opts->stream and frees. Algorithm 4
+ * with the nearly-optimal probabilities samples every mode of the same tensor;
+ * the T-HOSVD driver forms an order-3 tensor's three weight vectors from this
+ * pass. Not in the paper as a separate step. */
+tucker_status tucker_fiber_norms123(const void* A, tucker_dtype dt, const int64_t* dims, int N,
+                                    double* w1, double* w2, double* w3, const tucker_opts* opts);
+/* Device bytes of tucker_fiber_norms123's partials for dims (N == 3). */
+tucker_status tucker_fiber_norms123_workspace_size(const int64_t* dims, int N, size_t* bytes);
+
 /* Integer sampling weights W_j = ceil(w_j / max(w) * 2^24) (0 where w_j == 0;
  * all ones if every w_j is 0), or all ones for uniform probabilities. */
 tucker_status tucker_quantize_weights(const double* w, int64_t J, tucker_prob prob,

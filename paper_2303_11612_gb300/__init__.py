@@ -9,7 +9,7 @@ loaded.
 """
 from ._binding import (  # noqa: F401
     TuckerError, decompose, rthosvd, rsthosvd, rsthosvd_adaptive, workspace_size, plan_describe, factor_tensor,
-    gaussian, power_step, range_sketch, fiber_norms, fiber_norms12, quantize_weights, sample_fibers, gather_fibers, leading_factor,
+    gaussian, power_step, range_sketch, fiber_norms, fiber_norms12, fiber_norms123, fiber_norms123_workspace_size, quantize_weights, sample_fibers, gather_fibers, leading_factor,
     ttm, gram, cholqr, leading_factor_chain, sample_factor, quantize_weights_max, sample_fibers_slab,
     relative_error, last_device_status, lib, exported_symbols, FLAG_ASYNC, launch_count, profile_enable, batch_describe,
     profile_read, Server, Batch, autotune_enable, autotune_entries,

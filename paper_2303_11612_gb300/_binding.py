@@ -81,6 +81,8 @@ _SIGS = {
     "tucker_range_sketch": [_VP, _INT, _P(_I64), _INT, _INT, _I64, _U64, _VP, _P(Opts)],
     "tucker_fiber_norms": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _P(Opts)],
     "tucker_fiber_norms12": [_VP, _INT, _P(_I64), _INT, _VP, _VP, _P(Opts)],
+    "tucker_fiber_norms123": [_VP, _INT, _P(_I64), _INT, _VP, _VP, _VP, _P(Opts)],
+    "tucker_fiber_norms123_workspace_size": [_P(_I64), _INT, _P(C.c_size_t)],
     "tucker_quantize_weights": [_VP, _I64, _INT, _VP, _P(Opts)],
     "tucker_sample_fibers": [_VP, _I64, _I64, _U64, _INT, _VP, _VP, _P(Opts)],
     "tucker_gather_fibers": [_VP, _INT, _P(_I64), _INT, _INT, _VP, _VP, _I64, _VP, _P(Opts)],
@@ -474,6 +476,30 @@ def fiber_norms12(A, dims, stream=None):
     _check("tucker_fiber_norms12", lib().tucker_fiber_norms12(A.data_ptr(), _dt(A), _i64(dims), len(dims),
                                                               w1.data_ptr(), w2.data_ptr(), C.byref(o)))
     return w1, w2
+
+
+def fiber_norms123(A, dims, stream=None, workspace=None):
+    """tucker_fiber_norms123: the three modes' fiber norms of an order-3 tensor from one
+    pass over A (the partials in ``workspace`` if given, else in a block the call
+    allocates)."""
+    dims = _view(A, dims, 2)
+    if len(dims) != 3:
+        raise ValueError("fiber_norms123 takes an order-3 tensor")
+    I1, I2, I3 = dims
+    w1 = torch.empty(I2 * I3, dtype=torch.float64, device=A.device)
+    w2 = torch.empty(I1 * I3, dtype=torch.float64, device=A.device)
+    w3 = torch.empty(I1 * I2, dtype=torch.float64, device=A.device)
+    o = make_opts(stream=stream, workspace=workspace)
+    _check("tucker_fiber_norms123", lib().tucker_fiber_norms123(A.data_ptr(), _dt(A), _i64(dims), 3, w1.data_ptr(),
+                                                                w2.data_ptr(), w3.data_ptr(), C.byref(o)))
+    return w1, w2, w3
+
+
+def fiber_norms123_workspace_size(dims):
+    n = C.c_size_t(0)
+    _check("tucker_fiber_norms123_workspace_size",
+           lib().tucker_fiber_norms123_workspace_size(_i64(dims), len(dims), C.byref(n)))
+    return n.value
 
 
 def quantize_weights(w, prob="nearly_optimal", stream=None):

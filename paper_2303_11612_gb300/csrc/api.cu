@@ -277,6 +277,8 @@ struct Work {
     void* orth;
     double* w; uint64_t* W; void* samp; int64_t* idx; double* scale; void* Cp;
     double* w2;            // T-HOSVD with sampling: mode 2's fiber norms, formed beside mode 1's
+    double* w3;            // order 3: mode 3's, with the partials of the pass that forms all three
+    void* nscr;
     void* inter[2];
     void* Y; void* QY;     // half steps: T x L product and its orthonormal factor
     void* Gn;              // Strategy B: the I_n x I_n Gram matrix (FP32)
@@ -308,9 +310,14 @@ void carve(const Plan& p, Arena& a, Work& w) {
         w.scale = (double*)a.take(sizeof(double) * (size_t)p.maxT);
         w.Cp = a.take((size_t)p.maxIT * p.elem);
         w.w2 = p.st ? nullptr : (double*)a.take(sizeof(double) * (size_t)p.maxJ);
+        const bool all3 = !p.st && p.N == 3 && fiber_norms123_supported(p.dims[0]);
+        w.w3 = all3 ? (double*)a.take(sizeof(double) * (size_t)p.maxJ) : nullptr;
+        w.nscr = all3 ? a.take(fiber_norms123_scratch_bytes(p.dims[0], p.dims[1], p.dims[2])) : nullptr;
     } else {
         w.w = nullptr; w.W = nullptr; w.samp = nullptr; w.idx = nullptr; w.scale = nullptr; w.Cp = nullptr;
         w.w2 = nullptr;
+        w.w3 = nullptr;
+        w.nscr = nullptr;
     }
     w.Y = p.maxTL ? a.take((size_t)p.maxTL * p.elem) : nullptr;
     w.QY = p.maxTL ? a.take((size_t)p.maxTL * p.elem) : nullptr;
@@ -524,11 +531,18 @@ cudaError_t run_driver(const Plan& p, const T* A, const int32_t* ranks, int q, i
             cur = out;
         }
     } else {
-        // Algorithm 4 with the nearly-optimal probabilities: modes 1 and 2 sample the same
-        // tensor, so their fiber norms come from one pass over it
-        const double* pre[2] = {nullptr, nullptr};
-        if (prob == TUCKER_PROB_NEARLY_OPTIMAL && N >= 2 && p.m[0].T > 0 && p.m[1].T > 0 && w.w2 &&
-            fiber_norms12_supported(p.dims[0])) {
+        // Algorithm 4 with the nearly-optimal probabilities: every mode samples the same
+        // tensor, so an order-3 tensor's three modes take their fiber norms from one pass
+        // over it, and modes 1 and 2 of higher orders from one pass
+        const double* pre[3] = {nullptr, nullptr, nullptr};
+        if (prob == TUCKER_PROB_NEARLY_OPTIMAL && N == 3 && p.m[0].T > 0 && p.m[1].T > 0 && p.m[2].T > 0 && w.w3 &&
+            w.nscr) {
+            TK_TRY(launch_fiber_norms123<T>(A, p.dims[0], p.dims[1], p.dims[2], w.w, w.w2, w.w3, w.nscr, s));
+            pre[0] = w.w;
+            pre[1] = w.w2;
+            pre[2] = w.w3;
+        } else if (prob == TUCKER_PROB_NEARLY_OPTIMAL && N >= 2 && p.m[0].T > 0 && p.m[1].T > 0 && w.w2 &&
+                   fiber_norms12_supported(p.dims[0])) {
             TK_TRY(launch_fiber_norms12<T>(A, p.dims[0], p.dims[1], prod(p.dims, N) / (p.dims[0] * p.dims[1]), w.w,
                                            w.w2, s));
             pre[0] = w.w;
@@ -536,7 +550,7 @@ cudaError_t run_driver(const Plan& p, const T* A, const int32_t* ranks, int q, i
         }
         for (int n = 0; n < N; ++n)
             TK_TRY(factor_mode<T>(A, p.m[n], n, q, prob, seed, p.form, U[n], w,
-                                  sample_out ? sample_out[n] : nullptr, s, n < 2 ? pre[n] : nullptr));
+                                  sample_out ? sample_out[n] : nullptr, s, n < 3 ? pre[n] : nullptr));
         int64_t e[kMaxOrder];
         for (int n = 0; n < N; ++n) e[n] = p.dims[n];
         const T* cur = A;
@@ -1426,6 +1440,40 @@ tucker_status tucker_fiber_norms12(const void* A, tucker_dtype dt, const int64_t
     if (e == cudaErrorInvalidValue) return TUCKER_ERR_INVALID_ARG;
     if (e != cudaSuccess) return from_cuda(e);
     return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_fiber_norms123(const void* A, tucker_dtype dt, const int64_t* dims, int N, double* w1,
+                                    double* w2, double* w3, const tucker_opts* opts) {
+    Opts o;
+    tucker_status rs = read_opts(opts, o);
+    if (rs != TUCKER_OK) return rs;
+    if (N != 3 || !mode_args_ok(A, dims, N, 2) || !w1 || !w2 || !w3) return TUCKER_ERR_INVALID_ARG;
+    if (dt != TUCKER_F32 && dt != TUCKER_F64) return TUCKER_ERR_INVALID_ARG;
+    if (!fiber_norms123_supported(dims[0])) return TUCKER_ERR_UNSUPPORTED;
+    const size_t need = fiber_norms123_scratch_bytes(dims[0], dims[1], dims[2]);
+    Scratch sc;
+    void* scr = o.workspace;
+    if (scr) {
+        if (o.workspace_bytes < need) return TUCKER_ERR_INVALID_ARG;
+    } else {
+        rs = sc.get(need, o.stream);
+        if (rs != TUCKER_OK) return rs;
+        scr = sc.p;
+    }
+    const cudaError_t e =
+        dt == TUCKER_F32 ? launch_fiber_norms123<float>((const float*)A, dims[0], dims[1], dims[2], w1, w2, w3, scr,
+                                                        o.stream)
+                         : launch_fiber_norms123<double>((const double*)A, dims[0], dims[1], dims[2], w1, w2, w3, scr,
+                                                         o.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return sync_status(o.stream, nullptr);
+}
+
+tucker_status tucker_fiber_norms123_workspace_size(const int64_t* dims, int N, size_t* bytes) {
+    if (!dims || !bytes || N != 3 || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return TUCKER_ERR_INVALID_ARG;
+    if (!fiber_norms123_supported(dims[0])) return TUCKER_ERR_UNSUPPORTED;
+    *bytes = fiber_norms123_scratch_bytes(dims[0], dims[1], dims[2]);
+    return TUCKER_OK;
 }
 
 tucker_status tucker_fiber_norms(const void* A, tucker_dtype dt, const int64_t* dims, int N, int mode, double* w,

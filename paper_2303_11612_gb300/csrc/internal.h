@@ -138,6 +138,13 @@ cudaError_t launch_fiber_norms(const T* A, const ModeView& v, double* w, cudaStr
 // Mode-1 and mode-2 fiber norms in one pass over the tensor read as I1 x I2 x rest:
 // w1[i2 + I2 r] (the mode-1 fibers' order), w2[i1 + I1 r] (the mode-2 fibers'); I1 <= 1024.
 bool fiber_norms12_supported(int64_t I1);
+// Order-3 tensors: all three modes' fiber norms from one pass (norms123_kernel),
+// through partials in scratch (fiber_norms123_scratch_bytes), summed in order.
+bool fiber_norms123_supported(int64_t I1);
+size_t fiber_norms123_scratch_bytes(int64_t I1, int64_t I2, int64_t I3);
+template <typename T>
+cudaError_t launch_fiber_norms123(const T* A, int64_t I1, int64_t I2, int64_t I3, double* w1, double* w2,
+                                  double* w3, void* scratch, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fiber_norms12(const T* A, int64_t I1, int64_t I2, int64_t rest, double* w1, double* w2,
                                  cudaStream_t s);

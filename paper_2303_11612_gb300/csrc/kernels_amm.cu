@@ -154,6 +154,97 @@ __global__ void __launch_bounds__(kT) norms12_kernel(const T* __restrict__ A, in
     }
 }
 
+// All three modes' squared fiber norms of an order-3 tensor from one pass
+// (Algorithm 4 samples every mode of the same tensor). CTA (b, c) takes the
+// band of rows i_2 = b RB .. b RB + RB - 1 (RB = 8 RR: warp w owns rows
+// b RB + w + 8 r, r < RR) of the slabs i_3 of chunk c. Mode 1: a row's sum is
+// complete, formed as norms_contig forms it (bitwise equal where that takes a
+// warp per fiber). Mode 2: per slab, the band's column sums (each warp's rows
+// in order, then the warps in order) go to P2[b] (i_1 + I_1 i_3). Mode 3: each
+// entry's sum over the chunk's slabs, in order, kept in shared memory beside
+// the band, goes to P3[c] (i_1 + I_1 i_2). norms_merge_kernel then adds the
+// bands' and the chunks' partials in order. A warp issues all its rows' loads
+// of a slab before summing them.
+template <typename T, int NK, int RR>
+__global__ void __launch_bounds__(kT) norms123_kernel(const T* __restrict__ A, int64_t I1, int64_t I2, int64_t I3,
+                                                      int64_t SC, double* __restrict__ w1, NormAcc<T>* __restrict__ P2,
+                                                      NormAcc<T>* __restrict__ P3) {
+    constexpr int kW = kT / 32, RB = kW * RR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    NormAcc<T>* part = reinterpret_cast<NormAcc<T>*>(smem_raw);    // [kW][I1]
+    NormAcc<T>* m3 = part + kW * I1;                                // [RB][I1]: row warp + kW r at r kW + warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t b = blockIdx.x, c = blockIdx.y;
+    const int64_t s0 = c * SC, s1 = s0 + SC < I3 ? s0 + SC : I3;
+    for (int64_t e = threadIdx.x; e < RB * I1; e += kT) m3[e] = NormAcc<T>();
+    __syncthreads();
+    for (int64_t s = s0; s < s1; ++s) {
+        const T* slab = A + s * I1 * I2;
+        T x[RR][NK];
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const int64_t i2 = b * RB + warp + kW * r;
+            const T* row = slab + i2 * I1;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const int64_t i = lane + 32 * k;
+                x[r][k] = (i2 < I2 && i < I1) ? __ldg(row + i) : T(0);
+            }
+        }
+        NormAcc<T> col[NK];
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const int64_t i2 = b * RB + warp + kW * r;
+            if (i2 >= I2) break;                                     // the same for the whole warp
+            NormAcc<T>* m3r = m3 + (r * kW + warp) * I1;
+            NormAcc<T> rs;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                rs.add(x[r][k]);
+                col[k].add(x[r][k]);
+                const int64_t i = lane + 32 * k;
+                if (i < I1) {
+                    NormAcc<T> t = m3r[i];
+                    t.add(x[r][k]);
+                    m3r[i] = t;
+                }
+            }
+            rs.warp_reduce();
+            if (lane == 0) w1[i2 + I2 * s] = rs.value();
+        }
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const int64_t i = lane + 32 * k;
+            if (i < I1) part[warp * I1 + i] = col[k];
+        }
+        __syncthreads();
+        NormAcc<T>* out2 = P2 + b * (I1 * I3) + I1 * s;
+        for (int64_t i = threadIdx.x; i < I1; i += kT) {
+            NormAcc<T> t = part[i];
+            for (int q = 1; q < kW; ++q) NormPart<T>::merge(t, part[q * I1 + i]);
+            out2[i] = t;
+        }
+        __syncthreads();
+    }
+    NormAcc<T>* out3 = P3 + c * (I1 * I2);
+    for (int64_t e = threadIdx.x; e < RB * I1; e += kT) {
+        const int64_t slot = e / I1, i = e - slot * I1;
+        const int64_t i2 = b * RB + (slot % kW) + kW * (slot / kW);
+        if (i2 < I2) out3[i + I1 * i2] = m3[e];
+    }
+}
+
+// out[x] = the partials P[p count + x], p = 0 .. parts - 1, added in order.
+template <typename T>
+__global__ void __launch_bounds__(kT) norms_merge_kernel(const NormAcc<T>* __restrict__ P, int64_t parts,
+                                                         int64_t count, double* __restrict__ out) {
+    for (int64_t x = blockIdx.x * (int64_t)kT + threadIdx.x; x < count; x += (int64_t)gridDim.x * kT) {
+        NormAcc<T> t = P[x];
+        for (int64_t p = 1; p < parts; ++p) NormPart<T>::merge(t, P[p * count + x]);
+        out[x] = t.value();
+    }
+}
+
 // ---------------------------------------------------------------- integer weights
 __global__ void __launch_bounds__(kT) max_kernel(const double* __restrict__ w, int64_t J,
                                                  unsigned long long* __restrict__ out) {
@@ -388,6 +479,67 @@ cudaError_t launch_fiber_norms12(const T* A, int64_t I1, int64_t I2, int64_t res
     return cudaGetLastError();
 }
 
+namespace {
+// Bands of 8 RR rows (RR = 2 up to I_1 = 512, else 1); chunks of slabs so that
+// the grid holds about four CTAs per SM.
+struct N123Grid {
+    int rr;
+    int64_t nb, nc, sc;
+};
+N123Grid n123_grid(int64_t I1, int64_t I2, int64_t I3) {
+    N123Grid g;
+    g.rr = I1 <= 512 ? 2 : 1;
+    g.nb = (I2 + 8 * g.rr - 1) / (8 * g.rr);
+    int64_t nc = (4 * (int64_t)num_sms() + g.nb - 1) / g.nb;
+    nc = nc < 1 ? 1 : (nc > I3 ? I3 : nc);
+    if (nc > 65535) nc = 65535;
+    g.sc = (I3 + nc - 1) / nc;
+    g.nc = (I3 + g.sc - 1) / g.sc;
+    return g;
+}
+}  // namespace
+
+bool fiber_norms123_supported(int64_t I1) { return I1 >= 1 && I1 <= 1024; }
+
+size_t fiber_norms123_scratch_bytes(int64_t I1, int64_t I2, int64_t I3) {
+    if (!fiber_norms123_supported(I1) || I2 < 1 || I3 < 1) return 0;
+    const N123Grid g = n123_grid(I1, I2, I3);
+    const size_t p2 = ((size_t)g.nb * I1 * I3 * 8 + 255) & ~size_t(255);
+    return p2 + (size_t)g.nc * I1 * I2 * 8;           // NormAcc is 8 bytes for both types
+}
+
+template <typename T>
+cudaError_t launch_fiber_norms123(const T* A, int64_t I1, int64_t I2, int64_t I3, double* w1, double* w2,
+                                  double* w3, void* scratch, cudaStream_t s) {
+    static_assert(sizeof(NormAcc<T>) == 8, "partials hold 8 bytes per entry");
+    if (!fiber_norms123_supported(I1) || I2 < 1 || I3 < 1 || !scratch) return cudaErrorInvalidValue;
+    const double elems = (double)I1 * (double)I2 * (double)I3;
+    ProfScope prof(kKNorms, elems * sizeof(T), 6.0 * elems, s);
+    const N123Grid g = n123_grid(I1, I2, I3);
+    NormAcc<T>* P2 = reinterpret_cast<NormAcc<T>*>(scratch);
+    NormAcc<T>* P3 = reinterpret_cast<NormAcc<T>*>((char*)scratch + (((size_t)g.nb * I1 * I3 * 8 + 255) & ~size_t(255)));
+    const size_t smem = (size_t)(kT / 32) * (1 + g.rr) * (size_t)I1 * sizeof(NormAcc<T>);
+    const dim3 grid((unsigned)g.nb, (unsigned)g.nc);
+    auto run = [&](auto kernel) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kernel<<<grid, kT, smem, s>>>(A, I1, I2, I3, g.sc, w1, P2, P3);
+    };
+    if (I1 <= 128) run(norms123_kernel<T, 4, 2>);
+    else if (I1 <= 256) run(norms123_kernel<T, 8, 2>);
+    else if (I1 <= 512) run(norms123_kernel<T, 16, 2>);
+    else run(norms123_kernel<T, 32, 1>);
+    note_launch();
+    auto merge = [&](const NormAcc<T>* P, int64_t parts, int64_t count, double* out) {
+        const int64_t blocks = (count + kT - 1) / kT;
+        const int64_t grid1 = blocks < 4 * (int64_t)num_sms() ? blocks : 4 * (int64_t)num_sms();
+        norms_merge_kernel<T><<<(unsigned)(grid1 > 0 ? grid1 : 1), kT, 0, s>>>(P, parts, count, out);
+        note_launch();
+    };
+    merge(P2, g.nb, I1 * I3, w2);
+    merge(P3, g.nc, I1 * I2, w3);
+    return cudaGetLastError();
+}
+
 size_t quantize_scratch_bytes(int64_t) { return 256; }
 
 cudaError_t launch_quantize(const double* w, int64_t J, int prob, uint64_t* W, void* scratch, cudaStream_t s) {
@@ -463,6 +615,10 @@ cudaError_t launch_gather(const T* A, const ModeView& v, const int64_t* idx, con
     return cudaGetLastError();
 }
 
+template cudaError_t launch_fiber_norms123<float>(const float*, int64_t, int64_t, int64_t, double*, double*,
+                                                 double*, void*, cudaStream_t);
+template cudaError_t launch_fiber_norms123<double>(const double*, int64_t, int64_t, int64_t, double*, double*,
+                                                  double*, void*, cudaStream_t);
 template cudaError_t launch_fiber_norms12<float>(const float*, int64_t, int64_t, int64_t, double*, double*,
                                                 cudaStream_t);
 template cudaError_t launch_fiber_norms12<double>(const double*, int64_t, int64_t, int64_t, double*, double*,

@@ -98,3 +98,17 @@ def test_binding_flags_match_the_header():
     text = (Path(__file__).resolve().parents[1] / "include" / "tucker.h").read_text()
     flags = {m.group(1): int(m.group(2), 16) for m in re.finditer(r"#define TUCKER_FLAG_(\w+) (0x[0-9a-fA-F]+)u", text)}
     assert flags == {"ASYNC": B.FLAG_ASYNC, "WORKLIST": B.FLAG_WORKLIST}
+
+
+def test_norms123_workspace_size_arguments():
+    """tucker_fiber_norms123_workspace_size: order 3 only, I_1 <= 1024; the size
+    covers the band partials (8 bytes per mode-2 entry and band) at least."""
+    from paper_2303_11612_gb300 import _binding as B
+    n = B.fiber_norms123_workspace_size((400, 300, 7))
+    assert n >= 400 * 7 * 8 * ((300 + 15) // 16)
+    with pytest.raises(B.TuckerError) as e:
+        B.fiber_norms123_workspace_size((1100, 4, 4))
+    assert e.value.status == 6
+    with pytest.raises(B.TuckerError) as e:
+        B.fiber_norms123_workspace_size((10, 4, 4, 4))
+    assert e.value.status == 1

@@ -83,3 +83,51 @@ def test_algorithm4_nearly_optimal_matches_the_oracle(tk, dims, ranks, q):
         s = info["sigma_C"][n]
         if s[ranks[n] - 1] >= 1.5 * s[ranks[n]]:
             assert np.linalg.norm(Ud[n] @ Ud[n].T - Uo[n] @ Uo[n].T, 2) < 1e-4, n
+
+
+ORDER3 = [(400, 300, 7), (64, 33, 20), (1024, 5, 3), (129, 1, 9), (1, 40, 30), (513, 70, 2), (37, 50, 40),
+          (100, 80, 1), (7, 300, 129), (257, 17, 65)]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("dims", ORDER3)
+def test_norms123_against_the_oracle_and_the_per_mode_kernel(tk, dims, dtype):
+    """The three modes of an order-3 tensor from one pass (tucker_fiber_norms123):
+    each against the oracle's squared fiber norms; mode 1 bitwise the per-mode
+    kernel's where that takes a warp per fiber; modes 2 and 3 within 1e-12."""
+    A = synth.lowrank_noise(dims, [min(2, d) for d in dims], rel_noise=0.5, seed=sum(dims), dtype=dtype)
+    At = flat_dev(A)
+    w1, w2, w3 = tk.fiber_norms123(At, dims)
+    A64 = A.astype(np.float64)
+    for n, w in ((0, w1), (1, w2), (2, w3)):
+        want = ot.fiber_weights(ot.unfold(A64, n), ot.PROB_NEARLY_OPTIMAL)
+        got = w.cpu().numpy()
+        assert got.shape == want.shape
+        assert np.max(np.abs(got - want) / want) < 1e-11, n
+        one = tk.fiber_norms(At, dims, n).cpu().numpy()
+        if n == 0 and dims[0] >= 64:
+            assert np.array_equal(got, one)
+        else:
+            assert np.max(np.abs(got - one) / one) < 1e-12, n
+    # the same bytes through a caller workspace of exactly the stated size
+    nb = tk.fiber_norms123_workspace_size(dims)
+    scratch = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    again = tk.fiber_norms123(At, dims, workspace=scratch)
+    for a, b in zip(again, (w1, w2, w3)):
+        assert torch.equal(a, b)
+
+
+def test_norms123_refusals(tk):
+    from paper_2303_11612_gb300 import _binding as B
+    A = torch.zeros(1100 * 3 * 2, dtype=torch.float32, device="cuda")
+    with pytest.raises(B.TuckerError) as e:
+        tk.fiber_norms123(A, (1100, 3, 2))
+    assert e.value.status == 6
+    with pytest.raises((B.TuckerError, ValueError)):
+        tk.fiber_norms123(A, (1100, 3, 1, 2))
+    dims = (40, 30, 20)
+    A = flat_dev(synth.lowrank_noise(dims, (2, 2, 2), seed=3))
+    small = torch.empty(tk.fiber_norms123_workspace_size(dims) - 8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.TuckerError) as e:
+        tk.fiber_norms123(A, dims, workspace=small)
+    assert e.value.status == 1
