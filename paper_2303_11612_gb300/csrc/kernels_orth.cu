@@ -797,6 +797,54 @@ __host__ __device__ inline XLayout xlayout(int L, int R, int elem) {
 }
 
 // Grid of Gram CTAs over Q1 (kXT threads each). The last CTA: Cholesky
+// Entries (scalars S) from a back-substitution stage to its U_M (T, [R][L]).
+__host__ __device__ inline size_t bs_um_offset(int L) { return ((size_t)packed_size(L) + (size_t)L + 1) & ~size_t(1); }
+
+// W(:, c0 .. c0 + kBsCols - 1) = R2^-1 U_M(:, ...) by one warp: lane q keeps
+// u_k - sum_{l' > l} R2_kl' w_l' for the rows k = q + 32 m (m < kBsRows, so
+// L <= 128); row l is finished by its lane, broadcast, and subtracted from
+// every row above it, so each row costs one dependent step, with the group's
+// columns in flight together.
+template <typename T>
+__device__ __forceinline__ void backsub_group(const T* __restrict__ UM, const typename SmallScalar<T>::type* Rf,
+                                              const typename SmallScalar<T>::type* dinv, int L, int R,
+                                              typename SmallScalar<T>::type* __restrict__ Wout, int c0, int lane) {
+    using S = typename SmallScalar<T>::type;
+    using F = Sc<S>;
+    S acc[kBsCols][kBsRows];
+#pragma unroll
+    for (int c = 0; c < kBsCols; ++c)
+#pragma unroll
+        for (int m = 0; m < kBsRows; ++m) {
+            const int k = lane + 32 * m;
+            acc[c][m] = (c0 + c < R && k < L) ? to_s<S>(UM[(size_t)(c0 + c) * L + k]) : F::zero();
+        }
+    for (int l = L - 1; l >= 0; --l) {
+        const int src = l & 31, ml = l >> 5;
+        const S d = dinv[l];
+        S rkl[kBsRows];                                      // R2_kl for this lane's rows above l
+#pragma unroll
+        for (int m = 0; m < kBsRows; ++m) {
+            const int k = lane + 32 * m;
+            rkl[m] = (32 * m < l && k < l) ? Rf[packed_index(k, l, L)] : F::zero();
+        }
+#pragma unroll
+        for (int c = 0; c < kBsCols; ++c) {
+            S v = acc[c][0];
+#pragma unroll
+            for (int m = 1; m < kBsRows; ++m)
+                if (ml == m) v = acc[c][m];
+            const S w = shfl_s(v * d, src);
+            if (lane == src && c0 + c < R) Wout[(size_t)(c0 + c) * L + l] = w;
+#pragma unroll
+            for (int m = 0; m < kBsRows; ++m) {
+                if (32 * m >= l) break;                        // the same for the whole warp
+                if (lane + 32 * m < l) acc[c][m] = F::fma(-rkl[m], w, acc[c][m]);
+            }
+        }
+    }
+}
+
 // Q1^T Q1 = R2^T R2, M = R2 P with P = prev[nprev-1] ... prev[0] (packed
 // factors fstride apart; prev[nprev-1] is R1), pivoted QR of M^T, Jacobi on
 // R^T, U_M (rounding-level columns re-orthogonalised) and W = R2^-1 U_M for the
@@ -808,7 +856,8 @@ __device__ __forceinline__ void extract_body(const T* __restrict__ X, int64_t I,
                                              typename SmallScalar<T>::type* __restrict__ partial, unsigned* ticket,
                                              const typename SmallScalar<T>::type* __restrict__ prev, size_t fstride,
                                              int nprev, int R, typename SmallScalar<T>::type* __restrict__ Wout,
-                                             int* status, int bid, int nblk) {
+                                             int* status, int bid, int nblk,
+                                             typename SmallScalar<T>::type* __restrict__ stage = nullptr) {
     using S = typename SmallScalar<T>::type;
     using F = Sc<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1027,45 +1076,19 @@ __device__ __forceinline__ void extract_body(const T* __restrict__ X, int64_t I,
         for (int a = tid; a < L; a += kXT) u[a] *= f;
         __syncthreads();
     }
-    // W(:, r) = R2^-1 U_M(:, r): back-substitution, one warp per group of
-    // kBsCols columns. Lane q keeps u_k - sum_{l' > l} R2_kl' w_l' for the rows
-    // k = q + 32 m (m < kBsRows, so L <= 128); row l is finished by its lane,
-    // broadcast, and subtracted from every row above it, so each row costs one
-    // dependent step, with the group's columns in flight together.
-    for (int c0 = warp * kBsCols; c0 < R; c0 += nwarps * kBsCols) {
-        S acc[kBsCols][kBsRows];
-#pragma unroll
-        for (int c = 0; c < kBsCols; ++c)
-#pragma unroll
-            for (int m = 0; m < kBsRows; ++m) {
-                const int k = lane + 32 * m;
-                acc[c][m] = (c0 + c < R && k < L) ? to_s<S>(UM[(size_t)(c0 + c) * L + k]) : F::zero();
-            }
-        for (int l = L - 1; l >= 0; --l) {
-            const int src = l & 31, ml = l >> 5;
-            const S d = dinv[l];
-            S rkl[kBsRows];                                      // R2_kl for this lane's rows above l
-#pragma unroll
-            for (int m = 0; m < kBsRows; ++m) {
-                const int k = lane + 32 * m;
-                rkl[m] = (32 * m < l && k < l) ? Rf[packed_index(k, l, L)] : F::zero();
-            }
-#pragma unroll
-            for (int c = 0; c < kBsCols; ++c) {
-                S v = acc[c][0];
-#pragma unroll
-                for (int m = 1; m < kBsRows; ++m)
-                    if (ml == m) v = acc[c][m];
-                const S w = shfl_s(v * d, src);
-                if (lane == src && c0 + c < R) Wout[(size_t)(c0 + c) * L + l] = w;
-#pragma unroll
-                for (int m = 0; m < kBsRows; ++m) {
-                    if (32 * m >= l) break;                        // the same for the whole warp
-                    if (lane + 32 * m < l) acc[c][m] = F::fma(-rkl[m], w, acc[c][m]);
-                }
-            }
-        }
+    // W(:, r) = R2^-1 U_M(:, r) (backsub_group): with a stage, R2, 1/R2_kk and U_M
+    // go to global memory and backsub_kernel runs the column groups on CTAs of
+    // their own (the steps are serial and issue-bound on one SM); else here, one
+    // warp per group
+    if (stage) {
+        const int np = (int)packed_size(L);
+        for (int p = tid; p < np; p += kXT) stage[p] = Rf[p];
+        for (int k = tid; k < L; k += kXT) stage[np + k] = dinv[k];
+        T* um = reinterpret_cast<T*>(stage + bs_um_offset(L));
+        for (int e = tid; e < L * R; e += kXT) um[e] = UM[e];
+        return;
     }
+    for (int c0 = warp * kBsCols; c0 < R; c0 += nwarps * kBsCols) backsub_group<T>(UM, Rf, dinv, L, R, Wout, c0, lane);
 }
 
 // U(:, r) = X W(:, r) in paired precision, one thread per entry of U.
@@ -1505,8 +1528,23 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
                                                       const typename SmallScalar<T>::type* __restrict__ prev,
                                                       size_t fstride, int nprev, int R,
                                                       typename SmallScalar<T>::type* __restrict__ Wout,
-                                                      int* status) {
-    extract_body<T>(X, I, L, rows, partial, ticket, prev, fstride, nprev, R, Wout, status, blockIdx.x, gridDim.x);
+                                                      int* status, typename SmallScalar<T>::type* __restrict__ stage) {
+    extract_body<T>(X, I, L, rows, partial, ticket, prev, fstride, nprev, R, Wout, status, blockIdx.x, gridDim.x,
+                    stage);
+}
+// The back-substitution of a staged extraction: column group blockIdx.x on one
+// warp, R2 and 1/R2_kk copied to shared memory first.
+template <typename T>
+__global__ void __launch_bounds__(32) backsub_kernel(const typename SmallScalar<T>::type* __restrict__ stage, int L,
+                                                     int R, typename SmallScalar<T>::type* __restrict__ Wout) {
+    using S = typename SmallScalar<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* rf = reinterpret_cast<S*>(smem_raw);
+    const int np = (int)packed_size(L);
+    for (int p = threadIdx.x; p < np + L; p += 32) rf[p] = stage[p];
+    __syncwarp();
+    backsub_group<T>(reinterpret_cast<const T*>(stage + bs_um_offset(L)), rf, rf + np, L, R, Wout,
+                     (int)blockIdx.x * kBsCols, (int)threadIdx.x);
 }
 template <typename T>
 __global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ X, int64_t I, int L, int R,
@@ -1620,11 +1658,12 @@ bool orth_supported(const OrthPlan& p, int R, int elem) {
            8 * packed_size(p.L) <= kSmemCap && finish_smem(R, elem, p.I) <= kSmemCap;
 }
 
+// partials | flag and ticket | W | back-substitution stage (R2, 1/R2_kk, U_M)
 size_t orth_scratch_bytes(const OrthPlan& p, int elem_size) {
-    (void)elem_size;
     const size_t np = packed_size(p.L);
     const size_t LL = (size_t)p.L * p.L;
-    return ((8 * np * (size_t)p.gram_blocks + 255) & ~size_t(255)) + 256 + 8 * LL + 512;
+    return ((8 * np * (size_t)p.gram_blocks + 255) & ~size_t(255)) + 256 + 8 * LL + 512 +
+           8 * bs_um_offset(p.L) + (size_t)(elem_size > 8 ? elem_size : 8) * LL;
 }
 
 struct OrthScratch {
@@ -1632,6 +1671,7 @@ struct OrthScratch {
     int* flag;
     unsigned* ticket;
     void* W;       // R^-1 of a CholeskyQR pass (packed), then the extraction's W (L x R)
+    void* bs;      // the extraction's back-substitution stage
 };
 static OrthScratch carve(const OrthPlan& p, void* scratch) {
     OrthScratch s;
@@ -1643,6 +1683,8 @@ static OrthScratch carve(const OrthPlan& p, void* scratch) {
     s.ticket = reinterpret_cast<unsigned*>(b + 64);
     b += 256;
     s.W = b;
+    b += 8 * (size_t)p.L * p.L + 512;
+    s.bs = b;
     return s;
 }
 
@@ -1687,7 +1729,12 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
     cudaFuncSetAttribute(extract_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
     cudaMemsetAsync(sc.flag, 0, 128, s);
     extract_kernel<T><<<p.gram_blocks, kXT, xsm, s>>>(Q1, p.I, L, rows, (S*)sc.partial, sc.ticket,
-                                                      (const S*)factors, slot, nprev + 1, R, (S*)sc.W, status);
+                                                      (const S*)factors, slot, nprev + 1, R, (S*)sc.W, status,
+                                                      (S*)sc.bs);
+    note_launch();
+    const size_t bsm = sizeof(S) * (packed_size(L) + (size_t)L);
+    cudaFuncSetAttribute(backsub_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+    backsub_kernel<T><<<(unsigned)((R + kBsCols - 1) / kBsCols), 32, bsm, s>>>((const S*)sc.bs, L, R, (S*)sc.W);
     note_launch();
     int64_t ublocks = (p.I * R + kT - 1) / kT;
     if (ublocks > 4 * 1024) ublocks = 4 * 1024;
