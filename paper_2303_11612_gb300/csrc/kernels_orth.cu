@@ -291,7 +291,8 @@ __device__ __forceinline__ void gram_chol_body(const T* __restrict__ X, int64_t 
                                                typename SmallScalar<T>::type* __restrict__ partial, unsigned* ticket,
                                                typename SmallScalar<T>::type* __restrict__ R,
                                                typename SmallScalar<T>::type* __restrict__ Rinv, int* status,
-                                               int bid, int nblk) {
+                                               int bid, int nblk,
+                                               typename SmallScalar<T>::type* __restrict__ stage = nullptr) {
     using S = typename SmallScalar<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     gram_partial<T, S>(X, I, L, rows, partial, smem_raw, bid);
@@ -302,6 +303,12 @@ __device__ __forceinline__ void gram_chol_body(const T* __restrict__ X, int64_t 
     S* RT = W + np;
     S* dinv = RT + np;
     reduce_cholesky<T, S>(partial, nblk, L, I, G, W, dinv, reinterpret_cast<int*>(RT), ticket, status);
+    if (stage) {
+        // R^-1 by tri_inverse_kernel: rows on warps of their own CTAs
+        for (int p = threadIdx.x; p < np; p += blockDim.x) R[p] = W[p];
+        for (int k = threadIdx.x; k < L; k += blockDim.x) stage[k] = dinv[k];
+        return;
+    }
     upper_inverse<S>(W, dinv, L, RT, G);
     for (int p = threadIdx.x; p < np; p += blockDim.x) {
         R[p] = W[p];
@@ -1512,8 +1519,51 @@ template <typename T>
 __global__ void __launch_bounds__(kST) gram_chol_kernel(const T* __restrict__ X, int64_t I, int L, int rows,
                                                        typename SmallScalar<T>::type* __restrict__ partial,
                                                        unsigned* ticket, typename SmallScalar<T>::type* __restrict__ R,
-                                                       typename SmallScalar<T>::type* __restrict__ Rinv, int* status) {
-    gram_chol_body<T>(X, I, L, rows, partial, ticket, R, Rinv, status, blockIdx.x, gridDim.x);
+                                                       typename SmallScalar<T>::type* __restrict__ Rinv, int* status,
+                                                       typename SmallScalar<T>::type* __restrict__ stage) {
+    gram_chol_body<T>(X, I, L, rows, partial, ticket, R, Rinv, status, blockIdx.x, gridDim.x, stage);
+}
+// R^-1 of the packed upper-triangular R (1/R_kk in dinv), row i on warp i of the
+// grid: x_ij = (delta_ij - sum_{k<j} x_ik R_kj) / R_jj, the sum accumulated in
+// increasing k by the lane that owns column j, as upper_inverse forms it (the
+// same operations in the same order, so the same bits), with x_ij broadcast
+// from its lane once final. R and dinv are copied to shared memory first.
+template <typename T>
+__global__ void __launch_bounds__(128) tri_inverse_kernel(const typename SmallScalar<T>::type* __restrict__ R,
+                                                          const typename SmallScalar<T>::type* __restrict__ dinv_g,
+                                                          int L, typename SmallScalar<T>::type* __restrict__ Ri) {
+    using S = typename SmallScalar<T>::type;
+    using F = Sc<S>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* rs = reinterpret_cast<S*>(smem_raw);
+    const int np = (int)packed_size(L);
+    S* dv = rs + np;
+#pragma unroll 4
+    for (int p = threadIdx.x; p < np + L; p += 128) {
+        if (p < np) rs[p] = R[p];
+        else dv[p - np] = dinv_g[p - np];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int i = (int)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (i >= L) return;                                   // a whole warp
+    S acc[kBsRows];
+#pragma unroll
+    for (int m = 0; m < kBsRows; ++m) acc[m] = F::zero();
+    for (int j = i; j < L; ++j) {
+        const int src = j & 31, mj = j >> 5;
+        S a = acc[0];
+#pragma unroll
+        for (int m = 1; m < kBsRows; ++m)
+            if (mj == m) a = acc[m];
+        const S x = shfl_s(((i == j ? F::one() : F::zero()) - a) * dv[j], src);
+        if (lane == src) Ri[packed_index(i, j, L)] = x;
+#pragma unroll
+        for (int m = 0; m < kBsRows; ++m) {
+            const int k = lane + 32 * m;
+            if (k > j && k < L) acc[m] = F::fma(x, rs[packed_index(j, k, L)], acc[m]);
+        }
+    }
 }
 template <typename T>
 __global__ void __launch_bounds__(kT) apply_rinv_kernel(const T* __restrict__ X, int64_t I, int L,
@@ -1535,16 +1585,19 @@ __global__ void __launch_bounds__(kXT, 1) extract_kernel(const T* __restrict__ X
 // The back-substitution of a staged extraction: column group blockIdx.x on one
 // warp, R2 and 1/R2_kk copied to shared memory first.
 template <typename T>
-__global__ void __launch_bounds__(32) backsub_kernel(const typename SmallScalar<T>::type* __restrict__ stage, int L,
-                                                     int R, typename SmallScalar<T>::type* __restrict__ Wout) {
+__global__ void __launch_bounds__(128) backsub_kernel(const typename SmallScalar<T>::type* __restrict__ stage, int L,
+                                                      int R, typename SmallScalar<T>::type* __restrict__ Wout) {
     using S = typename SmallScalar<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* rf = reinterpret_cast<S*>(smem_raw);
     const int np = (int)packed_size(L);
-    for (int p = threadIdx.x; p < np + L; p += 32) rf[p] = stage[p];
-    __syncwarp();
-    backsub_group<T>(reinterpret_cast<const T*>(stage + bs_um_offset(L)), rf, rf + np, L, R, Wout,
-                     (int)blockIdx.x * kBsCols, (int)threadIdx.x);
+#pragma unroll 4
+    for (int p = threadIdx.x; p < np + L; p += 128) rf[p] = stage[p];
+    __syncthreads();
+    const int c0 = ((int)blockIdx.x * 4 + (int)(threadIdx.x >> 5)) * kBsCols;
+    if (c0 >= R) return;                                  // a whole warp
+    backsub_group<T>(reinterpret_cast<const T*>(stage + bs_um_offset(L)), rf, rf + np, L, R, Wout, c0,
+                     (int)(threadIdx.x & 31));
 }
 template <typename T>
 __global__ void __launch_bounds__(kT) form_u_kernel(const T* __restrict__ X, int64_t I, int L, int R,
@@ -1706,7 +1759,11 @@ cudaError_t launch_cholqr(const T* X, T* Q, const OrthPlan& p, double* factor, v
     if (ablocks > 4 * 1024) ablocks = 4 * 1024;
     // R^-1 goes to the W block, which the extraction writes only after this pass
     gram_chol_kernel<T><<<p.gram_blocks, kST, gsm, s>>>(X, p.I, L, rows, (S*)sc.partial, sc.ticket, (S*)factor,
-                                                        (S*)sc.W, status);
+                                                        (S*)sc.W, status, (S*)sc.bs);
+    note_launch();
+    const size_t ism = sizeof(S) * (packed_size(L) + (size_t)L);
+    cudaFuncSetAttribute(tri_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+    tri_inverse_kernel<T><<<(unsigned)((L + 3) / 4), 128, ism, s>>>((const S*)factor, (const S*)sc.bs, L, (S*)sc.W);
     note_launch();
     apply_rinv_kernel<T><<<(unsigned)ablocks, kT, asm_, s>>>(X, p.I, L, (const S*)sc.W, Q);
     note_launch();
@@ -1734,7 +1791,8 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
     note_launch();
     const size_t bsm = sizeof(S) * (packed_size(L) + (size_t)L);
     cudaFuncSetAttribute(backsub_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
-    backsub_kernel<T><<<(unsigned)((R + kBsCols - 1) / kBsCols), 32, bsm, s>>>((const S*)sc.bs, L, R, (S*)sc.W);
+    backsub_kernel<T><<<(unsigned)((R + 4 * kBsCols - 1) / (4 * kBsCols)), 128, bsm, s>>>((const S*)sc.bs, L, R,
+                                                                                          (S*)sc.W);
     note_launch();
     int64_t ublocks = (p.I * R + kT - 1) / kT;
     if (ublocks > 4 * 1024) ublocks = 4 * 1024;
