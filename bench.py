@@ -24,7 +24,9 @@ four requests of each variant per step), beside the host link's measured rate,
 the rate it bounds and the same steps' copies alone.
 
 Secondary lines, each with its own oracle check: the 400^3 batch (low-rank
-and Hilbert tensors, q = 1 / 2, AMM c = 4000; 32 distinct buffers), the 96^4
+and Hilbert tensors, q = 1 / 2, AMM c = 4000; 32 distinct buffers), the same
+low-rank tensors in the related form (Algorithm 7), fixed-precision ranks
+(Problem 2) on a 256^3 tensor beside the oracle's ranks, the 96^4
 decaying-core tensor (q = 2), the FP64 100^3 T-HOSVD, randomized T-HOSVD;
 the latency of one decomposition alone (headline tensor and 400^3, headline
 arithmetic and FP32); and the serving stream (2000 requests of orders 3 and 4, extents up to 256,
@@ -81,6 +83,14 @@ WORKLOADS = {
                   dict(name="hilbert_q2", gen="hilbert", q=2, c=0, prob="uniform", rank_deficient=True),
                   dict(name="hilbert_q1_amm4000_uniform", gen="hilbert", q=1, c=4000, prob="uniform",
                        rank_deficient=True)]),
+    # Algorithms 6/7 (the related forms): P_n from the paper-form sketch by CholeskyQR2, one more power
+    # step, the leading vectors of the L x L matrix P^T A A^T P, Q_n = P U
+    "cube400_related": dict(
+        desc="randomized ST-HOSVD of 400^3 FP32 low-rank tensors (Tucker core 20^3 + 1e-2 noise) in the related "
+             "form (Algorithm 7), R=20 P=10 q=1",
+        which="ST", dims=(400, 400, 400), ranks=(20, 20, 20), P=10, dtype="f32", copies=16, form="related",
+        forms=["bf16x1", "fp32"],
+        variants=[dict(name="lowrank_q1_related", gen="lowrank", q=1, c=0, prob="uniform")]),
     "quartic96": dict(
         desc="randomized ST-HOSVD of 96^4 FP32 tensors with a decaying 16^4 core (entries N(0,1) 0.8^(i1+i2+i3+i4), "
              "no noise), R=16 P=8 q=2",
@@ -454,6 +464,38 @@ def fusion_bench(tk, torch, stream):
                                               "(one pass over the tensor, then the partials summed)",
                                   "fused_ms": all3, "per_mode_ms": apart3, "fused_gbs": gb / (all3 * 1e-3),
                                   "speedup": apart3 / all3}}
+
+
+def adaptive_bench(tk, torch, precs):
+    """Fixed-precision ranks (Problem 2, tucker_rsthosvd_adaptive) on a 256^3 FP32 low-rank tensor (Tucker
+    core 16^3 + 1e-2 noise) at eps = 2e-2: ranks and relative error beside the oracle's on the same bytes,
+    and the call's wall time (it decides each mode's rank on the host between modes), 2 warm-up calls,
+    then the median of 7."""
+    import numpy as np
+    import synth
+    from oracle import tucker as ot
+    dims, eps = (256, 256, 256), 2e-2
+    host = synth.flat(synth.lowrank_noise(dims, (16, 16, 16), rel_noise=1e-2, seed=SEED))
+    A = torch.from_numpy(host).cuda()
+    A64 = synth.from_flat(host, dims).astype(np.float64)
+    t0 = time.perf_counter()
+    Qo, Go, ro = ot.rsthosvd_adaptive(A64, eps, q=1, seed=SEED)
+    t_or = time.perf_counter() - t0
+    out = {"workload": f"fixed-precision ST-HOSVD (Problem 2) of a 256^3 FP32 low-rank tensor, eps={eps}, q=1, "
+                       f"L0=8", "oracle_ranks": [int(r) for r in ro],
+           "oracle_rel_error": ot.relative_error(A64, Qo, Go), "oracle_seconds": t_or}
+    for prec in precs:
+        ts, res = [], None
+        for it in range(9):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            res = tk.rsthosvd_adaptive(A, dims, eps, q=1, seed=SEED, prec=prec, want_rel_error=True)
+            ts.append(time.perf_counter() - t1)
+        U, G, ranks, re = res
+        ms = 1e3 * sorted(ts[2:])[len(ts[2:]) // 2]
+        out[prec] = {"ms_per_call": ms, "decomps_per_s": 1e3 / ms, "ranks": [int(r) for r in ranks],
+                     "rel_error": re, "ranks_equal_oracle": [int(r) for r in ranks] == [int(r) for r in ro]}
+    return out
 
 
 # ---------------------------------------------------------------- ranks
@@ -903,7 +945,7 @@ def main():
     # ---- secondary workloads
     secondary = {}
     if not args.no_secondary:
-        for name in ("video1024_range", "cube400", "quartic96", "fp64cube100"):
+        for name in ("video1024_range", "cube400", "cube400_related", "quartic96", "fp64cube100"):
             try:
                 Wn = WORKLOADS[name]
                 Pn, rn = b.workload_line(name, Wn.get("forms", forms), max(3, args.steps // 2))
@@ -954,6 +996,10 @@ def main():
             secondary["fusions"] = fusion_bench(tk, torch, b.main_s)
         except Exception as exc:  # noqa: BLE001
             secondary["fusions"] = {"error": str(exc)[:300]}
+        try:
+            secondary["adaptive_ranks"] = adaptive_bench(tk, torch, list(dict.fromkeys([head, "fp32"])))
+        except Exception as exc:  # noqa: BLE001
+            secondary["adaptive_ranks"] = {"error": str(exc)[:300]}
 
     serving = None
     if not args.no_serving:
