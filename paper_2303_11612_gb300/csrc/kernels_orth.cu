@@ -1741,6 +1741,21 @@ static OrthScratch carve(const OrthPlan& p, void* scratch) {
     return s;
 }
 
+// Whether the serial steps whose rows or columns are independent (the
+// triangular inverse, the back-substitution) run on CTAs of their own, which
+// shortens a call that runs alone, or inside the one-CTA kernels: a stream
+// being captured belongs to a batch graph, where many decompositions run at
+// once and the extra launches cost more than the shorter chain saves
+// (measured). Both give the same bits.
+static bool split_serial(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return cs == cudaStreamCaptureStatusNone;
+}
+
 template <typename T>
 cudaError_t launch_cholqr(const T* X, T* Q, const OrthPlan& p, double* factor, void* scratch, int* status,
                           cudaStream_t s) {
@@ -1758,13 +1773,17 @@ cudaError_t launch_cholqr(const T* X, T* Q, const OrthPlan& p, double* factor, v
     int64_t ablocks = (p.I * L + kT - 1) / kT;
     if (ablocks > 4 * 1024) ablocks = 4 * 1024;
     // R^-1 goes to the W block, which the extraction writes only after this pass
+    const bool split = split_serial(s);
     gram_chol_kernel<T><<<p.gram_blocks, kST, gsm, s>>>(X, p.I, L, rows, (S*)sc.partial, sc.ticket, (S*)factor,
-                                                        (S*)sc.W, status, (S*)sc.bs);
+                                                        (S*)sc.W, status, split ? (S*)sc.bs : nullptr);
     note_launch();
-    const size_t ism = sizeof(S) * (packed_size(L) + (size_t)L);
-    cudaFuncSetAttribute(tri_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
-    tri_inverse_kernel<T><<<(unsigned)((L + 3) / 4), 128, ism, s>>>((const S*)factor, (const S*)sc.bs, L, (S*)sc.W);
-    note_launch();
+    if (split) {
+        const size_t ism = sizeof(S) * (packed_size(L) + (size_t)L);
+        cudaFuncSetAttribute(tri_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+        tri_inverse_kernel<T><<<(unsigned)((L + 3) / 4), 128, ism, s>>>((const S*)factor, (const S*)sc.bs, L,
+                                                                       (S*)sc.W);
+        note_launch();
+    }
     apply_rinv_kernel<T><<<(unsigned)ablocks, kT, asm_, s>>>(X, p.I, L, (const S*)sc.W, Q);
     note_launch();
     return cudaGetLastError();
@@ -1785,15 +1804,18 @@ cudaError_t launch_extract(const T* X, T* Q1, const OrthPlan& p, double* factors
     const size_t xsm = extract_smem(p, R, sizeof(T));
     cudaFuncSetAttribute(extract_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm);
     cudaMemsetAsync(sc.flag, 0, 128, s);
+    const bool split = split_serial(s);
     extract_kernel<T><<<p.gram_blocks, kXT, xsm, s>>>(Q1, p.I, L, rows, (S*)sc.partial, sc.ticket,
                                                       (const S*)factors, slot, nprev + 1, R, (S*)sc.W, status,
-                                                      (S*)sc.bs);
+                                                      split ? (S*)sc.bs : nullptr);
     note_launch();
-    const size_t bsm = sizeof(S) * (packed_size(L) + (size_t)L);
-    cudaFuncSetAttribute(backsub_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
-    backsub_kernel<T><<<(unsigned)((R + 4 * kBsCols - 1) / (4 * kBsCols)), 128, bsm, s>>>((const S*)sc.bs, L, R,
-                                                                                          (S*)sc.W);
-    note_launch();
+    if (split) {
+        const size_t bsm = sizeof(S) * (packed_size(L) + (size_t)L);
+        cudaFuncSetAttribute(backsub_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+        backsub_kernel<T><<<(unsigned)((R + 4 * kBsCols - 1) / (4 * kBsCols)), 128, bsm, s>>>((const S*)sc.bs, L,
+                                                                                              R, (S*)sc.W);
+        note_launch();
+    }
     int64_t ublocks = (p.I * R + kT - 1) / kT;
     if (ublocks > 4 * 1024) ublocks = 4 * 1024;
     form_u_kernel<T><<<(unsigned)ublocks, kT, 0, s>>>(Q1, p.I, L, R, (const S*)sc.W, U);
